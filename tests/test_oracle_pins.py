@@ -1,0 +1,343 @@
+"""Pins of the FP64 oracle to facts fixed outside itself (CPU only).
+
+Each test checks the oracle against a closed form, a brute-force computation
+written independently here, an invariant, or a number printed in the paper,
+so that a dropped term, a wrong sign/index or a transposed operand anywhere
+in the oracle fails at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from numpy.polynomial.legendre import leggauss
+
+import oracle
+import scenegen as sg
+
+C0 = sg.C0
+
+
+# ---------------------------------------------------------------------------
+# facet integral J(w)
+# ---------------------------------------------------------------------------
+def _quad_J(tri, w, n=240):
+    """Brute force: tensor Gauss-Legendre on the Duffy-collapsed square."""
+    v0, v1, v2 = tri.reshape(3, 3)
+    c = (v0 + v1 + v2) / 3.0
+    x, wx = leggauss(n)
+    x = 0.5 * (x + 1.0)
+    wx = 0.5 * wx
+    S, T = np.meshgrid(x, x, indexing="ij")
+    W = np.outer(wx, wx)
+    P = v0 + S[..., None] * (v1 - v0) + (S * T)[..., None] * (v2 - v1)
+    jac = S * np.linalg.norm(np.cross(v1 - v0, v2 - v1))
+    return np.sum(W * jac * np.exp(1j * ((P - c) @ w)))
+
+
+def test_J_at_zero_is_area():
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        tri = rng.normal(size=9)
+        v = tri.reshape(3, 3)
+        A = 0.5 * np.linalg.norm(np.cross(v[1] - v[0], v[2] - v[0]))
+        J = oracle.facet_integral(tri, np.zeros(3))
+        assert abs(J - A) <= 1e-14 * A
+
+
+@pytest.mark.parametrize("scale", [1e-4, 2e-2, 1.0, 40.0, 400.0, 3000.0])
+def test_J_matches_quadrature(scale):
+    """Random triangles, wave vectors on both sides of the series/edge-form
+    switch (|w_t| * diameter = 1e-3) and up to ~100 rad across the facet."""
+    rng = np.random.default_rng(int(scale * 1000) % 2**31)
+    for _ in range(4):
+        tri = rng.normal(size=9) * 0.03
+        w = rng.normal(size=3) * scale
+        J = oracle.facet_integral(tri, w)
+        ref = _quad_J(tri, w)
+        assert abs(J - ref) <= 1e-11 * max(abs(ref), 1e-30) + 1e-18, (J, ref)
+
+
+def test_J_across_series_switch_is_continuous():
+    tri = np.array([0.0, 0.0, 0.0, 0.05, 0.0, 0.0, 0.01, 0.04, 0.0])
+    diam = max(np.linalg.norm(tri[3:6] - tri[0:3]), np.linalg.norm(tri[6:9] - tri[3:6]),
+               np.linalg.norm(tri[0:3] - tri[6:9]))
+    d = np.array([0.6, 0.8, 0.0])
+    for s in (0.999e-3, 1.001e-3):
+        w = d * s / diam + np.array([0.0, 0.0, 500.0])      # big normal part
+        ref = _quad_J(tri, w)
+        assert abs(oracle.facet_integral(tri, w) - ref) <= 1e-12 * abs(ref)
+
+
+def test_J_two_triangle_rectangle_closed_form():
+    """Sum over the two triangles of a rectangle a x b equals
+    ab sinc(w_x a/2) sinc(w_y b/2) exp(j w.centre)."""
+    a, b = 0.3, 0.2
+    v = np.array([[0, 0, 0], [a, 0, 0], [a, b, 0], [0, b, 0]], float) + [0.1, -0.2, 0.3]
+    tris = [np.concatenate([v[0], v[1], v[2]]), np.concatenate([v[0], v[2], v[3]])]
+    rng = np.random.default_rng(3)
+    sinc = lambda x: np.sinc(x / np.pi)
+    for _ in range(6):
+        w = rng.normal(size=3) * 80.0
+        tot = 0
+        for t in tris:
+            c = t.reshape(3, 3).mean(0)
+            tot += oracle.facet_integral(t, w) * np.exp(1j * w @ c)
+        centre = v.mean(0)
+        ref = a * b * sinc(w[0] * a / 2) * sinc(w[1] * b / 2) * np.exp(1j * w @ centre)
+        assert abs(tot - ref) <= 1e-12 * a * b
+
+
+# ---------------------------------------------------------------------------
+# RCS closed forms (physical optics)
+# ---------------------------------------------------------------------------
+def _plate_world(n=10, size=1.0, rot=np.eye(3)):
+    sc = sg.Scene([sg.plate(size, size, n)], [sg.Instance(0, (0, 0, 0), rot, (0, 0, 0))],
+                  sg.plate_scene().radar)
+    tri, _, rho = oracle.world_facets(sc, 0.0)
+    return tri, rho
+
+
+def test_flat_plate_normal_incidence_4piA2_over_lambda2():
+    tri, rho = _plate_world()
+    f = np.array([76e9, 77e9, 78.3e9, 81e9])
+    sig = oracle.rcs_farfield(tri, rho, [0, -1, 0], [0, -1, 0], f)
+    lam = C0 / f
+    np.testing.assert_allclose(sig, 4 * np.pi * 1.0 / lam ** 2, rtol=1e-12)
+    # 1 m^2 at 77 GHz is 59.19 dBsm
+    assert abs(10 * np.log10(sig[1]) - 59.19) < 0.01
+
+
+@pytest.mark.parametrize("theta_deg", [0.05, 0.3, 1.0, 7.0])
+def test_flat_plate_oblique_sinc_squared(theta_deg):
+    """Square plate side a, monostatic at angle theta off normal in the plane
+    containing one side: sigma = 4 pi A^2/lambda^2 cos^2 th sinc^2(k a sin th)."""
+    th = math.radians(theta_deg)
+    tri, rho = _plate_world(n=6)
+    d = np.array([math.sin(th), -math.cos(th), 0.0])
+    f = np.array([77.5e9])
+    k = 2 * np.pi * f / C0
+    sig = oracle.rcs_farfield(tri, rho, d, d, f)
+    x = k * 1.0 * math.sin(th)
+    ref = 4 * np.pi / (C0 / f) ** 2 * math.cos(th) ** 2 * np.sinc(x / np.pi) ** 2
+    np.testing.assert_allclose(sig, ref, rtol=1e-9, atol=float(1e-9 * 4 * np.pi / (C0 / f[0]) ** 2))
+
+
+@pytest.mark.slow
+def test_sphere_optical_limit():
+    """Band-averaged monostatic PO RCS of a faceted sphere (a = 0.1 m, edge
+    ~ lambda) is pi a^2 within 0.5 dB."""
+    a = 0.1
+    sc = sg.Scene([sg.icosphere(a, 5)], [sg.Instance(0, (0, 0, 0), np.eye(3), (0, 0, 0))],
+                  sg.plate_scene().radar)
+    tri, _, rho = oracle.world_facets(sc, 0.0)
+    f = np.linspace(76e9, 81e9, 41)
+    d = np.array([0.3, -0.9, 0.2])
+    sig = oracle.rcs_farfield(tri, rho, d, d, f)
+    err_db = 10 * np.log10(sig.mean() / (np.pi * a * a))
+    assert abs(err_db) < 0.5, err_db
+
+
+# ---------------------------------------------------------------------------
+# Table 2 radar arithmetic (printed numbers)
+# ---------------------------------------------------------------------------
+def test_table2_profiles(golden_dir):
+    g = json.load(open(os.path.join(golden_dir, "table2.json")))
+    for e in g["experiments"]:
+        p = sg.radar_profile(e["samples"], g["fs_sps"], g["slope_hz_per_s"])
+        assert abs(p["B"] / 1e9 - e["bandwidth_ghz"]) < 1e-12
+        assert abs(p["Tc"] * 1e6 - e["pulse_time_us"]) < 1e-9
+        assert round(p["range_res"], 2) == e["range_res_m"]
+        assert round(p["v_max"], 2) == e["v_max_mps"]
+        assert (g["target_speed_mps"] > p["v_max"]) == (e["rdm_display"] == "abnormal")
+        assert abs(p["r_max"] - g["max_range_m"]) < 2.0      # "60 m" = 61.4 m
+
+
+# ---------------------------------------------------------------------------
+# echo chain: Eq. 4 / Eq. 5 / Eq. 7 / Eq. 13 through the oracle's ADC
+# ---------------------------------------------------------------------------
+def test_point_target_radar_equation_and_eq13():
+    """A tiny facet (area << lambda^2) facing a monostatic radar is a point
+    target: |x| = sqrt(P) of Eq. 7 with sigma = 4 pi A^2/lambda^2 and the phase
+    of Eq. 13 with tau = 2R/c."""
+    R, edge = 17.3, 0.4e-3
+    sc = sg.point_target_scene(R, 0.0, M=64, N=2, edge=edge)
+    fr = oracle.Frame(sc)
+    adc = fr.adc_full()[0]
+    r = sc.radar
+    tm = np.arange(r.M) / r.fs
+    fm = r.f0 + r.slope * tm
+    lam = C0 / fm
+    A = edge * edge
+    sigma = 4 * np.pi * A * A / lam ** 2
+    amp = np.sqrt(sigma) * lam / ((4 * np.pi) ** 1.5 * R * R)
+    tau = 2 * R / C0
+    ph = 2 * np.pi * (r.f0 * tau + r.slope * tm * tau - 0.5 * r.slope * tau * tau)
+    for n in range(r.N):
+        np.testing.assert_allclose(np.abs(adc[n]), amp, rtol=2e-6)
+        dph = np.angle(adc[n] * np.exp(-1j * ph))
+        assert np.max(np.abs(dph)) < 2e-5
+
+
+def test_beat_frequency_bin_config1_plate():
+    """Eq. 4: f_IF = 2 R mu / c; the 1 m plate at 20 m, mu = 30 MHz/us,
+    fs = 5.12 Msps, M = 128 peaks at range bin 100 (100.07)."""
+    sc = sg.plate_scene()
+    fr = oracle.Frame(sc)
+    assert (fr.state == oracle.LIT).all()
+    adc = fr.adc_full()
+    r = sc.radar
+    expect = 2 * 20.0 * r.slope / C0 / r.fs * r.M
+    assert abs(expect - 100.07) < 0.01
+    X = np.abs(np.fft.fft(adc * oracle.hann(r.M), axis=2)) ** 2
+    assert np.argmax(X.sum(axis=(0, 1))) == round(expect)
+    rdm = oracle.range_doppler_map(adc)
+    rr, dd = np.unravel_index(np.argmax(rdm), rdm.shape)
+    assert rr == 100 and dd == r.N // 2          # static: zero Doppler
+
+
+@pytest.mark.parametrize("M,expect_aliased", [(256, False), (512, True)])
+def test_doppler_bin_and_table2_aliasing(M, expect_aliased):
+    """Eq. 5 / Table 2: the target at 40 m approaching at 10 m/s.  With 256
+    samples (v_max 16.16 m/s) the Doppler peak sits at -2 v T_c N / lambda_c
+    bins; with 512 samples (v_max 8.78 m/s) it wraps to the receding side
+    ("abnormal" RDM)."""
+    N = 32
+    sc = sg.point_target_scene(40.0, -10.0, M=M, N=N, slope=12.5e12, fs=5.12e6,
+                               edge=0.6e-3)
+    fr = oracle.Frame(sc)
+    rdm = oracle.range_doppler_map(fr.adc_full())
+    rr, dd = np.unravel_index(np.argmax(rdm), rdm.shape)
+    r = sc.radar
+    prof = sg.radar_profile(M)
+    cyc = 2 * (-10.0) * r.Tc / prof["lam_c"]           # cycles per chirp, signed
+    wrapped = (cyc + 0.5) % 1.0 - 0.5
+    assert (abs(cyc) > 0.5) == expect_aliased
+    assert dd == N // 2 + int(round(wrapped * N))
+    assert (dd > N // 2) == expect_aliased              # approaching shows < N/2
+    f_b = 2 * 40.0 * r.slope / C0
+    assert abs(rr - f_b / r.fs * M) <= 1.0
+
+
+# ---------------------------------------------------------------------------
+# invariants
+# ---------------------------------------------------------------------------
+def test_reciprocity_tx_rx_swap():
+    base = sg.small_car_scene(ntri=600, M=32, N=3, P=2, Q=3)
+    r = base.radar
+    swapped = sg.Scene(base.meshes, base.instances,
+                       sg.Radar(r.f0, r.slope, r.fs, r.Tc, r.M, r.N, r.rx, r.tx,
+                                r.intra_chirp_motion))
+    a = oracle.Frame(base).adc_full()
+    b = oracle.Frame(swapped).adc_full()
+    P, Q = r.P, r.Q
+    b_perm = np.stack([b[q * P + p] for p in range(P) for q in range(Q)])
+    assert np.linalg.norm(a - b_perm) <= 1e-13 * np.linalg.norm(a)
+
+
+def test_superposition_of_separated_targets():
+    radar = sg.make_radar(64, 4, 1, 2, 5.12e6, 30e12, 2.0, centre=(0, 0, 0))
+    pa, pb = sg.plate(0.2, 0.2, 2), sg.plate(0.3, 0.1, 3)
+    ia = sg.Instance(0, (0.5, 9.0, 0.2), np.eye(3), (0, -3.0, 0))
+    ib = sg.Instance(1, (-1.0, 14.0, -0.4), sg.rot_z(0.1), (0.5, 2.0, 0))
+    both = oracle.Frame(sg.Scene([pa, pb], [ia, ib], radar)).adc_full()
+    a = oracle.Frame(sg.Scene([pa], [ia], radar)).adc_full()
+    b = oracle.Frame(sg.Scene([pb], [sg.Instance(0, ib.pos, ib.rot, ib.vel)], radar)).adc_full()
+    assert np.linalg.norm(both - (a + b)) <= 1e-13 * np.linalg.norm(both)
+
+
+def test_intra_chirp_motion_flag_only_moves_phase():
+    """With the flag off, tau is held at the chirp start; for a static target
+    the two readings coincide exactly."""
+    sc = sg.point_target_scene(12.0, 0.0, M=32, N=2)
+    a = oracle.Frame(sc).adc_full()
+    sc.radar.intra_chirp_motion = False
+    b = oracle.Frame(sc).adc_full()
+    assert np.array_equal(a, b)
+
+
+# ---------------------------------------------------------------------------
+# visibility
+# ---------------------------------------------------------------------------
+def test_visibility_convex_sphere_is_front_facing_set():
+    sc = sg.Scene([sg.icosphere(1.0, 3)], [sg.Instance(0, (0, 8, 1), np.eye(3), (0, 0, 0))],
+                  sg.plate_scene().radar)
+    tri, _, _ = oracle.world_facets(sc, 0.0)
+    ant = np.array([[0.3, 0.0, 0.2], [-5.0, 1.0, 3.0]])
+    st = oracle.visibility(tri, ant)
+    v = tri.reshape(-1, 3, 3)
+    n = np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0])
+    c = v.mean(1)
+    for a in range(2):
+        d = ant[a] - c
+        cos = (n * d).sum(1) / (np.linalg.norm(n, axis=1) * np.linalg.norm(d, axis=1))
+        clear = np.abs(np.abs(cos) - oracle.EPS_FACE) > 1e-9
+        exp = np.where(cos >= oracle.EPS_FACE, oracle.LIT,
+                       np.where(cos <= -oracle.EPS_FACE, oracle.BACK, oracle.GRAZE))
+        assert np.array_equal(st[a][clear], exp[clear])
+        assert (st[a] != oracle.OCCL).all()
+
+
+def test_visibility_geometric_shadow():
+    """A 2 m x 2 m plate at y = 10 shadows part of a 1 m plate at y = 12 seen
+    from the origin: a back facet is occluded iff its centroid projects
+    through the front plate."""
+    front = sg.plate(2.0, 2.0, 4)
+    back = sg.plate(1.0, 1.0, 12)
+    sc = sg.Scene([front, back],
+                  [sg.Instance(0, (0, 10.0, 0), np.eye(3), (0, 0, 0)),
+                   sg.Instance(1, (1.07, 12.0, 0.33), np.eye(3), (0, 0, 0))],
+                  sg.plate_scene().radar)
+    tri, _, _ = oracle.world_facets(sc, 0.0)
+    st = oracle.visibility(tri, np.zeros((1, 3)))[0]
+    nf = front.nf
+    assert (st[:nf] == oracle.LIT).all()
+    c = tri[nf:].reshape(-1, 3, 3).mean(1)
+    x = c[:, 0] * 10.0 / c[:, 1]
+    z = c[:, 2] * 10.0 / c[:, 1]
+    inside = (np.abs(x) < 1.0) & (np.abs(z) < 1.0)
+    assert np.min(np.abs(np.abs(x) - 1.0)) > 1e-6
+    assert inside.any() and (~inside).any()
+    exp = np.where(inside, oracle.OCCL, oracle.LIT)
+    assert np.array_equal(st[nf:], exp)
+
+
+def test_world_vertices_match_rigid_motion():
+    sc = sg.small_car_scene(ntri=300)
+    t = 0.0123
+    tri, fvel, _ = oracle.world_facets(sc, t)
+    ins = sc.instances[0]
+    m = sc.meshes[0]
+    ref = (m.verts[m.tris] @ ins.rot.T + ins.pos + ins.vel * t).reshape(-1, 9)
+    np.testing.assert_allclose(tri, ref, rtol=0, atol=1e-12)
+    assert np.array_equal(fvel, np.tile(ins.vel, (m.nf, 1)))
+
+
+# ---------------------------------------------------------------------------
+# range-Doppler map
+# ---------------------------------------------------------------------------
+def test_rdm_matches_explicit_dft():
+    rng = np.random.default_rng(7)
+    O, N, M = 3, 8, 16
+    adc = rng.normal(size=(O, N, M)) + 1j * rng.normal(size=(O, N, M))
+    Fm = np.exp(-2j * np.pi * np.outer(np.arange(M), np.arange(M)) / M)
+    Fn = np.exp(-2j * np.pi * np.outer(np.arange(N), np.arange(N)) / N)
+    wm = np.array([0.5 - 0.5 * math.cos(2 * math.pi * i / (M - 1)) for i in range(M)])
+    wn = np.array([0.5 - 0.5 * math.cos(2 * math.pi * i / (N - 1)) for i in range(N)])
+    ref = np.zeros((M, N))
+    for o in range(O):
+        X = (adc[o] * wm) @ Fm.T                 # [n][r]
+        Y = Fn @ (X * wn[:, None])               # [d][r]
+        for d in range(N):
+            ref[:, (d + N // 2) % N] += np.abs(Y[d]) ** 2
+    np.testing.assert_allclose(oracle.range_doppler_map(adc), ref, rtol=1e-12)
+
+
+def test_hann_window():
+    for L in (8, 9, 64, 128):
+        w = oracle.hann(L)
+        assert w[0] == 0.0 and abs(w[-1]) < 1e-16
+        np.testing.assert_allclose(w, w[::-1], atol=1e-15)
+        if L % 2:
+            assert w[L // 2] == 1.0
