@@ -207,15 +207,19 @@ void orc_visibility(const double *tri, int64_t F, const double *ant, int A,
 /* physical optics facet integral                                      */
 /* ------------------------------------------------------------------ */
 
-/* Complete homogeneous symmetric polynomial h_p(x0, x1, x2). */
+/* Complete homogeneous symmetric polynomial h_p(x0, x1, x2) = sum over
+ * i + j + l = p of x0^i x1^j x2^l (p <= 16). */
 static double hsym(int p, const double *x)
 {
+    double pw[3][17];
+    for (int r = 0; r < 3; ++r) {
+        pw[r][0] = 1.0;
+        for (int e = 1; e <= p; ++e) pw[r][e] = pw[r][e - 1] * x[r];
+    }
     double s = 0.0;
     for (int i = 0; i <= p; ++i)
-        for (int j = 0; j <= p - i; ++j) {
-            const int l = p - i - j;
-            s += pow(x[0], i) * pow(x[1], j) * pow(x[2], l);
-        }
+        for (int j = 0; j <= p - i; ++j)
+            s += pw[0][i] * pw[1][j] * pw[2][p - i - j];
     return s;
 }
 
@@ -223,9 +227,11 @@ static double hsym(int p, const double *x)
  * centroid.  Gordon's edge form (divergence theorem in the facet plane):
  *   J = sum_i (-j) e_i.(n x w) / |w_t|^2 * exp(j w.(m_i - c)) * sinc(w.e_i/2)
  * with CCW edges e_i, midpoints m_i, unit normal n, w_t the in-plane part
- * of w.  When |w_t| * diameter < 1e-3 the edge form cancels badly; there
- * the power series of the same integral is used:
- *   J = 2A sum_p j^p h_p(a_0, a_1, a_2) / (p+2)!,  a_i = w.(v_i - c). */
+ * of w.  The edge terms cancel to O(|w_t| d) of their size (d = longest
+ * edge), losing ~(|w_t| d)^-2 in relative accuracy, so for |w_t| d < 0.5
+ * the power series of the same integral is used instead:
+ *   J = 2A sum_{p=0}^{14} j^p h_p(a_0, a_1, a_2) / (p+2)!,  a_i = w.(v_i - c)
+ * (|a_i| < 0.5, truncation below 1e-16 relative). */
 void orc_facet_integral(const double *tri, const double *w, double *re, double *im)
 {
     double c[3], e1[3], e2[3], nn[3], nh[3];
@@ -247,7 +253,7 @@ void orc_facet_integral(const double *tri, const double *w, double *re, double *
         const double l = sqrt(dot3(e, e));
         if (l > diam) diam = l;
     }
-    if (sqrt(wt2) * diam < 1e-3) {
+    if (sqrt(wt2) * diam < 0.5) {
         double a[3];
         for (int i = 0; i < 3; ++i) {
             double d[3];
@@ -255,7 +261,7 @@ void orc_facet_integral(const double *tri, const double *w, double *re, double *
             a[i] = dot3(w, d);
         }
         double sr = 0.0, si = 0.0, fact = 2.0;        /* (p+2)! */
-        for (int p = 0; p <= 8; ++p) {
+        for (int p = 0; p <= 14; ++p) {
             const double t = hsym(p, a) / fact;
             switch (p & 3) {                           /* j^p */
             case 0: sr += t; break;

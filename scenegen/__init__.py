@@ -238,51 +238,55 @@ def icosphere(radius: float = 0.1, subdiv: int = 5, rho: float = 1.0) -> Mesh:
     return Mesh(V, F, np.full(len(F), rho, np.float32), "icosphere")
 
 
-def _sgnpow(w: np.ndarray, e: float) -> np.ndarray:
-    return np.sign(w) * np.abs(w) ** e
-
-
-def superquadric(ax: float, ay: float, az: float, n_lat: int, n_lon: int,
-                 e1: float = 0.25, e2: float = 0.25,
-                 centre=(0.0, 0.0, 0.0)) -> tuple:
-    """Closed superquadric surface ("rounded box"), semi-axes ax, ay, az.
-
-    Latitude rings u in (-pi/2, pi/2), longitude v in [-pi, pi); two pole
-    vertices.  Facets: 2 * n_lon * (n_lat - 1), CCW seen from outside.
-    """
-    us = -0.5 * math.pi + math.pi * np.arange(1, n_lat) / n_lat
-    vs = -math.pi + 2.0 * math.pi * np.arange(n_lon) / n_lon
-    U, V = np.meshgrid(us, vs, indexing="ij")          # (n_lat-1, n_lon)
-    cu, su = np.cos(U), np.sin(U)
-    x = ax * _sgnpow(cu, e1) * _sgnpow(np.cos(V), e2)
-    y = ay * _sgnpow(cu, e1) * _sgnpow(np.sin(V), e2)
-    z = az * _sgnpow(su, e1)
-    ring = np.stack([x, y, z], -1).reshape(-1, 3)
-    south = np.array([[0.0, 0.0, -az]])
-    north = np.array([[0.0, 0.0, az]])
-    verts = np.concatenate([ring, south, north], 0) + np.asarray(centre)
-    S = ring.shape[0]
-    N_ = S + 1
-    vid = lambda i, j: i * n_lon + (j % n_lon)
-    tris = []
-    for j in range(n_lon):                               # south cap
-        tris.append((S, vid(0, j + 1), vid(0, j)))
-    for i in range(n_lat - 2):
-        for j in range(n_lon):
-            a, b = vid(i, j), vid(i, j + 1)
-            c, d = vid(i + 1, j + 1), vid(i + 1, j)
-            tris.append((a, b, c))
-            tris.append((a, c, d))
-    for j in range(n_lon):                               # north cap
-        tris.append((N_, vid(n_lat - 2, j), vid(n_lat - 2, j + 1)))
-    return verts, np.asarray(tris, np.int32)
-
-
-def _grid_for(ntri: int, aspect: float = 2.0) -> tuple:
-    """n_lat, n_lon with 2*n_lon*(n_lat-1) ~= ntri and n_lon ~= aspect*n_lat."""
-    n_lat = max(3, int(round(math.sqrt(ntri / (2.0 * aspect)))) + 1)
-    n_lon = max(4, int(round(ntri / (2.0 * (n_lat - 1)))))
-    return n_lat, n_lon
+def rounded_box(hx: float, hy: float, hz: float, r: float, ntri: int,
+                centre=(0.0, 0.0, 0.0)) -> tuple:
+    """Closed rounded box: the Minkowski sum of a box with half extents
+    (hx-r, hy-r, hz-r) and a sphere of radius r, meshed with ~``ntri``
+    near-uniform triangles.  Each face of the outer box gets a regular grid;
+    every grid point q is moved to core(q) + r (q - core(q))/|q - core(q)|,
+    core(q) = clamp(q, -(h-r), h-r).  Vertices shared along the cube edges
+    are merged, and every triangle is wound CCW seen from outside."""
+    h = np.array([hx, hy, hz], np.float64)
+    area = 8.0 * (hx * hy + hy * hz + hx * hz)
+    edge = math.sqrt(2.0 * area / max(ntri, 12))
+    ns = [max(2, int(round(2.0 * e / edge))) for e in h]
+    verts, tris = [], []
+    off = 0
+    for ax in range(3):
+        u_ax, v_ax = [a for a in range(3) if a != ax]
+        nu, nv = ns[u_ax], ns[v_ax]
+        uu = np.linspace(-h[u_ax], h[u_ax], nu + 1)
+        vv = np.linspace(-h[v_ax], h[v_ax], nv + 1)
+        U, V = np.meshgrid(uu, vv, indexing="ij")
+        for sgn in (-1.0, 1.0):
+            q = np.zeros((U.size, 3))
+            q[:, ax] = sgn * h[ax]
+            q[:, u_ax] = U.ravel()
+            q[:, v_ax] = V.ravel()
+            verts.append(q)
+            i, j = np.meshgrid(np.arange(nu), np.arange(nv), indexing="ij")
+            a = (i * (nv + 1) + j).ravel() + off
+            b = ((i + 1) * (nv + 1) + j).ravel() + off
+            c = ((i + 1) * (nv + 1) + j + 1).ravel() + off
+            d = (i * (nv + 1) + j + 1).ravel() + off
+            tris.append(np.stack([a, b, c], 1))
+            tris.append(np.stack([a, c, d], 1))
+            off += q.shape[0]
+    Q = np.concatenate(verts, 0)
+    T = np.concatenate(tris, 0)
+    key = np.round(Q / (1e-9 * max(h))).astype(np.int64)
+    _, first, inv = np.unique(key, axis=0, return_index=True, return_inverse=True)
+    Q = Q[first]
+    T = inv.reshape(-1)[T]
+    core = np.clip(Q, -(h - r), h - r)
+    d = Q - core
+    dn = np.linalg.norm(d, axis=1)
+    P = core + r * d / np.where(dn > 0, dn, 1.0)[:, None]
+    v = P[T]
+    n = np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0])
+    flip = (n * v.mean(1)).sum(1) < 0.0            # convex: outward = away from centre
+    T[flip] = T[flip][:, ::-1]
+    return P + np.asarray(centre, np.float64), T.astype(np.int32)
 
 
 def merge(meshes: Sequence[tuple], rho: float = 1.0, name: str = "mesh") -> Mesh:
@@ -308,8 +312,9 @@ VEHICLE_CLASSES = {
 
 def vehicle(cls: str = "car", seed: int = 0, ntri: Optional[int] = None,
             jitter: float = 0.05, rho: float = 1.0) -> Mesh:
-    """Procedural rounded-box vehicle: a superquadric lower body plus a
-    superquadric cabin, extents jittered by +-``jitter`` (seeded).
+    """Procedural rounded-box vehicle: a rounded-box lower body plus a
+    rounded-box cabin, extents jittered by +-``jitter`` (seeded); the
+    triangle budget is split in proportion to surface area.
 
     Local frame: length along Y (front at +Y), ground contact plane z = 0,
     ground clearance 0.25 m.  Two closed shells; the part of the cabin
@@ -325,14 +330,14 @@ def vehicle(cls: str = "car", seed: int = 0, ntri: Optional[int] = None,
     cab_l = 0.53 * L if cls in ("car", "suv") else 0.25 * L
     cab_w = 0.9 * W
     cab_y = -0.05 * L if cls in ("car", "suv") else 0.35 * L
-    n_body = int(ntri * 0.65)
+    a_body = 2 * (L * W + L * body_h + W * body_h)
+    a_cab = 2 * (cab_l * cab_w + cab_l * cab_h + cab_w * cab_h)
+    n_body = int(ntri * a_body / (a_body + a_cab))
     n_cab = ntri - n_body
-    la, lo = _grid_for(n_body)
-    vb, tb = superquadric(0.5 * W, 0.5 * L, 0.5 * body_h, la, lo, 0.2, 0.2,
-                          centre=(0.0, 0.0, clear + 0.5 * body_h))
-    la, lo = _grid_for(n_cab)
-    vc, tc = superquadric(0.5 * cab_w, 0.5 * cab_l, 0.5 * cab_h, la, lo, 0.3, 0.3,
-                          centre=(0.0, cab_y, clear + body_h - 0.1 + 0.5 * cab_h))
+    vb, tb = rounded_box(0.5 * W, 0.5 * L, 0.5 * body_h, 0.2 * body_h, n_body,
+                         centre=(0.0, 0.0, clear + 0.5 * body_h))
+    vc, tc = rounded_box(0.5 * cab_w, 0.5 * cab_l, 0.5 * cab_h, 0.25 * cab_h, n_cab,
+                         centre=(0.0, cab_y, clear + body_h - 0.1 + 0.5 * cab_h))
     return merge([(vb, tb), (vc, tc)], rho, name=f"{cls}{seed}")
 
 

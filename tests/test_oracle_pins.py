@@ -49,7 +49,7 @@ def test_J_at_zero_is_area():
 @pytest.mark.parametrize("scale", [1e-4, 2e-2, 1.0, 40.0, 400.0, 3000.0])
 def test_J_matches_quadrature(scale):
     """Random triangles, wave vectors on both sides of the series/edge-form
-    switch (|w_t| * diameter = 1e-3) and up to ~100 rad across the facet."""
+    switch (|w_t| * diameter = 0.5) and up to ~100 rad across the facet."""
     rng = np.random.default_rng(int(scale * 1000) % 2**31)
     for _ in range(4):
         tri = rng.normal(size=9) * 0.03
@@ -59,12 +59,31 @@ def test_J_matches_quadrature(scale):
         assert abs(J - ref) <= 1e-11 * max(abs(ref), 1e-30) + 1e-18, (J, ref)
 
 
+@pytest.mark.parametrize("wt_d", [1e-4, 1.3e-3, 2e-2, 0.3, 0.7, 3.0])
+def test_J_near_specular_matches_quadrature(wt_d):
+    """Large normal component, small in-plane part |w_t| d: the regime of
+    near-specular facets, where an edge-sum evaluation cancels."""
+    rng = np.random.default_rng(int(wt_d * 1e4))
+    for _ in range(4):
+        tri = rng.normal(size=9) * 0.03
+        v = tri.reshape(3, 3)
+        n = np.cross(v[1] - v[0], v[2] - v[0])
+        n /= np.linalg.norm(n)
+        d = max(np.linalg.norm(v[i] - v[(i + 1) % 3]) for i in range(3))
+        t = rng.normal(size=3)
+        t -= (t @ n) * n
+        t /= np.linalg.norm(t)
+        w = 3100.0 * n + t * wt_d / d
+        ref = _quad_J(tri, w)
+        assert abs(oracle.facet_integral(tri, w) - ref) <= 1e-13 * abs(ref)
+
+
 def test_J_across_series_switch_is_continuous():
     tri = np.array([0.0, 0.0, 0.0, 0.05, 0.0, 0.0, 0.01, 0.04, 0.0])
     diam = max(np.linalg.norm(tri[3:6] - tri[0:3]), np.linalg.norm(tri[6:9] - tri[3:6]),
                np.linalg.norm(tri[0:3] - tri[6:9]))
     d = np.array([0.6, 0.8, 0.0])
-    for s in (0.999e-3, 1.001e-3):
+    for s in (0.4999, 0.5001):
         w = d * s / diam + np.array([0.0, 0.0, 500.0])      # big normal part
         ref = _quad_J(tri, w)
         assert abs(oracle.facet_integral(tri, w) - ref) <= 1e-12 * abs(ref)
