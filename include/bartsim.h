@@ -1,0 +1,217 @@
+/*
+ * bartsim.h -- C-ABI of the GB300 (sm_103a) BART radar-echo library.
+ *
+ * The library computes, on one GPU, the data-parallel hot path of the MMW
+ * radar simulator of arXiv 2208.10939 (Zong & Zhu):
+ *
+ *   meshed targets  ->  BART single-bounce visibility  ->  physical-optics
+ *   facet scattering per (TX, RX, frequency sample, chirp)  ->  coherent
+ *   MIMO FMCW echo synthesis into the ADC cube  ->  windowed range-Doppler
+ *   FFT into the range-Doppler map (RDM).
+ *
+ * Conventions for every entry point:
+ *   - Return value: BART_OK (0) or a negative BART_E* status.  The text of
+ *     the last error of the calling thread is returned by bart_last_error().
+ *     No C++ exception crosses this interface.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory of the context's device (e.g. torch tensor data_ptr()).
+ *   - Work is enqueued asynchronously on the stream bound with
+ *     bart_set_stream (default: the legacy default stream).  Errors that
+ *     only the device can detect (a BVH stack overflow) are latched in a
+ *     device status word and returned by the next bart_sync().
+ *   - The caller owns every pointer it passes; the library copies what it
+ *     keeps (meshes, instances, radar) and owns all its scratch memory.
+ *   - Geometry is in metres, time in seconds, frequency in hertz.
+ *   - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef BARTSIM_H
+#define BARTSIM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define BART_OK        0
+#define BART_EINVAL   (-1)   /* invalid argument or configuration */
+#define BART_ENOMEM   (-2)   /* device allocation failed */
+#define BART_ECUDA    (-3)   /* CUDA runtime error */
+#define BART_ETIMEOUT (-4)   /* bounded device wait expired */
+#define BART_ESTATE   (-5)   /* call out of order (e.g. simulate before radar_set) */
+#define BART_EDEVICE  (-6)   /* device-side check failed (see bart_last_error) */
+
+/* echo-synthesis precision paths */
+#define BART_PATH_FP64  0    /* every quantity in FP64, exact per-sample delay */
+#define BART_PATH_MIXED 1    /* FP64 path length + mod-1 reduction, FP32 phasors,
+                                compensated (Kahan) accumulation */
+
+/* complex sample types of an ADC cube (interleaved re, im) */
+#define BART_C128 0          /* complex double */
+#define BART_C64  1          /* complex float */
+
+/* RDM windows */
+#define BART_WINDOW_HANN 0   /* symmetric Hann, w[i] = 0.5 - 0.5 cos(2 pi i/(L-1)) */
+#define BART_WINDOW_RECT 1
+
+/* per-(antenna, facet) visibility states returned by bart_get_visibility */
+#define BART_VIS_BACK  0     /* facet faces away from the antenna */
+#define BART_VIS_LIT   1     /* front facing and unoccluded */
+#define BART_VIS_GRAZE 2     /* within the grazing margins: excluded, counted */
+#define BART_VIS_OCCL  3     /* centroid->antenna segment hits another facet */
+
+#define BART_MAX_TX 16
+#define BART_MAX_RX 16
+
+typedef struct bart_ctx bart_ctx;
+
+/* A rigid placement of an uploaded mesh (Sec. 3.1 scene, Eq. 12 motion):
+ *   x_world(t) = rot * x_local + pos + vel * t
+ * rot is row-major 3x3.  rho_scale multiplies the mesh's facet
+ * reflectivities (1 = perfect electric conductor). */
+typedef struct bart_instance {
+    int32_t mesh_id;
+    float   rho_scale;
+    double  pos[3];
+    double  rot[9];
+    double  vel[3];
+} bart_instance;
+
+/* FMCW MIMO radar (Sec. 2.1, Eq. 8; Sec. 3.3).  Channel o = p*Q + q pairs
+ * TX p with RX q.  The ADC cube is [O][N][M] complex, fast-time sample m
+ * contiguous (the paper's O x M x N data matrix, stored sample-major).
+ * Sample m of chirp n is taken at t0 + n*Tc + m/fs; its instantaneous
+ * transmit frequency is f0 + slope*m/fs.
+ * Constraints (else BART_EINVAL): M a power of two in [32, 1024];
+ * N a power of two in [2, 1024]; 1 <= P <= BART_MAX_TX; 1 <= Q <= BART_MAX_RX;
+ * f0, slope, fs > 0; Tc >= M/fs. */
+typedef struct bart_radar {
+    double  f0;                  /* chirp start frequency, Hz */
+    double  slope;               /* mu, Hz/s */
+    double  fs;                  /* ADC sampling rate, samples/s */
+    double  Tc;                  /* chirp repetition period, s */
+    int32_t M, N, P, Q;
+    int32_t intra_chirp_motion;  /* 1: delay at t_n + t_m (Eq. 12, continuous t);
+                                    0: delay held at the chirp start */
+    int32_t window;              /* BART_WINDOW_* for bart_form_rdm */
+    double  tx[BART_MAX_TX][3];  /* TX phase centres (first P used) */
+    double  rx[BART_MAX_RX][3];  /* RX phase centres (first Q used) */
+} bart_radar;
+
+/* Per-frame counters (filled when a non-NULL pointer is passed; doing so
+ * synchronises the stream). */
+typedef struct bart_stats {
+    int64_t n_facets;       /* facets in the scene */
+    int64_t n_terms;        /* echo terms: sum over channels of lit facets x N x M */
+    int64_t n_lit_pairs;    /* (facet, channel) pairs lit from TX and RX */
+    int64_t n_grazing;      /* (antenna, facet) pairs flagged BART_VIS_GRAZE */
+    int64_t n_series;       /* (facet, channel, chirp) records by the series form */
+    int64_t n_edge;         /* records by the edge form */
+    int64_t n_vertex;       /* records by the vertex form */
+} bart_stats;
+
+/* Per-stage device times of the last frame, from CUDA events recorded on
+ * the context's stream while timing is enabled (bart_set_timing). */
+typedef struct bart_timing {
+    float   scene_ms;        /* world facets at t0 */
+    float   bvh_ms;          /* Morton codes, radix sort, hierarchy, refit */
+    float   visibility_ms;   /* visibility states + per-channel lit lists */
+    float   kinematics_ms;   /* FP64 per-chirp path lengths (mixed path) */
+    float   synthesis_ms;    /* echo-synthesis kernels */
+    float   rdm_ms;          /* last bart_form_rdm */
+    int32_t synthesis_launches;   /* synthesis kernel launches in the frame */
+    int32_t launches;        /* kernels launched by the last simulate + form_rdm */
+} bart_timing;
+
+/* Text of the calling thread's last error ("" if none).  Valid until the
+ * thread's next bart_* call. */
+const char *bart_last_error(void);
+
+/* Library version string. */
+const char *bart_version(void);
+
+/* Create a context on CUDA device `device`.  *out receives the handle.
+ * Errors: EINVAL (bad device / NULL out), ECUDA. */
+int bart_create(bart_ctx **out, int device);
+
+/* Free the context and every device buffer it owns.  NULL is ignored. */
+void bart_destroy(bart_ctx *ctx);
+
+/* Enqueue all later work on `stream` (a cudaStream_t, e.g. torch's
+ * torch.cuda.current_stream().cuda_stream); 0 = legacy default stream. */
+int bart_set_stream(bart_ctx *ctx, void *stream);
+
+/* Upload a triangle mesh (host pointers, copied; the caller may free them
+ * on return).  verts: nv x 3 float64; tris: nf x 3 int32 vertex indices,
+ * counter-clockwise seen from outside (outward normal (v1-v0)x(v2-v0));
+ * rho: nf float32 reflectivities or NULL for all 1.  *mesh_id receives the
+ * id used by bart_instance.  Errors: EINVAL (index out of range, nf < 1),
+ * ENOMEM, ECUDA. */
+int bart_mesh_upload(bart_ctx *ctx, const double *verts, int64_t nv,
+                     const int32_t *tris, int64_t nf, const float *rho,
+                     int32_t *mesh_id);
+
+/* Remove every uploaded mesh and the scene. */
+int bart_mesh_clear(bart_ctx *ctx);
+
+/* Set the scene's instances (host array of n, copied).  Each mesh_id must
+ * name an uploaded mesh.  Errors: EINVAL. */
+int bart_scene_set(bart_ctx *ctx, const bart_instance *inst, int32_t n);
+
+/* Total facet count of the current scene (host out). */
+int bart_scene_facets(bart_ctx *ctx, int64_t *n_facets);
+
+/* Set the radar (host struct, copied and validated).  Errors: EINVAL. */
+int bart_radar_set(bart_ctx *ctx, const bart_radar *radar);
+
+/* Simulate one frame starting at absolute time t0 (Sec. 3.2):
+ *   1. world facets at t0 (rigid instance poses),
+ *   2. LBVH over the facets and the BART single-bounce visibility of every
+ *      facet from every antenna (Sec. 2.2), held for the frame,
+ *   3. per (channel, chirp) the physical-optics coefficient of every facet
+ *      lit from TX and RX, and the dechirped IF samples (Eqs. 7, 9-13).
+ * adc: device pointer to O*N*M complex samples of type `dtype`, written
+ * completely.  path: BART_PATH_FP64 or BART_PATH_MIXED.
+ * stats: optional host pointer (NULL = fully asynchronous).
+ * Errors: ESTATE (no radar / scene), EINVAL, ENOMEM, ECUDA. */
+int bart_simulate_frame(bart_ctx *ctx, double t0, int32_t path, void *adc,
+                        int32_t dtype, bart_stats *stats);
+
+/* Range-Doppler map (Sec. 3.3) of an ADC cube of the current radar shape:
+ * window + forward FFT over fast time, window + forward FFT over chirps,
+ * |.|^2 summed over the O channels, zero Doppler shifted to bin N/2.
+ * adc: device pointer, O*N*M complex of `dtype` (FP64 arithmetic for C128,
+ * FP32 for C64).  rdm: device pointer, M x N float32 (range-major).
+ * Errors: ESTATE, EINVAL, ENOMEM, ECUDA. */
+int bart_form_rdm(bart_ctx *ctx, const void *adc, int32_t dtype, float *rdm);
+
+/* One whole frame with host buffers: simulate into library-owned device
+ * memory, form the RDM and copy it to the host array rdm_host (M x N
+ * float32), then synchronise.  Meshes/instances/radar must already be set.
+ * stats: optional host pointer. */
+int bart_frame_host(bart_ctx *ctx, double t0, int32_t path, float *rdm_host,
+                    bart_stats *stats);
+
+/* Copy the frame-start visibility states of the last simulated frame into
+ * the device buffer `state` (A x F uint8, A = P + Q antennas, TX first, then
+ * RX).  Errors: ESTATE (no frame simulated). */
+int bart_get_visibility(bart_ctx *ctx, uint8_t *state);
+
+/* Enable (1) or disable (0) recording of per-stage CUDA events.  The events
+ * are recorded on the context's stream; enabling adds no synchronisation. */
+int bart_set_timing(bart_ctx *ctx, int32_t enable);
+
+/* Per-stage times of the last simulated frame and RDM (host out); waits for
+ * the recorded events.  Errors: ESTATE (timing disabled or no frame). */
+int bart_get_timing(bart_ctx *ctx, bart_timing *out);
+
+/* Wait for the context's stream; return a latched device-side error
+ * (BART_EDEVICE) or a CUDA error, else BART_OK. */
+int bart_sync(bart_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BARTSIM_H */

@@ -164,7 +164,8 @@ static int boxes_disjoint(const double *O, const double *Pa, const double *tri,
 }
 
 /* State of facet k seen from antenna a:
- *   BACK  : cos(angle between outward normal and antenna) <= -eps_face
+ *   BACK  : cos(angle between outward normal and antenna) <= -eps_face, or a
+ *           zero-area facet (it has no normal and cannot be lit)
  *   GRAZE : |cos| < eps_face, or no robust hit but a grazing one
  *   OCCL  : the centroid->antenna segment robustly hits another facet
  *   LIT   : otherwise
@@ -184,7 +185,7 @@ void orc_visibility(const double *tri, int64_t F, const double *ant, int A,
             sub3(ant + 3 * a, c, D);
             const double cosang = dot3(n, D) / (sqrt(dot3(n, n)) * sqrt(dot3(D, D)));
             uint8_t st;
-            if (cosang <= -eps_face) {
+            if (dot3(n, n) == 0.0 || cosang <= -eps_face) {   /* zero area: no normal */
                 st = ORC_BACK;
             } else {
                 int graze = fabs(cosang) < eps_face;

@@ -1,0 +1,351 @@
+"""Python binding of ``libbartsim`` (GB300 BART radar echo synthesis).
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+kernels of ``libbartsim.so`` (see ``include/bartsim.h``).  Torch supplies
+device memory and streams.  There is no CPU fallback: if the library has not
+been built, every call raises ``RuntimeError``.
+
+Function names follow the C-ABI (``bart_create``, ``bart_simulate_frame``,
+...).  ``Simulator`` bundles them for scene objects that carry ``meshes``,
+``instances`` and ``radar`` attributes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbartsim.so")
+
+BART_OK, BART_EINVAL, BART_ENOMEM, BART_ECUDA = 0, -1, -2, -3
+BART_ETIMEOUT, BART_ESTATE, BART_EDEVICE = -4, -5, -6
+PATH_FP64, PATH_MIXED = 0, 1
+C128, C64 = 0, 1
+WINDOW_HANN, WINDOW_RECT = 0, 1
+VIS_BACK, VIS_LIT, VIS_GRAZE, VIS_OCCL = 0, 1, 2, 3
+MAX_TX = MAX_RX = 16
+
+EXPORTED = ["bart_last_error", "bart_version", "bart_create", "bart_destroy",
+            "bart_set_stream", "bart_mesh_upload", "bart_mesh_clear", "bart_scene_set",
+            "bart_scene_facets", "bart_radar_set", "bart_simulate_frame", "bart_form_rdm",
+            "bart_frame_host", "bart_get_visibility", "bart_set_timing", "bart_get_timing",
+            "bart_sync"]
+
+
+class BartError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+class bart_instance(ctypes.Structure):
+    _fields_ = [("mesh_id", ctypes.c_int32), ("rho_scale", ctypes.c_float),
+                ("pos", ctypes.c_double * 3), ("rot", ctypes.c_double * 9),
+                ("vel", ctypes.c_double * 3)]
+
+
+class bart_radar(ctypes.Structure):
+    _fields_ = [("f0", ctypes.c_double), ("slope", ctypes.c_double),
+                ("fs", ctypes.c_double), ("Tc", ctypes.c_double),
+                ("M", ctypes.c_int32), ("N", ctypes.c_int32), ("P", ctypes.c_int32),
+                ("Q", ctypes.c_int32), ("intra_chirp_motion", ctypes.c_int32),
+                ("window", ctypes.c_int32),
+                ("tx", (ctypes.c_double * 3) * MAX_TX),
+                ("rx", (ctypes.c_double * 3) * MAX_RX)]
+
+
+class bart_stats(ctypes.Structure):
+    _fields_ = [("n_facets", ctypes.c_int64), ("n_terms", ctypes.c_int64),
+                ("n_lit_pairs", ctypes.c_int64), ("n_grazing", ctypes.c_int64),
+                ("n_series", ctypes.c_int64), ("n_edge", ctypes.c_int64),
+                ("n_vertex", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+class bart_timing(ctypes.Structure):
+    _fields_ = [("scene_ms", ctypes.c_float), ("bvh_ms", ctypes.c_float),
+                ("visibility_ms", ctypes.c_float), ("kinematics_ms", ctypes.c_float),
+                ("synthesis_ms", ctypes.c_float), ("rdm_ms", ctypes.c_float),
+                ("synthesis_launches", ctypes.c_int32), ("launches", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: (float(getattr(self, f)) if t is ctypes.c_float else int(getattr(self, f)))
+                for f, t in self._fields_}
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib_available() -> bool:
+    return os.path.exists(LIB_PATH)
+
+
+def load_library() -> ctypes.CDLL:
+    """Load ``libbartsim.so`` (raises RuntimeError when it is not built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with "
+                "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        L.bart_last_error.restype = ctypes.c_char_p
+        L.bart_version.restype = ctypes.c_char_p
+        L.bart_create.argtypes = [ctypes.POINTER(P), ctypes.c_int]
+        L.bart_destroy.argtypes = [P]
+        L.bart_destroy.restype = None
+        L.bart_set_stream.argtypes = [P, P]
+        L.bart_mesh_upload.argtypes = [P, P, I64, P, I64, P, ctypes.POINTER(I32)]
+        L.bart_mesh_clear.argtypes = [P]
+        L.bart_scene_set.argtypes = [P, P, I32]
+        L.bart_scene_facets.argtypes = [P, ctypes.POINTER(I64)]
+        L.bart_radar_set.argtypes = [P, ctypes.POINTER(bart_radar)]
+        L.bart_simulate_frame.argtypes = [P, D, I32, P, I32, ctypes.POINTER(bart_stats)]
+        L.bart_form_rdm.argtypes = [P, P, I32, P]
+        L.bart_frame_host.argtypes = [P, D, I32, P, ctypes.POINTER(bart_stats)]
+        L.bart_get_visibility.argtypes = [P, P]
+        L.bart_set_timing.argtypes = [P, I32]
+        L.bart_get_timing.argtypes = [P, ctypes.POINTER(bart_timing)]
+        L.bart_sync.argtypes = [P]
+        for name in EXPORTED:
+            if name not in ("bart_last_error", "bart_version", "bart_destroy"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def _check(rc: int) -> None:
+    if rc != BART_OK:
+        msg = load_library().bart_last_error().decode(errors="replace")
+        raise BartError(rc, msg)
+
+
+def _ptr(t) -> int:
+    """Device (or host) address of a torch tensor / numpy array."""
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return int(t.data_ptr())
+
+
+# ---------------------------------------------------------------------------
+# C-ABI mirrors
+# ---------------------------------------------------------------------------
+def bart_version() -> str:
+    return load_library().bart_version().decode()
+
+
+def bart_create(device: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(load_library().bart_create(ctypes.byref(h), int(device)))
+    return h.value
+
+
+def bart_destroy(ctx: int) -> None:
+    load_library().bart_destroy(ctx)
+
+
+def bart_set_stream(ctx: int, stream: int) -> None:
+    _check(load_library().bart_set_stream(ctx, ctypes.c_void_p(int(stream))))
+
+
+def bart_mesh_upload(ctx: int, verts: np.ndarray, tris: np.ndarray,
+                     rho: Optional[np.ndarray] = None) -> int:
+    v = np.ascontiguousarray(verts, np.float64)
+    t = np.ascontiguousarray(tris, np.int32)
+    r = None if rho is None else np.ascontiguousarray(rho, np.float32)
+    mid = ctypes.c_int32()
+    _check(load_library().bart_mesh_upload(
+        ctx, v.ctypes.data, v.shape[0], t.ctypes.data, t.shape[0],
+        None if r is None else r.ctypes.data, ctypes.byref(mid)))
+    return mid.value
+
+
+def bart_mesh_clear(ctx: int) -> None:
+    _check(load_library().bart_mesh_clear(ctx))
+
+
+def make_instances(instances) -> ctypes.Array:
+    arr = (bart_instance * len(instances))()
+    for i, ins in enumerate(instances):
+        arr[i].mesh_id = int(ins.mesh_id)
+        arr[i].rho_scale = float(getattr(ins, "rho_scale", 1.0))
+        for k in range(3):
+            arr[i].pos[k] = float(ins.pos[k])
+            arr[i].vel[k] = float(ins.vel[k])
+        rot = np.asarray(ins.rot, np.float64).reshape(9)
+        for k in range(9):
+            arr[i].rot[k] = float(rot[k])
+    return arr
+
+
+def bart_scene_set(ctx: int, instances) -> None:
+    arr = make_instances(instances)
+    _check(load_library().bart_scene_set(ctx, ctypes.cast(arr, ctypes.c_void_p), len(instances)))
+
+
+def bart_scene_facets(ctx: int) -> int:
+    n = ctypes.c_int64()
+    _check(load_library().bart_scene_facets(ctx, ctypes.byref(n)))
+    return n.value
+
+
+def make_radar(radar, window: int = WINDOW_HANN) -> bart_radar:
+    r = bart_radar()
+    r.f0, r.slope, r.fs, r.Tc = float(radar.f0), float(radar.slope), float(radar.fs), float(radar.Tc)
+    r.M, r.N = int(radar.M), int(radar.N)
+    tx = np.asarray(radar.tx, np.float64).reshape(-1, 3)
+    rx = np.asarray(radar.rx, np.float64).reshape(-1, 3)
+    r.P, r.Q = tx.shape[0], rx.shape[0]
+    r.intra_chirp_motion = int(bool(getattr(radar, "intra_chirp_motion", True)))
+    r.window = int(window)
+    for p in range(min(r.P, MAX_TX)):
+        for k in range(3):
+            r.tx[p][k] = float(tx[p, k])
+    for q in range(min(r.Q, MAX_RX)):
+        for k in range(3):
+            r.rx[q][k] = float(rx[q, k])
+    return r
+
+
+def bart_radar_set(ctx: int, radar, window: int = WINDOW_HANN) -> None:
+    r = radar if isinstance(radar, bart_radar) else make_radar(radar, window)
+    _check(load_library().bart_radar_set(ctx, ctypes.byref(r)))
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.complex64:
+        return C64
+    if t.dtype == torch.complex128:
+        return C128
+    raise TypeError(f"ADC tensor must be complex64 or complex128, got {t.dtype}")
+
+
+def bart_simulate_frame(ctx: int, t0: float, path: int, adc, stats: bool = False):
+    """Simulate one frame into the contiguous complex CUDA tensor ``adc``
+    ([O][N][M]).  Returns the stats dict when ``stats`` (synchronises)."""
+    if not adc.is_cuda or not adc.is_contiguous():
+        raise ValueError("adc must be a contiguous CUDA tensor")
+    st = bart_stats() if stats else None
+    _check(load_library().bart_simulate_frame(
+        ctx, float(t0), int(path), ctypes.c_void_p(_ptr(adc)), _dtype_code(adc),
+        ctypes.byref(st) if st is not None else None))
+    return st.as_dict() if st is not None else None
+
+
+def bart_form_rdm(ctx: int, adc, rdm) -> None:
+    import torch
+    if not (adc.is_cuda and rdm.is_cuda and adc.is_contiguous() and rdm.is_contiguous()):
+        raise ValueError("adc and rdm must be contiguous CUDA tensors")
+    if rdm.dtype != torch.float32:
+        raise TypeError("rdm must be float32")
+    _check(load_library().bart_form_rdm(ctx, ctypes.c_void_p(_ptr(adc)), _dtype_code(adc),
+                                        ctypes.c_void_p(_ptr(rdm))))
+
+
+def bart_frame_host(ctx: int, t0: float, path: int, rdm_host, stats: bool = False):
+    """Whole frame into a host float32 buffer (numpy array or CPU tensor,
+    ideally pinned) of M x N; synchronises."""
+    st = bart_stats() if stats else None
+    _check(load_library().bart_frame_host(ctx, float(t0), int(path),
+                                          ctypes.c_void_p(_ptr(rdm_host)),
+                                          ctypes.byref(st) if st is not None else None))
+    return st.as_dict() if st is not None else None
+
+
+def bart_get_visibility(ctx: int, state) -> None:
+    _check(load_library().bart_get_visibility(ctx, ctypes.c_void_p(_ptr(state))))
+
+
+def bart_set_timing(ctx: int, enable: bool) -> None:
+    _check(load_library().bart_set_timing(ctx, int(bool(enable))))
+
+
+def bart_get_timing(ctx: int) -> dict:
+    t = bart_timing()
+    _check(load_library().bart_get_timing(ctx, ctypes.byref(t)))
+    return t.as_dict()
+
+
+def bart_sync(ctx: int) -> None:
+    _check(load_library().bart_sync(ctx))
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper
+# ---------------------------------------------------------------------------
+class Simulator:
+    """One library context bound to a CUDA device and torch's current stream."""
+
+    def __init__(self, device: int = 0):
+        import torch
+        self.device = int(device)
+        self.ctx = bart_create(self.device)
+        with torch.cuda.device(self.device):
+            bart_set_stream(self.ctx, torch.cuda.current_stream().cuda_stream)
+        self.radar = None
+        self.n_facets = 0
+
+    def close(self) -> None:
+        if self.ctx:
+            bart_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load_scene(self, scene, window: int = WINDOW_HANN) -> None:
+        """Upload meshes, instances and radar of a scene object."""
+        bart_mesh_clear(self.ctx)
+        for m in scene.meshes:
+            bart_mesh_upload(self.ctx, m.verts, m.tris, m.rho)
+        bart_scene_set(self.ctx, scene.instances)
+        bart_radar_set(self.ctx, scene.radar, window)
+        self.radar = scene.radar
+        self.t0 = float(getattr(scene, "t0", 0.0))
+        self.n_facets = bart_scene_facets(self.ctx)
+
+    def adc_shape(self):
+        r = self.radar
+        return (int(r.tx.shape[0]) * int(r.rx.shape[0]), int(r.N), int(r.M))
+
+    def simulate(self, path: int = PATH_MIXED, dtype=None, t0: Optional[float] = None,
+                 out=None, stats: bool = False):
+        import torch
+        if dtype is None:
+            dtype = torch.complex128 if path == PATH_FP64 else torch.complex64
+        if out is None:
+            out = torch.empty(self.adc_shape(), dtype=dtype, device=f"cuda:{self.device}")
+        st = bart_simulate_frame(self.ctx, self.t0 if t0 is None else t0, path, out, stats)
+        return (out, st) if stats else out
+
+    def rdm(self, adc, out=None):
+        import torch
+        if out is None:
+            out = torch.empty((int(self.radar.M), int(self.radar.N)), dtype=torch.float32,
+                              device=adc.device)
+        bart_form_rdm(self.ctx, adc, out)
+        return out
+
+    def visibility(self):
+        import torch
+        A = int(self.radar.tx.shape[0]) + int(self.radar.rx.shape[0])
+        st = torch.empty((A, self.n_facets), dtype=torch.uint8, device=f"cuda:{self.device}")
+        bart_get_visibility(self.ctx, st)
+        return st
+
+    def sync(self) -> None:
+        bart_sync(self.ctx)

@@ -1,0 +1,141 @@
+// Internal declarations shared by the CUDA translation units of libbartsim.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bartsim.h"
+
+namespace bart {
+
+constexpr double kC0 = 299792458.0;
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kMaxAnt = BART_MAX_TX + BART_MAX_RX;
+
+// Visibility margins (BART single bounce, Sec. 2.2).  A facet whose normal
+// makes |cos| < kEpsFace with its antenna, or whose centroid->antenna segment
+// passes within the barycentric / parameter margins of another facet
+// without a clear hit, is "grazing": excluded and counted.
+constexpr double kEpsFace = 1e-6;
+constexpr double kEpsB = 1e-9;
+constexpr double kEpsT = 1e-9;
+
+// Record classes of the facet integral (see synth.cu).
+constexpr int kRecVertex = 0;
+constexpr int kRecSeries = 1;
+constexpr int kRecEdge = 2;
+constexpr double kSeriesKD = 1.0;     // k_max * (u_max - u_min) below this: series
+constexpr double kEdgeKd = 0.03;      // k_max * min pair gap below this: edge form
+constexpr double kSincSeries = 0.25;  // |k gamma| below this: sinc by its series
+constexpr int kSeriesTerms = 15;      // p = 0..14
+
+// Radar constants passed by value to kernels.
+struct RadarDev {
+    double f0, slope, fs, Tc;
+    int M, N, P, Q, O, A;
+    int intra;
+    int window;
+    double ant[kMaxAnt][3];   // TX 0..P-1, then RX P..P+Q-1
+};
+
+// Frame-start facet record in FP32 (80 B, 16-B aligned).
+struct __align__(16) FacetRec {
+    float c[3];     // centroid
+    float area;
+    float dv[9];    // vertex offsets from the centroid
+    float rho;      // reflectivity
+    float n[3];     // unit outward normal
+    int inst;       // instance index
+    float pad[2];
+};
+static_assert(sizeof(FacetRec) == 80, "FacetRec layout");
+
+// LBVH node with both child boxes stored in the parent (64 B).  A child
+// index >= 0 is an internal node, < 0 is ~facet_id.
+struct __align__(16) BvhNode {
+    float lmin[3];
+    int left;
+    float lmax[3];
+    int right;
+    float rmin[3];
+    int pad0;
+    float rmax[3];
+    int pad1;
+};
+static_assert(sizeof(BvhNode) == 64, "BvhNode layout");
+
+struct MeshDesc {
+    const double *verts;
+    const int32_t *tris;
+    const float *rho;
+    int64_t nf;
+};
+
+struct InstDev {
+    int32_t mesh;
+    float rho_scale;
+    int64_t off;          // first global facet of this instance
+    double pos[3];
+    double rot[9];
+    double vel[3];
+};
+
+// Device status word bits (latched, read by bart_sync).
+constexpr int kStatusStackOverflow = 1;
+
+// ---- scene + BVH (scene_bvh.cu) ----
+void launch_build_facets(const MeshDesc *meshes, const InstDev *insts, int n_inst,
+                         int64_t F, double t0, double *tri64, double *c64,
+                         FacetRec *fac, float *aabb, float *vel32, unsigned int *bounds,
+                         cudaStream_t s);
+void launch_morton(const FacetRec *fac, int64_t F, const unsigned int *bounds,
+                   uint32_t *keys, int32_t *vals, cudaStream_t s);
+// Stable LSD radix sort of (key, value) pairs on the low `bits` bits.
+// Temp buffers sized by radix_sort_temp_words(n).
+int64_t radix_sort_temp_words(int64_t n);
+void radix_sort_pairs(uint32_t *keys, int32_t *vals, uint32_t *keys_tmp, int32_t *vals_tmp,
+                      uint32_t *temp, int64_t n, int bits, cudaStream_t s);
+void launch_lbvh_build(const uint32_t *keys, const int32_t *vals, int64_t n,
+                       BvhNode *nodes, int32_t *parent, int32_t *leaf_parent,
+                       cudaStream_t s);
+void launch_lbvh_refit(const int32_t *vals, const float *aabb, int64_t n, BvhNode *nodes,
+                       const int32_t *parent, const int32_t *leaf_parent, int32_t *flags,
+                       cudaStream_t s);
+
+// ---- visibility (visibility.cu) ----
+void launch_visibility(const double *tri64, const double *c64, const BvhNode *nodes,
+                       int64_t F, const RadarDev &rd, uint8_t *state,
+                       unsigned long long *n_graze, int *status, cudaStream_t s);
+void launch_compact(const uint8_t *state, int64_t F, const RadarDev &rd,
+                    int32_t *blk_cnt, int32_t *vis_idx, int32_t *vis_cnt, cudaStream_t s);
+int64_t compact_blk_words(int64_t F, int O);
+
+// ---- synthesis (synth.cu) ----
+struct SynthArgs {
+    const FacetRec *fac;
+    const double *tri64;
+    const double *c64;
+    const double *vel64;     // per instance, 3 doubles
+    const float *vel32;      // per instance, 4 floats (xyz, pad)
+    const int32_t *vis_idx;  // [O][F]
+    const int32_t *vis_cnt;  // [O]
+    int64_t F;
+    const float4 *kin;       // [nc][A][F] (mixed path)
+    int n0, nc;              // chirp chunk
+    void *out;
+    int out_c64;
+    unsigned long long *counters;   // [0] vertex, [1] series, [2] edge records
+    RadarDev rd;
+};
+void launch_kinematics(const double *c64, const FacetRec *fac, const double *vel64,
+                       const uint8_t *state, int64_t F, const RadarDev &rd, int n0, int nc,
+                       float4 *kin, cudaStream_t s);
+void launch_synth_mixed(const SynthArgs &a, cudaStream_t s);
+void launch_synth_fp64(const SynthArgs &a, cudaStream_t s);
+
+// ---- range-Doppler map (rdm.cu) ----
+int64_t rdm_workspace_bytes(const RadarDev &rd, int dtype);
+void launch_rdm(const void *adc, int dtype, const RadarDev &rd, void *ws, float *rdm,
+                cudaStream_t s);
+
+}  // namespace bart

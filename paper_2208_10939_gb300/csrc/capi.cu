@@ -1,0 +1,659 @@
+// C-ABI of libbartsim (include/bartsim.h): context, uploads and the frame
+// orchestration (world facets -> LBVH -> visibility -> kinematics ->
+// synthesis -> RDM), all enqueued on the context's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "bart_internal.cuh"
+#include "bartsim.h"
+
+using namespace bart;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? BART_ENOMEM : BART_ECUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+template <typename T> struct DevBuf {
+    T *p = nullptr;
+    size_t cap = 0;
+    int ensure(size_t n, const char *what)
+    {
+        if (n <= cap) return BART_OK;
+        release();
+        if (n == 0) return BART_OK;
+        cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+        if (e != cudaSuccess) {
+            p = nullptr;
+            cudaGetLastError();
+            return fail(BART_ENOMEM, "cudaMalloc(%zu bytes) for %s failed: %s", n * sizeof(T),
+                        what, cudaGetErrorString(e));
+        }
+        cap = n;
+        return BART_OK;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+struct MeshStore {
+    DevBuf<double> verts;
+    DevBuf<int32_t> tris;
+    DevBuf<float> rho;
+    int64_t nv = 0, nf = 0;
+    bool has_rho = false;
+};
+
+}  // namespace
+
+struct bart_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<MeshStore *> pool;     // reused across bart_mesh_clear
+    int n_meshes = 0;
+    std::vector<bart_instance> insts;
+    bart_radar radar{};
+    bool have_radar = false;
+    bool have_frame = false;
+    bool tables_dirty = true;   // mesh / instance tables changed since the last frame
+    int64_t frame_F = 0;
+    int frame_A = 0;
+    int64_t kin_budget = 2LL << 30;
+
+    DevBuf<MeshDesc> d_meshes;
+    DevBuf<InstDev> d_insts;
+    DevBuf<double> tri64, c64, vel64;
+    DevBuf<float> vel32, aabb;
+    DevBuf<FacetRec> fac;
+    DevBuf<unsigned int> bounds;
+    DevBuf<uint32_t> keys, keys_tmp, sort_temp;
+    DevBuf<int32_t> vals, vals_tmp;
+    DevBuf<BvhNode> nodes;
+    DevBuf<int32_t> parent, leaf_parent, flags;
+    DevBuf<uint8_t> state;
+    DevBuf<int32_t> blk_cnt, vis_idx, vis_cnt;
+    DevBuf<float4> kin;
+    DevBuf<unsigned long long> counters;   // 0 vertex, 1 series, 2 edge, 3 grazing
+    DevBuf<int> status;
+    DevBuf<unsigned char> rdm_ws, adc_own;
+    DevBuf<float> rdm_own;
+
+    // stage timing: fixed events + two per chirp chunk
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;        // 0 start, 1 facets, 2 bvh, 3 vis, 4 end, 5/6 rdm
+    std::vector<cudaEvent_t> ev_kin;    // per chunk: before kin, after kin (= before synth)
+    std::vector<cudaEvent_t> ev_syn;    // per chunk: after synth
+    int chunks = 0;
+    int path = 0;
+    bool have_rdm_timing = false;
+    bool timed_frame = false;           // the last frame recorded its events
+    int32_t frame_launches = 0, rdm_launches = 0;
+
+    ~bart_ctx()
+    {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        for (cudaEvent_t e : ev_kin) cudaEventDestroy(e);
+        for (cudaEvent_t e : ev_syn) cudaEventDestroy(e);
+        for (MeshStore *m : pool) {
+            m->verts.release();
+            m->tris.release();
+            m->rho.release();
+            delete m;
+        }
+        d_meshes.release(); d_insts.release(); tri64.release(); c64.release();
+        vel64.release(); vel32.release(); aabb.release(); fac.release(); bounds.release();
+        keys.release(); keys_tmp.release(); sort_temp.release(); vals.release();
+        vals_tmp.release(); nodes.release(); parent.release(); leaf_parent.release();
+        flags.release(); state.release(); blk_cnt.release(); vis_idx.release();
+        vis_cnt.release(); kin.release(); counters.release(); status.release();
+        rdm_ws.release(); adc_own.release(); rdm_own.release();
+    }
+};
+
+#define BART_TRY(expr)                    \
+    do {                                  \
+        const int _rc = (expr);           \
+        if (_rc != BART_OK) return _rc;   \
+    } while (0)
+
+#define CUDA_TRY(expr, what)                          \
+    do {                                              \
+        const cudaError_t _e = (expr);                \
+        if (_e != cudaSuccess) return cuda_fail(_e, what); \
+    } while (0)
+
+static bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+static RadarDev make_rd(const bart_radar &r)
+{
+    RadarDev d;
+    std::memset(&d, 0, sizeof d);
+    d.f0 = r.f0;
+    d.slope = r.slope;
+    d.fs = r.fs;
+    d.Tc = r.Tc;
+    d.M = r.M;
+    d.N = r.N;
+    d.P = r.P;
+    d.Q = r.Q;
+    d.O = r.P * r.Q;
+    d.A = r.P + r.Q;
+    d.intra = r.intra_chirp_motion ? 1 : 0;
+    d.window = r.window;
+    for (int p = 0; p < r.P; ++p)
+        for (int k = 0; k < 3; ++k) d.ant[p][k] = r.tx[p][k];
+    for (int q = 0; q < r.Q; ++q)
+        for (int k = 0; k < 3; ++k) d.ant[r.P + q][k] = r.rx[q][k];
+    return d;
+}
+
+static int ensure_events(std::vector<cudaEvent_t> &v, size_t n)
+{
+    while (v.size() < n) {
+        cudaEvent_t e;
+        CUDA_TRY(cudaEventCreate(&e), "cudaEventCreate");
+        v.push_back(e);
+    }
+    return BART_OK;
+}
+
+static int set_device(bart_ctx *ctx)
+{
+    CUDA_TRY(cudaSetDevice(ctx->device), "cudaSetDevice");
+    return BART_OK;
+}
+
+extern "C" {
+
+const char *bart_last_error(void) { return g_err.c_str(); }
+
+const char *bart_version(void) { return "bartsim 0.1 (sm_103a)"; }
+
+int bart_create(bart_ctx **out, int device)
+{
+    g_err.clear();
+    if (!out) return fail(BART_EINVAL, "bart_create: out is NULL");
+    *out = nullptr;
+    int n = 0;
+    CUDA_TRY(cudaGetDeviceCount(&n), "cudaGetDeviceCount");
+    if (device < 0 || device >= n)
+        return fail(BART_EINVAL, "bart_create: device %d out of range [0, %d)", device, n);
+    CUDA_TRY(cudaSetDevice(device), "cudaSetDevice");
+    bart_ctx *c = new (std::nothrow) bart_ctx();
+    if (!c) return fail(BART_ENOMEM, "bart_create: host allocation failed");
+    c->device = device;
+    int rc = c->counters.ensure(4, "counters");
+    if (rc == BART_OK) rc = c->status.ensure(1, "status");
+    if (rc == BART_OK) rc = c->bounds.ensure(6, "bounds");
+    if (rc != BART_OK) {
+        delete c;
+        return rc;
+    }
+    cudaError_t e = cudaMemset(c->status.p, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "cudaMemset");
+    }
+    *out = c;
+    return BART_OK;
+}
+
+void bart_destroy(bart_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    delete ctx;
+}
+
+int bart_set_stream(bart_ctx *ctx, void *stream)
+{
+    g_err.clear();
+    if (!ctx) return fail(BART_EINVAL, "bart_set_stream: ctx is NULL");
+    ctx->stream = reinterpret_cast<cudaStream_t>(stream);
+    return BART_OK;
+}
+
+int bart_mesh_upload(bart_ctx *ctx, const double *verts, int64_t nv, const int32_t *tris,
+                     int64_t nf, const float *rho, int32_t *mesh_id)
+{
+    g_err.clear();
+    if (!ctx || !verts || !tris || !mesh_id) return fail(BART_EINVAL, "bart_mesh_upload: NULL argument");
+    if (nv < 3 || nf < 1) return fail(BART_EINVAL, "bart_mesh_upload: nv=%lld nf=%lld", (long long)nv, (long long)nf);
+    if (nf > (int64_t)1 << 30) return fail(BART_EINVAL, "bart_mesh_upload: nf too large");
+    for (int64_t i = 0; i < 3 * nf; ++i)
+        if (tris[i] < 0 || tris[i] >= nv)
+            return fail(BART_EINVAL, "bart_mesh_upload: tris[%lld]=%d out of [0,%lld)",
+                        (long long)i, tris[i], (long long)nv);
+    BART_TRY(set_device(ctx));
+    if (ctx->n_meshes == (int)ctx->pool.size()) {
+        MeshStore *m = new (std::nothrow) MeshStore();
+        if (!m) return fail(BART_ENOMEM, "bart_mesh_upload: host allocation failed");
+        ctx->pool.push_back(m);
+    }
+    MeshStore *m = ctx->pool[ctx->n_meshes];
+    BART_TRY(m->verts.ensure((size_t)(3 * nv), "mesh vertices"));
+    BART_TRY(m->tris.ensure((size_t)(3 * nf), "mesh triangles"));
+    BART_TRY(m->rho.ensure((size_t)nf, "mesh reflectivity"));
+    CUDA_TRY(cudaMemcpyAsync(m->verts.p, verts, (size_t)(3 * nv) * sizeof(double),
+                             cudaMemcpyHostToDevice, ctx->stream), "mesh vertex copy");
+    CUDA_TRY(cudaMemcpyAsync(m->tris.p, tris, (size_t)(3 * nf) * sizeof(int32_t),
+                             cudaMemcpyHostToDevice, ctx->stream), "mesh index copy");
+    if (rho) {
+        CUDA_TRY(cudaMemcpyAsync(m->rho.p, rho, (size_t)nf * sizeof(float),
+                                 cudaMemcpyHostToDevice, ctx->stream), "mesh rho copy");
+    }
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+    m->has_rho = rho != nullptr;
+    m->nv = nv;
+    m->nf = nf;
+    *mesh_id = ctx->n_meshes++;
+    ctx->tables_dirty = true;
+    return BART_OK;
+}
+
+int bart_mesh_clear(bart_ctx *ctx)
+{
+    g_err.clear();
+    if (!ctx) return fail(BART_EINVAL, "bart_mesh_clear: ctx is NULL");
+    ctx->n_meshes = 0;
+    ctx->insts.clear();
+    ctx->have_frame = false;
+    ctx->tables_dirty = true;
+    return BART_OK;
+}
+
+int bart_scene_set(bart_ctx *ctx, const bart_instance *inst, int32_t n)
+{
+    g_err.clear();
+    if (!ctx || (n > 0 && !inst)) return fail(BART_EINVAL, "bart_scene_set: NULL argument");
+    if (n < 0) return fail(BART_EINVAL, "bart_scene_set: n=%d", n);
+    for (int i = 0; i < n; ++i) {
+        if (inst[i].mesh_id < 0 || inst[i].mesh_id >= ctx->n_meshes)
+            return fail(BART_EINVAL, "bart_scene_set: instance %d names mesh %d (have %d)", i,
+                        inst[i].mesh_id, ctx->n_meshes);
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(inst[i].pos[k]) || !std::isfinite(inst[i].vel[k]))
+                return fail(BART_EINVAL, "bart_scene_set: instance %d has a non-finite pose", i);
+    }
+    ctx->insts.assign(inst, inst + n);
+    ctx->tables_dirty = true;
+    return BART_OK;
+}
+
+int bart_scene_facets(bart_ctx *ctx, int64_t *n_facets)
+{
+    g_err.clear();
+    if (!ctx || !n_facets) return fail(BART_EINVAL, "bart_scene_facets: NULL argument");
+    int64_t F = 0;
+    for (const bart_instance &i : ctx->insts) F += ctx->pool[i.mesh_id]->nf;
+    *n_facets = F;
+    return BART_OK;
+}
+
+int bart_radar_set(bart_ctx *ctx, const bart_radar *r)
+{
+    g_err.clear();
+    if (!ctx || !r) return fail(BART_EINVAL, "bart_radar_set: NULL argument");
+    if (!is_pow2(r->M) || r->M < 32 || r->M > 1024)
+        return fail(BART_EINVAL, "bart_radar_set: M=%d must be a power of two in [32,1024]", r->M);
+    if (!is_pow2(r->N) || r->N < 2 || r->N > 1024)
+        return fail(BART_EINVAL, "bart_radar_set: N=%d must be a power of two in [2,1024]", r->N);
+    if (r->P < 1 || r->P > BART_MAX_TX || r->Q < 1 || r->Q > BART_MAX_RX)
+        return fail(BART_EINVAL, "bart_radar_set: P=%d Q=%d out of range", r->P, r->Q);
+    if (!(r->f0 > 0) || !(r->slope > 0) || !(r->fs > 0) || !(r->Tc > 0))
+        return fail(BART_EINVAL, "bart_radar_set: f0, slope, fs, Tc must be positive");
+    if (r->Tc < (double)r->M / r->fs * (1.0 - 1e-12))
+        return fail(BART_EINVAL, "bart_radar_set: Tc=%g shorter than M/fs=%g", r->Tc,
+                    (double)r->M / r->fs);
+    if (r->window != BART_WINDOW_HANN && r->window != BART_WINDOW_RECT)
+        return fail(BART_EINVAL, "bart_radar_set: window=%d", r->window);
+    ctx->radar = *r;
+    ctx->have_radar = true;
+    ctx->have_frame = false;
+    return BART_OK;
+}
+
+static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t dtype,
+                     bart_stats *stats)
+{
+    if (!ctx->have_radar) return fail(BART_ESTATE, "bart_simulate_frame: radar not set");
+    if (ctx->insts.empty()) return fail(BART_ESTATE, "bart_simulate_frame: scene has no instances");
+    if (path != BART_PATH_FP64 && path != BART_PATH_MIXED)
+        return fail(BART_EINVAL, "bart_simulate_frame: path=%d", path);
+    if (dtype != BART_C64 && dtype != BART_C128)
+        return fail(BART_EINVAL, "bart_simulate_frame: dtype=%d", dtype);
+    if (!adc) return fail(BART_EINVAL, "bart_simulate_frame: adc is NULL");
+    if (!std::isfinite(t0)) return fail(BART_EINVAL, "bart_simulate_frame: t0 not finite");
+    BART_TRY(set_device(ctx));
+    cudaStream_t s = ctx->stream;
+    const RadarDev rd = make_rd(ctx->radar);
+
+    // instance + mesh tables
+    const int I = (int)ctx->insts.size();
+    std::vector<MeshDesc> md(ctx->n_meshes);
+    for (int i = 0; i < ctx->n_meshes; ++i) {
+        MeshStore *m = ctx->pool[i];
+        md[i] = MeshDesc{m->verts.p, m->tris.p, m->has_rho ? m->rho.p : nullptr, m->nf};
+    }
+    std::vector<InstDev> id(I);
+    int64_t F = 0;
+    for (int i = 0; i < I; ++i) {
+        const bart_instance &b = ctx->insts[i];
+        InstDev &d = id[i];
+        d.mesh = b.mesh_id;
+        d.rho_scale = b.rho_scale;
+        d.off = F;
+        std::memcpy(d.pos, b.pos, sizeof d.pos);
+        std::memcpy(d.rot, b.rot, sizeof d.rot);
+        std::memcpy(d.vel, b.vel, sizeof d.vel);
+        F += ctx->pool[b.mesh_id]->nf;
+    }
+    if (F > ((int64_t)1 << 31) - 2) return fail(BART_EINVAL, "scene has %lld facets (max 2^31-2)", (long long)F);
+    const int A = rd.A, O = rd.O;
+
+    if (md.size() > ctx->d_meshes.cap || (size_t)I > ctx->d_insts.cap ||
+        (size_t)(3 * I) > ctx->vel64.cap)
+        ctx->tables_dirty = true;
+    BART_TRY(ctx->d_meshes.ensure(md.size(), "mesh table"));
+    BART_TRY(ctx->d_insts.ensure(I, "instance table"));
+    BART_TRY(ctx->tri64.ensure(9 * F, "facet vertices"));
+    BART_TRY(ctx->c64.ensure(3 * F, "facet centroids"));
+    BART_TRY(ctx->vel64.ensure(3 * I, "instance velocities"));
+    BART_TRY(ctx->vel32.ensure(4 * I, "instance velocities (f32)"));
+    BART_TRY(ctx->aabb.ensure(6 * F, "facet boxes"));
+    BART_TRY(ctx->fac.ensure(F, "facet records"));
+    BART_TRY(ctx->keys.ensure(F, "morton keys"));
+    BART_TRY(ctx->keys_tmp.ensure(F, "morton keys"));
+    BART_TRY(ctx->vals.ensure(F, "sort values"));
+    BART_TRY(ctx->vals_tmp.ensure(F, "sort values"));
+    BART_TRY(ctx->sort_temp.ensure(radix_sort_temp_words(F), "sort histogram"));
+    BART_TRY(ctx->nodes.ensure(F > 1 ? F - 1 : 1, "bvh nodes"));
+    BART_TRY(ctx->parent.ensure(F > 1 ? F - 1 : 1, "bvh parents"));
+    BART_TRY(ctx->leaf_parent.ensure(F, "bvh leaf parents"));
+    BART_TRY(ctx->flags.ensure(F > 1 ? F - 1 : 1, "bvh refit flags"));
+    BART_TRY(ctx->state.ensure((size_t)A * F, "visibility states"));
+    BART_TRY(ctx->blk_cnt.ensure(compact_blk_words(F, O), "compaction counts"));
+    BART_TRY(ctx->vis_idx.ensure((size_t)O * F, "lit facet lists"));
+    BART_TRY(ctx->vis_cnt.ensure(O, "lit facet counts"));
+
+    if (ctx->tables_dirty) {
+        // pageable sources: each copy is staged before the call returns
+        CUDA_TRY(cudaMemcpyAsync(ctx->d_meshes.p, md.data(), md.size() * sizeof(MeshDesc),
+                                 cudaMemcpyHostToDevice, s), "mesh table copy");
+        CUDA_TRY(cudaMemcpyAsync(ctx->d_insts.p, id.data(), (size_t)I * sizeof(InstDev),
+                                 cudaMemcpyHostToDevice, s), "instance table copy");
+        std::vector<double> v(3 * I);
+        for (int i = 0; i < I; ++i)
+            for (int k = 0; k < 3; ++k) v[3 * i + k] = ctx->insts[i].vel[k];
+        CUDA_TRY(cudaMemcpyAsync(ctx->vel64.p, v.data(), v.size() * sizeof(double),
+                                 cudaMemcpyHostToDevice, s), "velocity copy");
+        ctx->tables_dirty = false;
+    }
+    CUDA_TRY(cudaMemsetAsync(ctx->counters.p, 0, 4 * sizeof(unsigned long long), s), "memset");
+    const bool tm = ctx->timing;
+    if (tm) {
+        BART_TRY(ensure_events(ctx->ev, 7));
+        CUDA_TRY(cudaEventRecord(ctx->ev[0], s), "cudaEventRecord");
+    }
+    int launches = 0;
+
+    // 1. world facets at t0
+    launch_build_facets(ctx->d_meshes.p, ctx->d_insts.p, I, F, t0, ctx->tri64.p, ctx->c64.p,
+                        ctx->fac.p, ctx->aabb.p, ctx->vel32.p, ctx->bounds.p, s);
+    launches += 1;
+    if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[1], s), "cudaEventRecord");
+    // 2. LBVH
+    launch_morton(ctx->fac.p, F, ctx->bounds.p, ctx->keys.p, ctx->vals.p, s);
+    radix_sort_pairs(ctx->keys.p, ctx->vals.p, ctx->keys_tmp.p, ctx->vals_tmp.p,
+                     ctx->sort_temp.p, F, 30, s);
+    launch_lbvh_build(ctx->keys.p, ctx->vals.p, F, ctx->nodes.p, ctx->parent.p,
+                      ctx->leaf_parent.p, s);
+    launch_lbvh_refit(ctx->vals.p, ctx->aabb.p, F, ctx->nodes.p, ctx->parent.p,
+                      ctx->leaf_parent.p, ctx->flags.p, s);
+    launches += 1 + 3 * 4 + (F >= 2 ? 2 : 0);
+    if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[2], s), "cudaEventRecord");
+    // 3. visibility + per-channel lit lists
+    launch_visibility(ctx->tri64.p, ctx->c64.p, ctx->nodes.p, F, rd, ctx->state.p,
+                      ctx->counters.p + 3, ctx->status.p, s);
+    launch_compact(ctx->state.p, F, rd, ctx->blk_cnt.p, ctx->vis_idx.p, ctx->vis_cnt.p, s);
+    launches += 1 + 3;
+    if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[3], s), "cudaEventRecord");
+    // 4. synthesis
+    SynthArgs a;
+    a.fac = ctx->fac.p;
+    a.tri64 = ctx->tri64.p;
+    a.c64 = ctx->c64.p;
+    a.vel64 = ctx->vel64.p;
+    a.vel32 = ctx->vel32.p;
+    a.vis_idx = ctx->vis_idx.p;
+    a.vis_cnt = ctx->vis_cnt.p;
+    a.F = F;
+    a.kin = nullptr;
+    a.out = adc;
+    a.out_c64 = dtype == BART_C64;
+    a.counters = ctx->counters.p;
+    a.rd = rd;
+    if (path == BART_PATH_MIXED) {
+        const int64_t per_chirp = (int64_t)A * F * (int64_t)sizeof(float4);
+        int nc = (int)std::min<int64_t>(rd.N, std::max<int64_t>(1, ctx->kin_budget / per_chirp));
+        BART_TRY(ctx->kin.ensure((size_t)nc * A * F, "kinematics table"));
+        a.kin = ctx->kin.p;
+        const int chunks = (rd.N + nc - 1) / nc;
+        if (tm) {
+            BART_TRY(ensure_events(ctx->ev_kin, 2 * chunks));
+            BART_TRY(ensure_events(ctx->ev_syn, chunks));
+        }
+        for (int c = 0; c < chunks; ++c) {
+            const int n0 = c * nc;
+            const int cnt = std::min(nc, rd.N - n0);
+            if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_kin[2 * c], s), "cudaEventRecord");
+            launch_kinematics(ctx->c64.p, ctx->fac.p, ctx->vel64.p, ctx->state.p, F, rd, n0, cnt,
+                              ctx->kin.p, s);
+            if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_kin[2 * c + 1], s), "cudaEventRecord");
+            a.n0 = n0;
+            a.nc = cnt;
+            launch_synth_mixed(a, s);
+            if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_syn[c], s), "cudaEventRecord");
+        }
+        ctx->chunks = chunks;
+        launches += 2 * chunks;
+    } else {
+        a.n0 = 0;
+        a.nc = rd.N;
+        launch_synth_fp64(a, s);
+        ctx->chunks = 1;
+        launches += 1;
+    }
+    if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[4], s), "cudaEventRecord");
+    ctx->path = path;
+    ctx->frame_launches = launches;
+    ctx->have_rdm_timing = false;
+    ctx->timed_frame = tm;
+    CUDA_TRY(cudaGetLastError(), "kernel launch");
+    ctx->have_frame = true;
+    ctx->frame_F = F;
+    ctx->frame_A = A;
+    if (stats) {
+        std::vector<int32_t> cnt(O);
+        unsigned long long ctr[4];
+        CUDA_TRY(cudaMemcpyAsync(cnt.data(), ctx->vis_cnt.p, O * sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, s), "stats copy");
+        CUDA_TRY(cudaMemcpyAsync(ctr, ctx->counters.p, sizeof ctr, cudaMemcpyDeviceToHost, s),
+                 "stats copy");
+        CUDA_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+        int64_t lit = 0;
+        for (int o = 0; o < O; ++o) lit += cnt[o];
+        stats->n_facets = F;
+        stats->n_lit_pairs = lit;
+        stats->n_terms = lit * (int64_t)rd.N * rd.M;
+        stats->n_vertex = (int64_t)ctr[0];
+        stats->n_series = (int64_t)ctr[1];
+        stats->n_edge = (int64_t)ctr[2];
+        stats->n_grazing = (int64_t)ctr[3];
+    }
+    return BART_OK;
+}
+
+int bart_simulate_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t dtype,
+                        bart_stats *stats)
+{
+    g_err.clear();
+    if (!ctx) return fail(BART_EINVAL, "bart_simulate_frame: ctx is NULL");
+    return run_frame(ctx, t0, path, adc, dtype, stats);
+}
+
+static int run_rdm(bart_ctx *ctx, const void *adc, int32_t dtype, float *rdm)
+{
+    if (!ctx->have_radar) return fail(BART_ESTATE, "bart_form_rdm: radar not set");
+    if (!adc || !rdm) return fail(BART_EINVAL, "bart_form_rdm: NULL buffer");
+    if (dtype != BART_C64 && dtype != BART_C128)
+        return fail(BART_EINVAL, "bart_form_rdm: dtype=%d", dtype);
+    BART_TRY(set_device(ctx));
+    const RadarDev rd = make_rd(ctx->radar);
+    BART_TRY(ctx->rdm_ws.ensure((size_t)rdm_workspace_bytes(rd, dtype), "rdm workspace"));
+    if (ctx->timing) {
+        BART_TRY(ensure_events(ctx->ev, 7));
+        CUDA_TRY(cudaEventRecord(ctx->ev[5], ctx->stream), "cudaEventRecord");
+    }
+    launch_rdm(adc, dtype, rd, ctx->rdm_ws.p, rdm, ctx->stream);
+    CUDA_TRY(cudaGetLastError(), "rdm launch");
+    if (ctx->timing) {
+        CUDA_TRY(cudaEventRecord(ctx->ev[6], ctx->stream), "cudaEventRecord");
+        ctx->have_rdm_timing = true;
+    }
+    ctx->rdm_launches = 2;
+    return BART_OK;
+}
+
+int bart_form_rdm(bart_ctx *ctx, const void *adc, int32_t dtype, float *rdm)
+{
+    g_err.clear();
+    if (!ctx) return fail(BART_EINVAL, "bart_form_rdm: ctx is NULL");
+    return run_rdm(ctx, adc, dtype, rdm);
+}
+
+int bart_frame_host(bart_ctx *ctx, double t0, int32_t path, float *rdm_host, bart_stats *stats)
+{
+    g_err.clear();
+    if (!ctx || !rdm_host) return fail(BART_EINVAL, "bart_frame_host: NULL argument");
+    if (!ctx->have_radar) return fail(BART_ESTATE, "bart_frame_host: radar not set");
+    const bart_radar &r = ctx->radar;
+    const int dtype = path == BART_PATH_FP64 ? BART_C128 : BART_C64;
+    const size_t esz = dtype == BART_C64 ? 8 : 16;
+    BART_TRY(set_device(ctx));
+    BART_TRY(ctx->adc_own.ensure((size_t)r.P * r.Q * r.N * r.M * esz, "frame adc"));
+    BART_TRY(ctx->rdm_own.ensure((size_t)r.M * r.N, "frame rdm"));
+    BART_TRY(run_frame(ctx, t0, path, ctx->adc_own.p, dtype, stats));
+    BART_TRY(run_rdm(ctx, ctx->adc_own.p, dtype, ctx->rdm_own.p));
+    CUDA_TRY(cudaMemcpyAsync(rdm_host, ctx->rdm_own.p, (size_t)r.M * r.N * sizeof(float),
+                             cudaMemcpyDeviceToHost, ctx->stream), "rdm copy");
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+    return BART_OK;
+}
+
+int bart_get_visibility(bart_ctx *ctx, uint8_t *state)
+{
+    g_err.clear();
+    if (!ctx || !state) return fail(BART_EINVAL, "bart_get_visibility: NULL argument");
+    if (!ctx->have_frame) return fail(BART_ESTATE, "bart_get_visibility: no frame simulated");
+    BART_TRY(set_device(ctx));
+    CUDA_TRY(cudaMemcpyAsync(state, ctx->state.p, (size_t)ctx->frame_A * ctx->frame_F,
+                             cudaMemcpyDeviceToDevice, ctx->stream), "state copy");
+    return BART_OK;
+}
+
+int bart_set_timing(bart_ctx *ctx, int32_t enable)
+{
+    g_err.clear();
+    if (!ctx) return fail(BART_EINVAL, "bart_set_timing: ctx is NULL");
+    ctx->timing = enable != 0;
+    return BART_OK;
+}
+
+static float elapsed(cudaEvent_t a, cudaEvent_t b)
+{
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+}
+
+int bart_get_timing(bart_ctx *ctx, bart_timing *out)
+{
+    g_err.clear();
+    if (!ctx || !out) return fail(BART_EINVAL, "bart_get_timing: NULL argument");
+    if (!ctx->timed_frame || !ctx->have_frame || ctx->ev.size() < 7)
+        return fail(BART_ESTATE, "bart_get_timing: timing disabled or no frame simulated");
+    BART_TRY(set_device(ctx));
+    CUDA_TRY(cudaEventSynchronize(ctx->ev[4]), "cudaEventSynchronize");
+    std::memset(out, 0, sizeof *out);
+    out->scene_ms = elapsed(ctx->ev[0], ctx->ev[1]);
+    out->bvh_ms = elapsed(ctx->ev[1], ctx->ev[2]);
+    out->visibility_ms = elapsed(ctx->ev[2], ctx->ev[3]);
+    if (ctx->path == BART_PATH_MIXED) {
+        for (int c = 0; c < ctx->chunks; ++c) {
+            out->kinematics_ms += elapsed(ctx->ev_kin[2 * c], ctx->ev_kin[2 * c + 1]);
+            out->synthesis_ms += elapsed(ctx->ev_kin[2 * c + 1], ctx->ev_syn[c]);
+        }
+    } else {
+        out->synthesis_ms = elapsed(ctx->ev[3], ctx->ev[4]);
+    }
+    out->synthesis_launches = ctx->chunks;
+    out->launches = ctx->frame_launches;
+    if (ctx->have_rdm_timing) {
+        CUDA_TRY(cudaEventSynchronize(ctx->ev[6]), "cudaEventSynchronize");
+        out->rdm_ms = elapsed(ctx->ev[5], ctx->ev[6]);
+        out->launches += ctx->rdm_launches;
+    }
+    return BART_OK;
+}
+
+int bart_sync(bart_ctx *ctx)
+{
+    g_err.clear();
+    if (!ctx) return fail(BART_EINVAL, "bart_sync: ctx is NULL");
+    BART_TRY(set_device(ctx));
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+    int st = 0;
+    CUDA_TRY(cudaMemcpy(&st, ctx->status.p, sizeof st, cudaMemcpyDeviceToHost), "status copy");
+    if (st) {
+        cudaMemset(ctx->status.p, 0, sizeof st);
+        if (st & kStatusStackOverflow)
+            return fail(BART_EDEVICE, "BVH traversal stack overflow (facets marked grazing)");
+        return fail(BART_EDEVICE, "device status 0x%x", st);
+    }
+    return BART_OK;
+}
+
+}  // extern "C"

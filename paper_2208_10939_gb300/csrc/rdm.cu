@@ -1,0 +1,180 @@
+// Range-Doppler map (Sec. 3.3): per channel, a windowed forward FFT over the
+// M fast-time samples of every chirp (range), then a windowed forward FFT
+// over the N chirps of every range bin (Doppler); |.|^2 summed over the O
+// channels; the Doppler axis shifted so that zero velocity is bin N/2.
+//
+// Radix-2 Stockham autosort FFTs in shared memory (no bit reversal): stage
+// with current length n and stride s = L/n maps
+//   y[q + s(2p)] = x[q + s p] + x[q + s(p + n/2)]
+//   y[q + s(2p+1)] = (x[q + s p] - x[q + s(p + n/2)]) * exp(-2 pi i p s / L)
+// Both passes are HBM-bound: each reads and writes the cube once.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bart_internal.cuh"
+
+namespace bart {
+
+template <typename T> struct Cplx;
+template <> struct Cplx<float> { using type = float2; };
+template <> struct Cplx<double> { using type = double2; };
+
+__device__ __forceinline__ void sincospi_t(float x, float *s, float *c) { sincospif(x, s, c); }
+__device__ __forceinline__ void sincospi_t(double x, double *s, double *c) { sincospi(x, s, c); }
+__device__ __forceinline__ float cospi_t(float x) { return cospif(x); }
+__device__ __forceinline__ double cospi_t(double x) { return cospi(x); }
+
+template <typename T>
+__device__ __forceinline__ T window_val(int i, int L, int kind)
+{
+    if (kind == BART_WINDOW_RECT || L < 2) return (T)1;
+    // symmetric Hann: 0.5 - 0.5 cos(2 pi i / (L-1)); cospi of a double ratio
+    return (T)(0.5 - 0.5 * cospi_t((double)(2 * i) / (double)(L - 1)));
+}
+
+// Stockham stages over `cols` interleaved transforms of length L stored as
+// buf[col * L + idx]; `tw` holds exp(-2 pi i j / L), j < L/2.
+template <typename C>
+__device__ C *stockham(C *x, C *y, const C *tw, int L, int cols)
+{
+    const int half_tot = (L >> 1) * cols;
+    for (int n = L, s = 1; n > 1; n >>= 1, s <<= 1) {
+        const int h = n >> 1;
+        for (int t = threadIdx.x; t < half_tot; t += blockDim.x) {
+            const int col = t / (L >> 1), b = t % (L >> 1);
+            const int p = b / s, q = b % s;
+            const C *xc = x + col * L;
+            C *yc = y + col * L;
+            const C a = xc[q + s * p], c = xc[q + s * (p + h)];
+            const C w = tw[p * s];
+            C sum, dif;
+            sum.x = a.x + c.x;
+            sum.y = a.y + c.y;
+            dif.x = a.x - c.x;
+            dif.y = a.y - c.y;
+            yc[q + s * (2 * p)] = sum;
+            C r;
+            r.x = dif.x * w.x - dif.y * w.y;
+            r.y = dif.x * w.y + dif.y * w.x;
+            yc[q + s * (2 * p + 1)] = r;
+        }
+        __syncthreads();
+        C *tmp = x;
+        x = y;
+        y = tmp;
+    }
+    return x;
+}
+
+template <typename T>
+__device__ void fill_twiddles(typename Cplx<T>::type *tw, int L)
+{
+    for (int j = threadIdx.x; j < (L >> 1); j += blockDim.x) {
+        T s, c;
+        sincospi_t((T)(-2.0 * (double)j / (double)L), &s, &c);
+        tw[j].x = c;
+        tw[j].y = s;
+    }
+}
+
+// one block per (channel, chirp) row
+template <typename T>
+__global__ void range_fft_kernel(const typename Cplx<T>::type *__restrict__ adc,
+                                 typename Cplx<T>::type *__restrict__ X, int M, int window)
+{
+    using C = typename Cplx<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf0 = reinterpret_cast<C *>(smem_raw);
+    C *buf1 = buf0 + M;
+    C *tw = buf1 + M;
+    fill_twiddles<T>(tw, M);
+    const int64_t row = blockIdx.x;
+    const C *in = adc + row * M;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        const T w = window_val<T>(i, M, window);
+        C v = in[i];
+        v.x *= w;
+        v.y *= w;
+        buf0[i] = v;
+    }
+    __syncthreads();
+    const C *res = stockham<C>(buf0, buf1, tw, M, 1);
+    C *out = X + row * M;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) out[i] = res[i];
+}
+
+// one block per RB consecutive range bins, looping over channels
+template <typename T>
+__global__ void doppler_rdm_kernel(const typename Cplx<T>::type *__restrict__ X, int O, int N,
+                                   int M, int RB, int window, float *__restrict__ rdm)
+{
+    using C = typename Cplx<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf0 = reinterpret_cast<C *>(smem_raw);
+    C *buf1 = buf0 + RB * N;
+    C *tw = buf1 + RB * N;
+    T *pw = reinterpret_cast<T *>(tw + (N >> 1));     // RB * N accumulated power
+    fill_twiddles<T>(tw, N);
+    const int r0 = blockIdx.x * RB;
+    for (int i = threadIdx.x; i < RB * N; i += blockDim.x) pw[i] = (T)0;
+    for (int o = 0; o < O; ++o) {
+        __syncthreads();
+        // load X[o][n][r0 + c] into column-major buf0[c * N + n]
+        for (int i = threadIdx.x; i < RB * N; i += blockDim.x) {
+            const int n = i / RB, c = i % RB;
+            const T w = window_val<T>(n, N, window);
+            C v = X[((int64_t)o * N + n) * M + r0 + c];
+            v.x *= w;
+            v.y *= w;
+            buf0[c * N + n] = v;
+        }
+        __syncthreads();
+        const C *res = stockham<C>(buf0, buf1, tw, N, RB);
+        for (int i = threadIdx.x; i < RB * N; i += blockDim.x) {
+            const C v = res[i];
+            pw[i] += v.x * v.x + v.y * v.y;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < RB * N; i += blockDim.x) {
+        const int c = i / N, d = i % N;
+        rdm[(int64_t)(r0 + c) * N + ((d + (N >> 1)) & (N - 1))] = (float)pw[i];
+    }
+}
+
+static int rdm_rb(int N) { return N >= 2048 ? 1 : (2048 / N > 16 ? 16 : 2048 / N); }
+
+int64_t rdm_workspace_bytes(const RadarDev &rd, int dtype)
+{
+    const int64_t e = dtype == BART_C64 ? 8 : 16;
+    return (int64_t)rd.O * rd.N * rd.M * e;
+}
+
+template <typename T>
+static void run_rdm(const void *adc, const RadarDev &rd, void *ws, float *rdm, cudaStream_t s)
+{
+    using C = typename Cplx<T>::type;
+    const int M = rd.M, N = rd.N;
+    const size_t sm1 = (size_t)(2 * M + M / 2) * sizeof(C);
+    const int t1 = M / 2 < 1024 ? (M / 2 < 32 ? 32 : M / 2) : 1024;
+    cudaFuncSetAttribute(range_fft_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sm1);
+    range_fft_kernel<T><<<(unsigned int)((int64_t)rd.O * N), t1, sm1, s>>>(
+        reinterpret_cast<const C *>(adc), reinterpret_cast<C *>(ws), M, rd.window);
+    int RB = rdm_rb(N);
+    if (RB > M) RB = M;
+    const size_t sm2 = (size_t)(2 * RB * N + N / 2) * sizeof(C) + (size_t)RB * N * sizeof(T);
+    cudaFuncSetAttribute(doppler_rdm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sm2);
+    doppler_rdm_kernel<T><<<(unsigned int)(M / RB), 256, sm2, s>>>(
+        reinterpret_cast<const C *>(ws), rd.O, N, M, RB, rd.window, rdm);
+}
+
+void launch_rdm(const void *adc, int dtype, const RadarDev &rd, void *ws, float *rdm,
+                cudaStream_t s)
+{
+    if (dtype == BART_C64) run_rdm<float>(adc, rd, ws, rdm, s);
+    else run_rdm<double>(adc, rd, ws, rdm, s);
+}
+
+}  // namespace bart

@@ -1,0 +1,248 @@
+// BART single-bounce visibility (Sec. 2.2): the forward ray from a TX and the
+// backward ray from an RX "meet" on a facet when the facet is lit from the
+// TX and seen from the RX.  Each (antenna, facet) pair gets a state from the
+// facet-centroid -> antenna segment cast through the LBVH:
+//   BACK  (facing away), LIT, GRAZE (within margins: excluded, counted),
+//   OCCL  (a robust hit on another facet).
+// The segment/triangle decision is Moller-Trumbore (1997) in FP64 with one
+// IEEE rounding per operation in a fixed order (explicit __d*_rn intrinsics:
+// no FMA contraction), so states are reproducible bit for bit by any
+// IEEE-754 implementation of the same steps.  The BVH boxes are FP32,
+// rounded outward and padded, so box culling never drops a candidate.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bart_internal.cuh"
+
+namespace bart {
+
+__device__ __forceinline__ void sub3(const double *a, const double *b, double *o)
+{
+    o[0] = __dsub_rn(a[0], b[0]);
+    o[1] = __dsub_rn(a[1], b[1]);
+    o[2] = __dsub_rn(a[2], b[2]);
+}
+__device__ __forceinline__ double dot3(const double *a, const double *b)
+{
+    double s = __dmul_rn(a[0], b[0]);
+    s = __dadd_rn(s, __dmul_rn(a[1], b[1]));
+    s = __dadd_rn(s, __dmul_rn(a[2], b[2]));
+    return s;
+}
+__device__ __forceinline__ void cross3(const double *a, const double *b, double *o)
+{
+    o[0] = __dsub_rn(__dmul_rn(a[1], b[2]), __dmul_rn(a[2], b[1]));
+    o[1] = __dsub_rn(__dmul_rn(a[2], b[0]), __dmul_rn(a[0], b[2]));
+    o[2] = __dsub_rn(__dmul_rn(a[0], b[1]), __dmul_rn(a[1], b[0]));
+}
+
+// 2 = hit with margin, 1 = grazing (inside the margins), 0 = miss
+__device__ int mt_segment(const double *O, const double *D, const double *tri)
+{
+    double e1[3], e2[3], P[3], T[3], Qv[3];
+    sub3(tri + 3, tri, e1);
+    sub3(tri + 6, tri, e2);
+    cross3(D, e2, P);
+    const double det = dot3(e1, P);
+    if (det == 0.0) return 0;
+    const double inv = __ddiv_rn(1.0, det);
+    sub3(O, tri, T);
+    const double u = __dmul_rn(dot3(T, P), inv);
+    if (u < -kEpsB || u > __dadd_rn(1.0, kEpsB)) return 0;
+    cross3(T, e1, Qv);
+    const double v = __dmul_rn(dot3(D, Qv), inv);
+    const double uv = __dadd_rn(u, v);
+    if (v < -kEpsB || uv > __dadd_rn(1.0, kEpsB)) return 0;
+    const double t = __dmul_rn(dot3(e2, Qv), inv);
+    if (t < -kEpsT || t > __dadd_rn(1.0, kEpsT)) return 0;
+    if (u >= kEpsB && v >= kEpsB && uv <= __dsub_rn(1.0, kEpsB) && t >= kEpsT &&
+        t <= __dsub_rn(1.0, kEpsT))
+        return 2;
+    return 1;
+}
+
+__device__ __forceinline__ bool slab_hit(const float *bmin, const float *bmax, const float *o,
+                                         const float *inv)
+{
+    float tn = -1e-3f, tf = 1.0f + 1e-3f;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const float t0 = (bmin[r] - o[r]) * inv[r];
+        const float t1 = (bmax[r] - o[r]) * inv[r];
+        tn = fmaxf(tn, fminf(t0, t1));
+        tf = fminf(tf, fmaxf(t0, t1));
+    }
+    return tn <= tf;
+}
+
+constexpr int kStack = 64;
+
+__global__ void __launch_bounds__(128)
+visibility_kernel(const double *__restrict__ tri64, const double *__restrict__ c64,
+                  const BvhNode *__restrict__ nodes, int64_t F, RadarDev rd,
+                  uint8_t *__restrict__ state, unsigned long long *n_graze, int *status)
+{
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int a = blockIdx.y;
+    bool graze_flag = false;
+    if (gid < F) {
+        const int64_t k = gid;
+        const double *tk = tri64 + 9 * k;
+        double tri[9];
+        for (int i = 0; i < 9; ++i) tri[i] = tk[i];
+        const double c[3] = {c64[3 * k], c64[3 * k + 1], c64[3 * k + 2]};
+        const double pa[3] = {rd.ant[a][0], rd.ant[a][1], rd.ant[a][2]};
+        double e1[3], e2[3], n[3], D[3];
+        sub3(tri + 3, tri, e1);
+        sub3(tri + 6, tri, e2);
+        cross3(e1, e2, n);
+        sub3(pa, c, D);
+        const double cosang =
+            __ddiv_rn(dot3(n, D), __dmul_rn(__dsqrt_rn(dot3(n, n)), __dsqrt_rn(dot3(D, D))));
+        uint8_t st;
+        if (dot3(n, n) == 0.0 || cosang <= -kEpsFace) {   // zero area: no normal
+            st = BART_VIS_BACK;
+        } else {
+            bool graze = fabs(cosang) < kEpsFace;
+            bool hit = false;
+            if (F >= 2) {
+                const float o[3] = {(float)c[0], (float)c[1], (float)c[2]};
+                float inv[3];
+                for (int r = 0; r < 3; ++r) {
+                    float d = (float)D[r];
+                    if (fabsf(d) < 1e-30f) d = copysignf(1e-30f, d);
+                    inv[r] = 1.0f / d;
+                }
+                int stack[kStack];
+                int sp = 0;
+                stack[sp++] = 0;
+                while (sp > 0 && !hit) {
+                    const BvhNode nd = nodes[stack[--sp]];
+                    const bool hl = slab_hit(nd.lmin, nd.lmax, o, inv);
+                    const bool hr = slab_hit(nd.rmin, nd.rmax, o, inv);
+                    const int ch[2] = {nd.left, nd.right};
+                    const bool hh[2] = {hl, hr};
+                    for (int q = 0; q < 2 && !hit; ++q) {
+                        if (!hh[q]) continue;
+                        const int cc = ch[q];
+                        if (cc < 0) {
+                            const int64_t j = ~cc;
+                            if (j == k) continue;
+                            double tj[9];
+                            for (int i = 0; i < 9; ++i) tj[i] = tri64[9 * j + i];
+                            const int r = mt_segment(c, D, tj);
+                            if (r == 2) hit = true;
+                            else if (r == 1) graze = true;
+                        } else if (sp < kStack) {
+                            stack[sp++] = cc;
+                        } else {
+                            atomicOr(status, kStatusStackOverflow);
+                            graze = true;
+                        }
+                    }
+                }
+            }
+            st = hit ? BART_VIS_OCCL : (graze ? BART_VIS_GRAZE : BART_VIS_LIT);
+        }
+        state[(int64_t)a * F + k] = st;
+        graze_flag = (st == BART_VIS_GRAZE);
+    }
+    const unsigned int b = __ballot_sync(0xffffffffu, graze_flag);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(n_graze, (unsigned long long)__popc(b));
+}
+
+void launch_visibility(const double *tri64, const double *c64, const BvhNode *nodes, int64_t F,
+                       const RadarDev &rd, uint8_t *state, unsigned long long *n_graze,
+                       int *status, cudaStream_t s)
+{
+    const int T = 128;
+    dim3 grid((unsigned int)((F + T - 1) / T), (unsigned int)rd.A);
+    visibility_kernel<<<grid, T, 0, s>>>(tri64, c64, nodes, F, rd, state, n_graze, status);
+}
+
+// -------------------------------------------------------------------------
+// per-channel compaction of the facets lit from TX p AND RX q (ascending)
+// -------------------------------------------------------------------------
+constexpr int kCompactBlk = 1024;
+
+int64_t compact_blk_words(int64_t F, int O) { return (int64_t)O * ((F + kCompactBlk - 1) / kCompactBlk); }
+
+__device__ __forceinline__ bool lit_pair(const uint8_t *state, int64_t F, int p, int q, int P,
+                                         int64_t k)
+{
+    return state[(int64_t)p * F + k] == BART_VIS_LIT &&
+           state[(int64_t)(P + q) * F + k] == BART_VIS_LIT;
+}
+
+__global__ void compact_count_kernel(const uint8_t *__restrict__ state, int64_t F, int P, int Q,
+                                     int32_t *__restrict__ blk_cnt, int64_t nblk)
+{
+    const int o = blockIdx.y, p = o / Q, q = o % Q;
+    const int64_t k = (int64_t)blockIdx.x * kCompactBlk + threadIdx.x;
+    const bool lit = k < F && lit_pair(state, F, p, q, P, k);
+    const int c = __syncthreads_count(lit);
+    if (threadIdx.x == 0) blk_cnt[(int64_t)o * nblk + blockIdx.x] = c;
+}
+
+// exclusive scan of each channel's block counts (one warp per channel)
+__global__ void compact_scan_kernel(int32_t *__restrict__ blk_cnt, int64_t nblk,
+                                    int32_t *__restrict__ vis_cnt)
+{
+    const int o = blockIdx.x, lane = threadIdx.x;
+    int32_t *c = blk_cnt + (int64_t)o * nblk;
+    int32_t run = 0;
+    for (int64_t b0 = 0; b0 < nblk; b0 += 32) {
+        const int64_t b = b0 + lane;
+        const int32_t v = b < nblk ? c[b] : 0;
+        int32_t x = v;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, x, off);
+            if (lane >= off) x += y;
+        }
+        if (b < nblk) c[b] = run + x - v;
+        run += __shfl_sync(0xffffffffu, x, 31);
+    }
+    if (lane == 0) vis_cnt[o] = run;
+}
+
+__global__ void compact_write_kernel(const uint8_t *__restrict__ state, int64_t F, int P, int Q,
+                                     const int32_t *__restrict__ blk_cnt, int64_t nblk,
+                                     int32_t *__restrict__ vis_idx)
+{
+    __shared__ int32_t s_w[kCompactBlk / 32];
+    const int o = blockIdx.y, p = o / Q, q = o % Q;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int64_t k = (int64_t)blockIdx.x * kCompactBlk + t;
+    const bool lit = k < F && lit_pair(state, F, p, q, P, k);
+    const unsigned int b = __ballot_sync(0xffffffffu, lit);
+    if (lane == 0) s_w[warp] = __popc(b);
+    __syncthreads();
+    if (warp == 0) {
+        const int32_t v = s_w[lane];
+        int32_t x = v;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, x, off);
+            if (lane >= off) x += y;
+        }
+        s_w[lane] = x - v;
+    }
+    __syncthreads();
+    if (lit) {
+        const int32_t pos = blk_cnt[(int64_t)o * nblk + blockIdx.x] + s_w[warp] +
+                            __popc(b & ((1u << lane) - 1u));
+        vis_idx[(int64_t)o * F + pos] = (int32_t)k;
+    }
+}
+
+void launch_compact(const uint8_t *state, int64_t F, const RadarDev &rd, int32_t *blk_cnt,
+                    int32_t *vis_idx, int32_t *vis_cnt, cudaStream_t s)
+{
+    const int64_t nblk = (F + kCompactBlk - 1) / kCompactBlk;
+    dim3 grid((unsigned int)nblk, (unsigned int)rd.O);
+    compact_count_kernel<<<grid, kCompactBlk, 0, s>>>(state, F, rd.P, rd.Q, blk_cnt, nblk);
+    compact_scan_kernel<<<rd.O, 32, 0, s>>>(blk_cnt, nblk, vis_cnt);
+    compact_write_kernel<<<grid, kCompactBlk, 0, s>>>(state, F, rd.P, rd.Q, blk_cnt, nblk,
+                                                      vis_idx);
+}
+
+}  // namespace bart

@@ -1,0 +1,79 @@
+"""CPU checks of the C-ABI boundary: the library builds and loads, exports
+every function include/bartsim.h declares, the ctypes mirrors have the C
+struct layouts, and the product path fails loudly without a GPU."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2208_10939_gb300 as pkg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bartsim.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(bart_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2208_10939_gb300 import _build
+    _build.build()
+    return pkg.load_library()
+
+
+def test_header_declares_the_binding_names():
+    assert declared_functions() == sorted(pkg.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", pkg.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s(bart_\w+)", out))
+    missing = set(declared_functions()) - exported
+    assert not missing, missing
+    for name in declared_functions():
+        assert getattr(lib, name) is not None
+
+
+def test_struct_layouts_match_c(tmp_path):
+    prog = tmp_path / "sz.c"
+    prog.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "bartsim.h"\n'
+        'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(bart_instance),'
+        ' sizeof(bart_radar), sizeof(bart_stats), offsetof(bart_radar, tx),'
+        ' offsetof(bart_instance, pos));return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)],
+                   check=True)
+    vals = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True,
+                                        check=True).stdout.split()))
+    assert vals == [ctypes.sizeof(pkg.bart_instance), ctypes.sizeof(pkg.bart_radar),
+                    ctypes.sizeof(pkg.bart_stats), pkg.bart_radar.tx.offset,
+                    pkg.bart_instance.pos.offset]
+
+
+def test_version_and_error_string(lib):
+    assert "sm_103a" in pkg.bart_version()
+    assert lib.bart_last_error() is not None
+
+
+def test_create_without_gpu_fails_loudly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(pkg.BartError) as e:
+        pkg.bart_create(0)
+    assert e.value.code in (pkg.BART_ECUDA, pkg.BART_EINVAL)
+
+
+def test_null_arguments_are_rejected(lib):
+    assert lib.bart_set_stream(None, None) == pkg.BART_EINVAL
+    assert lib.bart_sync(None) == pkg.BART_EINVAL
+    assert lib.bart_radar_set(None, None) == pkg.BART_EINVAL
+    assert b"NULL" in lib.bart_last_error()
