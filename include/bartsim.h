@@ -83,9 +83,10 @@ typedef struct bart_instance {
  * contiguous (the paper's O x M x N data matrix, stored sample-major).
  * Sample m of chirp n is taken at t0 + n*Tc + m/fs; its instantaneous
  * transmit frequency is f0 + slope*m/fs.
- * Constraints (else BART_EINVAL): M a power of two in [32, 1024];
- * N a power of two in [2, 1024]; 1 <= P <= BART_MAX_TX; 1 <= Q <= BART_MAX_RX;
- * f0, slope, fs > 0; Tc >= M/fs. */
+ * Constraints (else BART_EINVAL): M a multiple of 32 in [32, 1024];
+ * 1 <= N <= 65536; 1 <= P <= BART_MAX_TX; 1 <= Q <= BART_MAX_RX;
+ * f0, slope, fs > 0; Tc >= M/fs.  bart_form_rdm further needs M and N
+ * powers of two (N <= 1024). */
 typedef struct bart_radar {
     double  f0;                  /* chirp start frequency, Hz */
     double  slope;               /* mu, Hz/s */
@@ -183,7 +184,8 @@ int bart_simulate_frame(bart_ctx *ctx, double t0, int32_t path, void *adc,
  * |.|^2 summed over the O channels, zero Doppler shifted to bin N/2.
  * adc: device pointer, O*N*M complex of `dtype` (FP64 arithmetic for C128,
  * FP32 for C64).  rdm: device pointer, M x N float32 (range-major).
- * Errors: ESTATE, EINVAL, ENOMEM, ECUDA. */
+ * Errors: ESTATE, EINVAL (M or N not a power of two, N > 1024), ENOMEM,
+ * ECUDA. */
 int bart_form_rdm(bart_ctx *ctx, const void *adc, int32_t dtype, float *rdm);
 
 /* One whole frame with host buffers: simulate into library-owned device

@@ -326,10 +326,10 @@ int bart_radar_set(bart_ctx *ctx, const bart_radar *r)
 {
     g_err.clear();
     if (!ctx || !r) return fail(BART_EINVAL, "bart_radar_set: NULL argument");
-    if (!is_pow2(r->M) || r->M < 32 || r->M > 1024)
-        return fail(BART_EINVAL, "bart_radar_set: M=%d must be a power of two in [32,1024]", r->M);
-    if (!is_pow2(r->N) || r->N < 2 || r->N > 1024)
-        return fail(BART_EINVAL, "bart_radar_set: N=%d must be a power of two in [2,1024]", r->N);
+    if (r->M < 32 || r->M > 1024 || r->M % 32 != 0)
+        return fail(BART_EINVAL, "bart_radar_set: M=%d must be a multiple of 32 in [32,1024]", r->M);
+    if (r->N < 1 || r->N > 65536)
+        return fail(BART_EINVAL, "bart_radar_set: N=%d out of [1,65536]", r->N);
     if (r->P < 1 || r->P > BART_MAX_TX || r->Q < 1 || r->Q > BART_MAX_RX)
         return fail(BART_EINVAL, "bart_radar_set: P=%d Q=%d out of range", r->P, r->Q);
     if (!(r->f0 > 0) || !(r->slope > 0) || !(r->fs > 0) || !(r->Tc > 0))
@@ -540,6 +540,10 @@ static int run_rdm(bart_ctx *ctx, const void *adc, int32_t dtype, float *rdm)
     if (!adc || !rdm) return fail(BART_EINVAL, "bart_form_rdm: NULL buffer");
     if (dtype != BART_C64 && dtype != BART_C128)
         return fail(BART_EINVAL, "bart_form_rdm: dtype=%d", dtype);
+    if (!is_pow2(ctx->radar.M) || !is_pow2(ctx->radar.N) || ctx->radar.N < 2 ||
+        ctx->radar.N > 1024)
+        return fail(BART_EINVAL, "bart_form_rdm: radix-2 FFTs need power-of-two M and N "
+                    "(M=%d, N=%d, N <= 1024)", ctx->radar.M, ctx->radar.N);
     BART_TRY(set_device(ctx));
     const RadarDev rd = make_rd(ctx->radar);
     BART_TRY(ctx->rdm_ws.ensure((size_t)rdm_workspace_bytes(rd, dtype), "rdm workspace"));

@@ -200,10 +200,15 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
             const float Rt = kt.w, Rr = kr.w, L = Rt + Rr;
             const float o_k = 0.5f * (fr.n[0] * b[0] + fr.n[1] * b[1] + fr.n[2] * b[2]);
             const float g = fr.rho * o_k / (Rt * Rr);
+            // in-plane part of b, formed once: u_v, |b_t|^2 and n x b_t all derive
+            // from it, so the forms below evaluate J exactly at one wave vector
+            // (|b|^2 - (b.n)^2 would cancel catastrophically near specular)
+            const float bn = fr.n[0] * b[0] + fr.n[1] * b[1] + fr.n[2] * b[2];
+            const float bt[3] = {b[0] - bn * fr.n[0], b[1] - bn * fr.n[1], b[2] - bn * fr.n[2]};
             float u[3];
 #pragma unroll
             for (int v = 0; v < 3; ++v)
-                u[v] = b[0] * fr.dv[3 * v] + b[1] * fr.dv[3 * v + 1] + b[2] * fr.dv[3 * v + 2];
+                u[v] = bt[0] * fr.dv[3 * v] + bt[1] * fr.dv[3 * v + 1] + bt[2] * fr.dv[3 * v + 2];
             float Ld = 0.f, Ldd = 0.f;
             if (A.rd.intra) {
                 const float v2 = vv.x * vv.x + vv.y * vv.y + vv.z * vv.z;
@@ -259,11 +264,10 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
                 R.hi = hi;
                 R.loc = loc;
                 R.p2 = p2;
-                const float bn = b[0] * fr.n[0] + b[1] * fr.n[1] + b[2] * fr.n[2];
-                const float bt2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2] - bn * bn;
-                const float nxb[3] = {fr.n[1] * b[2] - fr.n[2] * b[1],
-                                      fr.n[2] * b[0] - fr.n[0] * b[2],
-                                      fr.n[0] * b[1] - fr.n[1] * b[0]};
+                const float bt2 = bt[0] * bt[0] + bt[1] * bt[1] + bt[2] * bt[2];
+                const float nxb[3] = {fr.n[1] * bt[2] - fr.n[2] * bt[1],
+                                      fr.n[2] * bt[0] - fr.n[0] * bt[2],
+                                      fr.n[0] * bt[1] - fr.n[1] * bt[0]};
                 int flags = 0;
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
@@ -372,7 +376,7 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
                             sn = fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, 1.f / 362880.f, -1.f / 5040.f),
                                                         1.f / 120.f), -1.f / 6.f), 1.f);
                         } else {
-                            sn = __sinf(x) / x;
+                            sn = sinf(x) / x;   // accurate sinf: |x| may reach ~1e3
                         }
                         const float coef = kp * R.d[4 * e + 3] * sn;
                         pr[j] = fmaf(-coef, zs, pr[j]);
@@ -414,6 +418,15 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
     }
 }
 
+// consecutive samples per lane: the largest S in {8, 4, 2, 1} with 32 S | M;
+// a (channel, chirp) row of M samples then takes W = M / (32 S) warps
+static int samples_per_lane(int M)
+{
+    for (int S = 8; S > 1; S >>= 1)
+        if (M % (32 * S) == 0) return S;
+    return 1;
+}
+
 static MixConsts mix_consts(const RadarDev &rd)
 {
     MixConsts K;
@@ -442,7 +455,7 @@ void launch_synth_mixed(const SynthArgs &a, cudaStream_t s)
 {
     const MixConsts K = mix_consts(a.rd);
     const int M = a.rd.M;
-    const int S = M >= 256 ? 8 : M / 32;
+    const int S = samples_per_lane(M);
     const int W = M / (32 * S);
     const int64_t warps = (int64_t)a.rd.O * a.nc * W;
     const unsigned int grid = (unsigned int)((warps + kMixWarps - 1) / kMixWarps);
@@ -538,9 +551,11 @@ synth_fp64_kernel(SynthArgs A, int W)
             } else {
                 R.qt[1] = R.qr[1] = R.qt[2] = 0.0;
             }
+            const double bn = b[0] * nn[0] + b[1] * nn[1] + b[2] * nn[2];
+            const double bt[3] = {b[0] - bn * nn[0], b[1] - bn * nn[1], b[2] - bn * nn[2]};
             double u[3];
             for (int v = 0; v < 3; ++v)
-                u[v] = b[0] * dv[3 * v] + b[1] * dv[3 * v + 1] + b[2] * dv[3 * v + 2];
+                u[v] = bt[0] * dv[3 * v] + bt[1] * dv[3 * v + 1] + bt[2] * dv[3 * v + 2];
             const double umin = fmin(fmin(u[0], u[1]), u[2]);
             const double umax = fmax(fmax(u[0], u[1]), u[2]);
             const double dmin = fmin(fmin(fabs(u[0] - u[1]), fabs(u[1] - u[2])),
@@ -564,10 +579,9 @@ synth_fp64_kernel(SynthArgs A, int W)
                     R.d[9 + i] = ((i & 1) ? sc : -sc) * h[2 * i + 1] * c_inv_fact[2 * i + 3];
             } else if (kmax * dmin < kEdgeKd) {
                 cls = R.kind = kRecEdge;
-                const double bn = b[0] * nn[0] + b[1] * nn[1] + b[2] * nn[2];
-                const double bt2 = b[0] * b[0] + b[1] * b[1] + b[2] * b[2] - bn * bn;
-                const double nxb[3] = {nn[1] * b[2] - nn[2] * b[1], nn[2] * b[0] - nn[0] * b[2],
-                                       nn[0] * b[1] - nn[1] * b[0]};
+                const double bt2 = bt[0] * bt[0] + bt[1] * bt[1] + bt[2] * bt[2];
+                const double nxb[3] = {nn[1] * bt[2] - nn[2] * bt[1], nn[2] * bt[0] - nn[0] * bt[2],
+                                       nn[0] * bt[1] - nn[1] * bt[0]};
                 int flags = 0;
                 for (int i = 0; i < 3; ++i) {
                     const int i1 = (i + 1) % 3;
@@ -676,7 +690,7 @@ synth_fp64_kernel(SynthArgs A, int W)
 void launch_synth_fp64(const SynthArgs &a, cudaStream_t s)
 {
     const int M = a.rd.M;
-    const int S = M >= 256 ? 8 : M / 32;
+    const int S = samples_per_lane(M);
     const int W = M / (32 * S);
     const int64_t warps = (int64_t)a.rd.O * a.rd.N * W;
     const unsigned int grid = (unsigned int)((warps + kF64Warps - 1) / kF64Warps);
