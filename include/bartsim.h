@@ -188,6 +188,33 @@ int bart_simulate_frame(bart_ctx *ctx, double t0, int32_t path, void *adc,
  * ECUDA. */
 int bart_form_rdm(bart_ctx *ctx, const void *adc, int32_t dtype, float *rdm);
 
+/* bart_form_rdm without any device allocation, for callers that cannot let
+ * a library allocate GPU memory: applications that own all device memory
+ * through their own pool allocator or run under a hard memory cap (a
+ * foreign cudaMalloc breaks their accounting or fails), and latency-bound
+ * loops where cudaMalloc/cudaFree would stall on a device synchronisation.
+ * The paper has no counterpart; it is an operational variant of the RDM
+ * (Sec. 3.3) computation above and gives the same result.
+ *
+ * No context is needed: the cube shape is passed explicitly.  adc: device
+ * pointer, O*N*M complex samples of `dtype`, [O][N][M]; rdm: device pointer,
+ * M x N float32; window: BART_WINDOW_*; stream: a cudaStream_t (0 = legacy
+ * default stream) on the current device.  The range-FFT intermediate lives
+ * in a fixed 16 MiB array compiled into the library, which every GPU that
+ * loads the library holds until the process exits; cubes needing more
+ * (O*N*M > 2^21 complex64 or 2^20 complex128 samples) are rejected with
+ * BART_EINVAL.  M and N must be powers of two (M in [32, 1024], N in
+ * [2, 1024]).  The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  The array is shared by every call and keeps
+ * the last call's contents (each call overwrites the part it reads before
+ * reading it, so nothing carries over); calls that overlap on the GPU,
+ * from any thread or stream, race on it and must be serialised by the
+ * caller.  The call calls no cudaMalloc/cudaFree.
+ * Errors: EINVAL, ECUDA. */
+int bart_form_rdm_static(const void *adc, int32_t dtype, int32_t O, int32_t N,
+                         int32_t M, int32_t window, float *rdm, void *stream);
+
 /* One whole frame with host buffers: simulate into library-owned device
  * memory, form the RDM and copy it to the host array rdm_host (M x N
  * float32), then synchronise.  Meshes/instances/radar must already be set.

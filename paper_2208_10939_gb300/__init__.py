@@ -33,7 +33,7 @@ EXPORTED = ["bart_last_error", "bart_version", "bart_create", "bart_destroy",
             "bart_set_stream", "bart_mesh_upload", "bart_mesh_clear", "bart_scene_set",
             "bart_scene_facets", "bart_radar_set", "bart_simulate_frame", "bart_form_rdm",
             "bart_frame_host", "bart_get_visibility", "bart_set_timing", "bart_get_timing",
-            "bart_sync"]
+            "bart_sync", "bart_form_rdm_static"]
 
 
 class BartError(RuntimeError):
@@ -117,6 +117,7 @@ def load_library() -> ctypes.CDLL:
         L.bart_set_timing.argtypes = [P, I32]
         L.bart_get_timing.argtypes = [P, ctypes.POINTER(bart_timing)]
         L.bart_sync.argtypes = [P]
+        L.bart_form_rdm_static.argtypes = [P, I32, I32, I32, I32, I32, P, P]
         for name in EXPORTED:
             if name not in ("bart_last_error", "bart_version", "bart_destroy"):
                 getattr(L, name).restype = ctypes.c_int
@@ -261,6 +262,19 @@ def bart_frame_host(ctx: int, t0: float, path: int, rdm_host, stats: bool = Fals
                                           ctypes.c_void_p(_ptr(rdm_host)),
                                           ctypes.byref(st) if st is not None else None))
     return st.as_dict() if st is not None else None
+
+
+def bart_form_rdm_static(adc, rdm, O: int, N: int, M: int, window: int = WINDOW_HANN,
+                         stream: Optional[int] = None) -> None:
+    """RDM of ``adc`` into ``rdm`` without any device allocation by the
+    library (its workspace is a fixed array compiled into it); see
+    ``include/bartsim.h`` for the size limit and the sharing rules."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(adc.device).cuda_stream
+    _check(load_library().bart_form_rdm_static(
+        ctypes.c_void_p(_ptr(adc)), _dtype_code(adc), int(O), int(N), int(M), int(window),
+        ctypes.c_void_p(_ptr(rdm)), ctypes.c_void_p(int(stream))))
 
 
 def bart_get_visibility(ctx: int, state) -> None:

@@ -138,4 +138,10 @@ int64_t rdm_workspace_bytes(const RadarDev &rd, int dtype);
 void launch_rdm(const void *adc, int dtype, const RadarDev &rd, void *ws, float *rdm,
                 cudaStream_t s);
 
+// Size of the static workspace used by bart_form_rdm_static (16 MiB).
+constexpr int64_t kRdmStaticWorkspaceBytes = 16ll << 20;
+// Device address of that workspace on the current device (looked up on the
+// first call per device).  Returns BART_OK or BART_ECUDA with *err set.
+int rdm_static_workspace(void **ws, const char **err);
+
 }  // namespace bart

@@ -568,6 +568,42 @@ int bart_form_rdm(bart_ctx *ctx, const void *adc, int32_t dtype, float *rdm)
     return run_rdm(ctx, adc, dtype, rdm);
 }
 
+int bart_form_rdm_static(const void *adc, int32_t dtype, int32_t O, int32_t N, int32_t M,
+                         int32_t window, float *rdm, void *stream)
+{
+    g_err.clear();
+    if (!adc || !rdm) return fail(BART_EINVAL, "bart_form_rdm_static: NULL buffer");
+    if (dtype != BART_C64 && dtype != BART_C128)
+        return fail(BART_EINVAL, "bart_form_rdm_static: dtype=%d", dtype);
+    if (window != BART_WINDOW_HANN && window != BART_WINDOW_RECT)
+        return fail(BART_EINVAL, "bart_form_rdm_static: window=%d", window);
+    if (O < 1 || !is_pow2(M) || M < 32 || M > 1024 || !is_pow2(N) || N < 2 || N > 1024)
+        return fail(BART_EINVAL, "bart_form_rdm_static: need O >= 1 and power-of-two "
+                    "M in [32,1024], N in [2,1024] (O=%d N=%d M=%d)", O, N, M);
+    RadarDev rd;
+    std::memset(&rd, 0, sizeof rd);
+    rd.O = O;
+    rd.N = N;
+    rd.M = M;
+    rd.P = O;
+    rd.Q = 1;
+    rd.window = window;
+    const int64_t need = rdm_workspace_bytes(rd, dtype);
+    if (need > kRdmStaticWorkspaceBytes)
+        return fail(BART_EINVAL, "bart_form_rdm_static: the cube needs %lld bytes of workspace, "
+                    "more than the fixed %lld (O*N*M <= %lld complex%s samples)",
+                    (long long)need, (long long)kRdmStaticWorkspaceBytes,
+                    (long long)(kRdmStaticWorkspaceBytes / (dtype == BART_C64 ? 8 : 16)),
+                    dtype == BART_C64 ? "64" : "128");
+    void *ws = nullptr;
+    const char *err = nullptr;
+    const int rc = rdm_static_workspace(&ws, &err);
+    if (rc != BART_OK) return fail(rc, "bart_form_rdm_static: %s", err);
+    launch_rdm(adc, dtype, rd, ws, rdm, reinterpret_cast<cudaStream_t>(stream));
+    CUDA_TRY(cudaGetLastError(), "bart_form_rdm_static launch");
+    return BART_OK;
+}
+
 int bart_frame_host(bart_ctx *ctx, double t0, int32_t path, float *rdm_host, bart_stats *stats)
 {
     g_err.clear();
