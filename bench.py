@@ -268,8 +268,9 @@ def main():
 
     # plain FP64 path on the same frame (fewer steps: it is the reference path)
     adc64 = torch.empty((O, N, M), dtype=torch.complex128, device=dev)
-    sim.simulate(pkg.PATH_FP64, out=adc64)
-    sim.sync()
+    if args.fp64_steps > 0:
+        sim.simulate(pkg.PATH_FP64, out=adc64)
+        sim.sync()
     f64_ms, f64_syn = [], []
     for _ in range(args.fp64_steps):
         flush.zero_()
@@ -284,8 +285,10 @@ def main():
         f64_ms.append(e0.elapsed_time(e1))
         f64_syn.append(tm64["synthesis_ms"])
     del adc64
-    fp64 = {"value": terms * len(f64_ms) / (sum(f64_ms) / 1e3), "unit": UNIT,
-            "ms_per_step": statistics.mean(f64_ms), "synthesis_ms": statistics.mean(f64_syn)}
+    fp64 = None
+    if f64_ms:
+        fp64 = {"value": terms * len(f64_ms) / (sum(f64_ms) / 1e3), "unit": UNIT,
+                "ms_per_step": statistics.mean(f64_ms), "synthesis_ms": statistics.mean(f64_syn)}
 
     # end to end through the public API with host buffers: every step uploads
     # the mesh and the instance from pinned host memory and reads the RDM back

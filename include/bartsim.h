@@ -84,7 +84,7 @@ typedef struct bart_instance {
  * Sample m of chirp n is taken at t0 + n*Tc + m/fs; its instantaneous
  * transmit frequency is f0 + slope*m/fs.
  * Constraints (else BART_EINVAL): M a multiple of 32 in [32, 1024];
- * 1 <= N <= 65536; 1 <= P <= BART_MAX_TX; 1 <= Q <= BART_MAX_RX;
+ * 1 <= N <= 32768; 1 <= P <= BART_MAX_TX; 1 <= Q <= BART_MAX_RX;
  * f0, slope, fs > 0; Tc >= M/fs.  bart_form_rdm further needs M and N
  * powers of two (N <= 1024). */
 typedef struct bart_radar {
@@ -118,7 +118,8 @@ typedef struct bart_timing {
     float   scene_ms;        /* world facets at t0 */
     float   bvh_ms;          /* Morton codes, radix sort, hierarchy, refit */
     float   visibility_ms;   /* visibility states + per-channel lit lists */
-    float   kinematics_ms;   /* FP64 per-chirp path lengths (mixed path) */
+    float   kinematics_ms;   /* FP64 per-chirp path lengths (mixed path; runs on an
+                                internal stream, overlapping the synthesis) */
     float   synthesis_ms;    /* echo-synthesis kernels */
     float   rdm_ms;          /* last bart_form_rdm */
     int32_t synthesis_launches;   /* synthesis kernel launches in the frame */

@@ -103,12 +103,15 @@ void launch_lbvh_refit(const int32_t *vals, const float *aabb, int64_t n, BvhNod
                        cudaStream_t s);
 
 // ---- visibility (visibility.cu) ----
+// order: facet ids in the sequence the ray threads take them (Morton order), or NULL
 void launch_visibility(const double *tri64, const double *c64, const BvhNode *nodes,
-                       int64_t F, const RadarDev &rd, uint8_t *state,
+                       const int32_t *order, int64_t F, const RadarDev &rd, uint8_t *state,
                        unsigned long long *n_graze, int *status, cudaStream_t s);
+// lists 0..O-1: facets lit from both antennas of each channel; O..O+A-1: facets
+// lit from each antenna.  vis_idx is [O+A][F], vis_cnt [O+A].
 void launch_compact(const uint8_t *state, int64_t F, const RadarDev &rd,
                     int32_t *blk_cnt, int32_t *vis_idx, int32_t *vis_cnt, cudaStream_t s);
-int64_t compact_blk_words(int64_t F, int O);
+int64_t compact_blk_words(int64_t F, int L);
 
 // ---- synthesis (synth.cu) ----
 struct SynthArgs {
@@ -125,12 +128,19 @@ struct SynthArgs {
     void *out;
     int out_c64;
     unsigned long long *counters;   // [0] vertex, [1] series, [2] edge records
+    // mixed path work queue (see synth.cu)
+    int32_t *item_off;       // [O + 1] first work item of each channel
+    int *item_counter;       // next item to hand out
+    float2 *partial;         // [items][32 S] unscaled partial sums
+    int tiles_per_item;      // 32-record tiles per item
     RadarDev rd;
 };
 void launch_kinematics(const double *c64, const FacetRec *fac, const double *vel64,
-                       const uint8_t *state, int64_t F, const RadarDev &rd, int n0, int nc,
-                       float4 *kin, cudaStream_t s);
+                       const int32_t *vis_idx, const int32_t *vis_cnt, int64_t F,
+                       const RadarDev &rd, int n0, int nc, float4 *kin, cudaStream_t s);
 void launch_synth_mixed(const SynthArgs &a, cudaStream_t s);
+// scratch of the mixed path for F facets and a chunk of nc chirps
+int64_t synth_partial_words(int64_t F, const RadarDev &rd, int nc);   // float2 words
 void launch_synth_fp64(const SynthArgs &a, cudaStream_t s);
 
 // ---- range-Doppler map (rdm.cu) ----

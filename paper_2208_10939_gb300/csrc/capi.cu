@@ -103,6 +103,9 @@ struct bart_ctx {
     DevBuf<uint8_t> state;
     DevBuf<int32_t> blk_cnt, vis_idx, vis_cnt;
     DevBuf<float4> kin;
+    DevBuf<float2> partial;             // mixed-path per-item partial sums
+    DevBuf<int32_t> item_off;
+    DevBuf<int> item_counter;
     DevBuf<unsigned long long> counters;   // 0 vertex, 1 series, 2 edge, 3 grazing
     DevBuf<int> status;
     DevBuf<unsigned char> rdm_ws, adc_own;
@@ -113,6 +116,9 @@ struct bart_ctx {
     std::vector<cudaEvent_t> ev;        // 0 start, 1 facets, 2 bvh, 3 vis, 4 end, 5/6 rdm
     std::vector<cudaEvent_t> ev_kin;    // per chunk: before kin, after kin (= before synth)
     std::vector<cudaEvent_t> ev_syn;    // per chunk: after synth
+    // side stream running the kinematics of chunk c+1 while chunk c is synthesised
+    cudaStream_t side = nullptr;
+    std::vector<cudaEvent_t> sync_ev;   // fork + per-chunk kin-done / synth-done (no timing)
     int chunks = 0;
     int path = 0;
     bool have_rdm_timing = false;
@@ -124,6 +130,8 @@ struct bart_ctx {
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
         for (cudaEvent_t e : ev_kin) cudaEventDestroy(e);
         for (cudaEvent_t e : ev_syn) cudaEventDestroy(e);
+        for (cudaEvent_t e : sync_ev) cudaEventDestroy(e);
+        if (side) cudaStreamDestroy(side);
         for (MeshStore *m : pool) {
             m->verts.release();
             m->tris.release();
@@ -135,7 +143,8 @@ struct bart_ctx {
         keys.release(); keys_tmp.release(); sort_temp.release(); vals.release();
         vals_tmp.release(); nodes.release(); parent.release(); leaf_parent.release();
         flags.release(); state.release(); blk_cnt.release(); vis_idx.release();
-        vis_cnt.release(); kin.release(); counters.release(); status.release();
+        vis_cnt.release(); kin.release(); partial.release(); item_off.release();
+        item_counter.release(); counters.release(); status.release();
         rdm_ws.release(); adc_own.release(); rdm_own.release();
     }
 };
@@ -177,11 +186,12 @@ static RadarDev make_rd(const bart_radar &r)
     return d;
 }
 
-static int ensure_events(std::vector<cudaEvent_t> &v, size_t n)
+static int ensure_events(std::vector<cudaEvent_t> &v, size_t n, bool timing = true)
 {
     while (v.size() < n) {
         cudaEvent_t e;
-        CUDA_TRY(cudaEventCreate(&e), "cudaEventCreate");
+        CUDA_TRY(cudaEventCreateWithFlags(&e, timing ? cudaEventDefault : cudaEventDisableTiming),
+                 "cudaEventCreate");
         v.push_back(e);
     }
     return BART_OK;
@@ -328,8 +338,8 @@ int bart_radar_set(bart_ctx *ctx, const bart_radar *r)
     if (!ctx || !r) return fail(BART_EINVAL, "bart_radar_set: NULL argument");
     if (r->M < 32 || r->M > 1024 || r->M % 32 != 0)
         return fail(BART_EINVAL, "bart_radar_set: M=%d must be a multiple of 32 in [32,1024]", r->M);
-    if (r->N < 1 || r->N > 65536)
-        return fail(BART_EINVAL, "bart_radar_set: N=%d out of [1,65536]", r->N);
+    if (r->N < 1 || r->N > 32768)
+        return fail(BART_EINVAL, "bart_radar_set: N=%d out of [1,32768]", r->N);
     if (r->P < 1 || r->P > BART_MAX_TX || r->Q < 1 || r->Q > BART_MAX_RX)
         return fail(BART_EINVAL, "bart_radar_set: P=%d Q=%d out of range", r->P, r->Q);
     if (!(r->f0 > 0) || !(r->slope > 0) || !(r->fs > 0) || !(r->Tc > 0))
@@ -404,9 +414,9 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
     BART_TRY(ctx->leaf_parent.ensure(F, "bvh leaf parents"));
     BART_TRY(ctx->flags.ensure(F > 1 ? F - 1 : 1, "bvh refit flags"));
     BART_TRY(ctx->state.ensure((size_t)A * F, "visibility states"));
-    BART_TRY(ctx->blk_cnt.ensure(compact_blk_words(F, O), "compaction counts"));
-    BART_TRY(ctx->vis_idx.ensure((size_t)O * F, "lit facet lists"));
-    BART_TRY(ctx->vis_cnt.ensure(O, "lit facet counts"));
+    BART_TRY(ctx->blk_cnt.ensure(compact_blk_words(F, O + A), "compaction counts"));
+    BART_TRY(ctx->vis_idx.ensure((size_t)(O + A) * F, "lit facet lists"));
+    BART_TRY(ctx->vis_cnt.ensure(O + A, "lit facet counts"));
 
     if (ctx->tables_dirty) {
         // pageable sources: each copy is staged before the call returns
@@ -445,8 +455,8 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
     launches += 1 + 3 * 4 + (F >= 2 ? 2 : 0);
     if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[2], s), "cudaEventRecord");
     // 3. visibility + per-channel lit lists
-    launch_visibility(ctx->tri64.p, ctx->c64.p, ctx->nodes.p, F, rd, ctx->state.p,
-                      ctx->counters.p + 3, ctx->status.p, s);
+    launch_visibility(ctx->tri64.p, ctx->c64.p, ctx->nodes.p, F >= 2 ? ctx->vals.p : nullptr, F,
+                      rd, ctx->state.p, ctx->counters.p + 3, ctx->status.p, s);
     launch_compact(ctx->state.p, F, rd, ctx->blk_cnt.p, ctx->vis_idx.p, ctx->vis_cnt.p, s);
     launches += 1 + 3;
     if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[3], s), "cudaEventRecord");
@@ -464,31 +474,67 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
     a.out = adc;
     a.out_c64 = dtype == BART_C64;
     a.counters = ctx->counters.p;
+    a.item_off = nullptr;
+    a.item_counter = nullptr;
+    a.partial = nullptr;
+    a.tiles_per_item = 0;
     a.rd = rd;
     if (path == BART_PATH_MIXED) {
+        // chirp chunks only when the kinematics table would exceed its budget;
+        // the table is then double-buffered so that the side stream fills
+        // chunk c+1 while the main stream synthesises chunk c (one chunk
+        // measured faster than forced chunking at the sedan size)
         const int64_t per_chirp = (int64_t)A * F * (int64_t)sizeof(float4);
-        int nc = (int)std::min<int64_t>(rd.N, std::max<int64_t>(1, ctx->kin_budget / per_chirp));
-        BART_TRY(ctx->kin.ensure((size_t)nc * A * F, "kinematics table"));
-        a.kin = ctx->kin.p;
+        const int nc = (int)std::min<int64_t>(rd.N, std::max<int64_t>(1, ctx->kin_budget / per_chirp));
         const int chunks = (rd.N + nc - 1) / nc;
+        const int nbuf = chunks > 1 ? 2 : 1;
+        const size_t chunk_words = (size_t)nc * A * F;
+        BART_TRY(ctx->kin.ensure(nbuf * chunk_words, "kinematics table"));
+        BART_TRY(ctx->partial.ensure((size_t)synth_partial_words(F, rd, nc), "synthesis partials"));
+        BART_TRY(ctx->item_off.ensure(O + 1, "synthesis item table"));
+        BART_TRY(ctx->item_counter.ensure(1, "synthesis item counter"));
+        if (!ctx->side)
+            CUDA_TRY(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking), "cudaStreamCreate");
+        BART_TRY(ensure_events(ctx->sync_ev, 1 + 2 * chunks, false));
+        cudaEvent_t fork = ctx->sync_ev[0];
+        cudaEvent_t *kin_done = ctx->sync_ev.data() + 1;
+        cudaEvent_t *syn_done = ctx->sync_ev.data() + 1 + chunks;
+        a.partial = ctx->partial.p;
+        a.item_off = ctx->item_off.p;
+        a.item_counter = ctx->item_counter.p;
         if (tm) {
             BART_TRY(ensure_events(ctx->ev_kin, 2 * chunks));
-            BART_TRY(ensure_events(ctx->ev_syn, chunks));
+            BART_TRY(ensure_events(ctx->ev_syn, 2 * chunks));
         }
-        for (int c = 0; c < chunks; ++c) {
+        CUDA_TRY(cudaEventRecord(fork, s), "cudaEventRecord");
+        CUDA_TRY(cudaStreamWaitEvent(ctx->side, fork, 0), "cudaStreamWaitEvent");
+        auto kin_chunk = [&](int c) -> int {
             const int n0 = c * nc;
             const int cnt = std::min(nc, rd.N - n0);
-            if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_kin[2 * c], s), "cudaEventRecord");
-            launch_kinematics(ctx->c64.p, ctx->fac.p, ctx->vel64.p, ctx->state.p, F, rd, n0, cnt,
-                              ctx->kin.p, s);
-            if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_kin[2 * c + 1], s), "cudaEventRecord");
-            a.n0 = n0;
-            a.nc = cnt;
+            if (c >= 2)   // its buffer was read by the synthesis of chunk c-2
+                CUDA_TRY(cudaStreamWaitEvent(ctx->side, syn_done[c - 2], 0), "cudaStreamWaitEvent");
+            if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_kin[2 * c], ctx->side), "cudaEventRecord");
+            launch_kinematics(ctx->c64.p, ctx->fac.p, ctx->vel64.p, ctx->vis_idx.p,
+                              ctx->vis_cnt.p, F, rd, n0, cnt, ctx->kin.p + (c % nbuf) * chunk_words,
+                              ctx->side);
+            if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_kin[2 * c + 1], ctx->side), "cudaEventRecord");
+            CUDA_TRY(cudaEventRecord(kin_done[c], ctx->side), "cudaEventRecord");
+            return BART_OK;
+        };
+        BART_TRY(kin_chunk(0));
+        for (int c = 0; c < chunks; ++c) {
+            if (c + 1 < chunks) BART_TRY(kin_chunk(c + 1));
+            CUDA_TRY(cudaStreamWaitEvent(s, kin_done[c], 0), "cudaStreamWaitEvent");
+            a.n0 = c * nc;
+            a.nc = std::min(nc, rd.N - a.n0);
+            a.kin = ctx->kin.p + (c % nbuf) * chunk_words;
+            if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_syn[2 * c], s), "cudaEventRecord");
             launch_synth_mixed(a, s);
-            if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_syn[c], s), "cudaEventRecord");
+            if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_syn[2 * c + 1], s), "cudaEventRecord");
+            CUDA_TRY(cudaEventRecord(syn_done[c], s), "cudaEventRecord");
         }
         ctx->chunks = chunks;
-        launches += 2 * chunks;
+        launches += 4 * chunks;
     } else {
         a.n0 = 0;
         a.nc = rd.N;
@@ -662,9 +708,11 @@ int bart_get_timing(bart_ctx *ctx, bart_timing *out)
     out->bvh_ms = elapsed(ctx->ev[1], ctx->ev[2]);
     out->visibility_ms = elapsed(ctx->ev[2], ctx->ev[3]);
     if (ctx->path == BART_PATH_MIXED) {
+        // kinematics runs on a side stream, overlapping the synthesis of the
+        // previous chunk: both sums are device time, not wall time
         for (int c = 0; c < ctx->chunks; ++c) {
             out->kinematics_ms += elapsed(ctx->ev_kin[2 * c], ctx->ev_kin[2 * c + 1]);
-            out->synthesis_ms += elapsed(ctx->ev_kin[2 * c + 1], ctx->ev_syn[c]);
+            out->synthesis_ms += elapsed(ctx->ev_syn[2 * c], ctx->ev_syn[2 * c + 1]);
         }
     } else {
         out->synthesis_ms = elapsed(ctx->ev[3], ctx->ev[4]);

@@ -40,6 +40,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "bart_internal.cuh"
 
 namespace bart {
@@ -57,14 +59,30 @@ __constant__ double c_inv_fact[18] = {
 //   hi = x1 rounded to a multiple of 2^-14, lo = x1 - hi
 // stored as float4 (x0, hi, lo, R).  Since m is an integer, frac(L q m) =
 // frac(frac(L q) m) and frac(hi m) is exact in FP32 for m < 1024.
+//
+// R(t) = sqrt(A + B t + C t^2) is expanded about the middle of the frame,
+// R = sum_j a_j tau^j, with a_0 = sqrt(q_0) and
+// a_j = (q_j - sum_{i=1}^{j-1} a_i a_{j-i}) / (2 a_0)  (from R^2 = q).  The
+// series converges with ratio rho = tau_max |v| / R (the roots of q lie at
+// |tau| = R/|v|); the degree is the smallest d <= 8 with
+// R rho^(d+1) / (1 - rho) <= 1e-11 m, else R is taken by a square root per
+// chirp.  This replaces an FP64 square root per chirp by d FMAs.
 // -------------------------------------------------------------------------
+constexpr int kKinMaxDeg = 8;
+constexpr int kKinChirpsPerThread = 16;   // chirps per thread: enough warps to hide FP64 latency
+
 __global__ void kin_kernel(const double *__restrict__ c64, const FacetRec *__restrict__ fac,
-                           const double *__restrict__ vel64, const uint8_t *__restrict__ state,
-                           int64_t F, RadarDev rd, int n0, int nc, float4 *__restrict__ kin)
+                           const double *__restrict__ vel64, const int32_t *__restrict__ vis_idx,
+                           const int32_t *__restrict__ vis_cnt, int64_t F, RadarDev rd, int n0,
+                           int nc, float4 *__restrict__ kin)
 {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int a = blockIdx.y;
-    if (k >= F || state[(int64_t)a * F + k] != BART_VIS_LIT) return;
+    if (i >= vis_cnt[rd.O + a]) return;              // facets lit from antenna a
+    // this thread's group of chirps within the chunk
+    const int g0 = blockIdx.z * kKinChirpsPerThread;
+    const int g1 = min(nc, g0 + kKinChirpsPerThread);
+    const int64_t k = vis_idx[(int64_t)(rd.O + a) * F + i];
     const int inst = fac[k].inst;
     const double vx = vel64[3 * inst], vy = vel64[3 * inst + 1], vz = vel64[3 * inst + 2];
     const double dx = c64[3 * k] - rd.ant[a][0];
@@ -74,27 +92,82 @@ __global__ void kin_kernel(const double *__restrict__ c64, const FacetRec *__res
     const double B = 2.0 * (dx * vx + dy * vy + dz * vz);
     const double Cq = vx * vx + vy * vy + vz * vz;
     const double f0c = rd.f0 / kC0;
-    const double muc = rd.slope / (rd.fs * kC0);
-    for (int nl = 0; nl < nc; ++nl) {
+    const double mu_f0 = rd.slope / (rd.fs * rd.f0);          // (mu/(fs c)) / (f0/c)
+    // expansion point: middle of the frame's chirp starts
+    const double tc = 0.5 * (double)(rd.N - 1) * rd.Tc;
+    const double tmax = tc > 0.0 ? tc : rd.Tc;
+    const double q0 = A + tc * (B + tc * Cq), q1 = B + 2.0 * Cq * tc;
+    const double a0 = sqrt(q0);
+    const double rho = tmax * sqrt(Cq / q0);
+    int deg = -1;
+    if (rho < 0.25) {
+        double bound = a0 * rho * rho / (1.0 - rho);
+        for (int d = 1; d <= kKinMaxDeg; ++d, bound *= rho)
+            if (bound <= 1e-11) { deg = d; break; }
+    }
+    // all kKinMaxDeg + 1 coefficients are formed (constant indices keep them
+    // in registers); only the first deg + 1 are used
+    double cf[kKinMaxDeg + 1];                   // f0/c * a_j: R in cycles at f0
+    float cr[kKinMaxDeg + 1];                    // a_j in FP32, for R itself
+    {
+        double aj[kKinMaxDeg + 1];
+        aj[0] = a0;
+        const double inv2a0 = 0.5 / a0;
+#pragma unroll
+        for (int j = 1; j <= kKinMaxDeg; ++j) {
+            double sacc = j == 1 ? q1 : (j == 2 ? Cq : 0.0);
+#pragma unroll
+            for (int l = 1; l < j; ++l) sacc -= aj[l] * aj[j - l];
+            aj[j] = sacc * inv2a0;
+        }
+#pragma unroll
+        for (int j = 0; j <= kKinMaxDeg; ++j) {
+            cf[j] = f0c * aj[j];
+            cr[j] = (float)aj[j];
+        }
+    }
+    for (int nl = g0; nl < g1; ++nl) {
         const double t = (double)(n0 + nl) * rd.Tc;
-        const double R = sqrt(A + t * (B + t * Cq));
-        double x0 = R * f0c;
-        x0 -= floor(x0);
-        double x1 = R * muc;
+        const double tau = t - tc;
+        double x0u = 0.0;
+        float Rf = 0.f;
+        switch (deg) {
+#define BART_KIN_CASE(D)                                                  \
+        case D: {                                                         \
+            const float tauf = (float)tau;                                \
+            x0u = cf[D];                                                  \
+            Rf = cr[D];                                                   \
+            _Pragma("unroll") for (int j = D - 1; j >= 0; --j) {          \
+                x0u = fma(x0u, tau, cf[j]);                               \
+                Rf = fmaf(Rf, tauf, cr[j]);                               \
+            }                                                             \
+        } break;
+        BART_KIN_CASE(1) BART_KIN_CASE(2) BART_KIN_CASE(3) BART_KIN_CASE(4)
+        BART_KIN_CASE(5) BART_KIN_CASE(6) BART_KIN_CASE(7) BART_KIN_CASE(8)
+#undef BART_KIN_CASE
+        default: {
+            const double R = sqrt(A + t * (B + t * Cq));
+            x0u = R * f0c;
+            Rf = (float)R;
+        }
+        }
+        double x1 = x0u * mu_f0;
         x1 -= floor(x1);
+        const double x0 = x0u - floor(x0u);
         const double hi = rint(x1 * 16384.0) * (1.0 / 16384.0);
         kin[((int64_t)nl * rd.A + a) * F + k] =
-            make_float4((float)x0, (float)hi, (float)(x1 - hi), (float)R);
+            make_float4((float)x0, (float)hi, (float)(x1 - hi), Rf);
     }
 }
 
 void launch_kinematics(const double *c64, const FacetRec *fac, const double *vel64,
-                       const uint8_t *state, int64_t F, const RadarDev &rd, int n0, int nc,
-                       float4 *kin, cudaStream_t s)
+                       const int32_t *vis_idx, const int32_t *vis_cnt, int64_t F,
+                       const RadarDev &rd, int n0, int nc, float4 *kin, cudaStream_t s)
 {
-    const int T = 256;
-    dim3 grid((unsigned int)((F + T - 1) / T), (unsigned int)rd.A);
-    kin_kernel<<<grid, T, 0, s>>>(c64, fac, vel64, state, F, rd, n0, nc, kin);
+    const int T = 128;
+    dim3 grid((unsigned int)((F + T - 1) / T), (unsigned int)rd.A,
+              (unsigned int)((nc + kKinChirpsPerThread - 1) / kKinChirpsPerThread));
+    kin_kernel<<<grid, T, 0, s>>>(c64, fac, vel64, vis_idx, vis_cnt, F, rd, n0, nc, kin);
 }
 
 // -------------------------------------------------------------------------
@@ -115,43 +188,72 @@ struct MixConsts {
     float ant[kMaxAnt][3];
 };
 
-struct __align__(16) RecV {   // vertex form
-    float ph0[3];             // static phase per vertex, cycles in [-0.5, 0.5)
-    float lo[3];              // per-sample rate remainder per vertex, cycles/sample
-    float w[3];               // weight g w_v
-    float sre[3], sim[3];     // step phasor exp(j 2 pi (hi + lo_v))
-    float hi;                 // quantised rate, multiple of 2^-14
-    float p2;                 // cycles / sample^2
-    float pad;
-};
-struct __align__(16) RecS {   // series / edge form
-    int kind;                 // kRecSeries or kRecEdge
-    int flags;                // edge: bit i = sinc of edge i by its series
-    float ph0c, hi, loc, p2;  // centroid phase terms
-    float d[18];
+// One record per (facet, channel, chirp), 24 words in shared memory; the
+// layout depends on its form:
+//   vertex (V): [0..2] ph0_v  [3..5] lo_v  [6..8] w_v  [9..11] step re
+//               [12..14] step im  [15] hi  [16] p2
+//   factored (F): [0] ph0c [1] hi [2] loc [3] p2 [4..5] centroid step
+//               [6..8] psi_v  [9..11] a_v  [12..14] w_v  [15..17] w_v A_v
+//               [18..20] -w_v A_v^2 / 2  [21..23] w_v A_v^3 / 6
+//   series (S): [0] ph0c [1] hi [2] loc [3] p2 [4] po [5] pl [6..13] cr [14..20] ci
+//   edge (E):   [0] ph0c [1] hi [2] loc [3] p2 [4+4e] po [5+4e] pl [6+4e] G [7+4e] K
+//               [16] sinc-series flags (int bits)
+// Phases are in cycles.  ph0 / psi are reduced to [-0.5, 0.5]; hi is a
+// multiple of 2^-14 so that frac(hi m) is exact in FP32.
+struct __align__(16) RecM {
+    float f[24];
 };
 
+constexpr int kRecFact = 3;
+// factored form when max_v |2 pi a_v| (S - 1) stays below this many radians:
+// the vertex sum W then follows a cubic in the sample offset within a lane
+// to (0.06)^4 / 24 = 5.4e-7 of sum |w_v|
+constexpr float kFactMaxRot = 0.06f;
+
 constexpr int kMixWarps = 4;
+constexpr int kMixMinBlocks = 5;     // resident CTAs per SM the register budget targets
 
 __device__ __forceinline__ float red1(float x) { return x - rintf(x); }
 
 template <int S>
-__global__ void __launch_bounds__(kMixWarps * 32)
+__global__ void __launch_bounds__(kMixWarps * 32, kMixMinBlocks)
 synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
 {
-    __shared__ RecV sV[kMixWarps][32];
-    __shared__ RecS sS[kMixWarps][32];
+    __shared__ RecM sRec[kMixWarps][32];
+    // running sums and Kahan compensations: [warp][re, im, c_re, c_im][S][lane]
+    __shared__ float sAcc[kMixWarps][4][S][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t gw = (int64_t)blockIdx.x * kMixWarps + warp;
-    const int nc = A.nc;
-    const int64_t unit = gw / W;
-    const int seg = (int)(gw % W);
-    if (unit >= (int64_t)A.rd.O * nc) return;
-    const int o = (int)(unit / nc), nl = (int)(unit % nc);
-    const int n = A.n0 + nl;
-    const int P = A.rd.P, Q = A.rd.Q, AA = A.rd.A;
-    const int tx = o / Q, rx = o % Q;
+    const int O = A.rd.O, P = A.rd.P, Q = A.rd.Q, AA = A.rd.A;
+    const int TPI = A.tiles_per_item;
     const int64_t F = A.F;
+    const float fact_lim = kFactMaxRot / (6.283185307179586f * (float)(S > 1 ? S - 1 : 1));
+    const int total = A.item_off[O];
+    unsigned long long nV = 0, nSr = 0, nE = 0;
+
+    // persistent warps: each pulls (channel, chirp, sample segment, record
+    // chunk) items from a device counter until none remain
+    for (;;) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(A.item_counter, 1);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= total) break;
+    int clo = 0, chi = O - 1;                  // channel: last o with item_off[o] <= item
+    while (clo < chi) {
+        const int mid = (clo + chi + 1) >> 1;
+        if (A.item_off[mid] <= item) clo = mid;
+        else chi = mid - 1;
+    }
+    const int o = clo;
+    const int cnt = A.vis_cnt[o];
+    const int ipu = max(1, ((cnt + 31) / 32 + TPI - 1) / TPI);
+    const int local = item - A.item_off[o];
+    const int jchunk = local % ipu;
+    const int rowseg = local / ipu;
+    const int seg = rowseg % W, nl = rowseg / W;
+    const int rbeg = jchunk * TPI * 32;
+    const int rend = min(cnt, rbeg + TPI * 32);
+    const int n = A.n0 + nl;
+    const int tx = o / Q, rx = o % Q;
     const int m0 = (seg * 32 + lane) * S;
     const float fm0 = (float)m0;
     const float fm0sq = fm0 * fm0;
@@ -160,25 +262,26 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
     const float prx[3] = {K.ant[P + rx][0], K.ant[P + rx][1], K.ant[P + rx][2]};
     const float tn = (float)n * K.tc;
 
-    float kap[S];
+    float pr[S], pi[S];
 #pragma unroll
-    for (int j = 0; j < S; ++j) kap[j] = fmaf((float)(m0 + j), K.kap_step, 1.f);
-
-    float sr[S], si[S], cr_[S], ci_[S], pr[S], pi[S];
-#pragma unroll
-    for (int j = 0; j < S; ++j) sr[j] = si[j] = cr_[j] = ci_[j] = pr[j] = pi[j] = 0.f;
+    for (int j = 0; j < S; ++j) {
+        pr[j] = pi[j] = 0.f;
+        sAcc[warp][0][j][lane] = 0.f;
+        sAcc[warp][1][j][lane] = 0.f;
+        sAcc[warp][2][j][lane] = 0.f;
+        sAcc[warp][3][j][lane] = 0.f;
+    }
 
     const int32_t *list = A.vis_idx + (int64_t)o * F;
-    const int cnt = A.vis_cnt[o];
     const float4 *kin_t = A.kin + ((int64_t)nl * AA + tx) * F;
     const float4 *kin_r = A.kin + ((int64_t)nl * AA + P + rx) * F;
-    unsigned long long nV = 0, nSr = 0, nE = 0;
 
-    for (int base = 0; base < cnt; base += 32) {
+    for (int base = rbeg; base < rend; base += 32) {
         // ---------------- build one record per lane ----------------
-        const bool valid = base + lane < cnt;
+        const bool valid = base + lane < rend;
         int cls = -1;
         if (valid) {
+            float *R = sRec[warp][lane].f;
             const int k = list[base + lane];
             const FacetRec fr = A.fac[k];
             const float4 vv = reinterpret_cast<const float4 *>(A.vel32)[fr.inst];
@@ -201,7 +304,7 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
             const float o_k = 0.5f * (fr.n[0] * b[0] + fr.n[1] * b[1] + fr.n[2] * b[2]);
             const float g = fr.rho * o_k / (Rt * Rr);
             // in-plane part of b, formed once: u_v, |b_t|^2 and n x b_t all derive
-            // from it, so the forms below evaluate J exactly at one wave vector
+            // from it, so every form evaluates J exactly at one wave vector
             // (|b|^2 - (b.n)^2 would cancel catastrophically near specular)
             const float bn = fr.n[0] * b[0] + fr.n[1] * b[1] + fr.n[2] * b[2];
             const float bt[3] = {b[0] - bn * fr.n[0], b[1] - bn * fr.n[1], b[2] - bn * fr.n[2]};
@@ -229,16 +332,13 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
             const float A2 = 2.f * fr.area * g;
             if (K.kmax * (umax - umin) < (float)kSeriesKD) {
                 cls = kRecSeries;
-                RecS &R = sS[warp][lane];
-                R.kind = kRecSeries;
-                R.flags = 0;
-                R.ph0c = ph0c;
-                R.hi = hi;
-                R.loc = loc;
-                R.p2 = p2;
+                R[0] = ph0c;
+                R[1] = hi;
+                R[2] = loc;
+                R[3] = p2;
                 const float ub = (u[0] + u[1] + u[2]) * (1.f / 3.f);
-                R.d[0] = red1(-K.f0c * ub);
-                R.d[1] = -K.muc * ub;
+                R[4] = red1(-K.f0c * ub);
+                R[5] = -K.muc * ub;
                 const float y0 = K.k0 * (u[0] - ub), y1 = K.k0 * (u[1] - ub),
                             y2 = K.k0 * (u[2] - ub);
                 const float e2 = y0 * y1 + y0 * y2 + y1 * y2, e3 = y0 * y1 * y2;
@@ -251,19 +351,16 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
                 const float sc = A2 * K.k0 * K.k0;
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
-                    R.d[2 + i] = ((i & 1) ? -sc : sc) * h[2 * i] * (float)c_inv_fact[2 * i + 2];
+                    R[6 + i] = ((i & 1) ? -sc : sc) * h[2 * i] * (float)c_inv_fact[2 * i + 2];
 #pragma unroll
                 for (int i = 0; i < 7; ++i)
-                    R.d[10 + i] = ((i & 1) ? sc : -sc) * h[2 * i + 1] *
-                                  (float)c_inv_fact[2 * i + 3];
+                    R[14 + i] = ((i & 1) ? sc : -sc) * h[2 * i + 1] * (float)c_inv_fact[2 * i + 3];
             } else if (K.kmax * dmin < (float)kEdgeKd) {
                 cls = kRecEdge;
-                RecS &R = sS[warp][lane];
-                R.kind = kRecEdge;
-                R.ph0c = ph0c;
-                R.hi = hi;
-                R.loc = loc;
-                R.p2 = p2;
+                R[0] = ph0c;
+                R[1] = hi;
+                R[2] = loc;
+                R[3] = p2;
                 const float bt2 = bt[0] * bt[0] + bt[1] * bt[1] + bt[2] * bt[2];
                 const float nxb[3] = {fr.n[1] * bt[2] - fr.n[2] * bt[1],
                                       fr.n[2] * bt[0] - fr.n[0] * bt[2],
@@ -278,56 +375,78 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
                     const float beta = 0.5f * (u[i] + u[i1]);
                     const float gam = 0.5f * (u[i1] - u[i]);
                     const float ci = (e[0] * nxb[0] + e[1] * nxb[1] + e[2] * nxb[2]) / bt2;
-                    R.d[4 * i] = red1(-K.f0c * beta);
-                    R.d[4 * i + 1] = -K.muc * beta;
-                    R.d[4 * i + 2] = K.k0 * gam;
-                    R.d[4 * i + 3] = K.k0 * ci * g;
+                    R[4 + 4 * i] = red1(-K.f0c * beta);
+                    R[5 + 4 * i] = -K.muc * beta;
+                    R[6 + 4 * i] = K.k0 * gam;
+                    R[7 + 4 * i] = K.k0 * ci * g;
                     if (K.kmax * fabsf(gam) < (float)kSincSeries) flags |= 1 << i;
                 }
-                R.flags = flags;
-            } else {
-                cls = kRecVertex;
-                RecV &R = sV[warp][lane];
-                R.hi = hi;
-                R.p2 = p2;
-                R.pad = 0.f;
+                R[16] = __int_as_float(flags);
+            } else if (fmaxf(fabsf(umin), fabsf(umax)) * K.muc <= fact_lim) {
+                cls = kRecFact;
+                R[0] = ph0c;
+                R[1] = hi;
+                R[2] = loc;
+                R[3] = p2;
+                float s_, c_;
+                sincospif(2.f * red1(hi + loc), &s_, &c_);
+                R[4] = c_;
+                R[5] = s_;
 #pragma unroll
                 for (int v = 0; v < 3; ++v) {
                     const float ua = u[v], ub_ = u[(v + 1) % 3], uc = u[(v + 2) % 3];
-                    R.ph0[v] = red1(ph0c - K.f0c * ua);
+                    const float w = -A2 / ((ua - ub_) * (ua - uc));
+                    const float av = -K.muc * ua;
+                    const float Av = 6.283185307179586f * av;
+                    R[6 + v] = red1(-K.f0c * ua);
+                    R[9 + v] = av;
+                    R[12 + v] = w;
+                    R[15 + v] = w * Av;
+                    R[18 + v] = -0.5f * w * Av * Av;
+                    R[21 + v] = w * Av * Av * Av * (1.f / 6.f);
+                }
+            } else {
+                cls = kRecVertex;
+                R[15] = hi;
+                R[16] = p2;
+#pragma unroll
+                for (int v = 0; v < 3; ++v) {
+                    const float ua = u[v], ub_ = u[(v + 1) % 3], uc = u[(v + 2) % 3];
+                    R[v] = red1(ph0c - K.f0c * ua);
                     const float lo = loc - K.muc * ua;
-                    R.lo[v] = lo;
-                    R.w[v] = -A2 / ((ua - ub_) * (ua - uc));
-                    float s, c;
-                    sincospif(2.f * red1(hi + lo), &s, &c);
-                    R.sre[v] = c;
-                    R.sim[v] = s;
+                    R[3 + v] = lo;
+                    R[6 + v] = -A2 / ((ua - ub_) * (ua - uc));
+                    float s_, c_;
+                    sincospif(2.f * red1(hi + lo), &s_, &c_);
+                    R[9 + v] = c_;
+                    R[12 + v] = s_;
                 }
             }
         }
         __syncwarp();
         unsigned int mv = __ballot_sync(0xffffffffu, cls == kRecVertex);
+        unsigned int mf = __ballot_sync(0xffffffffu, cls == kRecFact);
         unsigned int ms = __ballot_sync(0xffffffffu, cls == kRecSeries || cls == kRecEdge);
         const unsigned int mser = __ballot_sync(0xffffffffu, cls == kRecSeries);
-        nV += __popc(mv);
+        nV += __popc(mv) + __popc(mf);
         nSr += __popc(mser);
         nE += __popc(ms & ~mser);
-        // ---------------- vertex records: recurrence ----------------
+        // ---------------- vertex records: one rotation per vertex ----------------
         while (mv) {
             const int i = __ffs(mv) - 1;
             mv &= mv - 1;
-            const RecV &R = sV[warp][i];
-            const float t1 = red1(R.hi * fm0);
-            const float q2 = R.p2 * fm0sq;
-            const float eps = R.p2 * eps_lane;
+            const float *R = sRec[warp][i].f;
+            const float t1 = red1(R[15] * fm0);
+            const float q2 = R[16] * fm0sq;
+            const float eps = R[16] * eps_lane;
 #pragma unroll
             for (int v = 0; v < 3; ++v) {
-                const float thv = red1(fmaf(R.lo[v], fm0, R.ph0[v] + t1) + q2);
+                const float thv = red1(fmaf(R[3 + v], fm0, R[v] + t1) + q2);
                 float zs, zc;
                 __sincosf(6.283185307179586f * thv, &zs, &zc);
-                const float stc = fmaf(-eps, R.sim[v], R.sre[v]);
-                const float sts = fmaf(eps, R.sre[v], R.sim[v]);
-                const float w = R.w[v];
+                const float stc = fmaf(-eps, R[12 + v], R[9 + v]);
+                const float sts = fmaf(eps, R[9 + v], R[12 + v]);
+                const float w = R[6 + v];
 #pragma unroll
                 for (int j = 0; j < S; ++j) {
                     pr[j] = fmaf(w, zc, pr[j]);
@@ -340,45 +459,96 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
                 }
             }
         }
+        // ---------------- factored records: centroid rotation x quadratic W ----------------
+        while (mf) {
+            const int i = __ffs(mf) - 1;
+            mf &= mf - 1;
+            const float *R = sRec[warp][i].f;
+            const float thc = red1(fmaf(R[2], fm0, R[0] + red1(R[1] * fm0)) + R[3] * fm0sq);
+            float cs, cc;
+            __sincosf(6.283185307179586f * thc, &cs, &cc);
+            const float eps = R[3] * eps_lane;
+            const float stc = fmaf(-eps, R[5], R[4]);
+            const float sts = fmaf(eps, R[4], R[5]);
+            // W(s) = sum_v w_v exp(j 2 pi (psi_v + a_v (m0 + s))) as a cubic in s
+            float w0r = 0.f, w0i = 0.f, w1r = 0.f, w1i = 0.f, w2r = 0.f, w2i = 0.f;
+            float w3r = 0.f, w3i = 0.f;
+#pragma unroll
+            for (int v = 0; v < 3; ++v) {
+                const float ps = red1(fmaf(R[9 + v], fm0, R[6 + v]));
+                float zs, zc;
+                __sincosf(6.283185307179586f * ps, &zs, &zc);
+                w0r = fmaf(R[12 + v], zc, w0r);          // w z
+                w0i = fmaf(R[12 + v], zs, w0i);
+                w1r = fmaf(-R[15 + v], zs, w1r);         // w A j z
+                w1i = fmaf(R[15 + v], zc, w1i);
+                w2r = fmaf(R[18 + v], zc, w2r);          // -w A^2/2 z
+                w2i = fmaf(R[18 + v], zs, w2i);
+                w3r = fmaf(R[21 + v], zs, w3r);          // -j w A^3/6 z
+                w3i = fmaf(-R[21 + v], zc, w3i);
+            }
+            // forward differences of the cubic
+            float d1r = w1r + w2r + w3r, d1i = w1i + w2i + w3i;
+            float d2r = fmaf(6.f, w3r, 2.f * w2r), d2i = fmaf(6.f, w3i, 2.f * w2i);
+            const float d3r = 6.f * w3r, d3i = 6.f * w3i;
+#pragma unroll
+            for (int j = 0; j < S; ++j) {
+                pr[j] = fmaf(cc, w0r, fmaf(-cs, w0i, pr[j]));
+                pi[j] = fmaf(cc, w0i, fmaf(cs, w0r, pi[j]));
+                if (j + 1 < S) {
+                    const float nc_ = fmaf(cc, stc, -cs * sts);
+                    cs = fmaf(cc, sts, cs * stc);
+                    cc = nc_;
+                    w0r += d1r;
+                    w0i += d1i;
+                    d1r += d2r;
+                    d1i += d2i;
+                    d2r += d3r;
+                    d2i += d3i;
+                }
+            }
+        }
         // ---------------- series / edge records: per sample ----------------
         while (ms) {
             const int i = __ffs(ms) - 1;
             ms &= ms - 1;
-            const RecS &R = sS[warp][i];
+            const float *R = sRec[warp][i].f;
+            const bool series = (mser >> i) & 1u;
 #pragma unroll
             for (int j = 0; j < S; ++j) {
                 const float fm = (float)(m0 + j);
-                const float thc = fmaf(R.p2, fm * fm, fmaf(R.loc, fm, R.ph0c + red1(R.hi * fm)));
-                const float kp = kap[j];
-                if (R.kind == kRecSeries) {
-                    const float th = red1(thc + fmaf(R.d[1], fm, R.d[0]));
+                const float thc = fmaf(R[3], fm * fm, fmaf(R[2], fm, R[0] + red1(R[1] * fm)));
+                const float kp = fmaf(fm, K.kap_step, 1.f);
+                if (series) {
+                    const float th = red1(thc + fmaf(R[5], fm, R[4]));
                     float zs, zc;
                     __sincosf(6.283185307179586f * th, &zs, &zc);
                     const float k2 = kp * kp;
-                    float a = R.d[9], bb = R.d[16];
+                    float a = R[13], bb = R[20];
 #pragma unroll
-                    for (int q = 6; q >= 0; --q) a = fmaf(a, k2, R.d[2 + q]);
+                    for (int q = 6; q >= 0; --q) a = fmaf(a, k2, R[6 + q]);
 #pragma unroll
-                    for (int q = 5; q >= 0; --q) bb = fmaf(bb, k2, R.d[10 + q]);
+                    for (int q = 5; q >= 0; --q) bb = fmaf(bb, k2, R[14 + q]);
                     const float re = a * k2, im = bb * k2 * kp;
                     pr[j] += zc * re - zs * im;
                     pi[j] += zc * im + zs * re;
                 } else {
+                    const int flags = __float_as_int(R[16]);
 #pragma unroll
                     for (int e = 0; e < 3; ++e) {
-                        const float th = red1(thc + fmaf(R.d[4 * e + 1], fm, R.d[4 * e]));
+                        const float th = red1(thc + fmaf(R[5 + 4 * e], fm, R[4 + 4 * e]));
                         float zs, zc;
                         __sincosf(6.283185307179586f * th, &zs, &zc);
-                        const float x = kp * R.d[4 * e + 2];
+                        const float x = kp * R[6 + 4 * e];
                         float sn;
-                        if (R.flags & (1 << e)) {
+                        if (flags & (1 << e)) {
                             const float x2 = x * x;
                             sn = fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, 1.f / 362880.f, -1.f / 5040.f),
                                                         1.f / 120.f), -1.f / 6.f), 1.f);
                         } else {
                             sn = sinf(x) / x;   // accurate sinf: |x| may reach ~1e3
                         }
-                        const float coef = kp * R.d[4 * e + 3] * sn;
+                        const float coef = kp * R[7 + 4 * e] * sn;
                         pr[j] = fmaf(-coef, zs, pr[j]);
                         pi[j] = fmaf(coef, zc, pi[j]);
                     }
@@ -388,34 +558,78 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
         // ---------------- Kahan-compensated tile accumulation ----------------
 #pragma unroll
         for (int j = 0; j < S; ++j) {
-            float y = pr[j] - cr_[j];
-            float t = sr[j] + y;
-            cr_[j] = (t - sr[j]) - y;
-            sr[j] = t;
-            y = pi[j] - ci_[j];
-            t = si[j] + y;
-            ci_[j] = (t - si[j]) - y;
-            si[j] = t;
+            float sr = sAcc[warp][0][j][lane], si = sAcc[warp][1][j][lane];
+            float cr = sAcc[warp][2][j][lane], ci = sAcc[warp][3][j][lane];
+            float y = pr[j] - cr;
+            float t = sr + y;
+            cr = (t - sr) - y;
+            sr = t;
+            y = pi[j] - ci;
+            t = si + y;
+            ci = (t - si) - y;
+            si = t;
+            sAcc[warp][0][j][lane] = sr;
+            sAcc[warp][1][j][lane] = si;
+            sAcc[warp][2][j][lane] = cr;
+            sAcc[warp][3][j][lane] = ci;
             pr[j] = pi[j] = 0.f;
         }
         __syncwarp();
     }
-    if (lane == 0 && seg == 0 && A.counters) {
+    // unscaled partial sums of this item
+    float2 *dst = A.partial + (int64_t)item * (32 * S) + lane * S;
+#pragma unroll
+    for (int j = 0; j < S; ++j) dst[j] = make_float2(sAcc[warp][0][j][lane], sAcc[warp][1][j][lane]);
+    __syncwarp();
+    }   // item loop
+    if (lane == 0 && A.counters) {
         atomicAdd(A.counters + 0, nV);
         atomicAdd(A.counters + 1, nSr);
         atomicAdd(A.counters + 2, nE);
     }
-    const int64_t row = ((int64_t)o * A.rd.N + n) * A.rd.M + m0;
-#pragma unroll
-    for (int j = 0; j < S; ++j) {
-        const float sc = K.out_scale / (kap[j] * kap[j]);
-        if (A.out_c64) {
-            reinterpret_cast<float2 *>(A.out)[row + j] = make_float2(sr[j] * sc, si[j] * sc);
-        } else {
-            reinterpret_cast<double2 *>(A.out)[row + j] =
-                make_double2((double)sr[j] * sc, (double)si[j] * sc);
-        }
+}
+
+// item table: channel o owns ipu_o = ceil(ceil(cnt_o / 32) / TPI) record
+// chunks (at least one) per (chirp, sample segment); item_off is their prefix
+__global__ void synth_items_kernel(const int32_t *__restrict__ vis_cnt, int O, int TPI, int nc,
+                                   int W, int32_t *__restrict__ item_off, int *counter)
+{
+    if (threadIdx.x != 0) return;
+    int run = 0;
+    for (int o = 0; o < O; ++o) {
+        item_off[o] = run;
+        const int ipu = max(1, ((vis_cnt[o] + 31) / 32 + TPI - 1) / TPI);
+        run += ipu * nc * W;
     }
+    item_off[O] = run;
+    *counter = 0;
+}
+
+// sums the item partials of each (channel, chirp, sample) in FP64, in item
+// order, and applies C / k_m^2
+__global__ void synth_reduce_kernel(const float2 *__restrict__ partial,
+                                    const int32_t *__restrict__ item_off,
+                                    const int32_t *__restrict__ vis_cnt, int TPI, int W, int S,
+                                    RadarDev rd, int n0, void *out, int out_c64)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nl = blockIdx.y, o = blockIdx.z;
+    if (m >= rd.M) return;
+    const int seg = m / (32 * S), ml = m % (32 * S);
+    const int ipu = max(1, ((vis_cnt[o] + 31) / 32 + TPI - 1) / TPI);
+    const int64_t it0 = (int64_t)item_off[o] + (int64_t)(nl * W + seg) * ipu;
+    double sr = 0.0, si = 0.0;
+    for (int j = 0; j < ipu; ++j) {
+        const float2 p = partial[(it0 + j) * (32 * S) + ml];
+        sr += (double)p.x;
+        si += (double)p.y;
+    }
+    const double fm = rd.f0 + rd.slope * (double)m / rd.fs;
+    const double km = 2.0 * kPi * fm / kC0;
+    const double sc = 2.0 * sqrt(kPi) / pow(4.0 * kPi, 1.5) / (km * km);
+    const int64_t idx = ((int64_t)o * rd.N + n0 + nl) * rd.M + m;
+    if (out_c64) reinterpret_cast<float2 *>(out)[idx] = make_float2((float)(sr * sc), (float)(si * sc));
+    else reinterpret_cast<double2 *>(out)[idx] = make_double2(sr * sc, si * sc);
 }
 
 // consecutive samples per lane: the largest S in {8, 4, 2, 1} with 32 S | M;
@@ -451,20 +665,58 @@ static MixConsts mix_consts(const RadarDev &rd)
     return K;
 }
 
-void launch_synth_mixed(const SynthArgs &a, cudaStream_t s)
+// 32-record tiles per work item: at least 16 (512 records), more for large
+// scenes so that a channel row splits into at most 64 items; the partial
+// sums cost one 8-byte store and load per sample and item
+int synth_tiles_per_item(int64_t F) { return (int)std::max<int64_t>(16, ((F + 31) / 32 + 63) / 64); }
+
+int64_t synth_max_items(int64_t F, const RadarDev &rd, int nc)
 {
+    const int S = samples_per_lane(rd.M), W = rd.M / (32 * S);
+    const int64_t tiles = (F + 31) / 32, TPI = synth_tiles_per_item(F);
+    return (int64_t)rd.O * std::max<int64_t>(1, (tiles + TPI - 1) / TPI) * nc * W;
+}
+
+int64_t synth_partial_words(int64_t F, const RadarDev &rd, int nc)
+{
+    return synth_max_items(F, rd, nc) * 32 * samples_per_lane(rd.M);
+}
+
+template <int S> static int mixed_grid(int64_t items)
+{
+    static int blocks_per_sm = -1, sms = 0;
+    if (blocks_per_sm < 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, synth_mixed_kernel<S>,
+                                                      kMixWarps * 32, 0);
+        if (blocks_per_sm < 1) blocks_per_sm = 1;
+    }
+    const int64_t need = (items + kMixWarps - 1) / kMixWarps;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)blocks_per_sm * sms));
+}
+
+void launch_synth_mixed(const SynthArgs &a0, cudaStream_t s)
+{
+    SynthArgs a = a0;
     const MixConsts K = mix_consts(a.rd);
     const int M = a.rd.M;
     const int S = samples_per_lane(M);
     const int W = M / (32 * S);
-    const int64_t warps = (int64_t)a.rd.O * a.nc * W;
-    const unsigned int grid = (unsigned int)((warps + kMixWarps - 1) / kMixWarps);
+    a.tiles_per_item = synth_tiles_per_item(a.F);
+    synth_items_kernel<<<1, 32, 0, s>>>(a.vis_cnt, a.rd.O, a.tiles_per_item, a.nc, W,
+                                        a.item_off, a.item_counter);
+    const int64_t items = synth_max_items(a.F, a.rd, a.nc);
     switch (S) {
-    case 8: synth_mixed_kernel<8><<<grid, kMixWarps * 32, 0, s>>>(a, K, W); break;
-    case 4: synth_mixed_kernel<4><<<grid, kMixWarps * 32, 0, s>>>(a, K, W); break;
-    case 2: synth_mixed_kernel<2><<<grid, kMixWarps * 32, 0, s>>>(a, K, W); break;
-    default: synth_mixed_kernel<1><<<grid, kMixWarps * 32, 0, s>>>(a, K, W); break;
+    case 8: synth_mixed_kernel<8><<<mixed_grid<8>(items), kMixWarps * 32, 0, s>>>(a, K, W); break;
+    case 4: synth_mixed_kernel<4><<<mixed_grid<4>(items), kMixWarps * 32, 0, s>>>(a, K, W); break;
+    case 2: synth_mixed_kernel<2><<<mixed_grid<2>(items), kMixWarps * 32, 0, s>>>(a, K, W); break;
+    default: synth_mixed_kernel<1><<<mixed_grid<1>(items), kMixWarps * 32, 0, s>>>(a, K, W); break;
     }
+    dim3 rg((unsigned int)((M + 255) / 256), (unsigned int)a.nc, (unsigned int)a.rd.O);
+    synth_reduce_kernel<<<rg, 256, 0, s>>>(a.partial, a.item_off, a.vis_cnt, a.tiles_per_item, W,
+                                           S, a.rd, a.n0, a.out, a.out_c64);
 }
 
 // -------------------------------------------------------------------------

@@ -79,14 +79,17 @@ constexpr int kStack = 64;
 
 __global__ void __launch_bounds__(128)
 visibility_kernel(const double *__restrict__ tri64, const double *__restrict__ c64,
-                  const BvhNode *__restrict__ nodes, int64_t F, RadarDev rd,
-                  uint8_t *__restrict__ state, unsigned long long *n_graze, int *status)
+                  const BvhNode *__restrict__ nodes, const int32_t *__restrict__ order,
+                  int64_t F, RadarDev rd, uint8_t *__restrict__ state,
+                  unsigned long long *n_graze, int *status)
 {
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int a = blockIdx.y;
     bool graze_flag = false;
     if (gid < F) {
-        const int64_t k = gid;
+        // threads walk the facets in Morton order so that a warp's segments
+        // start close together and traverse similar BVH paths
+        const int64_t k = order ? (int64_t)order[gid] : gid;
         const double *tk = tri64 + 9 * k;
         double tri[9];
         for (int i = 0; i < 9; ++i) tri[i] = tk[i];
@@ -151,35 +154,39 @@ visibility_kernel(const double *__restrict__ tri64, const double *__restrict__ c
     if ((threadIdx.x & 31) == 0 && b) atomicAdd(n_graze, (unsigned long long)__popc(b));
 }
 
-void launch_visibility(const double *tri64, const double *c64, const BvhNode *nodes, int64_t F,
-                       const RadarDev &rd, uint8_t *state, unsigned long long *n_graze,
-                       int *status, cudaStream_t s)
+void launch_visibility(const double *tri64, const double *c64, const BvhNode *nodes,
+                       const int32_t *order, int64_t F, const RadarDev &rd, uint8_t *state,
+                       unsigned long long *n_graze, int *status, cudaStream_t s)
 {
     const int T = 128;
     dim3 grid((unsigned int)((F + T - 1) / T), (unsigned int)rd.A);
-    visibility_kernel<<<grid, T, 0, s>>>(tri64, c64, nodes, F, rd, state, n_graze, status);
+    visibility_kernel<<<grid, T, 0, s>>>(tri64, c64, nodes, order, F, rd, state, n_graze, status);
 }
 
 // -------------------------------------------------------------------------
-// per-channel compaction of the facets lit from TX p AND RX q (ascending)
+// compaction into ascending facet lists: list l < O holds the facets lit
+// from TX p AND RX q of channel l = p Q + q; list O + a holds the facets lit
+// from antenna a (used by the kinematics)
 // -------------------------------------------------------------------------
 constexpr int kCompactBlk = 1024;
 
-int64_t compact_blk_words(int64_t F, int O) { return (int64_t)O * ((F + kCompactBlk - 1) / kCompactBlk); }
+int64_t compact_blk_words(int64_t F, int L) { return (int64_t)L * ((F + kCompactBlk - 1) / kCompactBlk); }
 
-__device__ __forceinline__ bool lit_pair(const uint8_t *state, int64_t F, int p, int q, int P,
-                                         int64_t k)
+__device__ __forceinline__ bool in_list(const uint8_t *state, int64_t F, int l, int O, int P,
+                                        int Q, int64_t k)
 {
+    if (l >= O) return state[(int64_t)(l - O) * F + k] == BART_VIS_LIT;
+    const int p = l / Q, q = l % Q;
     return state[(int64_t)p * F + k] == BART_VIS_LIT &&
            state[(int64_t)(P + q) * F + k] == BART_VIS_LIT;
 }
 
-__global__ void compact_count_kernel(const uint8_t *__restrict__ state, int64_t F, int P, int Q,
-                                     int32_t *__restrict__ blk_cnt, int64_t nblk)
+__global__ void compact_count_kernel(const uint8_t *__restrict__ state, int64_t F, int O, int P,
+                                     int Q, int32_t *__restrict__ blk_cnt, int64_t nblk)
 {
-    const int o = blockIdx.y, p = o / Q, q = o % Q;
+    const int o = blockIdx.y;
     const int64_t k = (int64_t)blockIdx.x * kCompactBlk + threadIdx.x;
-    const bool lit = k < F && lit_pair(state, F, p, q, P, k);
+    const bool lit = k < F && in_list(state, F, o, O, P, Q, k);
     const int c = __syncthreads_count(lit);
     if (threadIdx.x == 0) blk_cnt[(int64_t)o * nblk + blockIdx.x] = c;
 }
@@ -205,15 +212,15 @@ __global__ void compact_scan_kernel(int32_t *__restrict__ blk_cnt, int64_t nblk,
     if (lane == 0) vis_cnt[o] = run;
 }
 
-__global__ void compact_write_kernel(const uint8_t *__restrict__ state, int64_t F, int P, int Q,
-                                     const int32_t *__restrict__ blk_cnt, int64_t nblk,
+__global__ void compact_write_kernel(const uint8_t *__restrict__ state, int64_t F, int O, int P,
+                                     int Q, const int32_t *__restrict__ blk_cnt, int64_t nblk,
                                      int32_t *__restrict__ vis_idx)
 {
     __shared__ int32_t s_w[kCompactBlk / 32];
-    const int o = blockIdx.y, p = o / Q, q = o % Q;
+    const int o = blockIdx.y;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int64_t k = (int64_t)blockIdx.x * kCompactBlk + t;
-    const bool lit = k < F && lit_pair(state, F, p, q, P, k);
+    const bool lit = k < F && in_list(state, F, o, O, P, Q, k);
     const unsigned int b = __ballot_sync(0xffffffffu, lit);
     if (lane == 0) s_w[warp] = __popc(b);
     __syncthreads();
@@ -238,10 +245,11 @@ void launch_compact(const uint8_t *state, int64_t F, const RadarDev &rd, int32_t
                     int32_t *vis_idx, int32_t *vis_cnt, cudaStream_t s)
 {
     const int64_t nblk = (F + kCompactBlk - 1) / kCompactBlk;
-    dim3 grid((unsigned int)nblk, (unsigned int)rd.O);
-    compact_count_kernel<<<grid, kCompactBlk, 0, s>>>(state, F, rd.P, rd.Q, blk_cnt, nblk);
-    compact_scan_kernel<<<rd.O, 32, 0, s>>>(blk_cnt, nblk, vis_cnt);
-    compact_write_kernel<<<grid, kCompactBlk, 0, s>>>(state, F, rd.P, rd.Q, blk_cnt, nblk,
+    const int L = rd.O + rd.A;
+    dim3 grid((unsigned int)nblk, (unsigned int)L);
+    compact_count_kernel<<<grid, kCompactBlk, 0, s>>>(state, F, rd.O, rd.P, rd.Q, blk_cnt, nblk);
+    compact_scan_kernel<<<L, 32, 0, s>>>(blk_cnt, nblk, vis_cnt);
+    compact_write_kernel<<<grid, kCompactBlk, 0, s>>>(state, F, rd.O, rd.P, rd.Q, blk_cnt, nblk,
                                                       vis_idx);
 }
 
