@@ -201,9 +201,10 @@ int bart_form_rdm(bart_ctx *ctx, const void *adc, int32_t dtype, float *rdm);
  * pointer, O*N*M complex samples of `dtype`, [O][N][M]; rdm: device pointer,
  * M x N float32; window: BART_WINDOW_*; stream: a cudaStream_t (0 = legacy
  * default stream) on the current device.  The range-FFT intermediate lives
- * in a fixed 16 MiB array compiled into the library, which every GPU that
- * loads the library holds until the process exits; cubes needing more
- * (O*N*M > 2^21 complex64 or 2^20 complex128 samples) are rejected with
+ * and the per-channel Doppler power live in a fixed 16 MiB array compiled
+ * into the library, which every GPU that loads the library holds until the
+ * process exits; cubes needing more (O*N*M > 1398101 complex64 or 699050
+ * complex128 samples: 12 bytes, resp. 24, per sample) are rejected with
  * BART_EINVAL.  M and N must be powers of two (M in [32, 1024], N in
  * [2, 1024]).  The first call on a device looks the array's address up
  * (cudaGetSymbolAddress) with that device current; make that first call

@@ -84,8 +84,10 @@ struct InstDev {
 constexpr int kStatusStackOverflow = 1;
 
 // ---- scene + BVH (scene_bvh.cu) ----
+// tri32: per facet 12 floats -- the world vertices rounded to FP32 and the
+// largest |coordinate| among them (for the visibility FP32 pre-test)
 void launch_build_facets(const MeshDesc *meshes, const InstDev *insts, int n_inst,
-                         int64_t F, double t0, double *tri64, double *c64,
+                         int64_t F, double t0, double *tri64, float *tri32, double *c64,
                          FacetRec *fac, float *aabb, float *vel32, unsigned int *bounds,
                          cudaStream_t s);
 void launch_morton(const FacetRec *fac, int64_t F, const unsigned int *bounds,
@@ -104,9 +106,9 @@ void launch_lbvh_refit(const int32_t *vals, const float *aabb, int64_t n, BvhNod
 
 // ---- visibility (visibility.cu) ----
 // order: facet ids in the sequence the ray threads take them (Morton order), or NULL
-void launch_visibility(const double *tri64, const double *c64, const BvhNode *nodes,
-                       const int32_t *order, int64_t F, const RadarDev &rd, uint8_t *state,
-                       unsigned long long *n_graze, int *status, cudaStream_t s);
+void launch_visibility(const double *tri64, const float *tri32, const double *c64,
+                       const BvhNode *nodes, const int32_t *order, int64_t F, const RadarDev &rd,
+                       uint8_t *state, unsigned long long *n_graze, int *status, cudaStream_t s);
 // lists 0..O-1: facets lit from both antennas of each channel; O..O+A-1: facets
 // lit from each antenna.  vis_idx is [O+A][F], vis_cnt [O+A].
 void launch_compact(const uint8_t *state, int64_t F, const RadarDev &rd,

@@ -93,6 +93,7 @@ struct bart_ctx {
     DevBuf<MeshDesc> d_meshes;
     DevBuf<InstDev> d_insts;
     DevBuf<double> tri64, c64, vel64;
+    DevBuf<float> tri32;
     DevBuf<float> vel32, aabb;
     DevBuf<FacetRec> fac;
     DevBuf<unsigned int> bounds;
@@ -138,7 +139,7 @@ struct bart_ctx {
             m->rho.release();
             delete m;
         }
-        d_meshes.release(); d_insts.release(); tri64.release(); c64.release();
+        d_meshes.release(); d_insts.release(); tri64.release(); tri32.release(); c64.release();
         vel64.release(); vel32.release(); aabb.release(); fac.release(); bounds.release();
         keys.release(); keys_tmp.release(); sort_temp.release(); vals.release();
         vals_tmp.release(); nodes.release(); parent.release(); leaf_parent.release();
@@ -399,6 +400,7 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
     BART_TRY(ctx->d_meshes.ensure(md.size(), "mesh table"));
     BART_TRY(ctx->d_insts.ensure(I, "instance table"));
     BART_TRY(ctx->tri64.ensure(9 * F, "facet vertices"));
+    BART_TRY(ctx->tri32.ensure(12 * F, "facet vertices (f32)"));
     BART_TRY(ctx->c64.ensure(3 * F, "facet centroids"));
     BART_TRY(ctx->vel64.ensure(3 * I, "instance velocities"));
     BART_TRY(ctx->vel32.ensure(4 * I, "instance velocities (f32)"));
@@ -440,8 +442,8 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
     int launches = 0;
 
     // 1. world facets at t0
-    launch_build_facets(ctx->d_meshes.p, ctx->d_insts.p, I, F, t0, ctx->tri64.p, ctx->c64.p,
-                        ctx->fac.p, ctx->aabb.p, ctx->vel32.p, ctx->bounds.p, s);
+    launch_build_facets(ctx->d_meshes.p, ctx->d_insts.p, I, F, t0, ctx->tri64.p, ctx->tri32.p,
+                        ctx->c64.p, ctx->fac.p, ctx->aabb.p, ctx->vel32.p, ctx->bounds.p, s);
     launches += 1;
     if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[1], s), "cudaEventRecord");
     // 2. LBVH
@@ -455,8 +457,9 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
     launches += 1 + 3 * 4 + (F >= 2 ? 2 : 0);
     if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[2], s), "cudaEventRecord");
     // 3. visibility + per-channel lit lists
-    launch_visibility(ctx->tri64.p, ctx->c64.p, ctx->nodes.p, F >= 2 ? ctx->vals.p : nullptr, F,
-                      rd, ctx->state.p, ctx->counters.p + 3, ctx->status.p, s);
+    launch_visibility(ctx->tri64.p, ctx->tri32.p, ctx->c64.p, ctx->nodes.p,
+                      F >= 2 ? ctx->vals.p : nullptr, F, rd, ctx->state.p, ctx->counters.p + 3,
+                      ctx->status.p, s);
     launch_compact(ctx->state.p, F, rd, ctx->blk_cnt.p, ctx->vis_idx.p, ctx->vis_cnt.p, s);
     launches += 1 + 3;
     if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[3], s), "cudaEventRecord");
@@ -603,7 +606,7 @@ static int run_rdm(bart_ctx *ctx, const void *adc, int32_t dtype, float *rdm)
         CUDA_TRY(cudaEventRecord(ctx->ev[6], ctx->stream), "cudaEventRecord");
         ctx->have_rdm_timing = true;
     }
-    ctx->rdm_launches = 2;
+    ctx->rdm_launches = 3;
     return BART_OK;
 }
 
@@ -639,7 +642,7 @@ int bart_form_rdm_static(const void *adc, int32_t dtype, int32_t O, int32_t N, i
         return fail(BART_EINVAL, "bart_form_rdm_static: the cube needs %lld bytes of workspace, "
                     "more than the fixed %lld (O*N*M <= %lld complex%s samples)",
                     (long long)need, (long long)kRdmStaticWorkspaceBytes,
-                    (long long)(kRdmStaticWorkspaceBytes / (dtype == BART_C64 ? 8 : 16)),
+                    (long long)(kRdmStaticWorkspaceBytes / (dtype == BART_C64 ? 12 : 24)),
                     dtype == BART_C64 ? "64" : "128");
     void *ws = nullptr;
     const char *err = nullptr;

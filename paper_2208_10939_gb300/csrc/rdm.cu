@@ -105,51 +105,58 @@ __global__ void range_fft_kernel(const typename Cplx<T>::type *__restrict__ adc,
     for (int i = threadIdx.x; i < M; i += blockDim.x) out[i] = res[i];
 }
 
-// one block per RB consecutive range bins, looping over channels
+// one block per (RB consecutive range bins, channel): Doppler FFT of the
+// channel's RB columns, |Y|^2 written per channel (summed by rdm_sum_kernel)
 template <typename T>
-__global__ void doppler_rdm_kernel(const typename Cplx<T>::type *__restrict__ X, int O, int N,
-                                   int M, int RB, int window, float *__restrict__ rdm)
+__global__ void doppler_power_kernel(const typename Cplx<T>::type *__restrict__ X, int N, int M,
+                                     int RB, int window, T *__restrict__ pw_out)
 {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *buf0 = reinterpret_cast<C *>(smem_raw);
     C *buf1 = buf0 + RB * N;
     C *tw = buf1 + RB * N;
-    T *pw = reinterpret_cast<T *>(tw + (N >> 1));     // RB * N accumulated power
     fill_twiddles<T>(tw, N);
     const int r0 = blockIdx.x * RB;
-    for (int i = threadIdx.x; i < RB * N; i += blockDim.x) pw[i] = (T)0;
-    for (int o = 0; o < O; ++o) {
-        __syncthreads();
-        // load X[o][n][r0 + c] into column-major buf0[c * N + n]
-        for (int i = threadIdx.x; i < RB * N; i += blockDim.x) {
-            const int n = i / RB, c = i % RB;
-            const T w = window_val<T>(n, N, window);
-            C v = X[((int64_t)o * N + n) * M + r0 + c];
-            v.x *= w;
-            v.y *= w;
-            buf0[c * N + n] = v;
-        }
-        __syncthreads();
-        const C *res = stockham<C>(buf0, buf1, tw, N, RB);
-        for (int i = threadIdx.x; i < RB * N; i += blockDim.x) {
-            const C v = res[i];
-            pw[i] += v.x * v.x + v.y * v.y;
-        }
+    const int o = blockIdx.y;
+    // load X[o][n][r0 + c] into column-major buf0[c * N + n]
+    for (int i = threadIdx.x; i < RB * N; i += blockDim.x) {
+        const int n = i / RB, c = i % RB;
+        const T w = window_val<T>(n, N, window);
+        C v = X[((int64_t)o * N + n) * M + r0 + c];
+        v.x *= w;
+        v.y *= w;
+        buf0[c * N + n] = v;
     }
     __syncthreads();
+    const C *res = stockham<C>(buf0, buf1, tw, N, RB);
     for (int i = threadIdx.x; i < RB * N; i += blockDim.x) {
         const int c = i / N, d = i % N;
-        rdm[(int64_t)(r0 + c) * N + ((d + (N >> 1)) & (N - 1))] = (float)pw[i];
+        const C v = res[i];
+        // [o][r][d'] with the Doppler shift applied
+        pw_out[((int64_t)o * M + r0 + c) * N + ((d + (N >> 1)) & (N - 1))] = v.x * v.x + v.y * v.y;
     }
 }
 
-static int rdm_rb(int N) { return N >= 2048 ? 1 : (2048 / N > 16 ? 16 : 2048 / N); }
+// RDM[r][d] = sum over channels, in channel order
+template <typename T>
+__global__ void rdm_sum_kernel(const T *__restrict__ pw, int O, int64_t MN, float *__restrict__ rdm)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= MN) return;
+    T acc = (T)0;
+    for (int o = 0; o < O; ++o) acc += pw[(int64_t)o * MN + i];
+    rdm[i] = (float)acc;
+}
 
+static int rdm_rb(int N) { return N >= 512 ? 1 : 512 / N; }
+
+// workspace: the range-FFT output (O N M complex) followed by the
+// per-channel Doppler power (O M N reals of the same precision)
 int64_t rdm_workspace_bytes(const RadarDev &rd, int dtype)
 {
     const int64_t e = dtype == BART_C64 ? 8 : 16;
-    return (int64_t)rd.O * rd.N * rd.M * e;
+    return (int64_t)rd.O * rd.N * rd.M * (e + e / 2);
 }
 
 template <typename T>
@@ -165,11 +172,14 @@ static void run_rdm(const void *adc, const RadarDev &rd, void *ws, float *rdm, c
         reinterpret_cast<const C *>(adc), reinterpret_cast<C *>(ws), M, rd.window);
     int RB = rdm_rb(N);
     if (RB > M) RB = M;
-    const size_t sm2 = (size_t)(2 * RB * N + N / 2) * sizeof(C) + (size_t)RB * N * sizeof(T);
-    cudaFuncSetAttribute(doppler_rdm_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    T *pw = reinterpret_cast<T *>(reinterpret_cast<C *>(ws) + (int64_t)rd.O * N * M);
+    const size_t sm2 = (size_t)(2 * RB * N + N / 2) * sizeof(C);
+    cudaFuncSetAttribute(doppler_power_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sm2);
-    doppler_rdm_kernel<T><<<(unsigned int)(M / RB), 256, sm2, s>>>(
-        reinterpret_cast<const C *>(ws), rd.O, N, M, RB, rd.window, rdm);
+    doppler_power_kernel<T><<<dim3((unsigned int)(M / RB), (unsigned int)rd.O), 256, sm2, s>>>(
+        reinterpret_cast<const C *>(ws), N, M, RB, rd.window, pw);
+    const int64_t MN = (int64_t)M * N;
+    rdm_sum_kernel<T><<<(unsigned int)((MN + 255) / 256), 256, 0, s>>>(pw, rd.O, MN, rdm);
 }
 
 void launch_rdm(const void *adc, int dtype, const RadarDev &rd, void *ws, float *rdm,

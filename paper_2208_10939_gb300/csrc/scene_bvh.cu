@@ -40,6 +40,7 @@ __device__ __forceinline__ double world_coord(const double *r, double x, double 
 __global__ void build_facets_kernel(const MeshDesc *__restrict__ meshes,
                                     const InstDev *__restrict__ insts, int n_inst, int64_t F,
                                     double t0, double *__restrict__ tri64,
+                                    float *__restrict__ tri32,
                                     double *__restrict__ c64, FacetRec *__restrict__ fac,
                                     float *__restrict__ aabb, float *__restrict__ vel32,
                                     unsigned int *__restrict__ bounds)
@@ -64,7 +65,16 @@ __global__ void build_facets_kernel(const MeshDesc *__restrict__ meshes,
             for (int r = 0; r < 3; ++r)
                 v[3 * k + r] = world_coord(in.rot + 3 * r, x, y, z, in.pos[r], in.vel[r], t0);
         }
-        for (int i = 0; i < 9; ++i) tri64[9 * f + i] = v[i];
+        float vmax = 0.f;
+        for (int i = 0; i < 9; ++i) {
+            tri64[9 * f + i] = v[i];
+            const float vf = (float)v[i];
+            tri32[12 * f + i] = vf;
+            vmax = fmaxf(vmax, fabsf(vf));
+        }
+        tri32[12 * f + 9] = vmax;
+        tri32[12 * f + 10] = 0.f;
+        tri32[12 * f + 11] = 0.f;
         double c[3];
         for (int r = 0; r < 3; ++r) {
             c[r] = __ddiv_rn(__dadd_rn(__dadd_rn(v[r], v[3 + r]), v[6 + r]), 3.0);
@@ -127,15 +137,15 @@ __global__ void build_facets_kernel(const MeshDesc *__restrict__ meshes,
 }
 
 void launch_build_facets(const MeshDesc *meshes, const InstDev *insts, int n_inst, int64_t F,
-                         double t0, double *tri64, double *c64, FacetRec *fac, float *aabb,
-                         float *vel32, unsigned int *bounds, cudaStream_t s)
+                         double t0, double *tri64, float *tri32, double *c64, FacetRec *fac,
+                         float *aabb, float *vel32, unsigned int *bounds, cudaStream_t s)
 {
     cudaMemsetAsync(bounds, 0xff, 3 * sizeof(unsigned int), s);
     cudaMemsetAsync(bounds + 3, 0, 3 * sizeof(unsigned int), s);
     const int T = 256;
     const unsigned int G = (unsigned int)((F + T - 1) / T);
-    build_facets_kernel<<<G, T, 0, s>>>(meshes, insts, n_inst, F, t0, tri64, c64, fac, aabb,
-                                        vel32, bounds);
+    build_facets_kernel<<<G, T, 0, s>>>(meshes, insts, n_inst, F, t0, tri64, tri32, c64, fac,
+                                        aabb, vel32, bounds);
 }
 
 // -------------------------------------------------------------------------

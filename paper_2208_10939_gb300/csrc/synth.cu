@@ -210,28 +210,36 @@ constexpr int kRecFact = 3;
 // to (0.06)^4 / 24 = 5.4e-7 of sum |w_v|
 constexpr float kFactMaxRot = 0.06f;
 
-constexpr int kMixWarps = 4;
-constexpr int kMixMinBlocks = 5;     // resident CTAs per SM the register budget targets
+constexpr int kMixWarps = 2;         // 2-warp CTAs: 22 KB of shared memory at S = 16
+constexpr int kMixMinBlocks = 10;    // resident CTAs per SM the register budget targets
 
 __device__ __forceinline__ float red1(float x) { return x - rintf(x); }
 
-template <int S>
+// S: consecutive samples per lane; LPR: lanes per chirp row (RPW = 32/LPR
+// rows of the same channel share a warp, e.g. two 256-sample chirps at
+// S = 16).  A 32-record tile holds LPR facets x RPW chirps: lane l builds
+// the record of facet (l mod LPR) for its own row.
+template <int S, int LPR>
 __global__ void __launch_bounds__(kMixWarps * 32, kMixMinBlocks)
 synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
 {
+    constexpr int RPW = 32 / LPR;
     __shared__ RecM sRec[kMixWarps][32];
     // running sums and Kahan compensations: [warp][re, im, c_re, c_im][S][lane]
     __shared__ float sAcc[kMixWarps][4][S][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = lane / LPR, col = lane % LPR;
     const int O = A.rd.O, P = A.rd.P, Q = A.rd.Q, AA = A.rd.A;
     const int TPI = A.tiles_per_item;
     const int64_t F = A.F;
+    const int nc = A.nc;
+    const int ngroups = (nc + RPW - 1) / RPW;
     const float fact_lim = kFactMaxRot / (6.283185307179586f * (float)(S > 1 ? S - 1 : 1));
     const int total = A.item_off[O];
     unsigned long long nV = 0, nSr = 0, nE = 0;
 
-    // persistent warps: each pulls (channel, chirp, sample segment, record
-    // chunk) items from a device counter until none remain
+    // persistent warps: each pulls (channel, chirp group, sample segment,
+    // record chunk) items from a device counter until none remain
     for (;;) {
     int item = 0;
     if (lane == 0) item = atomicAdd(A.item_counter, 1);
@@ -249,15 +257,22 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
     const int local = item - A.item_off[o];
     const int jchunk = local % ipu;
     const int rowseg = local / ipu;
-    const int seg = rowseg % W, nl = rowseg / W;
+    const int seg = rowseg % W, grp = rowseg / W;
+    (void)ngroups;
     const int rbeg = jchunk * TPI * 32;
     const int rend = min(cnt, rbeg + TPI * 32);
+    const int nl_raw = grp * RPW + row;
+    const bool row_ok = nl_raw < nc;
+    const int nl = row_ok ? nl_raw : 0;
     const int n = A.n0 + nl;
     const int tx = o / Q, rx = o % Q;
-    const int m0 = (seg * 32 + lane) * S;
+    const int m0 = (seg * LPR + col) * S;
     const float fm0 = (float)m0;
     const float fm0sq = fm0 * fm0;
-    const float eps_lane = 6.283185307179586f * (2.f * fm0 + 1.f);   // times p2
+    // the within-chirp quadratic phase p2 ((m0 + s)^2 - m0^2) is followed by a
+    // constant step of p2 (2 m0 + S - 1) per sample: exact at s = 0 and
+    // s = S - 1, off by at most p2 (S - 1)^2 / 4 cycles in between
+    const float eps_lane = 6.283185307179586f * (2.f * fm0 + (float)(S - 1));   // times p2
     const float ptx[3] = {K.ant[tx][0], K.ant[tx][1], K.ant[tx][2]};
     const float prx[3] = {K.ant[P + rx][0], K.ant[P + rx][1], K.ant[P + rx][2]};
     const float tn = (float)n * K.tc;
@@ -276,13 +291,13 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
     const float4 *kin_t = A.kin + ((int64_t)nl * AA + tx) * F;
     const float4 *kin_r = A.kin + ((int64_t)nl * AA + P + rx) * F;
 
-    for (int base = rbeg; base < rend; base += 32) {
+    for (int base = rbeg; base < rend; base += LPR) {
         // ---------------- build one record per lane ----------------
-        const bool valid = base + lane < rend;
+        const bool valid = row_ok && base + col < rend;
         int cls = -1;
         if (valid) {
             float *R = sRec[warp][lane].f;
-            const int k = list[base + lane];
+            const int k = list[base + col];
             const FacetRec fr = A.fac[k];
             const float4 vv = reinterpret_cast<const float4 *>(A.vel32)[fr.inst];
             const float4 kt = kin_t[k], kr = kin_r[k];
@@ -424,135 +439,153 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
             }
         }
         __syncwarp();
-        unsigned int mv = __ballot_sync(0xffffffffu, cls == kRecVertex);
-        unsigned int mf = __ballot_sync(0xffffffffu, cls == kRecFact);
-        unsigned int ms = __ballot_sync(0xffffffffu, cls == kRecSeries || cls == kRecEdge);
+        const unsigned int mv = __ballot_sync(0xffffffffu, cls == kRecVertex);
+        const unsigned int mf = __ballot_sync(0xffffffffu, cls == kRecFact);
+        const unsigned int ms = __ballot_sync(0xffffffffu, cls == kRecSeries || cls == kRecEdge);
         const unsigned int mser = __ballot_sync(0xffffffffu, cls == kRecSeries);
         nV += __popc(mv) + __popc(mf);
         nSr += __popc(mser);
         nE += __popc(ms & ~mser);
-        // ---------------- vertex records: one rotation per vertex ----------------
-        while (mv) {
-            const int i = __ffs(mv) - 1;
-            mv &= mv - 1;
-            const float *R = sRec[warp][i].f;
-            const float t1 = red1(R[15] * fm0);
-            const float q2 = R[16] * fm0sq;
-            const float eps = R[16] * eps_lane;
-#pragma unroll
-            for (int v = 0; v < 3; ++v) {
-                const float thv = red1(fmaf(R[3 + v], fm0, R[v] + t1) + q2);
-                float zs, zc;
-                __sincosf(6.283185307179586f * thv, &zs, &zc);
-                const float stc = fmaf(-eps, R[12 + v], R[9 + v]);
-                const float sts = fmaf(eps, R[9 + v], R[12 + v]);
-                const float w = R[6 + v];
-#pragma unroll
-                for (int j = 0; j < S; ++j) {
-                    pr[j] = fmaf(w, zc, pr[j]);
-                    pi[j] = fmaf(w, zs, pi[j]);
-                    if (j + 1 < S) {
-                        const float nc_ = fmaf(zc, stc, -zs * sts);
-                        zs = fmaf(zc, sts, zs * stc);
-                        zc = nc_;
+        // each lane walks its row's records; rows of one warp normally share
+        // the record forms (same facets, neighbouring chirps), so the
+        // branches below rarely diverge
+        for (int ii = 0; ii < LPR; ++ii) {
+            const int i = row * LPR + ii;
+            if ((mv >> i) & 1u) {
+                // ---------------- vertex form: one rotation per vertex ----------------
+                // 128-bit broadcast loads of the record
+                const float4 *R4 = reinterpret_cast<const float4 *>(sRec[warp][i].f);
+                const float4 q0 = R4[0], q1 = R4[1], q2v = R4[2], q3 = R4[3], q4 = R4[4];
+                const float ph0[3] = {q0.x, q0.y, q0.z};
+                const float lo[3] = {q0.w, q1.x, q1.y};
+                const float wv[3] = {q1.z, q1.w, q2v.x};
+                const float sre[3] = {q2v.y, q2v.z, q2v.w};
+                const float sim[3] = {q3.x, q3.y, q3.z};
+                const float hi = q3.w, p2 = q4.x;
+                const float t1 = red1(hi * fm0);
+                const float q2 = p2 * fm0sq;
+                const float eps = p2 * eps_lane;
+    #pragma unroll
+                for (int v = 0; v < 3; ++v) {
+                    const float thv = red1(fmaf(lo[v], fm0, ph0[v] + t1) + q2);
+                    float zs, zc;
+                    __sincosf(6.283185307179586f * thv, &zs, &zc);
+                    const float stc = fmaf(-eps, sim[v], sre[v]);
+                    const float sts = fmaf(eps, sre[v], sim[v]);
+                    const float w = wv[v];
+    #pragma unroll
+                    for (int j = 0; j < S; ++j) {
+                        pr[j] = fmaf(w, zc, pr[j]);
+                        pi[j] = fmaf(w, zs, pi[j]);
+                        if (j + 1 < S) {
+                            const float nc_ = fmaf(zc, stc, -zs * sts);
+                            zs = fmaf(zc, sts, zs * stc);
+                            zc = nc_;
+                        }
                     }
                 }
-            }
-        }
-        // ---------------- factored records: centroid rotation x quadratic W ----------------
-        while (mf) {
-            const int i = __ffs(mf) - 1;
-            mf &= mf - 1;
-            const float *R = sRec[warp][i].f;
-            const float thc = red1(fmaf(R[2], fm0, R[0] + red1(R[1] * fm0)) + R[3] * fm0sq);
-            float cs, cc;
-            __sincosf(6.283185307179586f * thc, &cs, &cc);
-            const float eps = R[3] * eps_lane;
-            const float stc = fmaf(-eps, R[5], R[4]);
-            const float sts = fmaf(eps, R[4], R[5]);
-            // W(s) = sum_v w_v exp(j 2 pi (psi_v + a_v (m0 + s))) as a cubic in s
-            float w0r = 0.f, w0i = 0.f, w1r = 0.f, w1i = 0.f, w2r = 0.f, w2i = 0.f;
-            float w3r = 0.f, w3i = 0.f;
-#pragma unroll
-            for (int v = 0; v < 3; ++v) {
-                const float ps = red1(fmaf(R[9 + v], fm0, R[6 + v]));
-                float zs, zc;
-                __sincosf(6.283185307179586f * ps, &zs, &zc);
-                w0r = fmaf(R[12 + v], zc, w0r);          // w z
-                w0i = fmaf(R[12 + v], zs, w0i);
-                w1r = fmaf(-R[15 + v], zs, w1r);         // w A j z
-                w1i = fmaf(R[15 + v], zc, w1i);
-                w2r = fmaf(R[18 + v], zc, w2r);          // -w A^2/2 z
-                w2i = fmaf(R[18 + v], zs, w2i);
-                w3r = fmaf(R[21 + v], zs, w3r);          // -j w A^3/6 z
-                w3i = fmaf(-R[21 + v], zc, w3i);
-            }
-            // forward differences of the cubic
-            float d1r = w1r + w2r + w3r, d1i = w1i + w2i + w3i;
-            float d2r = fmaf(6.f, w3r, 2.f * w2r), d2i = fmaf(6.f, w3i, 2.f * w2i);
-            const float d3r = 6.f * w3r, d3i = 6.f * w3i;
-#pragma unroll
-            for (int j = 0; j < S; ++j) {
-                pr[j] = fmaf(cc, w0r, fmaf(-cs, w0i, pr[j]));
-                pi[j] = fmaf(cc, w0i, fmaf(cs, w0r, pi[j]));
-                if (j + 1 < S) {
-                    const float nc_ = fmaf(cc, stc, -cs * sts);
-                    cs = fmaf(cc, sts, cs * stc);
-                    cc = nc_;
-                    w0r += d1r;
-                    w0i += d1i;
-                    d1r += d2r;
-                    d1i += d2i;
-                    d2r += d3r;
-                    d2i += d3i;
-                }
-            }
-        }
-        // ---------------- series / edge records: per sample ----------------
-        while (ms) {
-            const int i = __ffs(ms) - 1;
-            ms &= ms - 1;
-            const float *R = sRec[warp][i].f;
-            const bool series = (mser >> i) & 1u;
-#pragma unroll
-            for (int j = 0; j < S; ++j) {
-                const float fm = (float)(m0 + j);
-                const float thc = fmaf(R[3], fm * fm, fmaf(R[2], fm, R[0] + red1(R[1] * fm)));
-                const float kp = fmaf(fm, K.kap_step, 1.f);
-                if (series) {
-                    const float th = red1(thc + fmaf(R[5], fm, R[4]));
+        
+            } else if ((mf >> i) & 1u) {
+                // ---------------- factored form: centroid rotation x cubic W ----------------
+                const float4 *R4 = reinterpret_cast<const float4 *>(sRec[warp][i].f);
+                const float4 q0 = R4[0], q1 = R4[1], q2v = R4[2], q3 = R4[3], q4 = R4[4], q5 = R4[5];
+                // [0] ph0c [1] hi [2] loc [3] p2 [4..5] step [6..8] psi [9..11] a
+                // [12..14] w [15..17] wA [18..20] wA2 [21..23] wA3
+                const float psi[3] = {q1.z, q1.w, q2v.x};
+                const float av[3] = {q2v.y, q2v.z, q2v.w};
+                const float wv[3] = {q3.x, q3.y, q3.z};
+                const float wA[3] = {q3.w, q4.x, q4.y};
+                const float wA2[3] = {q4.z, q4.w, q5.x};
+                const float wA3[3] = {q5.y, q5.z, q5.w};
+                const float thc = red1(fmaf(q0.z, fm0, q0.x + red1(q0.y * fm0)) + q0.w * fm0sq);
+                float cs, cc;
+                __sincosf(6.283185307179586f * thc, &cs, &cc);
+                const float eps = q0.w * eps_lane;
+                const float stc = fmaf(-eps, q1.y, q1.x);
+                const float sts = fmaf(eps, q1.x, q1.y);
+                // W(s) = sum_v w_v exp(j 2 pi (psi_v + a_v (m0 + s))) as a cubic in s
+                float w0r = 0.f, w0i = 0.f, w1r = 0.f, w1i = 0.f, w2r = 0.f, w2i = 0.f;
+                float w3r = 0.f, w3i = 0.f;
+    #pragma unroll
+                for (int v = 0; v < 3; ++v) {
+                    const float ps = red1(fmaf(av[v], fm0, psi[v]));
                     float zs, zc;
-                    __sincosf(6.283185307179586f * th, &zs, &zc);
-                    const float k2 = kp * kp;
-                    float a = R[13], bb = R[20];
-#pragma unroll
-                    for (int q = 6; q >= 0; --q) a = fmaf(a, k2, R[6 + q]);
-#pragma unroll
-                    for (int q = 5; q >= 0; --q) bb = fmaf(bb, k2, R[14 + q]);
-                    const float re = a * k2, im = bb * k2 * kp;
-                    pr[j] += zc * re - zs * im;
-                    pi[j] += zc * im + zs * re;
-                } else {
-                    const int flags = __float_as_int(R[16]);
-#pragma unroll
-                    for (int e = 0; e < 3; ++e) {
-                        const float th = red1(thc + fmaf(R[5 + 4 * e], fm, R[4 + 4 * e]));
+                    __sincosf(6.283185307179586f * ps, &zs, &zc);
+                    w0r = fmaf(wv[v], zc, w0r);          // w z
+                    w0i = fmaf(wv[v], zs, w0i);
+                    w1r = fmaf(-wA[v], zs, w1r);         // w A j z
+                    w1i = fmaf(wA[v], zc, w1i);
+                    w2r = fmaf(wA2[v], zc, w2r);         // -w A^2/2 z
+                    w2i = fmaf(wA2[v], zs, w2i);
+                    w3r = fmaf(wA3[v], zs, w3r);         // -j w A^3/6 z
+                    w3i = fmaf(-wA3[v], zc, w3i);
+                }
+                // forward differences of the cubic
+                float d1r = w1r + w2r + w3r, d1i = w1i + w2i + w3i;
+                float d2r = fmaf(6.f, w3r, 2.f * w2r), d2i = fmaf(6.f, w3i, 2.f * w2i);
+                const float d3r = 6.f * w3r, d3i = 6.f * w3i;
+    #pragma unroll
+                for (int j = 0; j < S; ++j) {
+                    pr[j] = fmaf(cc, w0r, fmaf(-cs, w0i, pr[j]));
+                    pi[j] = fmaf(cc, w0i, fmaf(cs, w0r, pi[j]));
+                    if (j + 1 < S) {
+                        const float nc_ = fmaf(cc, stc, -cs * sts);
+                        cs = fmaf(cc, sts, cs * stc);
+                        cc = nc_;
+                        w0r += d1r;
+                        w0i += d1i;
+                        d1r += d2r;
+                        d1i += d2i;
+                        d2r += d3r;
+                        d2i += d3i;
+                    }
+                }
+        
+            } else if ((ms >> i) & 1u) {
+                // ---------------- series / edge forms: per sample ----------------
+                const bool series = (mser >> i) & 1u;
+                const float *R = sRec[warp][i].f;
+    #pragma unroll
+                for (int j = 0; j < S; ++j) {
+                    const float fm = (float)(m0 + j);
+                    const float thc = fmaf(R[3], fm * fm, fmaf(R[2], fm, R[0] + red1(R[1] * fm)));
+                    const float kp = fmaf(fm, K.kap_step, 1.f);
+                    if (series) {
+                        const float th = red1(thc + fmaf(R[5], fm, R[4]));
                         float zs, zc;
                         __sincosf(6.283185307179586f * th, &zs, &zc);
-                        const float x = kp * R[6 + 4 * e];
-                        float sn;
-                        if (flags & (1 << e)) {
-                            const float x2 = x * x;
-                            sn = fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, 1.f / 362880.f, -1.f / 5040.f),
-                                                        1.f / 120.f), -1.f / 6.f), 1.f);
-                        } else {
-                            sn = sinf(x) / x;   // accurate sinf: |x| may reach ~1e3
+                        const float k2 = kp * kp;
+                        float a = R[13], bb = R[20];
+    #pragma unroll
+                        for (int q = 6; q >= 0; --q) a = fmaf(a, k2, R[6 + q]);
+    #pragma unroll
+                        for (int q = 5; q >= 0; --q) bb = fmaf(bb, k2, R[14 + q]);
+                        const float re = a * k2, im = bb * k2 * kp;
+                        pr[j] += zc * re - zs * im;
+                        pi[j] += zc * im + zs * re;
+                    } else {
+                        const int flags = __float_as_int(R[16]);
+    #pragma unroll
+                        for (int e = 0; e < 3; ++e) {
+                            const float th = red1(thc + fmaf(R[5 + 4 * e], fm, R[4 + 4 * e]));
+                            float zs, zc;
+                            __sincosf(6.283185307179586f * th, &zs, &zc);
+                            const float x = kp * R[6 + 4 * e];
+                            float sn;
+                            if (flags & (1 << e)) {
+                                const float x2 = x * x;
+                                sn = fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, 1.f / 362880.f, -1.f / 5040.f),
+                                                            1.f / 120.f), -1.f / 6.f), 1.f);
+                            } else {
+                                sn = sinf(x) / x;   // accurate sinf: |x| may reach ~1e3
+                            }
+                            const float coef = kp * R[7 + 4 * e] * sn;
+                            pr[j] = fmaf(-coef, zs, pr[j]);
+                            pi[j] = fmaf(coef, zc, pi[j]);
                         }
-                        const float coef = kp * R[7 + 4 * e] * sn;
-                        pr[j] = fmaf(-coef, zs, pr[j]);
-                        pi[j] = fmaf(coef, zc, pi[j]);
                     }
                 }
+        
             }
         }
         // ---------------- Kahan-compensated tile accumulation ----------------
@@ -592,14 +625,15 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
 // item table: channel o owns ipu_o = ceil(ceil(cnt_o / 32) / TPI) record
 // chunks (at least one) per (chirp, sample segment); item_off is their prefix
 __global__ void synth_items_kernel(const int32_t *__restrict__ vis_cnt, int O, int TPI, int nc,
-                                   int W, int32_t *__restrict__ item_off, int *counter)
+                                   int RPW, int W, int32_t *__restrict__ item_off, int *counter)
 {
     if (threadIdx.x != 0) return;
     int run = 0;
+    const int ngroups = (nc + RPW - 1) / RPW;
     for (int o = 0; o < O; ++o) {
         item_off[o] = run;
         const int ipu = max(1, ((vis_cnt[o] + 31) / 32 + TPI - 1) / TPI);
-        run += ipu * nc * W;
+        run += ipu * ngroups * W;
     }
     item_off[O] = run;
     *counter = 0;
@@ -610,17 +644,20 @@ __global__ void synth_items_kernel(const int32_t *__restrict__ vis_cnt, int O, i
 __global__ void synth_reduce_kernel(const float2 *__restrict__ partial,
                                     const int32_t *__restrict__ item_off,
                                     const int32_t *__restrict__ vis_cnt, int TPI, int W, int S,
-                                    RadarDev rd, int n0, void *out, int out_c64)
+                                    int LPR, RadarDev rd, int n0, void *out, int out_c64)
 {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     const int nl = blockIdx.y, o = blockIdx.z;
     if (m >= rd.M) return;
-    const int seg = m / (32 * S), ml = m % (32 * S);
+    const int RPW = 32 / LPR;
+    const int grp = nl / RPW, row = nl % RPW;
+    const int seg = m / (LPR * S), ml = m % (LPR * S);
+    const int slot = (row * LPR + ml / S) * S + ml % S;     // lane * S + j
     const int ipu = max(1, ((vis_cnt[o] + 31) / 32 + TPI - 1) / TPI);
-    const int64_t it0 = (int64_t)item_off[o] + (int64_t)(nl * W + seg) * ipu;
+    const int64_t it0 = (int64_t)item_off[o] + (int64_t)(grp * W + seg) * ipu;
     double sr = 0.0, si = 0.0;
     for (int j = 0; j < ipu; ++j) {
-        const float2 p = partial[(it0 + j) * (32 * S) + ml];
+        const float2 p = partial[(it0 + j) * (32 * S) + slot];
         sr += (double)p.x;
         si += (double)p.y;
     }
@@ -670,26 +707,42 @@ static MixConsts mix_consts(const RadarDev &rd)
 // sums cost one 8-byte store and load per sample and item
 int synth_tiles_per_item(int64_t F) { return (int)std::max<int64_t>(16, ((F + 31) / 32 + 63) / 64); }
 
+// lane layout of the mixed kernel: S samples per lane, LPR lanes per chirp
+// row, W warps per row.  16 samples per lane halve the per-lane start-up
+// work (MUFU start phasors, cubic coefficients) against 8.
+struct MixLayout {
+    int S, LPR, W;
+};
+static MixLayout mix_layout(int M)
+{
+    if (M <= 512 && 512 % M == 0) return {16, M / 16, 1};
+    if (M % 512 == 0) return {16, 32, M / 512};
+    const int S = samples_per_lane(M);
+    return {S, 32, M / (32 * S)};
+}
+
 int64_t synth_max_items(int64_t F, const RadarDev &rd, int nc)
 {
-    const int S = samples_per_lane(rd.M), W = rd.M / (32 * S);
+    const MixLayout L = mix_layout(rd.M);
+    const int RPW = 32 / L.LPR;
     const int64_t tiles = (F + 31) / 32, TPI = synth_tiles_per_item(F);
-    return (int64_t)rd.O * std::max<int64_t>(1, (tiles + TPI - 1) / TPI) * nc * W;
+    return (int64_t)rd.O * std::max<int64_t>(1, (tiles + TPI - 1) / TPI) *
+           ((nc + RPW - 1) / RPW) * L.W;
 }
 
 int64_t synth_partial_words(int64_t F, const RadarDev &rd, int nc)
 {
-    return synth_max_items(F, rd, nc) * 32 * samples_per_lane(rd.M);
+    return synth_max_items(F, rd, nc) * 32 * mix_layout(rd.M).S;
 }
 
-template <int S> static int mixed_grid(int64_t items)
+template <int S, int LPR> static int mixed_grid(int64_t items)
 {
     static int blocks_per_sm = -1, sms = 0;
     if (blocks_per_sm < 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, synth_mixed_kernel<S>,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, synth_mixed_kernel<S, LPR>,
                                                       kMixWarps * 32, 0);
         if (blocks_per_sm < 1) blocks_per_sm = 1;
     }
@@ -697,26 +750,41 @@ template <int S> static int mixed_grid(int64_t items)
     return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)blocks_per_sm * sms));
 }
 
+template <int S, int LPR>
+static void run_mixed(const SynthArgs &a, const MixConsts &K, int W, int64_t items, cudaStream_t s)
+{
+    synth_mixed_kernel<S, LPR><<<mixed_grid<S, LPR>(items), kMixWarps * 32, 0, s>>>(a, K, W);
+}
+
 void launch_synth_mixed(const SynthArgs &a0, cudaStream_t s)
 {
     SynthArgs a = a0;
     const MixConsts K = mix_consts(a.rd);
     const int M = a.rd.M;
-    const int S = samples_per_lane(M);
-    const int W = M / (32 * S);
+    const MixLayout L = mix_layout(M);
     a.tiles_per_item = synth_tiles_per_item(a.F);
-    synth_items_kernel<<<1, 32, 0, s>>>(a.vis_cnt, a.rd.O, a.tiles_per_item, a.nc, W,
-                                        a.item_off, a.item_counter);
+    synth_items_kernel<<<1, 32, 0, s>>>(a.vis_cnt, a.rd.O, a.tiles_per_item, a.nc, 32 / L.LPR,
+                                        L.W, a.item_off, a.item_counter);
     const int64_t items = synth_max_items(a.F, a.rd, a.nc);
-    switch (S) {
-    case 8: synth_mixed_kernel<8><<<mixed_grid<8>(items), kMixWarps * 32, 0, s>>>(a, K, W); break;
-    case 4: synth_mixed_kernel<4><<<mixed_grid<4>(items), kMixWarps * 32, 0, s>>>(a, K, W); break;
-    case 2: synth_mixed_kernel<2><<<mixed_grid<2>(items), kMixWarps * 32, 0, s>>>(a, K, W); break;
-    default: synth_mixed_kernel<1><<<mixed_grid<1>(items), kMixWarps * 32, 0, s>>>(a, K, W); break;
+    if (L.S == 16) {
+        switch (L.LPR) {
+        case 2: run_mixed<16, 2>(a, K, L.W, items, s); break;
+        case 4: run_mixed<16, 4>(a, K, L.W, items, s); break;
+        case 8: run_mixed<16, 8>(a, K, L.W, items, s); break;
+        case 16: run_mixed<16, 16>(a, K, L.W, items, s); break;
+        default: run_mixed<16, 32>(a, K, L.W, items, s); break;
+        }
+    } else {
+        switch (L.S) {
+        case 8: run_mixed<8, 32>(a, K, L.W, items, s); break;
+        case 4: run_mixed<4, 32>(a, K, L.W, items, s); break;
+        case 2: run_mixed<2, 32>(a, K, L.W, items, s); break;
+        default: run_mixed<1, 32>(a, K, L.W, items, s); break;
+        }
     }
     dim3 rg((unsigned int)((M + 255) / 256), (unsigned int)a.nc, (unsigned int)a.rd.O);
-    synth_reduce_kernel<<<rg, 256, 0, s>>>(a.partial, a.item_off, a.vis_cnt, a.tiles_per_item, W,
-                                           S, a.rd, a.n0, a.out, a.out_c64);
+    synth_reduce_kernel<<<rg, 256, 0, s>>>(a.partial, a.item_off, a.vis_cnt, a.tiles_per_item, L.W,
+                                           L.S, L.LPR, a.rd, a.n0, a.out, a.out_c64);
 }
 
 // -------------------------------------------------------------------------
