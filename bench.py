@@ -200,6 +200,7 @@ def main():
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
     import paper_2208_10939_gb300 as pkg
+    from paper_2208_10939_gb300 import sharding
     import scenegen as sg
     pkg.load_library()
     torch.cuda.set_device(local)
@@ -248,18 +249,12 @@ def main():
         torch.distributed.barrier()
     clk = clocks.stop()
     sim.sync()
-    total_ms = float(sum(step_ms))
     last_tm = tm
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-        tt = torch.tensor([float(terms)], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt)
-        job_terms_per_step = float(tt.item())
-    else:
-        job_terms_per_step = float(terms)
-    value = job_terms_per_step * args.steps / (total_ms / 1e3)
+    # replicas: whole-job terms over the slowest rank's time
+    job = sharding.job_throughput(float(terms) * args.steps, float(sum(step_ms)) / 1e3)
+    total_ms = 1e3 * job["seconds"]
+    job_terms_per_step = job["work"] / args.steps
+    value = job["per_second"]
     frames = world * args.steps / (total_ms / 1e3)
 
     # dominant kernel: echo synthesis, average launch duration from CUDA events
@@ -324,11 +319,7 @@ def main():
     for _ in range(args.e2e_steps):
         e2e_step()
     torch.cuda.synchronize(dev)
-    e2e_s = time.perf_counter() - t
-    if world > 1:
-        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = sharding.reduce_scalar(time.perf_counter() - t, "max")
     e2e = {"value": job_terms_per_step * args.e2e_steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
            "ms_per_step": 1e3 * e2e_s / args.e2e_steps}
