@@ -72,6 +72,12 @@ def _load():
                                            ctypes.c_double, ctypes.c_double,
                                            ctypes.c_double, P]
             lib.orc_facet_integral.argtypes = [P, P, P, P]
+            lib.orc_visibility_bvh.argtypes = [P, ctypes.c_int64, P, ctypes.c_int,
+                                               ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_double, P]
+            lib.orc_visibility_pairs.argtypes = [P, ctypes.c_int64, P, P, ctypes.c_int64,
+                                                 ctypes.c_double, ctypes.c_double,
+                                                 ctypes.c_double, P]
             lib.orc_rcs_farfield.argtypes = [P, ctypes.c_int64, P, P, P, P,
                                              ctypes.c_int, P]
             lib.orc_adc_full.argtypes = [P, P, P, P, ctypes.c_int64, P, P,
@@ -129,6 +135,32 @@ def visibility(tri: np.ndarray, antennas: np.ndarray, eps_face: float = EPS_FACE
     return st
 
 
+def visibility_bvh(tri: np.ndarray, antennas: np.ndarray, eps_face: float = EPS_FACE,
+                   eps_b: float = EPS_B, eps_t: float = EPS_T) -> np.ndarray:
+    """``visibility`` through the oracle's own top-down median-split BVH
+    (for scenes too large for all pairs); same definition, same states."""
+    tri = np.ascontiguousarray(tri, np.float64)
+    ant = np.ascontiguousarray(antennas, np.float64).reshape(-1, 3)
+    F, A = tri.shape[0], ant.shape[0]
+    st = np.empty((A, F), np.uint8)
+    _load().orc_visibility_bvh(_p(tri), F, _p(ant), A, eps_face, eps_b, eps_t, _p(st))
+    return st
+
+
+def visibility_pairs(tri: np.ndarray, antennas: np.ndarray, pairs: np.ndarray,
+                     eps_face: float = EPS_FACE, eps_b: float = EPS_B,
+                     eps_t: float = EPS_T) -> np.ndarray:
+    """States of selected (antenna, facet) pairs (E x 2), brute force over
+    all occluders: the per-pair definition of ``visibility`` (Sec. 2.2)."""
+    tri = np.ascontiguousarray(tri, np.float64)
+    ant = np.ascontiguousarray(antennas, np.float64).reshape(-1, 3)
+    pr = np.ascontiguousarray(pairs, np.int64).reshape(-1, 2)
+    st = np.empty(pr.shape[0], np.uint8)
+    _load().orc_visibility_pairs(_p(tri), tri.shape[0], _p(ant), _p(pr), pr.shape[0],
+                                 eps_face, eps_b, eps_t, _p(st))
+    return st
+
+
 def facet_integral(tri9: np.ndarray, w: np.ndarray) -> complex:
     """J(w) = integral of exp(j w.(r - c)) over one flat triangle."""
     tri9 = np.ascontiguousarray(tri9, np.float64).reshape(9)
@@ -158,13 +190,18 @@ def _radar_struct(radar) -> _Radar:
 
 
 class Frame:
-    """Frame-start geometry and visibility of a scene (computed once)."""
+    """Frame-start geometry and visibility of a scene (computed once): brute
+    force over all occluders up to 60k facets, the oracle's own BVH above."""
 
-    def __init__(self, scene, state: np.ndarray | None = None):
+    def __init__(self, scene, state: np.ndarray | None = None, bvh: bool | None = None):
         self.scene = scene
         self.radar = scene.radar
         self.tri0, self.fvel, self.rho = world_facets(scene, scene.t0)
-        self.state = visibility(self.tri0, self.radar.antennas) if state is None else state
+        if state is None:
+            use_bvh = self.tri0.shape[0] > 60_000 if bvh is None else bvh
+            fn = visibility_bvh if use_bvh else visibility
+            state = fn(self.tri0, self.radar.antennas)
+        self.state = state
         self._rs = _radar_struct(self.radar)
 
     def adc_full(self) -> np.ndarray:

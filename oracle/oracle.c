@@ -204,6 +204,208 @@ void orc_visibility(const double *tri, int64_t F, const double *ant, int A,
     }
 }
 
+/* ---- a plain top-down BVH for large scenes (median split on the longest
+ * axis of the centroid box, leaves of <= 4 facets, FP64 boxes grown by 1e-6).
+ * Box culling only skips work: the decision is the same segment test over
+ * every facet whose grown box meets the segment's box, so the states equal
+ * the brute-force ones. */
+typedef struct {
+    double lo[3], hi[3];
+    int64_t left, right;     /* children, or -1 for a leaf */
+    int64_t first, count;    /* leaf range in the index array */
+} orc_node;
+
+typedef struct {
+    const double *tri;
+    double *cen;
+    int64_t *idx;
+    orc_node *nodes;
+    int64_t n_nodes;
+    int axis;
+} orc_bvh;
+
+static const double *g_sort_cen;
+static int g_sort_axis;
+static int cmp_cen(const void *a, const void *b)
+{
+    const double x = g_sort_cen[3 * *(const int64_t *)a + g_sort_axis];
+    const double y = g_sort_cen[3 * *(const int64_t *)b + g_sort_axis];
+    if (x < y) return -1;
+    if (x > y) return 1;
+    return (*(const int64_t *)a < *(const int64_t *)b) ? -1 : 1;
+}
+
+static int64_t bvh_build(orc_bvh *b, int64_t first, int64_t count)
+{
+    const int64_t id = b->n_nodes++;
+    orc_node *nd = &b->nodes[id];
+    for (int r = 0; r < 3; ++r) {
+        nd->lo[r] = 1e300;
+        nd->hi[r] = -1e300;
+    }
+    double clo[3] = {1e300, 1e300, 1e300}, chi[3] = {-1e300, -1e300, -1e300};
+    for (int64_t i = first; i < first + count; ++i) {
+        const double *t = b->tri + 9 * b->idx[i];
+        for (int v = 0; v < 3; ++v)
+            for (int r = 0; r < 3; ++r) {
+                if (t[3 * v + r] < nd->lo[r]) nd->lo[r] = t[3 * v + r];
+                if (t[3 * v + r] > nd->hi[r]) nd->hi[r] = t[3 * v + r];
+            }
+        for (int r = 0; r < 3; ++r) {
+            const double c = b->cen[3 * b->idx[i] + r];
+            if (c < clo[r]) clo[r] = c;
+            if (c > chi[r]) chi[r] = c;
+        }
+    }
+    for (int r = 0; r < 3; ++r) {
+        nd->lo[r] -= 1e-6;
+        nd->hi[r] += 1e-6;
+    }
+    if (count <= 4) {
+        nd->left = nd->right = -1;
+        nd->first = first;
+        nd->count = count;
+        return id;
+    }
+    int axis = 0;
+    for (int r = 1; r < 3; ++r)
+        if (chi[r] - clo[r] > chi[axis] - clo[axis]) axis = r;
+    g_sort_cen = b->cen;
+    g_sort_axis = axis;
+    qsort(b->idx + first, (size_t)count, sizeof(int64_t), cmp_cen);
+    const int64_t half = count / 2;
+    const int64_t l = bvh_build(b, first, half);
+    const int64_t rr = bvh_build(b, first + half, count - half);
+    b->nodes[id].left = l;
+    b->nodes[id].right = rr;
+    b->nodes[id].first = b->nodes[id].count = 0;
+    return id;
+}
+
+/* segment box [min(O,Pa), max(O,Pa)] against a node box, then the slab
+ * test of the segment in FP64; both conservative (boxes are grown). */
+static int seg_meets_box(const double *O, const double *D, const orc_node *nd)
+{
+    double t0 = 0.0, t1 = 1.0;
+    for (int r = 0; r < 3; ++r) {
+        if (D[r] == 0.0) {
+            if (O[r] < nd->lo[r] || O[r] > nd->hi[r]) return 0;
+            continue;
+        }
+        double a = (nd->lo[r] - O[r]) / D[r], b = (nd->hi[r] - O[r]) / D[r];
+        if (a > b) {
+            const double tmp = a;
+            a = b;
+            b = tmp;
+        }
+        a -= 1e-7 * (fabs(a) + 1.0);      /* slack for the division's rounding */
+        b += 1e-7 * (fabs(b) + 1.0);
+        if (a > t0) t0 = a;
+        if (b < t1) t1 = b;
+        if (t0 > t1) return 0;
+    }
+    return 1;
+}
+
+/* Visibility states (A x F) using the BVH above; same definition as
+ * orc_visibility. */
+void orc_visibility_bvh(const double *tri, int64_t F, const double *ant, int A,
+                        double eps_face, double eps_b, double eps_t, uint8_t *state)
+{
+    orc_bvh b;
+    b.tri = tri;
+    b.cen = (double *)malloc(sizeof(double) * 3 * (size_t)F);
+    b.idx = (int64_t *)malloc(sizeof(int64_t) * (size_t)F);
+    b.nodes = (orc_node *)malloc(sizeof(orc_node) * (size_t)(2 * F + 1));
+    b.n_nodes = 0;
+    for (int64_t k = 0; k < F; ++k) {
+        centroid3(tri + 9 * k, b.cen + 3 * k);
+        b.idx[k] = k;
+    }
+    bvh_build(&b, 0, F);
+#pragma omp parallel for schedule(dynamic, 256) collapse(2)
+    for (int a = 0; a < A; ++a) {
+        for (int64_t k = 0; k < F; ++k) {
+            const double *tk = tri + 9 * k;
+            double c[3], e1[3], e2[3], n[3], D[3];
+            centroid3(tk, c);
+            sub3(tk + 3, tk, e1);
+            sub3(tk + 6, tk, e2);
+            cross3(e1, e2, n);
+            sub3(ant + 3 * a, c, D);
+            const double cosang = dot3(n, D) / (sqrt(dot3(n, n)) * sqrt(dot3(D, D)));
+            uint8_t st;
+            if (dot3(n, n) == 0.0 || cosang <= -eps_face) {
+                st = ORC_BACK;
+            } else {
+                int graze = fabs(cosang) < eps_face;
+                int hit = 0;
+                int64_t stack[128];
+                int sp = 0;
+                stack[sp++] = 0;
+                while (sp > 0 && !hit) {
+                    const orc_node *nd = &b.nodes[stack[--sp]];
+                    if (!seg_meets_box(c, D, nd)) continue;
+                    if (nd->left < 0) {
+                        for (int64_t i = nd->first; i < nd->first + nd->count && !hit; ++i) {
+                            const int64_t j = b.idx[i];
+                            if (j == k) continue;
+                            const int r = mt_segment(c, D, tri + 9 * j, eps_b, eps_t);
+                            if (r == 2) hit = 1;
+                            else if (r == 1) graze = 1;
+                        }
+                    } else {
+                        stack[sp++] = nd->left;
+                        stack[sp++] = nd->right;
+                    }
+                }
+                st = hit ? ORC_OCCL : (graze ? ORC_GRAZE : ORC_LIT);
+            }
+            state[(int64_t)a * F + k] = st;
+        }
+    }
+    free(b.cen);
+    free(b.idx);
+    free(b.nodes);
+}
+
+/* The same states for selected (antenna, facet) pairs only (pairs: E x 2
+ * int64 rows (a, k)), still by brute force over every other facet: used on
+ * scenes too large for all pairs. */
+void orc_visibility_pairs(const double *tri, int64_t F, const double *ant, const int64_t *pairs,
+                          int64_t E, double eps_face, double eps_b, double eps_t, uint8_t *state)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t e = 0; e < E; ++e) {
+        const int a = (int)pairs[2 * e];
+        const int64_t k = pairs[2 * e + 1];
+        const double *tk = tri + 9 * k;
+        double c[3], e1[3], e2[3], n[3], D[3];
+        centroid3(tk, c);
+        sub3(tk + 3, tk, e1);
+        sub3(tk + 6, tk, e2);
+        cross3(e1, e2, n);
+        sub3(ant + 3 * a, c, D);
+        const double cosang = dot3(n, D) / (sqrt(dot3(n, n)) * sqrt(dot3(D, D)));
+        uint8_t st;
+        if (dot3(n, n) == 0.0 || cosang <= -eps_face) {
+            st = ORC_BACK;
+        } else {
+            int graze = fabs(cosang) < eps_face;
+            int hit = 0;
+            for (int64_t j = 0; j < F && !hit; ++j) {
+                if (j == k) continue;
+                if (boxes_disjoint(c, ant + 3 * a, tri + 9 * j, 1e-6)) continue;
+                const int r = mt_segment(c, D, tri + 9 * j, eps_b, eps_t);
+                if (r == 2) hit = 1;
+                else if (r == 1) graze = 1;
+            }
+            st = hit ? ORC_OCCL : (graze ? ORC_GRAZE : ORC_LIT);
+        }
+        state[e] = st;
+    }
+}
+
 /* ------------------------------------------------------------------ */
 /* physical optics facet integral                                      */
 /* ------------------------------------------------------------------ */

@@ -360,3 +360,21 @@ def test_hann_window():
         np.testing.assert_allclose(w, w[::-1], atol=1e-15)
         if L % 2:
             assert w[L // 2] == 1.0
+
+
+def test_oracle_bvh_visibility_equals_brute_force():
+    """The oracle's median-split BVH only skips work: its states equal the
+    all-pairs brute force on scenes with occlusion, grazing-prone ground and
+    several vehicles."""
+    for sc in (sg.small_car_scene(ntri=2500, P=2, Q=2),
+               sg.intersection_scene(seed=7, n_vehicles=5, M=64, N=2, P=2, Q=3, ground_n=30,
+                                     tri_scale=0.02)):
+        tri, _, _ = oracle.world_facets(sc, 0.0)
+        a = oracle.visibility(tri, sc.radar.antennas)
+        b = oracle.visibility_bvh(tri, sc.radar.antennas)
+        assert np.array_equal(a, b)
+        assert (a == oracle.OCCL).any() and (a == oracle.LIT).any()
+        pairs = np.stack([np.arange(60) % sc.radar.antennas.shape[0],
+                          np.arange(60) * 37 % tri.shape[0]], 1)
+        assert np.array_equal(oracle.visibility_pairs(tri, sc.radar.antennas, pairs),
+                              a[pairs[:, 0], pairs[:, 1]])
