@@ -26,12 +26,13 @@ __device__ __forceinline__ void sincospi_t(double x, double *s, double *c) { sin
 __device__ __forceinline__ float cospi_t(float x) { return cospif(x); }
 __device__ __forceinline__ double cospi_t(double x) { return cospi(x); }
 
+// symmetric Hann: 0.5 - 0.5 cos(2 pi i / (L-1)), evaluated in the FFT's own
+// precision (cospif / cospi)
 template <typename T>
 __device__ __forceinline__ T window_val(int i, int L, int kind)
 {
     if (kind == BART_WINDOW_RECT || L < 2) return (T)1;
-    // symmetric Hann: 0.5 - 0.5 cos(2 pi i / (L-1)); cospi of a double ratio
-    return (T)(0.5 - 0.5 * cospi_t((double)(2 * i) / (double)(L - 1)));
+    return (T)0.5 - (T)0.5 * cospi_t((T)(2 * i) / (T)(L - 1));
 }
 
 // Stockham stages over `cols` interleaved transforms of length L stored as
@@ -73,7 +74,7 @@ __device__ void fill_twiddles(typename Cplx<T>::type *tw, int L)
 {
     for (int j = threadIdx.x; j < (L >> 1); j += blockDim.x) {
         T s, c;
-        sincospi_t((T)(-2.0 * (double)j / (double)L), &s, &c);
+        sincospi_t((T)(-2 * j) / (T)L, &s, &c);
         tw[j].x = c;
         tw[j].y = s;
     }

@@ -639,34 +639,40 @@ __global__ void synth_items_kernel(const int32_t *__restrict__ vis_cnt, int O, i
     *counter = 0;
 }
 
-// sums the item partials of each (channel, chirp, sample) in FP64, in item
-// order, and applies C / k_m^2
+// sums the item partials of each (channel, chirp, sample) in item order with
+// Kahan compensation, and applies C / k_m^2 = out_scale / kappa_m^2
 __global__ void synth_reduce_kernel(const float2 *__restrict__ partial,
                                     const int32_t *__restrict__ item_off,
                                     const int32_t *__restrict__ vis_cnt, int TPI, int W, int S,
-                                    int LPR, RadarDev rd, int n0, void *out, int out_c64)
+                                    int LPR, int O, int N, int M, int n0, float out_scale,
+                                    float kap_step, void *out, int out_c64)
 {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     const int nl = blockIdx.y, o = blockIdx.z;
-    if (m >= rd.M) return;
+    if (m >= M) return;
     const int RPW = 32 / LPR;
     const int grp = nl / RPW, row = nl % RPW;
     const int seg = m / (LPR * S), ml = m % (LPR * S);
     const int slot = (row * LPR + ml / S) * S + ml % S;     // lane * S + j
     const int ipu = max(1, ((vis_cnt[o] + 31) / 32 + TPI - 1) / TPI);
     const int64_t it0 = (int64_t)item_off[o] + (int64_t)(grp * W + seg) * ipu;
-    double sr = 0.0, si = 0.0;
+    const float2 *src = partial + it0 * (32 * S) + slot;
+    float sr = 0.f, si = 0.f, cr = 0.f, ci = 0.f;
     for (int j = 0; j < ipu; ++j) {
-        const float2 p = partial[(it0 + j) * (32 * S) + slot];
-        sr += (double)p.x;
-        si += (double)p.y;
+        const float2 p = src[(int64_t)j * (32 * S)];
+        float y = p.x - cr, t = sr + y;
+        cr = (t - sr) - y;
+        sr = t;
+        y = p.y - ci;
+        t = si + y;
+        ci = (t - si) - y;
+        si = t;
     }
-    const double fm = rd.f0 + rd.slope * (double)m / rd.fs;
-    const double km = 2.0 * kPi * fm / kC0;
-    const double sc = 2.0 * sqrt(kPi) / pow(4.0 * kPi, 1.5) / (km * km);
-    const int64_t idx = ((int64_t)o * rd.N + n0 + nl) * rd.M + m;
-    if (out_c64) reinterpret_cast<float2 *>(out)[idx] = make_float2((float)(sr * sc), (float)(si * sc));
-    else reinterpret_cast<double2 *>(out)[idx] = make_double2(sr * sc, si * sc);
+    const float kp = fmaf((float)m, kap_step, 1.f);
+    const float sc = out_scale / (kp * kp);
+    const int64_t idx = ((int64_t)o * N + n0 + nl) * M + m;
+    if (out_c64) reinterpret_cast<float2 *>(out)[idx] = make_float2(sr * sc, si * sc);
+    else reinterpret_cast<double2 *>(out)[idx] = make_double2((double)sr * sc, (double)si * sc);
 }
 
 // consecutive samples per lane: the largest S in {8, 4, 2, 1} with 32 S | M;
@@ -784,7 +790,8 @@ void launch_synth_mixed(const SynthArgs &a0, cudaStream_t s)
     }
     dim3 rg((unsigned int)((M + 255) / 256), (unsigned int)a.nc, (unsigned int)a.rd.O);
     synth_reduce_kernel<<<rg, 256, 0, s>>>(a.partial, a.item_off, a.vis_cnt, a.tiles_per_item, L.W,
-                                           L.S, L.LPR, a.rd, a.n0, a.out, a.out_c64);
+                                           L.S, L.LPR, a.rd.O, a.rd.N, M, a.n0, K.out_scale,
+                                           K.kap_step, a.out, a.out_c64);
 }
 
 // -------------------------------------------------------------------------
