@@ -124,6 +124,8 @@ typedef struct bart_timing {
     float   rdm_ms;          /* last bart_form_rdm */
     int32_t synthesis_launches;   /* synthesis kernel launches in the frame */
     int32_t launches;        /* kernels launched by the last simulate + form_rdm */
+    float   detect_ms;       /* last bart_detect (RDM, CFAR, angle, points) */
+    int32_t detect_launches; /* kernels launched by the last bart_detect */
 } bart_timing;
 
 /* Text of the calling thread's last error ("" if none).  Valid until the
@@ -180,6 +182,18 @@ int bart_radar_set(bart_ctx *ctx, const bart_radar *radar);
 int bart_simulate_frame(bart_ctx *ctx, double t0, int32_t path, void *adc,
                         int32_t dtype, bart_stats *stats);
 
+/* Add white complex Gaussian noise to an ADC cube of the current radar
+ * shape, in place (Sec. 3.2: noise "with a certain signal-to-noise ratio"):
+ *   x[e] += sigma n[e],  sigma^2 = P / 10^(snr_db/10),  P = mean |x|^2 of the cube,
+ *   n[e] ~ CN(0, 1) from Philox4x32-10 (Salmon et al., SC 2011) with counter
+ *   (e mod 2^32, e div 2^32, frame, 0) and key (seed mod 2^32, seed div 2^32),
+ *   mapped to uniforms (w + 1) 2^-32 and through Box-Muller;
+ * e is the element index in the [O][N][M] cube.  adc: device pointer of
+ * `dtype` (FP64 arithmetic for C128, FP32 for C64).  Deterministic for a
+ * given (seed, frame).  Errors: ESTATE, EINVAL, ENOMEM, ECUDA. */
+int bart_add_noise(bart_ctx *ctx, void *adc, int32_t dtype, double snr_db, uint64_t seed,
+                   uint32_t frame);
+
 /* Range-Doppler map (Sec. 3.3) of an ADC cube of the current radar shape:
  * window + forward FFT over fast time, window + forward FFT over chirps,
  * |.|^2 summed over the O channels, zero Doppler shifted to bin N/2.
@@ -200,7 +214,7 @@ int bart_form_rdm(bart_ctx *ctx, const void *adc, int32_t dtype, float *rdm);
  * No context is needed: the cube shape is passed explicitly.  adc: device
  * pointer, O*N*M complex samples of `dtype`, [O][N][M]; rdm: device pointer,
  * M x N float32; window: BART_WINDOW_*; stream: a cudaStream_t (0 = legacy
- * default stream) on the current device.  The range-FFT intermediate lives
+ * default stream) on the current device.  The range-FFT intermediate
  * and the per-channel Doppler power live in a fixed 16 MiB array compiled
  * into the library, which every GPU that loads the library holds until the
  * process exits; cubes needing more (O*N*M > 1398101 complex64 or 699050
@@ -216,6 +230,59 @@ int bart_form_rdm(bart_ctx *ctx, const void *adc, int32_t dtype, float *rdm);
  * Errors: EINVAL, ECUDA. */
 int bart_form_rdm_static(const void *adc, int32_t dtype, int32_t O, int32_t N,
                          int32_t M, int32_t window, float *rdm, void *stream);
+
+/* CA-CFAR detector and azimuth estimator settings (Sec. 3.3).  The
+ * training cells of a cell under test are those of the rectangle of
+ * half-sizes (guard_r + train_r) x (guard_d + train_d) around it that lie
+ * outside the guard rectangle of half-sizes guard_r x guard_d; the Doppler
+ * axis wraps, range cells whose rectangle leaves [0, M) are not tested.
+ * Constraints (else BART_EINVAL): guard_*, train_* >= 0; at least one
+ * training cell; guard_r + train_r <= 64 and 2 (guard_r + train_r) < M;
+ * guard_d + train_d <= 64 and 2 (guard_d + train_d) < N; 0 < pfa < 1;
+ * 2 <= angle_bins <= 4096; reserved == 0. */
+typedef struct bart_detect_cfg {
+    int32_t guard_r, guard_d;    /* guard half-widths, range / Doppler bins */
+    int32_t train_r, train_d;    /* training band widths beyond the guard */
+    double  pfa;                 /* design false-alarm probability in exponential
+                                    (square-law) noise: threshold factor
+                                    alpha = n (pfa^(-1/n) - 1), n training cells */
+    int32_t angle_bins;          /* azimuth grid: s_i = sin(az) = -1 + 2 i / angle_bins */
+    int32_t reserved;            /* must be 0 */
+} bart_detect_cfg;
+
+/* One detected point (56 bytes).  Frame: radar-centred, boresight +Y,
+ * azimuth from +Y toward +X. */
+typedef struct bart_point {
+    double  range;               /* m: c fs r_bin / (2 slope M)              (Eq. 4) */
+    double  rate;                /* m/s: lambda_c (d_bin - N/2) / (2 N Tc),
+                                    positive receding, lambda_c = c / (f0 + B/2),
+                                    B = slope M / fs                         (Eq. 5) */
+    double  azimuth;             /* rad: asin(s_i) at the angle-spectrum peak (Eq. 6) */
+    double  x, y;                /* m: range sin(azimuth), range cos(azimuth) */
+    double  power;               /* RDM value of the cell */
+    int32_t r_bin, d_bin;        /* range bin; Doppler bin after the N/2 shift */
+} bart_point;
+
+/* Radar point cloud from an ADC cube of the current radar shape (Sec. 3.3,
+ * Eqs. 4-6): the RDM of bart_form_rdm; CA-CFAR on it, deciding in FP64
+ * (power > alpha * mean of the training cells); for every detection, in
+ * row-major (r_bin, d_bin) order, the angle spectrum
+ *   S(s_i) = | sum_o Y_o(r, d) exp(+j 2 pi x_o s_i / lambda_c) |^2
+ * over the O virtual channels (x_o = tx[p][0] + rx[q][0], o = p Q + q;
+ * Y the windowed range-Doppler cube in the FFT's precision), its first
+ * maximum giving the azimuth.
+ *   adc: device pointer, O*N*M complex of `dtype` (C64: FP32 FFTs and
+ *        spectrum; C128: FP64).
+ *   rdm: device pointer, M x N float32, receives the RDM; may be NULL.
+ *   points: device pointer of max_points bart_point (may be NULL when
+ *        max_points is 0); receives the first min(count, max_points) points.
+ *   n_points: host pointer or NULL.  When given, the call synchronises the
+ *        stream and stores the number of detections (which may exceed
+ *        max_points); when NULL the call stays asynchronous.
+ * M and N must be powers of two (N <= 1024) as for bart_form_rdm.
+ * Errors: ESTATE, EINVAL, ENOMEM, ECUDA. */
+int bart_detect(bart_ctx *ctx, const void *adc, int32_t dtype, const bart_detect_cfg *cfg,
+                float *rdm, bart_point *points, int32_t max_points, int32_t *n_points);
 
 /* One whole frame with host buffers: simulate into library-owned device
  * memory, form the RDM and copy it to the host array rdm_host (M x N

@@ -242,14 +242,142 @@ def hann(L: int) -> np.ndarray:
     return 0.5 - 0.5 * np.cos(2.0 * np.pi * i / (L - 1))
 
 
-def range_doppler_map(adc: np.ndarray) -> np.ndarray:
-    """RDM[r][d] (FP64) from an ADC cube [O][N][M] (Sec. 3.3): Hann window
-    and forward FFT over fast time (range), Hann window and forward FFT over
-    slow time (Doppler), |.|^2 summed over the O channels, Doppler axis
-    shifted so zero velocity sits at bin N/2."""
+def range_doppler_cube(adc: np.ndarray) -> np.ndarray:
+    """Y[o][d][r]: Hann window and forward FFT over fast time (range), then
+    Hann window and forward FFT over slow time (Doppler), per channel
+    (Sec. 3.3); Doppler index unshifted."""
     O, N, M = adc.shape
     X = np.fft.fft(adc * hann(M)[None, None, :], axis=2)
-    Y = np.fft.fft(X * hann(N)[None, :, None], axis=1)
+    return np.fft.fft(X * hann(N)[None, :, None], axis=1)
+
+
+def range_doppler_map(adc: np.ndarray) -> np.ndarray:
+    """RDM[r][d] (FP64) from an ADC cube [O][N][M] (Sec. 3.3): the range and
+    Doppler FFTs of ``range_doppler_cube``, |.|^2 summed over the O
+    channels, Doppler axis shifted so zero velocity sits at bin N/2."""
+    Y = range_doppler_cube(adc)
     P = (np.abs(Y) ** 2).sum(axis=0)                 # [N][M]
     P = np.fft.fftshift(P, axes=0)
     return np.ascontiguousarray(P.T)                 # [M][N]
+
+
+# ---------------------------------------------------------------------------
+# detection, angle and point cloud (Sec. 3.3, Eqs. 4-6)
+# ---------------------------------------------------------------------------
+def cfar_alpha(n_train: int, pfa: float) -> float:
+    """CA-CFAR threshold factor for square-law (exponential) noise:
+    Pfa = (1 + alpha/n)^-n  =>  alpha = n (Pfa^(-1/n) - 1)."""
+    return n_train * (pfa ** (-1.0 / n_train) - 1.0)
+
+
+def ca_cfar(rdm: np.ndarray, guard_r: int, guard_d: int, train_r: int, train_d: int,
+            pfa: float):
+    """Cell-averaging CFAR on RDM[r][d] (Sec. 3.3, CA-CFAR): the noise level
+    of a cell is the mean of its training cells -- the cells of the
+    rectangle of half-sizes (guard + train) around it that lie outside the
+    guard rectangle of half-sizes guard -- and the cell is a detection when
+    its power exceeds alpha times that mean.  Doppler wraps cyclically;
+    range cells whose rectangle leaves [0, M) are not tested.  Returns
+    (detections as a boolean M x N map, threshold map, +inf where untested)."""
+    M, N = rdm.shape
+    hr, hd = guard_r + train_r, guard_d + train_d
+    mask = np.ones((2 * hr + 1, 2 * hd + 1), bool)
+    mask[train_r:train_r + 2 * guard_r + 1, train_d:train_d + 2 * guard_d + 1] = False
+    n_train = int(mask.sum())
+    alpha = cfar_alpha(n_train, pfa)
+    det = np.zeros((M, N), bool)
+    thr = np.full((M, N), np.inf)
+    for r in range(hr, M - hr):
+        for d in range(N):
+            cols = [(d + k) % N for k in range(-hd, hd + 1)]
+            rect = rdm[r - hr:r + hr + 1][:, cols]
+            noise = rect[mask].sum() / n_train
+            thr[r, d] = alpha * noise
+            det[r, d] = rdm[r, d] > thr[r, d]
+    return det, thr
+
+
+def angle_spectrum(values: np.ndarray, xpos: np.ndarray, lam: float, bins: int) -> np.ndarray:
+    """|sum_o Y_o exp(+j 2 pi x_o s / lambda)|^2 on the grid s_i = -1 + 2i/bins
+    (the angle FFT across the virtual array, Eq. 6, for arbitrary element
+    positions x_o along X; s = sin(theta), theta from boresight +Y to +X)."""
+    s = -1.0 + 2.0 * np.arange(bins) / bins
+    steer = np.exp(2j * np.pi * np.outer(s, xpos) / lam)
+    return np.abs(steer @ values) ** 2
+
+
+def point_cloud(adc: np.ndarray, radar, guard_r=2, guard_d=2, train_r=8, train_d=4,
+                pfa=1e-6, angle_bins=512) -> list:
+    """Points (range, range rate, azimuth, x, y, power, r_bin, d_bin) of the
+    CA-CFAR detections in row-major (range, shifted Doppler) order:
+    range R = c fs r / (2 mu M) (Eq. 4), range rate lambda_c (d - N/2) / (2 N T_c)
+    (Eq. 5, positive receding), azimuth asin(s*) at the angle-spectrum peak
+    (Eq. 6), x = R sin(theta), y = R cos(theta)."""
+    O, N, M = adc.shape
+    Y = range_doppler_cube(adc)
+    rdm = np.fft.fftshift((np.abs(Y) ** 2).sum(axis=0), axes=0).T
+    det, _ = ca_cfar(rdm, guard_r, guard_d, train_r, train_d, pfa)
+    B = radar.slope * radar.M / radar.fs
+    lam_c = C0 / (radar.f0 + 0.5 * B)
+    xpos = np.array([radar.tx[p][0] + radar.rx[q][0] for p in range(radar.P)
+                     for q in range(radar.Q)])
+    pts = []
+    for r, ds in zip(*np.nonzero(det)):
+        d = (ds + N // 2) % N
+        spec = angle_spectrum(Y[:, d, r], xpos, lam_c, angle_bins)
+        i = int(np.argmax(spec))
+        s = -1.0 + 2.0 * i / angle_bins
+        th = float(np.arcsin(np.clip(s, -1.0, 1.0)))
+        R = C0 * radar.fs * r / (2.0 * radar.slope * M)
+        v = lam_c * (ds - N / 2) / (2.0 * N * radar.Tc)
+        pts.append((R, v, th, R * np.sin(th), R * np.cos(th), float(rdm[r, ds]), int(r), int(ds)))
+    return pts
+
+
+# ---------------------------------------------------------------------------
+# additive white Gaussian noise (Sec. 3.2: noise "with a certain
+# signal-to-noise ratio")
+# ---------------------------------------------------------------------------
+_PHILOX_M = (np.uint64(0xD2511F53), np.uint64(0xCD9E8D57))
+_PHILOX_W = (np.uint64(0x9E3779B9), np.uint64(0xBB67AE85))
+_MASK32 = np.uint64(0xFFFFFFFF)
+
+
+def philox4x32_10(ctr: np.ndarray, key) -> np.ndarray:
+    """Philox4x32 with 10 rounds (Salmon et al., SC 2011), vectorised over
+    rows of ``ctr`` (E x 4 uint32); ``key`` is two uint32 words."""
+    c = [np.asarray(ctr[:, i], np.uint64) for i in range(4)]
+    k0, k1 = np.uint64(int(key[0]) & 0xFFFFFFFF), np.uint64(int(key[1]) & 0xFFFFFFFF)
+    for _ in range(10):
+        p0 = _PHILOX_M[0] * c[0]
+        p1 = _PHILOX_M[1] * c[2]
+        hi0, lo0 = p0 >> np.uint64(32), p0 & _MASK32
+        hi1, lo1 = p1 >> np.uint64(32), p1 & _MASK32
+        c = [hi1 ^ c[1] ^ k0, lo1, hi0 ^ c[3] ^ k1, lo0]
+        k0 = (k0 + _PHILOX_W[0]) & _MASK32
+        k1 = (k1 + _PHILOX_W[1]) & _MASK32
+    return np.stack([x.astype(np.uint32) for x in c], axis=1)
+
+
+def unit_normal_pairs(n: int, seed: int, frame: int) -> np.ndarray:
+    """Standard complex normals CN(0, 1) for elements 0..n-1: Philox output
+    (counter = element index, frame; key = seed) mapped to (0, 1] uniforms
+    u = (w + 1) 2^-32 and through Box-Muller, (g1 + j g2)/sqrt(2)."""
+    e = np.arange(n, dtype=np.uint64)
+    ctr = np.stack([e & _MASK32, e >> np.uint64(32),
+                    np.full(n, frame & 0xFFFFFFFF, np.uint64), np.zeros(n, np.uint64)], 1)
+    w = philox4x32_10(ctr, (seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)).astype(np.float64)
+    u1 = (w[:, 0] + 1.0) * 2.0 ** -32
+    u2 = (w[:, 1] + 1.0) * 2.0 ** -32
+    r = np.sqrt(-2.0 * np.log(u1))
+    return (r * np.cos(2 * np.pi * u2) + 1j * r * np.sin(2 * np.pi * u2)) / np.sqrt(2.0)
+
+
+def add_noise(adc: np.ndarray, snr_db: float, seed: int, frame: int = 0) -> np.ndarray:
+    """ADC cube plus white complex Gaussian noise of power P / 10^(SNR/10),
+    P the cube's mean |x|^2 (a new array)."""
+    x = np.asarray(adc, np.complex128)
+    p = float(np.mean(np.abs(x) ** 2))
+    sigma = np.sqrt(p / 10.0 ** (snr_db / 10.0))
+    n = unit_normal_pairs(x.size, seed, frame).reshape(x.shape)
+    return x + sigma * n

@@ -33,7 +33,7 @@ EXPORTED = ["bart_last_error", "bart_version", "bart_create", "bart_destroy",
             "bart_set_stream", "bart_mesh_upload", "bart_mesh_clear", "bart_scene_set",
             "bart_scene_facets", "bart_radar_set", "bart_simulate_frame", "bart_form_rdm",
             "bart_frame_host", "bart_get_visibility", "bart_set_timing", "bart_get_timing",
-            "bart_sync", "bart_form_rdm_static"]
+            "bart_sync", "bart_form_rdm_static", "bart_add_noise", "bart_detect"]
 
 
 class BartError(RuntimeError):
@@ -72,12 +72,31 @@ class bart_timing(ctypes.Structure):
     _fields_ = [("scene_ms", ctypes.c_float), ("bvh_ms", ctypes.c_float),
                 ("visibility_ms", ctypes.c_float), ("kinematics_ms", ctypes.c_float),
                 ("synthesis_ms", ctypes.c_float), ("rdm_ms", ctypes.c_float),
-                ("synthesis_launches", ctypes.c_int32), ("launches", ctypes.c_int32)]
+                ("synthesis_launches", ctypes.c_int32), ("launches", ctypes.c_int32),
+                ("detect_ms", ctypes.c_float), ("detect_launches", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: (float(getattr(self, f)) if t is ctypes.c_float else int(getattr(self, f)))
                 for f, t in self._fields_}
 
+
+class bart_detect_cfg(ctypes.Structure):
+    _fields_ = [("guard_r", ctypes.c_int32), ("guard_d", ctypes.c_int32),
+                ("train_r", ctypes.c_int32), ("train_d", ctypes.c_int32),
+                ("pfa", ctypes.c_double), ("angle_bins", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class bart_point(ctypes.Structure):
+    _fields_ = [("range", ctypes.c_double), ("rate", ctypes.c_double),
+                ("azimuth", ctypes.c_double), ("x", ctypes.c_double), ("y", ctypes.c_double),
+                ("power", ctypes.c_double), ("r_bin", ctypes.c_int32), ("d_bin", ctypes.c_int32)]
+
+
+# numpy view of a bart_point array
+POINT_DTYPE = np.dtype([("range", "<f8"), ("rate", "<f8"), ("azimuth", "<f8"), ("x", "<f8"),
+                        ("y", "<f8"), ("power", "<f8"), ("r_bin", "<i4"), ("d_bin", "<i4")])
+assert POINT_DTYPE.itemsize == ctypes.sizeof(bart_point) == 56
 
 _lib = None
 _lock = threading.Lock()
@@ -118,6 +137,9 @@ def load_library() -> ctypes.CDLL:
         L.bart_get_timing.argtypes = [P, ctypes.POINTER(bart_timing)]
         L.bart_sync.argtypes = [P]
         L.bart_form_rdm_static.argtypes = [P, I32, I32, I32, I32, I32, P, P]
+        L.bart_add_noise.argtypes = [P, P, I32, D, ctypes.c_uint64, ctypes.c_uint32]
+        L.bart_detect.argtypes = [P, P, I32, ctypes.POINTER(bart_detect_cfg), P, P, I32,
+                                  ctypes.POINTER(I32)]
         for name in EXPORTED:
             if name not in ("bart_last_error", "bart_version", "bart_destroy"):
                 getattr(L, name).restype = ctypes.c_int
@@ -264,6 +286,50 @@ def bart_frame_host(ctx: int, t0: float, path: int, rdm_host, stats: bool = Fals
     return st.as_dict() if st is not None else None
 
 
+def bart_add_noise(ctx: int, adc, snr_db: float, seed: int, frame: int = 0) -> None:
+    """Add white complex Gaussian noise at ``snr_db`` to the CUDA ADC tensor
+    in place (Philox4x32-10 counter-based, deterministic per seed/frame)."""
+    if not adc.is_cuda or not adc.is_contiguous():
+        raise ValueError("adc must be a contiguous CUDA tensor")
+    _check(load_library().bart_add_noise(ctx, ctypes.c_void_p(_ptr(adc)), _dtype_code(adc),
+                                         float(snr_db), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                         int(frame) & 0xFFFFFFFF))
+
+
+def make_detect_cfg(guard_r: int = 2, guard_d: int = 2, train_r: int = 8, train_d: int = 4,
+                    pfa: float = 1e-6, angle_bins: int = 512) -> bart_detect_cfg:
+    c = bart_detect_cfg()
+    c.guard_r, c.guard_d, c.train_r, c.train_d = int(guard_r), int(guard_d), int(train_r), int(train_d)
+    c.pfa, c.angle_bins, c.reserved = float(pfa), int(angle_bins), 0
+    return c
+
+
+def bart_detect(ctx: int, adc, cfg: bart_detect_cfg, points=None, rdm=None,
+                sync: bool = True) -> Optional[int]:
+    """CA-CFAR detections and their range, rate and azimuth (Sec. 3.3).
+    ``points``: CUDA uint8 tensor of max_points * 56 bytes (bart_point
+    records) or None; ``rdm``: CUDA float32 M x N tensor or None.  Returns
+    the number of detections when ``sync`` (the call then synchronises)."""
+    import torch
+    if not adc.is_cuda or not adc.is_contiguous():
+        raise ValueError("adc must be a contiguous CUDA tensor")
+    max_points = 0
+    if points is not None:
+        if not points.is_cuda or not points.is_contiguous() or points.dtype != torch.uint8:
+            raise ValueError("points must be a contiguous CUDA uint8 tensor")
+        max_points = points.numel() // POINT_DTYPE.itemsize
+    if rdm is not None and (not rdm.is_cuda or not rdm.is_contiguous()
+                            or rdm.dtype != torch.float32):
+        raise ValueError("rdm must be a contiguous CUDA float32 tensor")
+    n = ctypes.c_int32(-1)
+    _check(load_library().bart_detect(
+        ctx, ctypes.c_void_p(_ptr(adc)), _dtype_code(adc), ctypes.byref(cfg),
+        None if rdm is None else ctypes.c_void_p(_ptr(rdm)),
+        None if points is None else ctypes.c_void_p(_ptr(points)), int(max_points),
+        ctypes.byref(n) if sync else None))
+    return n.value if sync else None
+
+
 def bart_form_rdm_static(adc, rdm, O: int, N: int, M: int, window: int = WINDOW_HANN,
                          stream: Optional[int] = None) -> None:
     """RDM of ``adc`` into ``rdm`` without any device allocation by the
@@ -353,6 +419,22 @@ class Simulator:
                               device=adc.device)
         bart_form_rdm(self.ctx, adc, out)
         return out
+
+    def add_noise(self, adc, snr_db: float, seed: int, frame: int = 0):
+        bart_add_noise(self.ctx, adc, snr_db, seed, frame)
+        return adc
+
+    def detect(self, adc, max_points: int = 4096, rdm=None, **cfg):
+        """Point cloud of ``adc``: returns (structured numpy array of the
+        detections -- at most ``max_points`` -- and the total count)."""
+        import torch
+        buf = torch.empty(max(1, max_points) * POINT_DTYPE.itemsize, dtype=torch.uint8,
+                          device=adc.device)
+        n = bart_detect(self.ctx, adc, make_detect_cfg(**cfg),
+                        buf if max_points > 0 else None, rdm)
+        k = min(n, max_points)
+        host = buf[:k * POINT_DTYPE.itemsize].cpu().numpy()
+        return host.view(POINT_DTYPE), n
 
     def visibility(self):
         import torch

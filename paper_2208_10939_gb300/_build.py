@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libbartsim.so")
-SOURCES = ["capi.cu", "scene_bvh.cu", "visibility.cu", "synth.cu", "rdm.cu"]
+SOURCES = ["capi.cu", "scene_bvh.cu", "visibility.cu", "synth.cu", "rdm.cu", "noise.cu", "detect.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

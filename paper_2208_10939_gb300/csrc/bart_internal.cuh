@@ -145,10 +145,46 @@ void launch_synth_mixed(const SynthArgs &a, cudaStream_t s);
 int64_t synth_partial_words(int64_t F, const RadarDev &rd, int nc);   // float2 words
 void launch_synth_fp64(const SynthArgs &a, cudaStream_t s);
 
+// ---- additive noise (noise.cu) ----
+int64_t noise_scratch_words();   // doubles
+void launch_add_noise(void *adc, int dtype, int64_t n, double snr_db, uint64_t seed,
+                      unsigned int frame, double *scratch, cudaStream_t s);
+
 // ---- range-Doppler map (rdm.cu) ----
 int64_t rdm_workspace_bytes(const RadarDev &rd, int dtype);
 void launch_rdm(const void *adc, int dtype, const RadarDev &rd, void *ws, float *rdm,
                 cudaStream_t s);
+
+// RDM that also keeps the complex range-Doppler cube Y[o][r][d'] (Doppler
+// shifted) in `cube`; X is an O*N*M complex scratch of the same precision.
+void launch_rdm_cube(const void *adc, int dtype, const RadarDev &rd, void *X, void *cube,
+                     float *rdm, cudaStream_t s);
+
+// ---- detection: CA-CFAR, angle spectrum, points (detect.cu) ----
+struct DetectDev {
+    int guard_r, guard_d, hr, hd;  // guard and outer half-sizes
+    int n_train;
+    double alpha;                  // CA-CFAR threshold factor
+    int bins;                      // azimuth grid size
+    double lam_c;                  // band-centre wavelength
+    double range_scale;            // metres per range bin (Eq. 4)
+    double rate_scale;             // m/s per Doppler bin (Eq. 5)
+};
+struct DetectBufs {
+    void *X, *cube;                // O*N*M complex each
+    float *rdm;                    // M*N
+    void *steer;                   // O*bins complex
+    uint8_t *flag;                 // M*N
+    int32_t *blk_cnt;              // M*N / rows_per_block
+    int32_t *list;                 // M*N cell indices
+    int32_t *count;                // 1
+};
+// bytes of each DetectBufs member for a radar / dtype / grid, 256-B aligned
+int64_t detect_workspace_bytes(const RadarDev &rd, int dtype, int bins);
+void detect_carve(void *ws, const RadarDev &rd, int dtype, int bins, DetectBufs *b);
+// launches the RDM, CFAR, compaction and angle kernels; returns the count
+int launch_detect(const void *adc, int dtype, const RadarDev &rd, const DetectDev &dd,
+                  const DetectBufs &b, bart_point *points, int max_points, cudaStream_t s);
 
 // Size of the static workspace used by bart_form_rdm_static (16 MiB).
 constexpr int64_t kRdmStaticWorkspaceBytes = 16ll << 20;

@@ -110,11 +110,14 @@ struct bart_ctx {
     DevBuf<unsigned long long> counters;   // 0 vertex, 1 series, 2 edge, 3 grazing
     DevBuf<int> status;
     DevBuf<unsigned char> rdm_ws, adc_own;
+    DevBuf<double> noise_scratch;
     DevBuf<float> rdm_own;
+    DevBuf<unsigned char> det_ws;       // detection: cube, RDM, steering table, lists
 
     // stage timing: fixed events + two per chirp chunk
     bool timing = false;
-    std::vector<cudaEvent_t> ev;        // 0 start, 1 facets, 2 bvh, 3 vis, 4 end, 5/6 rdm
+    std::vector<cudaEvent_t> ev;        // 0 start, 1 facets, 2 bvh, 3 vis, 4 end, 5/6 rdm,
+                                        // 7/8 detect
     std::vector<cudaEvent_t> ev_kin;    // per chunk: before kin, after kin (= before synth)
     std::vector<cudaEvent_t> ev_syn;    // per chunk: after synth
     // side stream running the kinematics of chunk c+1 while chunk c is synthesised
@@ -123,6 +126,9 @@ struct bart_ctx {
     int chunks = 0;
     int path = 0;
     bool have_rdm_timing = false;
+    bool have_detect_timing = false;
+    int32_t detect_launches = 0;
+    int32_t *count_host = nullptr;      // pinned readback of the detection count
     bool timed_frame = false;           // the last frame recorded its events
     int32_t frame_launches = 0, rdm_launches = 0;
 
@@ -146,7 +152,9 @@ struct bart_ctx {
         flags.release(); state.release(); blk_cnt.release(); vis_idx.release();
         vis_cnt.release(); kin.release(); partial.release(); item_off.release();
         item_counter.release(); counters.release(); status.release();
-        rdm_ws.release(); adc_own.release(); rdm_own.release();
+        rdm_ws.release(); adc_own.release(); rdm_own.release(); noise_scratch.release();
+        det_ws.release();
+        if (count_host) cudaFreeHost(count_host);
     }
 };
 
@@ -549,6 +557,7 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
     ctx->path = path;
     ctx->frame_launches = launches;
     ctx->have_rdm_timing = false;
+    ctx->have_detect_timing = false;
     ctx->timed_frame = tm;
     CUDA_TRY(cudaGetLastError(), "kernel launch");
     ctx->have_frame = true;
@@ -615,6 +624,96 @@ int bart_form_rdm(bart_ctx *ctx, const void *adc, int32_t dtype, float *rdm)
     g_err.clear();
     if (!ctx) return fail(BART_EINVAL, "bart_form_rdm: ctx is NULL");
     return run_rdm(ctx, adc, dtype, rdm);
+}
+
+int bart_add_noise(bart_ctx *ctx, void *adc, int32_t dtype, double snr_db, uint64_t seed,
+                   uint32_t frame)
+{
+    g_err.clear();
+    if (!ctx || !adc) return fail(BART_EINVAL, "bart_add_noise: NULL argument");
+    if (!ctx->have_radar) return fail(BART_ESTATE, "bart_add_noise: radar not set");
+    if (dtype != BART_C64 && dtype != BART_C128)
+        return fail(BART_EINVAL, "bart_add_noise: dtype=%d", dtype);
+    if (!std::isfinite(snr_db)) return fail(BART_EINVAL, "bart_add_noise: snr_db not finite");
+    BART_TRY(set_device(ctx));
+    BART_TRY(ctx->noise_scratch.ensure((size_t)noise_scratch_words(), "noise scratch"));
+    const int64_t n = (int64_t)ctx->radar.P * ctx->radar.Q * ctx->radar.N * ctx->radar.M;
+    launch_add_noise(adc, dtype, n, snr_db, seed, frame, ctx->noise_scratch.p, ctx->stream);
+    CUDA_TRY(cudaGetLastError(), "bart_add_noise launch");
+    return BART_OK;
+}
+
+int bart_detect(bart_ctx *ctx, const void *adc, int32_t dtype, const bart_detect_cfg *cfg,
+                float *rdm, bart_point *points, int32_t max_points, int32_t *n_points)
+{
+    g_err.clear();
+    if (!ctx || !adc || !cfg) return fail(BART_EINVAL, "bart_detect: NULL argument");
+    if (!ctx->have_radar) return fail(BART_ESTATE, "bart_detect: radar not set");
+    if (dtype != BART_C64 && dtype != BART_C128)
+        return fail(BART_EINVAL, "bart_detect: dtype=%d", dtype);
+    const bart_radar &r = ctx->radar;
+    if (!is_pow2(r.M) || !is_pow2(r.N) || r.N < 2 || r.N > 1024)
+        return fail(BART_EINVAL, "bart_detect: radix-2 FFTs need power-of-two M and N "
+                    "(M=%d, N=%d, N <= 1024)", r.M, r.N);
+    const int gr = cfg->guard_r, gd = cfg->guard_d, tr = cfg->train_r, td = cfg->train_d;
+    if (gr < 0 || gd < 0 || tr < 0 || td < 0 || gr + tr > 64 || gd + td > 64)
+        return fail(BART_EINVAL, "bart_detect: guard/train sizes must be in [0, 64] "
+                    "(guard %d,%d train %d,%d)", gr, gd, tr, td);
+    const int hr = gr + tr, hd = gd + td;
+    if (2 * hr >= r.M || 2 * hd >= r.N)
+        return fail(BART_EINVAL, "bart_detect: CFAR window %dx%d does not fit the %dx%d RDM",
+                    2 * hr + 1, 2 * hd + 1, r.M, r.N);
+    const int64_t n_train = (int64_t)(2 * hr + 1) * (2 * hd + 1) -
+                            (int64_t)(2 * gr + 1) * (2 * gd + 1);
+    if (n_train < 1) return fail(BART_EINVAL, "bart_detect: no training cells");
+    if (!(cfg->pfa > 0.0 && cfg->pfa < 1.0))
+        return fail(BART_EINVAL, "bart_detect: pfa=%g outside (0, 1)", cfg->pfa);
+    if (cfg->angle_bins < 2 || cfg->angle_bins > 4096 || cfg->reserved != 0)
+        return fail(BART_EINVAL, "bart_detect: angle_bins=%d outside [2, 4096] or reserved != 0",
+                    cfg->angle_bins);
+    if (max_points < 0 || (max_points > 0 && !points))
+        return fail(BART_EINVAL, "bart_detect: max_points=%d with points=%p", max_points,
+                    (const void *)points);
+    BART_TRY(set_device(ctx));
+    const RadarDev rd = make_rd(r);
+    DetectDev dd;
+    dd.guard_r = gr;
+    dd.guard_d = gd;
+    dd.hr = hr;
+    dd.hd = hd;
+    dd.n_train = (int)n_train;
+    dd.alpha = (double)n_train * (std::pow(cfg->pfa, -1.0 / (double)n_train) - 1.0);
+    dd.bins = cfg->angle_bins;
+    const double B = r.slope * r.M / r.fs;
+    dd.lam_c = kC0 / (r.f0 + 0.5 * B);
+    dd.range_scale = kC0 * r.fs / (2.0 * r.slope * r.M);
+    dd.rate_scale = dd.lam_c / (2.0 * r.N * r.Tc);
+    BART_TRY(ctx->det_ws.ensure((size_t)detect_workspace_bytes(rd, dtype, dd.bins),
+                                "detection workspace"));
+    DetectBufs b;
+    detect_carve(ctx->det_ws.p, rd, dtype, dd.bins, &b);
+    if (ctx->timing) {
+        BART_TRY(ensure_events(ctx->ev, 9));
+        CUDA_TRY(cudaEventRecord(ctx->ev[7], ctx->stream), "cudaEventRecord");
+    }
+    ctx->detect_launches = launch_detect(adc, dtype, rd, dd, b, points, max_points, ctx->stream);
+    CUDA_TRY(cudaGetLastError(), "bart_detect launch");
+    if (rdm)
+        CUDA_TRY(cudaMemcpyAsync(rdm, b.rdm, (size_t)r.M * r.N * sizeof(float),
+                                 cudaMemcpyDeviceToDevice, ctx->stream), "rdm copy");
+    if (ctx->timing) {
+        CUDA_TRY(cudaEventRecord(ctx->ev[8], ctx->stream), "cudaEventRecord");
+        ctx->have_detect_timing = true;
+    }
+    if (n_points) {
+        if (!ctx->count_host)
+            CUDA_TRY(cudaMallocHost(&ctx->count_host, sizeof(int32_t)), "cudaMallocHost");
+        CUDA_TRY(cudaMemcpyAsync(ctx->count_host, b.count, sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, ctx->stream), "count copy");
+        CUDA_TRY(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+        *n_points = *ctx->count_host;
+    }
+    return BART_OK;
 }
 
 int bart_form_rdm_static(const void *adc, int32_t dtype, int32_t O, int32_t N, int32_t M,
@@ -726,6 +825,11 @@ int bart_get_timing(bart_ctx *ctx, bart_timing *out)
         CUDA_TRY(cudaEventSynchronize(ctx->ev[6]), "cudaEventSynchronize");
         out->rdm_ms = elapsed(ctx->ev[5], ctx->ev[6]);
         out->launches += ctx->rdm_launches;
+    }
+    if (ctx->have_detect_timing) {
+        CUDA_TRY(cudaEventSynchronize(ctx->ev[8]), "cudaEventSynchronize");
+        out->detect_ms = elapsed(ctx->ev[7], ctx->ev[8]);
+        out->detect_launches = ctx->detect_launches;
     }
     return BART_OK;
 }

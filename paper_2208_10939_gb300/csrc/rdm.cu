@@ -107,10 +107,14 @@ __global__ void range_fft_kernel(const typename Cplx<T>::type *__restrict__ adc,
 }
 
 // one block per (RB consecutive range bins, channel): Doppler FFT of the
-// channel's RB columns, |Y|^2 written per channel (summed by rdm_sum_kernel)
-template <typename T>
-__global__ void doppler_power_kernel(const typename Cplx<T>::type *__restrict__ X, int N, int M,
-                                     int RB, int window, T *__restrict__ pw_out)
+// channel's RB columns.  CUBE = false: |Y|^2 written per channel, [o][r][d']
+// (summed by rdm_sum_kernel); CUBE = true: the complex Y written, [o][r][d']
+// (summed by rdm_cube_sum_kernel and kept for the angle spectrum).  d' is the
+// Doppler bin after the N/2 shift.
+template <typename T, bool CUBE>
+__global__ void doppler_kernel(const typename Cplx<T>::type *__restrict__ X, int N, int M,
+                               int RB, int window, T *__restrict__ pw_out,
+                               typename Cplx<T>::type *__restrict__ cube_out)
 {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -134,8 +138,9 @@ __global__ void doppler_power_kernel(const typename Cplx<T>::type *__restrict__ 
     for (int i = threadIdx.x; i < RB * N; i += blockDim.x) {
         const int c = i / N, d = i % N;
         const C v = res[i];
-        // [o][r][d'] with the Doppler shift applied
-        pw_out[((int64_t)o * M + r0 + c) * N + ((d + (N >> 1)) & (N - 1))] = v.x * v.x + v.y * v.y;
+        const int64_t at = ((int64_t)o * M + r0 + c) * N + ((d + (N >> 1)) & (N - 1));
+        if (CUBE) cube_out[at] = v;
+        else pw_out[at] = v.x * v.x + v.y * v.y;
     }
 }
 
@@ -150,6 +155,21 @@ __global__ void rdm_sum_kernel(const T *__restrict__ pw, int O, int64_t MN, floa
     rdm[i] = (float)acc;
 }
 
+// RDM[r][d'] = sum over channels of |Y[o][r][d']|^2, in channel order
+template <typename T>
+__global__ void rdm_cube_sum_kernel(const typename Cplx<T>::type *__restrict__ Y, int O,
+                                    int64_t MN, float *__restrict__ rdm)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= MN) return;
+    T acc = (T)0;
+    for (int o = 0; o < O; ++o) {
+        const typename Cplx<T>::type v = Y[(int64_t)o * MN + i];
+        acc += v.x * v.x + v.y * v.y;
+    }
+    rdm[i] = (float)acc;
+}
+
 static int rdm_rb(int N) { return N >= 512 ? 1 : 512 / N; }
 
 // workspace: the range-FFT output (O N M complex) followed by the
@@ -161,26 +181,60 @@ int64_t rdm_workspace_bytes(const RadarDev &rd, int dtype)
 }
 
 template <typename T>
-static void run_rdm(const void *adc, const RadarDev &rd, void *ws, float *rdm, cudaStream_t s)
+static void range_fft(const void *adc, const RadarDev &rd, void *X, cudaStream_t s)
 {
     using C = typename Cplx<T>::type;
-    const int M = rd.M, N = rd.N;
+    const int M = rd.M;
     const size_t sm1 = (size_t)(2 * M + M / 2) * sizeof(C);
     const int t1 = M / 2 < 1024 ? (M / 2 < 32 ? 32 : M / 2) : 1024;
     cudaFuncSetAttribute(range_fft_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sm1);
-    range_fft_kernel<T><<<(unsigned int)((int64_t)rd.O * N), t1, sm1, s>>>(
-        reinterpret_cast<const C *>(adc), reinterpret_cast<C *>(ws), M, rd.window);
+    range_fft_kernel<T><<<(unsigned int)((int64_t)rd.O * rd.N), t1, sm1, s>>>(
+        reinterpret_cast<const C *>(adc), reinterpret_cast<C *>(X), M, rd.window);
+}
+
+template <typename T, bool CUBE>
+static void doppler(const void *X, const RadarDev &rd, T *pw, void *cube, cudaStream_t s)
+{
+    using C = typename Cplx<T>::type;
+    const int M = rd.M, N = rd.N;
     int RB = rdm_rb(N);
     if (RB > M) RB = M;
-    T *pw = reinterpret_cast<T *>(reinterpret_cast<C *>(ws) + (int64_t)rd.O * N * M);
     const size_t sm2 = (size_t)(2 * RB * N + N / 2) * sizeof(C);
-    cudaFuncSetAttribute(doppler_power_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(doppler_kernel<T, CUBE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sm2);
-    doppler_power_kernel<T><<<dim3((unsigned int)(M / RB), (unsigned int)rd.O), 256, sm2, s>>>(
-        reinterpret_cast<const C *>(ws), N, M, RB, rd.window, pw);
-    const int64_t MN = (int64_t)M * N;
+    doppler_kernel<T, CUBE><<<dim3((unsigned int)(M / RB), (unsigned int)rd.O), 256, sm2, s>>>(
+        reinterpret_cast<const C *>(X), N, M, RB, rd.window, pw, reinterpret_cast<C *>(cube));
+}
+
+template <typename T>
+static void run_rdm(const void *adc, const RadarDev &rd, void *ws, float *rdm, cudaStream_t s)
+{
+    using C = typename Cplx<T>::type;
+    range_fft<T>(adc, rd, ws, s);
+    T *pw = reinterpret_cast<T *>(reinterpret_cast<C *>(ws) + (int64_t)rd.O * rd.N * rd.M);
+    doppler<T, false>(ws, rd, pw, nullptr, s);
+    const int64_t MN = (int64_t)rd.M * rd.N;
     rdm_sum_kernel<T><<<(unsigned int)((MN + 255) / 256), 256, 0, s>>>(pw, rd.O, MN, rdm);
+}
+
+template <typename T>
+static void run_rdm_cube(const void *adc, const RadarDev &rd, void *X, void *cube, float *rdm,
+                         cudaStream_t s)
+{
+    using C = typename Cplx<T>::type;
+    range_fft<T>(adc, rd, X, s);
+    doppler<T, true>(X, rd, nullptr, cube, s);
+    const int64_t MN = (int64_t)rd.M * rd.N;
+    rdm_cube_sum_kernel<T><<<(unsigned int)((MN + 255) / 256), 256, 0, s>>>(
+        reinterpret_cast<const C *>(cube), rd.O, MN, rdm);
+}
+
+void launch_rdm_cube(const void *adc, int dtype, const RadarDev &rd, void *X, void *cube,
+                     float *rdm, cudaStream_t s)
+{
+    if (dtype == BART_C64) run_rdm_cube<float>(adc, rd, X, cube, rdm, s);
+    else run_rdm_cube<double>(adc, rd, X, cube, rdm, s);
 }
 
 void launch_rdm(const void *adc, int dtype, const RadarDev &rd, void *ws, float *rdm,

@@ -45,9 +45,11 @@ def test_struct_layouts_match_c(tmp_path):
     prog = tmp_path / "sz.c"
     prog.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "bartsim.h"\n'
-        'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(bart_instance),'
-        ' sizeof(bart_radar), sizeof(bart_stats), offsetof(bart_radar, tx),'
-        ' offsetof(bart_instance, pos));return 0;}\n')
+        'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
+        ' sizeof(bart_instance), sizeof(bart_radar), sizeof(bart_stats),'
+        ' offsetof(bart_radar, tx), offsetof(bart_instance, pos), sizeof(bart_timing),'
+        ' offsetof(bart_timing, detect_ms), sizeof(bart_detect_cfg), sizeof(bart_point),'
+        ' offsetof(bart_point, r_bin));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)],
                    check=True)
@@ -55,7 +57,9 @@ def test_struct_layouts_match_c(tmp_path):
                                         check=True).stdout.split()))
     assert vals == [ctypes.sizeof(pkg.bart_instance), ctypes.sizeof(pkg.bart_radar),
                     ctypes.sizeof(pkg.bart_stats), pkg.bart_radar.tx.offset,
-                    pkg.bart_instance.pos.offset]
+                    pkg.bart_instance.pos.offset, ctypes.sizeof(pkg.bart_timing),
+                    pkg.bart_timing.detect_ms.offset, ctypes.sizeof(pkg.bart_detect_cfg),
+                    ctypes.sizeof(pkg.bart_point), pkg.bart_point.r_bin.offset]
 
 
 def test_version_and_error_string(lib):

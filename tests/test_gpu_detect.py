@@ -1,0 +1,258 @@
+"""GPU parity of the point-cloud stage (Sec. 3.3, Eqs. 4-6): CA-CFAR
+detections, range / rate / azimuth of each detection, through bart_detect,
+against the FP64 oracle on the same seeded ADC.
+
+What is compared:
+  - detection set: identical except cells whose oracle margin
+    |P - threshold| / max(P, threshold) is below the path's decision band
+    (FP32 rounding of the RDM for complex128 input, FP32 FFTs for
+    complex64), which are counted and bounded;
+  - order: row-major (range bin, shifted Doppler bin);
+  - range and rate: the Eq. 4 / Eq. 5 values of the same bins (1e-12);
+  - azimuth: the oracle's angle spectrum at the GPU's grid index is the
+    spectrum's maximum (to 1e-9 for complex128, 1e-3 for complex64);
+    complex128 picks the oracle's own index unless the two are within that
+    band.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2208_10939_gb300 as pkg
+import scenegen as sg
+
+pytestmark = pytest.mark.gpu
+
+CFG = dict(guard_r=2, guard_d=2, train_r=6, train_d=3, pfa=1e-4, angle_bins=256)
+
+
+@pytest.fixture(scope="module")
+def sim():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    s = pkg.Simulator(0)
+    yield s
+    s.close()
+
+
+_cache = {}
+
+
+def noisy_car():
+    """Coarse sedan, 3 TX x 4 RX (12-element filled virtual ULA), 128 x 32,
+    oracle ADC plus seeded white noise at 25 dB."""
+    if "car" not in _cache:
+        sc = sg.small_car_scene(ntri=1500, M=128, N=32, P=3, Q=4)
+        adc = oracle.add_noise(oracle.Frame(sc).adc_full(), 25.0, seed=77, frame=0)
+        _cache["car"] = (sc, adc)
+    return _cache["car"]
+
+
+def two_targets():
+    """Two point-like plates at different ranges and azimuths, one receding."""
+    if "two" not in _cache:
+        radar = sg.make_radar(128, 32, 3, 4, 5.12e6, 30e12, 2.0, centre=(0.0, 0.0, 0.0))
+        insts = []
+        for R, deg, v in ((9.0, -25.0, 0.0), (16.0, 35.0, 4.0)):
+            th = math.radians(deg)
+            u = np.array([math.sin(th), math.cos(th), 0.0])
+            insts.append(sg.Instance(0, R * u, sg.rot_z(-th), v * u))
+        sc = sg.Scene([sg.plate(0.01, 0.01, 1)], insts, radar, name="two_targets")
+        adc = oracle.add_noise(oracle.Frame(sc).adc_full(), 30.0, seed=5, frame=1)
+        _cache["two"] = (sc, adc)
+    return _cache["two"]
+
+
+def oracle_reference(sc, adc):
+    r = sc.radar
+    Y = oracle.range_doppler_cube(adc)
+    rdm = oracle.range_doppler_map(adc)
+    det, thr = oracle.ca_cfar(rdm, CFG["guard_r"], CFG["guard_d"], CFG["train_r"],
+                              CFG["train_d"], CFG["pfa"])
+    pts = oracle.point_cloud(adc, r, **CFG)
+    return Y, rdm, det, thr, pts
+
+
+def run_gpu(sim, sc, adc, dtype):
+    sim.load_scene(sc)
+    x = torch.from_numpy(np.ascontiguousarray(adc)).to("cuda").to(dtype)
+    rdm = torch.empty((sc.radar.M, sc.radar.N), dtype=torch.float32, device="cuda")
+    pts, n = sim.detect(x, max_points=8192, rdm=rdm, **CFG)
+    sim.sync()
+    return pts, n, rdm.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("case", ["car", "two"])
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+def test_point_cloud_matches_oracle(sim, case, dtype):
+    sc, adc = noisy_car() if case == "car" else two_targets()
+    r = sc.radar
+    M, N = r.M, r.N
+    Y, rdm_o, det_o, thr_o, pts_o = oracle_reference(sc, adc)
+    pts, n, rdm_g = run_gpu(sim, sc, adc, dtype)
+    c128 = dtype == torch.complex128
+    assert n == len(pts)
+
+    # the RDM the detector used
+    peak = rdm_o.max()
+    assert np.abs(rdm_g - rdm_o).max() / peak <= (1e-7 if c128 else 2e-6)
+
+    # detection sets, excluding cells inside the decision band
+    tested = np.isfinite(thr_o)
+    margin = np.full(rdm_o.shape, np.inf)
+    margin[tested] = np.abs(rdm_o[tested] - thr_o[tested]) / np.maximum(rdm_o[tested], thr_o[tested])
+    # FP32 FFTs: error of |Y|^2 at a cell ~ 1e-7 |Y_peak| |Y_cell|
+    band = 1e-6 if c128 else 1e-3 + 1e-6 * np.sqrt(peak / np.maximum(rdm_o, 1e-300))
+    sure = margin > band
+    det_g = np.zeros_like(det_o)
+    det_g[pts["r_bin"], pts["d_bin"]] = True
+    assert not det_g[~tested].any()
+    assert np.array_equal(det_g[sure], det_o[sure])
+    n_marginal = int((tested & ~sure).sum())
+    print(f"{case} {dtype}: {n} detections, {len(pts_o)} oracle, {n_marginal} marginal cells")
+    assert n_marginal <= max(2, 0.02 * len(pts_o))
+    assert len(pts_o) >= 1
+
+    # row-major order
+    key = pts["r_bin"].astype(np.int64) * N + pts["d_bin"]
+    assert np.all(np.diff(key) > 0)
+
+    # per-point values
+    ref = {(p[6], p[7]): p for p in pts_o}
+    lam_c = sg.C0 / (r.f0 + 0.5 * r.slope * M / r.fs)
+    xpos = np.array([r.tx[p][0] + r.rx[q][0] for p in range(r.P) for q in range(r.Q)])
+    bins = CFG["angle_bins"]
+    tol_a = 1e-9 if c128 else 1e-3
+    for p in pts:
+        rb, db = int(p["r_bin"]), int(p["d_bin"])
+        assert p["range"] == pytest.approx(sg.C0 * r.fs * rb / (2 * r.slope * M), rel=1e-12)
+        assert p["rate"] == pytest.approx(lam_c * (db - N / 2) / (2 * N * r.Tc), rel=1e-12,
+                                          abs=1e-12)
+        assert p["power"] == pytest.approx(rdm_o[rb, db], rel=1e-6 if c128 else 1e-3,
+                                           abs=2e-6 * peak)
+        d = (db + N // 2) % N
+        spec = oracle.angle_spectrum(Y[:, d, rb], xpos, lam_c, bins)
+        i_g = int(round((math.sin(p["azimuth"]) + 1.0) * bins / 2.0))
+        assert abs(-1.0 + 2.0 * i_g / bins - math.sin(p["azimuth"])) < 1e-9
+        assert spec[i_g] >= spec.max() * (1.0 - tol_a)
+        if c128 and (rb, db) in ref:
+            # the oracle's own choice, unless the two bins tie within 1e-9
+            i_o = int(round((math.sin(ref[(rb, db)][2]) + 1.0) * bins / 2.0))
+            assert i_o == i_g or spec[i_g] >= spec[i_o] * (1.0 - 1e-9)
+        assert p["x"] == pytest.approx(p["range"] * math.sin(p["azimuth"]), rel=1e-12, abs=1e-12)
+        assert p["y"] == pytest.approx(p["range"] * math.cos(p["azimuth"]), rel=1e-12, abs=1e-12)
+
+
+def test_two_targets_positions(sim):
+    """The strongest detection of each target sits at its Eq. 4 range, its
+    Eq. 5 rate and its Eq. 6 azimuth (within one range bin and 4 degrees)."""
+    sc, adc = two_targets()
+    pts, n, _ = run_gpu(sim, sc, adc, torch.complex64)
+    r = sc.radar
+    r_res = sg.C0 * r.fs / (2 * r.slope * r.M)
+    v_res = sg.C0 / (r.f0 + 0.5 * r.slope * r.M / r.fs) / (2 * r.N * r.Tc)
+    for R, deg, v in ((9.0, -25.0, 0.0), (16.0, 35.0, 4.0)):
+        near = pts[np.abs(pts["range"] - R) < 2 * r_res]
+        assert len(near), (R, deg)
+        best = near[np.argmax(near["power"])]
+        assert abs(best["range"] - R) <= r_res
+        assert abs(best["rate"] - v) <= v_res
+        assert abs(math.degrees(best["azimuth"]) - deg) < 4.0
+
+
+def test_truncation_and_async(sim):
+    """max_points below the count: the first max_points of the row-major
+    list, and the full count; without n_points the call is asynchronous
+    and writes the same records."""
+    sc, adc = noisy_car()
+    full, n, _ = run_gpu(sim, sc, adc, torch.complex64)
+    assert n > 3
+    x = torch.from_numpy(np.ascontiguousarray(adc)).to("cuda").to(torch.complex64)
+    k = n // 2
+    part, n2 = sim.detect(x, max_points=k, **CFG)
+    assert n2 == n and len(part) == k
+    assert np.array_equal(part, full[:k])
+    buf = torch.zeros(n * pkg.POINT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    assert pkg.bart_detect(sim.ctx, x, pkg.make_detect_cfg(**CFG), buf, None, sync=False) is None
+    sim.sync()
+    assert np.array_equal(buf.cpu().numpy().view(pkg.POINT_DTYPE), full)
+
+
+def test_silent_cube_has_no_detections(sim):
+    sc, _ = noisy_car()
+    sim.load_scene(sc)
+    x = torch.zeros((sc.radar.P * sc.radar.Q, sc.radar.N, sc.radar.M), dtype=torch.complex64,
+                    device="cuda")
+    pts, n = sim.detect(x, **CFG)
+    assert n == 0 and len(pts) == 0
+
+
+@pytest.mark.parametrize("bad", [dict(train_r=0, train_d=0, guard_r=0, guard_d=0),
+                                 dict(guard_d=10, train_d=10),
+                                 dict(pfa=0.0), dict(pfa=1.0), dict(angle_bins=1),
+                                 dict(angle_bins=8192), dict(guard_r=-1),
+                                 dict(guard_r=40, train_r=30)])
+def test_invalid_detector_settings(sim, bad):
+    sc, _ = noisy_car()
+    sim.load_scene(sc)
+    x = torch.zeros((sc.radar.P * sc.radar.Q, sc.radar.N, sc.radar.M), dtype=torch.complex64,
+                    device="cuda")
+    cfg = dict(CFG)
+    cfg.update(bad)
+    with pytest.raises(pkg.BartError) as e:
+        sim.detect(x, **cfg)
+    assert e.value.code == pkg.BART_EINVAL
+
+
+def test_config2_detect_full_size():
+    """Moving sedan, 256 x 128, 3 TX x 4 RX, mixed path, 20 dB noise: the
+    detector's RDM equals bart_form_rdm's, every reported cell passes the
+    CA-CFAR rule recomputed in FP64 from that RDM, sampled unreported cells
+    fail it, and the strongest return lies at the sedan's range and closing
+    speed."""
+    s = pkg.Simulator(0)
+    try:
+        sc = sg.car_scene()
+        s.load_scene(sc)
+        adc = s.simulate(pkg.PATH_MIXED)
+        s.add_noise(adc, 20.0, seed=9)
+        rdm_ref = s.rdm(adc)
+        rdm = torch.empty_like(rdm_ref)
+        cfg = dict(guard_r=2, guard_d=2, train_r=8, train_d=4, pfa=1e-6, angle_bins=512)
+        pts, n = s.detect(adc, max_points=1 << 16, rdm=rdm, **cfg)
+        s.sync()
+    finally:
+        s.close()
+    P = rdm.cpu().numpy().astype(np.float64)
+    assert np.abs(P - rdm_ref.cpu().numpy()).max() <= 1e-6 * P.max()
+    assert 0 < n == len(pts)
+    M, N = P.shape
+    hr, hd = 10, 6
+    mask = np.ones((2 * hr + 1, 2 * hd + 1), bool)
+    mask[8:13, 4:9] = False
+    n_train = int(mask.sum())
+    alpha = n_train * (cfg["pfa"] ** (-1.0 / n_train) - 1.0)
+
+    def decide(rb, db):
+        cols = [(db + k) % N for k in range(-hd, hd + 1)]
+        thr = alpha * P[rb - hr:rb + hr + 1][:, cols][mask].sum() / n_train
+        return P[rb, db] > thr, abs(P[rb, db] - thr) / max(P[rb, db], thr)
+
+    for p in pts:
+        ok, m = decide(int(p["r_bin"]), int(p["d_bin"]))
+        assert ok or m < 1e-9
+    rng = np.random.default_rng(3)
+    got = set(zip(pts["r_bin"].tolist(), pts["d_bin"].tolist()))
+    for _ in range(2000):
+        rb, db = int(rng.integers(hr, M - hr)), int(rng.integers(0, N))
+        if (rb, db) in got:
+            continue
+        ok, m = decide(rb, db)
+        assert not ok or m < 1e-9
+    best = pts[np.argmax(pts["power"])]
+    r = sc.radar
+    r_res = sg.C0 * r.fs / (2 * r.slope * r.M)
+    assert abs(best["range"] - 30.0) < 3.0 + r_res     # 30 m slant range to the car centre
+    assert -11.0 < best["rate"] < -8.0                  # closing at ~10 m/s

@@ -280,3 +280,22 @@ def test_config3_intersection_precision_study(sim):
           f"mixed vs oracle {err_mo:.3e}, fp64 vs oracle {err_do:.3e}")
     assert err_do <= TOL_FP64
     assert err_md <= TOL_MIXED and err_mo <= TOL_MIXED
+
+
+@pytest.mark.parametrize("path,tol", [(pkg.PATH_FP64, 1e-9), (pkg.PATH_MIXED, 1e-4)])
+def test_additive_noise_matches_oracle(sim, path, tol):
+    """Same Philox stream and Box-Muller map on both sides; the noise scale
+    follows each side's own cube power."""
+    sc, fr, ref = frame("small_car")
+    sim.load_scene(sc)
+    clean = sim.simulate(path)
+    noisy = clean.clone()
+    sim.add_noise(noisy, 12.0, seed=2024, frame=3)
+    n_gpu = (noisy - clean).cpu().numpy().astype(np.complex128)
+    n_ref = oracle.add_noise(ref, 12.0, seed=2024, frame=3) - ref
+    assert rel_l2(n_gpu, n_ref) <= tol
+    again = clean.clone()
+    sim.add_noise(again, 12.0, seed=2024, frame=3)
+    assert torch.equal(again, noisy)                       # deterministic
+    snr = 10 * np.log10(np.mean(np.abs(clean.cpu().numpy()) ** 2) / np.mean(np.abs(n_gpu) ** 2))
+    assert abs(snr - 12.0) < 0.2

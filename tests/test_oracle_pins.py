@@ -378,3 +378,84 @@ def test_oracle_bvh_visibility_equals_brute_force():
                           np.arange(60) * 37 % tri.shape[0]], 1)
         assert np.array_equal(oracle.visibility_pairs(tri, sc.radar.antennas, pairs),
                               a[pairs[:, 0], pairs[:, 1]])
+
+
+# ---------------------------------------------------------------------------
+# additive noise
+# ---------------------------------------------------------------------------
+def test_philox_known_answers(golden_dir):
+    g = json.load(open(os.path.join(golden_dir, "philox4x32_10_kat.json")))
+    for v in g["vectors"]:
+        ctr = np.array([[int(x, 16) for x in v["ctr"]]], np.uint32)
+        key = [int(x, 16) for x in v["key"]]
+        out = oracle.philox4x32_10(ctr, key)[0]
+        assert [int(x) for x in out] == [int(x, 16) for x in v["out"]]
+
+
+def test_noise_statistics_and_snr():
+    """CN(0,1) noise: zero mean, unit power, equal and uncorrelated quadratures,
+    white (flat periodogram); the SNR realised on a cube is the requested one."""
+    n = oracle.unit_normal_pairs(1 << 18, seed=12345, frame=7)
+    assert abs(n.mean()) < 5 * (1 / np.sqrt(n.size))
+    p = np.mean(np.abs(n) ** 2)
+    assert abs(p - 1.0) < 5 * np.sqrt(2.0 / n.size) * 1.0
+    assert abs(np.mean(n.real ** 2) - 0.5) < 0.01 and abs(np.mean(n.real * n.imag)) < 0.01
+    spec = np.abs(np.fft.fft(n.reshape(1024, -1), axis=1)) ** 2   # 256 bins, 1024 averages
+    flat = spec.mean(0) / spec.mean()
+    assert flat.min() > 0.8 and flat.max() < 1.2
+    assert not np.array_equal(n[:100], oracle.unit_normal_pairs(100, seed=12345, frame=8))
+    rng = np.random.default_rng(0)
+    adc = (rng.normal(size=(4, 8, 256)) + 1j * rng.normal(size=(4, 8, 256))) * 3e-7
+    noisy = oracle.add_noise(adc, 10.0, seed=99, frame=1)
+    ratio = np.mean(np.abs(adc) ** 2) / np.mean(np.abs(noisy - adc) ** 2)
+    assert abs(10 * np.log10(ratio) - 10.0) < 0.1
+
+
+# ---------------------------------------------------------------------------
+# CA-CFAR, angle FFT, point cloud (Sec. 3.3, Eqs. 4-6)
+# ---------------------------------------------------------------------------
+def test_cfar_false_alarm_rate_on_exponential_noise():
+    """Square-law noise is exponential; CA-CFAR's false-alarm probability is
+    (1 + alpha/n)^-n for the mean of n training cells: check it empirically."""
+    rng = np.random.default_rng(5)
+    pfa = 1e-2
+    det, thr = oracle.ca_cfar(rng.exponential(size=(96, 64)), 1, 1, 4, 3, pfa)
+    tested = np.isfinite(thr)
+    rate = det[tested].mean()
+    assert 0.5 * pfa < rate < 1.6 * pfa, rate
+    n = (2 * 5 + 1) * (2 * 4 + 1) - 9
+    assert abs((1 + oracle.cfar_alpha(n, pfa) / n) ** -n - pfa) < 1e-12
+
+
+def test_cfar_brute_force_window():
+    rng = np.random.default_rng(6)
+    rdm = rng.exponential(size=(20, 16))
+    rdm[9, 3] = 300.0
+    det, thr = oracle.ca_cfar(rdm, 1, 2, 2, 1, 1e-3)
+    # cell (9, 3) by hand: training = 7 x 7 rectangle minus 3 x 5 guard, Doppler cyclic
+    cells = [(r, d % 16) for r in range(6, 13) for d in range(0, 7)
+             if not (8 <= r <= 10 and 1 <= d <= 5)]
+    noise = np.mean([rdm[r, d] for r, d in cells])
+    assert abs(thr[9, 3] - oracle.cfar_alpha(len(cells), 1e-3) * noise) < 1e-12
+    assert det[9, 3] and not np.isfinite(thr[1, 0])
+
+
+def test_point_cloud_recovers_target_position():
+    """A point-like plate at 14 m, 30 deg azimuth, seen by a 12-element
+    virtual ULA: the strongest detection lies at the Eq. 4 range and the
+    Eq. 6 azimuth (within one range bin and the array's beamwidth)."""
+    th = math.radians(30.0)
+    R = 14.0
+    radar = sg.make_radar(128, 16, 3, 4, 5.12e6, 30e12, 2.0, centre=(0, 0, 0))
+    pos = np.array([R * math.sin(th), R * math.cos(th), 0.0])
+    inst = sg.Instance(0, pos, sg.rot_z(-th), (0, 0, 0))
+    sc = sg.Scene([sg.plate(0.01, 0.01, 1)], [inst], radar)
+    adc = oracle.Frame(sc).adc_full()
+    pts = oracle.point_cloud(adc, radar, pfa=1e-4)
+    assert pts
+    best = max(pts, key=lambda p: p[5])
+    r_res = sg.C0 * radar.fs / (2 * radar.slope * radar.M)
+    assert abs(best[0] - R) < 1.0 * r_res
+    assert abs(math.degrees(best[2]) - 30.0) < 3.0
+    assert abs(best[1]) < 1e-9                                   # static
+    assert abs(best[3] - best[0] * math.sin(best[2])) < 1e-9
