@@ -85,8 +85,8 @@ typedef struct bart_instance {
  * transmit frequency is f0 + slope*m/fs.
  * Constraints (else BART_EINVAL): M a multiple of 32 in [32, 1024];
  * 1 <= N <= 32768; 1 <= P <= BART_MAX_TX; 1 <= Q <= BART_MAX_RX;
- * f0, slope, fs > 0; Tc >= M/fs.  bart_form_rdm further needs M and N
- * powers of two (N <= 1024). */
+ * f0, slope, fs > 0; Tc >= M/fs.  bart_form_rdm and bart_detect further
+ * need M and N of the form 2^a 3^b (radix-2/3 FFTs; N in [2, 1024]). */
 typedef struct bart_radar {
     double  f0;                  /* chirp start frequency, Hz */
     double  slope;               /* mu, Hz/s */
@@ -199,8 +199,8 @@ int bart_add_noise(bart_ctx *ctx, void *adc, int32_t dtype, double snr_db, uint6
  * |.|^2 summed over the O channels, zero Doppler shifted to bin N/2.
  * adc: device pointer, O*N*M complex of `dtype` (FP64 arithmetic for C128,
  * FP32 for C64).  rdm: device pointer, M x N float32 (range-major).
- * Errors: ESTATE, EINVAL (M or N not a power of two, N > 1024), ENOMEM,
- * ECUDA. */
+ * Errors: ESTATE, EINVAL (M or N not of the form 2^a 3^b, N > 1024),
+ * ENOMEM, ECUDA. */
 int bart_form_rdm(bart_ctx *ctx, const void *adc, int32_t dtype, float *rdm);
 
 /* bart_form_rdm without any device allocation, for callers that cannot let
@@ -219,7 +219,7 @@ int bart_form_rdm(bart_ctx *ctx, const void *adc, int32_t dtype, float *rdm);
  * into the library, which every GPU that loads the library holds until the
  * process exits; cubes needing more (O*N*M > 1398101 complex64 or 699050
  * complex128 samples: 12 bytes, resp. 24, per sample) are rejected with
- * BART_EINVAL.  M and N must be powers of two (M in [32, 1024], N in
+ * BART_EINVAL.  M and N must be of the form 2^a 3^b (M in [32, 1024], N in
  * [2, 1024]).  The first call on a device looks the array's address up
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  The array is shared by every call and keeps
@@ -279,7 +279,7 @@ typedef struct bart_point {
  *   n_points: host pointer or NULL.  When given, the call synchronises the
  *        stream and stores the number of detections (which may exceed
  *        max_points); when NULL the call stays asynchronous.
- * M and N must be powers of two (N <= 1024) as for bart_form_rdm.
+ * M and N must be of the form 2^a 3^b (N <= 1024) as for bart_form_rdm.
  * Errors: ESTATE, EINVAL, ENOMEM, ECUDA. */
 int bart_detect(bart_ctx *ctx, const void *adc, int32_t dtype, const bart_detect_cfg *cfg,
                 float *rdm, bart_point *points, int32_t max_points, int32_t *n_points);

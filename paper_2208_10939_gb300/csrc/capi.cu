@@ -170,7 +170,14 @@ struct bart_ctx {
         if (_e != cudaSuccess) return cuda_fail(_e, what); \
     } while (0)
 
-static bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+// FFT lengths of the RDM kernels: 2^a 3^b
+static bool is_fft_len(int x)
+{
+    if (x < 1) return false;
+    while (x % 2 == 0) x /= 2;
+    while (x % 3 == 0) x /= 3;
+    return x == 1;
+}
 
 static RadarDev make_rd(const bart_radar &r)
 {
@@ -598,10 +605,10 @@ static int run_rdm(bart_ctx *ctx, const void *adc, int32_t dtype, float *rdm)
     if (!adc || !rdm) return fail(BART_EINVAL, "bart_form_rdm: NULL buffer");
     if (dtype != BART_C64 && dtype != BART_C128)
         return fail(BART_EINVAL, "bart_form_rdm: dtype=%d", dtype);
-    if (!is_pow2(ctx->radar.M) || !is_pow2(ctx->radar.N) || ctx->radar.N < 2 ||
+    if (!is_fft_len(ctx->radar.M) || !is_fft_len(ctx->radar.N) || ctx->radar.N < 2 ||
         ctx->radar.N > 1024)
-        return fail(BART_EINVAL, "bart_form_rdm: radix-2 FFTs need power-of-two M and N "
-                    "(M=%d, N=%d, N <= 1024)", ctx->radar.M, ctx->radar.N);
+        return fail(BART_EINVAL, "bart_form_rdm: the radix-2/3 FFTs need M and N of the form "
+                    "2^a 3^b (M=%d, N=%d, 2 <= N <= 1024)", ctx->radar.M, ctx->radar.N);
     BART_TRY(set_device(ctx));
     const RadarDev rd = make_rd(ctx->radar);
     BART_TRY(ctx->rdm_ws.ensure((size_t)rdm_workspace_bytes(rd, dtype), "rdm workspace"));
@@ -652,9 +659,9 @@ int bart_detect(bart_ctx *ctx, const void *adc, int32_t dtype, const bart_detect
     if (dtype != BART_C64 && dtype != BART_C128)
         return fail(BART_EINVAL, "bart_detect: dtype=%d", dtype);
     const bart_radar &r = ctx->radar;
-    if (!is_pow2(r.M) || !is_pow2(r.N) || r.N < 2 || r.N > 1024)
-        return fail(BART_EINVAL, "bart_detect: radix-2 FFTs need power-of-two M and N "
-                    "(M=%d, N=%d, N <= 1024)", r.M, r.N);
+    if (!is_fft_len(r.M) || !is_fft_len(r.N) || r.N < 2 || r.N > 1024)
+        return fail(BART_EINVAL, "bart_detect: the radix-2/3 FFTs need M and N of the form "
+                    "2^a 3^b (M=%d, N=%d, 2 <= N <= 1024)", r.M, r.N);
     const int gr = cfg->guard_r, gd = cfg->guard_d, tr = cfg->train_r, td = cfg->train_d;
     if (gr < 0 || gd < 0 || tr < 0 || td < 0 || gr + tr > 64 || gd + td > 64)
         return fail(BART_EINVAL, "bart_detect: guard/train sizes must be in [0, 64] "
@@ -725,9 +732,9 @@ int bart_form_rdm_static(const void *adc, int32_t dtype, int32_t O, int32_t N, i
         return fail(BART_EINVAL, "bart_form_rdm_static: dtype=%d", dtype);
     if (window != BART_WINDOW_HANN && window != BART_WINDOW_RECT)
         return fail(BART_EINVAL, "bart_form_rdm_static: window=%d", window);
-    if (O < 1 || !is_pow2(M) || M < 32 || M > 1024 || !is_pow2(N) || N < 2 || N > 1024)
-        return fail(BART_EINVAL, "bart_form_rdm_static: need O >= 1 and power-of-two "
-                    "M in [32,1024], N in [2,1024] (O=%d N=%d M=%d)", O, N, M);
+    if (O < 1 || !is_fft_len(M) || M < 32 || M > 1024 || !is_fft_len(N) || N < 2 || N > 1024)
+        return fail(BART_EINVAL, "bart_form_rdm_static: need O >= 1 and M in [32,1024], "
+                    "N in [2,1024], both of the form 2^a 3^b (O=%d N=%d M=%d)", O, N, M);
     RadarDev rd;
     std::memset(&rd, 0, sizeof rd);
     rd.O = O;

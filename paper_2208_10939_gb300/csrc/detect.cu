@@ -2,7 +2,7 @@
 //
 //  1. RDM with the complex cube kept: Y[o][r][d'] (rdm.cu).
 //  2. cfar_kernel: cell-averaging CFAR.  A block owns TR whole range rows
-//     (TR * N <= 1024 cells), so the cyclic Doppler neighbourhood of every
+//     (TR * N <= 1024 cells, TR | M), so the cyclic Doppler neighbourhood of every
 //     cell is inside the block.  Vertical partial sums first, per column:
 //       vout[r][c] = sum_{gr < |u| <= hr} P[r+u][c]   (rows outside the guard)
 //       vmid[r][c] = sum_{|u| <= gr}       P[r+u][c]   (rows of the guard)
@@ -39,10 +39,13 @@ constexpr int kCfarCells = 1024;      // cells per CFAR block (TR * N)
 constexpr int kAngleThreads = 256;
 constexpr int kAngleBlocks = 4 * 152;
 
+// whole range rows per CFAR block: the largest power of two TR with
+// TR N <= kCfarCells that divides M
 int rows_per_block(int M, int N)
 {
-    int tr = N >= kCfarCells ? 1 : kCfarCells / N;
-    return tr > M ? M : tr;
+    int tr = 1;
+    while (2 * tr * N <= kCfarCells && M % (2 * tr) == 0) tr *= 2;
+    return tr;
 }
 
 __global__ void __launch_bounds__(kCfarThreads)
@@ -54,7 +57,6 @@ cfar_kernel(const float *__restrict__ P, int M, int N, int TR, DetectDev dd,
     const int r0 = blockIdx.x * TR;
     const int cells = TR * N;
     const int gr = dd.guard_r, hr = dd.hr, gd = dd.guard_d, hd = dd.hd;
-    const int nmask = N - 1;
     for (int i = threadIdx.x; i < cells; i += blockDim.x) {
         const int r = r0 + i / N, c = i % N;
         if (r < hr || r >= M - hr) continue;
@@ -79,8 +81,15 @@ cfar_kernel(const float *__restrict__ P, int M, int N, int TR, DetectDev dd,
                 const double *vo = vout + j * N;
                 const double *vm = vmid + j * N;
                 double t = vo[c];
-                for (int k = 1; k <= hd; ++k) t += vo[(c - k) & nmask] + vo[(c + k) & nmask];
-                for (int k = gd + 1; k <= hd; ++k) t += vm[(c - k) & nmask] + vm[(c + k) & nmask];
+                // cyclic Doppler neighbours (hd < N/2)
+                for (int k = 1; k <= hd; ++k) {
+                    const int lo = c - k < 0 ? c - k + N : c - k, hi = c + k >= N ? c + k - N : c + k;
+                    t += vo[lo] + vo[hi];
+                }
+                for (int k = gd + 1; k <= hd; ++k) {
+                    const int lo = c - k < 0 ? c - k + N : c - k, hi = c + k >= N ? c + k - N : c + k;
+                    t += vm[lo] + vm[hi];
+                }
                 const double thr = dd.alpha * (t / (double)dd.n_train);
                 det = (double)P[(int64_t)r * N + c] > thr;
             }

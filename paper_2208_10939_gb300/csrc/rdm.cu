@@ -3,10 +3,11 @@
 // over the N chirps of every range bin (Doppler); |.|^2 summed over the O
 // channels; the Doppler axis shifted so that zero velocity is bin N/2.
 //
-// Radix-2 Stockham autosort FFTs in shared memory (no bit reversal): stage
-// with current length n and stride s = L/n maps
-//   y[q + s(2p)] = x[q + s p] + x[q + s(p + n/2)]
-//   y[q + s(2p+1)] = (x[q + s p] - x[q + s(p + n/2)]) * exp(-2 pi i p s / L)
+// Mixed-radix (2, 3) Stockham autosort FFTs in shared memory (no digit
+// reversal), lengths L = 2^a 3^b.  A stage with current length n, radix p
+// (2 while n is even, else 3), m = n/p and stride s = L/n maps, for
+// j < m, q < s and k' < p,
+//   y[q + s(p j + k')] = exp(-2 pi i j k' / n) sum_k x[q + s(j + k m)] exp(-2 pi i k k' / p)
 // Both passes are HBM-bound: each reads and writes the cube once.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -35,36 +36,68 @@ __device__ __forceinline__ T window_val(int i, int L, int kind)
     return (T)0.5 - (T)0.5 * cospi_t((T)(2 * i) / (T)(L - 1));
 }
 
+__host__ __device__ __forceinline__ bool is_pow2_len(int L) { return (L & (L - 1)) == 0; }
+
+// twiddle table length: exp(-2 pi i t / L) for t < L/2 (radix 2 only) or
+// t < L (a radix-3 stage reaches t = 2 j s < 2L/3)
+__host__ __device__ __forceinline__ int tw_len(int L) { return is_pow2_len(L) ? L / 2 : L; }
+
 // Stockham stages over `cols` interleaved transforms of length L stored as
-// buf[col * L + idx]; `tw` holds exp(-2 pi i j / L), j < L/2.
-template <typename C>
+// buf[col * L + idx]; `tw` holds exp(-2 pi i t / L), t < tw_len(L).
+template <typename C, typename T>
 __device__ C *stockham(C *x, C *y, const C *tw, int L, int cols)
 {
-    const int half_tot = (L >> 1) * cols;
-    for (int n = L, s = 1; n > 1; n >>= 1, s <<= 1) {
-        const int h = n >> 1;
-        for (int t = threadIdx.x; t < half_tot; t += blockDim.x) {
-            const int col = t / (L >> 1), b = t % (L >> 1);
-            const int p = b / s, q = b % s;
+    const T h3 = (T)0.86602540378443864676;    // sin(2 pi / 3)
+    for (int n = L, s = 1; n > 1;) {
+        const int p = (n & 1) ? 3 : 2;
+        const int m = n / p;
+        const int per_col = m * s;
+        for (int t = threadIdx.x; t < per_col * cols; t += blockDim.x) {
+            const int col = t / per_col, b = t % per_col;
+            const int j = b / s, q = b % s;
             const C *xc = x + col * L;
             C *yc = y + col * L;
-            const C a = xc[q + s * p], c = xc[q + s * (p + h)];
-            const C w = tw[p * s];
-            C sum, dif;
-            sum.x = a.x + c.x;
-            sum.y = a.y + c.y;
-            dif.x = a.x - c.x;
-            dif.y = a.y - c.y;
-            yc[q + s * (2 * p)] = sum;
-            C r;
-            r.x = dif.x * w.x - dif.y * w.y;
-            r.y = dif.x * w.y + dif.y * w.x;
-            yc[q + s * (2 * p + 1)] = r;
+            if (p == 2) {
+                const C a = xc[q + s * j], c = xc[q + s * (j + m)];
+                const C w = tw[j * s];
+                C sum, dif, r;
+                sum.x = a.x + c.x;
+                sum.y = a.y + c.y;
+                dif.x = a.x - c.x;
+                dif.y = a.y - c.y;
+                r.x = dif.x * w.x - dif.y * w.y;
+                r.y = dif.x * w.y + dif.y * w.x;
+                yc[q + s * (2 * j)] = sum;
+                yc[q + s * (2 * j + 1)] = r;
+            } else {
+                const C a0 = xc[q + s * j], a1 = xc[q + s * (j + m)], a2 = xc[q + s * (j + 2 * m)];
+                const T t1x = a1.x + a2.x, t1y = a1.y + a2.y;
+                const T t2x = a0.x - (T)0.5 * t1x, t2y = a0.y - (T)0.5 * t1y;
+                // -i sin(2 pi/3) (a1 - a2)
+                const T t3x = h3 * (a1.y - a2.y), t3y = -h3 * (a1.x - a2.x);
+                C y0, u1, u2, r1, r2;
+                y0.x = a0.x + t1x;
+                y0.y = a0.y + t1y;
+                u1.x = t2x + t3x;
+                u1.y = t2y + t3y;
+                u2.x = t2x - t3x;
+                u2.y = t2y - t3y;
+                const C w1 = tw[j * s], w2 = tw[2 * j * s];
+                r1.x = u1.x * w1.x - u1.y * w1.y;
+                r1.y = u1.x * w1.y + u1.y * w1.x;
+                r2.x = u2.x * w2.x - u2.y * w2.y;
+                r2.y = u2.x * w2.y + u2.y * w2.x;
+                yc[q + s * (3 * j)] = y0;
+                yc[q + s * (3 * j + 1)] = r1;
+                yc[q + s * (3 * j + 2)] = r2;
+            }
         }
         __syncthreads();
         C *tmp = x;
         x = y;
         y = tmp;
+        n = m;
+        s *= p;
     }
     return x;
 }
@@ -72,7 +105,7 @@ __device__ C *stockham(C *x, C *y, const C *tw, int L, int cols)
 template <typename T>
 __device__ void fill_twiddles(typename Cplx<T>::type *tw, int L)
 {
-    for (int j = threadIdx.x; j < (L >> 1); j += blockDim.x) {
+    for (int j = threadIdx.x; j < tw_len(L); j += blockDim.x) {
         T s, c;
         sincospi_t((T)(-2 * j) / (T)L, &s, &c);
         tw[j].x = c;
@@ -101,7 +134,7 @@ __global__ void range_fft_kernel(const typename Cplx<T>::type *__restrict__ adc,
         buf0[i] = v;
     }
     __syncthreads();
-    const C *res = stockham<C>(buf0, buf1, tw, M, 1);
+    const C *res = stockham<C, T>(buf0, buf1, tw, M, 1);
     C *out = X + row * M;
     for (int i = threadIdx.x; i < M; i += blockDim.x) out[i] = res[i];
 }
@@ -134,11 +167,12 @@ __global__ void doppler_kernel(const typename Cplx<T>::type *__restrict__ X, int
         buf0[c * N + n] = v;
     }
     __syncthreads();
-    const C *res = stockham<C>(buf0, buf1, tw, N, RB);
+    const C *res = stockham<C, T>(buf0, buf1, tw, N, RB);
     for (int i = threadIdx.x; i < RB * N; i += blockDim.x) {
         const int c = i / N, d = i % N;
         const C v = res[i];
-        const int64_t at = ((int64_t)o * M + r0 + c) * N + ((d + (N >> 1)) & (N - 1));
+        const int ds = d + (N >> 1);
+        const int64_t at = ((int64_t)o * M + r0 + c) * N + (ds >= N ? ds - N : ds);
         if (CUBE) cube_out[at] = v;
         else pw_out[at] = v.x * v.x + v.y * v.y;
     }
@@ -170,7 +204,14 @@ __global__ void rdm_cube_sum_kernel(const typename Cplx<T>::type *__restrict__ Y
     rdm[i] = (float)acc;
 }
 
-static int rdm_rb(int N) { return N >= 512 ? 1 : 512 / N; }
+// range bins per Doppler block: the largest power of two RB with RB N <= 512
+// that divides M
+static int rdm_rb(int N, int M)
+{
+    int rb = 1;
+    while (2 * rb * N <= 512 && M % (2 * rb) == 0) rb *= 2;
+    return rb;
+}
 
 // workspace: the range-FFT output (O N M complex) followed by the
 // per-channel Doppler power (O M N reals of the same precision)
@@ -185,7 +226,7 @@ static void range_fft(const void *adc, const RadarDev &rd, void *X, cudaStream_t
 {
     using C = typename Cplx<T>::type;
     const int M = rd.M;
-    const size_t sm1 = (size_t)(2 * M + M / 2) * sizeof(C);
+    const size_t sm1 = (size_t)(2 * M + tw_len(M)) * sizeof(C);
     const int t1 = M / 2 < 1024 ? (M / 2 < 32 ? 32 : M / 2) : 1024;
     cudaFuncSetAttribute(range_fft_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sm1);
@@ -198,9 +239,8 @@ static void doppler(const void *X, const RadarDev &rd, T *pw, void *cube, cudaSt
 {
     using C = typename Cplx<T>::type;
     const int M = rd.M, N = rd.N;
-    int RB = rdm_rb(N);
-    if (RB > M) RB = M;
-    const size_t sm2 = (size_t)(2 * RB * N + N / 2) * sizeof(C);
+    const int RB = rdm_rb(N, M);
+    const size_t sm2 = (size_t)(2 * RB * N + tw_len(N)) * sizeof(C);
     cudaFuncSetAttribute(doppler_kernel<T, CUBE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sm2);
     doppler_kernel<T, CUBE><<<dim3((unsigned int)(M / RB), (unsigned int)rd.O), 256, sm2, s>>>(

@@ -216,12 +216,12 @@ def test_beat_frequency_bin_config1_plate():
     assert rr == 100 and dd == r.N // 2          # static: zero Doppler
 
 
-@pytest.mark.parametrize("M,expect_aliased", [(256, False), (512, True)])
+@pytest.mark.parametrize("M,expect_aliased", [(256, False), (384, False), (512, True)])
 def test_doppler_bin_and_table2_aliasing(M, expect_aliased):
     """Eq. 5 / Table 2: the target at 40 m approaching at 10 m/s.  With 256
-    samples (v_max 16.16 m/s) the Doppler peak sits at -2 v T_c N / lambda_c
-    bins; with 512 samples (v_max 8.78 m/s) it wraps to the receding side
-    ("abnormal" RDM)."""
+    or 384 samples (v_max 16.16 / 11.38 m/s) the Doppler peak sits at
+    -2 v T_c N / lambda_c bins; with 512 samples (v_max 8.78 m/s) it wraps to
+    the receding side ("abnormal" RDM)."""
     N = 32
     sc = sg.point_target_scene(40.0, -10.0, M=M, N=N, slope=12.5e12, fs=5.12e6,
                                edge=0.6e-3)
