@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-scenes", type=int, default=32,
+                    help="dataset scenes (seeded, 1-8 vehicles, 5k-200k facets) for the "
+                         "batched-vs-per-scene measurement; 0 skips it")
+    ap.add_argument("--batch-size", type=int, default=8)
     return ap.parse_args()
 
 
@@ -186,6 +190,106 @@ def run_reference(args):
                             "kind": "oracle", "sample": sample},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+def dataset_batch(pkg, sg, torch, dev, K: int, bsz: int) -> dict:
+    """Dataset generation (seeded scenes of 1-8 vehicles, 5k-200k facets,
+    radar as the sedan workload): scene-frames per second simulated one
+    scene per frame call versus bsz scenes per call (bart_scene_partition),
+    each including the instance-table upload, synthesis and RDM, meshes
+    resident; then the autotuned layout, and a 4-frame time sequence of one
+    batch replayed as a CUDA graph versus direct launches."""
+    scenes = [sg.batch_scene(i) for i in range(K)]
+    sim = pkg.Simulator(dev.index or 0)
+    pkg.bart_mesh_clear(sim.ctx)
+    placed = []
+    for sc in scenes:
+        ids = [pkg.bart_mesh_upload(sim.ctx, m.verts, m.tris, m.rho) for m in sc.meshes]
+        placed.append([pkg._Placed(ids[i.mesh_id], i) for i in sc.instances])
+    radar = scenes[0].radar
+    pkg.bart_radar_set(sim.ctx, radar)
+    sim.radar = radar
+    O, N, M = radar.O, radar.N, radar.M
+    facets = [sum(s.meshes[i.mesh_id].nf for i in s.instances) for s in scenes]
+    stream = torch.cuda.current_stream(dev)
+
+    def run(groups, out_pool):
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for g in groups:
+            insts = [x for b in g for x in placed[b]]
+            pkg.bart_scene_set(sim.ctx, insts)
+            if len(g) > 1:
+                first = np.cumsum([0] + [len(placed[b]) for b in g])
+                pkg.bart_scene_partition(sim.ctx, first)
+            adc, rdm = out_pool[len(g)]
+            pkg.bart_simulate_frame(sim.ctx, 0.0, pkg.PATH_MIXED, adc)
+            pkg.bart_form_rdm(sim.ctx, adc, rdm)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return time.perf_counter() - t, e0.elapsed_time(e1) / 1e3
+
+    pool = {}
+    for b in {1, bsz}:
+        pool[b] = (torch.empty((b, O, N, M), dtype=torch.complex64, device=dev),
+                   torch.empty((b, M, N), dtype=torch.float32, device=dev))
+    single = [[i] for i in range(K)]
+    batched = [list(range(i, min(K, i + bsz))) for i in range(0, K, bsz)]
+    if K % bsz:
+        pool[K % bsz] = (torch.empty((K % bsz, O, N, M), dtype=torch.complex64, device=dev),
+                         torch.empty((K % bsz, M, N), dtype=torch.float32, device=dev))
+    run(single, pool)
+    wall1, dev1 = run(single, pool)
+    run(batched, pool)
+    wallB, devB = run(batched, pool)
+
+    # autotuned synthesis layout on the first batch, kept for all batches
+    g0 = batched[0]
+    pkg.bart_scene_set(sim.ctx, [x for b in g0 for x in placed[b]])
+    pkg.bart_scene_partition(sim.ctx, np.cumsum([0] + [len(placed[b]) for b in g0]))
+    tune = pkg.bart_autotune(sim.ctx, 0.0, pool[len(g0)][0], reps=1)
+    run(batched, pool)
+    wallT, devT = run(batched, pool)
+
+    # a time sequence of one batch: direct launches vs a replayed frame graph
+    pkg.bart_scene_set(sim.ctx, [x for b in g0 for x in placed[b]])
+    pkg.bart_scene_partition(sim.ctx, np.cumsum([0] + [len(placed[b]) for b in g0]))
+    adc, rdm = pool[len(g0)]
+    frame_T = N * radar.Tc
+    seq = [k * frame_T for k in range(4)]
+
+    def sequence():
+        torch.cuda.synchronize(dev)
+        t = time.perf_counter()
+        for t0 in seq:
+            pkg.bart_simulate_frame(sim.ctx, t0, pkg.PATH_MIXED, adc)
+            pkg.bart_form_rdm(sim.ctx, adc, rdm)
+        torch.cuda.synchronize(dev)
+        return time.perf_counter() - t
+
+    sequence()
+    direct_s = sequence()
+    pkg.bart_set_graph(sim.ctx, True)
+    sequence()
+    graph_s = sequence()
+    pkg.bart_set_graph(sim.ctx, False)
+    sim.close()
+    return {
+        "workload": f"{K} seeded dataset scenes (1-8 vehicles, 5k-200k facets, "
+                    f"mean {int(np.mean(facets))}), radar as the sedan workload, mixed path + RDM",
+        "unit": "scene-frames/s",
+        "per_scene": {"value": K / wall1, "device_s": dev1, "wall_s": wall1},
+        "batched": {"value": K / wallB, "device_s": devB, "wall_s": wallB, "batch_size": bsz},
+        "batched_autotuned": {"value": K / wallT, "device_s": devT, "wall_s": wallT,
+                              "layout": {"samples_per_lane": tune["best"][0],
+                                         "tiles_per_item": tune["best"][1]},
+                              "trials": tune["trials"]},
+        "sequence_4_frames": {"direct": len(g0) * len(seq) / direct_s,
+                              "graph": len(g0) * len(seq) / graph_s},
+    }
 
 
 def main():
@@ -327,6 +431,9 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(scene, args.cpu_seconds)
+    batch = None
+    if world == 1 and args.batch_scenes > 0:
+        batch = dataset_batch(pkg, sg, torch, dev, args.batch_scenes, args.batch_size)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -352,6 +459,7 @@ def main():
         "e2e": e2e,
         "gpu_launches": launches,
         "cpu_baseline": cpu,
+        "dataset_batch": batch,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -156,6 +156,13 @@ int bart_mesh_upload(bart_ctx *ctx, const double *verts, int64_t nv,
                      const int32_t *tris, int64_t nf, const float *rho,
                      int32_t *mesh_id);
 
+/* Replace the vertices (and, if rho is not NULL, the reflectivities) of an
+ * uploaded mesh from DEVICE arrays of the uploaded sizes (nv x 3 float64,
+ * nf float32), asynchronously on the context's stream.  Topology is kept,
+ * so a recorded frame graph stays valid and picks the new values up (the
+ * gradient-descent loop of the differentiable echo).  Errors: EINVAL, ECUDA. */
+int bart_mesh_update(bart_ctx *ctx, int32_t mesh_id, const double *verts, const float *rho);
+
 /* Remove every uploaded mesh and the scene. */
 int bart_mesh_clear(bart_ctx *ctx);
 
@@ -165,6 +172,22 @@ int bart_scene_set(bart_ctx *ctx, const bart_instance *inst, int32_t n);
 
 /* Total facet count of the current scene (host out). */
 int bart_scene_facets(bart_ctx *ctx, int64_t *n_facets);
+
+/* Split the instance table of the last bart_scene_set into independent
+ * scenes simulated in one pass (dataset generation: many small scenes per
+ * launch).  Instances [first[b], first[b+1]) form scene b, with
+ * 0 = first[0] < first[1] < ... < first[n_scenes] = number of instances
+ * (host array of n_scenes + 1 int32).  Each scene is simulated as if alone
+ * -- its facets are lit, shadowed and summed among its own facets only --
+ * and owns one slab of the batched outputs: bart_simulate_frame then writes
+ * n_scenes x O x N x M samples ([scene][channel][chirp][sample]), and
+ * bart_form_rdm / bart_frame_host read that many and write n_scenes x M x N.
+ * Work of all scenes shares each launch: one hierarchy with a subtree per
+ * scene, one visibility launch, one synthesis work queue over (scene,
+ * channel, chirp group, record chunk) items.  bart_scene_set resets the
+ * partition to one scene.  n_scenes x O must not exceed 65535.
+ * Errors: EINVAL (bad offsets), ESTATE (no instances). */
+int bart_scene_partition(bart_ctx *ctx, const int32_t *first, int32_t n_scenes);
 
 /* Set the radar (host struct, copied and validated).  Errors: EINVAL. */
 int bart_radar_set(bart_ctx *ctx, const bart_radar *radar);
@@ -194,6 +217,66 @@ int bart_simulate_frame(bart_ctx *ctx, double t0, int32_t path, void *adc,
 int bart_add_noise(bart_ctx *ctx, void *adc, int32_t dtype, double snr_db, uint64_t seed,
                    uint32_t frame);
 
+/* Adjoint of the plain FP64 echo synthesis (the differentiable echo).  For
+ * a real loss L of the ADC cube of the frame at t0, given
+ * grad_adc = dL/dRe(adc) + i dL/dIm(adc) (device, the layout
+ * bart_simulate_frame writes, dtype C128 or C64), writes
+ *   grad_verts: dL/d(mesh-local vertex coordinates), device FP64,
+ *       instance-major: instance i's mesh vertices (x, y, z each) start at
+ *       3 * (sum of the vertex counts of the meshes of instances 0..i-1);
+ *       sum over the instances that share a mesh for that mesh's gradient;
+ *   grad_rho: dL/d(mesh reflectivity of each facet), device FP64, one per
+ *       scene facet (instance-major), or NULL.
+ * The derivative is the exact one of the FP64 synthesis as implemented
+ * (every facet-integral form), through the facet integral, the obliquity,
+ * the distances and the delay; visibility is recomputed at t0 and held
+ * fixed (it is piecewise constant in the vertices).  Instance poses,
+ * velocities and rho_scale are constants.  Works with scene partitions.
+ * Errors: ESTATE, EINVAL, ENOMEM, ECUDA. */
+int bart_simulate_adjoint(bart_ctx *ctx, double t0, const void *grad_adc, int32_t dtype,
+                          double *grad_verts, double *grad_rho);
+
+/* Frame graphs.  With enable = 1, bart_simulate_frame records its kernel
+ * launches (world facets, hierarchy, visibility, lit lists, kinematics,
+ * synthesis: some 25-40 launches on two streams) into a CUDA graph the
+ * first time it meets a configuration -- meshes, instances, partition,
+ * radar, synthesis layout, path, dtype, output pointer and stream -- and
+ * replays that graph, one launch, on later calls that differ at most in
+ * t0 (the new t0 is written into the recorded world-facet launch).  Any
+ * change of the configuration records again.  Calls that request stats,
+ * or run with timing enabled, run directly.  enable = 0 (the default)
+ * drops the graph.  Errors: EINVAL, ECUDA. */
+int bart_set_graph(bart_ctx *ctx, int32_t enable);
+
+/* Work layout of the mixed-path synthesis kernel: samples_per_lane 16 (or
+ * 0, the default) or 8 (where M allows: M divides 256 or 256 divides M);
+ * tiles_per_item = 32-record tiles per work item (0 = default, scaled with
+ * the largest scene).  The results differ only by FP32 summation order.
+ * Errors: EINVAL. */
+int bart_set_synth_layout(bart_ctx *ctx, int32_t samples_per_lane, int32_t tiles_per_item);
+
+#define BART_TUNE_MAX 16
+/* Autotuner result: every trial's layout and best synthesis time. */
+typedef struct bart_tune {
+    int32_t n_trials;
+    int32_t best_samples_per_lane;
+    int32_t best_tiles_per_item;
+    float   best_ms;
+    int32_t samples_per_lane[BART_TUNE_MAX];
+    int32_t tiles_per_item[BART_TUNE_MAX];
+    float   synthesis_ms[BART_TUNE_MAX];
+} bart_tune;
+
+/* Time the mixed-path synthesis of the current scene at t0 for each
+ * candidate layout (samples per lane 16 and, where M allows, 8; tiles per
+ * item 8 ... 512), each run once to warm up and then `reps` times (best
+ * time kept, CUDA events around the synthesis launches), and keep the
+ * fastest layout for later frames (as bart_set_synth_layout).  adc: device
+ * output of the shape bart_simulate_frame writes (overwritten).  Blocks
+ * until done.  Errors: EINVAL, ESTATE, ENOMEM, ECUDA. */
+int bart_autotune(bart_ctx *ctx, double t0, void *adc, int32_t dtype, int32_t reps,
+                  bart_tune *out);
+
 /* Range-Doppler map (Sec. 3.3) of an ADC cube of the current radar shape:
  * window + forward FFT over fast time, window + forward FFT over chirps,
  * |.|^2 summed over the O channels, zero Doppler shifted to bin N/2.
@@ -202,6 +285,16 @@ int bart_add_noise(bart_ctx *ctx, void *adc, int32_t dtype, double snr_db, uint6
  * Errors: ESTATE, EINVAL (M or N not of the form 2^a 3^b, N > 1024),
  * ENOMEM, ECUDA. */
 int bart_form_rdm(bart_ctx *ctx, const void *adc, int32_t dtype, float *rdm);
+
+/* Adjoint of bart_form_rdm (the RDM step of the differentiable echo): for a
+ * real loss L with dL/dRDM = grad_rdm (device, M x N float32 per scene, the
+ * RDM layout), writes grad_adc = dL/dRe(adc) + i dL/dIm(adc) (device, the
+ * layout and dtype of adc): 2 grad_rdm Y on the range-Doppler cube Y of adc,
+ * then the conjugate transposes of the windowed Doppler and range DFTs.
+ * adc is the cube the RDM was formed from (the RDM is nonlinear in it).
+ * Errors: ESTATE, EINVAL, ENOMEM, ECUDA. */
+int bart_rdm_adjoint(bart_ctx *ctx, const void *adc, int32_t dtype, const float *grad_rdm,
+                     void *grad_adc);
 
 /* bart_form_rdm without any device allocation, for callers that cannot let
  * a library allocate GPU memory: applications that own all device memory

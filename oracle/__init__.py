@@ -261,6 +261,20 @@ def range_doppler_map(adc: np.ndarray) -> np.ndarray:
     return np.ascontiguousarray(P.T)                 # [M][N]
 
 
+def rdm_adjoint(adc: np.ndarray, grad_rdm: np.ndarray) -> np.ndarray:
+    """Gradient of a real loss L(RDM) with respect to the ADC cube, as
+    dL/dRe(x) + i dL/dIm(x), given dL/dRDM = grad_rdm [M][N] (Doppler
+    shifted): with Y the windowed range-Doppler cube, Ybar = 2 G Y, then the
+    conjugate transposes of the Doppler and range DFT steps (window times the
+    unnormalised inverse DFT)."""
+    O, N, M = adc.shape
+    Y = range_doppler_cube(adc)                                    # [O][N(d)][M(r)]
+    G = np.fft.ifftshift(np.asarray(grad_rdm, np.float64).T, axes=0)   # [d][r]
+    Ybar = 2.0 * G[None] * Y
+    Xbar = hann(N)[None, :, None] * (N * np.fft.ifft(Ybar, axis=1))
+    return hann(M)[None, None, :] * (M * np.fft.ifft(Xbar, axis=2))
+
+
 # ---------------------------------------------------------------------------
 # detection, angle and point cloud (Sec. 3.3, Eqs. 4-6)
 # ---------------------------------------------------------------------------

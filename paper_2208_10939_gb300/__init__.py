@@ -33,7 +33,10 @@ EXPORTED = ["bart_last_error", "bart_version", "bart_create", "bart_destroy",
             "bart_set_stream", "bart_mesh_upload", "bart_mesh_clear", "bart_scene_set",
             "bart_scene_facets", "bart_radar_set", "bart_simulate_frame", "bart_form_rdm",
             "bart_frame_host", "bart_get_visibility", "bart_set_timing", "bart_get_timing",
-            "bart_sync", "bart_form_rdm_static", "bart_add_noise", "bart_detect"]
+            "bart_sync", "bart_form_rdm_static", "bart_add_noise", "bart_detect",
+            "bart_scene_partition", "bart_set_graph", "bart_set_synth_layout",
+            "bart_autotune", "bart_rdm_adjoint", "bart_simulate_adjoint",
+            "bart_mesh_update"]
 
 
 class BartError(RuntimeError):
@@ -98,6 +101,24 @@ POINT_DTYPE = np.dtype([("range", "<f8"), ("rate", "<f8"), ("azimuth", "<f8"), (
                         ("y", "<f8"), ("power", "<f8"), ("r_bin", "<i4"), ("d_bin", "<i4")])
 assert POINT_DTYPE.itemsize == ctypes.sizeof(bart_point) == 56
 
+TUNE_MAX = 16
+
+
+class bart_tune(ctypes.Structure):
+    _fields_ = [("n_trials", ctypes.c_int32), ("best_samples_per_lane", ctypes.c_int32),
+                ("best_tiles_per_item", ctypes.c_int32), ("best_ms", ctypes.c_float),
+                ("samples_per_lane", ctypes.c_int32 * TUNE_MAX),
+                ("tiles_per_item", ctypes.c_int32 * TUNE_MAX),
+                ("synthesis_ms", ctypes.c_float * TUNE_MAX)]
+
+    def as_dict(self) -> dict:
+        n = int(self.n_trials)
+        return {"best": (int(self.best_samples_per_lane), int(self.best_tiles_per_item),
+                         float(self.best_ms)),
+                "trials": [(int(self.samples_per_lane[i]), int(self.tiles_per_item[i]),
+                            float(self.synthesis_ms[i])) for i in range(n)]}
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -138,6 +159,13 @@ def load_library() -> ctypes.CDLL:
         L.bart_sync.argtypes = [P]
         L.bart_form_rdm_static.argtypes = [P, I32, I32, I32, I32, I32, P, P]
         L.bart_add_noise.argtypes = [P, P, I32, D, ctypes.c_uint64, ctypes.c_uint32]
+        L.bart_scene_partition.argtypes = [P, P, I32]
+        L.bart_set_graph.argtypes = [P, I32]
+        L.bart_rdm_adjoint.argtypes = [P, P, I32, P, P]
+        L.bart_simulate_adjoint.argtypes = [P, D, P, I32, P, P]
+        L.bart_mesh_update.argtypes = [P, I32, P, P]
+        L.bart_set_synth_layout.argtypes = [P, I32, I32]
+        L.bart_autotune.argtypes = [P, D, P, I32, I32, ctypes.POINTER(bart_tune)]
         L.bart_detect.argtypes = [P, P, I32, ctypes.POINTER(bart_detect_cfg), P, P, I32,
                                   ctypes.POINTER(I32)]
         for name in EXPORTED:
@@ -193,6 +221,18 @@ def bart_mesh_upload(ctx: int, verts: np.ndarray, tris: np.ndarray,
     return mid.value
 
 
+def bart_mesh_update(ctx: int, mesh_id: int, verts, rho=None) -> None:
+    """Replace an uploaded mesh's vertices (CUDA float64 nv x 3) and
+    optionally reflectivities (CUDA float32 nf) in place, asynchronously."""
+    import torch
+    if not verts.is_cuda or not verts.is_contiguous() or verts.dtype != torch.float64:
+        raise ValueError("verts must be a contiguous CUDA float64 tensor")
+    if rho is not None and (not rho.is_cuda or not rho.is_contiguous() or rho.dtype != torch.float32):
+        raise ValueError("rho must be a contiguous CUDA float32 tensor")
+    _check(load_library().bart_mesh_update(ctx, int(mesh_id), ctypes.c_void_p(_ptr(verts)),
+                                           None if rho is None else ctypes.c_void_p(_ptr(rho))))
+
+
 def bart_mesh_clear(ctx: int) -> None:
     _check(load_library().bart_mesh_clear(ctx))
 
@@ -214,6 +254,13 @@ def make_instances(instances) -> ctypes.Array:
 def bart_scene_set(ctx: int, instances) -> None:
     arr = make_instances(instances)
     _check(load_library().bart_scene_set(ctx, ctypes.cast(arr, ctypes.c_void_p), len(instances)))
+
+
+def bart_scene_partition(ctx: int, first) -> None:
+    """Split the current instances into independent scenes: instances
+    [first[b], first[b+1]) form scene b (len(first) = n_scenes + 1)."""
+    f = np.ascontiguousarray(first, np.int32)
+    _check(load_library().bart_scene_partition(ctx, f.ctypes.data, int(f.size) - 1))
 
 
 def bart_scene_facets(ctx: int) -> int:
@@ -347,6 +394,53 @@ def bart_get_visibility(ctx: int, state) -> None:
     _check(load_library().bart_get_visibility(ctx, ctypes.c_void_p(_ptr(state))))
 
 
+def bart_rdm_adjoint(ctx: int, adc, grad_rdm, grad_adc) -> None:
+    """grad_adc = dL/dRe(adc) + i dL/dIm(adc) for dL/dRDM = grad_rdm."""
+    import torch
+    for t in (adc, grad_rdm, grad_adc):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("adc, grad_rdm and grad_adc must be contiguous CUDA tensors")
+    if grad_rdm.dtype != torch.float32 or grad_adc.dtype != adc.dtype:
+        raise TypeError("grad_rdm must be float32 and grad_adc of adc's dtype")
+    _check(load_library().bart_rdm_adjoint(ctx, ctypes.c_void_p(_ptr(adc)), _dtype_code(adc),
+                                           ctypes.c_void_p(_ptr(grad_rdm)),
+                                           ctypes.c_void_p(_ptr(grad_adc))))
+
+
+def bart_simulate_adjoint(ctx: int, t0: float, grad_adc, grad_verts, grad_rho=None) -> None:
+    """Mesh-vertex (instance-major, mesh-local) and per-facet reflectivity
+    gradients of a real loss with dL/dRe(adc) + i dL/dIm(adc) = grad_adc."""
+    import torch
+    if not grad_adc.is_cuda or not grad_adc.is_contiguous():
+        raise ValueError("grad_adc must be a contiguous CUDA tensor")
+    for t in (grad_verts, grad_rho):
+        if t is not None and (not t.is_cuda or not t.is_contiguous() or t.dtype != torch.float64):
+            raise ValueError("gradient outputs must be contiguous CUDA float64 tensors")
+    _check(load_library().bart_simulate_adjoint(
+        ctx, float(t0), ctypes.c_void_p(_ptr(grad_adc)), _dtype_code(grad_adc),
+        ctypes.c_void_p(_ptr(grad_verts)),
+        None if grad_rho is None else ctypes.c_void_p(_ptr(grad_rho))))
+
+
+def bart_set_graph(ctx: int, enable: bool) -> None:
+    _check(load_library().bart_set_graph(ctx, int(bool(enable))))
+
+
+def bart_set_synth_layout(ctx: int, samples_per_lane: int = 0, tiles_per_item: int = 0) -> None:
+    _check(load_library().bart_set_synth_layout(ctx, int(samples_per_lane), int(tiles_per_item)))
+
+
+def bart_autotune(ctx: int, t0: float, adc, reps: int = 3) -> dict:
+    """Try the mixed-path synthesis layouts on the current scene, keep the
+    fastest; returns the trial table (samples/lane, tiles/item, ms)."""
+    if not adc.is_cuda or not adc.is_contiguous():
+        raise ValueError("adc must be a contiguous CUDA tensor")
+    t = bart_tune()
+    _check(load_library().bart_autotune(ctx, float(t0), ctypes.c_void_p(_ptr(adc)),
+                                        _dtype_code(adc), int(reps), ctypes.byref(t)))
+    return t.as_dict()
+
+
 def bart_set_timing(ctx: int, enable: bool) -> None:
     _check(load_library().bart_set_timing(ctx, int(bool(enable))))
 
@@ -364,6 +458,14 @@ def bart_sync(ctx: int) -> None:
 # ---------------------------------------------------------------------------
 # convenience wrapper
 # ---------------------------------------------------------------------------
+class _Placed:
+    """An instance re-pointed at a mesh id of the batch's mesh pool."""
+
+    def __init__(self, mesh_id: int, ins):
+        self.mesh_id = mesh_id
+        self.pos, self.rot, self.vel = ins.pos, ins.rot, ins.vel
+        self.rho_scale = getattr(ins, "rho_scale", 1.0)
+
 class Simulator:
     """One library context bound to a CUDA device and torch's current stream."""
 
@@ -394,13 +496,33 @@ class Simulator:
             bart_mesh_upload(self.ctx, m.verts, m.tris, m.rho)
         bart_scene_set(self.ctx, scene.instances)
         bart_radar_set(self.ctx, scene.radar, window)
+        self.n_scenes = 1
         self.radar = scene.radar
         self.t0 = float(getattr(scene, "t0", 0.0))
         self.n_facets = bart_scene_facets(self.ctx)
 
+    def load_scenes(self, scenes, window: int = WINDOW_HANN) -> None:
+        """Upload several scenes sharing one radar profile as one batch
+        (bart_scene_partition): outputs gain a leading scene axis."""
+        bart_mesh_clear(self.ctx)
+        insts, first = [], [0]
+        for sc in scenes:
+            ids = [bart_mesh_upload(self.ctx, m.verts, m.tris, m.rho) for m in sc.meshes]
+            for ins in sc.instances:
+                insts.append(_Placed(ids[ins.mesh_id], ins))
+            first.append(len(insts))
+        bart_scene_set(self.ctx, insts)
+        bart_scene_partition(self.ctx, first)
+        self.radar = scenes[0].radar
+        bart_radar_set(self.ctx, self.radar, window)
+        self.t0 = float(getattr(scenes[0], "t0", 0.0))
+        self.n_facets = bart_scene_facets(self.ctx)
+        self.n_scenes = len(scenes)
+
     def adc_shape(self):
         r = self.radar
-        return (int(r.tx.shape[0]) * int(r.rx.shape[0]), int(r.N), int(r.M))
+        shape = (int(r.tx.shape[0]) * int(r.rx.shape[0]), int(r.N), int(r.M))
+        return shape if getattr(self, "n_scenes", 1) == 1 else (self.n_scenes,) + shape
 
     def simulate(self, path: int = PATH_MIXED, dtype=None, t0: Optional[float] = None,
                  out=None, stats: bool = False):
@@ -415,8 +537,10 @@ class Simulator:
     def rdm(self, adc, out=None):
         import torch
         if out is None:
-            out = torch.empty((int(self.radar.M), int(self.radar.N)), dtype=torch.float32,
-                              device=adc.device)
+            shape = (int(self.radar.M), int(self.radar.N))
+            if getattr(self, "n_scenes", 1) > 1:
+                shape = (self.n_scenes,) + shape
+            out = torch.empty(shape, dtype=torch.float32, device=adc.device)
         bart_form_rdm(self.ctx, adc, out)
         return out
 

@@ -17,7 +17,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libbartsim.so")
-SOURCES = ["capi.cu", "scene_bvh.cu", "visibility.cu", "synth.cu", "rdm.cu", "noise.cu", "detect.cu"]
+SOURCES = ["capi.cu", "scene_bvh.cu", "visibility.cu", "synth.cu", "rdm.cu", "noise.cu", "detect.cu",
+           "adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -37,7 +38,8 @@ def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
     t = os.path.getmtime(obj)
-    deps = [src, os.path.join(CSRC, "bart_internal.cuh"), os.path.join(INCLUDE, "bartsim.h")]
+    deps = [src, os.path.join(CSRC, "bart_internal.cuh"), os.path.join(CSRC, "record_fp64.cuh"),
+            os.path.join(INCLUDE, "bartsim.h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

@@ -86,6 +86,8 @@ constexpr int kStatusStackOverflow = 1;
 // ---- scene + BVH (scene_bvh.cu) ----
 // tri32: per facet 12 floats -- the world vertices rounded to FP32 and the
 // largest |coordinate| among them (for the visibility FP32 pre-test)
+// the world-facet kernel (its t0 argument is updated in replayed frame graphs)
+const void *build_facets_kernel_fn(int *t0_arg_index, int *n_args);
 void launch_build_facets(const MeshDesc *meshes, const InstDev *insts, int n_inst,
                          int64_t F, double t0, double *tri64, float *tri32, double *c64,
                          FacetRec *fac, float *aabb, float *vel32, unsigned int *bounds,
@@ -100,20 +102,43 @@ void radix_sort_pairs(uint32_t *keys, int32_t *vals, uint32_t *keys_tmp, int32_t
 void launch_lbvh_build(const uint32_t *keys, const int32_t *vals, int64_t n,
                        BvhNode *nodes, int32_t *parent, int32_t *leaf_parent,
                        cudaStream_t s);
+// Batched scenes (facets [foff[b], foff[b+1]) form scene b, foff on the
+// device): Morton codes, a sort by (scene, code), and one hierarchy whose
+// scene subtrees are disjoint; root[b] receives scene b's root node (~facet
+// for a one-facet scene).  mkeys, skeys: F words of scratch.
+void launch_lbvh_batched(const FacetRec *fac, int64_t F, const unsigned int *bounds,
+                         const int64_t *foff, int B, uint32_t *keys, int32_t *vals,
+                         uint32_t *keys_tmp, int32_t *vals_tmp, uint32_t *temp, uint32_t *mkeys,
+                         uint32_t *skeys, BvhNode *nodes, int32_t *parent, int32_t *leaf_parent,
+                         int32_t *root, cudaStream_t s);
+int lbvh_batched_launches(int B);
 void launch_lbvh_refit(const int32_t *vals, const float *aabb, int64_t n, BvhNode *nodes,
                        const int32_t *parent, const int32_t *leaf_parent, int32_t *flags,
                        cudaStream_t s);
 
 // ---- visibility (visibility.cu) ----
-// order: facet ids in the sequence the ray threads take them (Morton order), or NULL
+// order: facet ids in the sequence the ray threads take them (Morton order), or NULL.
+// Batched scenes: foff (B + 1 facet offsets) and root (B scene roots) on the
+// device, B > 1; a ray then only meets facets of its own scene.
+struct SceneSplit {
+    int B = 1;
+    const int64_t *foff = nullptr;
+    const int32_t *root = nullptr;
+};
 void launch_visibility(const double *tri64, const float *tri32, const double *c64,
                        const BvhNode *nodes, const int32_t *order, int64_t F, const RadarDev &rd,
-                       uint8_t *state, unsigned long long *n_graze, int *status, cudaStream_t s);
+                       const SceneSplit &sc, uint8_t *state, unsigned long long *n_graze,
+                       int *status, cudaStream_t s);
 // lists 0..O-1: facets lit from both antennas of each channel; O..O+A-1: facets
 // lit from each antenna.  vis_idx is [O+A][F], vis_cnt [O+A].
 void launch_compact(const uint8_t *state, int64_t F, const RadarDev &rd,
                     int32_t *blk_cnt, int32_t *vis_idx, int32_t *vis_cnt, cudaStream_t s);
 int64_t compact_blk_words(int64_t F, int L);
+// per (scene, channel) sub-ranges of the channel lists: vstart[b O + o] is
+// the first entry of list o with facet >= foff[b], vcnt its length
+void launch_scene_lists(const int32_t *vis_idx, const int32_t *vis_cnt, int64_t F, int O,
+                        const int64_t *foff, int B, int32_t *vstart, int32_t *vcnt,
+                        cudaStream_t s);
 
 // ---- synthesis (synth.cu) ----
 struct SynthArgs {
@@ -123,7 +148,12 @@ struct SynthArgs {
     const double *vel64;     // per instance, 3 doubles
     const float *vel32;      // per instance, 4 floats (xyz, pad)
     const int32_t *vis_idx;  // [O][F]
-    const int32_t *vis_cnt;  // [O]
+    const int32_t *vis_cnt;  // [O + A]
+    // virtual channels: VO = scenes x O rows of the output; row v reads
+    // vcnt[v] entries of list v % O from entry vstart[v] (vstart NULL: 0)
+    int VO;
+    const int32_t *vstart;
+    const int32_t *vcnt;
     int64_t F;
     const float4 *kin;       // [nc][A][F] (mixed path)
     int n0, nc;              // chirp chunk
@@ -134,7 +164,9 @@ struct SynthArgs {
     int32_t *item_off;       // [O + 1] first work item of each channel
     int *item_counter;       // next item to hand out
     float2 *partial;         // [items][32 S] unscaled partial sums
-    int tiles_per_item;      // 32-record tiles per item
+    int tiles_per_item;      // 32-record tiles per item (set by the caller)
+    int64_t max_items;       // upper bound of the work items (grid sizing)
+    int layout_S;            // mixed-kernel samples per lane request (0 default, 8)
     RadarDev rd;
 };
 void launch_kinematics(const double *c64, const FacetRec *fac, const double *vel64,
@@ -142,8 +174,26 @@ void launch_kinematics(const double *c64, const FacetRec *fac, const double *vel
                        const RadarDev &rd, int n0, int nc, float4 *kin, cudaStream_t s);
 void launch_synth_mixed(const SynthArgs &a, cudaStream_t s);
 // scratch of the mixed path for F facets and a chunk of nc chirps
-int64_t synth_partial_words(int64_t F, const RadarDev &rd, int nc);   // float2 words
+// scene_F: facets of each scene (n_scene entries); tpi: 32-record tiles per
+// work item (0: the default for the largest scene)
+int64_t synth_partial_words(const int64_t *scene_F, int n_scene, const RadarDev &rd, int nc,
+                            int tpi, int S_req);   // float2 words
+int64_t synth_max_items(const int64_t *scene_F, int n_scene, const RadarDev &rd, int nc, int tpi,
+                        int S_req);
+// samples per lane the mixed kernel uses for M and a layout request
+int synth_layout_samples(int M, int S_req);
+int synth_tiles_per_item(int64_t F);
 void launch_synth_fp64(const SynthArgs &a, cudaStream_t s);
+
+// ---- adjoint of the FP64 synthesis (adjoint.cu) ----
+// gfac: F x 10 (world vertex coordinates at t0, reflectivity) per facet
+void launch_adjoint_fp64(const SynthArgs &a, const void *grad, int grad_c64, double *gfac,
+                         cudaStream_t s);
+// facet gradients -> instance-major mesh-local vertex gradients (voff: first
+// vertex of each instance) and per-facet reflectivity gradients (may be NULL)
+void launch_adjoint_scatter(const double *gfac, const FacetRec *fac, const InstDev *insts,
+                            const MeshDesc *meshes, const int64_t *voff, int64_t F, double *gverts,
+                            int64_t n_vert_words, double *grho, cudaStream_t s);
 
 // ---- additive noise (noise.cu) ----
 int64_t noise_scratch_words();   // doubles
@@ -152,13 +202,21 @@ void launch_add_noise(void *adc, int dtype, int64_t n, double snr_db, uint64_t s
 
 // ---- range-Doppler map (rdm.cu) ----
 int64_t rdm_workspace_bytes(const RadarDev &rd, int dtype);
-void launch_rdm(const void *adc, int dtype, const RadarDev &rd, void *ws, float *rdm,
+// groups: independent cubes of rd.O channels each, back to back (batched
+// scenes); rdm receives groups x M x N; ws holds groups x rdm_workspace_bytes
+void launch_rdm(const void *adc, int dtype, const RadarDev &rd, int groups, void *ws, float *rdm,
                 cudaStream_t s);
 
 // RDM that also keeps the complex range-Doppler cube Y[o][r][d'] (Doppler
 // shifted) in `cube`; X is an O*N*M complex scratch of the same precision.
 void launch_rdm_cube(const void *adc, int dtype, const RadarDev &rd, void *X, void *cube,
                      float *rdm, cudaStream_t s);
+
+// Adjoint of the RDM for dL/dRDM = grad_rdm (groups x M x N float32):
+// grad_adc (same layout and precision as adc) = d L / d Re(adc) + i d L / d Im(adc).
+// X and cube: groups x O x N x M complex scratch each.
+void launch_rdm_adjoint(const void *adc, int dtype, const float *grad_rdm, const RadarDev &rd,
+                        int groups, void *X, void *cube, void *grad_adc, cudaStream_t s);
 
 // ---- detection: CA-CFAR, angle spectrum, points (detect.cu) ----
 struct DetectDev {

@@ -113,6 +113,46 @@ struct bart_ctx {
     DevBuf<double> noise_scratch;
     DevBuf<float> rdm_own;
     DevBuf<unsigned char> det_ws;       // detection: cube, RDM, steering table, lists
+    DevBuf<unsigned char> adj_ws;       // adjoints: RDM cube scratch
+    DevBuf<double> gfac;                // synthesis adjoint: per-facet gradients [F][10]
+    DevBuf<int64_t> d_voff;             // first mesh vertex of each instance (adjoint output)
+    const void *adj_grad = nullptr;     // the pending adjoint call's arguments
+    int adj_grad_c64 = 0;
+    double *adj_gverts = nullptr, *adj_grho = nullptr;
+    int64_t adj_vwords = 0;
+    // scene partition (batched dataset frames): instances [scene_first[b],
+    // scene_first[b+1]) form scene b; empty = one scene
+    std::vector<int32_t> scene_first;
+    int n_scenes = 1;
+    DevBuf<int64_t> d_foff;             // facet offsets of the scenes [B + 1]
+    DevBuf<int32_t> d_root;             // BVH root of each scene [B]
+    DevBuf<int32_t> vstart, vcnt;       // per (scene, channel) list ranges [B O]
+    DevBuf<uint32_t> mkeys, skeys;      // batched sort scratch
+    int tpi_override = 0;               // synthesis tiles per item (autotuner), 0 = default
+    int layout_S = 0;                   // synthesis samples per lane request, 0 = default
+    uint64_t version = 1;               // bumped by every change of meshes/scene/radar/layout
+    bool graph = false;                 // replay frames as CUDA graphs
+    struct FrameGraph {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        cudaGraphNode_t t0_node = nullptr;
+        cudaKernelNodeParams t0_params{};
+        int t0_arg = 0, n_args = 0;
+        uint64_t version = 0;
+        int path = -1, dtype = -1;
+        void *adc = nullptr;
+        cudaStream_t stream = nullptr;
+        double t0 = 0.0;
+        int launches = 0, chunks = 0;
+        void release()
+        {
+            if (exec) cudaGraphExecDestroy(exec);
+            if (graph) cudaGraphDestroy(graph);
+            exec = nullptr;
+            graph = nullptr;
+            t0_node = nullptr;
+        }
+    } fg;
 
     // stage timing: fixed events + two per chirp chunk
     bool timing = false;
@@ -122,6 +162,7 @@ struct bart_ctx {
     std::vector<cudaEvent_t> ev_syn;    // per chunk: after synth
     // side stream running the kinematics of chunk c+1 while chunk c is synthesised
     cudaStream_t side = nullptr;
+    cudaStream_t cap_stream = nullptr;  // frame-graph recording stream
     std::vector<cudaEvent_t> sync_ev;   // fork + per-chunk kin-done / synth-done (no timing)
     int chunks = 0;
     int path = 0;
@@ -139,6 +180,7 @@ struct bart_ctx {
         for (cudaEvent_t e : ev_syn) cudaEventDestroy(e);
         for (cudaEvent_t e : sync_ev) cudaEventDestroy(e);
         if (side) cudaStreamDestroy(side);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
         for (MeshStore *m : pool) {
             m->verts.release();
             m->tris.release();
@@ -153,7 +195,9 @@ struct bart_ctx {
         vis_cnt.release(); kin.release(); partial.release(); item_off.release();
         item_counter.release(); counters.release(); status.release();
         rdm_ws.release(); adc_own.release(); rdm_own.release(); noise_scratch.release();
-        det_ws.release();
+        fg.release();
+        det_ws.release(); adj_ws.release(); gfac.release(); d_voff.release(); d_foff.release(); d_root.release(); vstart.release();
+        vcnt.release(); mkeys.release(); skeys.release();
         if (count_host) cudaFreeHost(count_host);
     }
 };
@@ -306,6 +350,29 @@ int bart_mesh_upload(bart_ctx *ctx, const double *verts, int64_t nv, const int32
     m->nf = nf;
     *mesh_id = ctx->n_meshes++;
     ctx->tables_dirty = true;
+    ++ctx->version;
+    return BART_OK;
+}
+
+int bart_mesh_update(bart_ctx *ctx, int32_t mesh_id, const double *verts, const float *rho)
+{
+    g_err.clear();
+    if (!ctx || !verts) return fail(BART_EINVAL, "bart_mesh_update: NULL argument");
+    if (mesh_id < 0 || mesh_id >= ctx->n_meshes)
+        return fail(BART_EINVAL, "bart_mesh_update: mesh %d (have %d)", mesh_id, ctx->n_meshes);
+    BART_TRY(set_device(ctx));
+    MeshStore *m = ctx->pool[mesh_id];
+    CUDA_TRY(cudaMemcpyAsync(m->verts.p, verts, (size_t)(3 * m->nv) * sizeof(double),
+                             cudaMemcpyDeviceToDevice, ctx->stream), "mesh vertex update");
+    if (rho) {
+        CUDA_TRY(cudaMemcpyAsync(m->rho.p, rho, (size_t)m->nf * sizeof(float),
+                                 cudaMemcpyDeviceToDevice, ctx->stream), "mesh rho update");
+        if (!m->has_rho) {
+            m->has_rho = true;
+            ctx->tables_dirty = true;
+            ++ctx->version;
+        }
+    }
     return BART_OK;
 }
 
@@ -317,6 +384,7 @@ int bart_mesh_clear(bart_ctx *ctx)
     ctx->insts.clear();
     ctx->have_frame = false;
     ctx->tables_dirty = true;
+    ++ctx->version;
     return BART_OK;
 }
 
@@ -334,7 +402,30 @@ int bart_scene_set(bart_ctx *ctx, const bart_instance *inst, int32_t n)
                 return fail(BART_EINVAL, "bart_scene_set: instance %d has a non-finite pose", i);
     }
     ctx->insts.assign(inst, inst + n);
+    ctx->scene_first.clear();
+    ctx->n_scenes = 1;
     ctx->tables_dirty = true;
+    ++ctx->version;
+    return BART_OK;
+}
+
+int bart_scene_partition(bart_ctx *ctx, const int32_t *first, int32_t n_scenes)
+{
+    g_err.clear();
+    if (!ctx || !first) return fail(BART_EINVAL, "bart_scene_partition: NULL argument");
+    const int I = (int)ctx->insts.size();
+    if (I == 0) return fail(BART_ESTATE, "bart_scene_partition: no instances set");
+    if (n_scenes < 1 || n_scenes > I)
+        return fail(BART_EINVAL, "bart_scene_partition: n_scenes=%d with %d instances", n_scenes, I);
+    if (first[0] != 0 || first[n_scenes] != I)
+        return fail(BART_EINVAL, "bart_scene_partition: offsets must run from 0 to %d", I);
+    for (int b = 0; b < n_scenes; ++b)
+        if (first[b + 1] <= first[b])
+            return fail(BART_EINVAL, "bart_scene_partition: scene %d is empty or offsets decrease", b);
+    ctx->scene_first.assign(first, first + n_scenes + 1);
+    ctx->n_scenes = n_scenes;
+    ctx->tables_dirty = true;
+    ++ctx->version;
     return BART_OK;
 }
 
@@ -366,17 +457,21 @@ int bart_radar_set(bart_ctx *ctx, const bart_radar *r)
     if (r->window != BART_WINDOW_HANN && r->window != BART_WINDOW_RECT)
         return fail(BART_EINVAL, "bart_radar_set: window=%d", r->window);
     ctx->radar = *r;
+    ++ctx->version;
     ctx->have_radar = true;
     ctx->have_frame = false;
     return BART_OK;
 }
+
+// internal path: the adjoint of the FP64 synthesis (bart_simulate_adjoint)
+constexpr int kPathAdjoint = 100;
 
 static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t dtype,
                      bart_stats *stats)
 {
     if (!ctx->have_radar) return fail(BART_ESTATE, "bart_simulate_frame: radar not set");
     if (ctx->insts.empty()) return fail(BART_ESTATE, "bart_simulate_frame: scene has no instances");
-    if (path != BART_PATH_FP64 && path != BART_PATH_MIXED)
+    if (path != BART_PATH_FP64 && path != BART_PATH_MIXED && path != kPathAdjoint)
         return fail(BART_EINVAL, "bart_simulate_frame: path=%d", path);
     if (dtype != BART_C64 && dtype != BART_C128)
         return fail(BART_EINVAL, "bart_simulate_frame: dtype=%d", dtype);
@@ -408,6 +503,13 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
     }
     if (F > ((int64_t)1 << 31) - 2) return fail(BART_EINVAL, "scene has %lld facets (max 2^31-2)", (long long)F);
     const int A = rd.A, O = rd.O;
+    const int B = ctx->n_scenes;
+    if ((int64_t)B * O > 65535)
+        return fail(BART_EINVAL, "bart_simulate_frame: %d scenes x %d channels exceed 65535", B, O);
+    std::vector<int64_t> foff(B + 1), scene_F(B);
+    for (int b = 0; b < B; ++b) foff[b] = B > 1 ? id[ctx->scene_first[b]].off : 0;
+    foff[B] = F;
+    for (int b = 0; b < B; ++b) scene_F[b] = foff[b + 1] - foff[b];
 
     if (md.size() > ctx->d_meshes.cap || (size_t)I > ctx->d_insts.cap ||
         (size_t)(3 * I) > ctx->vel64.cap)
@@ -434,6 +536,27 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
     BART_TRY(ctx->blk_cnt.ensure(compact_blk_words(F, O + A), "compaction counts"));
     BART_TRY(ctx->vis_idx.ensure((size_t)(O + A) * F, "lit facet lists"));
     BART_TRY(ctx->vis_cnt.ensure(O + A, "lit facet counts"));
+    if (path == kPathAdjoint) {
+        BART_TRY(ctx->gfac.ensure((size_t)10 * F, "facet gradients"));
+        BART_TRY(ctx->d_voff.ensure((size_t)I, "instance vertex offsets"));
+        std::vector<int64_t> voff(I);
+        int64_t nvtot = 0;
+        for (int i = 0; i < I; ++i) {
+            voff[i] = nvtot;
+            nvtot += ctx->pool[ctx->insts[i].mesh_id]->nv;
+        }
+        ctx->adj_vwords = 3 * nvtot;
+        CUDA_TRY(cudaMemcpyAsync(ctx->d_voff.p, voff.data(), I * sizeof(int64_t),
+                                 cudaMemcpyHostToDevice, s), "vertex offset copy");
+    }
+    if (B > 1) {
+        BART_TRY(ctx->d_foff.ensure(B + 1, "scene facet offsets"));
+        BART_TRY(ctx->d_root.ensure(B, "scene roots"));
+        BART_TRY(ctx->vstart.ensure((size_t)B * O, "scene list starts"));
+        BART_TRY(ctx->vcnt.ensure((size_t)B * O, "scene list counts"));
+        BART_TRY(ctx->mkeys.ensure(F, "morton keys by facet"));
+        BART_TRY(ctx->skeys.ensure(F, "scene keys"));
+    }
 
     if (ctx->tables_dirty) {
         // pageable sources: each copy is staged before the call returns
@@ -446,126 +569,256 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
             for (int k = 0; k < 3; ++k) v[3 * i + k] = ctx->insts[i].vel[k];
         CUDA_TRY(cudaMemcpyAsync(ctx->vel64.p, v.data(), v.size() * sizeof(double),
                                  cudaMemcpyHostToDevice, s), "velocity copy");
+        if (B > 1)
+            CUDA_TRY(cudaMemcpyAsync(ctx->d_foff.p, foff.data(), (B + 1) * sizeof(int64_t),
+                                     cudaMemcpyHostToDevice, s), "scene offset copy");
         ctx->tables_dirty = false;
     }
-    CUDA_TRY(cudaMemsetAsync(ctx->counters.p, 0, 4 * sizeof(unsigned long long), s), "memset");
-    const bool tm = ctx->timing;
-    if (tm) {
-        BART_TRY(ensure_events(ctx->ev, 7));
-        CUDA_TRY(cudaEventRecord(ctx->ev[0], s), "cudaEventRecord");
-    }
-    int launches = 0;
-
-    // 1. world facets at t0
-    launch_build_facets(ctx->d_meshes.p, ctx->d_insts.p, I, F, t0, ctx->tri64.p, ctx->tri32.p,
-                        ctx->c64.p, ctx->fac.p, ctx->aabb.p, ctx->vel32.p, ctx->bounds.p, s);
-    launches += 1;
-    if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[1], s), "cudaEventRecord");
-    // 2. LBVH
-    launch_morton(ctx->fac.p, F, ctx->bounds.p, ctx->keys.p, ctx->vals.p, s);
-    radix_sort_pairs(ctx->keys.p, ctx->vals.p, ctx->keys_tmp.p, ctx->vals_tmp.p,
-                     ctx->sort_temp.p, F, 30, s);
-    launch_lbvh_build(ctx->keys.p, ctx->vals.p, F, ctx->nodes.p, ctx->parent.p,
-                      ctx->leaf_parent.p, s);
-    launch_lbvh_refit(ctx->vals.p, ctx->aabb.p, F, ctx->nodes.p, ctx->parent.p,
-                      ctx->leaf_parent.p, ctx->flags.p, s);
-    launches += 1 + 3 * 4 + (F >= 2 ? 2 : 0);
-    if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[2], s), "cudaEventRecord");
-    // 3. visibility + per-channel lit lists
-    launch_visibility(ctx->tri64.p, ctx->tri32.p, ctx->c64.p, ctx->nodes.p,
-                      F >= 2 ? ctx->vals.p : nullptr, F, rd, ctx->state.p, ctx->counters.p + 3,
-                      ctx->status.p, s);
-    launch_compact(ctx->state.p, F, rd, ctx->blk_cnt.p, ctx->vis_idx.p, ctx->vis_cnt.p, s);
-    launches += 1 + 3;
-    if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[3], s), "cudaEventRecord");
-    // 4. synthesis
-    SynthArgs a;
-    a.fac = ctx->fac.p;
-    a.tri64 = ctx->tri64.p;
-    a.c64 = ctx->c64.p;
-    a.vel64 = ctx->vel64.p;
-    a.vel32 = ctx->vel32.p;
-    a.vis_idx = ctx->vis_idx.p;
-    a.vis_cnt = ctx->vis_cnt.p;
-    a.F = F;
-    a.kin = nullptr;
-    a.out = adc;
-    a.out_c64 = dtype == BART_C64;
-    a.counters = ctx->counters.p;
-    a.item_off = nullptr;
-    a.item_counter = nullptr;
-    a.partial = nullptr;
-    a.tiles_per_item = 0;
-    a.rd = rd;
+    // sizes and buffers of the synthesis (before any capture: no allocation
+    // may happen while a frame graph is being recorded)
+    const int tpi = ctx->tpi_override > 0
+                        ? ctx->tpi_override
+                        : synth_tiles_per_item(*std::max_element(scene_F.begin(), scene_F.end()));
+    int nc = rd.N, chunks = 1, nbuf = 1;
+    size_t chunk_words = 0;
+    int64_t max_items = 0;
     if (path == BART_PATH_MIXED) {
         // chirp chunks only when the kinematics table would exceed its budget;
         // the table is then double-buffered so that the side stream fills
         // chunk c+1 while the main stream synthesises chunk c (one chunk
         // measured faster than forced chunking at the sedan size)
         const int64_t per_chirp = (int64_t)A * F * (int64_t)sizeof(float4);
-        const int nc = (int)std::min<int64_t>(rd.N, std::max<int64_t>(1, ctx->kin_budget / per_chirp));
-        const int chunks = (rd.N + nc - 1) / nc;
-        const int nbuf = chunks > 1 ? 2 : 1;
-        const size_t chunk_words = (size_t)nc * A * F;
+        nc = (int)std::min<int64_t>(rd.N, std::max<int64_t>(1, ctx->kin_budget / per_chirp));
+        chunks = (rd.N + nc - 1) / nc;
+        nbuf = chunks > 1 ? 2 : 1;
+        chunk_words = (size_t)nc * A * F;
         BART_TRY(ctx->kin.ensure(nbuf * chunk_words, "kinematics table"));
-        BART_TRY(ctx->partial.ensure((size_t)synth_partial_words(F, rd, nc), "synthesis partials"));
-        BART_TRY(ctx->item_off.ensure(O + 1, "synthesis item table"));
+        BART_TRY(ctx->partial.ensure((size_t)synth_partial_words(scene_F.data(), B, rd, nc,
+                                                                 tpi, ctx->layout_S),
+                                     "synthesis partials"));
+        max_items = synth_max_items(scene_F.data(), B, rd, nc, tpi, ctx->layout_S);
+        BART_TRY(ctx->item_off.ensure((size_t)B * O + 1, "synthesis item table"));
         BART_TRY(ctx->item_counter.ensure(1, "synthesis item counter"));
         if (!ctx->side)
             CUDA_TRY(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking), "cudaStreamCreate");
         BART_TRY(ensure_events(ctx->sync_ev, 1 + 2 * chunks, false));
-        cudaEvent_t fork = ctx->sync_ev[0];
-        cudaEvent_t *kin_done = ctx->sync_ev.data() + 1;
-        cudaEvent_t *syn_done = ctx->sync_ev.data() + 1 + chunks;
-        a.partial = ctx->partial.p;
-        a.item_off = ctx->item_off.p;
-        a.item_counter = ctx->item_counter.p;
-        if (tm) {
+        if (ctx->timing) {
             BART_TRY(ensure_events(ctx->ev_kin, 2 * chunks));
             BART_TRY(ensure_events(ctx->ev_syn, 2 * chunks));
         }
-        CUDA_TRY(cudaEventRecord(fork, s), "cudaEventRecord");
-        CUDA_TRY(cudaStreamWaitEvent(ctx->side, fork, 0), "cudaStreamWaitEvent");
-        auto kin_chunk = [&](int c) -> int {
-            const int n0 = c * nc;
-            const int cnt = std::min(nc, rd.N - n0);
-            if (c >= 2)   // its buffer was read by the synthesis of chunk c-2
-                CUDA_TRY(cudaStreamWaitEvent(ctx->side, syn_done[c - 2], 0), "cudaStreamWaitEvent");
-            if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_kin[2 * c], ctx->side), "cudaEventRecord");
-            launch_kinematics(ctx->c64.p, ctx->fac.p, ctx->vel64.p, ctx->vis_idx.p,
-                              ctx->vis_cnt.p, F, rd, n0, cnt, ctx->kin.p + (c % nbuf) * chunk_words,
-                              ctx->side);
-            if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_kin[2 * c + 1], ctx->side), "cudaEventRecord");
-            CUDA_TRY(cudaEventRecord(kin_done[c], ctx->side), "cudaEventRecord");
-            return BART_OK;
-        };
-        BART_TRY(kin_chunk(0));
-        for (int c = 0; c < chunks; ++c) {
-            if (c + 1 < chunks) BART_TRY(kin_chunk(c + 1));
-            CUDA_TRY(cudaStreamWaitEvent(s, kin_done[c], 0), "cudaStreamWaitEvent");
-            a.n0 = c * nc;
-            a.nc = std::min(nc, rd.N - a.n0);
-            a.kin = ctx->kin.p + (c % nbuf) * chunk_words;
-            if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_syn[2 * c], s), "cudaEventRecord");
-            launch_synth_mixed(a, s);
-            if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_syn[2 * c + 1], s), "cudaEventRecord");
-            CUDA_TRY(cudaEventRecord(syn_done[c], s), "cudaEventRecord");
-        }
-        ctx->chunks = chunks;
-        launches += 4 * chunks;
-    } else {
-        a.n0 = 0;
-        a.nc = rd.N;
-        launch_synth_fp64(a, s);
-        ctx->chunks = 1;
-        launches += 1;
     }
-    if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[4], s), "cudaEventRecord");
-    ctx->path = path;
-    ctx->frame_launches = launches;
-    ctx->have_rdm_timing = false;
-    ctx->have_detect_timing = false;
-    ctx->timed_frame = tm;
+    if (ctx->timing) BART_TRY(ensure_events(ctx->ev, 7));
+
+    // every launch of the frame, on the context's stream (and the side
+    // stream, joined back): run directly, or recorded into a frame graph
+    auto enqueue = [&](double t0v, bool tm, cudaStream_t s) -> int {
+        CUDA_TRY(cudaMemsetAsync(ctx->counters.p, 0, 4 * sizeof(unsigned long long), s), "memset");
+        if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[0], s), "cudaEventRecord");
+        int launches = 0;
+
+        // 1. world facets at t0
+        launch_build_facets(ctx->d_meshes.p, ctx->d_insts.p, I, F, t0v, ctx->tri64.p, ctx->tri32.p,
+                            ctx->c64.p, ctx->fac.p, ctx->aabb.p, ctx->vel32.p, ctx->bounds.p, s);
+        launches += 1;
+        if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[1], s), "cudaEventRecord");
+        // 2. LBVH (batched scenes: one hierarchy with a subtree per scene)
+        SceneSplit split;
+        if (B > 1) {
+            launch_lbvh_batched(ctx->fac.p, F, ctx->bounds.p, ctx->d_foff.p, B, ctx->keys.p,
+                                ctx->vals.p, ctx->keys_tmp.p, ctx->vals_tmp.p, ctx->sort_temp.p,
+                                ctx->mkeys.p, ctx->skeys.p, ctx->nodes.p, ctx->parent.p,
+                                ctx->leaf_parent.p, ctx->d_root.p, s);
+            launches += lbvh_batched_launches(B);
+            split.B = B;
+            split.foff = ctx->d_foff.p;
+            split.root = ctx->d_root.p;
+        } else {
+            launch_morton(ctx->fac.p, F, ctx->bounds.p, ctx->keys.p, ctx->vals.p, s);
+            radix_sort_pairs(ctx->keys.p, ctx->vals.p, ctx->keys_tmp.p, ctx->vals_tmp.p,
+                             ctx->sort_temp.p, F, 30, s);
+            launch_lbvh_build(ctx->keys.p, ctx->vals.p, F, ctx->nodes.p, ctx->parent.p,
+                              ctx->leaf_parent.p, s);
+            launches += 1 + 3 * 4 + (F >= 2 ? 1 : 0);
+        }
+        launch_lbvh_refit(ctx->vals.p, ctx->aabb.p, F, ctx->nodes.p, ctx->parent.p,
+                          ctx->leaf_parent.p, ctx->flags.p, s);
+        launches += F >= 2 ? 1 : 0;
+        if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[2], s), "cudaEventRecord");
+        // 3. visibility + per-channel lit lists (+ their per-scene ranges)
+        launch_visibility(ctx->tri64.p, ctx->tri32.p, ctx->c64.p, ctx->nodes.p,
+                          F >= 2 ? ctx->vals.p : nullptr, F, rd, split, ctx->state.p,
+                          ctx->counters.p + 3, ctx->status.p, s);
+        launch_compact(ctx->state.p, F, rd, ctx->blk_cnt.p, ctx->vis_idx.p, ctx->vis_cnt.p, s);
+        launches += 1 + 3;
+        if (B > 1) {
+            launch_scene_lists(ctx->vis_idx.p, ctx->vis_cnt.p, F, O, ctx->d_foff.p, B, ctx->vstart.p,
+                               ctx->vcnt.p, s);
+            launches += 1;
+        }
+        if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[3], s), "cudaEventRecord");
+        // 4. synthesis
+        SynthArgs a;
+        a.fac = ctx->fac.p;
+        a.tri64 = ctx->tri64.p;
+        a.c64 = ctx->c64.p;
+        a.vel64 = ctx->vel64.p;
+        a.vel32 = ctx->vel32.p;
+        a.vis_idx = ctx->vis_idx.p;
+        a.vis_cnt = ctx->vis_cnt.p;
+        a.VO = B * O;
+        a.vstart = B > 1 ? ctx->vstart.p : nullptr;
+        a.vcnt = B > 1 ? ctx->vcnt.p : ctx->vis_cnt.p;
+        a.F = F;
+        a.kin = nullptr;
+        a.out = adc;
+        a.out_c64 = dtype == BART_C64;
+        a.counters = ctx->counters.p;
+        a.item_off = nullptr;
+        a.item_counter = nullptr;
+        a.partial = nullptr;
+        a.tiles_per_item = tpi;
+        a.max_items = 0;
+        a.layout_S = ctx->layout_S;
+        a.rd = rd;
+        if (path == BART_PATH_MIXED) {
+            cudaEvent_t fork = ctx->sync_ev[0];
+            cudaEvent_t *kin_done = ctx->sync_ev.data() + 1;
+            cudaEvent_t *syn_done = ctx->sync_ev.data() + 1 + chunks;
+            a.partial = ctx->partial.p;
+            a.item_off = ctx->item_off.p;
+            a.item_counter = ctx->item_counter.p;
+            a.max_items = max_items;
+            CUDA_TRY(cudaEventRecord(fork, s), "cudaEventRecord");
+            CUDA_TRY(cudaStreamWaitEvent(ctx->side, fork, 0), "cudaStreamWaitEvent");
+            auto kin_chunk = [&](int c) -> int {
+                const int n0 = c * nc;
+                const int cnt = std::min(nc, rd.N - n0);
+                if (c >= 2)   // its buffer was read by the synthesis of chunk c-2
+                    CUDA_TRY(cudaStreamWaitEvent(ctx->side, syn_done[c - 2], 0), "cudaStreamWaitEvent");
+                if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_kin[2 * c], ctx->side), "cudaEventRecord");
+                launch_kinematics(ctx->c64.p, ctx->fac.p, ctx->vel64.p, ctx->vis_idx.p,
+                                  ctx->vis_cnt.p, F, rd, n0, cnt, ctx->kin.p + (c % nbuf) * chunk_words,
+                                  ctx->side);
+                if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_kin[2 * c + 1], ctx->side), "cudaEventRecord");
+                CUDA_TRY(cudaEventRecord(kin_done[c], ctx->side), "cudaEventRecord");
+                return BART_OK;
+            };
+            BART_TRY(kin_chunk(0));
+            for (int c = 0; c < chunks; ++c) {
+                if (c + 1 < chunks) BART_TRY(kin_chunk(c + 1));
+                CUDA_TRY(cudaStreamWaitEvent(s, kin_done[c], 0), "cudaStreamWaitEvent");
+                a.n0 = c * nc;
+                a.nc = std::min(nc, rd.N - a.n0);
+                a.kin = ctx->kin.p + (c % nbuf) * chunk_words;
+                if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_syn[2 * c], s), "cudaEventRecord");
+                launch_synth_mixed(a, s);
+                if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_syn[2 * c + 1], s), "cudaEventRecord");
+                CUDA_TRY(cudaEventRecord(syn_done[c], s), "cudaEventRecord");
+            }
+            ctx->chunks = chunks;
+            launches += 4 * chunks;
+        } else if (path == kPathAdjoint) {
+            a.n0 = 0;
+            a.nc = rd.N;
+            launch_adjoint_fp64(a, ctx->adj_grad, ctx->adj_grad_c64, ctx->gfac.p, s);
+            launch_adjoint_scatter(ctx->gfac.p, ctx->fac.p, ctx->d_insts.p, ctx->d_meshes.p,
+                                   ctx->d_voff.p, F, ctx->adj_gverts, ctx->adj_vwords,
+                                   ctx->adj_grho, s);
+            ctx->chunks = 1;
+            launches += 2;
+        } else {
+            a.n0 = 0;
+            a.nc = rd.N;
+            launch_synth_fp64(a, s);
+            ctx->chunks = 1;
+            launches += 1;
+        }
+        if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[4], s), "cudaEventRecord");
+        ctx->path = path;
+        ctx->frame_launches = launches;
+        ctx->have_rdm_timing = false;
+        ctx->have_detect_timing = false;
+        ctx->timed_frame = tm;
+        return BART_OK;
+    };
+
+    const bool use_graph = ctx->graph && !stats && !ctx->timing && path != kPathAdjoint;
+    if (use_graph) {
+        bart_ctx::FrameGraph &g = ctx->fg;
+        const bool hit = g.exec && g.version == ctx->version && g.path == path &&
+                         g.dtype == dtype && g.adc == adc && g.stream == s;
+        if (!hit) {
+            g.release();
+            // record on a private stream (the legacy default stream, torch's
+            // usual current stream, cannot be captured); the graph is then
+            // launched on the caller's stream, after everything queued there
+            if (!ctx->cap_stream)
+                CUDA_TRY(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking),
+                         "cudaStreamCreate");
+            cudaGraph_t graph = nullptr;
+            CUDA_TRY(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed),
+                     "cudaStreamBeginCapture");
+            const int rc = enqueue(t0, false, ctx->cap_stream);
+            const cudaError_t ce = cudaStreamEndCapture(ctx->cap_stream, &graph);
+            if (rc != BART_OK || ce != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                cudaGetLastError();
+                return rc != BART_OK ? rc : fail(BART_ECUDA, "frame graph capture: %s",
+                                                 cudaGetErrorString(ce));
+            }
+            g.graph = graph;
+            CUDA_TRY(cudaGraphInstantiate(&g.exec, graph, 0), "cudaGraphInstantiate");
+            const void *fn = build_facets_kernel_fn(&g.t0_arg, &g.n_args);
+            size_t nn = 0;
+            CUDA_TRY(cudaGraphGetNodes(graph, nullptr, &nn), "cudaGraphGetNodes");
+            std::vector<cudaGraphNode_t> nodes(nn);
+            CUDA_TRY(cudaGraphGetNodes(graph, nodes.data(), &nn), "cudaGraphGetNodes");
+            for (cudaGraphNode_t n : nodes) {
+                cudaGraphNodeType t;
+                CUDA_TRY(cudaGraphNodeGetType(n, &t), "cudaGraphNodeGetType");
+                if (t != cudaGraphNodeTypeKernel) continue;
+                cudaKernelNodeParams kp;
+                CUDA_TRY(cudaGraphKernelNodeGetParams(n, &kp), "cudaGraphKernelNodeGetParams");
+                if (kp.func == fn) {
+                    g.t0_node = n;
+                    g.t0_params = kp;
+                    break;
+                }
+            }
+            if (!g.t0_node) {
+                g.release();
+                return fail(BART_ECUDA, "frame graph: world-facet kernel node not found");
+            }
+            g.version = ctx->version;
+            g.path = path;
+            g.dtype = dtype;
+            g.adc = adc;
+            g.stream = s;
+            g.t0 = t0;
+            g.launches = ctx->frame_launches;
+            g.chunks = ctx->chunks;
+        } else if (t0 != g.t0) {
+            // a new frame time: only the world-facet kernel's t0 argument changes
+            void *args[32];
+            cudaKernelNodeParams kp = g.t0_params;
+            double t0_arg = t0;
+            for (int k = 0; k < g.n_args && k < 32; ++k) args[k] = kp.kernelParams[k];
+            args[g.t0_arg] = &t0_arg;
+            kp.kernelParams = args;
+            CUDA_TRY(cudaGraphExecKernelNodeSetParams(g.exec, g.t0_node, &kp),
+                     "cudaGraphExecKernelNodeSetParams");
+            g.t0 = t0;
+        }
+        CUDA_TRY(cudaGraphLaunch(g.exec, s), "cudaGraphLaunch");
+        ctx->path = path;
+        ctx->frame_launches = g.launches;
+        ctx->chunks = g.chunks;
+        ctx->have_rdm_timing = false;
+        ctx->have_detect_timing = false;
+        ctx->timed_frame = false;
+    } else {
+        BART_TRY(enqueue(t0, ctx->timing, s));
+    }
     CUDA_TRY(cudaGetLastError(), "kernel launch");
     ctx->have_frame = true;
     ctx->frame_F = F;
@@ -599,6 +852,121 @@ int bart_simulate_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32
     return run_frame(ctx, t0, path, adc, dtype, stats);
 }
 
+int bart_simulate_adjoint(bart_ctx *ctx, double t0, const void *grad_adc, int32_t dtype,
+                          double *grad_verts, double *grad_rho)
+{
+    g_err.clear();
+    if (!ctx || !grad_adc || !grad_verts)
+        return fail(BART_EINVAL, "bart_simulate_adjoint: NULL argument");
+    if (dtype != BART_C64 && dtype != BART_C128)
+        return fail(BART_EINVAL, "bart_simulate_adjoint: dtype=%d", dtype);
+    ctx->adj_grad = grad_adc;
+    ctx->adj_grad_c64 = dtype == BART_C64;
+    ctx->adj_gverts = grad_verts;
+    ctx->adj_grho = grad_rho;
+    // the synthesis output pointer is unused on this path
+    const int rc = run_frame(ctx, t0, kPathAdjoint, const_cast<void *>(grad_adc), dtype, nullptr);
+    ctx->adj_grad = nullptr;
+    ctx->adj_gverts = ctx->adj_grho = nullptr;
+    return rc;
+}
+
+int bart_set_graph(bart_ctx *ctx, int32_t enable)
+{
+    g_err.clear();
+    if (!ctx) return fail(BART_EINVAL, "bart_set_graph: ctx is NULL");
+    ctx->graph = enable != 0;
+    if (!ctx->graph) {
+        BART_TRY(set_device(ctx));
+        if (ctx->fg.exec) CUDA_TRY(cudaStreamSynchronize(ctx->fg.stream), "cudaStreamSynchronize");
+        ctx->fg.release();
+    }
+    return BART_OK;
+}
+
+int bart_set_synth_layout(bart_ctx *ctx, int32_t samples_per_lane, int32_t tiles_per_item)
+{
+    g_err.clear();
+    if (!ctx) return fail(BART_EINVAL, "bart_set_synth_layout: ctx is NULL");
+    if (samples_per_lane != 0 && samples_per_lane != 8 && samples_per_lane != 16)
+        return fail(BART_EINVAL, "bart_set_synth_layout: samples_per_lane=%d (0, 8 or 16)",
+                    samples_per_lane);
+    if (tiles_per_item < 0 || tiles_per_item > 65536)
+        return fail(BART_EINVAL, "bart_set_synth_layout: tiles_per_item=%d", tiles_per_item);
+    ctx->layout_S = samples_per_lane == 16 ? 0 : samples_per_lane;
+    ctx->tpi_override = tiles_per_item;
+    ++ctx->version;
+    return BART_OK;
+}
+
+int bart_autotune(bart_ctx *ctx, double t0, void *adc, int32_t dtype, int32_t reps,
+                  bart_tune *out)
+{
+    g_err.clear();
+    if (!ctx || !adc || !out) return fail(BART_EINVAL, "bart_autotune: NULL argument");
+    if (!ctx->have_radar) return fail(BART_ESTATE, "bart_autotune: radar not set");
+    if (reps < 1 || reps > 100) return fail(BART_EINVAL, "bart_autotune: reps=%d", reps);
+    BART_TRY(set_device(ctx));
+    const bool timing = ctx->timing, graph = ctx->graph;
+    const int S0 = ctx->layout_S, T0 = ctx->tpi_override;
+    ctx->timing = true;
+    ctx->graph = false;
+    std::memset(out, 0, sizeof *out);
+    std::vector<int> Ss = {0};
+    if (synth_layout_samples(ctx->radar.M, 8) == 8) Ss.push_back(8);
+    const int tpis[] = {8, 16, 32, 64, 128, 256, 512};
+    int rc = BART_OK;
+    float best = 0.f;
+    for (int S : Ss) {
+        for (int tpi : tpis) {
+            if (out->n_trials >= BART_TUNE_MAX) break;
+            ctx->layout_S = S;
+            ctx->tpi_override = tpi;
+            float ms_best = 0.f;
+            for (int r = 0; r <= reps && rc == BART_OK; ++r) {   // r = 0 warms up
+                rc = run_frame(ctx, t0, BART_PATH_MIXED, adc, dtype, nullptr);
+                if (rc != BART_OK) break;
+                if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+                    cudaGetLastError();
+                    rc = fail(BART_ECUDA, "bart_autotune: frame failed");
+                    break;
+                }
+                float ms = 0.f;
+                for (int c = 0; c < ctx->chunks; ++c) {
+                    float e = 0.f;
+                    cudaEventElapsedTime(&e, ctx->ev_syn[2 * c], ctx->ev_syn[2 * c + 1]);
+                    ms += e;
+                }
+                if (r > 0 && (r == 1 || ms < ms_best)) ms_best = ms;
+            }
+            if (rc != BART_OK) break;
+            const int i = out->n_trials++;
+            out->samples_per_lane[i] = synth_layout_samples(ctx->radar.M, S);
+            out->tiles_per_item[i] = tpi;
+            out->synthesis_ms[i] = ms_best;
+            if (i == 0 || ms_best < best) {
+                best = ms_best;
+                out->best_samples_per_lane = out->samples_per_lane[i];
+                out->best_tiles_per_item = tpi;
+                out->best_ms = ms_best;
+            }
+        }
+        if (rc != BART_OK) break;
+    }
+    ctx->timing = timing;
+    ctx->graph = graph;
+    if (rc != BART_OK) {
+        ctx->layout_S = S0;
+        ctx->tpi_override = T0;
+        ++ctx->version;
+        return rc;
+    }
+    ctx->layout_S = out->best_samples_per_lane == 8 ? 8 : 0;
+    ctx->tpi_override = out->best_tiles_per_item;
+    ++ctx->version;
+    return BART_OK;
+}
+
 static int run_rdm(bart_ctx *ctx, const void *adc, int32_t dtype, float *rdm)
 {
     if (!ctx->have_radar) return fail(BART_ESTATE, "bart_form_rdm: radar not set");
@@ -611,12 +979,16 @@ static int run_rdm(bart_ctx *ctx, const void *adc, int32_t dtype, float *rdm)
                     "2^a 3^b (M=%d, N=%d, 2 <= N <= 1024)", ctx->radar.M, ctx->radar.N);
     BART_TRY(set_device(ctx));
     const RadarDev rd = make_rd(ctx->radar);
-    BART_TRY(ctx->rdm_ws.ensure((size_t)rdm_workspace_bytes(rd, dtype), "rdm workspace"));
+    const int groups = ctx->n_scenes;
+    if ((int64_t)groups * ctx->radar.P * ctx->radar.Q > 65535)
+        return fail(BART_EINVAL, "bart_form_rdm: %d scenes x %d channels exceed 65535", groups,
+                    ctx->radar.P * ctx->radar.Q);
+    BART_TRY(ctx->rdm_ws.ensure((size_t)rdm_workspace_bytes(rd, dtype) * groups, "rdm workspace"));
     if (ctx->timing) {
         BART_TRY(ensure_events(ctx->ev, 7));
         CUDA_TRY(cudaEventRecord(ctx->ev[5], ctx->stream), "cudaEventRecord");
     }
-    launch_rdm(adc, dtype, rd, ctx->rdm_ws.p, rdm, ctx->stream);
+    launch_rdm(adc, dtype, rd, groups, ctx->rdm_ws.p, rdm, ctx->stream);
     CUDA_TRY(cudaGetLastError(), "rdm launch");
     if (ctx->timing) {
         CUDA_TRY(cudaEventRecord(ctx->ev[6], ctx->stream), "cudaEventRecord");
@@ -723,6 +1095,34 @@ int bart_detect(bart_ctx *ctx, const void *adc, int32_t dtype, const bart_detect
     return BART_OK;
 }
 
+int bart_rdm_adjoint(bart_ctx *ctx, const void *adc, int32_t dtype, const float *grad_rdm,
+                     void *grad_adc)
+{
+    g_err.clear();
+    if (!ctx || !adc || !grad_rdm || !grad_adc)
+        return fail(BART_EINVAL, "bart_rdm_adjoint: NULL argument");
+    if (!ctx->have_radar) return fail(BART_ESTATE, "bart_rdm_adjoint: radar not set");
+    if (dtype != BART_C64 && dtype != BART_C128)
+        return fail(BART_EINVAL, "bart_rdm_adjoint: dtype=%d", dtype);
+    const bart_radar &r = ctx->radar;
+    if (!is_fft_len(r.M) || !is_fft_len(r.N) || r.N < 2 || r.N > 1024)
+        return fail(BART_EINVAL, "bart_rdm_adjoint: M and N must be of the form 2^a 3^b "
+                    "(M=%d, N=%d, 2 <= N <= 1024)", r.M, r.N);
+    const int groups = ctx->n_scenes;
+    if ((int64_t)groups * r.P * r.Q > 65535)
+        return fail(BART_EINVAL, "bart_rdm_adjoint: %d scenes x %d channels exceed 65535", groups,
+                    r.P * r.Q);
+    BART_TRY(set_device(ctx));
+    const RadarDev rd = make_rd(r);
+    const size_t cube = (size_t)groups * rd.O * rd.N * rd.M * (dtype == BART_C64 ? 8 : 16);
+    const size_t half = (cube + 255) & ~(size_t)255;
+    BART_TRY(ctx->adj_ws.ensure(2 * half, "rdm adjoint workspace"));
+    launch_rdm_adjoint(adc, dtype, grad_rdm, rd, groups, ctx->adj_ws.p, ctx->adj_ws.p + half,
+                       grad_adc, ctx->stream);
+    CUDA_TRY(cudaGetLastError(), "bart_rdm_adjoint launch");
+    return BART_OK;
+}
+
 int bart_form_rdm_static(const void *adc, int32_t dtype, int32_t O, int32_t N, int32_t M,
                          int32_t window, float *rdm, void *stream)
 {
@@ -754,7 +1154,7 @@ int bart_form_rdm_static(const void *adc, int32_t dtype, int32_t O, int32_t N, i
     const char *err = nullptr;
     const int rc = rdm_static_workspace(&ws, &err);
     if (rc != BART_OK) return fail(rc, "bart_form_rdm_static: %s", err);
-    launch_rdm(adc, dtype, rd, ws, rdm, reinterpret_cast<cudaStream_t>(stream));
+    launch_rdm(adc, dtype, rd, 1, ws, rdm, reinterpret_cast<cudaStream_t>(stream));
     CUDA_TRY(cudaGetLastError(), "bart_form_rdm_static launch");
     return BART_OK;
 }
@@ -768,11 +1168,12 @@ int bart_frame_host(bart_ctx *ctx, double t0, int32_t path, float *rdm_host, bar
     const int dtype = path == BART_PATH_FP64 ? BART_C128 : BART_C64;
     const size_t esz = dtype == BART_C64 ? 8 : 16;
     BART_TRY(set_device(ctx));
-    BART_TRY(ctx->adc_own.ensure((size_t)r.P * r.Q * r.N * r.M * esz, "frame adc"));
-    BART_TRY(ctx->rdm_own.ensure((size_t)r.M * r.N, "frame rdm"));
+    const size_t B = (size_t)ctx->n_scenes;
+    BART_TRY(ctx->adc_own.ensure(B * r.P * r.Q * r.N * r.M * esz, "frame adc"));
+    BART_TRY(ctx->rdm_own.ensure(B * r.M * r.N, "frame rdm"));
     BART_TRY(run_frame(ctx, t0, path, ctx->adc_own.p, dtype, stats));
     BART_TRY(run_rdm(ctx, ctx->adc_own.p, dtype, ctx->rdm_own.p));
-    CUDA_TRY(cudaMemcpyAsync(rdm_host, ctx->rdm_own.p, (size_t)r.M * r.N * sizeof(float),
+    CUDA_TRY(cudaMemcpyAsync(rdm_host, ctx->rdm_own.p, B * r.M * r.N * sizeof(float),
                              cudaMemcpyDeviceToHost, ctx->stream), "rdm copy");
     CUDA_TRY(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
     return BART_OK;

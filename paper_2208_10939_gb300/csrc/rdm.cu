@@ -45,9 +45,11 @@ __host__ __device__ __forceinline__ int tw_len(int L) { return is_pow2_len(L) ? 
 // Stockham stages over `cols` interleaved transforms of length L stored as
 // buf[col * L + idx]; `tw` holds exp(-2 pi i t / L), t < tw_len(L).
 template <typename C, typename T>
-__device__ C *stockham(C *x, C *y, const C *tw, int L, int cols)
+__device__ C *stockham(C *x, C *y, const C *tw, int L, int cols, int sgn = 1)
 {
-    const T h3 = (T)0.86602540378443864676;    // sin(2 pi / 3)
+    // sgn = +1: forward transform (exp(-i ...)); -1: unnormalised inverse
+    // (exp(+i ...), with `tw` holding the conjugate twiddles)
+    const T h3 = (T)sgn * (T)0.86602540378443864676;    // sin(2 pi / 3)
     for (int n = L, s = 1; n > 1;) {
         const int p = (n & 1) ? 3 : 2;
         const int m = n / p;
@@ -103,13 +105,13 @@ __device__ C *stockham(C *x, C *y, const C *tw, int L, int cols)
 }
 
 template <typename T>
-__device__ void fill_twiddles(typename Cplx<T>::type *tw, int L)
+__device__ void fill_twiddles(typename Cplx<T>::type *tw, int L, int sgn = 1)
 {
     for (int j = threadIdx.x; j < tw_len(L); j += blockDim.x) {
         T s, c;
         sincospi_t((T)(-2 * j) / (T)L, &s, &c);
         tw[j].x = c;
-        tw[j].y = s;
+        tw[j].y = (T)sgn * s;
     }
 }
 
@@ -178,14 +180,17 @@ __global__ void doppler_kernel(const typename Cplx<T>::type *__restrict__ X, int
     }
 }
 
-// RDM[r][d] = sum over channels, in channel order
+// RDM[g][r][d] = sum over the O channels of group g, in channel order
 template <typename T>
-__global__ void rdm_sum_kernel(const T *__restrict__ pw, int O, int64_t MN, float *__restrict__ rdm)
+__global__ void rdm_sum_kernel(const T *__restrict__ pw, int O, int64_t MN, int groups,
+                               float *__restrict__ rdm)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= MN) return;
+    if (i >= MN * groups) return;
+    const int64_t g = i / MN, j = i - g * MN;
+    const T *src = pw + g * O * MN + j;
     T acc = (T)0;
-    for (int o = 0; o < O; ++o) acc += pw[(int64_t)o * MN + i];
+    for (int o = 0; o < O; ++o) acc += src[(int64_t)o * MN];
     rdm[i] = (float)acc;
 }
 
@@ -206,6 +211,75 @@ __global__ void rdm_cube_sum_kernel(const typename Cplx<T>::type *__restrict__ Y
 
 // range bins per Doppler block: the largest power of two RB with RB N <= 512
 // that divides M
+// -------------------------------------------------------------------------
+// adjoint of the RDM: for a real loss L(RDM) with dL/dRDM = G[r][d'],
+//   Ybar[o][r][d'] = 2 G[r][d'] Y[o][r][d']            (|Y|^2 = Y conj(Y))
+//   Xbar[o][n][r]  = w_d[n] sum_d exp(+2 pi i n d / N) Ybar[o][r][d]
+//   xbar[o][n][m]  = w_r[m] sum_r exp(+2 pi i m r / M) Xbar[o][n][r]
+// i.e. the conjugate transposes of the two windowed DFTs; gradients of
+// complex tensors as d/dRe + i d/dIm.
+// -------------------------------------------------------------------------
+template <typename T>
+__global__ void doppler_adjoint_kernel(const typename Cplx<T>::type *__restrict__ Y,
+                                       const float *__restrict__ G, int O, int N, int M, int RB,
+                                       int window, typename Cplx<T>::type *__restrict__ Xbar)
+{
+    using C = typename Cplx<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf0 = reinterpret_cast<C *>(smem_raw);
+    C *buf1 = buf0 + RB * N;
+    C *tw = buf1 + RB * N;
+    fill_twiddles<T>(tw, N, -1);
+    const int r0 = blockIdx.x * RB;
+    const int o = blockIdx.y;              // group * O + channel
+    const int g = o / O;
+    // Ybar of range bins r0 .. r0 + RB - 1, unshifted Doppler order, column-major
+    for (int i = threadIdx.x; i < RB * N; i += blockDim.x) {
+        const int c = i / N, d = i % N;
+        const int ds = d + (N >> 1) >= N ? d + (N >> 1) - N : d + (N >> 1);
+        const int64_t cell = (int64_t)(r0 + c) * N + ds;
+        const C y = Y[(int64_t)o * M * N + cell];
+        const T w = (T)2 * (T)G[(int64_t)g * M * N + cell];
+        C v;
+        v.x = w * y.x;
+        v.y = w * y.y;
+        buf0[c * N + d] = v;
+    }
+    __syncthreads();
+    const C *res = stockham<C, T>(buf0, buf1, tw, N, RB, -1);
+    for (int i = threadIdx.x; i < RB * N; i += blockDim.x) {
+        const int n = i / RB, c = i % RB;
+        const T w = window_val<T>(n, N, window);
+        C v = res[c * N + n];
+        v.x *= w;
+        v.y *= w;
+        Xbar[((int64_t)o * N + n) * M + r0 + c] = v;
+    }
+}
+
+template <typename T>
+__global__ void range_adjoint_kernel(const typename Cplx<T>::type *__restrict__ Xbar, int M,
+                                     int window, typename Cplx<T>::type *__restrict__ xbar)
+{
+    using C = typename Cplx<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf0 = reinterpret_cast<C *>(smem_raw);
+    C *buf1 = buf0 + M;
+    C *tw = buf1 + M;
+    fill_twiddles<T>(tw, M, -1);
+    const int64_t row = blockIdx.x;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) buf0[i] = Xbar[row * M + i];
+    __syncthreads();
+    const C *res = stockham<C, T>(buf0, buf1, tw, M, 1, -1);
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        const T w = window_val<T>(i, M, window);
+        C v = res[i];
+        v.x *= w;
+        v.y *= w;
+        xbar[row * M + i] = v;
+    }
+}
+
 static int rdm_rb(int N, int M)
 {
     int rb = 1;
@@ -248,14 +322,18 @@ static void doppler(const void *X, const RadarDev &rd, T *pw, void *cube, cudaSt
 }
 
 template <typename T>
-static void run_rdm(const void *adc, const RadarDev &rd, void *ws, float *rdm, cudaStream_t s)
+static void run_rdm(const void *adc, const RadarDev &rd, int groups, void *ws, float *rdm,
+                    cudaStream_t s)
 {
     using C = typename Cplx<T>::type;
-    range_fft<T>(adc, rd, ws, s);
-    T *pw = reinterpret_cast<T *>(reinterpret_cast<C *>(ws) + (int64_t)rd.O * rd.N * rd.M);
-    doppler<T, false>(ws, rd, pw, nullptr, s);
+    RadarDev all = rd;                 // every group's channels in one pass
+    all.O = rd.O * groups;
+    range_fft<T>(adc, all, ws, s);
+    T *pw = reinterpret_cast<T *>(reinterpret_cast<C *>(ws) + (int64_t)all.O * rd.N * rd.M);
+    doppler<T, false>(ws, all, pw, nullptr, s);
     const int64_t MN = (int64_t)rd.M * rd.N;
-    rdm_sum_kernel<T><<<(unsigned int)((MN + 255) / 256), 256, 0, s>>>(pw, rd.O, MN, rdm);
+    rdm_sum_kernel<T><<<(unsigned int)((MN * groups + 255) / 256), 256, 0, s>>>(pw, rd.O, MN,
+                                                                               groups, rdm);
 }
 
 template <typename T>
@@ -270,6 +348,43 @@ static void run_rdm_cube(const void *adc, const RadarDev &rd, void *X, void *cub
         reinterpret_cast<const C *>(cube), rd.O, MN, rdm);
 }
 
+template <typename T>
+static void run_rdm_adjoint(const void *adc, const float *grad_rdm, const RadarDev &rd,
+                            int groups, void *X, void *cube, float *rdm, void *grad_adc,
+                            cudaStream_t s)
+{
+    using C = typename Cplx<T>::type;
+    RadarDev all = rd;
+    all.O = rd.O * groups;
+    const int M = rd.M, N = rd.N;
+    // forward cube Y (and the RDM, unused) into `cube`
+    range_fft<T>(adc, all, X, s);
+    doppler<T, true>(X, all, nullptr, cube, s);
+    const int RB = rdm_rb(N, M);
+    const size_t sm2 = (size_t)(2 * RB * N + tw_len(N)) * sizeof(C);
+    cudaFuncSetAttribute(doppler_adjoint_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sm2);
+    doppler_adjoint_kernel<T><<<dim3((unsigned int)(M / RB), (unsigned int)all.O), 256, sm2, s>>>(
+        reinterpret_cast<const C *>(cube), grad_rdm, rd.O, N, M, RB, rd.window,
+        reinterpret_cast<C *>(X));
+    const size_t sm1 = (size_t)(2 * M + tw_len(M)) * sizeof(C);
+    const int t1 = M / 2 < 1024 ? (M / 2 < 32 ? 32 : M / 2) : 1024;
+    cudaFuncSetAttribute(range_adjoint_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sm1);
+    range_adjoint_kernel<T><<<(unsigned int)((int64_t)all.O * N), t1, sm1, s>>>(
+        reinterpret_cast<const C *>(X), M, rd.window, reinterpret_cast<C *>(grad_adc));
+    (void)rdm;
+}
+
+void launch_rdm_adjoint(const void *adc, int dtype, const float *grad_rdm, const RadarDev &rd,
+                        int groups, void *X, void *cube, void *grad_adc, cudaStream_t s)
+{
+    if (dtype == BART_C64)
+        run_rdm_adjoint<float>(adc, grad_rdm, rd, groups, X, cube, nullptr, grad_adc, s);
+    else
+        run_rdm_adjoint<double>(adc, grad_rdm, rd, groups, X, cube, nullptr, grad_adc, s);
+}
+
 void launch_rdm_cube(const void *adc, int dtype, const RadarDev &rd, void *X, void *cube,
                      float *rdm, cudaStream_t s)
 {
@@ -277,11 +392,11 @@ void launch_rdm_cube(const void *adc, int dtype, const RadarDev &rd, void *X, vo
     else run_rdm_cube<double>(adc, rd, X, cube, rdm, s);
 }
 
-void launch_rdm(const void *adc, int dtype, const RadarDev &rd, void *ws, float *rdm,
+void launch_rdm(const void *adc, int dtype, const RadarDev &rd, int groups, void *ws, float *rdm,
                 cudaStream_t s)
 {
-    if (dtype == BART_C64) run_rdm<float>(adc, rd, ws, rdm, s);
-    else run_rdm<double>(adc, rd, ws, rdm, s);
+    if (dtype == BART_C64) run_rdm<float>(adc, rd, groups, ws, rdm, s);
+    else run_rdm<double>(adc, rd, groups, ws, rdm, s);
 }
 
 // -------------------------------------------------------------------------

@@ -136,6 +136,13 @@ __global__ void build_facets_kernel(const MeshDesc *__restrict__ meshes,
     else if (threadIdx.x < 6) atomicMax(&bounds[threadIdx.x], s_b[threadIdx.x]);
 }
 
+const void *build_facets_kernel_fn(int *t0_arg_index, int *n_args)
+{
+    *t0_arg_index = 4;      // meshes, insts, n_inst, F, t0, tri64, tri32, c64, fac, aabb,
+    *n_args = 12;           // vel32, bounds
+    return reinterpret_cast<const void *>(build_facets_kernel);
+}
+
 void launch_build_facets(const MeshDesc *meshes, const InstDev *insts, int n_inst, int64_t F,
                          double t0, double *tri64, float *tri32, double *c64, FacetRec *fac,
                          float *aabb, float *vel32, unsigned int *bounds, cudaStream_t s)
@@ -302,35 +309,45 @@ void radix_sort_pairs(uint32_t *keys, int32_t *vals, uint32_t *keys_tmp, int32_t
 // -------------------------------------------------------------------------
 // Karras hierarchy
 // -------------------------------------------------------------------------
-__device__ __forceinline__ int delta(const uint32_t *keys, int64_t n, int64_t i, int64_t j)
+// Common-prefix length of sorted leaves i and j (-1 outside [0, n)).  With
+// batched scenes the key is (scene, Morton code, index): leaves of
+// different scenes compare on the scene id alone (0..31), so every scene's
+// leaves form one subtree; equal codes fall back to the index.
+__device__ __forceinline__ int delta(const uint32_t *keys, const uint32_t *scene, int64_t n,
+                                     int64_t i, int64_t j)
 {
     if (j < 0 || j >= n) return -1;
+    if (scene) {
+        const uint32_t sa = scene[i], sb = scene[j];
+        if (sa != sb) return __clz((int)(sa ^ sb));
+    }
     const uint32_t a = keys[i], b = keys[j];
-    if (a == b) return 32 + __clz((int)(i ^ j));      // index tie-break for equal codes
-    return __clz((int)(a ^ b));
+    if (a == b) return 64 + __clz((int)(i ^ j));      // index tie-break for equal codes
+    return 32 + __clz((int)(a ^ b));
 }
 
 __global__ void lbvh_build_kernel(const uint32_t *__restrict__ keys,
+                                  const uint32_t *__restrict__ scene,
                                   const int32_t *__restrict__ vals, int64_t n,
                                   BvhNode *__restrict__ nodes, int32_t *__restrict__ parent,
-                                  int32_t *__restrict__ leaf_parent)
+                                  int32_t *__restrict__ leaf_parent, int32_t *__restrict__ root)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n - 1) return;
-    const int d = (delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
-    const int dmin = delta(keys, n, i, i - d);
+    const int d = (delta(keys, scene, n, i, i + 1) - delta(keys, scene, n, i, i - 1)) >= 0 ? 1 : -1;
+    const int dmin = delta(keys, scene, n, i, i - d);
     int64_t lmax = 2;
-    while (delta(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    while (delta(keys, scene, n, i, i + lmax * d) > dmin) lmax <<= 1;
     int64_t l = 0;
     for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
-        if (delta(keys, n, i, i + (l + t) * d) > dmin) l += t;
+        if (delta(keys, scene, n, i, i + (l + t) * d) > dmin) l += t;
     const int64_t j = i + l * d;
-    const int dnode = delta(keys, n, i, j);
+    const int dnode = delta(keys, scene, n, i, j);
     int64_t sp = 0;
     int64_t t = l;
     do {
         t = (t + 1) >> 1;
-        if (delta(keys, n, i, i + (sp + t) * d) > dnode) sp += t;
+        if (delta(keys, scene, n, i, i + (sp + t) * d) > dnode) sp += t;
     } while (t > 1);
     const int64_t gamma = i + sp * d + (d < 0 ? -1 : 0);
     const int64_t lo = i < j ? i : j, hi = i < j ? j : i;
@@ -352,6 +369,12 @@ __global__ void lbvh_build_kernel(const uint32_t *__restrict__ keys,
     nodes[i].left = left;
     nodes[i].right = right;
     if (i == 0) parent[0] = -1;
+    if (scene) {
+        // the node covering exactly one scene's leaves is that scene's root
+        const uint32_t sc = scene[lo];
+        if (scene[hi] == sc && (lo == 0 || scene[lo - 1] != sc) && (hi == n - 1 || scene[hi + 1] != sc))
+            root[sc] = (int32_t)i;
+    }
 }
 
 void launch_lbvh_build(const uint32_t *keys, const int32_t *vals, int64_t n, BvhNode *nodes,
@@ -359,8 +382,71 @@ void launch_lbvh_build(const uint32_t *keys, const int32_t *vals, int64_t n, Bvh
 {
     if (n < 2) return;
     const int T = 256;
-    lbvh_build_kernel<<<(unsigned int)((n - 1 + T - 1) / T), T, 0, s>>>(keys, vals, n, nodes,
-                                                                       parent, leaf_parent);
+    lbvh_build_kernel<<<(unsigned int)((n - 1 + T - 1) / T), T, 0, s>>>(
+        keys, nullptr, vals, n, nodes, parent, leaf_parent, nullptr);
+}
+
+// scene of each sorted leaf: facets [foff[b], foff[b+1]) belong to scene b
+__global__ void scene_keys_kernel(const int32_t *__restrict__ vals, int64_t n,
+                                  const int64_t *__restrict__ foff, int B,
+                                  uint32_t *__restrict__ skeys)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t f = vals[i];
+    int lo = 0, hi = B - 1;                 // last scene with foff <= f
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (foff[mid] <= f) lo = mid;
+        else hi = mid - 1;
+    }
+    skeys[i] = (uint32_t)lo;
+}
+
+__global__ void gather_keys_kernel(const int32_t *__restrict__ vals, int64_t n,
+                                   const uint32_t *__restrict__ by_facet, uint32_t *__restrict__ keys)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) keys[i] = by_facet[vals[i]];
+}
+
+// one-facet scenes have their leaf as root; the others get theirs from the build
+__global__ void scene_root_init_kernel(const int64_t *__restrict__ foff, int B,
+                                       int32_t *__restrict__ root)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < B) root[b] = foff[b + 1] - foff[b] == 1 ? ~(int32_t)foff[b] : 0;
+}
+
+void launch_lbvh_batched(const FacetRec *fac, int64_t F, const unsigned int *bounds,
+                         const int64_t *foff, int B, uint32_t *keys, int32_t *vals,
+                         uint32_t *keys_tmp, int32_t *vals_tmp, uint32_t *temp, uint32_t *mkeys,
+                         uint32_t *skeys, BvhNode *nodes, int32_t *parent, int32_t *leaf_parent,
+                         int32_t *root, cudaStream_t s)
+{
+    const int T = 256;
+    const unsigned int G = (unsigned int)((F + T - 1) / T);
+    launch_morton(fac, F, bounds, keys, vals, s);
+    cudaMemcpyAsync(mkeys, keys, (size_t)F * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+    radix_sort_pairs(keys, vals, keys_tmp, vals_tmp, temp, F, 30, s);
+    scene_keys_kernel<<<G, T, 0, s>>>(vals, F, foff, B, skeys);
+    int sbits = 1;
+    while ((1 << sbits) < B) ++sbits;
+    radix_sort_pairs(skeys, vals, keys_tmp, vals_tmp, temp, F, sbits, s);   // stable
+    gather_keys_kernel<<<G, T, 0, s>>>(vals, F, mkeys, keys);
+    scene_root_init_kernel<<<(B + T - 1) / T, T, 0, s>>>(foff, B, root);
+    if (F < 2) return;
+    lbvh_build_kernel<<<(unsigned int)((F - 1 + T - 1) / T), T, 0, s>>>(
+        keys, skeys, vals, F, nodes, parent, leaf_parent, root);
+}
+
+int lbvh_batched_launches(int B)
+{
+    int sbits = 1;
+    while ((1 << sbits) < B) ++sbits;
+    int p2 = (sbits + 7) / 8;
+    if (p2 & 1) ++p2;
+    return 1 + 3 * 4 + 1 + 3 * p2 + 1 + 1 + 1;
 }
 
 // bottom-up refit: each leaf writes its box into its parent's slot; the

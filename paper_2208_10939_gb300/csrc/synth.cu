@@ -43,15 +43,9 @@
 #include <algorithm>
 
 #include "bart_internal.cuh"
+#include "record_fp64.cuh"
 
 namespace bart {
-
-// 1/n! for n = 0..17
-__constant__ double c_inv_fact[18] = {
-    1.0, 1.0, 1.0 / 2, 1.0 / 6, 1.0 / 24, 1.0 / 120, 1.0 / 720, 1.0 / 5040, 1.0 / 40320,
-    1.0 / 362880, 1.0 / 3628800, 1.0 / 39916800, 1.0 / 479001600, 1.0 / 6227020800.0,
-    1.0 / 87178291200.0, 1.0 / 1307674368000.0, 1.0 / 20922789888000.0,
-    1.0 / 355687428096000.0};
 
 // -------------------------------------------------------------------------
 // kinematics (FP64): per antenna a, facet k lit from a, chirp n of the chunk
@@ -235,7 +229,8 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
     const int nc = A.nc;
     const int ngroups = (nc + RPW - 1) / RPW;
     const float fact_lim = kFactMaxRot / (6.283185307179586f * (float)(S > 1 ? S - 1 : 1));
-    const int total = A.item_off[O];
+    const int VO = A.VO;
+    const int total = A.item_off[VO];
     unsigned long long nV = 0, nSr = 0, nE = 0;
 
     // persistent warps: each pulls (channel, chirp group, sample segment,
@@ -245,16 +240,17 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
     if (lane == 0) item = atomicAdd(A.item_counter, 1);
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= total) break;
-    int clo = 0, chi = O - 1;                  // channel: last o with item_off[o] <= item
+    int clo = 0, chi = VO - 1;                 // row: last v with item_off[v] <= item
     while (clo < chi) {
         const int mid = (clo + chi + 1) >> 1;
         if (A.item_off[mid] <= item) clo = mid;
         else chi = mid - 1;
     }
-    const int o = clo;
-    const int cnt = A.vis_cnt[o];
+    const int vrow = clo;                      // scene * O + channel
+    const int o = vrow % O;
+    const int cnt = A.vcnt[vrow];
     const int ipu = max(1, ((cnt + 31) / 32 + TPI - 1) / TPI);
-    const int local = item - A.item_off[o];
+    const int local = item - A.item_off[vrow];
     const int jchunk = local % ipu;
     const int rowseg = local / ipu;
     const int seg = rowseg % W, grp = rowseg / W;
@@ -287,7 +283,7 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
         sAcc[warp][3][j][lane] = 0.f;
     }
 
-    const int32_t *list = A.vis_idx + (int64_t)o * F;
+    const int32_t *list = A.vis_idx + (int64_t)o * F + (A.vstart ? A.vstart[vrow] : 0);
     const float4 *kin_t = A.kin + ((int64_t)nl * AA + tx) * F;
     const float4 *kin_r = A.kin + ((int64_t)nl * AA + P + rx) * F;
 
@@ -622,28 +618,54 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
     }
 }
 
-// item table: channel o owns ipu_o = ceil(ceil(cnt_o / 32) / TPI) record
-// chunks (at least one) per (chirp, sample segment); item_off is their prefix
-__global__ void synth_items_kernel(const int32_t *__restrict__ vis_cnt, int O, int TPI, int nc,
+// item table: row v (scene * O + channel) owns ipu_v = ceil(ceil(cnt_v / 32)
+// / TPI) record chunks (at least one) per (chirp group, sample segment);
+// item_off is their prefix (one block-wide scan)
+__global__ void synth_items_kernel(const int32_t *__restrict__ vcnt, int VO, int TPI, int nc,
                                    int RPW, int W, int32_t *__restrict__ item_off, int *counter)
 {
-    if (threadIdx.x != 0) return;
-    int run = 0;
+    __shared__ int s_warp[32];
+    __shared__ int s_run;
     const int ngroups = (nc + RPW - 1) / RPW;
-    for (int o = 0; o < O; ++o) {
-        item_off[o] = run;
-        const int ipu = max(1, ((vis_cnt[o] + 31) / 32 + TPI - 1) / TPI);
-        run += ipu * ngroups * W;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (threadIdx.x == 0) s_run = 0;
+    __syncthreads();
+    for (int v0 = 0; v0 < VO; v0 += blockDim.x) {
+        const int v = v0 + threadIdx.x;
+        const int mine = v < VO ? max(1, ((vcnt[v] + 31) / 32 + TPI - 1) / TPI) * ngroups * W : 0;
+        int x = mine;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, off);
+            if (lane >= off) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int w = lane < nw ? s_warp[lane] : 0;
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, w, off);
+                if (lane >= off) w += y;
+            }
+            if (lane < nw) s_warp[lane] = w;
+        }
+        __syncthreads();
+        const int before = s_run + (warp > 0 ? s_warp[warp - 1] : 0) + x - mine;
+        if (v < VO) item_off[v] = before;
+        __syncthreads();
+        if (threadIdx.x == 0) s_run += s_warp[nw - 1];
+        __syncthreads();
     }
-    item_off[O] = run;
-    *counter = 0;
+    if (threadIdx.x == 0) {
+        item_off[VO] = s_run;
+        *counter = 0;
+    }
 }
 
 // sums the item partials of each (channel, chirp, sample) in item order with
 // Kahan compensation, and applies C / k_m^2 = out_scale / kappa_m^2
 __global__ void synth_reduce_kernel(const float2 *__restrict__ partial,
                                     const int32_t *__restrict__ item_off,
-                                    const int32_t *__restrict__ vis_cnt, int TPI, int W, int S,
+                                    const int32_t *__restrict__ vcnt, int TPI, int W, int S,
                                     int LPR, int O, int N, int M, int n0, float out_scale,
                                     float kap_step, void *out, int out_c64)
 {
@@ -654,7 +676,7 @@ __global__ void synth_reduce_kernel(const float2 *__restrict__ partial,
     const int grp = nl / RPW, row = nl % RPW;
     const int seg = m / (LPR * S), ml = m % (LPR * S);
     const int slot = (row * LPR + ml / S) * S + ml % S;     // lane * S + j
-    const int ipu = max(1, ((vis_cnt[o] + 31) / 32 + TPI - 1) / TPI);
+    const int ipu = max(1, ((vcnt[o] + 31) / 32 + TPI - 1) / TPI);
     const int64_t it0 = (int64_t)item_off[o] + (int64_t)(grp * W + seg) * ipu;
     const float2 *src = partial + it0 * (32 * S) + slot;
     float sr = 0.f, si = 0.f, cr = 0.f, ci = 0.f;
@@ -715,30 +737,42 @@ int synth_tiles_per_item(int64_t F) { return (int)std::max<int64_t>(16, ((F + 31
 
 // lane layout of the mixed kernel: S samples per lane, LPR lanes per chirp
 // row, W warps per row.  16 samples per lane halve the per-lane start-up
-// work (MUFU start phasors, cubic coefficients) against 8.
+// work (MUFU start phasors, cubic coefficients) against 8; S_req = 8 asks
+// for the 8-sample layout where M allows it (autotuner candidate).
 struct MixLayout {
     int S, LPR, W;
 };
-static MixLayout mix_layout(int M)
+static MixLayout mix_layout(int M, int S_req)
 {
+    if (S_req == 8) {
+        if (M <= 256 && 256 % M == 0) return {8, M / 8, 1};
+        if (M % 256 == 0) return {8, 32, M / 256};
+    }
     if (M <= 512 && 512 % M == 0) return {16, M / 16, 1};
     if (M % 512 == 0) return {16, 32, M / 512};
     const int S = samples_per_lane(M);
     return {S, 32, M / (32 * S)};
 }
 
-int64_t synth_max_items(int64_t F, const RadarDev &rd, int nc)
+int synth_layout_samples(int M, int S_req) { return mix_layout(M, S_req).S; }
+
+int64_t synth_max_items(const int64_t *scene_F, int n_scene, const RadarDev &rd, int nc, int tpi,
+                        int S_req)
 {
-    const MixLayout L = mix_layout(rd.M);
+    const MixLayout L = mix_layout(rd.M, S_req);
     const int RPW = 32 / L.LPR;
-    const int64_t tiles = (F + 31) / 32, TPI = synth_tiles_per_item(F);
-    return (int64_t)rd.O * std::max<int64_t>(1, (tiles + TPI - 1) / TPI) *
-           ((nc + RPW - 1) / RPW) * L.W;
+    int64_t per_group = 0;
+    for (int b = 0; b < n_scene; ++b) {
+        const int64_t tiles = (scene_F[b] + 31) / 32;
+        per_group += std::max<int64_t>(1, (tiles + tpi - 1) / tpi);
+    }
+    return (int64_t)rd.O * per_group * ((nc + RPW - 1) / RPW) * L.W;
 }
 
-int64_t synth_partial_words(int64_t F, const RadarDev &rd, int nc)
+int64_t synth_partial_words(const int64_t *scene_F, int n_scene, const RadarDev &rd, int nc,
+                            int tpi, int S_req)
 {
-    return synth_max_items(F, rd, nc) * 32 * mix_layout(rd.M).S;
+    return synth_max_items(scene_F, n_scene, rd, nc, tpi, S_req) * 32 * mix_layout(rd.M, S_req).S;
 }
 
 template <int S, int LPR> static int mixed_grid(int64_t items)
@@ -767,11 +801,10 @@ void launch_synth_mixed(const SynthArgs &a0, cudaStream_t s)
     SynthArgs a = a0;
     const MixConsts K = mix_consts(a.rd);
     const int M = a.rd.M;
-    const MixLayout L = mix_layout(M);
-    a.tiles_per_item = synth_tiles_per_item(a.F);
-    synth_items_kernel<<<1, 32, 0, s>>>(a.vis_cnt, a.rd.O, a.tiles_per_item, a.nc, 32 / L.LPR,
-                                        L.W, a.item_off, a.item_counter);
-    const int64_t items = synth_max_items(a.F, a.rd, a.nc);
+    const MixLayout L = mix_layout(M, a.layout_S);
+    synth_items_kernel<<<1, 1024, 0, s>>>(a.vcnt, a.VO, a.tiles_per_item, a.nc, 32 / L.LPR,
+                                          L.W, a.item_off, a.item_counter);
+    const int64_t items = a.max_items;
     if (L.S == 16) {
         switch (L.LPR) {
         case 2: run_mixed<16, 2>(a, K, L.W, items, s); break;
@@ -780,16 +813,22 @@ void launch_synth_mixed(const SynthArgs &a0, cudaStream_t s)
         case 16: run_mixed<16, 16>(a, K, L.W, items, s); break;
         default: run_mixed<16, 32>(a, K, L.W, items, s); break;
         }
+    } else if (L.S == 8) {
+        switch (L.LPR) {
+        case 4: run_mixed<8, 4>(a, K, L.W, items, s); break;
+        case 8: run_mixed<8, 8>(a, K, L.W, items, s); break;
+        case 16: run_mixed<8, 16>(a, K, L.W, items, s); break;
+        default: run_mixed<8, 32>(a, K, L.W, items, s); break;
+        }
     } else {
         switch (L.S) {
-        case 8: run_mixed<8, 32>(a, K, L.W, items, s); break;
         case 4: run_mixed<4, 32>(a, K, L.W, items, s); break;
         case 2: run_mixed<2, 32>(a, K, L.W, items, s); break;
         default: run_mixed<1, 32>(a, K, L.W, items, s); break;
         }
     }
-    dim3 rg((unsigned int)((M + 255) / 256), (unsigned int)a.nc, (unsigned int)a.rd.O);
-    synth_reduce_kernel<<<rg, 256, 0, s>>>(a.partial, a.item_off, a.vis_cnt, a.tiles_per_item, L.W,
+    dim3 rg((unsigned int)((M + 255) / 256), (unsigned int)a.nc, (unsigned int)a.VO);
+    synth_reduce_kernel<<<rg, 256, 0, s>>>(a.partial, a.item_off, a.vcnt, a.tiles_per_item, L.W,
                                            L.S, L.LPR, a.rd.O, a.rd.N, M, a.n0, K.out_scale,
                                            K.kap_step, a.out, a.out_c64);
 }
@@ -816,8 +855,9 @@ synth_fp64_kernel(SynthArgs A, int W)
     const int N = A.rd.N;
     const int64_t unit = gw / W;
     const int seg = (int)(gw % W);
-    if (unit >= (int64_t)A.rd.O * N) return;
-    const int o = (int)(unit / N), n = (int)(unit % N);
+    if (unit >= (int64_t)A.VO * N) return;
+    const int vrow = (int)(unit / N), n = (int)(unit % N);   // scene * O + channel
+    const int o = vrow % A.rd.O;
     const int P = A.rd.P, Q = A.rd.Q;
     const int tx = o / Q, rx = o % Q;
     const int64_t F = A.F;
@@ -833,8 +873,8 @@ synth_fp64_kernel(SynthArgs A, int W)
 #pragma unroll
     for (int j = 0; j < S; ++j) accr[j] = acci[j] = 0.0;
 
-    const int32_t *list = A.vis_idx + (int64_t)o * F;
-    const int cnt = A.vis_cnt[o];
+    const int32_t *list = A.vis_idx + (int64_t)o * F + (A.vstart ? A.vstart[vrow] : 0);
+    const int cnt = A.vcnt[vrow];
     unsigned long long nV = 0, nSr = 0, nE = 0;
 
     for (int base = 0; base < cnt; base += 32) {
@@ -846,89 +886,19 @@ synth_fp64_kernel(SynthArgs A, int W)
             const int inst = A.fac[k].inst;
             const double vel[3] = {A.vel64[3 * inst], A.vel64[3 * inst + 1],
                                    A.vel64[3 * inst + 2]};
-            double cc[3], dv[9];
-            for (int r = 0; r < 3; ++r) cc[r] = A.c64[3 * k + r];
-            for (int i = 0; i < 9; ++i) dv[i] = A.tri64[9 * k + i] - cc[i % 3];
-            for (int r = 0; r < 3; ++r) cc[r] += vel[r] * tn;
-            const double e1[3] = {dv[3] - dv[0], dv[4] - dv[1], dv[5] - dv[2]};
-            const double e2[3] = {dv[6] - dv[0], dv[7] - dv[1], dv[8] - dv[2]};
-            double nn[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
-                            e1[0] * e2[1] - e1[1] * e2[0]};
-            const double nl = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
-            const double area = 0.5 * nl;
-            for (int r = 0; r < 3; ++r) nn[r] /= nl;
-            double dt[3], dr[3];
-            for (int r = 0; r < 3; ++r) {
-                dt[r] = ptx[r] - cc[r];
-                dr[r] = prx[r] - cc[r];
-            }
-            const double Rt2 = dt[0] * dt[0] + dt[1] * dt[1] + dt[2] * dt[2];
-            const double Rr2 = dr[0] * dr[0] + dr[1] * dr[1] + dr[2] * dr[2];
-            const double Rt = sqrt(Rt2), Rr = sqrt(Rr2);
-            double b[3];
-            for (int r = 0; r < 3; ++r) b[r] = dt[r] / Rt + dr[r] / Rr;
-            const double ok = 0.5 * (nn[0] * b[0] + nn[1] * b[1] + nn[2] * b[2]);
-            const double g = (double)A.fac[k].rho * ok / (Rt * Rr);
-            R.qt[0] = Rt2;
-            R.qr[0] = Rr2;
-            if (A.rd.intra) {
-                R.qt[1] = -2.0 * (dt[0] * vel[0] + dt[1] * vel[1] + dt[2] * vel[2]);
-                R.qr[1] = -2.0 * (dr[0] * vel[0] + dr[1] * vel[1] + dr[2] * vel[2]);
-                R.qt[2] = vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2];
-            } else {
-                R.qt[1] = R.qr[1] = R.qt[2] = 0.0;
-            }
-            const double bn = b[0] * nn[0] + b[1] * nn[1] + b[2] * nn[2];
-            const double bt[3] = {b[0] - bn * nn[0], b[1] - bn * nn[1], b[2] - bn * nn[2]};
-            double u[3];
-            for (int v = 0; v < 3; ++v)
-                u[v] = bt[0] * dv[3 * v] + bt[1] * dv[3 * v + 1] + bt[2] * dv[3 * v + 2];
-            const double umin = fmin(fmin(u[0], u[1]), u[2]);
-            const double umax = fmax(fmax(u[0], u[1]), u[2]);
-            const double dmin = fmin(fmin(fabs(u[0] - u[1]), fabs(u[1] - u[2])),
-                                     fabs(u[0] - u[2]));
-            const double A2 = 2.0 * area * g;
-            if (kmax * (umax - umin) < kSeriesKD) {
-                cls = R.kind = kRecSeries;
-                const double ub = (u[0] + u[1] + u[2]) / 3.0;
-                R.d[0] = ub;
-                const double y0 = k0 * (u[0] - ub), y1 = k0 * (u[1] - ub), y2 = k0 * (u[2] - ub);
-                const double e2s = y0 * y1 + y0 * y2 + y1 * y2, e3s = y0 * y1 * y2;
-                double h[kSeriesTerms];
-                h[0] = 1.0;
-                h[1] = 0.0;
-                h[2] = -e2s;
-                for (int p = 3; p < kSeriesTerms; ++p) h[p] = -e2s * h[p - 2] + e3s * h[p - 3];
-                const double sc = A2 * k0 * k0;
-                for (int i = 0; i < 8; ++i)
-                    R.d[1 + i] = ((i & 1) ? -sc : sc) * h[2 * i] * c_inv_fact[2 * i + 2];
-                for (int i = 0; i < 7; ++i)
-                    R.d[9 + i] = ((i & 1) ? sc : -sc) * h[2 * i + 1] * c_inv_fact[2 * i + 3];
-            } else if (kmax * dmin < kEdgeKd) {
-                cls = R.kind = kRecEdge;
-                const double bt2 = bt[0] * bt[0] + bt[1] * bt[1] + bt[2] * bt[2];
-                const double nxb[3] = {nn[1] * bt[2] - nn[2] * bt[1], nn[2] * bt[0] - nn[0] * bt[2],
-                                       nn[0] * bt[1] - nn[1] * bt[0]};
-                int flags = 0;
-                for (int i = 0; i < 3; ++i) {
-                    const int i1 = (i + 1) % 3;
-                    const double e[3] = {dv[3 * i1] - dv[3 * i], dv[3 * i1 + 1] - dv[3 * i + 1],
-                                         dv[3 * i1 + 2] - dv[3 * i + 2]};
-                    const double gam = 0.5 * (u[i1] - u[i]);
-                    R.d[3 * i] = 0.5 * (u[i] + u[i1]);
-                    R.d[3 * i + 1] = k0 * gam;
-                    R.d[3 * i + 2] = k0 * g * (e[0] * nxb[0] + e[1] * nxb[1] + e[2] * nxb[2]) / bt2;
-                    if (kmax * fabs(gam) < kSincSeries) flags |= 1 << i;
-                }
-                R.flags = flags;
-            } else {
-                cls = R.kind = kRecVertex;
-                for (int v = 0; v < 3; ++v) {
-                    const double ua = u[v], ub_ = u[(v + 1) % 3], uc = u[(v + 2) % 3];
-                    R.d[v] = ua;
-                    R.d[3 + v] = -A2 / ((ua - ub_) * (ua - uc));
-                }
-            }
+            double tri[9], c0[3], rec[kRecEntries];
+            for (int i = 0; i < 9; ++i) tri[i] = A.tri64[9 * k + i];
+            for (int r = 0; r < 3; ++r) c0[r] = A.c64[3 * k + r];
+            int flags = 0;
+            cls = R.kind = build_record<double>(tri, c0, vel, tn, ptx, prx, (double)A.fac[k].rho,
+                                                A.rd.intra, k0, kmax, rec, &flags);
+            R.flags = flags;
+            R.qt[0] = rec[0];
+            R.qt[1] = rec[1];
+            R.qt[2] = rec[2];
+            R.qr[0] = rec[3];
+            R.qr[1] = rec[4];
+            for (int i = 0; i < 22; ++i) R.d[i] = rec[kRecD + i];
         }
         __syncwarp();
         unsigned int mask = __ballot_sync(0xffffffffu, valid);
@@ -999,7 +969,7 @@ synth_fp64_kernel(SynthArgs A, int W)
         atomicAdd(A.counters + 2, nE);
     }
     const double camp = 2.0 * sqrt(kPi) / pow(4.0 * kPi, 1.5);
-    const int64_t row = ((int64_t)o * N + n) * A.rd.M + m0;
+    const int64_t row = ((int64_t)vrow * N + n) * A.rd.M + m0;
 #pragma unroll
     for (int j = 0; j < S; ++j) {
         const double fm = f0 + mu * (double)(m0 + j) / fs;
@@ -1019,7 +989,7 @@ void launch_synth_fp64(const SynthArgs &a, cudaStream_t s)
     const int M = a.rd.M;
     const int S = samples_per_lane(M);
     const int W = M / (32 * S);
-    const int64_t warps = (int64_t)a.rd.O * a.rd.N * W;
+    const int64_t warps = (int64_t)a.VO * a.rd.N * W;
     const unsigned int grid = (unsigned int)((warps + kF64Warps - 1) / kF64Warps);
     switch (S) {
     case 8: synth_fp64_kernel<8><<<grid, kF64Warps * 32, 0, s>>>(a, W); break;

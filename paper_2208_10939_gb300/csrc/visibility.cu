@@ -140,7 +140,7 @@ constexpr int kStack = 64;
 __global__ void __launch_bounds__(128)
 visibility_kernel(const double *__restrict__ tri64, const float4 *__restrict__ tri32,
                   const double *__restrict__ c64, const BvhNode *__restrict__ nodes,
-                  const int32_t *__restrict__ order, int64_t F, RadarDev rd,
+                  const int32_t *__restrict__ order, int64_t F, RadarDev rd, SceneSplit sc,
                   uint8_t *__restrict__ state, unsigned long long *n_graze, int *status)
 {
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -168,7 +168,18 @@ visibility_kernel(const double *__restrict__ tri64, const float4 *__restrict__ t
         } else {
             bool graze = fabs(cosang) < kEpsFace;
             bool hit = false;
-            if (F >= 2) {
+            // traversal root: the whole tree, or the subtree of the facet's scene
+            int root = F >= 2 ? 0 : -1;
+            if (sc.B > 1) {
+                int lo = 0, hi = sc.B - 1;          // last scene with foff <= k
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (sc.foff[mid] <= k) lo = mid;
+                    else hi = mid - 1;
+                }
+                root = sc.root[lo];             // < 0: a one-facet scene, nothing to meet
+            }
+            if (root >= 0) {
                 const float o[3] = {(float)c[0], (float)c[1], (float)c[2]};
                 const float Df[3] = {(float)D[0], (float)D[1], (float)D[2]};
                 const float Dm = fmaxf(fmaxf(fabsf(Df[0]), fabsf(Df[1])), fabsf(Df[2]));
@@ -181,7 +192,7 @@ visibility_kernel(const double *__restrict__ tri64, const float4 *__restrict__ t
                 }
                 int stack[kStack];
                 int sp = 0;
-                stack[sp++] = 0;
+                stack[sp++] = root;
                 while (sp > 0 && !hit) {
                     const BvhNode nd = nodes[stack[--sp]];
                     const bool hl = slab_hit(nd.lmin, nd.lmax, o, inv);
@@ -222,12 +233,13 @@ visibility_kernel(const double *__restrict__ tri64, const float4 *__restrict__ t
 
 void launch_visibility(const double *tri64, const float *tri32, const double *c64,
                        const BvhNode *nodes, const int32_t *order, int64_t F, const RadarDev &rd,
-                       uint8_t *state, unsigned long long *n_graze, int *status, cudaStream_t s)
+                       const SceneSplit &sc, uint8_t *state, unsigned long long *n_graze,
+                       int *status, cudaStream_t s)
 {
     const int T = 128;
     dim3 grid((unsigned int)((F + T - 1) / T), (unsigned int)rd.A);
     visibility_kernel<<<grid, T, 0, s>>>(tri64, reinterpret_cast<const float4 *>(tri32), c64,
-                                         nodes, order, F, rd, state, n_graze, status);
+                                         nodes, order, F, rd, sc, state, n_graze, status);
 }
 
 // -------------------------------------------------------------------------
@@ -318,6 +330,42 @@ void launch_compact(const uint8_t *state, int64_t F, const RadarDev &rd, int32_t
     compact_scan_kernel<<<L, 32, 0, s>>>(blk_cnt, nblk, vis_cnt);
     compact_write_kernel<<<grid, kCompactBlk, 0, s>>>(state, F, rd.O, rd.P, rd.Q, blk_cnt, nblk,
                                                       vis_idx);
+}
+
+// lists are ascending in facet index and scenes own consecutive facets, so
+// each (scene, channel) part of list o is one contiguous run
+__global__ void scene_lists_kernel(const int32_t *__restrict__ vis_idx,
+                                   const int32_t *__restrict__ vis_cnt, int64_t F, int O,
+                                   const int64_t *__restrict__ foff, int B,
+                                   int32_t *__restrict__ vstart, int32_t *__restrict__ vcnt)
+{
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= B * O) return;
+    const int b = v / O, o = v % O;
+    const int32_t *list = vis_idx + (int64_t)o * F;
+    const int n = vis_cnt[o];
+    int lim[2];
+    for (int e = 0; e < 2; ++e) {           // first entry with facet >= foff[b + e]
+        const int64_t key = foff[b + e];
+        int lo = 0, hi = n;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (list[mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        lim[e] = lo;
+    }
+    vstart[v] = lim[0];
+    vcnt[v] = lim[1] - lim[0];
+}
+
+void launch_scene_lists(const int32_t *vis_idx, const int32_t *vis_cnt, int64_t F, int O,
+                        const int64_t *foff, int B, int32_t *vstart, int32_t *vcnt,
+                        cudaStream_t s)
+{
+    const int T = 128;
+    scene_lists_kernel<<<(B * O + T - 1) / T, T, 0, s>>>(vis_idx, vis_cnt, F, O, foff, B, vstart,
+                                                         vcnt);
 }
 
 }  // namespace bart

@@ -45,11 +45,12 @@ def test_struct_layouts_match_c(tmp_path):
     prog = tmp_path / "sz.c"
     prog.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "bartsim.h"\n'
-        'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
+        'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
         ' sizeof(bart_instance), sizeof(bart_radar), sizeof(bart_stats),'
         ' offsetof(bart_radar, tx), offsetof(bart_instance, pos), sizeof(bart_timing),'
         ' offsetof(bart_timing, detect_ms), sizeof(bart_detect_cfg), sizeof(bart_point),'
-        ' offsetof(bart_point, r_bin));return 0;}\n')
+        ' offsetof(bart_point, r_bin), sizeof(bart_tune), offsetof(bart_tune, synthesis_ms));'
+        'return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)],
                    check=True)
@@ -59,7 +60,8 @@ def test_struct_layouts_match_c(tmp_path):
                     ctypes.sizeof(pkg.bart_stats), pkg.bart_radar.tx.offset,
                     pkg.bart_instance.pos.offset, ctypes.sizeof(pkg.bart_timing),
                     pkg.bart_timing.detect_ms.offset, ctypes.sizeof(pkg.bart_detect_cfg),
-                    ctypes.sizeof(pkg.bart_point), pkg.bart_point.r_bin.offset]
+                    ctypes.sizeof(pkg.bart_point), pkg.bart_point.r_bin.offset,
+                    ctypes.sizeof(pkg.bart_tune), pkg.bart_tune.synthesis_ms.offset]
 
 
 def test_version_and_error_string(lib):

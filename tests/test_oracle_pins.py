@@ -459,3 +459,28 @@ def test_point_cloud_recovers_target_position():
     assert abs(math.degrees(best[2]) - 30.0) < 3.0
     assert abs(best[1]) < 1e-9                                   # static
     assert abs(best[3] - best[0] * math.sin(best[2])) < 1e-9
+
+
+# ---------------------------------------------------------------------------
+# adjoint of the RDM
+# ---------------------------------------------------------------------------
+def test_rdm_adjoint_central_differences():
+    """dL/dx of L = sum(G * RDM(x)) against central differences of the RDM
+    route, on the real and imaginary part of sampled entries (odd and
+    non-power-of-two lengths included)."""
+    rng = np.random.default_rng(21)
+    for (O, N, M) in ((2, 8, 16), (3, 6, 12), (2, 5, 9)):
+        x = rng.normal(size=(O, N, M)) + 1j * rng.normal(size=(O, N, M))
+        G = rng.normal(size=(M, N))
+        grad = oracle.rdm_adjoint(x, G)
+        L = lambda z: float((G * oracle.range_doppler_map(z)).sum())
+        h = 1e-6
+        for _ in range(12):
+            o, n, m = rng.integers(O), rng.integers(N), rng.integers(M)
+            for part, unit in ((0, 1.0), (1, 1j)):
+                xp, xm = x.copy(), x.copy()
+                xp[o, n, m] += h * unit
+                xm[o, n, m] -= h * unit
+                fd = (L(xp) - L(xm)) / (2 * h)
+                an = grad[o, n, m].real if part == 0 else grad[o, n, m].imag
+                assert abs(fd - an) <= 1e-6 * (1 + abs(an)), (O, N, M, o, n, m, part, fd, an)
