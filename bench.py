@@ -38,6 +38,20 @@ UNIT = "terms/s"
 WORKLOAD = "moving sedan 20k tris, 3TXx4RX (12 ch), 128 chirps x 256 samples"
 FLOPS_PER_TERM = 30          # 3 vertex phasors x (rotation 6 + weighted accumulate 4)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x lanes x FMA x max clock
+# DRAM bytes (read + write) of one synthesis launch on this workload, from the
+# ncu capture summarised in profiles/synth_mixed_moving_sedan.md; valid only
+# while the kernel's sources hash to the value they had at the capture
+SYNTH_TRAFFIC = {"bytes": 258.733568e6 + 31.002368e6, "sources_sha256_16": "90bbc5b01ce3e19e"}
+SYNTH_SOURCES = ("synth.cu", "bart_internal.cuh", "record_fp64.cuh")
+
+
+def synth_traffic():
+    import hashlib
+    h = hashlib.sha256()
+    for f in SYNTH_SOURCES:
+        with open(os.path.join(ROOT, "paper_2208_10939_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return SYNTH_TRAFFIC["bytes"] if h.hexdigest()[:16] == SYNTH_TRAFFIC["sources_sha256_16"] else None
 
 
 def parse():
@@ -54,6 +68,8 @@ def parse():
                     help="dataset scenes (seeded, 1-8 vehicles, 5k-200k facets) for the "
                          "batched-vs-per-scene measurement; 0 skips it")
     ap.add_argument("--batch-size", type=int, default=8)
+    ap.add_argument("--adjoint-reps", type=int, default=1,
+                    help="timed runs of the perturbed-sedan gradient (0 skips)")
     return ap.parse_args()
 
 
@@ -192,14 +208,15 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
-def dataset_batch(pkg, sg, torch, dev, K: int, bsz: int) -> dict:
+def dataset_batch(pkg, sg, torch, dev, K: int, bsz: int, tri_min: int = 5_000,
+                  tri_max: int = 200_000) -> dict:
     """Dataset generation (seeded scenes of 1-8 vehicles, 5k-200k facets,
     radar as the sedan workload): scene-frames per second simulated one
     scene per frame call versus bsz scenes per call (bart_scene_partition),
     each including the instance-table upload, synthesis and RDM, meshes
     resident; then the autotuned layout, and a 4-frame time sequence of one
     batch replayed as a CUDA graph versus direct launches."""
-    scenes = [sg.batch_scene(i) for i in range(K)]
+    scenes = [sg.batch_scene(i, tri_min=tri_min, tri_max=tri_max) for i in range(K)]
     sim = pkg.Simulator(dev.index or 0)
     pkg.bart_mesh_clear(sim.ctx)
     placed = []
@@ -278,7 +295,8 @@ def dataset_batch(pkg, sg, torch, dev, K: int, bsz: int) -> dict:
     pkg.bart_set_graph(sim.ctx, False)
     sim.close()
     return {
-        "workload": f"{K} seeded dataset scenes (1-8 vehicles, 5k-200k facets, "
+        "workload": f"{K} seeded dataset scenes (1-8 vehicles, {tri_min // 1000}k-"
+                    f"{tri_max // 1000}k facets, "
                     f"mean {int(np.mean(facets))}), radar as the sedan workload, mixed path + RDM",
         "unit": "scene-frames/s",
         "per_scene": {"value": K / wall1, "device_s": dev1, "wall_s": wall1},
@@ -290,6 +308,64 @@ def dataset_batch(pkg, sg, torch, dev, K: int, bsz: int) -> dict:
         "sequence_4_frames": {"direct": len(g0) * len(seq) / direct_s,
                               "graph": len(g0) * len(seq) / graph_s},
     }
+
+
+def detect_timing(pkg, torch, sim, adc, stream, reps: int = 10) -> dict:
+    """CA-CFAR + angle spectrum + point records (bart_detect) on the timed
+    frame's ADC: device time per call (CUDA events), points found."""
+    cfg = pkg.make_detect_cfg(guard_r=2, guard_d=2, train_r=8, train_d=4, pfa=1e-6, angle_bins=512)
+    buf = torch.empty(65536 * pkg.POINT_DTYPE.itemsize, dtype=torch.uint8, device=adc.device)
+    n = pkg.bart_detect(sim.ctx, adc, cfg, buf)
+    ms = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pkg.bart_detect(sim.ctx, adc, cfg, buf, sync=False)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return {"ms": statistics.median(ms), "points": int(n), "angle_bins": 512,
+            "cfar": "guard 2x2, train 8x4, Pfa 1e-6"}
+
+
+def adjoint_timing(pkg, sg, torch, dev, reps: int) -> dict:
+    """Differentiable echo on the perturbed-sedan inverse problem: the
+    sedan as target, its copy with 5 mm vertex noise (seed 5) as the
+    variable, L = ||adc(v) - adc_target||^2; FP64 forward and adjoint times
+    (CUDA events) and gradient throughput in echo terms per second."""
+    from paper_2208_10939_gb300 import autograd as bag
+    s = pkg.Simulator(dev.index or 0)
+    try:
+        sc = sg.car_scene()
+        es = bag.EchoScene(s, sc)
+        v_true = es.vertex_tensor(sc, dev)
+        with torch.no_grad():
+            target = bag.echo(v_true, None, es).clone()
+        rng = np.random.default_rng(5)
+        v0 = v_true + torch.from_numpy(0.005 * rng.normal(size=tuple(v_true.shape))).to(dev)
+        st = pkg.bart_simulate_frame(s.ctx, 0.0, pkg.PATH_FP64, target.clone(), stats=True)
+        fwd, bwd = [], []
+        for _ in range(reps):
+            verts = v0.clone().requires_grad_(True)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record()
+            adc = bag.echo(verts, None, es)
+            loss = (adc - target).abs().pow(2).sum()
+            e1.record()
+            loss.backward()
+            e2.record()
+            e2.synchronize()
+            fwd.append(e0.elapsed_time(e1))
+            bwd.append(e0.elapsed_time(e2) - e0.elapsed_time(e1))
+        terms = st["n_terms"]
+        return {"workload": "sedan 20k tris, target vs 5 mm vertex noise (seed 5), "
+                            "L = ||adc - adc_target||^2, FP64",
+                "forward_ms": min(fwd), "backward_ms": min(bwd), "terms": terms,
+                "gradient_terms_per_s": terms / (min(bwd) / 1e3),
+                "parameters": int(verts.numel())}
+    finally:
+        s.close()
 
 
 def main():
@@ -428,12 +504,20 @@ def main():
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
            "ms_per_step": 1e3 * e2e_s / args.e2e_steps}
 
+    det = detect_timing(pkg, torch, sim, adc, stream)
+    adj = None
+    if world == 1 and args.adjoint_reps > 0:
+        adj = adjoint_timing(pkg, sg, torch, dev, args.adjoint_reps)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(scene, args.cpu_seconds)
-    batch = None
+    batch = batch_small = None
     if world == 1 and args.batch_scenes > 0:
         batch = dataset_batch(pkg, sg, torch, dev, args.batch_scenes, args.batch_size)
+        # small scenes, where per-scene launches leave the GPU under-filled
+        batch_small = dataset_batch(pkg, sg, torch, dev, 2 * args.batch_scenes,
+                                    2 * args.batch_size, 5_000, 10_000)
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -451,7 +535,8 @@ def main():
                                  "synthesis_ms", "rdm_ms")},
         "roofline": {"bound": "alu", "kernel": "synth_mixed_kernel",
                      "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": synth_traffic(),
+                     "traffic_unit": "bytes per launch (ncu dram read + write)",
                      "flops_per_term": FLOPS_PER_TERM,
                      "launch_ms": synth_avg_ms,
                      "peak_basis": "FP32 FMA pipe: 152 SM x 128 lanes x 2 flop x 2070 MHz"},
@@ -459,7 +544,10 @@ def main():
         "e2e": e2e,
         "gpu_launches": launches,
         "cpu_baseline": cpu,
+        "point_cloud": det,
+        "differentiable_echo": adj,
         "dataset_batch": batch,
+        "dataset_batch_small": batch_small,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)

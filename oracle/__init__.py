@@ -56,7 +56,7 @@ class _Radar(ctypes.Structure):
                 ("fs", ctypes.c_double), ("Tc", ctypes.c_double),
                 ("M", ctypes.c_int), ("N", ctypes.c_int), ("P", ctypes.c_int),
                 ("Q", ctypes.c_int), ("intra_chirp_motion", ctypes.c_int),
-                ("pad_", ctypes.c_int)]
+                ("tdm", ctypes.c_int), ("delay_ref", ctypes.c_int), ("pad_", ctypes.c_int)]
 
 
 def _load():
@@ -80,9 +80,9 @@ def _load():
                                                  ctypes.c_double, P]
             lib.orc_rcs_farfield.argtypes = [P, ctypes.c_int64, P, P, P, P,
                                              ctypes.c_int, P]
-            lib.orc_adc_full.argtypes = [P, P, P, P, ctypes.c_int64, P, P,
+            lib.orc_adc_full.argtypes = [P, P, P, P, P, ctypes.c_int64, P, P,
                                          ctypes.POINTER(_Radar), P]
-            lib.orc_adc_entries.argtypes = [P, P, P, P, ctypes.c_int64, P, P,
+            lib.orc_adc_entries.argtypes = [P, P, P, P, P, ctypes.c_int64, P, P,
                                             ctypes.POINTER(_Radar), P,
                                             ctypes.c_int64, P]
             lib.orc_num_threads.restype = ctypes.c_int
@@ -121,6 +121,14 @@ def world_facets(scene, t: float):
                                _p(vel), float(t), _p(out))
     fvel = np.ascontiguousarray(vel[inst])
     return out, fvel, rho
+
+
+def reference_points(scene, t: float) -> np.ndarray:
+    """Per-facet reference point of the facet's instance (the instance
+    origin, Eq. 12's target position) at absolute time t: pos + vel t."""
+    _, inst, _, pos, _, vel = flatten(scene)
+    ref = pos + vel * float(t)
+    return np.ascontiguousarray(ref[inst])
 
 
 def visibility(tri: np.ndarray, antennas: np.ndarray, eps_face: float = EPS_FACE,
@@ -186,7 +194,9 @@ def rcs_farfield(tri: np.ndarray, rho: np.ndarray, t_hat, r_hat, freqs) -> np.nd
 
 def _radar_struct(radar) -> _Radar:
     return _Radar(radar.f0, radar.slope, radar.fs, radar.Tc, radar.M, radar.N,
-                  radar.P, radar.Q, int(bool(radar.intra_chirp_motion)), 0)
+                  radar.P, radar.Q, int(bool(radar.intra_chirp_motion)),
+                  int(bool(getattr(radar, "tdm", False))),
+                  int(bool(getattr(radar, "delay_ref", False))), 0)
 
 
 class Frame:
@@ -202,13 +212,14 @@ class Frame:
             fn = visibility_bvh if use_bvh else visibility
             state = fn(self.tri0, self.radar.antennas)
         self.state = state
+        self.fref = reference_points(scene, scene.t0)
         self._rs = _radar_struct(self.radar)
 
     def adc_full(self) -> np.ndarray:
         """ADC cube [O][N][M] complex128 (Eqs. 7, 9-13)."""
         r = self.radar
         out = np.empty((r.O, r.N, r.M), np.complex128)
-        _load().orc_adc_full(_p(self.tri0), _p(self.fvel), _p(self.rho),
+        _load().orc_adc_full(_p(self.tri0), _p(self.fvel), _p(self.rho), _p(self.fref),
                              _p(self.state), self.tri0.shape[0], _p(r.tx), _p(r.rx),
                              ctypes.byref(self._rs), _p(out))
         return out
@@ -218,7 +229,7 @@ class Frame:
         e = np.ascontiguousarray(entries, np.int32).reshape(-1, 3)
         out = np.empty(e.shape[0], np.complex128)
         r = self.radar
-        _load().orc_adc_entries(_p(self.tri0), _p(self.fvel), _p(self.rho),
+        _load().orc_adc_entries(_p(self.tri0), _p(self.fvel), _p(self.rho), _p(self.fref),
                                 _p(self.state), self.tri0.shape[0], _p(r.tx), _p(r.rx),
                                 ctypes.byref(self._rs), _p(e), e.shape[0], _p(out))
         return out

@@ -548,6 +548,8 @@ typedef struct {
     double f0, slope, fs, Tc;   /* start frequency, mu, sampling rate, chirp period */
     int M, N, P, Q;
     int intra_chirp_motion;     /* tau evaluated at t_n + t_m (1) or t_n (0) */
+    int tdm;                    /* 1: TX p transmits chirp n at (n P + p) T_c */
+    int delay_ref;              /* 1: reference-point delay form (Eqs. 11-13 per target) */
     int pad_;
 } orc_radar;
 
@@ -566,14 +568,36 @@ typedef struct {
  * t = t_n + t_m (Eq. 12 with the exact bistatic path of the centroid).
  * The IFFT route of Eqs. 9-11: with stretch processing, sample m sees the
  * instantaneous frequency f_m, so sigma_f at f_m times the dechirp phase is
- * the time-domain product; no separate transform is applied. */
+ * the time-domain product; no separate transform is applied.
+ *
+ * Time-division MIMO (tdm): the chirp of TX p with index n starts at
+ * (n P + p) T_c instead of n T_c; everything else is unchanged.
+ *
+ * Reference-point form (delay_ref), Eqs. 11-13 taken per target: the
+ * target's reference point r_i (its instance origin, fref per facet) moves
+ * with the target; with L_k and L_r the TX + RX path lengths of the facet
+ * centroid and of the reference point at the chirp start, and L_r(t) that of
+ * the reference point at t_n + t_m, the phase is
+ *   2 pi [ f_m (L_k - L_r + L_r(t)) / c - mu (L_r(t) / c)^2 / 2 ]
+ * i.e. the facet enters through the frequency response relative to the
+ * reference point at the chirp's aspect (sigma_f), the delay of Eq. 12, its
+ * motion within the chirp and the residual video phase belong to the
+ * reference point. */
+static double path_len(const double *x, const double *ptx, const double *prx)
+{
+    double ut[3], ur[3];
+    sub3(x, ptx, ut);
+    sub3(x, prx, ur);
+    return sqrt(dot3(ut, ut)) + sqrt(dot3(ur, ur));
+}
+
 static void adc_sample(const double *tri0, const double *fvel, const float *rho,
-                       const uint8_t *state, int64_t F, const double *tx,
+                       const double *fref, const uint8_t *state, int64_t F, const double *tx,
                        const double *rx, const orc_radar *rd, int o, int n, int m,
                        double *out_re, double *out_im)
 {
     const int p = o / rd->Q, q = o % rd->Q;
-    const double tn = (double)n * rd->Tc;
+    const double tn = (double)(rd->tdm ? (int64_t)n * rd->P + p : n) * rd->Tc;
     const double tm = (double)m / rd->fs;
     const double fm = rd->f0 + rd->slope * tm;
     const double km = 2.0 * ORC_PI * fm / ORC_C0;
@@ -607,15 +631,25 @@ static void adc_sample(const double *tri0, const double *fvel, const float *rho,
         const double s = (double)rho[k] * (km / sqrt(ORC_PI)) * ok;
         const double a = lam * amp0 / (Rt * Rr) * s;
         /* round-trip delay at t_n + t_m */
-        double ct[3] = {c[0], c[1], c[2]};
-        if (rd->intra_chirp_motion)
-            for (int r = 0; r < 3; ++r) ct[r] = c[r] + vk[r] * tm;
-        double ut[3], ur[3];
-        sub3(ct, ptx, ut);
-        sub3(ct, prx, ur);
-        const double tau = (sqrt(dot3(ut, ut)) + sqrt(dot3(ur, ur))) / ORC_C0;
-        const double phase = 2.0 * ORC_PI *
-            (rd->f0 * tau + rd->slope * tm * tau - 0.5 * rd->slope * tau * tau);
+        double phase;
+        if (!rd->delay_ref) {
+            double ct[3] = {c[0], c[1], c[2]};
+            if (rd->intra_chirp_motion)
+                for (int r = 0; r < 3; ++r) ct[r] = c[r] + vk[r] * tm;
+            const double tau = path_len(ct, ptx, prx) / ORC_C0;
+            phase = 2.0 * ORC_PI *
+                (rd->f0 * tau + rd->slope * tm * tau - 0.5 * rd->slope * tau * tau);
+        } else {
+            double r0[3], rt[3];
+            for (int r = 0; r < 3; ++r) {
+                r0[r] = fref[3 * k + r] + vk[r] * tn;
+                rt[r] = rd->intra_chirp_motion ? r0[r] + vk[r] * tm : r0[r];
+            }
+            const double Lk = path_len(c, ptx, prx), Lr0 = path_len(r0, ptx, prx);
+            const double Lrt = path_len(rt, ptx, prx);
+            const double tau_f = (Lk - Lr0 + Lrt) / ORC_C0, tau_r = Lrt / ORC_C0;
+            phase = 2.0 * ORC_PI * (fm * tau_f - 0.5 * rd->slope * tau_r * tau_r);
+        }
         const double cr = cos(phase), ci = sin(phase);
         sr += a * (jr * cr - ji * ci);
         si += a * (jr * ci + ji * cr);
@@ -626,7 +660,7 @@ static void adc_sample(const double *tri0, const double *fvel, const float *rho,
 
 /* Full ADC cube [O][N][M] (complex128, interleaved). */
 void orc_adc_full(const double *tri0, const double *fvel, const float *rho,
-                  const uint8_t *state, int64_t F, const double *tx,
+                  const double *fref, const uint8_t *state, int64_t F, const double *tx,
                   const double *rx, const orc_radar *rd, double *out)
 {
     const int O = rd->P * rd->Q;
@@ -635,19 +669,19 @@ void orc_adc_full(const double *tri0, const double *fvel, const float *rho,
         for (int n = 0; n < rd->N; ++n)
             for (int m = 0; m < rd->M; ++m) {
                 const int64_t idx = ((int64_t)o * rd->N + n) * rd->M + m;
-                adc_sample(tri0, fvel, rho, state, F, tx, rx, rd, o, n, m,
+                adc_sample(tri0, fvel, rho, fref, state, F, tx, rx, rd, o, n, m,
                            out + 2 * idx, out + 2 * idx + 1);
             }
 }
 
 /* Selected entries (o, n, m) of the ADC cube; entries: E x 3 int32. */
 void orc_adc_entries(const double *tri0, const double *fvel, const float *rho,
-                     const uint8_t *state, int64_t F, const double *tx,
+                     const double *fref, const uint8_t *state, int64_t F, const double *tx,
                      const double *rx, const orc_radar *rd, const int32_t *entries,
                      int64_t E, double *out)
 {
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t e = 0; e < E; ++e)
-        adc_sample(tri0, fvel, rho, state, F, tx, rx, rd, entries[3 * e],
+        adc_sample(tri0, fvel, rho, fref, state, F, tx, rx, rd, entries[3 * e],
                    entries[3 * e + 1], entries[3 * e + 2], out + 2 * e, out + 2 * e + 1);
 }

@@ -88,6 +88,8 @@ class Radar:
     tx: np.ndarray                 # (P,3)
     rx: np.ndarray                 # (Q,3)
     intra_chirp_motion: bool = True
+    tdm: bool = False              # time-division MIMO: TX p sends chirp n at (n P + p) Tc
+    delay_ref: bool = False        # reference-point delay form (one tau(t) per instance)
 
     def __post_init__(self):
         self.tx = np.ascontiguousarray(np.asarray(self.tx, np.float64).reshape(-1, 3))
@@ -155,13 +157,14 @@ def ula(n: int, spacing: float, centre: Sequence[float]) -> np.ndarray:
 def make_radar(M: int, N: int, P: int, Q: int, fs: float, slope: float,
                tx_spacing_wl: float, rx_spacing_wl: float = 0.5,
                centre=(0.0, 0.0, RADAR_HEIGHT), f0: float = F0_DEFAULT,
-               intra_chirp_motion: bool = True) -> Radar:
+               intra_chirp_motion: bool = True, tdm: bool = False,
+               delay_ref: bool = False) -> Radar:
     lam0 = C0 / f0
     prof = radar_profile(M, fs, slope, f0)
     return Radar(f0=f0, slope=slope, fs=fs, Tc=prof["Tc"], M=M, N=N,
                  tx=ula(P, tx_spacing_wl * lam0, centre),
                  rx=ula(Q, rx_spacing_wl * lam0, centre),
-                 intra_chirp_motion=intra_chirp_motion)
+                 intra_chirp_motion=intra_chirp_motion, tdm=tdm, delay_ref=delay_ref)
 
 
 # --------------------------------------------------------------------------

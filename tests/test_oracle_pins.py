@@ -484,3 +484,70 @@ def test_rdm_adjoint_central_differences():
                 fd = (L(xp) - L(xm)) / (2 * h)
                 an = grad[o, n, m].real if part == 0 else grad[o, n, m].imag
                 assert abs(fd - an) <= 1e-6 * (1 + abs(an)), (O, N, M, o, n, m, part, fd, an)
+
+
+# ---------------------------------------------------------------------------
+# variants: time-division MIMO, reference-point delay form (Eqs. 11-13)
+# ---------------------------------------------------------------------------
+def _moving_plate(radar, t0=0.0):
+    inst = sg.Instance(0, np.array([0.4, 14.0, 0.3]), np.eye(3), np.array([0.5, -7.0, 0.2]))
+    return sg.Scene([sg.plate(0.2, 0.2, 2)], [inst], radar, t0=t0)
+
+
+def test_tdm_channel_equals_simultaneous_run_shifted_in_time():
+    """With TX p sending chirp n at (n P + p) T_c, channel (p, q) of a TDM
+    frame is channel q of a one-TX frame with chirp period P T_c starting
+    p T_c later (both TX at one place, so only the timing differs)."""
+    base = sg.make_radar(64, 6, 2, 2, 5.12e6, 30e12, 0.0, centre=(0.0, 0.0, 0.0), tdm=True)
+    tdm = oracle.Frame(_moving_plate(base)).adc_full()
+    for p in range(2):
+        one = sg.Radar(f0=base.f0, slope=base.slope, fs=base.fs, Tc=2 * base.Tc, M=base.M,
+                       N=base.N, tx=base.tx[p:p + 1], rx=base.rx)
+        ref = oracle.Frame(_moving_plate(one, t0=p * base.Tc)).adc_full()
+        got = tdm[p * 2:(p + 1) * 2]
+        # time sums rounded differently: ~1e-15 relative in k L ~ 3e4 rad
+        assert np.abs(got - ref).max() <= 1e-9 * np.abs(ref).max()
+    sim = oracle.Frame(_moving_plate(sg.make_radar(64, 6, 2, 2, 5.12e6, 30e12, 0.0,
+                                                   centre=(0.0, 0.0, 0.0)))).adc_full()
+    assert np.abs(sim[2:] - tdm[2:]).max() > 1e-3 * np.abs(sim).max()   # timing does matter
+
+
+def _one_triangle(offset):
+    a, b = 2e-4, 2e-4
+    v = np.array([[-a, 0.0, -b], [a, 0.0, -b], [0.0, 0.0, 2 * b]]) + np.asarray(offset)
+    return sg.Mesh(v, np.array([[0, 1, 2]]), np.ones(1, np.float32))
+
+
+def test_reference_form_equals_per_facet_form_at_the_reference_point():
+    """A facet whose centroid is its instance origin has L_k = L_r at every
+    time: both delay forms coincide, moving, with intra-chirp motion."""
+    for delay_ref in (False, True):
+        r = sg.make_radar(128, 8, 1, 2, 5.12e6, 30e12, 2.0, centre=(0.0, 0.0, 0.0),
+                          delay_ref=delay_ref)
+        inst = sg.Instance(0, np.array([0.2, 11.0, 0.1]), np.eye(3), np.array([0.0, 9.0, 0.0]))
+        x = oracle.Frame(sg.Scene([_one_triangle((0, 0, 0))], [inst], r)).adc_full()
+        if delay_ref:
+            assert np.abs(x - x_facet).max() <= 1e-10 * np.abs(x_facet).max()
+        x_facet = x
+
+
+def test_reference_form_residual_video_phase_closed_form():
+    """Static facet 1.5 m from its instance origin: the two forms differ only
+    in the residual video phase, x_ref / x_facet = exp(-j pi mu (tau_r^2 -
+    tau_k^2)) with the delays of the centroid and of the reference point."""
+    off = np.array([0.3, 1.5, 0.1])
+    pos = np.array([0.0, 12.0, 0.0])
+    out = {}
+    for delay_ref in (False, True):
+        r = sg.make_radar(128, 4, 1, 1, 5.12e6, 30e12, 2.0, centre=(0.0, 0.0, 0.0),
+                          delay_ref=delay_ref)
+        inst = sg.Instance(0, pos, np.eye(3), np.zeros(3))
+        out[delay_ref] = oracle.Frame(sg.Scene([_one_triangle(off)], [inst], r)).adc_full()
+    tx, rx = r.tx[0], r.rx[0]
+    ck = pos + off
+    tau_k = (np.linalg.norm(ck - tx) + np.linalg.norm(ck - rx)) / C0
+    tau_r = (np.linalg.norm(pos - tx) + np.linalg.norm(pos - rx)) / C0
+    ratio = out[True] / out[False]
+    expect = np.exp(-1j * np.pi * r.slope * (tau_r ** 2 - tau_k ** 2))
+    assert abs(np.angle(expect)) > 0.1                 # a visible difference
+    assert np.abs(ratio - expect).max() <= 1e-9
