@@ -98,6 +98,15 @@ typedef struct bart_radar {
     int32_t window;              /* BART_WINDOW_* for bart_form_rdm */
     double  tx[BART_MAX_TX][3];  /* TX phase centres (first P used) */
     double  rx[BART_MAX_RX][3];  /* RX phase centres (first Q used) */
+    int32_t tdm;                 /* 0: all TX chirp together (chirp n at n Tc);
+                                    1: time-division MIMO, TX p sends chirp n at
+                                    (n P + p) Tc (Doppler period P Tc) */
+    int32_t delay_ref;           /* 0: delay of every facet from its own centroid;
+                                    1: reference-point form of Eqs. 11-13: the
+                                    facet's path length relative to its
+                                    instance origin at the chirp start, plus the
+                                    origin's path at t_n + t_m; residual video
+                                    phase from the origin's delay */
 } bart_radar;
 
 /* Per-frame counters (filled when a non-NULL pointer is passed; doing so
@@ -347,7 +356,8 @@ typedef struct bart_detect_cfg {
  * azimuth from +Y toward +X. */
 typedef struct bart_point {
     double  range;               /* m: c fs r_bin / (2 slope M)              (Eq. 4) */
-    double  rate;                /* m/s: lambda_c (d_bin - N/2) / (2 N Tc),
+    double  rate;                /* m/s: lambda_c (d_bin - N/2) / (2 N Tr), Tr = Tc
+                                    (P Tc with tdm),
                                     positive receding, lambda_c = c / (f0 + B/2),
                                     B = slope M / fs                         (Eq. 5) */
     double  azimuth;             /* rad: asin(s_i) at the angle-spectrum peak (Eq. 6) */

@@ -335,8 +335,9 @@ def point_cloud(adc: np.ndarray, radar, guard_r=2, guard_d=2, train_r=8, train_d
                 pfa=1e-6, angle_bins=512) -> list:
     """Points (range, range rate, azimuth, x, y, power, r_bin, d_bin) of the
     CA-CFAR detections in row-major (range, shifted Doppler) order:
-    range R = c fs r / (2 mu M) (Eq. 4), range rate lambda_c (d - N/2) / (2 N T_c)
-    (Eq. 5, positive receding), azimuth asin(s*) at the angle-spectrum peak
+    range R = c fs r / (2 mu M) (Eq. 4), range rate lambda_c (d - N/2) / (2 N T_r)
+    (Eq. 5, positive receding; T_r = T_c, or P T_c with time-division MIMO),
+    azimuth asin(s*) at the angle-spectrum peak
     (Eq. 6), x = R sin(theta), y = R cos(theta)."""
     O, N, M = adc.shape
     Y = range_doppler_cube(adc)
@@ -354,7 +355,8 @@ def point_cloud(adc: np.ndarray, radar, guard_r=2, guard_d=2, train_r=8, train_d
         s = -1.0 + 2.0 * i / angle_bins
         th = float(np.arcsin(np.clip(s, -1.0, 1.0)))
         R = C0 * radar.fs * r / (2.0 * radar.slope * M)
-        v = lam_c * (ds - N / 2) / (2.0 * N * radar.Tc)
+        Tr = radar.Tc * (radar.P if getattr(radar, "tdm", False) else 1)   # chirp repetition
+        v = lam_c * (ds - N / 2) / (2.0 * N * Tr)
         pts.append((R, v, th, R * np.sin(th), R * np.cos(th), float(rdm[r, ds]), int(r), int(ds)))
     return pts
 

@@ -58,7 +58,8 @@ class bart_radar(ctypes.Structure):
                 ("Q", ctypes.c_int32), ("intra_chirp_motion", ctypes.c_int32),
                 ("window", ctypes.c_int32),
                 ("tx", (ctypes.c_double * 3) * MAX_TX),
-                ("rx", (ctypes.c_double * 3) * MAX_RX)]
+                ("rx", (ctypes.c_double * 3) * MAX_RX),
+                ("tdm", ctypes.c_int32), ("delay_ref", ctypes.c_int32)]
 
 
 class bart_stats(ctypes.Structure):
@@ -278,6 +279,8 @@ def make_radar(radar, window: int = WINDOW_HANN) -> bart_radar:
     r.P, r.Q = tx.shape[0], rx.shape[0]
     r.intra_chirp_motion = int(bool(getattr(radar, "intra_chirp_motion", True)))
     r.window = int(window)
+    r.tdm = int(bool(getattr(radar, "tdm", False)))
+    r.delay_ref = int(bool(getattr(radar, "delay_ref", False)))
     for p in range(min(r.P, MAX_TX)):
         for k in range(3):
             r.tx[p][k] = float(tx[p, k])

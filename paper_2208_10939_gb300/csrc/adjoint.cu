@@ -59,7 +59,7 @@ adjoint_fp64_kernel(SynthArgs A, int W, const void *__restrict__ grad, int grad_
     const double c = kC0, f0 = A.rd.f0, mu = A.rd.slope, fs = A.rd.fs;
     const double f_max = f0 + mu * (M - 1) / fs;
     const double k0 = 2.0 * kPi * f0 / c, kmax = 2.0 * kPi * f_max / c;
-    const double tn = (double)n * A.rd.Tc;
+    const double tn = (double)((int64_t)n * A.rd.slots + (A.rd.tdm ? tx : 0)) * A.rd.Tc;
     const double *ptx = A.rd.ant[tx];
     const double *prx = A.rd.ant[P + rx];
     const double twopi = 2.0 * kPi;
@@ -104,7 +104,9 @@ adjoint_fp64_kernel(SynthArgs A, int W, const void *__restrict__ grad, int grad_
             RecA &R = sR[warp][lane];
             int flags = 0;
             R.kind = build_record<double>(tri, c0, vel, tn, ptx, prx, (double)A.fac[k].rho,
-                                          A.rd.intra, k0, kmax, R.r, &flags);
+                                          A.rd.intra, k0, kmax,
+                                          A.rd.delay_ref ? A.ref64 + 3 * inst : nullptr, R.r,
+                                          &flags);
             R.flags = flags;
         }
         __syncwarp();
@@ -128,7 +130,7 @@ adjoint_fp64_kernel(SynthArgs A, int W, const void *__restrict__ grad, int grad_
                 const double Qr = R.r[3] + t * (R.r[4] + t * R.r[2]);
                 const double sQt = sqrt(Qt), sQr = sqrt(Qr);
                 const double L = sQt + sQr;
-                double thc = fm * L / c - mu * L * L / (2.0 * c * c);
+                double thc = fm * (L + R.r[kRecLs]) / c - mu * L * L / (2.0 * c * c);
                 thc -= rint(thc);
                 const double fmc = fm / c;
                 const double kp = fm / f0;
@@ -186,7 +188,8 @@ adjoint_fp64_kernel(SynthArgs A, int W, const void *__restrict__ grad, int grad_
                         a_thc -= twopi * coef * zr;
                     }
                 }
-                // thc -> L -> path-length polynomial coefficients
+                // thc -> L -> path-length polynomial coefficients; thc -> shift
+                ab[kRecLs] += a_thc * fmc;
                 const double aL = a_thc * (fmc - mu * L / (c * c));
                 const double it = 0.5 / sQt, ir = 0.5 / sQr;
                 ab[0] += aL * it;
@@ -212,6 +215,7 @@ adjoint_fp64_kernel(SynthArgs A, int W, const void *__restrict__ grad, int grad_
             for (int q = 0; q < 9; ++q) tri[q] = A.tri64[9 * k + q];
             for (int r = 0; r < 3; ++r) c0[r] = A.c64[3 * k + r];
             const double rho = (double)A.fac[k].rho;
+            const double *ref = A.rd.delay_ref ? A.ref64 + 3 * A.fac[k].inst : nullptr;
             for (int p = 0; p < 10; ++p) {
                 Dual dtri[9], dc0[3], out[kRecEntries];
                 for (int e = 0; e < kRecEntries; ++e) out[e] = Dual(0.0, 0.0);
@@ -221,7 +225,7 @@ adjoint_fp64_kernel(SynthArgs A, int W, const void *__restrict__ grad, int grad_
                 const Dual drho(rho, p == 9 ? 1.0 : 0.0);
                 int flags = 0;
                 const int kind = build_record<Dual>(dtri, dc0, vel, tn, ptx, prx, drho, A.rd.intra,
-                                                    k0, kmax, out, &flags);
+                                                    k0, kmax, ref, out, &flags);
                 double gsum = 0.0;
                 if (kind == R.kind)
                     for (int e = 0; e < kRecEntries; ++e) gsum += mine[e] * out[e].d;

@@ -35,6 +35,9 @@ struct RadarDev {
     int M, N, P, Q, O, A;
     int intra;
     int window;
+    int tdm;        // time-division MIMO: chirp n of TX p at (n P + p) Tc
+    int delay_ref;  // reference-point delay form
+    int slots;      // chirp slots per chirp index: P with tdm, else 1
     double ant[kMaxAnt][3];   // TX 0..P-1, then RX P..P+Q-1
 };
 
@@ -91,7 +94,7 @@ const void *build_facets_kernel_fn(int *t0_arg_index, int *n_args);
 void launch_build_facets(const MeshDesc *meshes, const InstDev *insts, int n_inst,
                          int64_t F, double t0, double *tri64, float *tri32, double *c64,
                          FacetRec *fac, float *aabb, float *vel32, unsigned int *bounds,
-                         cudaStream_t s);
+                         double *ref64, float *ref32, cudaStream_t s);
 void launch_morton(const FacetRec *fac, int64_t F, const unsigned int *bounds,
                    uint32_t *keys, int32_t *vals, cudaStream_t s);
 // Stable LSD radix sort of (key, value) pairs on the low `bits` bits.
@@ -147,6 +150,8 @@ struct SynthArgs {
     const double *c64;
     const double *vel64;     // per instance, 3 doubles
     const float *vel32;      // per instance, 4 floats (xyz, pad)
+    const double *ref64;     // per instance, origin at t0 (3 doubles)
+    const float *ref32;      // per instance, origin at t0 (4 floats)
     const int32_t *vis_idx;  // [O][F]
     const int32_t *vis_cnt;  // [O + A]
     // virtual channels: VO = scenes x O rows of the output; row v reads

@@ -95,6 +95,8 @@ struct bart_ctx {
     DevBuf<double> tri64, c64, vel64;
     DevBuf<float> tri32;
     DevBuf<float> vel32, aabb;
+    DevBuf<double> ref64;               // instance origins at t0 (delay reference points)
+    DevBuf<float> ref32;
     DevBuf<FacetRec> fac;
     DevBuf<unsigned int> bounds;
     DevBuf<uint32_t> keys, keys_tmp, sort_temp;
@@ -189,6 +191,7 @@ struct bart_ctx {
         }
         d_meshes.release(); d_insts.release(); tri64.release(); tri32.release(); c64.release();
         vel64.release(); vel32.release(); aabb.release(); fac.release(); bounds.release();
+        ref64.release(); ref32.release();
         keys.release(); keys_tmp.release(); sort_temp.release(); vals.release();
         vals_tmp.release(); nodes.release(); parent.release(); leaf_parent.release();
         flags.release(); state.release(); blk_cnt.release(); vis_idx.release();
@@ -239,6 +242,9 @@ static RadarDev make_rd(const bart_radar &r)
     d.A = r.P + r.Q;
     d.intra = r.intra_chirp_motion ? 1 : 0;
     d.window = r.window;
+    d.tdm = r.tdm ? 1 : 0;
+    d.delay_ref = r.delay_ref ? 1 : 0;
+    d.slots = d.tdm ? r.P : 1;
     for (int p = 0; p < r.P; ++p)
         for (int k = 0; k < 3; ++k) d.ant[p][k] = r.tx[p][k];
     for (int q = 0; q < r.Q; ++q)
@@ -456,6 +462,9 @@ int bart_radar_set(bart_ctx *ctx, const bart_radar *r)
                     (double)r->M / r->fs);
     if (r->window != BART_WINDOW_HANN && r->window != BART_WINDOW_RECT)
         return fail(BART_EINVAL, "bart_radar_set: window=%d", r->window);
+    if ((r->tdm != 0 && r->tdm != 1) || (r->delay_ref != 0 && r->delay_ref != 1))
+        return fail(BART_EINVAL, "bart_radar_set: tdm=%d delay_ref=%d (0 or 1)", r->tdm,
+                    r->delay_ref);
     ctx->radar = *r;
     ++ctx->version;
     ctx->have_radar = true;
@@ -521,6 +530,8 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
     BART_TRY(ctx->c64.ensure(3 * F, "facet centroids"));
     BART_TRY(ctx->vel64.ensure(3 * I, "instance velocities"));
     BART_TRY(ctx->vel32.ensure(4 * I, "instance velocities (f32)"));
+    BART_TRY(ctx->ref64.ensure(3 * I, "instance origins"));
+    BART_TRY(ctx->ref32.ensure(4 * I, "instance origins (f32)"));
     BART_TRY(ctx->aabb.ensure(6 * F, "facet boxes"));
     BART_TRY(ctx->fac.ensure(F, "facet records"));
     BART_TRY(ctx->keys.ensure(F, "morton keys"));
@@ -587,11 +598,13 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
         // the table is then double-buffered so that the side stream fills
         // chunk c+1 while the main stream synthesises chunk c (one chunk
         // measured faster than forced chunking at the sedan size)
-        const int64_t per_chirp = (int64_t)A * F * (int64_t)sizeof(float4);
+        // one kinematics row per antenna, facet and chirp slot (P slots per
+        // chirp with time-division MIMO)
+        const int64_t per_chirp = (int64_t)rd.slots * A * F * (int64_t)sizeof(float4);
         nc = (int)std::min<int64_t>(rd.N, std::max<int64_t>(1, ctx->kin_budget / per_chirp));
         chunks = (rd.N + nc - 1) / nc;
         nbuf = chunks > 1 ? 2 : 1;
-        chunk_words = (size_t)nc * A * F;
+        chunk_words = (size_t)nc * rd.slots * A * F;
         BART_TRY(ctx->kin.ensure(nbuf * chunk_words, "kinematics table"));
         BART_TRY(ctx->partial.ensure((size_t)synth_partial_words(scene_F.data(), B, rd, nc,
                                                                  tpi, ctx->layout_S),
@@ -618,7 +631,8 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
 
         // 1. world facets at t0
         launch_build_facets(ctx->d_meshes.p, ctx->d_insts.p, I, F, t0v, ctx->tri64.p, ctx->tri32.p,
-                            ctx->c64.p, ctx->fac.p, ctx->aabb.p, ctx->vel32.p, ctx->bounds.p, s);
+                            ctx->c64.p, ctx->fac.p, ctx->aabb.p, ctx->vel32.p, ctx->bounds.p,
+                            ctx->ref64.p, ctx->ref32.p, s);
         launches += 1;
         if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[1], s), "cudaEventRecord");
         // 2. LBVH (batched scenes: one hierarchy with a subtree per scene)
@@ -663,6 +677,8 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
         a.c64 = ctx->c64.p;
         a.vel64 = ctx->vel64.p;
         a.vel32 = ctx->vel32.p;
+        a.ref64 = ctx->ref64.p;
+        a.ref32 = ctx->ref32.p;
         a.vis_idx = ctx->vis_idx.p;
         a.vis_cnt = ctx->vis_cnt.p;
         a.VO = B * O;
@@ -1066,7 +1082,8 @@ int bart_detect(bart_ctx *ctx, const void *adc, int32_t dtype, const bart_detect
     const double B = r.slope * r.M / r.fs;
     dd.lam_c = kC0 / (r.f0 + 0.5 * B);
     dd.range_scale = kC0 * r.fs / (2.0 * r.slope * r.M);
-    dd.rate_scale = dd.lam_c / (2.0 * r.N * r.Tc);
+    // chirp repetition of one channel: Tc, or P Tc with time-division MIMO
+    dd.rate_scale = dd.lam_c / (2.0 * r.N * (r.tdm ? r.P : 1) * r.Tc);
     BART_TRY(ctx->det_ws.ensure((size_t)detect_workspace_bytes(rd, dtype, dd.bins),
                                 "detection workspace"));
     DetectBufs b;

@@ -7,15 +7,21 @@
 // Record entries (kRecEntries doubles):
 //   [0..2] qt: R_t(t)^2 = qt0 + t (qt1 + t qt2), t = fast time
 //   [3..4] qr: R_r(t)^2 = qr0 + t (qr1 + t qt2)
-//   [5..]  d:  form coefficients (vertex / series / edge, see synth.cu)
+//   [5]    ls: path-length shift; the delay path is L(t) + ls, the residual
+//              video phase uses L(t) alone
+//   [6..]  d:  form coefficients (vertex / series / edge, see synth.cu)
+// Per-facet delay form: qt, qr from the facet centroid, ls = 0.  Reference-
+// point form (Eqs. 11-13 per target): qt, qr from the instance origin and
+// ls = L_facet - L_origin at the chirp start.
 #pragma once
 
 #include "bart_internal.cuh"
 
 namespace bart {
 
-constexpr int kRecEntries = 27;
-constexpr int kRecD = 5;            // first d[] entry
+constexpr int kRecEntries = 28;
+constexpr int kRecLs = 5;           // path-length shift entry
+constexpr int kRecD = 6;            // first d[] entry
 
 // 1/n!, n = 0..17 (series form of the facet integral)
 static __constant__ double c_inv_fact[18] = {
@@ -58,14 +64,15 @@ __device__ __forceinline__ double val(Dual a) { return a.v; }
 
 // Builds the record of one facet for channel antennas ptx/prx at chirp time
 // tn.  tri: world vertices at t0 (9), c0: the stored centroid at t0 (3), vel:
-// instance velocity, rho: reflectivity.  Returns the form (kRec*), the sinc
-// flags of the edge form in *flags.  Branches depend on values only, so the
-// double and dual builds take the same path.
+// instance velocity, rho: reflectivity, ref: the instance origin at t0 for
+// the reference-point delay form (NULL: per-facet form).  Returns the form
+// (kRec*), the sinc flags of the edge form in *flags.  Branches depend on
+// values only, so the double and dual builds take the same path.
 template <typename Sc>
 __device__ __forceinline__ int build_record(const Sc *tri, const Sc *c0, const double *vel,
                                             double tn, const double *ptx, const double *prx,
-                                            Sc rho, int intra, double k0, double kmax, Sc *out,
-                                            int *flags)
+                                            Sc rho, int intra, double k0, double kmax,
+                                            const double *ref, Sc *out, int *flags)
 {
     Sc cc[3], dv[9];
     for (int r = 0; r < 3; ++r) cc[r] = c0[r];
@@ -90,11 +97,34 @@ __device__ __forceinline__ int build_record(const Sc *tri, const Sc *c0, const d
     for (int r = 0; r < 3; ++r) b[r] = dt[r] / Rt + dr[r] / Rr;
     const Sc ok = 0.5 * (nn[0] * b[0] + nn[1] * b[1] + nn[2] * b[2]);
     const Sc g = rho * ok / (Rt * Rr);
-    out[0] = Rt2;
-    out[3] = Rr2;
+    if (!ref) {
+        out[0] = Rt2;
+        out[3] = Rr2;
+        out[kRecLs] = Sc(0.0);
+        if (intra) {
+            out[1] = -2.0 * (dt[0] * vel[0] + dt[1] * vel[1] + dt[2] * vel[2]);
+            out[4] = -2.0 * (dr[0] * vel[0] + dr[1] * vel[1] + dr[2] * vel[2]);
+        }
+    } else {
+        // the instance origin at the chirp start (a constant of the facet
+        // parameters): its path polynomial, and the facet's offset from it
+        double gt[3], gr[3];
+        for (int r = 0; r < 3; ++r) {
+            const double o = ref[r] + vel[r] * tn;
+            gt[r] = ptx[r] - o;
+            gr[r] = prx[r] - o;
+        }
+        const double qt0 = gt[0] * gt[0] + gt[1] * gt[1] + gt[2] * gt[2];
+        const double qr0 = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
+        out[0] = Sc(qt0);
+        out[3] = Sc(qr0);
+        out[kRecLs] = (Rt + Rr) - (::sqrt(qt0) + ::sqrt(qr0));
+        if (intra) {
+            out[1] = Sc(-2.0 * (gt[0] * vel[0] + gt[1] * vel[1] + gt[2] * vel[2]));
+            out[4] = Sc(-2.0 * (gr[0] * vel[0] + gr[1] * vel[1] + gr[2] * vel[2]));
+        }
+    }
     if (intra) {
-        out[1] = -2.0 * (dt[0] * vel[0] + dt[1] * vel[1] + dt[2] * vel[2]);
-        out[4] = -2.0 * (dr[0] * vel[0] + dr[1] * vel[1] + dr[2] * vel[2]);
         out[2] = Sc(vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]);
     } else {
         out[1] = out[4] = out[2] = Sc(0.0);

@@ -43,7 +43,8 @@ __global__ void build_facets_kernel(const MeshDesc *__restrict__ meshes,
                                     float *__restrict__ tri32,
                                     double *__restrict__ c64, FacetRec *__restrict__ fac,
                                     float *__restrict__ aabb, float *__restrict__ vel32,
-                                    unsigned int *__restrict__ bounds)
+                                    unsigned int *__restrict__ bounds,
+                                    double *__restrict__ ref64, float *__restrict__ ref32)
 {
     const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     float cf[3] = {0.f, 0.f, 0.f};
@@ -118,8 +119,15 @@ __global__ void build_facets_kernel(const MeshDesc *__restrict__ meshes,
             aabb[6 * f + 3 + r] += pad;
         }
         if (j == 0) {
-            for (int r = 0; r < 3; ++r) vel32[4 * lo + r] = (float)in.vel[r];
+            for (int r = 0; r < 3; ++r) {
+                vel32[4 * lo + r] = (float)in.vel[r];
+                // the instance origin at t0 (reference point of the delay form)
+                const double o = world_coord(in.rot + 3 * r, 0.0, 0.0, 0.0, in.pos[r], in.vel[r], t0);
+                ref64[3 * lo + r] = o;
+                ref32[4 * lo + r] = (float)o;
+            }
             vel32[4 * lo + 3] = 0.f;
+            ref32[4 * lo + 3] = 0.f;
         }
     }
     // centroid bounds for the Morton grid
@@ -139,20 +147,21 @@ __global__ void build_facets_kernel(const MeshDesc *__restrict__ meshes,
 const void *build_facets_kernel_fn(int *t0_arg_index, int *n_args)
 {
     *t0_arg_index = 4;      // meshes, insts, n_inst, F, t0, tri64, tri32, c64, fac, aabb,
-    *n_args = 12;           // vel32, bounds
+    *n_args = 14;           // vel32, bounds, ref64, ref32
     return reinterpret_cast<const void *>(build_facets_kernel);
 }
 
 void launch_build_facets(const MeshDesc *meshes, const InstDev *insts, int n_inst, int64_t F,
                          double t0, double *tri64, float *tri32, double *c64, FacetRec *fac,
-                         float *aabb, float *vel32, unsigned int *bounds, cudaStream_t s)
+                         float *aabb, float *vel32, unsigned int *bounds, double *ref64,
+                         float *ref32, cudaStream_t s)
 {
     cudaMemsetAsync(bounds, 0xff, 3 * sizeof(unsigned int), s);
     cudaMemsetAsync(bounds + 3, 0, 3 * sizeof(unsigned int), s);
     const int T = 256;
     const unsigned int G = (unsigned int)((F + T - 1) / T);
     build_facets_kernel<<<G, T, 0, s>>>(meshes, insts, n_inst, F, t0, tri64, tri32, c64, fac,
-                                        aabb, vel32, bounds);
+                                        aabb, vel32, bounds, ref64, ref32);
 }
 
 // -------------------------------------------------------------------------

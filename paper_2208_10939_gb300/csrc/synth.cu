@@ -73,9 +73,12 @@ __global__ void kin_kernel(const double *__restrict__ c64, const FacetRec *__res
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int a = blockIdx.y;
     if (i >= vis_cnt[rd.O + a]) return;              // facets lit from antenna a
-    // this thread's group of chirps within the chunk
+    // this thread's group of chirp slots within the chunk (one slot per chirp,
+    // or P with time-division MIMO: slot u of the chunk starts at
+    // (n0 slots + u) Tc)
+    const int nu = nc * rd.slots;
     const int g0 = blockIdx.z * kKinChirpsPerThread;
-    const int g1 = min(nc, g0 + kKinChirpsPerThread);
+    const int g1 = min(nu, g0 + kKinChirpsPerThread);
     const int64_t k = vis_idx[(int64_t)(rd.O + a) * F + i];
     const int inst = fac[k].inst;
     const double vx = vel64[3 * inst], vy = vel64[3 * inst + 1], vz = vel64[3 * inst + 2];
@@ -88,7 +91,7 @@ __global__ void kin_kernel(const double *__restrict__ c64, const FacetRec *__res
     const double f0c = rd.f0 / kC0;
     const double mu_f0 = rd.slope / (rd.fs * rd.f0);          // (mu/(fs c)) / (f0/c)
     // expansion point: middle of the frame's chirp starts
-    const double tc = 0.5 * (double)(rd.N - 1) * rd.Tc;
+    const double tc = 0.5 * (double)(rd.N * rd.slots - 1) * rd.Tc;
     const double tmax = tc > 0.0 ? tc : rd.Tc;
     const double q0 = A + tc * (B + tc * Cq), q1 = B + 2.0 * Cq * tc;
     const double a0 = sqrt(q0);
@@ -121,7 +124,7 @@ __global__ void kin_kernel(const double *__restrict__ c64, const FacetRec *__res
         }
     }
     for (int nl = g0; nl < g1; ++nl) {
-        const double t = (double)(n0 + nl) * rd.Tc;
+        const double t = (double)((int64_t)n0 * rd.slots + nl) * rd.Tc;
         const double tau = t - tc;
         double x0u = 0.0;
         float Rf = 0.f;
@@ -160,7 +163,7 @@ void launch_kinematics(const double *c64, const FacetRec *fac, const double *vel
 {
     const int T = 128;
     dim3 grid((unsigned int)((F + T - 1) / T), (unsigned int)rd.A,
-              (unsigned int)((nc + kKinChirpsPerThread - 1) / kKinChirpsPerThread));
+              (unsigned int)((nc * rd.slots + kKinChirpsPerThread - 1) / kKinChirpsPerThread));
     kin_kernel<<<grid, T, 0, s>>>(c64, fac, vel64, vis_idx, vis_cnt, F, rd, n0, nc, kin);
 }
 
@@ -271,7 +274,8 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
     const float eps_lane = 6.283185307179586f * (2.f * fm0 + (float)(S - 1));   // times p2
     const float ptx[3] = {K.ant[tx][0], K.ant[tx][1], K.ant[tx][2]};
     const float prx[3] = {K.ant[P + rx][0], K.ant[P + rx][1], K.ant[P + rx][2]};
-    const float tn = (float)n * K.tc;
+    const int slot = A.rd.tdm ? tx : 0;        // time-division MIMO: TX p in slot p
+    const float tn = (float)(n * A.rd.slots + slot) * K.tc;
 
     float pr[S], pi[S];
 #pragma unroll
@@ -284,8 +288,9 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
     }
 
     const int32_t *list = A.vis_idx + (int64_t)o * F + (A.vstart ? A.vstart[vrow] : 0);
-    const float4 *kin_t = A.kin + ((int64_t)nl * AA + tx) * F;
-    const float4 *kin_r = A.kin + ((int64_t)nl * AA + P + rx) * F;
+    const int64_t unit_s = (int64_t)nl * A.rd.slots + slot;
+    const float4 *kin_t = A.kin + (unit_s * AA + tx) * F;
+    const float4 *kin_r = A.kin + (unit_s * AA + P + rx) * F;
 
     for (int base = rbeg; base < rend; base += LPR) {
         // ---------------- build one record per lane ----------------
@@ -323,19 +328,41 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
 #pragma unroll
             for (int v = 0; v < 3; ++v)
                 u[v] = bt[0] * fr.dv[3 * v] + bt[1] * fr.dv[3 * v + 1] + bt[2] * fr.dv[3 * v + 2];
-            float Ld = 0.f, Ldd = 0.f;
-            if (A.rd.intra) {
-                const float v2 = vv.x * vv.x + vv.y * vv.y + vv.z * vv.z;
-                const float vt = vv.x * th[0] + vv.y * th[1] + vv.z * th[2];
-                const float vr = vv.x * rh[0] + vv.y * rh[1] + vv.z * rh[2];
-                Ld = -(vt + vr);
-                Ldd = (v2 - vt * vt) / Rt + (v2 - vr * vr) / Rr;
+            // the delay's motion within the chirp and the residual video phase
+            // follow the facet centroid, or (reference-point form) the
+            // instance origin: path Lp, its first and second time derivatives
+            float Lp = L, Ld = 0.f, Ldd = 0.f;
+            {
+                float ut[3] = {th[0], th[1], th[2]}, ur[3] = {rh[0], rh[1], rh[2]};
+                float Rtp = Rt, Rrp = Rr;
+                if (A.rd.delay_ref) {
+                    const float4 rf = reinterpret_cast<const float4 *>(A.ref32)[fr.inst];
+                    const float ox = fmaf(vv.x, tn, rf.x), oy = fmaf(vv.y, tn, rf.y),
+                                oz = fmaf(vv.z, tn, rf.z);
+                    float gt[3] = {ptx[0] - ox, ptx[1] - oy, ptx[2] - oz};
+                    float gr[3] = {prx[0] - ox, prx[1] - oy, prx[2] - oz};
+                    Rtp = sqrtf(gt[0] * gt[0] + gt[1] * gt[1] + gt[2] * gt[2]);
+                    Rrp = sqrtf(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
+                    Lp = Rtp + Rrp;
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) {
+                        ut[r] = gt[r] / Rtp;
+                        ur[r] = gr[r] / Rrp;
+                    }
+                }
+                if (A.rd.intra) {
+                    const float v2 = vv.x * vv.x + vv.y * vv.y + vv.z * vv.z;
+                    const float vt = vv.x * ut[0] + vv.y * ut[1] + vv.z * ut[2];
+                    const float vr = vv.x * ur[0] + vv.y * ur[1] + vv.z * ur[2];
+                    Ld = -(vt + vr);
+                    Ldd = (v2 - vt * vt) / Rtp + (v2 - vr * vr) / Rrp;
+                }
             }
             float hi = kt.y + kr.y;
             hi = hi >= 1.f ? hi - 1.f : hi;
-            const float loc = (kt.z + kr.z) + K.f0c_fs * Ld - K.mu_c2fs * L * Ld;
+            const float loc = (kt.z + kr.z) + K.f0c_fs * Ld - K.mu_c2fs * Lp * Ld;
             const float p2 = K.half_f0c_fs2 * Ldd + K.mu_c_fs2 * Ld;
-            const float ph0c = red1((kt.x + kr.x) - K.mu_2c2 * L * L);
+            const float ph0c = red1((kt.x + kr.x) - K.mu_2c2 * Lp * Lp);
             const float umin = fminf(fminf(u[0], u[1]), u[2]);
             const float umax = fmaxf(fmaxf(u[0], u[1]), u[2]);
             const float dmin = fminf(fminf(fabsf(u[0] - u[1]), fabsf(u[1] - u[2])),
@@ -840,6 +867,7 @@ struct __align__(16) RecD {
     int kind, flags;
     double qt[3];     // R_t(t)^2 = qt0 + t (qt1 + t qt2), t = fast time
     double qr[2];     // R_r(t)^2 = qr0 + t (qr1 + t qt2)
+    double ls;        // path-length shift of the delay (reference-point form)
     double d[22];
 };
 
@@ -865,7 +893,8 @@ synth_fp64_kernel(SynthArgs A, int W)
     const double c = kC0, f0 = A.rd.f0, mu = A.rd.slope, fs = A.rd.fs;
     const double f_max = f0 + mu * (A.rd.M - 1) / fs;
     const double k0 = 2.0 * kPi * f0 / c, kmax = 2.0 * kPi * f_max / c;
-    const double tn = (double)n * A.rd.Tc;
+    // chirp start of this channel: time-division MIMO puts TX p in slot p
+    const double tn = (double)((int64_t)n * A.rd.slots + (A.rd.tdm ? tx : 0)) * A.rd.Tc;
     const double *ptx = A.rd.ant[tx];
     const double *prx = A.rd.ant[P + rx];
 
@@ -891,13 +920,16 @@ synth_fp64_kernel(SynthArgs A, int W)
             for (int r = 0; r < 3; ++r) c0[r] = A.c64[3 * k + r];
             int flags = 0;
             cls = R.kind = build_record<double>(tri, c0, vel, tn, ptx, prx, (double)A.fac[k].rho,
-                                                A.rd.intra, k0, kmax, rec, &flags);
+                                                A.rd.intra, k0, kmax,
+                                                A.rd.delay_ref ? A.ref64 + 3 * inst : nullptr,
+                                                rec, &flags);
             R.flags = flags;
             R.qt[0] = rec[0];
             R.qt[1] = rec[1];
             R.qt[2] = rec[2];
             R.qr[0] = rec[3];
             R.qr[1] = rec[4];
+            R.ls = rec[kRecLs];
             for (int i = 0; i < 22; ++i) R.d[i] = rec[kRecD + i];
         }
         __syncwarp();
@@ -917,7 +949,7 @@ synth_fp64_kernel(SynthArgs A, int W)
                 const double fm = f0 + mu * t;
                 const double L = sqrt(R.qt[0] + t * (R.qt[1] + t * R.qt[2])) +
                                  sqrt(R.qr[0] + t * (R.qr[1] + t * R.qt[2]));
-                double thc = fm * L / c - mu * L * L / (2.0 * c * c);
+                double thc = fm * (L + R.ls) / c - mu * L * L / (2.0 * c * c);
                 thc -= rint(thc);
                 const double fmc = fm / c;
                 const double kp = fm / f0;
