@@ -160,7 +160,8 @@ struct SynthArgs {
     const int32_t *vstart;
     const int32_t *vcnt;
     int64_t F;
-    const float4 *kin;       // [nc][A][F] (mixed path)
+    const float4 *kin;       // [A][F][9] kinematics Taylor rows (mixed path)
+    const double *kquad;     // [A][F][3] R^2 quadratic of rows without a expansion
     int n0, nc;              // chirp chunk
     void *out;
     int out_c64;
@@ -174,9 +175,11 @@ struct SynthArgs {
     int layout_S;            // mixed-kernel samples per lane request (0 default, 8)
     RadarDev rd;
 };
-void launch_kinematics(const double *c64, const FacetRec *fac, const double *vel64,
-                       const int32_t *vis_idx, const int32_t *vis_cnt, int64_t F,
-                       const RadarDev &rd, int n0, int nc, float4 *kin, cudaStream_t s);
+// per (antenna, lit facet) Taylor rows of R(t) over the frame (see synth.cu)
+constexpr int kKinRowWords = 9;    // float4 per row
+void launch_kin_coef(const double *c64, const FacetRec *fac, const double *vel64,
+                     const int32_t *vis_idx, const int32_t *vis_cnt, int64_t F, const RadarDev &rd,
+                     float4 *coef, double *quad, cudaStream_t s);
 void launch_synth_mixed(const SynthArgs &a, cudaStream_t s);
 // scratch of the mixed path for F facets and a chunk of nc chirps
 // scene_F: facets of each scene (n_scene entries); tpi: 32-record tiles per

@@ -88,7 +88,6 @@ struct bart_ctx {
     bool tables_dirty = true;   // mesh / instance tables changed since the last frame
     int64_t frame_F = 0;
     int frame_A = 0;
-    int64_t kin_budget = 2LL << 30;
 
     DevBuf<MeshDesc> d_meshes;
     DevBuf<InstDev> d_insts;
@@ -105,7 +104,8 @@ struct bart_ctx {
     DevBuf<int32_t> parent, leaf_parent, flags;
     DevBuf<uint8_t> state;
     DevBuf<int32_t> blk_cnt, vis_idx, vis_cnt;
-    DevBuf<float4> kin;
+    DevBuf<float4> kin;                 // kinematics Taylor rows [A][F][9]
+    DevBuf<double> kquad;               // R^2 quadratics of the rows [A][F][3]
     DevBuf<float2> partial;             // mixed-path per-item partial sums
     DevBuf<int32_t> item_off;
     DevBuf<int> item_counter;
@@ -156,16 +156,13 @@ struct bart_ctx {
         }
     } fg;
 
-    // stage timing: fixed events + two per chirp chunk
+    // stage timing: fixed events + the kinematics and synthesis pairs
     bool timing = false;
     std::vector<cudaEvent_t> ev;        // 0 start, 1 facets, 2 bvh, 3 vis, 4 end, 5/6 rdm,
                                         // 7/8 detect
-    std::vector<cudaEvent_t> ev_kin;    // per chunk: before kin, after kin (= before synth)
-    std::vector<cudaEvent_t> ev_syn;    // per chunk: after synth
-    // side stream running the kinematics of chunk c+1 while chunk c is synthesised
-    cudaStream_t side = nullptr;
+    std::vector<cudaEvent_t> ev_kin;    // before / after the kinematics rows
+    std::vector<cudaEvent_t> ev_syn;    // before / after the synthesis
     cudaStream_t cap_stream = nullptr;  // frame-graph recording stream
-    std::vector<cudaEvent_t> sync_ev;   // fork + per-chunk kin-done / synth-done (no timing)
     int chunks = 0;
     int path = 0;
     bool have_rdm_timing = false;
@@ -180,8 +177,6 @@ struct bart_ctx {
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
         for (cudaEvent_t e : ev_kin) cudaEventDestroy(e);
         for (cudaEvent_t e : ev_syn) cudaEventDestroy(e);
-        for (cudaEvent_t e : sync_ev) cudaEventDestroy(e);
-        if (side) cudaStreamDestroy(side);
         if (cap_stream) cudaStreamDestroy(cap_stream);
         for (MeshStore *m : pool) {
             m->verts.release();
@@ -195,7 +190,7 @@ struct bart_ctx {
         keys.release(); keys_tmp.release(); sort_temp.release(); vals.release();
         vals_tmp.release(); nodes.release(); parent.release(); leaf_parent.release();
         flags.release(); state.release(); blk_cnt.release(); vis_idx.release();
-        vis_cnt.release(); kin.release(); partial.release(); item_off.release();
+        vis_cnt.release(); kin.release(); kquad.release(); partial.release(); item_off.release();
         item_counter.release(); counters.release(); status.release();
         rdm_ws.release(); adc_own.release(); rdm_own.release(); noise_scratch.release();
         fg.release();
@@ -590,40 +585,27 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
     const int tpi = ctx->tpi_override > 0
                         ? ctx->tpi_override
                         : synth_tiles_per_item(*std::max_element(scene_F.begin(), scene_F.end()));
-    int nc = rd.N, chunks = 1, nbuf = 1;
-    size_t chunk_words = 0;
     int64_t max_items = 0;
     if (path == BART_PATH_MIXED) {
-        // chirp chunks only when the kinematics table would exceed its budget;
-        // the table is then double-buffered so that the side stream fills
-        // chunk c+1 while the main stream synthesises chunk c (one chunk
-        // measured faster than forced chunking at the sedan size)
-        // one kinematics row per antenna, facet and chirp slot (P slots per
-        // chirp with time-division MIMO)
-        const int64_t per_chirp = (int64_t)rd.slots * A * F * (int64_t)sizeof(float4);
-        nc = (int)std::min<int64_t>(rd.N, std::max<int64_t>(1, ctx->kin_budget / per_chirp));
-        chunks = (rd.N + nc - 1) / nc;
-        nbuf = chunks > 1 ? 2 : 1;
-        chunk_words = (size_t)nc * rd.slots * A * F;
-        BART_TRY(ctx->kin.ensure(nbuf * chunk_words, "kinematics table"));
-        BART_TRY(ctx->partial.ensure((size_t)synth_partial_words(scene_F.data(), B, rd, nc,
+        // kinematics: Taylor rows of R(t) per antenna and facet (one launch,
+        // evaluated per record inside the synthesis)
+        BART_TRY(ctx->kin.ensure((size_t)A * F * kKinRowWords, "kinematics rows"));
+        BART_TRY(ctx->kquad.ensure((size_t)A * F * 3, "kinematics quadratics"));
+        BART_TRY(ctx->partial.ensure((size_t)synth_partial_words(scene_F.data(), B, rd, rd.N,
                                                                  tpi, ctx->layout_S),
                                      "synthesis partials"));
-        max_items = synth_max_items(scene_F.data(), B, rd, nc, tpi, ctx->layout_S);
+        max_items = synth_max_items(scene_F.data(), B, rd, rd.N, tpi, ctx->layout_S);
         BART_TRY(ctx->item_off.ensure((size_t)B * O + 1, "synthesis item table"));
         BART_TRY(ctx->item_counter.ensure(1, "synthesis item counter"));
-        if (!ctx->side)
-            CUDA_TRY(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking), "cudaStreamCreate");
-        BART_TRY(ensure_events(ctx->sync_ev, 1 + 2 * chunks, false));
         if (ctx->timing) {
-            BART_TRY(ensure_events(ctx->ev_kin, 2 * chunks));
-            BART_TRY(ensure_events(ctx->ev_syn, 2 * chunks));
+            BART_TRY(ensure_events(ctx->ev_kin, 2));
+            BART_TRY(ensure_events(ctx->ev_syn, 2));
         }
     }
     if (ctx->timing) BART_TRY(ensure_events(ctx->ev, 7));
 
-    // every launch of the frame, on the context's stream (and the side
-    // stream, joined back): run directly, or recorded into a frame graph
+    // every launch of the frame, on one stream: run directly, or recorded
+    // into a frame graph
     auto enqueue = [&](double t0v, bool tm, cudaStream_t s) -> int {
         CUDA_TRY(cudaMemsetAsync(ctx->counters.p, 0, 4 * sizeof(unsigned long long), s), "memset");
         if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[0], s), "cudaEventRecord");
@@ -686,6 +668,7 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
         a.vcnt = B > 1 ? ctx->vcnt.p : ctx->vis_cnt.p;
         a.F = F;
         a.kin = nullptr;
+        a.kquad = nullptr;
         a.out = adc;
         a.out_c64 = dtype == BART_C64;
         a.counters = ctx->counters.p;
@@ -697,42 +680,25 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
         a.layout_S = ctx->layout_S;
         a.rd = rd;
         if (path == BART_PATH_MIXED) {
-            cudaEvent_t fork = ctx->sync_ev[0];
-            cudaEvent_t *kin_done = ctx->sync_ev.data() + 1;
-            cudaEvent_t *syn_done = ctx->sync_ev.data() + 1 + chunks;
             a.partial = ctx->partial.p;
             a.item_off = ctx->item_off.p;
             a.item_counter = ctx->item_counter.p;
             a.max_items = max_items;
-            CUDA_TRY(cudaEventRecord(fork, s), "cudaEventRecord");
-            CUDA_TRY(cudaStreamWaitEvent(ctx->side, fork, 0), "cudaStreamWaitEvent");
-            auto kin_chunk = [&](int c) -> int {
-                const int n0 = c * nc;
-                const int cnt = std::min(nc, rd.N - n0);
-                if (c >= 2)   // its buffer was read by the synthesis of chunk c-2
-                    CUDA_TRY(cudaStreamWaitEvent(ctx->side, syn_done[c - 2], 0), "cudaStreamWaitEvent");
-                if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_kin[2 * c], ctx->side), "cudaEventRecord");
-                launch_kinematics(ctx->c64.p, ctx->fac.p, ctx->vel64.p, ctx->vis_idx.p,
-                                  ctx->vis_cnt.p, F, rd, n0, cnt, ctx->kin.p + (c % nbuf) * chunk_words,
-                                  ctx->side);
-                if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_kin[2 * c + 1], ctx->side), "cudaEventRecord");
-                CUDA_TRY(cudaEventRecord(kin_done[c], ctx->side), "cudaEventRecord");
-                return BART_OK;
-            };
-            BART_TRY(kin_chunk(0));
-            for (int c = 0; c < chunks; ++c) {
-                if (c + 1 < chunks) BART_TRY(kin_chunk(c + 1));
-                CUDA_TRY(cudaStreamWaitEvent(s, kin_done[c], 0), "cudaStreamWaitEvent");
-                a.n0 = c * nc;
-                a.nc = std::min(nc, rd.N - a.n0);
-                a.kin = ctx->kin.p + (c % nbuf) * chunk_words;
-                if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_syn[2 * c], s), "cudaEventRecord");
-                launch_synth_mixed(a, s);
-                if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_syn[2 * c + 1], s), "cudaEventRecord");
-                CUDA_TRY(cudaEventRecord(syn_done[c], s), "cudaEventRecord");
+            a.kin = ctx->kin.p;
+            a.kquad = ctx->kquad.p;
+            a.n0 = 0;
+            a.nc = rd.N;
+            if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_kin[0], s), "cudaEventRecord");
+            launch_kin_coef(ctx->c64.p, ctx->fac.p, ctx->vel64.p, ctx->vis_idx.p, ctx->vis_cnt.p,
+                            F, rd, ctx->kin.p, ctx->kquad.p, s);
+            if (tm) {
+                CUDA_TRY(cudaEventRecord(ctx->ev_kin[1], s), "cudaEventRecord");
+                CUDA_TRY(cudaEventRecord(ctx->ev_syn[0], s), "cudaEventRecord");
             }
-            ctx->chunks = chunks;
-            launches += 4 * chunks;
+            launch_synth_mixed(a, s);
+            if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_syn[1], s), "cudaEventRecord");
+            ctx->chunks = 1;
+            launches += 4;
         } else if (path == kPathAdjoint) {
             a.n0 = 0;
             a.nc = rd.N;
@@ -1235,8 +1201,7 @@ int bart_get_timing(bart_ctx *ctx, bart_timing *out)
     out->bvh_ms = elapsed(ctx->ev[1], ctx->ev[2]);
     out->visibility_ms = elapsed(ctx->ev[2], ctx->ev[3]);
     if (ctx->path == BART_PATH_MIXED) {
-        // kinematics runs on a side stream, overlapping the synthesis of the
-        // previous chunk: both sums are device time, not wall time
+        // the kinematics-row launch, then the synthesis launches
         for (int c = 0; c < ctx->chunks; ++c) {
             out->kinematics_ms += elapsed(ctx->ev_kin[2 * c], ctx->ev_kin[2 * c + 1]);
             out->synthesis_ms += elapsed(ctx->ev_syn[2 * c], ctx->ev_syn[2 * c + 1]);

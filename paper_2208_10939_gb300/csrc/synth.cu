@@ -48,37 +48,34 @@
 namespace bart {
 
 // -------------------------------------------------------------------------
-// kinematics (FP64): per antenna a, facet k lit from a, chirp n of the chunk
-//   R = |c_k + v t_n - p_a|,  x0 = frac(R f0/c),  x1 = frac(R mu/(fs c))
-//   hi = x1 rounded to a multiple of 2^-14, lo = x1 - hi
-// stored as float4 (x0, hi, lo, R).  Since m is an integer, frac(L q m) =
-// frac(frac(L q) m) and frac(hi m) is exact in FP32 for m < 1024.
-//
-// R(t) = sqrt(A + B t + C t^2) is expanded about the middle of the frame,
-// R = sum_j a_j tau^j, with a_0 = sqrt(q_0) and
+// kinematics: per antenna a and facet k lit from a, the one-way distance
+// R(t) = |c_k + v t - p_a| over the frame, as Taylor coefficients in the
+// chirp-slot index s (time s Tc; one slot per chirp, P with time-division
+// MIMO).  R^2 = A + B t + C t^2 is expanded about the middle slot s_c,
+// R = sum_j a_j tau^j with tau = s - s_c, a_0 = sqrt(q_0) and
 // a_j = (q_j - sum_{i=1}^{j-1} a_i a_{j-i}) / (2 a_0)  (from R^2 = q).  The
-// series converges with ratio rho = tau_max |v| / R (the roots of q lie at
-// |tau| = R/|v|); the degree is the smallest d <= 8 with
-// R rho^(d+1) / (1 - rho) <= 1e-11 m, else R is taken by a square root per
-// chirp.  This replaces an FP64 square root per chirp by d FMAs.
+// series converges with ratio rho = tau_max |v| Tc / R (the roots of q lie at
+// |tau| = R / (|v| Tc)); the degree is the smallest d <= 8 with
+// R rho^(d+1) / (1 - rho) <= 1e-11 m, else the record build takes an FP64
+// square root.  Computed once per frame in FP64 and stored per (a, k) as
+// kKinRow float4: (f0/c a_j split into a high and a low float, a_j in FP32);
+// the degree rides in row 0's w.  The mixed kernel evaluates the cycles
+// x0u = R f0 / c in double-float arithmetic (float pairs, error-free
+// transformations, Dekker 1971 / Knuth), reduces frac(x0u) and
+// frac(x0u mu / (fs f0)) (split into hi, a multiple of 2^-14, and lo) and R.
 // -------------------------------------------------------------------------
 constexpr int kKinMaxDeg = 8;
-constexpr int kKinChirpsPerThread = 16;   // chirps per thread: enough warps to hide FP64 latency
+constexpr int kKinRow = kKinMaxDeg + 1;    // float4 per antenna-facet row
 
-__global__ void kin_kernel(const double *__restrict__ c64, const FacetRec *__restrict__ fac,
-                           const double *__restrict__ vel64, const int32_t *__restrict__ vis_idx,
-                           const int32_t *__restrict__ vis_cnt, int64_t F, RadarDev rd, int n0,
-                           int nc, float4 *__restrict__ kin)
+__global__ void kin_coef_kernel(const double *__restrict__ c64, const FacetRec *__restrict__ fac,
+                                const double *__restrict__ vel64,
+                                const int32_t *__restrict__ vis_idx,
+                                const int32_t *__restrict__ vis_cnt, int64_t F, RadarDev rd,
+                                float4 *__restrict__ coef, double *__restrict__ quad)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int a = blockIdx.y;
     if (i >= vis_cnt[rd.O + a]) return;              // facets lit from antenna a
-    // this thread's group of chirp slots within the chunk (one slot per chirp,
-    // or P with time-division MIMO: slot u of the chunk starts at
-    // (n0 slots + u) Tc)
-    const int nu = nc * rd.slots;
-    const int g0 = blockIdx.z * kKinChirpsPerThread;
-    const int g1 = min(nu, g0 + kKinChirpsPerThread);
     const int64_t k = vis_idx[(int64_t)(rd.O + a) * F + i];
     const int inst = fac[k].inst;
     const double vx = vel64[3 * inst], vy = vel64[3 * inst + 1], vz = vel64[3 * inst + 2];
@@ -89,82 +86,113 @@ __global__ void kin_kernel(const double *__restrict__ c64, const FacetRec *__res
     const double B = 2.0 * (dx * vx + dy * vy + dz * vz);
     const double Cq = vx * vx + vy * vy + vz * vz;
     const double f0c = rd.f0 / kC0;
-    const double mu_f0 = rd.slope / (rd.fs * rd.f0);          // (mu/(fs c)) / (f0/c)
-    // expansion point: middle of the frame's chirp starts
-    const double tc = 0.5 * (double)(rd.N * rd.slots - 1) * rd.Tc;
-    const double tmax = tc > 0.0 ? tc : rd.Tc;
-    const double q0 = A + tc * (B + tc * Cq), q1 = B + 2.0 * Cq * tc;
+    const int64_t row = (int64_t)a * F + k;
+    double *qd = quad + 3 * row;
+    qd[0] = A;
+    qd[1] = B;
+    qd[2] = Cq;
+    // expansion point: the middle chirp slot; tau in slots
+    const double sc = 0.5 * (double)(rd.N * rd.slots - 1);
+    const double tc = sc * rd.Tc;
+    const double tmax = sc > 0.0 ? sc : 1.0;
+    const double q0 = A + tc * (B + tc * Cq);
+    const double q1 = (B + 2.0 * Cq * tc) * rd.Tc, q2 = Cq * rd.Tc * rd.Tc;
     const double a0 = sqrt(q0);
-    const double rho = tmax * sqrt(Cq / q0);
+    const double rho = tmax * sqrt(q2 / q0);
     int deg = -1;
     if (rho < 0.25) {
         double bound = a0 * rho * rho / (1.0 - rho);
         for (int d = 1; d <= kKinMaxDeg; ++d, bound *= rho)
             if (bound <= 1e-11) { deg = d; break; }
     }
-    // all kKinMaxDeg + 1 coefficients are formed (constant indices keep them
-    // in registers); only the first deg + 1 are used
-    double cf[kKinMaxDeg + 1];                   // f0/c * a_j: R in cycles at f0
-    float cr[kKinMaxDeg + 1];                    // a_j in FP32, for R itself
-    {
-        double aj[kKinMaxDeg + 1];
-        aj[0] = a0;
-        const double inv2a0 = 0.5 / a0;
-#pragma unroll
-        for (int j = 1; j <= kKinMaxDeg; ++j) {
-            double sacc = j == 1 ? q1 : (j == 2 ? Cq : 0.0);
-#pragma unroll
-            for (int l = 1; l < j; ++l) sacc -= aj[l] * aj[j - l];
-            aj[j] = sacc * inv2a0;
-        }
-#pragma unroll
-        for (int j = 0; j <= kKinMaxDeg; ++j) {
-            cf[j] = f0c * aj[j];
-            cr[j] = (float)aj[j];
-        }
+    float4 *out = coef + row * kKinRow;
+    if (deg < 0) {
+        out[0] = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+        return;
     }
-    for (int nl = g0; nl < g1; ++nl) {
-        const double t = (double)((int64_t)n0 * rd.slots + nl) * rd.Tc;
-        const double tau = t - tc;
-        double x0u = 0.0;
-        float Rf = 0.f;
-        switch (deg) {
-#define BART_KIN_CASE(D)                                                  \
-        case D: {                                                         \
-            const float tauf = (float)tau;                                \
-            x0u = cf[D];                                                  \
-            Rf = cr[D];                                                   \
-            _Pragma("unroll") for (int j = D - 1; j >= 0; --j) {          \
-                x0u = fma(x0u, tau, cf[j]);                               \
-                Rf = fmaf(Rf, tauf, cr[j]);                               \
-            }                                                             \
-        } break;
-        BART_KIN_CASE(1) BART_KIN_CASE(2) BART_KIN_CASE(3) BART_KIN_CASE(4)
-        BART_KIN_CASE(5) BART_KIN_CASE(6) BART_KIN_CASE(7) BART_KIN_CASE(8)
-#undef BART_KIN_CASE
-        default: {
-            const double R = sqrt(A + t * (B + t * Cq));
-            x0u = R * f0c;
-            Rf = (float)R;
-        }
-        }
-        double x1 = x0u * mu_f0;
-        x1 -= floor(x1);
-        const double x0 = x0u - floor(x0u);
-        const double hi = rint(x1 * 16384.0) * (1.0 / 16384.0);
-        kin[((int64_t)nl * rd.A + a) * F + k] =
-            make_float4((float)x0, (float)hi, (float)(x1 - hi), Rf);
+    double aj[kKinMaxDeg + 1];
+    aj[0] = a0;
+    const double inv2a0 = 0.5 / a0;
+#pragma unroll
+    for (int j = 1; j <= kKinMaxDeg; ++j) {
+        double sacc = j == 1 ? q1 : (j == 2 ? q2 : 0.0);
+#pragma unroll
+        for (int l = 1; l < j; ++l) sacc -= aj[l] * aj[j - l];
+        aj[j] = sacc * inv2a0;
+    }
+    for (int j = 0; j <= deg; ++j) {
+        const double cf = f0c * aj[j];
+        const float hi = (float)cf;
+        out[j] = make_float4(hi, (float)(cf - (double)hi), (float)aj[j],
+                             j == 0 ? __int_as_float(deg) : 0.f);
     }
 }
 
-void launch_kinematics(const double *c64, const FacetRec *fac, const double *vel64,
-                       const int32_t *vis_idx, const int32_t *vis_cnt, int64_t F,
-                       const RadarDev &rd, int n0, int nc, float4 *kin, cudaStream_t s)
+void launch_kin_coef(const double *c64, const FacetRec *fac, const double *vel64,
+                     const int32_t *vis_idx, const int32_t *vis_cnt, int64_t F, const RadarDev &rd,
+                     float4 *coef, double *quad, cudaStream_t s)
 {
     const int T = 128;
-    dim3 grid((unsigned int)((F + T - 1) / T), (unsigned int)rd.A,
-              (unsigned int)((nc * rd.slots + kKinChirpsPerThread - 1) / kKinChirpsPerThread));
-    kin_kernel<<<grid, T, 0, s>>>(c64, fac, vel64, vis_idx, vis_cnt, F, rd, n0, nc, kin);
+    dim3 grid((unsigned int)((F + T - 1) / T), (unsigned int)rd.A);
+    kin_coef_kernel<<<grid, T, 0, s>>>(c64, fac, vel64, vis_idx, vis_cnt, F, rd, coef, quad);
+}
+
+// double-float helpers: values xh + xl with |xl| <= ulp(xh) / 2; every
+// operation rounds once (explicit _rn intrinsics: no contraction)
+__device__ __forceinline__ void df_horner_step(float &xh, float &xl, float t, float ch, float cl)
+{
+    // (xh + xl) t + (ch + cl)
+    const float ph = __fmul_rn(xh, t);
+    float pl = __fmaf_rn(xh, t, -ph);                // exact product error
+    pl = __fmaf_rn(xl, t, pl);
+    const float sh = __fadd_rn(ph, ch);              // two-sum of ph and ch
+    const float bb = __fsub_rn(sh, ph);
+    float sl = __fadd_rn(__fsub_rn(ph, __fsub_rn(sh, bb)), __fsub_rn(ch, bb));
+    sl = __fadd_rn(sl, __fadd_rn(pl, cl));
+    xh = __fadd_rn(sh, sl);                          // renormalise
+    xl = __fsub_rn(sl, __fsub_rn(xh, sh));
+}
+
+// (x0 = frac(R f0 / c), hi, lo, R) of one antenna-facet row at chirp slot s;
+// hi + lo = frac(R mu / (fs c)), hi a multiple of 2^-14
+__device__ __forceinline__ float4 kin_eval(const float4 *__restrict__ row,
+                                           const double *__restrict__ quad, int s, float tau,
+                                           double Tc, double f0c, double mu_f0, float mfh, float mfl)
+{
+    const float4 r0 = row[0];
+    const int deg = __float_as_int(r0.w);
+    if (deg < 0) {
+        // no convergent expansion (a facet very close to the antenna): FP64
+        const double t = (double)s * Tc;
+        const double R = sqrt(quad[0] + t * (quad[1] + t * quad[2]));
+        const double x0u = R * f0c;
+        double x1 = x0u * mu_f0;
+        x1 -= floor(x1);
+        const double hi = rint(x1 * 16384.0) * (1.0 / 16384.0);
+        return make_float4((float)(x0u - floor(x0u)), (float)hi, (float)(x1 - hi), (float)R);
+    }
+    float4 c = row[deg];
+    float xh = c.x, xl = c.y, R = c.z;
+    for (int j = deg - 1; j >= 0; --j) {
+        c = j == 0 ? r0 : row[j];
+        df_horner_step(xh, xl, tau, c.x, c.y);
+        R = __fmaf_rn(R, tau, c.z);
+    }
+    // x0 = frac(x0u): xh - floor(xh) is exact (Sterbenz), then + xl
+    const float x0 = __fadd_rn(__fsub_rn(xh, floorf(xh)), xl);
+    // y = x0u mu_f0 in double-float, x1 = frac(y)
+    const float ph = __fmul_rn(xh, mfh);
+    float pl = __fmaf_rn(xh, mfh, -ph);
+    pl = __fmaf_rn(xh, mfl, pl);
+    pl = __fmaf_rn(xl, mfh, pl);
+    const float yh = __fadd_rn(ph, pl);
+    const float yl = __fsub_rn(pl, __fsub_rn(yh, ph));
+    const float x1h = __fsub_rn(yh, floorf(yh));
+    const float hi = __fmul_rn(rintf(__fmul_rn(x1h, 16384.f)), 1.f / 16384.f);
+    float lo = __fadd_rn(__fsub_rn(x1h, hi), yl);
+    float h2 = hi;
+    if (h2 >= 1.f) h2 -= 1.f;
+    return make_float4(x0, h2, lo, R);
 }
 
 // -------------------------------------------------------------------------
@@ -180,6 +208,9 @@ struct MixConsts {
     float mu_2c2;         // mu / (2 c^2)
     float k0, kmax;       // 2 pi f0 / c, 2 pi f_max / c
     float kap_step;       // mu / (fs f0): kappa_m = f_m / f0 = 1 + m kap_step
+    float mfh, mfl;       // mu / (fs f0) as a double-float (high, low)
+    double f0c_d, mu_f0_d;  // f0 / c and mu / (fs f0) in FP64 (fallback rows)
+    float s_mid;          // middle chirp slot of the frame (expansion point)
     float out_scale;      // C (c / (2 pi f0))^2
     float tc;
     float ant[kMaxAnt][3];
@@ -226,7 +257,7 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
     __shared__ float sAcc[kMixWarps][4][S][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row = lane / LPR, col = lane % LPR;
-    const int O = A.rd.O, P = A.rd.P, Q = A.rd.Q, AA = A.rd.A;
+    const int O = A.rd.O, P = A.rd.P, Q = A.rd.Q;
     const int TPI = A.tiles_per_item;
     const int64_t F = A.F;
     const int nc = A.nc;
@@ -288,9 +319,13 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
     }
 
     const int32_t *list = A.vis_idx + (int64_t)o * F + (A.vstart ? A.vstart[vrow] : 0);
-    const int64_t unit_s = (int64_t)nl * A.rd.slots + slot;
-    const float4 *kin_t = A.kin + (unit_s * AA + tx) * F;
-    const float4 *kin_r = A.kin + (unit_s * AA + P + rx) * F;
+    // kinematics rows of this channel's TX and RX, evaluated at chirp slot sl
+    const int sl = n * A.rd.slots + slot;
+    const float tau_s = (float)sl - K.s_mid;
+    const float4 *kin_t = A.kin + (int64_t)tx * F * kKinRow;
+    const float4 *kin_r = A.kin + (int64_t)(P + rx) * F * kKinRow;
+    const double *quad_t = A.kquad + (int64_t)tx * F * 3;
+    const double *quad_r = A.kquad + (int64_t)(P + rx) * F * 3;
 
     for (int base = rbeg; base < rend; base += LPR) {
         // ---------------- build one record per lane ----------------
@@ -301,7 +336,10 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
             const int k = list[base + col];
             const FacetRec fr = A.fac[k];
             const float4 vv = reinterpret_cast<const float4 *>(A.vel32)[fr.inst];
-            const float4 kt = kin_t[k], kr = kin_r[k];
+            const float4 kt = kin_eval(kin_t + (int64_t)k * kKinRow, quad_t + 3 * (int64_t)k, sl,
+                                       tau_s, A.rd.Tc, K.f0c_d, K.mu_f0_d, K.mfh, K.mfl);
+            const float4 kr = kin_eval(kin_r + (int64_t)k * kKinRow, quad_r + 3 * (int64_t)k, sl,
+                                       tau_s, A.rd.Tc, K.f0c_d, K.mu_f0_d, K.mfh, K.mfl);
             const float cx = fmaf(vv.x, tn, fr.c[0]);
             const float cy = fmaf(vv.y, tn, fr.c[1]);
             const float cz = fmaf(vv.z, tn, fr.c[2]);
@@ -748,6 +786,11 @@ static MixConsts mix_consts(const RadarDev &rd)
     K.k0 = (float)(2.0 * kPi * f0 / c);
     K.kmax = (float)(2.0 * kPi * f_max / c);
     K.kap_step = (float)(mu / (fs * f0));
+    K.mu_f0_d = mu / (fs * f0);
+    K.f0c_d = f0 / c;
+    K.mfh = (float)K.mu_f0_d;
+    K.mfl = (float)(K.mu_f0_d - (double)K.mfh);
+    K.s_mid = (float)(0.5 * (double)(rd.N * rd.slots - 1));
     const double camp = 2.0 * sqrt(kPi) / pow(4.0 * kPi, 1.5);
     const double lk = c / (2.0 * kPi * f0);
     K.out_scale = (float)(camp * lk * lk);
