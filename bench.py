@@ -41,7 +41,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x lanes x FMA x max cl
 # DRAM bytes (read + write) of one synthesis launch on this workload, from the
 # ncu capture summarised in profiles/synth_mixed_moving_sedan.md; valid only
 # while the kernel's sources hash to the value they had at the capture
-SYNTH_TRAFFIC = {"bytes": 258.733568e6 + 31.002368e6, "sources_sha256_16": "90bbc5b01ce3e19e"}
+SYNTH_TRAFFIC = {"bytes": 8.229376e6 + 0.495104e6, "sources_sha256_16": "112442227b65a597"}
 SYNTH_SOURCES = ("synth.cu", "bart_internal.cuh", "record_fp64.cuh")
 
 

@@ -108,6 +108,7 @@ __global__ void kin_coef_kernel(const double *__restrict__ c64, const FacetRec *
     float4 *out = coef + row * kKinRow;
     if (deg < 0) {
         out[0] = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+        for (int j = 1; j <= kKinMaxDeg; ++j) out[j] = make_float4(0.f, 0.f, 0.f, 0.f);
         return;
     }
     double aj[kKinMaxDeg + 1];
@@ -120,7 +121,13 @@ __global__ void kin_coef_kernel(const double *__restrict__ c64, const FacetRec *
         for (int l = 1; l < j; ++l) sacc -= aj[l] * aj[j - l];
         aj[j] = sacc * inv2a0;
     }
-    for (int j = 0; j <= deg; ++j) {
+    // rows above the degree are zero, so two rows of different degrees can
+    // share one Horner loop
+    for (int j = 0; j <= kKinMaxDeg; ++j) {
+        if (j > deg) {
+            out[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+            continue;
+        }
         const double cf = f0c * aj[j];
         const float hi = (float)cf;
         out[j] = make_float4(hi, (float)(cf - (double)hi), (float)aj[j],
@@ -153,34 +160,12 @@ __device__ __forceinline__ void df_horner_step(float &xh, float &xl, float t, fl
     xl = __fsub_rn(sl, __fsub_rn(xh, sh));
 }
 
-// (x0 = frac(R f0 / c), hi, lo, R) of one antenna-facet row at chirp slot s;
-// hi + lo = frac(R mu / (fs c)), hi a multiple of 2^-14
-__device__ __forceinline__ float4 kin_eval(const float4 *__restrict__ row,
-                                           const double *__restrict__ quad, int s, float tau,
-                                           double Tc, double f0c, double mu_f0, float mfh, float mfl)
+// (x0, hi, lo, R) from the double-float cycles x0u = xh + xl and R:
+// x0 = frac(x0u), hi + lo = frac(x0u mu / (fs f0)), hi a multiple of 2^-14
+__device__ __forceinline__ float4 kin_finish(float xh, float xl, float R, float mfh, float mfl)
 {
-    const float4 r0 = row[0];
-    const int deg = __float_as_int(r0.w);
-    if (deg < 0) {
-        // no convergent expansion (a facet very close to the antenna): FP64
-        const double t = (double)s * Tc;
-        const double R = sqrt(quad[0] + t * (quad[1] + t * quad[2]));
-        const double x0u = R * f0c;
-        double x1 = x0u * mu_f0;
-        x1 -= floor(x1);
-        const double hi = rint(x1 * 16384.0) * (1.0 / 16384.0);
-        return make_float4((float)(x0u - floor(x0u)), (float)hi, (float)(x1 - hi), (float)R);
-    }
-    float4 c = row[deg];
-    float xh = c.x, xl = c.y, R = c.z;
-    for (int j = deg - 1; j >= 0; --j) {
-        c = j == 0 ? r0 : row[j];
-        df_horner_step(xh, xl, tau, c.x, c.y);
-        R = __fmaf_rn(R, tau, c.z);
-    }
-    // x0 = frac(x0u): xh - floor(xh) is exact (Sterbenz), then + xl
+    // xh - floor(xh) is exact (Sterbenz), then + xl
     const float x0 = __fadd_rn(__fsub_rn(xh, floorf(xh)), xl);
-    // y = x0u mu_f0 in double-float, x1 = frac(y)
     const float ph = __fmul_rn(xh, mfh);
     float pl = __fmaf_rn(xh, mfh, -ph);
     pl = __fmaf_rn(xh, mfl, pl);
@@ -188,11 +173,54 @@ __device__ __forceinline__ float4 kin_eval(const float4 *__restrict__ row,
     const float yh = __fadd_rn(ph, pl);
     const float yl = __fsub_rn(pl, __fsub_rn(yh, ph));
     const float x1h = __fsub_rn(yh, floorf(yh));
-    const float hi = __fmul_rn(rintf(__fmul_rn(x1h, 16384.f)), 1.f / 16384.f);
-    float lo = __fadd_rn(__fsub_rn(x1h, hi), yl);
-    float h2 = hi;
-    if (h2 >= 1.f) h2 -= 1.f;
-    return make_float4(x0, h2, lo, R);
+    float hi = __fmul_rn(rintf(__fmul_rn(x1h, 16384.f)), 1.f / 16384.f);
+    const float lo = __fadd_rn(__fsub_rn(x1h, hi), yl);
+    if (hi >= 1.f) hi -= 1.f;
+    return make_float4(x0, hi, lo, R);
+}
+
+// a row without a convergent expansion: FP64 square root at slot s
+__device__ __forceinline__ float4 kin_fallback(const double *__restrict__ quad, int s, double Tc,
+                                               double f0c, double mu_f0)
+{
+    const double t = (double)s * Tc;
+    const double R = sqrt(quad[0] + t * (quad[1] + t * quad[2]));
+    const double x0u = R * f0c;
+    double x1 = x0u * mu_f0;
+    x1 -= floor(x1);
+    const double hi = rint(x1 * 16384.0) * (1.0 / 16384.0);
+    return make_float4((float)(x0u - floor(x0u)), (float)hi, (float)(x1 - hi), (float)R);
+}
+
+// the TX and RX rows of one record at chirp slot s (tau = s - s_mid), in one
+// Horner loop: each iteration loads the two rows' coefficients together
+__device__ __forceinline__ void kin_eval2(const float4 *__restrict__ rt,
+                                          const float4 *__restrict__ rr,
+                                          const double *__restrict__ qt,
+                                          const double *__restrict__ qr, int s, float tau,
+                                          double Tc, double f0c, double mu_f0, float mfh,
+                                          float mfl, float4 &kt, float4 &kr)
+{
+    const float4 t0 = rt[0], r0 = rr[0];
+    const int dt = __float_as_int(t0.w), dr = __float_as_int(r0.w);
+    const int D = max(dt, dr);
+    float th = 0.f, tl = 0.f, tR = 0.f, rh = 0.f, rl = 0.f, rR = 0.f;
+    if (D > 0) {
+        const float4 ct = rt[D], cr = rr[D];   // zero above each row's own degree
+        th = ct.x; tl = ct.y; tR = ct.z;
+        rh = cr.x; rl = cr.y; rR = cr.z;
+    }
+#pragma unroll 2
+    for (int j = D - 1; j >= 0; --j) {
+        const float4 ct = j == 0 ? t0 : rt[j];
+        const float4 cr = j == 0 ? r0 : rr[j];
+        df_horner_step(th, tl, tau, ct.x, ct.y);
+        tR = __fmaf_rn(tR, tau, ct.z);
+        df_horner_step(rh, rl, tau, cr.x, cr.y);
+        rR = __fmaf_rn(rR, tau, cr.z);
+    }
+    kt = dt < 0 ? kin_fallback(qt, s, Tc, f0c, mu_f0) : kin_finish(th, tl, tR, mfh, mfl);
+    kr = dr < 0 ? kin_fallback(qr, s, Tc, f0c, mu_f0) : kin_finish(rh, rl, rR, mfh, mfl);
 }
 
 // -------------------------------------------------------------------------
@@ -336,10 +364,10 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
             const int k = list[base + col];
             const FacetRec fr = A.fac[k];
             const float4 vv = reinterpret_cast<const float4 *>(A.vel32)[fr.inst];
-            const float4 kt = kin_eval(kin_t + (int64_t)k * kKinRow, quad_t + 3 * (int64_t)k, sl,
-                                       tau_s, A.rd.Tc, K.f0c_d, K.mu_f0_d, K.mfh, K.mfl);
-            const float4 kr = kin_eval(kin_r + (int64_t)k * kKinRow, quad_r + 3 * (int64_t)k, sl,
-                                       tau_s, A.rd.Tc, K.f0c_d, K.mu_f0_d, K.mfh, K.mfl);
+            float4 kt, kr;
+            kin_eval2(kin_t + (int64_t)k * kKinRow, kin_r + (int64_t)k * kKinRow,
+                      quad_t + 3 * (int64_t)k, quad_r + 3 * (int64_t)k, sl, tau_s, A.rd.Tc,
+                      K.f0c_d, K.mu_f0_d, K.mfh, K.mfl, kt, kr);
             const float cx = fmaf(vv.x, tn, fr.c[0]);
             const float cy = fmaf(vv.y, tn, fr.c[1]);
             const float cz = fmaf(vv.z, tn, fr.c[2]);
