@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--batch-size", type=int, default=8)
     ap.add_argument("--adjoint-reps", type=int, default=1,
                     help="timed runs of the perturbed-sedan gradient (0 skips)")
+    ap.add_argument("--no-intersection", action="store_true",
+                    help="skip the full-intersection frame")
     return ap.parse_args()
 
 
@@ -329,6 +331,38 @@ def detect_timing(pkg, torch, sim, adc, stream, reps: int = 10) -> dict:
             "cfar": "guard 2x2, train 8x4, Pfa 1e-6"}
 
 
+def intersection_frame(pkg, sg, torch, dev) -> dict:
+    """The full intersection (12 vehicles + ground, ~1.5M facets, 12 TX x
+    16 RX = 192 channels, 256 chirps x 512 samples): one mixed-path frame and
+    its RDM after a warm-up frame; per-stage CUDA-event times."""
+    sc = sg.intersection_scene()
+    s = pkg.Simulator(dev.index or 0)
+    try:
+        s.load_scene(sc)
+        r = sc.radar
+        adc = torch.empty((r.O, r.N, r.M), dtype=torch.complex64, device=dev)
+        rdm = torch.empty((r.M, r.N), dtype=torch.float32, device=dev)
+        pkg.bart_set_timing(s.ctx, True)
+        _, st = s.simulate(pkg.PATH_MIXED, out=adc, stats=True)
+        s.rdm(adc, rdm)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s.simulate(pkg.PATH_MIXED, out=adc)
+        s.rdm(adc, rdm)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        tm = pkg.bart_get_timing(s.ctx)
+        return {"workload": "intersection: %d facets, 192 channels, 256 x 512" % st["n_facets"],
+                "terms": st["n_terms"], "frame_ms": ms, "terms_per_s": st["n_terms"] / (ms / 1e3),
+                "stages_ms": {k: tm[k] for k in ("scene_ms", "bvh_ms", "visibility_ms",
+                                                 "kinematics_ms", "synthesis_ms", "rdm_ms")}}
+    finally:
+        s.close()
+
+
 def adjoint_timing(pkg, sg, torch, dev, reps: int) -> dict:
     """Differentiable echo on the perturbed-sedan inverse problem: the
     sedan as target, its copy with 5 mm vertex noise (seed 5) as the
@@ -346,7 +380,7 @@ def adjoint_timing(pkg, sg, torch, dev, reps: int) -> dict:
         v0 = v_true + torch.from_numpy(0.005 * rng.normal(size=tuple(v_true.shape))).to(dev)
         st = pkg.bart_simulate_frame(s.ctx, 0.0, pkg.PATH_FP64, target.clone(), stats=True)
         fwd, bwd = [], []
-        for _ in range(reps):
+        for rep in range(reps + 1):          # the first pass warms up (allocations)
             verts = v0.clone().requires_grad_(True)
             e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
             e0.record()
@@ -356,8 +390,9 @@ def adjoint_timing(pkg, sg, torch, dev, reps: int) -> dict:
             loss.backward()
             e2.record()
             e2.synchronize()
-            fwd.append(e0.elapsed_time(e1))
-            bwd.append(e0.elapsed_time(e2) - e0.elapsed_time(e1))
+            if rep > 0:
+                fwd.append(e0.elapsed_time(e1))
+                bwd.append(e0.elapsed_time(e2) - e0.elapsed_time(e1))
         terms = st["n_terms"]
         return {"workload": "sedan 20k tris, target vs 5 mm vertex noise (seed 5), "
                             "L = ||adc - adc_target||^2, FP64",
@@ -508,6 +543,9 @@ def main():
     adj = None
     if world == 1 and args.adjoint_reps > 0:
         adj = adjoint_timing(pkg, sg, torch, dev, args.adjoint_reps)
+    inter = None
+    if world == 1 and not args.no_intersection:
+        inter = intersection_frame(pkg, sg, torch, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -545,6 +583,7 @@ def main():
         "gpu_launches": launches,
         "cpu_baseline": cpu,
         "point_cloud": det,
+        "intersection_frame": inter,
         "differentiable_echo": adj,
         "dataset_batch": batch,
         "dataset_batch_small": batch_small,
