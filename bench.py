@@ -41,12 +41,18 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x lanes x FMA x max cl
 # DRAM bytes (read + write) of one synthesis launch on this workload, from the
 # ncu capture summarised in profiles/synth_mixed_moving_sedan.md; valid only
 # while the kernel's sources hash to the value they had at the capture
-SYNTH_TRAFFIC = {"bytes": 8.229376e6 + 0.495104e6, "sources_sha256_16": "112442227b65a597"}
+SYNTH_TRAFFIC = {"bytes": 8.229376e6 + 0.495104e6, "sources_sha256_16": "112442227b65a597",
+                 "samples_per_lane": 16}
 SYNTH_SOURCES = ("synth.cu", "bart_internal.cuh", "record_fp64.cuh")
 
 
-def synth_traffic():
+def synth_traffic(samples_per_lane: int = 16):
+    """Captured DRAM bytes per synthesis launch, or None when the kernel (its
+    sources, or the template instance chosen by the layout) differs from the
+    captured one."""
     import hashlib
+    if samples_per_lane != SYNTH_TRAFFIC["samples_per_lane"]:
+        return None
     h = hashlib.sha256()
     for f in SYNTH_SOURCES:
         with open(os.path.join(ROOT, "paper_2208_10939_gb300", "csrc", f), "rb") as fh:
@@ -70,6 +76,8 @@ def parse():
     ap.add_argument("--batch-size", type=int, default=8)
     ap.add_argument("--adjoint-reps", type=int, default=1,
                     help="timed runs of the perturbed-sedan gradient (0 skips)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="time the default synthesis layout instead of the autotuned one")
     ap.add_argument("--no-intersection", action="store_true",
                     help="skip the full-intersection frame")
     return ap.parse_args()
@@ -432,6 +440,11 @@ def main():
     pkg.bart_set_timing(sim.ctx, True)
     _, st = sim.simulate(pkg.PATH_MIXED, out=adc, stats=True)
     terms = st["n_terms"]
+    tune = None
+    if not args.no_autotune:
+        # the library's autotuner picks the synthesis layout for this scene
+        # (timed synthesis trials; untimed here, part of the warm-up)
+        tune = pkg.bart_autotune(sim.ctx, 0.0, adc, reps=2)
     for _ in range(args.warmup):
         sim.simulate(pkg.PATH_MIXED, out=adc)
         sim.rdm(adc, rdm)
@@ -565,15 +578,22 @@ def main():
         "config": {"workload": WORKLOAD, "path": "mixed (FP64 phase, FP32 phasors, Kahan)",
                    "adc": "complex64", "rdm": "256x128 fp32", "facets": st["n_facets"],
                    "echo_terms_per_frame": terms, "l2": "flushed between steps (256 MB write)",
-                   "parallelism": f"replicas x{world}", "seed": 2},
+                   "parallelism": f"replicas x{world}", "seed": 2,
+                   "synthesis_layout": (None if tune is None else
+                                        {"samples_per_lane": tune["best"][0],
+                                         "tiles_per_item": tune["best"][1],
+                                         "source": "bart_autotune"})},
         "frames_per_s": frames,
         "fp64_path": fp64,
         "stages_ms_last_step": {k: last_tm[k] for k in
                                 ("scene_ms", "bvh_ms", "visibility_ms", "kinematics_ms",
                                  "synthesis_ms", "rdm_ms")},
-        "roofline": {"bound": "alu", "kernel": "synth_mixed_kernel",
+        "roofline": {"bound": "alu",
+                     "kernel": "synth_mixed_kernel<%d, %d>" % (
+                         (16, 16) if tune is None or tune["best"][0] == 16 else (8, 32)),
                      "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": synth_traffic(),
+                     "frac": achieved / FP32_PEAK_TFLOPS,
+                     "traffic": synth_traffic(16 if tune is None else tune["best"][0]),
                      "traffic_unit": "bytes per launch (ncu dram read + write)",
                      "flops_per_term": FLOPS_PER_TERM,
                      "launch_ms": synth_avg_ms,
