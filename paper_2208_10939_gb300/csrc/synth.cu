@@ -271,6 +271,44 @@ constexpr int kMixMinBlocks = 10;    // resident CTAs per SM the register budget
 
 __device__ __forceinline__ float red1(float x) { return x - rintf(x); }
 
+// Packed FP32 pairs (sm_100+ f32x2 arithmetic): two floats in one 64-bit
+// register pair, one instruction for both lanes of a pair.  The mixed
+// kernel keeps two consecutive samples of a lane in one pair.
+__device__ __forceinline__ uint64_t pk2(float lo, float hi)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk2(uint64_t r, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r));
+}
+__device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t fmul2(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t fadd2(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t fsub2(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
 // S: consecutive samples per lane; LPR: lanes per chirp row (RPW = 32/LPR
 // rows of the same channel share a warp, e.g. two 256-sample chirps at
 // S = 16).  A 32-record tile holds LPR facets x RPW chirps: lane l builds
@@ -336,10 +374,15 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
     const int slot = A.rd.tdm ? tx : 0;        // time-division MIMO: TX p in slot p
     const float tn = (float)(n * A.rd.slots + slot) * K.tc;
 
-    float pr[S], pi[S];
+    // per-tile partial sums: samples (2k, 2k+1) of the lane packed in one pair
+    // (an odd S computes one extra sample in the last pair and drops it)
+    constexpr int S2 = (S + 1) / 2;
+    uint64_t PR[S2], PI[S2];
+    const uint64_t zero2 = pk2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < S2; ++k) PR[k] = PI[k] = zero2;
 #pragma unroll
     for (int j = 0; j < S; ++j) {
-        pr[j] = pi[j] = 0.f;
         sAcc[warp][0][j][lane] = 0.f;
         sAcc[warp][1][j][lane] = 0.f;
         sAcc[warp][2][j][lane] = 0.f;
@@ -562,14 +605,21 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
                     const float stc = fmaf(-eps, sim[v], sre[v]);
                     const float sts = fmaf(eps, sre[v], sim[v]);
                     const float w = wv[v];
+                    // the phasor at samples (m0 + 2k, m0 + 2k + 1), advanced by
+                    // the two-sample step
+                    const float zc1 = fmaf(zc, stc, -zs * sts), zs1 = fmaf(zc, sts, zs * stc);
+                    const float c2 = fmaf(stc, stc, -sts * sts), s2 = 2.f * stc * sts;
+                    uint64_t ZC = pk2(zc, zc1), ZS = pk2(zs, zs1);
+                    const uint64_t C2 = pk2(c2, c2), S2v = pk2(s2, s2), NS2 = pk2(-s2, -s2);
+                    const uint64_t W2 = pk2(w, w);
     #pragma unroll
-                    for (int j = 0; j < S; ++j) {
-                        pr[j] = fmaf(w, zc, pr[j]);
-                        pi[j] = fmaf(w, zs, pi[j]);
-                        if (j + 1 < S) {
-                            const float nc_ = fmaf(zc, stc, -zs * sts);
-                            zs = fmaf(zc, sts, zs * stc);
-                            zc = nc_;
+                    for (int k = 0; k < S2; ++k) {
+                        PR[k] = ffma2(W2, ZC, PR[k]);
+                        PI[k] = ffma2(W2, ZS, PI[k]);
+                        if (k + 1 < S2) {
+                            const uint64_t nc_ = ffma2(ZS, NS2, fmul2(ZC, C2));
+                            ZS = ffma2(ZC, S2v, fmul2(ZS, C2));
+                            ZC = nc_;
                         }
                     }
                 }
@@ -609,24 +659,37 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
                     w3r = fmaf(wA3[v], zs, w3r);         // -j w A^3/6 z
                     w3i = fmaf(-wA3[v], zc, w3i);
                 }
-                // forward differences of the cubic
-                float d1r = w1r + w2r + w3r, d1i = w1i + w2i + w3i;
-                float d2r = fmaf(6.f, w3r, 2.f * w2r), d2i = fmaf(6.f, w3i, 2.f * w2i);
-                const float d3r = 6.f * w3r, d3i = 6.f * w3i;
+                // W at the sample pairs (2k, 2k+1): forward differences of the
+                // cubic with step 2 -- for s^3 they start at 8, 26 (first),
+                // 48, 72 (second), 48 (third); for s^2 at 4, 8 and 8; for s at 2
+                uint64_t WR = pk2(w0r, w0r + w1r + w2r + w3r), WI = pk2(w0i, w0i + w1i + w2i + w3i);
+                uint64_t D1R = pk2(fmaf(8.f, w3r, fmaf(4.f, w2r, 2.f * w1r)),
+                                   fmaf(26.f, w3r, fmaf(8.f, w2r, 2.f * w1r)));
+                uint64_t D1I = pk2(fmaf(8.f, w3i, fmaf(4.f, w2i, 2.f * w1i)),
+                                   fmaf(26.f, w3i, fmaf(8.f, w2i, 2.f * w1i)));
+                uint64_t D2R = pk2(fmaf(48.f, w3r, 8.f * w2r), fmaf(72.f, w3r, 8.f * w2r));
+                uint64_t D2I = pk2(fmaf(48.f, w3i, 8.f * w2i), fmaf(72.f, w3i, 8.f * w2i));
+                const uint64_t D3R = pk2(48.f * w3r, 48.f * w3r), D3I = pk2(48.f * w3i, 48.f * w3i);
+                // the centroid phasor at the pairs, advanced by two samples
+                const float cc1 = fmaf(cc, stc, -cs * sts), cs1 = fmaf(cc, sts, cs * stc);
+                const float c2 = fmaf(stc, stc, -sts * sts), s2 = 2.f * stc * sts;
+                uint64_t CC = pk2(cc, cc1), CS = pk2(cs, cs1);
+                const uint64_t C2 = pk2(c2, c2), S2v = pk2(s2, s2), NS2 = pk2(-s2, -s2);
     #pragma unroll
-                for (int j = 0; j < S; ++j) {
-                    pr[j] = fmaf(cc, w0r, fmaf(-cs, w0i, pr[j]));
-                    pi[j] = fmaf(cc, w0i, fmaf(cs, w0r, pi[j]));
-                    if (j + 1 < S) {
-                        const float nc_ = fmaf(cc, stc, -cs * sts);
-                        cs = fmaf(cc, sts, cs * stc);
-                        cc = nc_;
-                        w0r += d1r;
-                        w0i += d1i;
-                        d1r += d2r;
-                        d1i += d2i;
-                        d2r += d3r;
-                        d2i += d3i;
+                for (int k = 0; k < S2; ++k) {
+                    // (pr, pi) += C W
+                    PR[k] = fsub2(ffma2(CC, WR, PR[k]), fmul2(CS, WI));
+                    PI[k] = ffma2(CS, WR, ffma2(CC, WI, PI[k]));
+                    if (k + 1 < S2) {
+                        const uint64_t nc_ = ffma2(CS, NS2, fmul2(CC, C2));
+                        CS = ffma2(CC, S2v, fmul2(CS, C2));
+                        CC = nc_;
+                        WR = fadd2(WR, D1R);
+                        WI = fadd2(WI, D1I);
+                        D1R = fadd2(D1R, D2R);
+                        D1I = fadd2(D1I, D2I);
+                        D2R = fadd2(D2R, D3R);
+                        D2I = fadd2(D2I, D3I);
                     }
                 }
         
@@ -639,6 +702,7 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
                     const float fm = (float)(m0 + j);
                     const float thc = fmaf(R[3], fm * fm, fmaf(R[2], fm, R[0] + red1(R[1] * fm)));
                     const float kp = fmaf(fm, K.kap_step, 1.f);
+                    float dr = 0.f, di = 0.f;        // this sample's term
                     if (series) {
                         const float th = red1(thc + fmaf(R[5], fm, R[4]));
                         float zs, zc;
@@ -650,8 +714,8 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
     #pragma unroll
                         for (int q = 5; q >= 0; --q) bb = fmaf(bb, k2, R[14 + q]);
                         const float re = a * k2, im = bb * k2 * kp;
-                        pr[j] += zc * re - zs * im;
-                        pi[j] += zc * im + zs * re;
+                        dr = zc * re - zs * im;
+                        di = zc * im + zs * re;
                     } else {
                         const int flags = __float_as_int(R[16]);
     #pragma unroll
@@ -669,15 +733,27 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
                                 sn = sinf(x) / x;   // accurate sinf: |x| may reach ~1e3
                             }
                             const float coef = kp * R[7 + 4 * e] * sn;
-                            pr[j] = fmaf(-coef, zs, pr[j]);
-                            pi[j] = fmaf(coef, zc, pi[j]);
+                            dr = fmaf(-coef, zs, dr);
+                            di = fmaf(coef, zc, di);
                         }
                     }
+                    // into sample j's half of its pair
+                    const uint64_t DR = (j & 1) ? pk2(0.f, dr) : pk2(dr, 0.f);
+                    const uint64_t DI = (j & 1) ? pk2(0.f, di) : pk2(di, 0.f);
+                    PR[j >> 1] = fadd2(PR[j >> 1], DR);
+                    PI[j >> 1] = fadd2(PI[j >> 1], DI);
                 }
         
             }
         }
         // ---------------- Kahan-compensated tile accumulation ----------------
+        float pr[2 * S2], pi[2 * S2];
+#pragma unroll
+        for (int k = 0; k < S2; ++k) {
+            upk2(PR[k], pr[2 * k], pr[2 * k + 1]);
+            upk2(PI[k], pi[2 * k], pi[2 * k + 1]);
+            PR[k] = PI[k] = zero2;
+        }
 #pragma unroll
         for (int j = 0; j < S; ++j) {
             float sr = sAcc[warp][0][j][lane], si = sAcc[warp][1][j][lane];
@@ -694,7 +770,6 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
             sAcc[warp][1][j][lane] = si;
             sAcc[warp][2][j][lane] = cr;
             sAcc[warp][3][j][lane] = ci;
-            pr[j] = pi[j] = 0.f;
         }
         __syncwarp();
     }
