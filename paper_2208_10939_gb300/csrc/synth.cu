@@ -247,7 +247,8 @@ struct MixConsts {
 // One record per (facet, channel, chirp), 24 words in shared memory; the
 // layout depends on its form:
 //   vertex (V): [0..2] ph0_v  [3..5] lo_v  [6..8] w_v  [9..11] step re
-//               [12..14] step im  [15] hi  [16] p2
+//               [12..14] step im  [15] hi  [16] p2  [17..19] two-sample step re
+//               [20..22] two-sample step im
 //   factored (F): [0] ph0c [1] hi [2] loc [3] p2 [4..5] centroid step
 //               [6..8] psi_v  [9..11] a_v  [12..14] w_v  [15..17] w_v A_v
 //               [18..20] -w_v A_v^2 / 2  [21..23] w_v A_v^3 / 6
@@ -320,7 +321,10 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
     constexpr int RPW = 32 / LPR;
     __shared__ RecM sRec[kMixWarps][32];
     // running sums and Kahan compensations: [warp][re, im, c_re, c_im][S][lane]
-    __shared__ float sAcc[kMixWarps][4][S][32];
+    constexpr int S2 = (S + 1) / 2;
+    // running sums and Kahan compensations of the sample pairs:
+    // [warp][re, im, c_re, c_im][pair][lane]
+    __shared__ uint64_t sAcc[kMixWarps][4][S2][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row = lane / LPR, col = lane % LPR;
     const int O = A.rd.O, P = A.rd.P, Q = A.rd.Q;
@@ -376,17 +380,15 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
 
     // per-tile partial sums: samples (2k, 2k+1) of the lane packed in one pair
     // (an odd S computes one extra sample in the last pair and drops it)
-    constexpr int S2 = (S + 1) / 2;
     uint64_t PR[S2], PI[S2];
     const uint64_t zero2 = pk2(0.f, 0.f);
 #pragma unroll
-    for (int k = 0; k < S2; ++k) PR[k] = PI[k] = zero2;
-#pragma unroll
-    for (int j = 0; j < S; ++j) {
-        sAcc[warp][0][j][lane] = 0.f;
-        sAcc[warp][1][j][lane] = 0.f;
-        sAcc[warp][2][j][lane] = 0.f;
-        sAcc[warp][3][j][lane] = 0.f;
+    for (int k = 0; k < S2; ++k) {
+        PR[k] = PI[k] = zero2;
+        sAcc[warp][0][k][lane] = zero2;
+        sAcc[warp][1][k][lane] = zero2;
+        sAcc[warp][2][k][lane] = zero2;
+        sAcc[warp][3][k][lane] = zero2;
     }
 
     const int32_t *list = A.vis_idx + (int64_t)o * F + (A.vstart ? A.vstart[vrow] : 0);
@@ -567,6 +569,9 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
                     sincospif(2.f * red1(hi + lo), &s_, &c_);
                     R[9 + v] = c_;
                     R[12 + v] = s_;
+                    sincospif(2.f * red1(2.f * (hi + lo)), &s_, &c_);
+                    R[17 + v] = c_;
+                    R[20 + v] = s_;
                 }
             }
         }
@@ -587,12 +592,15 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
                 // ---------------- vertex form: one rotation per vertex ----------------
                 // 128-bit broadcast loads of the record
                 const float4 *R4 = reinterpret_cast<const float4 *>(sRec[warp][i].f);
-                const float4 q0 = R4[0], q1 = R4[1], q2v = R4[2], q3 = R4[3], q4 = R4[4];
+                const float4 q0 = R4[0], q1 = R4[1], q2v = R4[2], q3 = R4[3], q4 = R4[4],
+                             q5 = R4[5];
                 const float ph0[3] = {q0.x, q0.y, q0.z};
                 const float lo[3] = {q0.w, q1.x, q1.y};
                 const float wv[3] = {q1.z, q1.w, q2v.x};
                 const float sre[3] = {q2v.y, q2v.z, q2v.w};
                 const float sim[3] = {q3.x, q3.y, q3.z};
+                const float s2re[3] = {q4.y, q4.z, q4.w};
+                const float s2im[3] = {q5.x, q5.y, q5.z};
                 const float hi = q3.w, p2 = q4.x;
                 const float t1 = red1(hi * fm0);
                 const float q2 = p2 * fm0sq;
@@ -608,7 +616,8 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
                     // the phasor at samples (m0 + 2k, m0 + 2k + 1), advanced by
                     // the two-sample step
                     const float zc1 = fmaf(zc, stc, -zs * sts), zs1 = fmaf(zc, sts, zs * stc);
-                    const float c2 = fmaf(stc, stc, -sts * sts), s2 = 2.f * stc * sts;
+                    const float c2 = fmaf(-2.f * eps, s2im[v], s2re[v]);
+                    const float s2 = fmaf(2.f * eps, s2re[v], s2im[v]);
                     uint64_t ZC = pk2(zc, zc1), ZS = pk2(zs, zs1);
                     const uint64_t C2 = pk2(c2, c2), S2v = pk2(s2, s2), NS2 = pk2(-s2, -s2);
                     const uint64_t W2 = pk2(w, w);
@@ -747,36 +756,36 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
             }
         }
         // ---------------- Kahan-compensated tile accumulation ----------------
-        float pr[2 * S2], pi[2 * S2];
 #pragma unroll
         for (int k = 0; k < S2; ++k) {
-            upk2(PR[k], pr[2 * k], pr[2 * k + 1]);
-            upk2(PI[k], pi[2 * k], pi[2 * k + 1]);
-            PR[k] = PI[k] = zero2;
-        }
-#pragma unroll
-        for (int j = 0; j < S; ++j) {
-            float sr = sAcc[warp][0][j][lane], si = sAcc[warp][1][j][lane];
-            float cr = sAcc[warp][2][j][lane], ci = sAcc[warp][3][j][lane];
-            float y = pr[j] - cr;
-            float t = sr + y;
-            cr = (t - sr) - y;
+            uint64_t sr = sAcc[warp][0][k][lane], si = sAcc[warp][1][k][lane];
+            uint64_t cr = sAcc[warp][2][k][lane], ci = sAcc[warp][3][k][lane];
+            uint64_t y = fsub2(PR[k], cr);
+            uint64_t t = fadd2(sr, y);
+            cr = fsub2(fsub2(t, sr), y);
             sr = t;
-            y = pi[j] - ci;
-            t = si + y;
-            ci = (t - si) - y;
+            y = fsub2(PI[k], ci);
+            t = fadd2(si, y);
+            ci = fsub2(fsub2(t, si), y);
             si = t;
-            sAcc[warp][0][j][lane] = sr;
-            sAcc[warp][1][j][lane] = si;
-            sAcc[warp][2][j][lane] = cr;
-            sAcc[warp][3][j][lane] = ci;
+            sAcc[warp][0][k][lane] = sr;
+            sAcc[warp][1][k][lane] = si;
+            sAcc[warp][2][k][lane] = cr;
+            sAcc[warp][3][k][lane] = ci;
+            PR[k] = PI[k] = zero2;
         }
         __syncwarp();
     }
     // unscaled partial sums of this item
     float2 *dst = A.partial + (int64_t)item * (32 * S) + lane * S;
 #pragma unroll
-    for (int j = 0; j < S; ++j) dst[j] = make_float2(sAcc[warp][0][j][lane], sAcc[warp][1][j][lane]);
+    for (int k = 0; k < S2; ++k) {
+        float r0, r1, i0, i1;
+        upk2(sAcc[warp][0][k][lane], r0, r1);
+        upk2(sAcc[warp][1][k][lane], i0, i1);
+        dst[2 * k] = make_float2(r0, i0);
+        if (2 * k + 1 < S) dst[2 * k + 1] = make_float2(r1, i1);
+    }
     __syncwarp();
     }   // item loop
     if (lane == 0 && A.counters) {
