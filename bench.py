@@ -78,6 +78,9 @@ def parse():
                     help="timed runs of the perturbed-sedan gradient (0 skips)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="time the default synthesis layout instead of the autotuned one")
+    ap.add_argument("--synth-layout", default=None, metavar="S,T",
+                    help="fix the synthesis layout (samples per lane, tiles per item) "
+                         "instead of autotuning it")
     ap.add_argument("--no-intersection", action="store_true",
                     help="skip the full-intersection frame")
     return ap.parse_args()
@@ -441,7 +444,11 @@ def main():
     _, st = sim.simulate(pkg.PATH_MIXED, out=adc, stats=True)
     terms = st["n_terms"]
     tune = None
-    if not args.no_autotune:
+    if args.synth_layout:
+        S_fix, T_fix = (int(x) for x in args.synth_layout.split(","))
+        pkg.bart_set_synth_layout(sim.ctx, S_fix, T_fix)
+        tune = {"best": (S_fix, T_fix), "source": "--synth-layout"}
+    elif not args.no_autotune:
         # the library's autotuner picks the synthesis layout for this scene
         # (timed synthesis trials; untimed here, part of the warm-up)
         tune = pkg.bart_autotune(sim.ctx, 0.0, adc, reps=2)
@@ -582,7 +589,7 @@ def main():
                    "synthesis_layout": (None if tune is None else
                                         {"samples_per_lane": tune["best"][0],
                                          "tiles_per_item": tune["best"][1],
-                                         "source": "bart_autotune"})},
+                                         "source": tune.get("source", "bart_autotune")})},
         "frames_per_s": frames,
         "fp64_path": fp64,
         "stages_ms_last_step": {k: last_tm[k] for k in
