@@ -247,28 +247,19 @@ struct MixConsts {
 // One record per (facet, channel, chirp), 24 words in shared memory; the
 // layout depends on its form:
 //   vertex (V): [0..2] ph0_v  [3..5] lo_v  [6..8] w_v  [9..11] step re
-//               [12..14] step im  [15] hi  [16] p2  [17..19] two-sample step re
-//               [20..22] two-sample step im
-//   factored (F): [0] ph0c [1] hi [2] loc [3] p2 [4..5] centroid step
-//               [6..8] psi_v  [9..11] a_v  [12..14] w_v  [15..17] w_v A_v
-//               [18..20] -w_v A_v^2 / 2  [21..23] w_v A_v^3 / 6
+//               [12..14] step im  [15] hi  [16] p2  [17..19] 2 cos(2 step)
+//               [20..22] 4 sin(2 step)
 //   series (S): [0] ph0c [1] hi [2] loc [3] p2 [4] po [5] pl [6..13] cr [14..20] ci
 //   edge (E):   [0] ph0c [1] hi [2] loc [3] p2 [4+4e] po [5+4e] pl [6+4e] G [7+4e] K
 //               [16] sinc-series flags (int bits)
-// Phases are in cycles.  ph0 / psi are reduced to [-0.5, 0.5]; hi is a
+// Phases are in cycles.  ph0 is reduced to [-0.5, 0.5]; hi is a
 // multiple of 2^-14 so that frac(hi m) is exact in FP32.
 struct __align__(16) RecM {
     float f[24];
 };
 
-constexpr int kRecFact = 3;
-// factored form when max_v |2 pi a_v| (S - 1) stays below this many radians:
-// the vertex sum W then follows a cubic in the sample offset within a lane
-// to (0.06)^4 / 24 = 5.4e-7 of sum |w_v|
-constexpr float kFactMaxRot = 0.06f;
-
 constexpr int kMixWarps = 2;         // 2-warp CTAs: 22 KB of shared memory at S = 16
-constexpr int kMixMinBlocks = 10;    // resident CTAs per SM the register budget targets
+constexpr int kMixMinBlocks = 9;     // resident CTAs per SM the register budget targets
 
 __device__ __forceinline__ float red1(float x) { return x - rintf(x); }
 
@@ -332,7 +323,6 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
     const int64_t F = A.F;
     const int nc = A.nc;
     const int ngroups = (nc + RPW - 1) / RPW;
-    const float fact_lim = kFactMaxRot / (6.283185307179586f * (float)(S > 1 ? S - 1 : 1));
     const int VO = A.VO;
     const int total = A.item_off[VO];
     unsigned long long nV = 0, nSr = 0, nE = 0;
@@ -531,29 +521,6 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
                     if (K.kmax * fabsf(gam) < (float)kSincSeries) flags |= 1 << i;
                 }
                 R[16] = __int_as_float(flags);
-            } else if (fmaxf(fabsf(umin), fabsf(umax)) * K.muc <= fact_lim) {
-                cls = kRecFact;
-                R[0] = ph0c;
-                R[1] = hi;
-                R[2] = loc;
-                R[3] = p2;
-                float s_, c_;
-                sincospif(2.f * red1(hi + loc), &s_, &c_);
-                R[4] = c_;
-                R[5] = s_;
-#pragma unroll
-                for (int v = 0; v < 3; ++v) {
-                    const float ua = u[v], ub_ = u[(v + 1) % 3], uc = u[(v + 2) % 3];
-                    const float w = -A2 / ((ua - ub_) * (ua - uc));
-                    const float av = -K.muc * ua;
-                    const float Av = 6.283185307179586f * av;
-                    R[6 + v] = red1(-K.f0c * ua);
-                    R[9 + v] = av;
-                    R[12 + v] = w;
-                    R[15 + v] = w * Av;
-                    R[18 + v] = -0.5f * w * Av * Av;
-                    R[21 + v] = w * Av * Av * Av * (1.f / 6.f);
-                }
             } else {
                 cls = kRecVertex;
                 R[15] = hi;
@@ -570,17 +537,16 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
                     R[9 + v] = c_;
                     R[12 + v] = s_;
                     sincospif(2.f * red1(2.f * (hi + lo)), &s_, &c_);
-                    R[17 + v] = c_;
-                    R[20 + v] = s_;
+                    R[17 + v] = 2.f * c_;
+                    R[20 + v] = 4.f * s_;
                 }
             }
         }
         __syncwarp();
         const unsigned int mv = __ballot_sync(0xffffffffu, cls == kRecVertex);
-        const unsigned int mf = __ballot_sync(0xffffffffu, cls == kRecFact);
         const unsigned int ms = __ballot_sync(0xffffffffu, cls == kRecSeries || cls == kRecEdge);
         const unsigned int mser = __ballot_sync(0xffffffffu, cls == kRecSeries);
-        nV += __popc(mv) + __popc(mf);
+        nV += __popc(mv);
         nSr += __popc(mser);
         nE += __popc(ms & ~mser);
         // each lane walks its row's records; rows of one warp normally share
@@ -589,7 +555,12 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
         for (int ii = 0; ii < LPR; ++ii) {
             const int i = row * LPR + ii;
             if ((mv >> i) & 1u) {
-                // ---------------- vertex form: one rotation per vertex ----------------
+                // ------- vertex form: a three-term recurrence per vertex -------
+                // e^{j(phi + (s+2) a)} = 2 cos(a) e^{j(phi + (s+1) a)} - e^{j(phi + s a)}:
+                // on sample pairs (2k, 2k+1) with the two-sample angle, one FMA
+                // per pair and component.  Pair k is held times sg(k) = +1 for
+                // k mod 4 in {0, 1}, else -1, so that the recurrence needs no
+                // negated addend: held(k) = sg(k) sg(k-1) c2 held(k-1) + held(k-2).
                 // 128-bit broadcast loads of the record
                 const float4 *R4 = reinterpret_cast<const float4 *>(sRec[warp][i].f);
                 const float4 q0 = R4[0], q1 = R4[1], q2v = R4[2], q3 = R4[3], q4 = R4[4],
@@ -599,8 +570,8 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
                 const float wv[3] = {q1.z, q1.w, q2v.x};
                 const float sre[3] = {q2v.y, q2v.z, q2v.w};
                 const float sim[3] = {q3.x, q3.y, q3.z};
-                const float s2re[3] = {q4.y, q4.z, q4.w};
-                const float s2im[3] = {q5.x, q5.y, q5.z};
+                const float c2x2[3] = {q4.y, q4.z, q4.w};     // 2 cos(2 step)
+                const float s2x4[3] = {q5.x, q5.y, q5.z};     // 4 sin(2 step)
                 const float hi = q3.w, p2 = q4.x;
                 const float t1 = red1(hi * fm0);
                 const float q2 = p2 * fm0sq;
@@ -610,95 +581,42 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
                     const float thv = red1(fmaf(lo[v], fm0, ph0[v] + t1) + q2);
                     float zs, zc;
                     __sincosf(6.283185307179586f * thv, &zs, &zc);
+                    zc *= wv[v];
+                    zs *= wv[v];
+                    // the lane's step (angle + eps) and its doubled cosines
                     const float stc = fmaf(-eps, sim[v], sre[v]);
                     const float sts = fmaf(eps, sre[v], sim[v]);
-                    const float w = wv[v];
-                    // the phasor at samples (m0 + 2k, m0 + 2k + 1), advanced by
-                    // the two-sample step
+                    const float a1 = 2.f * stc;
+                    const float a2 = fmaf(-eps, s2x4[v], c2x2[v]);
+                    // samples m0 + 1 (rotation), m0 + 2 and m0 + 3 (recurrence)
                     const float zc1 = fmaf(zc, stc, -zs * sts), zs1 = fmaf(zc, sts, zs * stc);
-                    const float c2 = fmaf(-2.f * eps, s2im[v], s2re[v]);
-                    const float s2 = fmaf(2.f * eps, s2re[v], s2im[v]);
-                    uint64_t ZC = pk2(zc, zc1), ZS = pk2(zs, zs1);
-                    const uint64_t C2 = pk2(c2, c2), S2v = pk2(s2, s2), NS2 = pk2(-s2, -s2);
-                    const uint64_t W2 = pk2(w, w);
-    #pragma unroll
-                    for (int k = 0; k < S2; ++k) {
-                        PR[k] = ffma2(W2, ZC, PR[k]);
-                        PI[k] = ffma2(W2, ZS, PI[k]);
-                        if (k + 1 < S2) {
-                            const uint64_t nc_ = ffma2(ZS, NS2, fmul2(ZC, C2));
-                            ZS = ffma2(ZC, S2v, fmul2(ZS, C2));
-                            ZC = nc_;
-                        }
+                    const float zc2 = fmaf(a1, zc1, -zc), zs2 = fmaf(a1, zs1, -zs);
+                    const float zc3 = fmaf(a1, zc2, -zc1), zs3 = fmaf(a1, zs2, -zs1);
+                    uint64_t XC = pk2(zc, zc1), XS = pk2(zs, zs1);       // held(k - 1)
+                    uint64_t YC = pk2(zc2, zc3), YS = pk2(zs2, zs3);     // held(k)
+                    const uint64_t A2 = pk2(a2, a2), NA2 = pk2(-a2, -a2);
+                    PR[0] = fadd2(PR[0], XC);
+                    PI[0] = fadd2(PI[0], XS);
+                    if (S2 > 1) {
+                        PR[1] = fadd2(PR[1], YC);
+                        PI[1] = fadd2(PI[1], YS);
                     }
-                }
-        
-            } else if ((mf >> i) & 1u) {
-                // ---------------- factored form: centroid rotation x cubic W ----------------
-                const float4 *R4 = reinterpret_cast<const float4 *>(sRec[warp][i].f);
-                const float4 q0 = R4[0], q1 = R4[1], q2v = R4[2], q3 = R4[3], q4 = R4[4], q5 = R4[5];
-                // [0] ph0c [1] hi [2] loc [3] p2 [4..5] step [6..8] psi [9..11] a
-                // [12..14] w [15..17] wA [18..20] wA2 [21..23] wA3
-                const float psi[3] = {q1.z, q1.w, q2v.x};
-                const float av[3] = {q2v.y, q2v.z, q2v.w};
-                const float wv[3] = {q3.x, q3.y, q3.z};
-                const float wA[3] = {q3.w, q4.x, q4.y};
-                const float wA2[3] = {q4.z, q4.w, q5.x};
-                const float wA3[3] = {q5.y, q5.z, q5.w};
-                const float thc = red1(fmaf(q0.z, fm0, q0.x + red1(q0.y * fm0)) + q0.w * fm0sq);
-                float cs, cc;
-                __sincosf(6.283185307179586f * thc, &cs, &cc);
-                const float eps = q0.w * eps_lane;
-                const float stc = fmaf(-eps, q1.y, q1.x);
-                const float sts = fmaf(eps, q1.x, q1.y);
-                // W(s) = sum_v w_v exp(j 2 pi (psi_v + a_v (m0 + s))) as a cubic in s
-                float w0r = 0.f, w0i = 0.f, w1r = 0.f, w1i = 0.f, w2r = 0.f, w2i = 0.f;
-                float w3r = 0.f, w3i = 0.f;
     #pragma unroll
-                for (int v = 0; v < 3; ++v) {
-                    const float ps = red1(fmaf(av[v], fm0, psi[v]));
-                    float zs, zc;
-                    __sincosf(6.283185307179586f * ps, &zs, &zc);
-                    w0r = fmaf(wv[v], zc, w0r);          // w z
-                    w0i = fmaf(wv[v], zs, w0i);
-                    w1r = fmaf(-wA[v], zs, w1r);         // w A j z
-                    w1i = fmaf(wA[v], zc, w1i);
-                    w2r = fmaf(wA2[v], zc, w2r);         // -w A^2/2 z
-                    w2i = fmaf(wA2[v], zs, w2i);
-                    w3r = fmaf(wA3[v], zs, w3r);         // -j w A^3/6 z
-                    w3i = fmaf(-wA3[v], zc, w3i);
-                }
-                // W at the sample pairs (2k, 2k+1): forward differences of the
-                // cubic with step 2 -- for s^3 they start at 8, 26 (first),
-                // 48, 72 (second), 48 (third); for s^2 at 4, 8 and 8; for s at 2
-                uint64_t WR = pk2(w0r, w0r + w1r + w2r + w3r), WI = pk2(w0i, w0i + w1i + w2i + w3i);
-                uint64_t D1R = pk2(fmaf(8.f, w3r, fmaf(4.f, w2r, 2.f * w1r)),
-                                   fmaf(26.f, w3r, fmaf(8.f, w2r, 2.f * w1r)));
-                uint64_t D1I = pk2(fmaf(8.f, w3i, fmaf(4.f, w2i, 2.f * w1i)),
-                                   fmaf(26.f, w3i, fmaf(8.f, w2i, 2.f * w1i)));
-                uint64_t D2R = pk2(fmaf(48.f, w3r, 8.f * w2r), fmaf(72.f, w3r, 8.f * w2r));
-                uint64_t D2I = pk2(fmaf(48.f, w3i, 8.f * w2i), fmaf(72.f, w3i, 8.f * w2i));
-                const uint64_t D3R = pk2(48.f * w3r, 48.f * w3r), D3I = pk2(48.f * w3i, 48.f * w3i);
-                // the centroid phasor at the pairs, advanced by two samples
-                const float cc1 = fmaf(cc, stc, -cs * sts), cs1 = fmaf(cc, sts, cs * stc);
-                const float c2 = fmaf(stc, stc, -sts * sts), s2 = 2.f * stc * sts;
-                uint64_t CC = pk2(cc, cc1), CS = pk2(cs, cs1);
-                const uint64_t C2 = pk2(c2, c2), S2v = pk2(s2, s2), NS2 = pk2(-s2, -s2);
-    #pragma unroll
-                for (int k = 0; k < S2; ++k) {
-                    // (pr, pi) += C W
-                    PR[k] = fsub2(ffma2(CC, WR, PR[k]), fmul2(CS, WI));
-                    PI[k] = ffma2(CS, WR, ffma2(CC, WI, PI[k]));
-                    if (k + 1 < S2) {
-                        const uint64_t nc_ = ffma2(CS, NS2, fmul2(CC, C2));
-                        CS = ffma2(CC, S2v, fmul2(CS, C2));
-                        CC = nc_;
-                        WR = fadd2(WR, D1R);
-                        WI = fadd2(WI, D1I);
-                        D1R = fadd2(D1R, D2R);
-                        D1I = fadd2(D1I, D2I);
-                        D2R = fadd2(D2R, D3R);
-                        D2I = fadd2(D2I, D3I);
+                    for (int k = 2; k < S2; ++k) {
+                        const bool neg = (k & 2) != 0;                   // sg(k) = -1
+                        const uint64_t A = (((k - 1) & 2) != 0) != neg ? NA2 : A2;
+                        const uint64_t NC = ffma2(A, YC, XC), NS = ffma2(A, YS, XS);
+                        XC = YC;
+                        XS = YS;
+                        YC = NC;
+                        YS = NS;
+                        if (neg) {
+                            PR[k] = fsub2(PR[k], YC);
+                            PI[k] = fsub2(PI[k], YS);
+                        } else {
+                            PR[k] = fadd2(PR[k], YC);
+                            PI[k] = fadd2(PI[k], YS);
+                        }
                     }
                 }
         
