@@ -259,7 +259,7 @@ struct __align__(16) RecM {
 };
 
 constexpr int kMixWarps = 2;         // 2-warp CTAs: 22 KB of shared memory at S = 16
-constexpr int kMixMinBlocks = 9;     // resident CTAs per SM the register budget targets
+constexpr int kMixMinBlocks = 8;     // resident CTAs per SM: 16 warps, 128 registers a thread
 
 __device__ __forceinline__ float red1(float x) { return x - rintf(x); }
 
