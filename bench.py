@@ -36,12 +36,16 @@ if ROOT not in sys.path:
 METRIC = "echo terms/s (facet x chan x chirp x sample), frames/s; mixed vs FP64 path"
 UNIT = "terms/s"
 WORKLOAD = "moving sedan 20k tris, 3TXx4RX (12 ch), 128 chirps x 256 samples"
-FLOPS_PER_TERM = 30          # 3 vertex phasors x (rotation 6 + weighted accumulate 4)
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x lanes x FMA x max clock
+# algorithmic work of one echo term in the mixed path: 3 vertex phases, 3 unit
+# phasors, 3 real x complex weighted accumulates and their compensation, about
+# 24 FP32 FMA-pipe operations (plus 6 SFU operations when the phasors come from
+# sincos); the roofline counts operations of the FMA pipe, whatever their kind
+OPS_PER_TERM = 24
+FP32_PIPE_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12    # SMs x FP32 lanes x max clock
 # DRAM bytes (read + write) of one synthesis launch on this workload, from the
 # ncu capture summarised in profiles/synth_mixed_moving_sedan.md; valid only
 # while the kernel's sources hash to the value they had at the capture
-SYNTH_TRAFFIC = {"bytes": 8.229376e6 + 0.495104e6, "sources_sha256_16": "112442227b65a597",
+SYNTH_TRAFFIC = {"bytes": 8.216320e6 + 30.044672e6, "sources_sha256_16": "c0342ecc9524573d",
                  "samples_per_lane": 16}
 SYNTH_SOURCES = ("synth.cu", "bart_internal.cuh", "record_fp64.cuh")
 
@@ -494,7 +498,7 @@ def main():
 
     # dominant kernel: echo synthesis, average launch duration from CUDA events
     synth_avg_ms = statistics.mean(synth_ms) / max(1, synth_launches)
-    achieved = terms / max(1, synth_launches) * FLOPS_PER_TERM / (synth_avg_ms / 1e3) / 1e12
+    achieved = terms / max(1, synth_launches) * OPS_PER_TERM / (synth_avg_ms / 1e3) / 1e12
 
     # plain FP64 path on the same frame (fewer steps: it is the reference path)
     adc64 = torch.empty((O, N, M), dtype=torch.complex128, device=dev)
@@ -598,13 +602,15 @@ def main():
         "roofline": {"bound": "alu",
                      "kernel": "synth_mixed_kernel<%d, %d>" % (
                          (16, 16) if tune is None or tune["best"][0] == 16 else (8, 32)),
-                     "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS,
+                     "achieved": achieved, "peak": FP32_PIPE_PEAK_TOPS,
+                     "unit": "Top/s (FP32 FMA-pipe operations)",
+                     "frac": achieved / FP32_PIPE_PEAK_TOPS,
                      "traffic": synth_traffic(16 if tune is None else tune["best"][0]),
                      "traffic_unit": "bytes per launch (ncu dram read + write)",
-                     "flops_per_term": FLOPS_PER_TERM,
+                     "ops_per_term": OPS_PER_TERM,
                      "launch_ms": synth_avg_ms,
-                     "peak_basis": "FP32 FMA pipe: 152 SM x 128 lanes x 2 flop x 2070 MHz"},
+                     "peak_basis": "FP32 FMA pipe: 152 SM x 128 lanes x 2070 MHz, one "
+                                   "operation per lane and clock"},
         "clocks": clk,
         "e2e": e2e,
         "gpu_launches": launches,
