@@ -329,8 +329,13 @@ def dataset_batch(pkg, sg, torch, dev, K: int, bsz: int, tri_min: int = 5_000,
 
 def detect_timing(pkg, torch, sim, adc, stream, reps: int = 10) -> dict:
     """CA-CFAR + angle spectrum + point records (bart_detect) on the timed
-    frame's ADC: device time per call (CUDA events), points found."""
+    frame's ADC with receiver noise added (20 dB SNR per sample, seed 9):
+    device time per call (CUDA events), points found.  A noise-free cube
+    would let CFAR pick up the synthesis' rounding floor (paired echoes
+    below -100 dB) instead of targets."""
     cfg = pkg.make_detect_cfg(guard_r=2, guard_d=2, train_r=8, train_d=4, pfa=1e-6, angle_bins=512)
+    adc = adc.clone()
+    pkg.bart_add_noise(sim.ctx, adc, 20.0, 9, 0)
     buf = torch.empty(65536 * pkg.POINT_DTYPE.itemsize, dtype=torch.uint8, device=adc.device)
     n = pkg.bart_detect(sim.ctx, adc, cfg, buf)
     ms = []
@@ -343,7 +348,7 @@ def detect_timing(pkg, torch, sim, adc, stream, reps: int = 10) -> dict:
         e1.synchronize()
         ms.append(e0.elapsed_time(e1))
     return {"ms": statistics.median(ms), "points": int(n), "angle_bins": 512,
-            "cfar": "guard 2x2, train 8x4, Pfa 1e-6"}
+            "cfar": "guard 2x2, train 8x4, Pfa 1e-6", "snr_db": 20.0}
 
 
 def intersection_frame(pkg, sg, torch, dev) -> dict:
