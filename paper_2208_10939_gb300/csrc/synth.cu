@@ -536,9 +536,12 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
                     sincospif(2.f * red1(hi + lo), &s_, &c_);
                     R[9 + v] = c_;
                     R[12 + v] = s_;
-                    sincospif(2.f * red1(2.f * (hi + lo)), &s_, &c_);
-                    R[17 + v] = 2.f * c_;
-                    R[20 + v] = 4.f * s_;
+                    // 2 cos(2 step) = 2 - 4 sin^2 = 4 cos^2 - 2, taken from the
+                    // smaller of sin and cos so that only its own rounding remains
+                    // (the recurrence is most sensitive to it near angle 0 and pi)
+                    R[17 + v] = fabsf(s_) < fabsf(c_) ? fmaf(-4.f * s_, s_, 2.f)
+                                                      : fmaf(4.f * c_, c_, -2.f);
+                    R[20 + v] = 8.f * c_ * s_;                // 4 sin(2 step)
                 }
             }
         }
@@ -573,12 +576,12 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
                 const float c2x2[3] = {q4.y, q4.z, q4.w};     // 2 cos(2 step)
                 const float s2x4[3] = {q5.x, q5.y, q5.z};     // 4 sin(2 step)
                 const float hi = q3.w, p2 = q4.x;
-                const float t1 = red1(hi * fm0);
-                const float q2 = p2 * fm0sq;
+                // the vertices' common phase at the lane's first sample
+                const float tq = red1(hi * fm0) + p2 * fm0sq;
                 const float eps = p2 * eps_lane;
     #pragma unroll
                 for (int v = 0; v < 3; ++v) {
-                    const float thv = red1(fmaf(lo[v], fm0, ph0[v] + t1) + q2);
+                    const float thv = red1(fmaf(lo[v], fm0, ph0[v] + tq));
                     float zs, zc;
                     __sincosf(6.283185307179586f * thv, &zs, &zc);
                     zc *= wv[v];
