@@ -129,7 +129,7 @@ struct SceneSplit {
     const int32_t *root = nullptr;
 };
 void launch_visibility(const double *tri64, const float *tri32, const double *c64,
-                       const BvhNode *nodes, const int32_t *order, int64_t F, const RadarDev &rd,
+                       const FacetRec *fac, const BvhNode *nodes, const int32_t *order, int64_t F, const RadarDev &rd,
                        const SceneSplit &sc, uint8_t *state, unsigned long long *n_graze,
                        int *status, cudaStream_t s);
 // lists 0..O-1: facets lit from both antennas of each channel; O..O+A-1: facets

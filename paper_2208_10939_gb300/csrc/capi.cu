@@ -641,7 +641,7 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
         launches += F >= 2 ? 1 : 0;
         if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[2], s), "cudaEventRecord");
         // 3. visibility + per-channel lit lists (+ their per-scene ranges)
-        launch_visibility(ctx->tri64.p, ctx->tri32.p, ctx->c64.p, ctx->nodes.p,
+        launch_visibility(ctx->tri64.p, ctx->tri32.p, ctx->c64.p, ctx->fac.p, ctx->nodes.p,
                           F >= 2 ? ctx->vals.p : nullptr, F, rd, split, ctx->state.p,
                           ctx->counters.p + 3, ctx->status.p, s);
         launch_compact(ctx->state.p, F, rd, ctx->blk_cnt.p, ctx->vis_idx.p, ctx->vis_cnt.p, s);

@@ -146,7 +146,8 @@ constexpr int kStack = 64;
 
 __global__ void __launch_bounds__(128)
 visibility_kernel(const double *__restrict__ tri64, const float4 *__restrict__ tri32,
-                  const double *__restrict__ c64, const BvhNode *__restrict__ nodes,
+                  const double *__restrict__ c64, const FacetRec *__restrict__ fac,
+                  const BvhNode *__restrict__ nodes,
                   const int32_t *__restrict__ order, int64_t F, RadarDev rd, SceneSplit sc,
                   uint8_t *__restrict__ state, unsigned long long *n_graze, int *status)
 {
@@ -157,23 +158,54 @@ visibility_kernel(const double *__restrict__ tri64, const float4 *__restrict__ t
         // threads walk the facets in Morton order so that a warp's segments
         // start close together and traverse similar BVH paths
         const int64_t k = order ? (int64_t)order[gid] : gid;
-        const double *tk = tri64 + 9 * k;
-        double tri[9];
-        for (int i = 0; i < 9; ++i) tri[i] = tk[i];
         const double c[3] = {c64[3 * k], c64[3 * k + 1], c64[3 * k + 2]};
         const double pa[3] = {rd.ant[a][0], rd.ant[a][1], rd.ant[a][2]};
-        double e1[3], e2[3], n[3], D[3];
-        sub3(tri + 3, tri, e1);
-        sub3(tri + 6, tri, e2);
-        cross3(e1, e2, n);
+        double D[3];
         sub3(pa, c, D);
-        const double cosang =
-            __ddiv_rn(dot3(n, D), __dmul_rn(__dsqrt_rn(dot3(n, n)), __dsqrt_rn(dot3(D, D))));
+        const float Df[3] = {(float)D[0], (float)D[1], (float)D[2]};
+        // FP32 pre-test of the facing test below.  n32 is the unit normal
+        // formed in FP64 and rounded (error < 2e-7), Df the rounded segment
+        // (relative error 2^-24 per component); with the dot product's and
+        // rsqrt's rounding, |cos32 - cos| < 6e-7, so beyond +-(kEpsFace + 2e-6)
+        // the FP64 decision is certain.  Slivers (2A below 1e-6 of the
+        // squared edge scale), whose FP64 normal direction is ill-conditioned,
+        // always take the FP64 test.
+        int face = 1;                                  // 0 back, 2 front, 1 undecided
+        {
+            const FacetRec *fr = fac + k;
+            const float n0 = fr->n[0], n1 = fr->n[1], n2 = fr->n[2];
+            float L2 = 0.f;
+#pragma unroll
+            for (int v = 0; v < 3; ++v) {
+                const float x = fr->dv[3 * v], y = fr->dv[3 * v + 1], z = fr->dv[3 * v + 2];
+                L2 = fmaxf(L2, fmaf(x, x, fmaf(y, y, z * z)));
+            }
+            const float dd = fmaf(Df[0], Df[0], fmaf(Df[1], Df[1], Df[2] * Df[2]));
+            const float cos32 = fmaf(n0, Df[0], fmaf(n1, Df[1], n2 * Df[2])) * rsqrtf(dd);
+            constexpr float thr = (float)kEpsFace + 2e-6f;
+            if (2.f * fr->area >= 4e-6f * L2 && dd > 0.f) {
+                if (cos32 >= thr) face = 2;
+                else if (cos32 <= -thr) face = 0;
+            }
+        }
         uint8_t st;
-        if (dot3(n, n) == 0.0 || cosang <= -kEpsFace) {   // zero area: no normal
+        bool graze = false;
+        if (face == 1) {
+            const double *tk = tri64 + 9 * k;
+            double tri[9];
+            for (int i = 0; i < 9; ++i) tri[i] = tk[i];
+            double e1[3], e2[3], n[3];
+            sub3(tri + 3, tri, e1);
+            sub3(tri + 6, tri, e2);
+            cross3(e1, e2, n);
+            const double cosang = __ddiv_rn(
+                dot3(n, D), __dmul_rn(__dsqrt_rn(dot3(n, n)), __dsqrt_rn(dot3(D, D))));
+            if (dot3(n, n) == 0.0 || cosang <= -kEpsFace) face = 0;   // zero area: no normal
+            else graze = fabs(cosang) < kEpsFace;
+        }
+        if (face == 0) {
             st = BART_VIS_BACK;
         } else {
-            bool graze = fabs(cosang) < kEpsFace;
             bool hit = false;
             // traversal root: the whole tree, or the subtree of the facet's scene
             int root = F >= 2 ? 0 : -1;
@@ -188,7 +220,6 @@ visibility_kernel(const double *__restrict__ tri64, const float4 *__restrict__ t
             }
             if (root >= 0) {
                 const float o[3] = {(float)c[0], (float)c[1], (float)c[2]};
-                const float Df[3] = {(float)D[0], (float)D[1], (float)D[2]};
                 const float Dm = fmaxf(fmaxf(fabsf(Df[0]), fabsf(Df[1])), fabsf(Df[2]));
                 const float Om = fmaxf(fmaxf(fabsf(o[0]), fabsf(o[1])), fabsf(o[2]));
                 float inv[3];
@@ -243,14 +274,14 @@ visibility_kernel(const double *__restrict__ tri64, const float4 *__restrict__ t
 }
 
 void launch_visibility(const double *tri64, const float *tri32, const double *c64,
-                       const BvhNode *nodes, const int32_t *order, int64_t F, const RadarDev &rd,
+                       const FacetRec *fac, const BvhNode *nodes, const int32_t *order, int64_t F, const RadarDev &rd,
                        const SceneSplit &sc, uint8_t *state, unsigned long long *n_graze,
                        int *status, cudaStream_t s)
 {
     const int T = 128;
     dim3 grid((unsigned int)((F + T - 1) / T), (unsigned int)rd.A);
     visibility_kernel<<<grid, T, 0, s>>>(tri64, reinterpret_cast<const float4 *>(tri32), c64,
-                                         nodes, order, F, rd, sc, state, n_graze, status);
+                                         fac, nodes, order, F, rd, sc, state, n_graze, status);
 }
 
 // -------------------------------------------------------------------------
