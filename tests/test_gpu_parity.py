@@ -223,6 +223,79 @@ def test_minimum_sizes_and_single_facet(sim):
     assert rel_l2(sim.simulate(pkg.PATH_MIXED).cpu().numpy(), ref) <= TOL_MIXED
 
 
+def _tilted_plate(M, N, P, Q, range_m=6.0, speed=0.0, n=3, size=0.3, slope=30e12):
+    radar = sg.make_radar(M, N, P, Q, 5.12e6, slope, 2.0, centre=(0.0, 0.0, 0.0))
+    inst = sg.Instance(0, (0.05, range_m, 0.02), sg.rot_z(0.3), (0.2, speed, 0.0))
+    return sg.Scene([sg.plate(size, size, n)], [inst], radar)
+
+
+@pytest.mark.parametrize("M,N,P,Q", [(1024, 2, 16, 16), (96, 3, 1, 2), (160, 5, 2, 1),
+                                     (768, 2, 2, 2)])
+def test_layout_edge_sizes_match_oracle(sim, M, N, P, Q):
+    """The largest M with the most antennas (256 channels), and sample
+    counts that force the fallback layouts (one or eight samples per lane,
+    two or three warps per chirp row): full cube, both paths."""
+    sc = _tilted_plate(M, N, P, Q)
+    fr = oracle.Frame(sc)
+    ref = fr.adc_full()
+    sim.load_scene(sc)
+    a64 = sim.simulate(pkg.PATH_FP64).cpu().numpy()
+    assert np.array_equal(sim.visibility().cpu().numpy(), fr.state)
+    assert rel_l2(a64, ref) <= TOL_FP64
+    err = rel_l2(sim.simulate(pkg.PATH_MIXED).cpu().numpy(), ref)
+    print(f"M={M} N={N} P={P} Q={Q}: mixed relL2 {err:.3e}")
+    assert err <= TOL_MIXED
+
+
+def test_kinematics_fallback_rows_match_oracle(sim):
+    """A target 2 m from the radar receding at 15 m/s over 4096 chirps: the
+    per-(antenna, facet) path-length series about the middle chirp cannot
+    reach 1e-11 m by degree 8, so the record build takes the FP64 square
+    root instead; both paths against the oracle."""
+    N, M = 4096, 32
+    sc = _tilted_plate(M, N, 1, 1, range_m=1.2, speed=15.0, n=1, size=0.02, slope=12.5e12)
+    r = sc.radar
+    t_mid = 0.5 * (N - 1) * r.Tc
+    R_mid = 1.2 + 15.0 * t_mid
+    rho = 0.5 * (N - 1) * r.Tc * 15.0 / R_mid
+    assert rho >= 0.25 or R_mid * rho ** 9 / (1 - rho) > 1e-11     # no convergent row
+    fr = oracle.Frame(sc)
+    ref = fr.adc_full()
+    sim.load_scene(sc)
+    assert rel_l2(sim.simulate(pkg.PATH_FP64).cpu().numpy(), ref) <= TOL_FP64
+    err = rel_l2(sim.simulate(pkg.PATH_MIXED).cpu().numpy(), ref)
+    print(f"fallback rows (rho {rho:.2f}): mixed relL2 {err:.3e}")
+    assert err <= TOL_MIXED
+
+
+def test_degenerate_and_sliver_facets(sim):
+    """A plate plus a zero-area (collinear) triangle and a sliver 1e-9 m
+    wide: the zero-area facet is BACK for every antenna, the sliver takes
+    the FP64 facing test; states bit-exact and both cubes at tolerance."""
+    base = sg.plate(0.3, 0.3, 3)
+    v = base.verts
+    a, b = v[0], v[1]
+    mid = 0.5 * (a + b)
+    extra = np.array([a + (0.0, 0.0, 0.5), b + (0.0, 0.0, 0.5), mid + (0.0, 0.0, 0.5),
+                      a + (0.0, 0.0, 0.8), b + (0.0, 0.0, 0.8), mid + (-1e-9, 0.0, 0.8)])
+    n0 = len(v)
+    verts = np.concatenate([v, extra])
+    tris = np.concatenate([base.tris, np.array([[n0, n0 + 1, n0 + 2], [n0 + 3, n0 + 4, n0 + 5]],
+                                               np.int32)])
+    mesh = sg.Mesh(verts, tris, np.ones(len(tris), np.float32))
+    radar = sg.make_radar(64, 4, 2, 2, 5.12e6, 30e12, 2.0, centre=(0.0, 0.0, 0.0))
+    sc = sg.Scene([mesh], [sg.Instance(0, (0.05, 6.0, 0.02), sg.rot_z(0.3), (0.2, -1.0, 0.0))],
+                  radar)
+    fr = oracle.Frame(sc)
+    ref = fr.adc_full()
+    assert (fr.state[:, -2] == pkg.VIS_BACK).all()
+    assert (fr.state[:, -1] == pkg.VIS_LIT).all()
+    sim.load_scene(sc)
+    assert rel_l2(sim.simulate(pkg.PATH_FP64).cpu().numpy(), ref) <= TOL_FP64
+    assert np.array_equal(sim.visibility().cpu().numpy(), fr.state)
+    assert rel_l2(sim.simulate(pkg.PATH_MIXED).cpu().numpy(), ref) <= TOL_MIXED
+
+
 def test_nothing_lit_gives_zero_cube(sim):
     """A plate facing away from the radar: every facet BACK, empty lists."""
     sc = sg.plate_scene(n=3, M=64, N=4)
