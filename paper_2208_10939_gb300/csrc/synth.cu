@@ -419,7 +419,7 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
             }
             const float Rt = kt.w, Rr = kr.w, L = Rt + Rr;
             const float o_k = 0.5f * (fr.n[0] * b[0] + fr.n[1] * b[1] + fr.n[2] * b[2]);
-            const float g = fr.rho * o_k / (Rt * Rr);
+            const float g = __fdividef(fr.rho * o_k, Rt * Rr);
             // in-plane part of b, formed once: u_v, |b_t|^2 and n x b_t all derive
             // from it, so every form evaluates J exactly at one wave vector
             // (|b|^2 - (b.n)^2 would cancel catastrophically near specular)
@@ -456,7 +456,7 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
                     const float vt = vv.x * ut[0] + vv.y * ut[1] + vv.z * ut[2];
                     const float vr = vv.x * ur[0] + vv.y * ur[1] + vv.z * ur[2];
                     Ld = -(vt + vr);
-                    Ldd = (v2 - vt * vt) / Rtp + (v2 - vr * vr) / Rrp;
+                    Ldd = __fdividef(v2 - vt * vt, Rtp) + __fdividef(v2 - vr * vr, Rrp);
                 }
             }
             float hi = kt.y + kr.y;
@@ -525,15 +525,29 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
                 cls = kRecVertex;
                 R[15] = hi;
                 R[16] = p2;
+                // vertex steps = the centroid's step times e^{j x_v},
+                // x_v = -2 pi mu/(fs c) u_v, from its Taylor series (error
+                // below x^6/720 = 1.4e-9 for |x| < 0.1), else sincospi
+                float sc_, cc_;
+                sincospif(2.f * red1(hi + loc), &sc_, &cc_);
 #pragma unroll
                 for (int v = 0; v < 3; ++v) {
                     const float ua = u[v], ub_ = u[(v + 1) % 3], uc = u[(v + 2) % 3];
                     R[v] = red1(ph0c - K.f0c * ua);
                     const float lo = loc - K.muc * ua;
                     R[3 + v] = lo;
-                    R[6 + v] = -A2 / ((ua - ub_) * (ua - uc));
+                    R[6 + v] = __fdividef(-A2, (ua - ub_) * (ua - uc));
                     float s_, c_;
-                    sincospif(2.f * red1(hi + lo), &s_, &c_);
+                    const float x = -6.283185307179586f * K.muc * ua;
+                    if (fabsf(x) < 0.1f) {
+                        const float x2 = x * x;
+                        const float cx = fmaf(x2, fmaf(x2, 1.f / 24.f, -0.5f), 1.f);
+                        const float sx = x * fmaf(x2, fmaf(x2, 1.f / 120.f, -1.f / 6.f), 1.f);
+                        c_ = fmaf(cc_, cx, -sc_ * sx);
+                        s_ = fmaf(sc_, cx, cc_ * sx);
+                    } else {
+                        sincospif(2.f * red1(hi + lo), &s_, &c_);
+                    }
                     R[9 + v] = c_;
                     R[12 + v] = s_;
                     // 2 cos(2 step) = 2 - 4 sin^2 = 4 cos^2 - 2, taken from the
