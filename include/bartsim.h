@@ -127,7 +127,9 @@ typedef struct bart_timing {
     float   scene_ms;        /* world facets at t0 */
     float   bvh_ms;          /* Morton codes, radix sort, hierarchy, refit */
     float   visibility_ms;   /* visibility states + per-channel lit lists */
-    float   kinematics_ms;   /* FP64 Taylor rows of the path lengths (mixed path) */
+    float   kinematics_ms;   /* FP64 Taylor rows of the path lengths (mixed path;
+                                on a second stream, overlapping bvh_ms and
+                                visibility_ms) */
     float   synthesis_ms;    /* echo-synthesis kernels */
     float   rdm_ms;          /* last bart_form_rdm */
     int32_t synthesis_launches;   /* synthesis kernel launches in the frame */

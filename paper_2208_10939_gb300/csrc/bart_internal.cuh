@@ -177,9 +177,8 @@ struct SynthArgs {
 };
 // per (antenna, lit facet) Taylor rows of R(t) over the frame (see synth.cu)
 constexpr int kKinRowWords = 9;    // float4 per row
-void launch_kin_coef(const double *c64, const FacetRec *fac, const double *vel64,
-                     const int32_t *vis_idx, const int32_t *vis_cnt, int64_t F, const RadarDev &rd,
-                     float4 *coef, double *quad, cudaStream_t s);
+void launch_kin_coef(const double *c64, const FacetRec *fac, const double *vel64, int64_t F,
+                     const RadarDev &rd, float4 *coef, double *quad, cudaStream_t s);
 void launch_synth_mixed(const SynthArgs &a, cudaStream_t s);
 // scratch of the mixed path for F facets and a chunk of nc chirps
 // scene_F: facets of each scene (n_scene entries); tpi: 32-record tiles per

@@ -163,6 +163,8 @@ struct bart_ctx {
     std::vector<cudaEvent_t> ev_kin;    // before / after the kinematics rows
     std::vector<cudaEvent_t> ev_syn;    // before / after the synthesis
     cudaStream_t cap_stream = nullptr;  // frame-graph recording stream
+    cudaStream_t side = nullptr;        // kinematics rows beside the hierarchy build
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     int chunks = 0;
     int path = 0;
     bool have_rdm_timing = false;
@@ -178,6 +180,9 @@ struct bart_ctx {
         for (cudaEvent_t e : ev_kin) cudaEventDestroy(e);
         for (cudaEvent_t e : ev_syn) cudaEventDestroy(e);
         if (cap_stream) cudaStreamDestroy(cap_stream);
+        if (side) cudaStreamDestroy(side);
+        if (fork_ev) cudaEventDestroy(fork_ev);
+        if (join_ev) cudaEventDestroy(join_ev);
         for (MeshStore *m : pool) {
             m->verts.release();
             m->tris.release();
@@ -597,6 +602,14 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
         max_items = synth_max_items(scene_F.data(), B, rd, rd.N, tpi, ctx->layout_S);
         BART_TRY(ctx->item_off.ensure((size_t)B * O + 1, "synthesis item table"));
         BART_TRY(ctx->item_counter.ensure(1, "synthesis item counter"));
+        if (!ctx->side) {
+            CUDA_TRY(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking),
+                     "cudaStreamCreateWithFlags");
+            CUDA_TRY(cudaEventCreateWithFlags(&ctx->fork_ev, cudaEventDisableTiming),
+                     "cudaEventCreateWithFlags");
+            CUDA_TRY(cudaEventCreateWithFlags(&ctx->join_ev, cudaEventDisableTiming),
+                     "cudaEventCreateWithFlags");
+        }
         if (ctx->timing) {
             BART_TRY(ensure_events(ctx->ev_kin, 2));
             BART_TRY(ensure_events(ctx->ev_syn, 2));
@@ -604,8 +617,9 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
     }
     if (ctx->timing) BART_TRY(ensure_events(ctx->ev, 7));
 
-    // every launch of the frame, on one stream: run directly, or recorded
-    // into a frame graph
+    // every launch of the frame, on the caller's stream (the mixed path's
+    // kinematics rows on a second stream, forked after the world facets and
+    // joined before the synthesis): run directly, or recorded into a frame graph
     auto enqueue = [&](double t0v, bool tm, cudaStream_t s) -> int {
         CUDA_TRY(cudaMemsetAsync(ctx->counters.p, 0, 4 * sizeof(unsigned long long), s), "memset");
         if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[0], s), "cudaEventRecord");
@@ -617,6 +631,17 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
                             ctx->ref64.p, ctx->ref32.p, s);
         launches += 1;
         if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[1], s), "cudaEventRecord");
+        // the mixed path's kinematics rows need only the world facets: they
+        // run on a second stream beside the hierarchy build and visibility
+        if (path == BART_PATH_MIXED) {
+            CUDA_TRY(cudaEventRecord(ctx->fork_ev, s), "cudaEventRecord");
+            CUDA_TRY(cudaStreamWaitEvent(ctx->side, ctx->fork_ev, 0), "cudaStreamWaitEvent");
+            if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_kin[0], ctx->side), "cudaEventRecord");
+            launch_kin_coef(ctx->c64.p, ctx->fac.p, ctx->vel64.p, F, rd, ctx->kin.p,
+                            ctx->kquad.p, ctx->side);
+            if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_kin[1], ctx->side), "cudaEventRecord");
+            CUDA_TRY(cudaEventRecord(ctx->join_ev, ctx->side), "cudaEventRecord");
+        }
         // 2. LBVH (batched scenes: one hierarchy with a subtree per scene)
         SceneSplit split;
         if (B > 1) {
@@ -688,13 +713,8 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
             a.kquad = ctx->kquad.p;
             a.n0 = 0;
             a.nc = rd.N;
-            if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_kin[0], s), "cudaEventRecord");
-            launch_kin_coef(ctx->c64.p, ctx->fac.p, ctx->vel64.p, ctx->vis_idx.p, ctx->vis_cnt.p,
-                            F, rd, ctx->kin.p, ctx->kquad.p, s);
-            if (tm) {
-                CUDA_TRY(cudaEventRecord(ctx->ev_kin[1], s), "cudaEventRecord");
-                CUDA_TRY(cudaEventRecord(ctx->ev_syn[0], s), "cudaEventRecord");
-            }
+            CUDA_TRY(cudaStreamWaitEvent(s, ctx->join_ev, 0), "cudaStreamWaitEvent");
+            if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_syn[0], s), "cudaEventRecord");
             launch_synth_mixed(a, s);
             if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_syn[1], s), "cudaEventRecord");
             ctx->chunks = 1;

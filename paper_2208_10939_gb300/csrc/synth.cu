@@ -67,16 +67,26 @@ namespace bart {
 constexpr int kKinMaxDeg = 8;
 constexpr int kKinRow = kKinMaxDeg + 1;    // float4 per antenna-facet row
 
+// Rows are formed for every facet that is not certainly back-facing (a
+// superset of the lit ones): the kernel then needs only the world facets and
+// runs beside the hierarchy build and visibility.  The facing decision is
+// the visibility kernel's FP32 pre-test: |cos32 - cos| < 6e-7.
 __global__ void kin_coef_kernel(const double *__restrict__ c64, const FacetRec *__restrict__ fac,
-                                const double *__restrict__ vel64,
-                                const int32_t *__restrict__ vis_idx,
-                                const int32_t *__restrict__ vis_cnt, int64_t F, RadarDev rd,
+                                const double *__restrict__ vel64, int64_t F, RadarDev rd,
                                 float4 *__restrict__ coef, double *__restrict__ quad)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int a = blockIdx.y;
-    if (i >= vis_cnt[rd.O + a]) return;              // facets lit from antenna a
-    const int64_t k = vis_idx[(int64_t)(rd.O + a) * F + i];
+    if (k >= F) return;
+    {
+        const float D0 = (float)(rd.ant[a][0] - c64[3 * k]);
+        const float D1 = (float)(rd.ant[a][1] - c64[3 * k + 1]);
+        const float D2 = (float)(rd.ant[a][2] - c64[3 * k + 2]);
+        const float dd = fmaf(D0, D0, fmaf(D1, D1, D2 * D2));
+        const float cs = fmaf(fac[k].n[0], D0, fmaf(fac[k].n[1], D1, fac[k].n[2] * D2)) *
+                         rsqrtf(dd);
+        if (dd > 0.f && cs <= -((float)kEpsFace + 2e-6f)) return;   // certainly BACK
+    }
     const int inst = fac[k].inst;
     const double vx = vel64[3 * inst], vy = vel64[3 * inst + 1], vz = vel64[3 * inst + 2];
     const double dx = c64[3 * k] - rd.ant[a][0];
@@ -135,13 +145,12 @@ __global__ void kin_coef_kernel(const double *__restrict__ c64, const FacetRec *
     }
 }
 
-void launch_kin_coef(const double *c64, const FacetRec *fac, const double *vel64,
-                     const int32_t *vis_idx, const int32_t *vis_cnt, int64_t F, const RadarDev &rd,
-                     float4 *coef, double *quad, cudaStream_t s)
+void launch_kin_coef(const double *c64, const FacetRec *fac, const double *vel64, int64_t F,
+                     const RadarDev &rd, float4 *coef, double *quad, cudaStream_t s)
 {
     const int T = 128;
     dim3 grid((unsigned int)((F + T - 1) / T), (unsigned int)rd.A);
-    kin_coef_kernel<<<grid, T, 0, s>>>(c64, fac, vel64, vis_idx, vis_cnt, F, rd, coef, quad);
+    kin_coef_kernel<<<grid, T, 0, s>>>(c64, fac, vel64, F, rd, coef, quad);
 }
 
 // double-float helpers: values xh + xl with |xl| <= ulp(xh) / 2; every
