@@ -32,9 +32,9 @@
 //   mixed : FP64 only where the phase spans ~1e5 cycles -- per-chirp
 //           positions, |c(t_n) - p_a| and its reduction mod 1 (kinematics
 //           kernel); everything else in FP32.  Per lane, S consecutive
-//           samples: one MUFU sincos per vertex, then an FMA-only phasor
-//           recurrence; partial sums per 32-record tile, Kahan-compensated
-//           into the running sum.
+//           samples: one MUFU sincos per vertex, then the FMA-only
+//           three-term phasor recurrence on sample pairs; partial sums per
+//           32-record tile, Kahan-compensated into the running sum.
 //   fp64  : every quantity in FP64, the exact per-sample delay
 //           sqrt(|c(t_n) + v t - p|^2), one sincospi per phasor per sample.
 #include <cuda_runtime.h>
@@ -863,8 +863,9 @@ int synth_tiles_per_item(int64_t F) { return (int)std::max<int64_t>(16, ((F + 31
 
 // lane layout of the mixed kernel: S samples per lane, LPR lanes per chirp
 // row, W warps per row.  16 samples per lane halve the per-lane start-up
-// work (MUFU start phasors, cubic coefficients) against 8; S_req = 8 asks
-// for the 8-sample layout where M allows it (autotuner candidate).
+// work (MUFU start phasors, the first samples of each recurrence) against
+// 8; S_req = 8 asks for the 8-sample layout where M allows it (autotuner
+// candidate).
 struct MixLayout {
     int S, LPR, W;
 };
