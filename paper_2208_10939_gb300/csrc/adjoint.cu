@@ -122,31 +122,87 @@ adjoint_fp64_kernel(SynthArgs A, int W, const void *__restrict__ grad, int grad_
             double ab[kRecEntries];
 #pragma unroll
             for (int e = 0; e < kRecEntries; ++e) ab[e] = 0.0;
+            // Per lane (samples m0 .. m0 + S - 1, t = t0 + tau):
+            //  - sqrt(Q(t)) and 0.5 / sqrt(Q(t)) from their expansions in
+            //    u = (Q(t) - Q(t0)) / Q(t0): sqrt(1+u) = 1 + u/2 - u^2/8 + u^3/16,
+            //    (1+u)^(-1/2) = 1 - u/2 + 3u^2/8 - 5u^3/16; |u| <= 2|dR/dt| tau / R
+            //    stays below 1e-4 (R >= 1 m, |v| <= 30 m/s, tau <= S / fs), so the
+            //    truncation is below 4e-18 relative;
+            //  - each phasor slot (three vertices, the series term, or three
+            //    edges) exp(j 2 pi phi(j)): one sincospi at j = 0 and one for
+            //    the first-step increment delta = red(phi(1) - phi(0)); sample j
+            //    is the rotated start times exp(j 2 pi r), r = red(phi(j) -
+            //    phi(0) - j delta) the phase's curvature residual (|r| < 1e-4
+            //    cycles, four series terms: error below 1e-17)
+            const int nslot = R.kind == kRecSeries ? 1 : 3;
+            const int sstride = R.kind == kRecVertex ? 1 : 3;
+            // reciprocals formed once (products instead of FP64 divisions per sample)
+            const double inv_fs = 1.0 / fs, inv_c = 1.0 / c, inv_f0 = 1.0 / f0;
+            const double mu_2c2 = mu / (2.0 * c * c), mu_c2 = mu / (c * c);
+            const double t0 = (double)m0 * inv_fs;
+            const double Qt0 = R.r[0] + t0 * (R.r[1] + t0 * R.r[2]);
+            const double Qr0 = R.r[3] + t0 * (R.r[4] + t0 * R.r[2]);
+            const double st0 = sqrt(Qt0), sr0 = sqrt(Qr0);
+            const double ht0 = 0.5 / st0, hr0 = 0.5 / sr0;
+            const double at1 = (R.r[1] + 2.0 * R.r[2] * t0) / Qt0, at2 = R.r[2] / Qt0;
+            const double ar1 = (R.r[4] + 2.0 * R.r[2] * t0) / Qr0, ar2 = R.r[2] / Qr0;
+            double ph0[3], dl[3], zc[3], zs[3], cd[3], sd[3];
 #pragma unroll 1
             for (int j = 0; j < S; ++j) {
-                const double t = (double)(m0 + j) / fs;
+                const double tau = (double)j * inv_fs;
+                const double t = t0 + tau;
                 const double fm = f0 + mu * t;
-                const double Qt = R.r[0] + t * (R.r[1] + t * R.r[2]);
-                const double Qr = R.r[3] + t * (R.r[4] + t * R.r[2]);
-                const double sQt = sqrt(Qt), sQr = sqrt(Qr);
+                const double ut = tau * (at1 + tau * at2), ur = tau * (ar1 + tau * ar2);
+                const double sQt = st0 * (1.0 + ut * (0.5 + ut * (-0.125 + ut * 0.0625)));
+                const double sQr = sr0 * (1.0 + ur * (0.5 + ur * (-0.125 + ur * 0.0625)));
+                const double it = ht0 * (1.0 + ut * (-0.5 + ut * (0.375 - ut * 0.3125)));
+                const double ir = hr0 * (1.0 + ur * (-0.5 + ur * (0.375 - ur * 0.3125)));
                 const double L = sQt + sQr;
-                double thc = fm * (L + R.r[kRecLs]) / c - mu * L * L / (2.0 * c * c);
+                const double fmc = fm * inv_c;
+                const double kp = fm * inv_f0;
+                double thc = fmc * (L + R.r[kRecLs]) - mu_2c2 * L * L;
                 thc -= rint(thc);
-                const double fmc = fm / c;
-                const double kp = fm / f0;
+                // the phasor of each slot at this sample
+                double pc[3], ps[3];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    if (q >= nslot) break;
+                    double ph = thc - fmc * d[q * sstride];
+                    ph -= rint(ph);
+                    if (j == 0) {
+                        ph0[q] = ph;
+                        sincospi(2.0 * ph, &zs[q], &zc[q]);
+                        pc[q] = zc[q];
+                        ps[q] = zs[q];
+                    } else {
+                        if (j == 1) {
+                            dl[q] = ph - ph0[q];
+                            dl[q] -= rint(dl[q]);
+                            sincospi(2.0 * dl[q], &sd[q], &cd[q]);
+                        }
+                        const double nc = zc[q] * cd[q] - zs[q] * sd[q];
+                        zs[q] = zc[q] * sd[q] + zs[q] * cd[q];
+                        zc[q] = nc;
+                        double r = ph - ph0[q] - (double)j * dl[q];
+                        r -= rint(r);
+                        const double x = twopi * r, x2 = x * x;
+                        const double ec = 1.0 - 0.5 * x2 * (1.0 - x2 * (1.0 / 12.0));
+                        const double es = x * (1.0 - x2 * (1.0 / 6.0));
+                        pc[q] = zc[q] * ec - zs[q] * es;
+                        ps[q] = zc[q] * es + zs[q] * ec;
+                    }
+                }
                 double a_thc = 0.0;
                 if (R.kind == kRecVertex) {
                     for (int v = 0; v < 3; ++v) {
-                        double s_, c_;
-                        sincospi(2.0 * (thc - fmc * d[v]), &s_, &c_);
+                        const double c_ = pc[v], s_ = ps[v];
                         const double zr = gr[j] * c_ - gi[j] * s_, zi = gr[j] * s_ + gi[j] * c_;
                         ab[kRecD + 3 + v] += zr;
                         ab[kRecD + v] += twopi * fmc * d[3 + v] * zi;
                         a_thc -= twopi * d[3 + v] * zi;
                     }
                 } else if (R.kind == kRecSeries) {
-                    double s_, c_;
-                    sincospi(2.0 * (thc - fmc * d[0]), &s_, &c_);
+                    const double c_ = pc[0], s_ = ps[0];
                     const double zr = gr[j] * c_ - gi[j] * s_, zi = gr[j] * s_ + gi[j] * c_;
                     const double k2 = kp * kp;
                     double a = d[8], bb = d[15];
@@ -164,8 +220,7 @@ adjoint_fp64_kernel(SynthArgs A, int W, const void *__restrict__ grad, int grad_
                     a_thc -= twopi * wi;
                 } else {
                     for (int e = 0; e < 3; ++e) {
-                        double s_, c_;
-                        sincospi(2.0 * (thc - fmc * d[3 * e]), &s_, &c_);
+                        const double c_ = pc[e], s_ = ps[e];
                         const double zr = gr[j] * c_ - gi[j] * s_, zi = gr[j] * s_ + gi[j] * c_;
                         const double x = kp * d[3 * e + 1];
                         double sn, snp;
@@ -190,8 +245,7 @@ adjoint_fp64_kernel(SynthArgs A, int W, const void *__restrict__ grad, int grad_
                 }
                 // thc -> L -> path-length polynomial coefficients; thc -> shift
                 ab[kRecLs] += a_thc * fmc;
-                const double aL = a_thc * (fmc - mu * L / (c * c));
-                const double it = 0.5 / sQt, ir = 0.5 / sQr;
+                const double aL = a_thc * (fmc - mu_c2 * L);
                 ab[0] += aL * it;
                 ab[1] += aL * it * t;
                 ab[2] += aL * (it + ir) * t * t;

@@ -1039,20 +1039,23 @@ synth_fp64_kernel(SynthArgs A, int W)
         nV += __popc(a1);
         nSr += __popc(a2);
         nE += __popc(mask & ~a1 & ~a2);
+        // reciprocals formed once: products instead of FP64 divisions per sample
+        const double inv_fs = 1.0 / fs, inv_c = 1.0 / c, inv_f0 = 1.0 / f0;
+        const double mu_2c2 = mu / (2.0 * c * c);
         while (mask) {
             const int i = __ffs(mask) - 1;
             mask &= mask - 1;
             const RecD &R = sR[warp][i];
 #pragma unroll 1
             for (int j = 0; j < S; ++j) {
-                const double t = (double)(m0 + j) / fs;
+                const double t = (double)(m0 + j) * inv_fs;
                 const double fm = f0 + mu * t;
                 const double L = sqrt(R.qt[0] + t * (R.qt[1] + t * R.qt[2])) +
                                  sqrt(R.qr[0] + t * (R.qr[1] + t * R.qt[2]));
-                double thc = fm * (L + R.ls) / c - mu * L * L / (2.0 * c * c);
+                const double fmc = fm * inv_c;
+                const double kp = fm * inv_f0;
+                double thc = fmc * (L + R.ls) - mu_2c2 * L * L;
                 thc -= rint(thc);
-                const double fmc = fm / c;
-                const double kp = fm / f0;
                 double re = 0.0, im = 0.0;
                 if (R.kind == kRecVertex) {
                     for (int v = 0; v < 3; ++v) {
