@@ -386,39 +386,52 @@ def intersection_frame(pkg, sg, torch, dev) -> dict:
 def adjoint_timing(pkg, sg, torch, dev, reps: int) -> dict:
     """Differentiable echo on the perturbed-sedan inverse problem: the
     sedan as target, its copy with 5 mm vertex noise (seed 5) as the
-    variable, L = ||adc(v) - adc_target||^2; FP64 forward and adjoint times
-    (CUDA events) and gradient throughput in echo terms per second."""
+    variable, L = ||adc(v) - adc_target||^2; forward and adjoint times (CUDA
+    events) and gradient throughput in echo terms per second, FP64 and
+    mixed precision (mixed-path forward, adjoint with FP32 per-sample work),
+    and the mixed gradient's relative L2 distance to the FP64 one."""
     from paper_2208_10939_gb300 import autograd as bag
     s = pkg.Simulator(dev.index or 0)
     try:
         sc = sg.car_scene()
-        es = bag.EchoScene(s, sc)
-        v_true = es.vertex_tensor(sc, dev)
-        with torch.no_grad():
-            target = bag.echo(v_true, None, es).clone()
-        rng = np.random.default_rng(5)
-        v0 = v_true + torch.from_numpy(0.005 * rng.normal(size=tuple(v_true.shape))).to(dev)
-        st = pkg.bart_simulate_frame(s.ctx, 0.0, pkg.PATH_FP64, target.clone(), stats=True)
-        fwd, bwd = [], []
-        for rep in range(reps + 1):          # the first pass warms up (allocations)
-            verts = v0.clone().requires_grad_(True)
-            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-            e0.record()
-            adc = bag.echo(verts, None, es)
-            loss = (adc - target).abs().pow(2).sum()
-            e1.record()
-            loss.backward()
-            e2.record()
-            e2.synchronize()
-            if rep > 0:
-                fwd.append(e0.elapsed_time(e1))
-                bwd.append(e0.elapsed_time(e2) - e0.elapsed_time(e1))
-        terms = st["n_terms"]
-        return {"workload": "sedan 20k tris, target vs 5 mm vertex noise (seed 5), "
-                            "L = ||adc - adc_target||^2, FP64",
-                "forward_ms": min(fwd), "backward_ms": min(bwd), "terms": terms,
-                "gradient_terms_per_s": terms / (min(bwd) / 1e3),
-                "parameters": int(verts.numel())}
+        out = {"workload": "sedan 20k tris, target vs 5 mm vertex noise (seed 5), "
+                           "L = ||adc - adc_target||^2"}
+        grads = {}
+        for prec in ("fp64", "mixed"):
+            es = bag.EchoScene(s, sc, precision=prec)
+            v_true = es.vertex_tensor(sc, dev)
+            with torch.no_grad():
+                target = bag.echo(v_true, None, es).clone()
+            rng = np.random.default_rng(5)
+            v0 = v_true + torch.from_numpy(0.005 * rng.normal(size=tuple(v_true.shape))).to(dev)
+            st = pkg.bart_simulate_frame(s.ctx, 0.0, pkg.PATH_FP64,
+                                         torch.empty_like(target, dtype=torch.complex128),
+                                         stats=True)
+            fwd, bwd = [], []
+            for rep in range(reps + 1):          # the first pass warms up (allocations)
+                verts = v0.clone().requires_grad_(True)
+                e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                e0.record()
+                adc = bag.echo(verts, None, es)
+                loss = (adc - target).abs().pow(2).sum()
+                e1.record()
+                loss.backward()
+                e2.record()
+                e2.synchronize()
+                if rep > 0:
+                    fwd.append(e0.elapsed_time(e1))
+                    bwd.append(e0.elapsed_time(e2) - e0.elapsed_time(e1))
+            grads[prec] = verts.grad.detach().clone()
+            terms = st["n_terms"]
+            key = "" if prec == "fp64" else "_mixed"
+            out["forward_ms" + key] = min(fwd)
+            out["backward_ms" + key] = min(bwd)
+            out["gradient_terms_per_s" + key] = terms / (min(bwd) / 1e3)
+            out["terms"] = terms
+            out["parameters"] = int(verts.numel())
+        out["mixed_gradient_rel_l2_vs_fp64"] = float(
+            torch.linalg.norm(grads["mixed"] - grads["fp64"]) / torch.linalg.norm(grads["fp64"]))
+        return out
     finally:
         s.close()
 

@@ -246,6 +246,18 @@ int bart_add_noise(bart_ctx *ctx, void *adc, int32_t dtype, double snr_db, uint6
 int bart_simulate_adjoint(bart_ctx *ctx, double t0, const void *grad_adc, int32_t dtype,
                           double *grad_verts, double *grad_rho);
 
+/* bart_simulate_adjoint with the per-sample work of vertex-form records in
+ * FP32 (Sec. 3.2, Eq. 13 differentiated as above): FP64 fixes each vertex's
+ * phase at three samples of a lane of 8, FP32 rotations carry the phasor
+ * along the chord of those phases, and the record adjoint is summed in FP32
+ * before the FP64 reduction and the FP64 pass through the record
+ * construction; series and edge records take the FP64 path.  Same
+ * arguments and results as bart_simulate_adjoint, to ~1e-5 of the gradient's
+ * norm (the phase's curvature over a lane, ~1e-5 rad on a moving car, and
+ * FP32 sums); several times faster.  Errors: ESTATE, EINVAL, ENOMEM, ECUDA. */
+int bart_simulate_adjoint_mixed(bart_ctx *ctx, double t0, const void *grad_adc, int32_t dtype,
+                                double *grad_verts, double *grad_rho);
+
 /* Frame graphs.  With enable = 1, bart_simulate_frame records its kernel
  * launches (world facets, hierarchy, visibility, lit lists, kinematics,
  * synthesis: some 25-40 launches on two streams) into a CUDA graph the

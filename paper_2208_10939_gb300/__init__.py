@@ -36,6 +36,7 @@ EXPORTED = ["bart_last_error", "bart_version", "bart_create", "bart_destroy",
             "bart_sync", "bart_form_rdm_static", "bart_add_noise", "bart_detect",
             "bart_scene_partition", "bart_set_graph", "bart_set_synth_layout",
             "bart_autotune", "bart_rdm_adjoint", "bart_simulate_adjoint",
+            "bart_simulate_adjoint_mixed",
             "bart_mesh_update"]
 
 
@@ -164,6 +165,7 @@ def load_library() -> ctypes.CDLL:
         L.bart_set_graph.argtypes = [P, I32]
         L.bart_rdm_adjoint.argtypes = [P, P, I32, P, P]
         L.bart_simulate_adjoint.argtypes = [P, D, P, I32, P, P]
+        L.bart_simulate_adjoint_mixed.argtypes = [P, D, P, I32, P, P]
         L.bart_mesh_update.argtypes = [P, I32, P, P]
         L.bart_set_synth_layout.argtypes = [P, I32, I32]
         L.bart_autotune.argtypes = [P, D, P, I32, I32, ctypes.POINTER(bart_tune)]
@@ -410,19 +412,22 @@ def bart_rdm_adjoint(ctx: int, adc, grad_rdm, grad_adc) -> None:
                                            ctypes.c_void_p(_ptr(grad_adc))))
 
 
-def bart_simulate_adjoint(ctx: int, t0: float, grad_adc, grad_verts, grad_rho=None) -> None:
+def bart_simulate_adjoint(ctx: int, t0: float, grad_adc, grad_verts, grad_rho=None,
+                          mixed: bool = False) -> None:
     """Mesh-vertex (instance-major, mesh-local) and per-facet reflectivity
-    gradients of a real loss with dL/dRe(adc) + i dL/dIm(adc) = grad_adc."""
+    gradients of a real loss with dL/dRe(adc) + i dL/dIm(adc) = grad_adc;
+    ``mixed`` selects bart_simulate_adjoint_mixed (FP32 per-sample work)."""
     import torch
     if not grad_adc.is_cuda or not grad_adc.is_contiguous():
         raise ValueError("grad_adc must be a contiguous CUDA tensor")
     for t in (grad_verts, grad_rho):
         if t is not None and (not t.is_cuda or not t.is_contiguous() or t.dtype != torch.float64):
             raise ValueError("gradient outputs must be contiguous CUDA float64 tensors")
-    _check(load_library().bart_simulate_adjoint(
-        ctx, float(t0), ctypes.c_void_p(_ptr(grad_adc)), _dtype_code(grad_adc),
-        ctypes.c_void_p(_ptr(grad_verts)),
-        None if grad_rho is None else ctypes.c_void_p(_ptr(grad_rho))))
+    lib = load_library()
+    fn = lib.bart_simulate_adjoint_mixed if mixed else lib.bart_simulate_adjoint
+    _check(fn(ctx, float(t0), ctypes.c_void_p(_ptr(grad_adc)), _dtype_code(grad_adc),
+              ctypes.c_void_p(_ptr(grad_verts)),
+              None if grad_rho is None else ctypes.c_void_p(_ptr(grad_rho))))
 
 
 def bart_set_graph(ctx: int, enable: bool) -> None:

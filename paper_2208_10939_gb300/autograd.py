@@ -15,15 +15,22 @@ from typing import List
 
 import torch
 
-from . import (PATH_FP64, Simulator, bart_form_rdm, bart_mesh_update, bart_rdm_adjoint,
-               bart_simulate_adjoint, bart_simulate_frame)
+from . import (PATH_FP64, PATH_MIXED, Simulator, bart_form_rdm, bart_mesh_update,
+               bart_rdm_adjoint, bart_simulate_adjoint, bart_simulate_frame)
 
 
 class EchoScene:
     """A scene whose every instance has its own mesh, so that the instance
-    vertices are the mesh vertices (the differentiable parameters)."""
+    vertices are the mesh vertices (the differentiable parameters).
 
-    def __init__(self, sim: Simulator, scene):
+    ``precision="mixed"`` runs the mixed-path forward (complex64 cube) and
+    the adjoint with FP32 per-sample work (``bart_simulate_adjoint_mixed``);
+    the default ``"fp64"`` runs both in FP64."""
+
+    def __init__(self, sim: Simulator, scene, precision: str = "fp64"):
+        if precision not in ("fp64", "mixed"):
+            raise ValueError("precision must be 'fp64' or 'mixed'")
+        self.precision = precision
         self.sim = sim
         sim.load_scene(scene)
         self.nv = [int(scene.meshes[i.mesh_id].verts.shape[0]) for i in scene.instances]
@@ -52,8 +59,11 @@ class _Echo(torch.autograd.Function):
     @staticmethod
     def forward(ctx, verts, rho, scene: EchoScene):
         scene.upload(verts.detach(), None if rho is None else rho.detach().float())
-        adc = torch.empty(scene.sim.adc_shape(), dtype=torch.complex128, device=verts.device)
-        bart_simulate_frame(scene.sim.ctx, scene.t0, PATH_FP64, adc)
+        mixed = scene.precision == "mixed"
+        adc = torch.empty(scene.sim.adc_shape(),
+                          dtype=torch.complex64 if mixed else torch.complex128,
+                          device=verts.device)
+        bart_simulate_frame(scene.sim.ctx, scene.t0, PATH_MIXED if mixed else PATH_FP64, adc)
         ctx.scene = scene
         ctx.has_rho = rho is not None
         ctx.shapes = (verts.shape, None if rho is None else rho.shape)
@@ -65,12 +75,14 @@ class _Echo(torch.autograd.Function):
         gv = torch.empty(ctx.shapes[0], dtype=torch.float64, device=grad_adc.device)
         gr = (torch.empty(sum(scene.nf), dtype=torch.float64, device=grad_adc.device)
               if ctx.has_rho else None)
-        bart_simulate_adjoint(scene.sim.ctx, scene.t0, grad_adc.contiguous(), gv, gr)
+        bart_simulate_adjoint(scene.sim.ctx, scene.t0, grad_adc.contiguous(), gv, gr,
+                              mixed=scene.precision == "mixed")
         return gv, (None if gr is None else gr.to(torch.float32).view(ctx.shapes[1])), None
 
 
 def echo(verts: torch.Tensor, rho: torch.Tensor | None, scene: EchoScene) -> torch.Tensor:
-    """ADC cube (complex128, [O][N][M]) of the scene with the given
+    """ADC cube (complex128, or complex64 for a mixed-precision EchoScene,
+    [O][N][M]) of the scene with the given
     instance-major vertices (float64, (sum nv, 3)) and optional per-facet
     reflectivities (float32); differentiable in both."""
     return _Echo.apply(verts, rho, scene)

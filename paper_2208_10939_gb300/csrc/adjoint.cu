@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "bart_internal.cuh"
 #include "record_fp64.cuh"
 
@@ -32,18 +34,155 @@ struct __align__(16) RecA {
     double r[kRecEntries];
 };
 
+// The mixed adjoint's record adds, about the row's middle sample t_c
+// (tau = t - t_c), the path length L(tau) = sqrt(Qt) + sqrt(Qr) and the
+// phase thc(tau) = fmc (L + shift) - mu L^2 / (2 c^2) as degree-4
+// polynomials (from L^2 = Q term by term; the series ratio |v| |tau| / R is
+// below 1e-3, so the truncation is ~1e-16 relative), and the quadratics'
+// normalised coefficients for 0.5 / sqrt(Q) = (0.5 / s)(1 + u)^(-1/2),
+// u = tau (a1 + a2 tau).  Formed once per record: no lane takes an FP64
+// square root or division.
+struct __align__(16) RecAX : RecA {
+    double tc, st, sr, at1, at2, ar1, ar2;
+    double Lk[5], thk[5];
+};
+
 __device__ __forceinline__ double warp_sum(double v)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
+// Record adjoint of a vertex-form record over one lane's S samples with the
+// per-sample work in FP32 (the mixed adjoint).  FP64 gives each vertex's
+// phase at the lane's samples 0, 1 and S - 1 (the path lengths as in the
+// FP64 loop); the phasors then advance by an FP32 rotation along the chord
+// of those phases (the phase's curvature over the lane, p2 (S - 1)^2 / 4
+// cycles, is left out: ~1e-5 rad on a moving car), and the sums over the
+// lane's samples run in FP32:
+//   rbar(w_v) = sum zr_v,   rbar(u_v) = 2 pi w_v sum fmc zi_v,
+//   a = -2 pi sum_v w_v zi_v,   rbar(shift) = sum a fmc,
+//   rbar(qt_i), rbar(qr_i) from sum a (fmc - mu L / c^2) t^i,
+// with z = conj(G) exp(j 2 pi phase); 0.5 / sqrt(Q) is held at the lane's
+// first sample (it moves by ~5e-7 of itself over 8 samples).
+// (1 + u)^(-1/2) to fourth order in u: with |u| <= 2 |dR/dt|
+// |tau| / R below 1.5e-3 (R >= 1 m, |v| <= 30 m/s, |tau| <= 25 us) the
+// truncation is below 2e-16 relative
+__device__ __forceinline__ double rsqrt1p4(double u)
+{
+    return 1.0 + u * (-0.5 + u * (0.375 + u * (-0.3125 + u * 0.2734375)));
+}
+
 template <int S>
-__global__ void __launch_bounds__(kAdjWarps * 32)
+__device__ __forceinline__ void adj_vertex_mixed(const RecAX &X, int m0, double f0, double mu,
+                                                 double fs, double c, const double *gr,
+                                                 const double *gi, float *fb)
+{
+    const double *rr = X.r;
+    const double *d = rr + kRecD;
+    const double inv_fs = 1.0 / fs, inv_c = 1.0 / c;
+    const double t0 = (double)m0 * inv_fs;
+    const int jp[3] = {0, 1, S - 1};
+    double th[3][3], Lp[3];
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+        const double t = t0 + (double)jp[p] * inv_fs;
+        const double tau = t - X.tc;
+        double thc = X.thk[4], L = X.Lk[4];
+#pragma unroll
+        for (int q = 3; q >= 0; --q) {
+            thc = fma(thc, tau, X.thk[q]);
+            L = fma(L, tau, X.Lk[q]);
+        }
+        thc -= rint(thc);
+        const double fmc = (f0 + mu * t) * inv_c;
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            double ph = thc - fmc * d[v];
+            th[p][v] = ph - rint(ph);
+        }
+        Lp[p] = L;
+    }
+    float zc[3], zs[3], cst[3], sst[3], wv[3], Sw[3], Su[3];
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+        double d1 = th[1][v] - th[0][v];
+        d1 -= rint(d1);
+        double slope = d1;
+        if (S > 2) {
+            double r = th[2][v] - th[0][v] - (double)(S - 1) * d1;
+            r -= rint(r);
+            slope += r / (double)(S > 2 ? S - 1 : 1);
+        }
+        sincospif(2.f * (float)th[0][v], &zs[v], &zc[v]);
+        sincospif(2.f * (float)slope, &sst[v], &cst[v]);
+        wv[v] = (float)d[3 + v];
+        Sw[v] = Su[v] = 0.f;
+    }
+    const float fmc0 = (float)((f0 + mu * t0) * inv_c), dfmc = (float)(mu * inv_fs * inv_c);
+    const float L0 = (float)Lp[0];
+    const float dL = S > 1 ? (float)((Lp[2] - Lp[0]) / (double)(S - 1)) : 0.f;
+    const float muc2 = (float)(mu * inv_c * inv_c);
+    const float t0f = (float)t0, dt = (float)inv_fs;
+    float A0 = 0.f, A1 = 0.f, A2 = 0.f, Ash = 0.f;
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+        const float fmc = fmaf((float)j, dfmc, fmc0);
+        const float t = fmaf((float)j, dt, t0f);
+        const float L = fmaf((float)j, dL, L0);
+        const float g_r = (float)gr[j], g_i = (float)gi[j];
+        float a = 0.f;
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            const float zr = fmaf(g_r, zc[v], -g_i * zs[v]);
+            const float zi = fmaf(g_r, zs[v], g_i * zc[v]);
+            Sw[v] += zr;
+            Su[v] = fmaf(fmc, zi, Su[v]);
+            a = fmaf(-wv[v], zi, a);
+            const float nc = fmaf(zc[v], cst[v], -zs[v] * sst[v]);
+            zs[v] = fmaf(zc[v], sst[v], zs[v] * cst[v]);
+            zc[v] = nc;
+        }
+        Ash = fmaf(a, fmc, Ash);
+        const float aL = a * fmaf(-muc2, L, fmc);
+        A0 += aL;
+        A1 = fmaf(aL, t, A1);
+        A2 = fmaf(aL * t, t, A2);
+    }
+    // 0.5 / sqrt(Q) at the lane's first sample
+    const double tau0 = t0 - X.tc;
+    const float twopi = 6.283185307179586f;
+    const float it = (float)(0.5 / X.st * rsqrt1p4(tau0 * (X.at1 + tau0 * X.at2)));
+    const float ir = (float)(0.5 / X.sr * rsqrt1p4(tau0 * (X.ar1 + tau0 * X.ar2)));
+    // the record adjoint's entries in record order (qt[3], qr[2], shift, u[3], w[3])
+    fb[0] = twopi * it * A0;
+    fb[1] = twopi * it * A1;
+    fb[2] = twopi * (it + ir) * A2;
+    fb[3] = twopi * ir * A0;
+    fb[4] = twopi * ir * A1;
+    fb[kRecLs] = twopi * Ash;
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+        fb[kRecD + v] = twopi * (float)d[3 + v] * Su[v];
+        fb[kRecD + 3 + v] = Sw[v];
+    }
+}
+
+__device__ __forceinline__ float warp_sum_f(float v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+constexpr int kAdjMixMinBlocks = 3;   // resident blocks the mixed variant's register budget targets
+
+template <int S, bool MX>
+__global__ void __launch_bounds__(kAdjWarps * 32, MX ? kAdjMixMinBlocks : 1)
 adjoint_fp64_kernel(SynthArgs A, int W, const void *__restrict__ grad, int grad_c64,
                     double *__restrict__ gfac)
 {
-    __shared__ RecA sR[kAdjWarps][32];
+    using Rec = typename std::conditional<MX, RecAX, RecA>::type;
+    __shared__ Rec sR[kAdjWarps][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t gw = (int64_t)blockIdx.x * kAdjWarps + warp;
     const int N = A.rd.N, M = A.rd.M;
@@ -101,13 +240,51 @@ adjoint_fp64_kernel(SynthArgs A, int W, const void *__restrict__ grad, int grad_
             double tri[9], c0[3];
             for (int i = 0; i < 9; ++i) tri[i] = A.tri64[9 * k + i];
             for (int r = 0; r < 3; ++r) c0[r] = A.c64[3 * k + r];
-            RecA &R = sR[warp][lane];
+            Rec &R = sR[warp][lane];
             int flags = 0;
             R.kind = build_record<double>(tri, c0, vel, tn, ptx, prx, (double)A.fac[k].rho,
                                           A.rd.intra, k0, kmax,
                                           A.rd.delay_ref ? A.ref64 + 3 * inst : nullptr, R.r,
                                           &flags);
             R.flags = flags;
+            if constexpr (MX) {
+                // the path lengths' expansion about the row's middle sample
+                R.tc = 0.5 * (double)(M - 1) / fs;
+                const double Qt = R.r[0] + R.tc * (R.r[1] + R.tc * R.r[2]);
+                const double Qr = R.r[3] + R.tc * (R.r[4] + R.tc * R.r[2]);
+                R.st = sqrt(Qt);
+                R.sr = sqrt(Qr);
+                R.at1 = (R.r[1] + 2.0 * R.r[2] * R.tc) / Qt;
+                R.at2 = R.r[2] / Qt;
+                R.ar1 = (R.r[4] + 2.0 * R.r[2] * R.tc) / Qr;
+                R.ar2 = R.r[2] / Qr;
+                // sqrt(q0 + q1 tau + q2 tau^2) = sum_k l_k tau^k: 2 l0 l1 = q1,
+                // 2 l0 l2 + l1^2 = q2, 2 l0 l3 + 2 l1 l2 = 0, 2 l0 l4 + 2 l1 l3 + l2^2 = 0
+                double lt[5], lr[5];
+                const double q1t = R.r[1] + 2.0 * R.r[2] * R.tc, q1r = R.r[4] + 2.0 * R.r[2] * R.tc;
+                lt[0] = R.st;
+                lr[0] = R.sr;
+                const double ht = 0.5 / R.st, hr = 0.5 / R.sr;
+                lt[1] = q1t * ht;
+                lr[1] = q1r * hr;
+                lt[2] = (R.r[2] - lt[1] * lt[1]) * ht;
+                lr[2] = (R.r[2] - lr[1] * lr[1]) * hr;
+                lt[3] = -2.0 * lt[1] * lt[2] * ht;
+                lr[3] = -2.0 * lr[1] * lr[2] * hr;
+                lt[4] = -(2.0 * lt[1] * lt[3] + lt[2] * lt[2]) * ht;
+                lr[4] = -(2.0 * lr[1] * lr[3] + lr[2] * lr[2]) * hr;
+                for (int q = 0; q < 5; ++q) R.Lk[q] = lt[q] + lr[q];
+                // thc = (fmc_c + mu/c tau)(L + shift) - mu / (2 c^2) L^2, degree 4
+                const double fmcc = (A.rd.f0 + A.rd.slope * R.tc) / kC0;
+                const double muc = A.rd.slope / kC0, mu2 = A.rd.slope / (2.0 * kC0 * kC0);
+                for (int q = 0; q < 5; ++q) {
+                    const double aq = R.Lk[q] + (q == 0 ? R.r[kRecLs] : 0.0);
+                    const double aq1 = q > 0 ? R.Lk[q - 1] + (q == 1 ? R.r[kRecLs] : 0.0) : 0.0;
+                    double sq = 0.0;
+                    for (int i = 0; i <= q; ++i) sq += R.Lk[i] * R.Lk[q - i];
+                    R.thk[q] = fmcc * aq + muc * aq1 - mu2 * sq;
+                }
+            }
         }
         __syncwarp();
         double mine[kRecEntries];
@@ -117,11 +294,26 @@ adjoint_fp64_kernel(SynthArgs A, int W, const void *__restrict__ grad, int grad_
         while (mask) {
             const int i = __ffs(mask) - 1;
             mask &= mask - 1;
-            const RecA &R = sR[warp][i];
+            const Rec &R = sR[warp][i];
             const double *d = R.r + kRecD;
+            bool mixed_done = false;
+            if constexpr (MX) {
+                if (R.kind == kRecVertex) {          // uniform over the warp (record i)
+                    float fb[kRecD + 6];
+                    adj_vertex_mixed<S>(R, m0, f0, mu, fs, c, gr, gi, fb);
+#pragma unroll
+                    for (int e = 0; e < kRecD + 6; ++e) {
+                        const float tot = warp_sum_f(fb[e]);
+                        if (lane == i) mine[e] = (double)tot;
+                    }
+                    mixed_done = true;
+                }
+            }
+            if (!mixed_done) {
             double ab[kRecEntries];
 #pragma unroll
             for (int e = 0; e < kRecEntries; ++e) ab[e] = 0.0;
+            {
             // Per lane (samples m0 .. m0 + S - 1, t = t0 + tau):
             //  - sqrt(Q(t)) and 0.5 / sqrt(Q(t)) from their expansions in
             //    u = (Q(t) - Q(t0)) / Q(t0): sqrt(1+u) = 1 + u/2 - u^2/8 + u^3/16,
@@ -252,6 +444,7 @@ adjoint_fp64_kernel(SynthArgs A, int W, const void *__restrict__ grad, int grad_
                 ab[3] += aL * ir;
                 ab[4] += aL * ir * t;
             }
+            }
             // entries each form uses: qt, qr and 6 / 16 / 9 coefficients
             const int used = kRecD + (R.kind == kRecVertex ? 6 : R.kind == kRecSeries ? 16 : 9);
 #pragma unroll
@@ -261,10 +454,11 @@ adjoint_fp64_kernel(SynthArgs A, int W, const void *__restrict__ grad, int grad_
                     if (lane == i) mine[e] = tot;
                 }
             }
+            }
         }
         // reverse through the record construction, one parameter at a time
         if (valid) {
-            const RecA &R = sR[warp][lane];
+            const Rec &R = sR[warp][lane];
             double tri[9], c0[3];
             for (int q = 0; q < 9; ++q) tri[q] = A.tri64[9 * k + q];
             for (int r = 0; r < 3; ++r) c0[r] = A.c64[3 * k + r];
@@ -318,8 +512,9 @@ __global__ void adjoint_scatter_kernel(const double *__restrict__ gfac, const Fa
 
 int64_t adjoint_facet_words(int64_t F) { return 10 * F; }
 
-void launch_adjoint_fp64(const SynthArgs &a, const void *grad, int grad_c64, double *gfac,
-                         cudaStream_t s)
+template <bool MX>
+static void launch_adjoint(const SynthArgs &a, const void *grad, int grad_c64, double *gfac,
+                           cudaStream_t s)
 {
     const int M = a.rd.M;
     int S = kAdjS;
@@ -329,11 +524,23 @@ void launch_adjoint_fp64(const SynthArgs &a, const void *grad, int grad_c64, dou
     const int64_t warps = (int64_t)a.VO * a.rd.N * W;
     const unsigned int grid = (unsigned int)((warps + kAdjWarps - 1) / kAdjWarps);
     switch (S) {
-    case 8: adjoint_fp64_kernel<8><<<grid, kAdjWarps * 32, 0, s>>>(a, W, grad, grad_c64, gfac); break;
-    case 4: adjoint_fp64_kernel<4><<<grid, kAdjWarps * 32, 0, s>>>(a, W, grad, grad_c64, gfac); break;
-    case 2: adjoint_fp64_kernel<2><<<grid, kAdjWarps * 32, 0, s>>>(a, W, grad, grad_c64, gfac); break;
-    default: adjoint_fp64_kernel<1><<<grid, kAdjWarps * 32, 0, s>>>(a, W, grad, grad_c64, gfac); break;
+    case 8: adjoint_fp64_kernel<8, MX><<<grid, kAdjWarps * 32, 0, s>>>(a, W, grad, grad_c64, gfac); break;
+    case 4: adjoint_fp64_kernel<4, MX><<<grid, kAdjWarps * 32, 0, s>>>(a, W, grad, grad_c64, gfac); break;
+    case 2: adjoint_fp64_kernel<2, MX><<<grid, kAdjWarps * 32, 0, s>>>(a, W, grad, grad_c64, gfac); break;
+    default: adjoint_fp64_kernel<1, MX><<<grid, kAdjWarps * 32, 0, s>>>(a, W, grad, grad_c64, gfac); break;
     }
+}
+
+void launch_adjoint_fp64(const SynthArgs &a, const void *grad, int grad_c64, double *gfac,
+                         cudaStream_t s)
+{
+    launch_adjoint<false>(a, grad, grad_c64, gfac, s);
+}
+
+void launch_adjoint_mixed(const SynthArgs &a, const void *grad, int grad_c64, double *gfac,
+                          cudaStream_t s)
+{
+    launch_adjoint<true>(a, grad, grad_c64, gfac, s);
 }
 
 void launch_adjoint_scatter(const double *gfac, const FacetRec *fac, const InstDev *insts,

@@ -196,6 +196,8 @@ void launch_synth_fp64(const SynthArgs &a, cudaStream_t s);
 // gfac: F x 10 (world vertex coordinates at t0, reflectivity) per facet
 void launch_adjoint_fp64(const SynthArgs &a, const void *grad, int grad_c64, double *gfac,
                          cudaStream_t s);
+void launch_adjoint_mixed(const SynthArgs &a, const void *grad, int grad_c64, double *gfac,
+                         cudaStream_t s);
 // facet gradients -> instance-major mesh-local vertex gradients (voff: first
 // vertex of each instance) and per-facet reflectivity gradients (may be NULL)
 void launch_adjoint_scatter(const double *gfac, const FacetRec *fac, const InstDev *insts,

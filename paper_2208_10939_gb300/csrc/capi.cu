@@ -472,15 +472,18 @@ int bart_radar_set(bart_ctx *ctx, const bart_radar *r)
     return BART_OK;
 }
 
-// internal path: the adjoint of the FP64 synthesis (bart_simulate_adjoint)
+// internal paths: the adjoint of the FP64 synthesis (bart_simulate_adjoint),
+// with its vertex-form per-sample work in FP32 (bart_simulate_adjoint_mixed)
 constexpr int kPathAdjoint = 100;
+constexpr int kPathAdjointMixed = 101;
 
 static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t dtype,
                      bart_stats *stats)
 {
     if (!ctx->have_radar) return fail(BART_ESTATE, "bart_simulate_frame: radar not set");
     if (ctx->insts.empty()) return fail(BART_ESTATE, "bart_simulate_frame: scene has no instances");
-    if (path != BART_PATH_FP64 && path != BART_PATH_MIXED && path != kPathAdjoint)
+    if (path != BART_PATH_FP64 && path != BART_PATH_MIXED && path != kPathAdjoint &&
+        path != kPathAdjointMixed)
         return fail(BART_EINVAL, "bart_simulate_frame: path=%d", path);
     if (dtype != BART_C64 && dtype != BART_C128)
         return fail(BART_EINVAL, "bart_simulate_frame: dtype=%d", dtype);
@@ -547,7 +550,7 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
     BART_TRY(ctx->blk_cnt.ensure(compact_blk_words(F, O + A), "compaction counts"));
     BART_TRY(ctx->vis_idx.ensure((size_t)(O + A) * F, "lit facet lists"));
     BART_TRY(ctx->vis_cnt.ensure(O + A, "lit facet counts"));
-    if (path == kPathAdjoint) {
+    if (path == kPathAdjoint || path == kPathAdjointMixed) {
         BART_TRY(ctx->gfac.ensure((size_t)10 * F, "facet gradients"));
         BART_TRY(ctx->d_voff.ensure((size_t)I, "instance vertex offsets"));
         std::vector<int64_t> voff(I);
@@ -719,10 +722,13 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
             if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_syn[1], s), "cudaEventRecord");
             ctx->chunks = 1;
             launches += 4;
-        } else if (path == kPathAdjoint) {
+        } else if (path == kPathAdjoint || path == kPathAdjointMixed) {
             a.n0 = 0;
             a.nc = rd.N;
-            launch_adjoint_fp64(a, ctx->adj_grad, ctx->adj_grad_c64, ctx->gfac.p, s);
+            if (path == kPathAdjoint)
+                launch_adjoint_fp64(a, ctx->adj_grad, ctx->adj_grad_c64, ctx->gfac.p, s);
+            else
+                launch_adjoint_mixed(a, ctx->adj_grad, ctx->adj_grad_c64, ctx->gfac.p, s);
             launch_adjoint_scatter(ctx->gfac.p, ctx->fac.p, ctx->d_insts.p, ctx->d_meshes.p,
                                    ctx->d_voff.p, F, ctx->adj_gverts, ctx->adj_vwords,
                                    ctx->adj_grho, s);
@@ -744,7 +750,8 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
         return BART_OK;
     };
 
-    const bool use_graph = ctx->graph && !stats && !ctx->timing && path != kPathAdjoint;
+    const bool use_graph = ctx->graph && !stats && !ctx->timing && path != kPathAdjoint &&
+                           path != kPathAdjointMixed;
     if (use_graph) {
         bart_ctx::FrameGraph &g = ctx->fg;
         const bool hit = g.exec && g.version == ctx->version && g.path == path &&
@@ -854,23 +861,36 @@ int bart_simulate_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32
     return run_frame(ctx, t0, path, adc, dtype, stats);
 }
 
-int bart_simulate_adjoint(bart_ctx *ctx, double t0, const void *grad_adc, int32_t dtype,
-                          double *grad_verts, double *grad_rho)
+static int run_adjoint(bart_ctx *ctx, double t0, const void *grad_adc, int32_t dtype,
+                       double *grad_verts, double *grad_rho, int path, const char *name)
 {
     g_err.clear();
-    if (!ctx || !grad_adc || !grad_verts)
-        return fail(BART_EINVAL, "bart_simulate_adjoint: NULL argument");
+    if (!ctx || !grad_adc || !grad_verts) return fail(BART_EINVAL, "%s: NULL argument", name);
     if (dtype != BART_C64 && dtype != BART_C128)
-        return fail(BART_EINVAL, "bart_simulate_adjoint: dtype=%d", dtype);
+        return fail(BART_EINVAL, "%s: dtype=%d", name, dtype);
     ctx->adj_grad = grad_adc;
     ctx->adj_grad_c64 = dtype == BART_C64;
     ctx->adj_gverts = grad_verts;
     ctx->adj_grho = grad_rho;
     // the synthesis output pointer is unused on this path
-    const int rc = run_frame(ctx, t0, kPathAdjoint, const_cast<void *>(grad_adc), dtype, nullptr);
+    const int rc = run_frame(ctx, t0, path, const_cast<void *>(grad_adc), dtype, nullptr);
     ctx->adj_grad = nullptr;
     ctx->adj_gverts = ctx->adj_grho = nullptr;
     return rc;
+}
+
+int bart_simulate_adjoint(bart_ctx *ctx, double t0, const void *grad_adc, int32_t dtype,
+                          double *grad_verts, double *grad_rho)
+{
+    return run_adjoint(ctx, t0, grad_adc, dtype, grad_verts, grad_rho, kPathAdjoint,
+                       "bart_simulate_adjoint");
+}
+
+int bart_simulate_adjoint_mixed(bart_ctx *ctx, double t0, const void *grad_adc, int32_t dtype,
+                                double *grad_verts, double *grad_rho)
+{
+    return run_adjoint(ctx, t0, grad_adc, dtype, grad_verts, grad_rho, kPathAdjointMixed,
+                       "bart_simulate_adjoint_mixed");
 }
 
 int bart_set_graph(bart_ctx *ctx, int32_t enable)

@@ -1,0 +1,127 @@
+"""GPU tests of the mixed-precision adjoint (bart_simulate_adjoint_mixed):
+the same record adjoint as the FP64 adjoint with the per-sample work of
+vertex-form records in FP32.  Its gradients are compared with the FP64
+adjoint's on the same weights, on small scenes (every facet-integral form:
+the point target's facets take the series form) and on the perturbed-sedan
+inverse problem; through torch.autograd with a mixed-precision EchoScene,
+the directional derivative against the FP64 adjoint's."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2208_10939_gb300 as pkg
+import scenegen as sg
+from paper_2208_10939_gb300 import autograd as bag
+
+pytestmark = pytest.mark.gpu
+
+TOL_GRAD = 2e-5         # relative L2 of the gradient vector against the FP64 adjoint
+
+
+def rel_l2(a, b):
+    return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def sim():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    s = pkg.Simulator(0)
+    yield s
+    s.close()
+
+
+def oblique_plate():
+    s = sg.plate_scene(range_m=12.0, n=6, M=128, N=4)
+    s.instances[0].rot = sg.rot_z(0.2)
+    s.instances[0].vel = np.array([0.3, -2.0, 0.0])
+    return s
+
+
+CASES = {"oblique_plate": oblique_plate,
+         "small_car": lambda: sg.small_car_scene(ntri=600, M=128, N=4, P=2, Q=2),
+         "point": lambda: sg.point_target_scene(9.0, 3.0, M=128, N=4, edge=0.6e-3),
+         "tdm_ref_car": lambda: sg.small_car_scene(ntri=600, M=256, N=4, P=2, Q=2)}
+
+
+def both_gradients(sim, sc, seed):
+    sim.load_scene(sc)
+    shape = sim.adc_shape()
+    rng = np.random.default_rng(seed)
+    W = torch.from_numpy(rng.normal(size=shape) + 1j * rng.normal(size=shape)).cuda()
+    nv = sum(sc.meshes[i.mesh_id].verts.shape[0] for i in sc.instances)
+    nf = sum(sc.meshes[i.mesh_id].tris.shape[0] for i in sc.instances)
+    out = {}
+    for mixed in (False, True):
+        gv = torch.empty((nv, 3), dtype=torch.float64, device="cuda")
+        gr = torch.empty(nf, dtype=torch.float64, device="cuda")
+        pkg.bart_simulate_adjoint(sim.ctx, 0.0, W, gv, gr, mixed=mixed)
+        out[mixed] = (gv, gr)
+    return out
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_mixed_adjoint_matches_fp64_adjoint(sim, name):
+    sc = CASES[name]()
+    if name == "tdm_ref_car":
+        sc.radar.tdm = True
+        sc.radar.delay_ref = True
+    g = both_gradients(sim, sc, 7)
+    ev, er = rel_l2(g[True][0], g[False][0]), rel_l2(g[True][1], g[False][1])
+    print(f"{name}: mixed adjoint relL2 vertices {ev:.3e} reflectivity {er:.3e}")
+    assert torch.isfinite(g[True][0]).all() and torch.isfinite(g[True][1]).all()
+    assert ev <= TOL_GRAD and er <= TOL_GRAD
+
+
+def test_mixed_adjoint_sedan_inverse_problem():
+    """Config-5 workload: L = ||adc(v) - adc_target||^2 on the 20k-facet
+    sedan with 5 mm vertex noise (seed 5); the mixed adjoint's gradient
+    against the FP64 adjoint's for the same dL/dadc, and both times."""
+    s = pkg.Simulator(0)
+    try:
+        sc = sg.car_scene()
+        es = bag.EchoScene(s, sc)
+        v_true = es.vertex_tensor(sc, "cuda")
+        with torch.no_grad():
+            target = bag.echo(v_true, None, es).clone()
+        rng = np.random.default_rng(5)
+        v0 = v_true + torch.from_numpy(0.005 * rng.normal(size=tuple(v_true.shape))).cuda()
+        with torch.no_grad():
+            adc = bag.echo(v0, None, es)
+        G = 2.0 * (adc - target)                 # dL/dRe + i dL/dIm of ||adc - target||^2
+        grads, times = {}, {}
+        for mixed in (False, True):
+            gv = torch.empty_like(v0)
+            pkg.bart_simulate_adjoint(s.ctx, 0.0, G, gv, None, mixed=mixed)   # warm-up
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            pkg.bart_simulate_adjoint(s.ctx, 0.0, G, gv, None, mixed=mixed)
+            torch.cuda.synchronize()
+            times[mixed] = time.perf_counter() - t
+            grads[mixed] = gv
+        err = rel_l2(grads[True], grads[False])
+        print(f"sedan adjoint: FP64 {1e3 * times[False]:.1f} ms, mixed {1e3 * times[True]:.1f} ms, "
+              f"gradient relL2 {err:.3e}")
+        assert err <= TOL_GRAD
+    finally:
+        s.close()
+
+
+def test_mixed_echo_autograd_directional_derivative(sim):
+    sc = sg.small_car_scene(ntri=600, M=128, N=4, P=2, Q=2)
+    es = bag.EchoScene(sim, sc, precision="mixed")
+    v0 = es.vertex_tensor(sc, "cuda")
+    verts = v0.clone().requires_grad_(True)
+    adc = bag.echo(verts, None, es)
+    assert adc.dtype == torch.complex64
+    W = torch.from_numpy(np.random.default_rng(3).normal(size=tuple(adc.shape))
+                         + 1j * np.random.default_rng(4).normal(size=tuple(adc.shape))).cuda()
+    (torch.conj(W.to(torch.complex64)) * adc).real.sum().backward()
+    u = torch.from_numpy(np.random.default_rng(6).normal(size=tuple(v0.shape))).cuda()
+    an = float((verts.grad * u).sum())
+    gv = torch.empty_like(v0)
+    pkg.bart_simulate_adjoint(sim.ctx, 0.0, W.to(torch.complex64).contiguous(), gv, None)
+    ref = float((gv * u).sum())
+    print(f"directional derivative: mixed {an:.8e} FP64 adjoint {ref:.8e}")
+    assert abs(an - ref) <= TOL_GRAD * abs(ref)
