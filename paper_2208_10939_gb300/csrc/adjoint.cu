@@ -13,7 +13,9 @@
 //   2. per record, each of the 10 parameters is pushed through the record
 //      construction in forward-mode dual numbers and dotted with rbar.
 // Facet gradients are then mapped to mesh-local vertices (transpose of the
-// instance rotation) and reflectivities.
+// instance rotation) and reflectivities.  The mixed variant
+// (bart_simulate_adjoint_mixed) runs stage 1 of vertex-form records in FP32
+// (adj_vertex_mixed); series and edge records and stage 2 stay FP64.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -55,8 +57,8 @@ __device__ __forceinline__ double warp_sum(double v)
 
 // Record adjoint of a vertex-form record over one lane's S samples with the
 // per-sample work in FP32 (the mixed adjoint).  FP64 gives each vertex's
-// phase at the lane's samples 0, 1 and S - 1 (the path lengths as in the
-// FP64 loop); the phasors then advance by an FP32 rotation along the chord
+// phase at the lane's samples 0, 1 and S - 1 (from the record's path-length
+// and phase polynomials); the phasors then advance by an FP32 rotation along the chord
 // of those phases (the phase's curvature over the lane, p2 (S - 1)^2 / 4
 // cycles, is left out: ~1e-5 rad on a moving car), and the sums over the
 // lane's samples run in FP32:
