@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "bart_internal.cuh"
@@ -180,7 +181,7 @@ constexpr int kAdjMixMinBlocks = 3;   // resident blocks the mixed variant's reg
 
 template <int S, bool MX>
 __global__ void __launch_bounds__(kAdjWarps * 32, MX ? kAdjMixMinBlocks : 1)
-adjoint_fp64_kernel(SynthArgs A, int W, const void *__restrict__ grad, int grad_c64,
+adjoint_fp64_kernel(SynthArgs A, int W, int NCH, const void *__restrict__ grad, int grad_c64,
                     double *__restrict__ gfac)
 {
     using Rec = typename std::conditional<MX, RecAX, RecA>::type;
@@ -188,8 +189,9 @@ adjoint_fp64_kernel(SynthArgs A, int W, const void *__restrict__ grad, int grad_
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t gw = (int64_t)blockIdx.x * kAdjWarps + warp;
     const int N = A.rd.N, M = A.rd.M;
-    const int64_t unit = gw / W;
-    const int seg = (int)(gw % W);
+    // warp = (row unit, sample segment, chunk of the row's facet list)
+    const int64_t unit = gw / ((int64_t)W * NCH);
+    const int seg = (int)(gw / NCH % W), chunk = (int)(gw % NCH);
     if (unit >= (int64_t)A.VO * N) return;
     const int vrow = (int)(unit / N), n = (int)(unit % N);
     const int o = vrow % A.rd.O;
@@ -231,7 +233,10 @@ adjoint_fp64_kernel(SynthArgs A, int W, const void *__restrict__ grad, int grad_
     const int32_t *list = A.vis_idx + (int64_t)o * F + (A.vstart ? A.vstart[vrow] : 0);
     const int cnt = A.vcnt[vrow];
 
-    for (int base = 0; base < cnt; base += 32) {
+    const int nbat = (cnt + 31) / 32;
+    const int bat0 = (int)((int64_t)nbat * chunk / NCH);
+    const int bat1 = (int)((int64_t)nbat * (chunk + 1) / NCH);
+    for (int base = bat0 * 32; base < bat1 * 32; base += 32) {
         const bool valid = base + lane < cnt;
         int64_t k = 0;
         double vel[3] = {0.0, 0.0, 0.0};
@@ -523,13 +528,20 @@ static void launch_adjoint(const SynthArgs &a, const void *grad, int grad_c64, d
     while (S > 1 && M % (32 * S) != 0) S >>= 1;
     const int W = M / (32 * S);
     cudaMemsetAsync(gfac, 0, (size_t)a.F * 10 * sizeof(double), s);
-    const int64_t warps = (int64_t)a.VO * a.rd.N * W;
+    // each row's facet list in NCH chunks: about four waves of resident
+    // blocks (a row per warp alone leaves the GPU a fraction of a wave on a
+    // single sedan: 1536 rows), at most one 32-facet batch per chunk
+    const int64_t rows = (int64_t)a.VO * a.rd.N * W;
+    const int64_t target = 4 * 152 * 3 * kAdjWarps;
+    const int64_t maxb = std::max<int64_t>(1, (a.F + 31) / 32);
+    const int NCH = (int)std::max<int64_t>(1, std::min<int64_t>(maxb, (target + rows - 1) / rows));
+    const int64_t warps = rows * NCH;
     const unsigned int grid = (unsigned int)((warps + kAdjWarps - 1) / kAdjWarps);
     switch (S) {
-    case 8: adjoint_fp64_kernel<8, MX><<<grid, kAdjWarps * 32, 0, s>>>(a, W, grad, grad_c64, gfac); break;
-    case 4: adjoint_fp64_kernel<4, MX><<<grid, kAdjWarps * 32, 0, s>>>(a, W, grad, grad_c64, gfac); break;
-    case 2: adjoint_fp64_kernel<2, MX><<<grid, kAdjWarps * 32, 0, s>>>(a, W, grad, grad_c64, gfac); break;
-    default: adjoint_fp64_kernel<1, MX><<<grid, kAdjWarps * 32, 0, s>>>(a, W, grad, grad_c64, gfac); break;
+    case 8: adjoint_fp64_kernel<8, MX><<<grid, kAdjWarps * 32, 0, s>>>(a, W, NCH, grad, grad_c64, gfac); break;
+    case 4: adjoint_fp64_kernel<4, MX><<<grid, kAdjWarps * 32, 0, s>>>(a, W, NCH, grad, grad_c64, gfac); break;
+    case 2: adjoint_fp64_kernel<2, MX><<<grid, kAdjWarps * 32, 0, s>>>(a, W, NCH, grad, grad_c64, gfac); break;
+    default: adjoint_fp64_kernel<1, MX><<<grid, kAdjWarps * 32, 0, s>>>(a, W, NCH, grad, grad_c64, gfac); break;
     }
 }
 
