@@ -532,7 +532,14 @@ static void launch_adjoint(const SynthArgs &a, const void *grad, int grad_c64, d
     // blocks (a row per warp alone leaves the GPU a fraction of a wave on a
     // single sedan: 1536 rows), at most one 32-facet batch per chunk
     const int64_t rows = (int64_t)a.VO * a.rd.N * W;
-    const int64_t target = 4 * 152 * 3 * kAdjWarps;
+    static int sms = 0;
+    if (sms <= 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    const int64_t target = 4 * (int64_t)sms * 3 * kAdjWarps;
     const int64_t maxb = std::max<int64_t>(1, (a.F + 31) / 32);
     const int NCH = (int)std::max<int64_t>(1, std::min<int64_t>(maxb, (target + rows - 1) / rows));
     const int64_t warps = rows * NCH;
