@@ -191,6 +191,9 @@ int64_t synth_max_items(const int64_t *scene_F, int n_scene, const RadarDev &rd,
 int synth_layout_samples(int M, int S_req);
 int synth_tiles_per_item(int64_t F);
 void launch_synth_fp64(const SynthArgs &a, cudaStream_t s);
+// chunks per chirp row of the FP64 synthesis; with more than one, SynthArgs
+// partial must hold chunks x VO x N x M double2 (the chunks' partial sums)
+int synth_fp64_chunks(const RadarDev &rd, int VO, int64_t F);
 
 // ---- adjoint of the FP64 synthesis (adjoint.cu) ----
 // gfac: F x 10 (world vertex coordinates at t0, reflectivity) per facet

@@ -618,6 +618,15 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
             BART_TRY(ensure_events(ctx->ev_syn, 2));
         }
     }
+    // the FP64 path splits each row's facet list over several warps when the
+    // rows alone would not fill the GPU; their partial sums need scratch
+    int fp64_chunks = 1;
+    if (path == BART_PATH_FP64) {
+        fp64_chunks = synth_fp64_chunks(rd, B * O, F);
+        if (fp64_chunks > 1)
+            BART_TRY(ctx->partial.ensure((size_t)fp64_chunks * B * O * rd.N * rd.M * 2,
+                                         "FP64 synthesis partials"));
+    }
     if (ctx->timing) BART_TRY(ensure_events(ctx->ev, 7));
 
     // every launch of the frame, on the caller's stream (the mixed path's
@@ -737,9 +746,10 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
         } else {
             a.n0 = 0;
             a.nc = rd.N;
+            a.partial = fp64_chunks > 1 ? ctx->partial.p : nullptr;
             launch_synth_fp64(a, s);
             ctx->chunks = 1;
-            launches += 1;
+            launches += fp64_chunks > 1 ? 2 : 1;
         }
         if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[4], s), "cudaEventRecord");
         ctx->path = path;

@@ -975,14 +975,15 @@ constexpr int kF64Warps = 4;
 
 template <int S>
 __global__ void __launch_bounds__(kF64Warps * 32)
-synth_fp64_kernel(SynthArgs A, int W)
+synth_fp64_kernel(SynthArgs A, int W, int NCH)
 {
     __shared__ RecD sR[kF64Warps][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t gw = (int64_t)blockIdx.x * kF64Warps + warp;
     const int N = A.rd.N;
-    const int64_t unit = gw / W;
-    const int seg = (int)(gw % W);
+    // warp = (row unit, sample segment, chunk of the row's facet list)
+    const int64_t unit = gw / ((int64_t)W * NCH);
+    const int seg = (int)(gw / NCH % W), chunk = (int)(gw % NCH);
     if (unit >= (int64_t)A.VO * N) return;
     const int vrow = (int)(unit / N), n = (int)(unit % N);   // scene * O + channel
     const int o = vrow % A.rd.O;
@@ -1006,7 +1007,10 @@ synth_fp64_kernel(SynthArgs A, int W)
     const int cnt = A.vcnt[vrow];
     unsigned long long nV = 0, nSr = 0, nE = 0;
 
-    for (int base = 0; base < cnt; base += 32) {
+    const int nbat = (cnt + 31) / 32;
+    const int bat0 = (int)((int64_t)nbat * chunk / NCH);
+    const int bat1 = (int)((int64_t)nbat * (chunk + 1) / NCH);
+    for (int base = bat0 * 32; base < bat1 * 32; base += 32) {
         const bool valid = base + lane < cnt;
         int cls = -1;
         if (valid) {
@@ -1110,7 +1114,10 @@ synth_fp64_kernel(SynthArgs A, int W)
         const double fm = f0 + mu * (double)(m0 + j) / fs;
         const double km = 2.0 * kPi * fm / c;
         const double sc = camp / (km * km);
-        if (A.out_c64) {
+        if (NCH > 1) {           // this chunk's scaled partial sums, added in order later
+            reinterpret_cast<double2 *>(A.partial)[(int64_t)chunk * A.VO * N * A.rd.M + row + j] =
+                make_double2(accr[j] * sc, acci[j] * sc);
+        } else if (A.out_c64) {
             reinterpret_cast<float2 *>(A.out)[row + j] =
                 make_float2((float)(accr[j] * sc), (float)(acci[j] * sc));
         } else {
@@ -1119,18 +1126,73 @@ synth_fp64_kernel(SynthArgs A, int W)
     }
 }
 
+// sums the chunks' partial sums of each (row, sample) in chunk order
+__global__ void synth_fp64_reduce_kernel(const double2 *__restrict__ partial, int64_t n, int NCH,
+                                         void *out, int out_c64)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double re = 0.0, im = 0.0;
+    for (int ch = 0; ch < NCH; ++ch) {
+        const double2 v = partial[(int64_t)ch * n + i];
+        re += v.x;
+        im += v.y;
+    }
+    if (out_c64) reinterpret_cast<float2 *>(out)[i] = make_float2((float)re, (float)im);
+    else reinterpret_cast<double2 *>(out)[i] = make_double2(re, im);
+}
+
+template <int S> static int fp64_blocks_per_sm()
+{
+    static int b = -1;
+    if (b < 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, synth_fp64_kernel<S>, kF64Warps * 32, 0);
+        if (b < 1) b = 1;
+    }
+    return b;
+}
+
+// chunks of each row's facet list: about four waves of resident blocks (a
+// warp per chirp row alone leaves a single sedan, 1536 rows, a fraction of
+// a wave), at most one 32-facet batch per chunk and 64 chunks
+int synth_fp64_chunks(const RadarDev &rd, int VO, int64_t F)
+{
+    const int M = rd.M;
+    const int S = samples_per_lane(M);
+    const int W = M / (32 * S);
+    static int sms = 0;
+    if (sms <= 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    const int bps = S == 8 ? fp64_blocks_per_sm<8>() : S == 4 ? fp64_blocks_per_sm<4>()
+                  : S == 2 ? fp64_blocks_per_sm<2>() : fp64_blocks_per_sm<1>();
+    const int64_t rows = (int64_t)VO * rd.N * W;
+    const int64_t target = 4 * (int64_t)sms * bps * kF64Warps;
+    const int64_t maxb = std::min<int64_t>(64, std::max<int64_t>(1, (F + 31) / 32));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(maxb, (target + rows - 1) / rows));
+}
+
 void launch_synth_fp64(const SynthArgs &a, cudaStream_t s)
 {
     const int M = a.rd.M;
     const int S = samples_per_lane(M);
     const int W = M / (32 * S);
-    const int64_t warps = (int64_t)a.VO * a.rd.N * W;
+    const int NCH = a.partial ? synth_fp64_chunks(a.rd, a.VO, a.F) : 1;
+    const int64_t warps = (int64_t)a.VO * a.rd.N * W * NCH;
     const unsigned int grid = (unsigned int)((warps + kF64Warps - 1) / kF64Warps);
     switch (S) {
-    case 8: synth_fp64_kernel<8><<<grid, kF64Warps * 32, 0, s>>>(a, W); break;
-    case 4: synth_fp64_kernel<4><<<grid, kF64Warps * 32, 0, s>>>(a, W); break;
-    case 2: synth_fp64_kernel<2><<<grid, kF64Warps * 32, 0, s>>>(a, W); break;
-    default: synth_fp64_kernel<1><<<grid, kF64Warps * 32, 0, s>>>(a, W); break;
+    case 8: synth_fp64_kernel<8><<<grid, kF64Warps * 32, 0, s>>>(a, W, NCH); break;
+    case 4: synth_fp64_kernel<4><<<grid, kF64Warps * 32, 0, s>>>(a, W, NCH); break;
+    case 2: synth_fp64_kernel<2><<<grid, kF64Warps * 32, 0, s>>>(a, W, NCH); break;
+    default: synth_fp64_kernel<1><<<grid, kF64Warps * 32, 0, s>>>(a, W, NCH); break;
+    }
+    if (NCH > 1) {
+        const int64_t n = (int64_t)a.VO * a.rd.N * M;
+        synth_fp64_reduce_kernel<<<(unsigned int)((n + 255) / 256), 256, 0, s>>>(
+            reinterpret_cast<const double2 *>(a.partial), n, NCH, a.out, a.out_c64);
     }
 }
 
