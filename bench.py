@@ -45,7 +45,7 @@ FP32_PIPE_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12    # SMs x FP32 lanes x max clo
 # DRAM bytes (read + write) of one synthesis launch on this workload, from the
 # ncu capture summarised in profiles/synth_mixed_moving_sedan.md; valid only
 # while the kernel's sources hash to the value they had at the capture
-SYNTH_TRAFFIC = {"bytes": 8.214016e6 + 30.114560e6, "sources_sha256_16": "2ec6592b853c1495",
+SYNTH_TRAFFIC = {"bytes": 8.219136e6 + 30.244096e6, "sources_sha256_16": "8c8d778b53f7a892",
                  "samples_per_lane": 16}
 SYNTH_SOURCES = ("synth.cu", "bart_internal.cuh", "record_fp64.cuh")
 
