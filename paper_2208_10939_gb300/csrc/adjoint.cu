@@ -177,7 +177,7 @@ __device__ __forceinline__ float warp_sum_f(float v)
     return v;
 }
 
-constexpr int kAdjMixMinBlocks = 3;   // resident blocks the mixed variant's register budget targets
+constexpr int kAdjMixMinBlocks = 4;   // resident blocks the mixed variant's register budget targets
 
 template <int S, bool MX>
 __global__ void __launch_bounds__(kAdjWarps * 32, MX ? kAdjMixMinBlocks : 1)
