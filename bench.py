@@ -1,20 +1,25 @@
 #!/usr/bin/env python
 """Throughput benchmark of the BART echo-synthesis hot path on GB300.
 
-Workload: the moving-sedan frame -- a procedural rounded-box sedan of 20k
-triangles (PEC) at 30 m slant range, approaching at 10 m/s, seen by a 3 TX x
-4 RX MIMO FMCW radar (12 virtual channels), 128 chirps x 256 samples, ADC
-cube complex64, RDM 256 x 128 FP32.  One step = one whole frame of the hot
-path: world facets, LBVH build, BART visibility, FP64 kinematics, echo
-synthesis (mixed path) and the windowed range-Doppler FFT into the RDM.
+Headline workload: the intersection frame -- 12 procedural vehicles (car
+20k, SUV 40k, bus 120k, truck 200k triangles; seeded positions 10-80 m,
+velocities -15..15 m/s) on a 100 m x 100 m ground of 50k triangles, ~1.47M
+facets in all, seen by a 12 TX x 16 RX sparse MIMO FMCW radar (192 virtual
+channels), 256 chirps x 512 samples, ADC cube complex64 (201 MB), RDM
+512 x 256 FP32.  One step = one whole frame of the hot path: world facets,
+LBVH build, BART visibility, FP64 kinematics rows, echo synthesis (mixed
+path) and the windowed range-Doppler FFT into the RDM.
 
-Metric: echo terms/s (lit facet x channel x chirp x sample); frames/s and the
-plain-FP64 path are reported beside it.  Inputs are resident in HBM when the
-timed region starts; L2 is flushed (256 MB write) between timed steps.
+Metric: echo terms/s (lit facet x channel x chirp x sample); frames/s, the
+moving-sedan frame (20k triangles, 12 channels, 128 x 256) and the plain-FP64
+path are reported beside it.  Inputs are resident in HBM when the timed
+region starts; the frame's working set (facet records, kinematics rows,
+ADC cube) is far larger than L2, which is also flushed (256 MB write)
+between timed steps.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-Under torchrun each rank simulates its own seeded sedan (weak scaling,
-replicas: the path needs no collective); rank 0 prints one JSON line.
+Under torchrun each rank simulates its own seeded intersection (weak
+scaling, replicas: the path needs no collective); rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -35,43 +40,63 @@ if ROOT not in sys.path:
 
 METRIC = "echo terms/s (facet x chan x chirp x sample), frames/s; mixed vs FP64 path"
 UNIT = "terms/s"
-WORKLOAD = "moving sedan 20k tris, 3TXx4RX (12 ch), 128 chirps x 256 samples"
+WORKLOAD = ("intersection: 12 vehicles (20k-200k tris) + 50k-tri ground, 12TXx16RX (192 ch), "
+            "256 chirps x 512 samples")
+SEDAN = "moving sedan 20k tris, 3TXx4RX (12 ch), 128 chirps x 256 samples"
 # algorithmic work of one echo term in the mixed path: 3 vertex phases, 3 unit
 # phasors, 3 real x complex weighted accumulates and their compensation, about
 # 24 FP32 FMA-pipe operations (plus 6 SFU operations when the phasors come from
 # sincos); the roofline counts operations of the FMA pipe, whatever their kind
 OPS_PER_TERM = 24
-FP32_PIPE_PEAK_TOPS = 152 * 128 * 2.070e9 / 1e12    # SMs x FP32 lanes x max clock
-# DRAM bytes (read + write) of one synthesis launch on this workload, from the
-# ncu capture summarised in profiles/synth_mixed_moving_sedan.md; valid only
+# DRAM bytes (read + write) per echo term of one synthesis launch and the
+# FMA-pipe activity, from ncu captures of the synthesis kernel; valid only
 # while the kernel's sources hash to the value they had at the capture
-SYNTH_TRAFFIC = {"bytes": 8.219136e6 + 30.244096e6, "sources_sha256_16": "8c8d778b53f7a892",
-                 "samples_per_lane": 16}
+SYNTH_PROFILE = {"sources_sha256_16": None, "samples_per_lane": 16,
+                 "dram_bytes_per_term": None, "fma_pipe_active": None}
 SYNTH_SOURCES = ("synth.cu", "bart_internal.cuh", "record_fp64.cuh")
 
 
-def synth_traffic(samples_per_lane: int = 16):
-    """Captured DRAM bytes per synthesis launch, or None when the kernel (its
-    sources, or the template instance chosen by the layout) differs from the
-    captured one."""
+def synth_sources_hash() -> str:
     import hashlib
-    if samples_per_lane != SYNTH_TRAFFIC["samples_per_lane"]:
-        return None
     h = hashlib.sha256()
     for f in SYNTH_SOURCES:
         with open(os.path.join(ROOT, "paper_2208_10939_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    return SYNTH_TRAFFIC["bytes"] if h.hexdigest()[:16] == SYNTH_TRAFFIC["sources_sha256_16"] else None
+    return h.hexdigest()[:16]
+
+
+def synth_profile(samples_per_lane: int):
+    """The captured per-term DRAM traffic and FMA-pipe activity, or None when
+    the kernel (its sources, or the template instance the layout picks)
+    differs from the captured one."""
+    if (samples_per_lane != SYNTH_PROFILE["samples_per_lane"]
+            or SYNTH_PROFILE["sources_sha256_16"] != synth_sources_hash()):
+        return None
+    return SYNTH_PROFILE
+
+
+def layout_samples(M: int, S_req: int) -> int:
+    """Samples per lane the mixed synthesis kernel uses for M samples per
+    chirp and a layout request (the library's rule, for naming the kernel)."""
+    if S_req == 8 and ((M <= 256 and 256 % M == 0) or M % 256 == 0):
+        return 8
+    if (M <= 512 and 512 % M == 0) or M % 512 == 0:
+        return 16
+    for S in (8, 4, 2):
+        if M % (32 * S) == 0:
+            return S
+    return 1
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=2)
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--sedan-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-scenes", type=int, default=32,
@@ -85,8 +110,14 @@ def parse():
     ap.add_argument("--synth-layout", default=None, metavar="S,T",
                     help="fix the synthesis layout (samples per lane, tiles per item) "
                          "instead of autotuning it")
-    ap.add_argument("--no-intersection", action="store_true",
-                    help="skip the full-intersection frame")
+    ap.add_argument("--workload", default="intersection", choices=["intersection", "sedan"],
+                    help="headline frame (the sedan for quick profiling runs)")
+    ap.add_argument("--no-sedan", action="store_true", help="skip the moving-sedan lines")
+    ap.add_argument("--no-peaks", action="store_true",
+                    help="skip the peak microbenchmarks (roofline against no measured peak)")
+    ap.add_argument("--log", default=os.environ.get("BART_RUN_LOG"),
+                    help="append the run's record (JSON line plus seeds, clocks, oracle errors, "
+                         "grazing counts) to this JSONL file")
     return ap.parse_args()
 
 
@@ -149,61 +180,77 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def cpu_baseline(scene, seconds: float, rank0_frame=None) -> dict:
-    """The FP64 oracle as it stands, on the host cores: terms/s of its echo
-    synthesis over a random sample of ADC entries of the same frame."""
+def _lit_per_channel(fr, r):
+    import oracle
+    lit = fr.state == oracle.LIT
+    return (lit[:r.P, None, :] & lit[None, r.P:, :]).sum(axis=2).reshape(-1)
+
+
+def _sample_entries(rng, r, E):
+    return np.stack([rng.integers(0, r.O, E), rng.integers(0, r.N, E),
+                     rng.integers(0, r.M, E)], 1).astype(np.int32)
+
+
+def cpu_baseline(scene, seconds: float, adc=None) -> dict:
+    """The FP64 oracle as it stands, on the host cores: echo terms/s of its
+    synthesis over a random sample of ADC entries of the same frame (sized
+    to ~``seconds`` of work), and the full-frame oracle time extrapolated
+    from that rate.  With ``adc`` (the GPU cube of the timed frame, host
+    array) the sampled entries also give the frame's error against the
+    oracle."""
     import oracle
     t = time.perf_counter()
-    fr = rank0_frame or oracle.Frame(scene)
+    fr = oracle.Frame(scene)
     t_vis = time.perf_counter() - t
     r = scene.radar
-    lit = fr.state == oracle.LIT
-    per_ch = (lit[:r.P, None, :] & lit[None, r.P:, :]).sum(axis=2).reshape(-1)
+    per_ch = _lit_per_channel(fr, r)
     rng = np.random.default_rng(12345)
-
-    def sample(E):
-        e = np.stack([rng.integers(0, r.O, E), rng.integers(0, r.N, E),
-                      rng.integers(0, r.M, E)], 1).astype(np.int32)
-        return e, int(per_ch[e[:, 0]].sum())
-
-    e, terms = sample(64)
+    e = _sample_entries(rng, r, 16)
     t = time.perf_counter()
     fr.adc_entries(e)
     dt = time.perf_counter() - t
-    E = max(64, int(64 * seconds / max(dt, 1e-3)))
-    e, terms = sample(E)
+    E = max(16, int(16 * seconds / max(dt, 1e-3)))
+    e = _sample_entries(rng, r, E)
+    terms = int(per_ch[e[:, 0]].sum())
     t = time.perf_counter()
-    fr.adc_entries(e)
+    ref = fr.adc_entries(e)
     dt = time.perf_counter() - t
-    return {"value": terms / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{E} random ADC entries of the frame ({terms} echo terms, {dt:.1f} s); "
-                      f"oracle brute-force visibility of the frame took {t_vis:.1f} s (untimed)"}
+    rate = terms / dt
+    frame_terms = int(per_ch.sum()) * r.N * r.M
+    out = {"value": rate, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": f"{E} random ADC entries of the frame ({terms} echo terms, {dt:.1f} s of "
+                     f"oracle synthesis); oracle visibility of the frame (its own BVH) took "
+                     f"{t_vis:.1f} s, untimed",
+           "frame_s_extrapolated": frame_terms / rate + t_vis}
+    if adc is not None:
+        got = adc[e[:, 0], e[:, 1], e[:, 2]].astype(np.complex128)
+        out["gpu_frame_rel_l2_vs_oracle"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        out["gpu_frame_checked_entries"] = int(E)
+    return out
 
 
 def run_reference(args):
-    """--impl reference: the oracle, timed on the host cores (rank 0 only)."""
+    """--impl reference: the oracle, timed on the host cores (rank 0 only),
+    on the headline workload: each step a bounded random sample of ADC
+    entries of the frame (~4 s of oracle work)."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
     import oracle
     import scenegen as sg
-    scene = sg.car_scene()
+    scene = sg.intersection_scene() if args.workload == "intersection" else sg.car_scene()
     fr = oracle.Frame(scene)
     r = scene.radar
-    lit = fr.state == oracle.LIT
-    per_ch = (lit[:r.P, None, :] & lit[None, r.P:, :]).sum(axis=2).reshape(-1)
+    per_ch = _lit_per_channel(fr, r)
     terms_frame = int(per_ch.sum()) * r.N * r.M
     rng = np.random.default_rng(7)
-    # size each step to ~4 s of oracle work
-    e = np.stack([rng.integers(0, r.O, 32), rng.integers(0, r.N, 32),
-                  rng.integers(0, r.M, 32)], 1).astype(np.int32)
+    e = _sample_entries(rng, r, 16)
     t = time.perf_counter()
     fr.adc_entries(e)
-    E = max(32, int(32 * 4.0 / max(time.perf_counter() - t, 1e-3)))
+    E = max(16, int(16 * 4.0 / max(time.perf_counter() - t, 1e-3)))
     tot_terms, tot_t = 0, 0.0
     for step in range(args.warmup + args.steps):
-        e = np.stack([rng.integers(0, r.O, E), rng.integers(0, r.N, E),
-                      rng.integers(0, r.M, E)], 1).astype(np.int32)
+        e = _sample_entries(rng, r, E)
         terms = int(per_ch[e[:, 0]].sum())
         t = time.perf_counter()
         fr.adc_entries(e)
@@ -218,7 +265,8 @@ def run_reference(args):
            "ms_per_step": 1e3 * tot_t / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
-           "config": {"workload": WORKLOAD, "path": "FP64 CPU oracle", "seed": 2},
+           "config": {"workload": WORKLOAD if args.workload == "intersection" else SEDAN,
+                      "path": "FP64 CPU oracle", "seed": 3 if args.workload == "intersection" else 2},
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(),
                             "kind": "oracle", "sample": sample},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -351,38 +399,6 @@ def detect_timing(pkg, torch, sim, adc, stream, reps: int = 10) -> dict:
             "cfar": "guard 2x2, train 8x4, Pfa 1e-6", "snr_db": 20.0}
 
 
-def intersection_frame(pkg, sg, torch, dev) -> dict:
-    """The full intersection (12 vehicles + ground, ~1.5M facets, 12 TX x
-    16 RX = 192 channels, 256 chirps x 512 samples): one mixed-path frame and
-    its RDM after a warm-up frame; per-stage CUDA-event times."""
-    sc = sg.intersection_scene()
-    s = pkg.Simulator(dev.index or 0)
-    try:
-        s.load_scene(sc)
-        r = sc.radar
-        adc = torch.empty((r.O, r.N, r.M), dtype=torch.complex64, device=dev)
-        rdm = torch.empty((r.M, r.N), dtype=torch.float32, device=dev)
-        pkg.bart_set_timing(s.ctx, True)
-        _, st = s.simulate(pkg.PATH_MIXED, out=adc, stats=True)
-        s.rdm(adc, rdm)
-        torch.cuda.synchronize(dev)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        s.simulate(pkg.PATH_MIXED, out=adc)
-        s.rdm(adc, rdm)
-        e1.record()
-        e1.synchronize()
-        ms = e0.elapsed_time(e1)
-        tm = pkg.bart_get_timing(s.ctx)
-        return {"workload": "intersection: %d facets, 192 channels, 256 x 512" % st["n_facets"],
-                "terms": st["n_terms"], "frame_ms": ms, "terms_per_s": st["n_terms"] / (ms / 1e3),
-                "stages_ms": {k: tm[k] for k in ("scene_ms", "bvh_ms", "visibility_ms",
-                                                 "kinematics_ms", "synthesis_ms", "rdm_ms")}}
-    finally:
-        s.close()
-
-
 def adjoint_timing(pkg, sg, torch, dev, reps: int) -> dict:
     """Differentiable echo on the perturbed-sedan inverse problem: the
     sedan as target, its copy with 5 mm vertex noise (seed 5) as the
@@ -436,6 +452,145 @@ def adjoint_timing(pkg, sg, torch, dev, reps: int) -> dict:
         s.close()
 
 
+def measure_peaks(pkg, dev_index: int) -> dict:
+    """Measured FP32 FMA-pipe, MUFU and FP64 rates of this GPU (the library's
+    own register-only microbenchmarks)."""
+    p = pkg.bart_measure_peaks(dev_index, reps=5)
+    fp32 = max(p["fp32_fma_per_s"], p["fp32x2_fma_per_s"])
+    return {"fp32_fma_pipe_tops": fp32 / 1e12,
+            "fp32_scalar_fma_tops": p["fp32_fma_per_s"] / 1e12,
+            "fp32x2_fma_tops": p["fp32x2_fma_per_s"] / 1e12,
+            "mufu_sincos_per_s": p["sincos_per_s"],
+            "fp64_fma_tops": p["fp64_fma_per_s"] / 1e12,
+            "sms": p["sms"], "how": "bart_measure_peaks: register-only FMA / f32x2 FMA / "
+                                    "__sincosf / FP64 FMA chains, 2048 threads per SM, "
+                                    "best of 5 CUDA-event-timed launches"}
+
+
+def timed_frames(pkg, torch, sim, adc, rdm, flush, stream, steps: int, path: int) -> dict:
+    """``steps`` frames (simulate + RDM), L2 flushed before each; per-step
+    device times (CUDA events on the launching stream) and the library's
+    per-stage times."""
+    step_ms, synth_ms, launches, tm = [], [], 0, None
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.simulate(path, out=adc)
+        sim.rdm(adc, rdm)
+        e1.record(stream)
+        tm = pkg.bart_get_timing(sim.ctx)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        synth_ms.append(tm["synthesis_ms"])
+        launches += tm["launches"]
+    return {"step_ms": step_ms, "synth_ms": synth_ms, "launches": launches, "last": tm}
+
+
+def e2e_run(pkg, torch, sim, scene, path: int, steps: int, job_terms_per_step: float) -> dict:
+    """End to end through the public C-ABI with host buffers: every step
+    uploads the meshes and instances from pinned host memory, sets the
+    radar, simulates the frame, forms the RDM and reads it back
+    (bart_frame_host)."""
+    import ctypes
+    from paper_2208_10939_gb300 import sharding
+    L = pkg.load_library()
+    r = scene.radar
+    hm = [(torch.from_numpy(m.verts).pin_memory(), torch.from_numpy(m.tris).pin_memory(),
+           torch.from_numpy(m.rho).pin_memory()) for m in scene.meshes]
+    h_rdm = torch.empty((r.M, r.N), dtype=torch.float32).pin_memory()
+    insts = pkg.make_instances(scene.instances)
+    radar_c = pkg.make_radar(r)
+    mid = ctypes.c_int32()
+    h2d = sum(v.numel() * 8 + t.numel() * 4 + p.numel() * 4 for v, t, p in hm)
+    h2d += ctypes.sizeof(insts) + ctypes.sizeof(pkg.bart_radar)
+
+    def step():
+        pkg._check(L.bart_mesh_clear(sim.ctx))
+        for v, t, p in hm:
+            pkg._check(L.bart_mesh_upload(sim.ctx, v.data_ptr(), v.shape[0], t.data_ptr(),
+                                          t.shape[0], p.data_ptr(), ctypes.byref(mid)))
+        pkg._check(L.bart_scene_set(sim.ctx, ctypes.cast(insts, ctypes.c_void_p), len(insts)))
+        pkg._check(L.bart_radar_set(sim.ctx, ctypes.byref(radar_c)))
+        pkg._check(L.bart_frame_host(sim.ctx, float(scene.t0), path, h_rdm.data_ptr(), None))
+
+    step()
+    sharding.reduce_scalar(0.0)          # barrier-like sync of the ranks
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize()
+    e2e_s = sharding.reduce_scalar(time.perf_counter() - t, "max")
+    return {"value": job_terms_per_step * steps / e2e_s, "unit": UNIT,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(r.M * r.N * 4),
+            "ms_per_step": 1e3 * e2e_s / steps}
+
+
+def sedan_lines(pkg, sg, torch, dev, args, peaks) -> dict:
+    """The moving-sedan frame (config 2): mixed path with the autotuned
+    layout, its synthesis roofline, the plain FP64 path on the same frame,
+    and the point cloud of the mixed cube with receiver noise."""
+    scene = sg.car_scene()
+    sim = pkg.Simulator(dev.index or 0)
+    try:
+        sim.load_scene(scene)
+        r = scene.radar
+        adc = torch.empty((r.O, r.N, r.M), dtype=torch.complex64, device=dev)
+        rdm = torch.empty((r.M, r.N), dtype=torch.float32, device=dev)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        stream = torch.cuda.current_stream(dev)
+        pkg.bart_set_timing(sim.ctx, True)
+        _, st = sim.simulate(pkg.PATH_MIXED, out=adc, stats=True)
+        terms = st["n_terms"]
+        if args.synth_layout:
+            S_fix, T_fix = (int(x) for x in args.synth_layout.split(","))
+            pkg.bart_set_synth_layout(sim.ctx, S_fix, T_fix)
+            tune = {"best": (S_fix, T_fix), "source": "--synth-layout"}
+        elif not args.no_autotune:
+            tune = pkg.bart_autotune(sim.ctx, 0.0, adc, reps=2)
+        else:
+            tune = None
+        for _ in range(3):
+            sim.simulate(pkg.PATH_MIXED, out=adc)
+            sim.rdm(adc, rdm)
+        sim.sync()
+        tf = timed_frames(pkg, torch, sim, adc, rdm, flush, stream, args.sedan_steps,
+                          pkg.PATH_MIXED)
+        synth_avg = statistics.mean(tf["synth_ms"]) / max(1, tf["last"]["synthesis_launches"])
+        out = {"workload": SEDAN, "facets": st["n_facets"], "echo_terms_per_frame": terms,
+               "value": terms * len(tf["step_ms"]) / (sum(tf["step_ms"]) / 1e3), "unit": UNIT,
+               "ms_per_step": statistics.mean(tf["step_ms"]),
+               "frames_per_s": 1e3 / statistics.mean(tf["step_ms"]),
+               "synthesis_ms": synth_avg,
+               "synthesis_layout": None if tune is None else
+               {"samples_per_lane": tune["best"][0], "tiles_per_item": tune["best"][1]},
+               "stages_ms_last_step": {k: tf["last"][k] for k in
+                                       ("scene_ms", "bvh_ms", "visibility_ms", "kinematics_ms",
+                                        "synthesis_ms", "rdm_ms")}}
+        if peaks:
+            ach = terms * OPS_PER_TERM / (synth_avg / 1e3) / 1e12
+            out["roofline_frac_of_measured_fp32"] = ach / peaks["fp32_fma_pipe_tops"]
+        # plain FP64 path on the same frame (the parity reference path)
+        adc64 = torch.empty((r.O, r.N, r.M), dtype=torch.complex128, device=dev)
+        if args.fp64_steps > 0:
+            sim.simulate(pkg.PATH_FP64, out=adc64)
+            sim.sync()
+            t64 = timed_frames(pkg, torch, sim, adc64, rdm, flush, stream, args.fp64_steps,
+                               pkg.PATH_FP64)
+            out["fp64_path"] = {"value": terms * len(t64["step_ms"]) / (sum(t64["step_ms"]) / 1e3),
+                                "unit": UNIT, "ms_per_step": statistics.mean(t64["step_ms"]),
+                                "synthesis_ms": statistics.mean(t64["synth_ms"])}
+            if peaks:
+                out["fp64_path"]["fp64_fma_tops_measured"] = peaks["fp64_fma_tops"]
+        del adc64
+        out["point_cloud"] = detect_timing(pkg, torch, sim, adc, stream)
+        return out
+    finally:
+        sim.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -453,8 +608,17 @@ def main():
     pkg.load_library()
     torch.cuda.set_device(local)
     dev = torch.device(f"cuda:{local}")
+    peaks = None if args.no_peaks else measure_peaks(pkg, local)
 
-    scene = sg.car_scene(seed=2 + rank)
+    # ---------------- headline frame ----------------
+    if args.workload == "intersection":
+        seed = 3 + rank
+        scene = sg.intersection_scene(seed=seed)
+        workload = WORKLOAD
+    else:
+        seed = 2 + rank
+        scene = sg.car_scene(seed=seed)
+        workload = SEDAN
     sim = pkg.Simulator(local)
     sim.load_scene(scene)
     r = scene.radar
@@ -465,15 +629,15 @@ def main():
     pkg.bart_set_timing(sim.ctx, True)
     _, st = sim.simulate(pkg.PATH_MIXED, out=adc, stats=True)
     terms = st["n_terms"]
-    tune = None
+    layout = None
     if args.synth_layout:
         S_fix, T_fix = (int(x) for x in args.synth_layout.split(","))
         pkg.bart_set_synth_layout(sim.ctx, S_fix, T_fix)
-        tune = {"best": (S_fix, T_fix), "source": "--synth-layout"}
-    elif not args.no_autotune:
-        # the library's autotuner picks the synthesis layout for this scene
-        # (timed synthesis trials; untimed here, part of the warm-up)
+        layout = {"samples_per_lane": S_fix, "tiles_per_item": T_fix, "source": "--synth-layout"}
+    elif args.workload == "sedan" and not args.no_autotune:
         tune = pkg.bart_autotune(sim.ctx, 0.0, adc, reps=2)
+        layout = {"samples_per_lane": tune["best"][0], "tiles_per_item": tune["best"][1],
+                  "source": "bart_autotune"}
     for _ in range(args.warmup):
         sim.simulate(pkg.PATH_MIXED, out=adc)
         sim.rdm(adc, rdm)
@@ -484,114 +648,60 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
-    step_ms, synth_ms, kin_ms, launches = [], [], [], 0
-    synth_launches = 0
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        sim.simulate(pkg.PATH_MIXED, out=adc)
-        sim.rdm(adc, rdm)
-        e1.record(stream)
-        tm = pkg.bart_get_timing(sim.ctx)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        synth_ms.append(tm["synthesis_ms"])
-        kin_ms.append(tm["kinematics_ms"])
-        launches += tm["launches"]
-        synth_launches = tm["synthesis_launches"]
+    tf = timed_frames(pkg, torch, sim, adc, rdm, flush, stream, args.steps, pkg.PATH_MIXED)
     torch.cuda.synchronize(dev)
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
     sim.sync()
-    last_tm = tm
+    last_tm = tf["last"]
     # replicas: whole-job terms over the slowest rank's time
-    job = sharding.job_throughput(float(terms) * args.steps, float(sum(step_ms)) / 1e3)
+    job = sharding.job_throughput(float(terms) * args.steps, float(sum(tf["step_ms"])) / 1e3)
     total_ms = 1e3 * job["seconds"]
     job_terms_per_step = job["work"] / args.steps
     value = job["per_second"]
     frames = world * args.steps / (total_ms / 1e3)
 
     # dominant kernel: echo synthesis, average launch duration from CUDA events
-    synth_avg_ms = statistics.mean(synth_ms) / max(1, synth_launches)
-    achieved = terms / max(1, synth_launches) * OPS_PER_TERM / (synth_avg_ms / 1e3) / 1e12
+    synth_launches = max(1, last_tm["synthesis_launches"])
+    synth_avg_ms = statistics.mean(tf["synth_ms"]) / synth_launches
+    achieved = terms / synth_launches * OPS_PER_TERM / (synth_avg_ms / 1e3) / 1e12
+    S_used = layout_samples(M, 0 if layout is None else layout["samples_per_lane"])
+    prof = synth_profile(S_used)
+    if peaks:
+        peak, peak_basis = peaks["fp32_fma_pipe_tops"], (
+            "measured: FP32 FMA-pipe operations/s of this GPU (bart_measure_peaks, the faster "
+            "of scalar and packed f32x2 FMA chains)")
+    else:
+        peak, peak_basis = 152 * 128 * 2.070e9 / 1e12, "nominal: 152 SM x 128 lanes x 2070 MHz"
+    roofline = {"bound": "alu", "kernel": f"synth_mixed_kernel<{S_used}, *>",
+                "achieved": achieved, "peak": peak, "unit": "Top/s (FP32 FMA-pipe operations)",
+                "frac": achieved / peak,
+                "traffic": None if prof is None or prof["dram_bytes_per_term"] is None
+                else prof["dram_bytes_per_term"] * terms / synth_launches,
+                "traffic_unit": "bytes per launch (ncu dram read + write, scaled per echo term)",
+                "ops_per_term": OPS_PER_TERM, "launch_ms": synth_avg_ms,
+                "ncu_fma_pipe_active": None if prof is None else prof["fma_pipe_active"],
+                "peak_basis": peak_basis}
 
-    # plain FP64 path on the same frame (fewer steps: it is the reference path)
-    adc64 = torch.empty((O, N, M), dtype=torch.complex128, device=dev)
-    if args.fp64_steps > 0:
-        sim.simulate(pkg.PATH_FP64, out=adc64)
-        sim.sync()
-    f64_ms, f64_syn = [], []
-    for _ in range(args.fp64_steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        sim.simulate(pkg.PATH_FP64, out=adc64)
-        sim.rdm(adc64, rdm)
-        e1.record(stream)
-        tm64 = pkg.bart_get_timing(sim.ctx)
-        e1.synchronize()
-        f64_ms.append(e0.elapsed_time(e1))
-        f64_syn.append(tm64["synthesis_ms"])
-    del adc64
-    fp64 = None
-    if f64_ms:
-        fp64 = {"value": terms * len(f64_ms) / (sum(f64_ms) / 1e3), "unit": UNIT,
-                "ms_per_step": statistics.mean(f64_ms), "synthesis_ms": statistics.mean(f64_syn)}
+    e2e = e2e_run(pkg, torch, sim, scene, pkg.PATH_MIXED, args.e2e_steps, job_terms_per_step)
+    h_adc = adc.cpu().numpy() if rank == 0 and world == 1 and not args.no_cpu_baseline else None
+    stages = {k: last_tm[k] for k in ("scene_ms", "bvh_ms", "visibility_ms", "kinematics_ms",
+                                      "synthesis_ms", "rdm_ms")}
+    sim.close()
+    del adc, rdm, flush
+    torch.cuda.empty_cache()
 
-    # end to end through the public API with host buffers: every step uploads
-    # the mesh and the instance from pinned host memory and reads the RDM back
-    mesh = scene.meshes[0]
-    h_verts = torch.from_numpy(mesh.verts).pin_memory()
-    h_tris = torch.from_numpy(mesh.tris).pin_memory()
-    h_rho = torch.from_numpy(mesh.rho).pin_memory()
-    h_rdm = torch.empty((M, N), dtype=torch.float32).pin_memory()
-    insts = pkg.make_instances(scene.instances)
-    L = pkg.load_library()
-    import ctypes
-    mid = ctypes.c_int32()
-    h2d = (h_verts.numel() * 8 + h_tris.numel() * 4 + h_rho.numel() * 4 +
-           ctypes.sizeof(insts) + ctypes.sizeof(pkg.bart_radar))
-    d2h = M * N * 4
-    radar_c = pkg.make_radar(r)
-
-    def e2e_step():
-        pkg._check(L.bart_mesh_clear(sim.ctx))
-        pkg._check(L.bart_mesh_upload(sim.ctx, h_verts.data_ptr(), mesh.verts.shape[0],
-                                      h_tris.data_ptr(), mesh.tris.shape[0], h_rho.data_ptr(),
-                                      ctypes.byref(mid)))
-        pkg._check(L.bart_scene_set(sim.ctx, ctypes.cast(insts, ctypes.c_void_p), len(insts)))
-        pkg._check(L.bart_radar_set(sim.ctx, ctypes.byref(radar_c)))
-        pkg._check(L.bart_frame_host(sim.ctx, 0.0, pkg.PATH_MIXED, h_rdm.data_ptr(), None))
-
-    for _ in range(2):
-        e2e_step()
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize(dev)
-    t = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        e2e_step()
-    torch.cuda.synchronize(dev)
-    e2e_s = sharding.reduce_scalar(time.perf_counter() - t, "max")
-    e2e = {"value": job_terms_per_step * args.e2e_steps / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-           "ms_per_step": 1e3 * e2e_s / args.e2e_steps}
-
-    det = detect_timing(pkg, torch, sim, adc, stream)
+    cpu = None
+    if h_adc is not None:
+        cpu = cpu_baseline(scene, args.cpu_seconds, h_adc)
+        del h_adc
+    sedan = None
+    if world == 1 and not args.no_sedan and args.workload == "intersection":
+        sedan = sedan_lines(pkg, sg, torch, dev, args, peaks)
     adj = None
     if world == 1 and args.adjoint_reps > 0:
         adj = adjoint_timing(pkg, sg, torch, dev, args.adjoint_reps)
-    inter = None
-    if world == 1 and not args.no_intersection:
-        inter = intersection_frame(pkg, sg, torch, dev)
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(scene, args.cpu_seconds)
     batch = batch_small = None
     if world == 1 and args.batch_scenes > 0:
         batch = dataset_batch(pkg, sg, torch, dev, args.batch_scenes, args.batch_size)
@@ -604,44 +714,35 @@ def main():
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "path": "mixed (FP64 phase, FP32 phasors, Kahan)",
-                   "adc": "complex64", "rdm": "256x128 fp32", "facets": st["n_facets"],
-                   "echo_terms_per_frame": terms, "l2": "flushed between steps (256 MB write)",
-                   "parallelism": f"replicas x{world}", "seed": 2,
-                   "synthesis_layout": (None if tune is None else
-                                        {"samples_per_lane": tune["best"][0],
-                                         "tiles_per_item": tune["best"][1],
-                                         "source": tune.get("source", "bart_autotune")})},
+        "config": {"workload": workload, "path": "mixed (FP64 phase, FP32 phasors, Kahan)",
+                   "adc": "complex64", "rdm": f"{M}x{N} fp32", "facets": st["n_facets"],
+                   "echo_terms_per_frame": terms,
+                   "l2": "working set larger than L2 (facet records, kinematics rows, ADC "
+                         "cube); also flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{world}", "seed": seed,
+                   "synthesis_layout": layout},
         "frames_per_s": frames,
-        "fp64_path": fp64,
-        "stages_ms_last_step": {k: last_tm[k] for k in
-                                ("scene_ms", "bvh_ms", "visibility_ms", "kinematics_ms",
-                                 "synthesis_ms", "rdm_ms")},
-        "roofline": {"bound": "alu",
-                     "kernel": "synth_mixed_kernel<%d, %d>" % (
-                         (16, 16) if tune is None or tune["best"][0] == 16 else (8, 32)),
-                     "achieved": achieved, "peak": FP32_PIPE_PEAK_TOPS,
-                     "unit": "Top/s (FP32 FMA-pipe operations)",
-                     "frac": achieved / FP32_PIPE_PEAK_TOPS,
-                     "traffic": synth_traffic(16 if tune is None else tune["best"][0]),
-                     "traffic_unit": "bytes per launch (ncu dram read + write)",
-                     "ops_per_term": OPS_PER_TERM,
-                     "launch_ms": synth_avg_ms,
-                     "peak_basis": "FP32 FMA pipe: 152 SM x 128 lanes x 2070 MHz, one "
-                                   "operation per lane and clock"},
+        "stages_ms_last_step": stages,
+        "roofline": roofline,
         "clocks": clk,
         "e2e": e2e,
-        "gpu_launches": launches,
+        "gpu_launches": tf["launches"],
         "cpu_baseline": cpu,
-        "point_cloud": det,
-        "intersection_frame": inter,
+        "peaks": peaks,
+        "grazing_pairs": st["n_grazing"],
+        "moving_sedan": sedan,
         "differentiable_echo": adj,
         "dataset_batch": batch,
         "dataset_batch_small": batch_small,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
-    sim.close()
+        if args.log:
+            rec = dict(out)
+            rec["run"] = {"time": time.time(), "argv": sys.argv[1:], "seed": seed,
+                          "host_cores": os.cpu_count()}
+            with open(args.log, "a") as fh:
+                fh.write(json.dumps(rec) + "\n")
     if world > 1:
         torch.distributed.destroy_process_group()
 

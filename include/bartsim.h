@@ -335,13 +335,17 @@ int bart_rdm_adjoint(bart_ctx *ctx, const void *adc, int32_t dtype, const float 
  * process exits; cubes needing more (O*N*M > 1398101 complex64 or 699050
  * complex128 samples: 12 bytes, resp. 24, per sample) are rejected with
  * BART_EINVAL.  M and N must be of the form 2^a 3^b (M in [32, 1024], N in
- * [2, 1024]).  The first call on a device looks the array's address up
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  The array is shared by every call and keeps
- * the last call's contents (each call overwrites the part it reads before
- * reading it, so nothing carries over); calls that overlap on the GPU,
- * from any thread or stream, race on it and must be serialised by the
- * caller.  The call calls no cudaMalloc/cudaFree.
+ * [2, 1024]).  Every call looks the array's address up
+ * (cudaGetSymbolAddress, which allocates nothing) with the current device,
+ * which must be the device of adc and rdm.  Under CUDA's default lazy
+ * module loading the array is reserved when this file's module first loads
+ * on a device -- the first RDM call or symbol lookup there -- so a process
+ * under a hard memory cap should make one warm-up call at initialisation,
+ * before it fills the device and before any stream capture.  The array is
+ * shared by every call and keeps the last call's contents (each call
+ * overwrites the part it reads before reading it, so nothing carries over);
+ * calls that overlap on the GPU, from any thread or stream, race on it and
+ * must be serialised by the caller.  The call calls no cudaMalloc/cudaFree.
  * Errors: EINVAL, ECUDA. */
 int bart_form_rdm_static(const void *adc, int32_t dtype, int32_t O, int32_t N,
                          int32_t M, int32_t window, float *rdm, void *stream);
@@ -423,6 +427,24 @@ int bart_get_timing(bart_ctx *ctx, bart_timing *out);
 /* Wait for the context's stream; return a latched device-side error
  * (BART_EDEVICE) or a CUDA error, else BART_OK. */
 int bart_sync(bart_ctx *ctx);
+
+/* Measured arithmetic-pipe rates of the device (the denominators of the
+ * echo-synthesis roofline).  Register-only kernels, eight independent
+ * dependency chains per thread, 2048 threads per SM, CUDA-event timed, best
+ * of `reps` runs after one warm-up; at whatever clocks the device runs. */
+typedef struct bart_peaks {
+    double fp32_fma_per_s;     /* scalar FP32 FMAs/s (one FMA-pipe operation each) */
+    double fp32x2_fma_per_s;   /* FP32 FMAs/s issued as packed fma.rn.f32x2 (two per instruction) */
+    double sincos_per_s;       /* __sincosf pairs/s (MUFU sine + cosine) */
+    double fp64_fma_per_s;     /* FP64 FMAs/s */
+    int32_t sms;               /* streaming multiprocessors of the device */
+    int32_t threads;           /* threads of each launch */
+} bart_peaks;
+
+/* Run the peak microbenchmarks on CUDA device `device` (made current),
+ * reps in [1, 100].  Allocates and frees a small device buffer; blocks.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int bart_measure_peaks(int32_t device, int32_t reps, bart_peaks *out);
 
 #ifdef __cplusplus
 }

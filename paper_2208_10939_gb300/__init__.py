@@ -37,7 +37,7 @@ EXPORTED = ["bart_last_error", "bart_version", "bart_create", "bart_destroy",
             "bart_scene_partition", "bart_set_graph", "bart_set_synth_layout",
             "bart_autotune", "bart_rdm_adjoint", "bart_simulate_adjoint",
             "bart_simulate_adjoint_mixed",
-            "bart_mesh_update"]
+            "bart_mesh_update", "bart_measure_peaks"]
 
 
 class BartError(RuntimeError):
@@ -106,6 +106,12 @@ assert POINT_DTYPE.itemsize == ctypes.sizeof(bart_point) == 56
 TUNE_MAX = 16
 
 
+class bart_peaks(ctypes.Structure):
+    _fields_ = [("fp32_fma_per_s", ctypes.c_double), ("fp32x2_fma_per_s", ctypes.c_double),
+                ("sincos_per_s", ctypes.c_double), ("fp64_fma_per_s", ctypes.c_double),
+                ("sms", ctypes.c_int32), ("threads", ctypes.c_int32)]
+
+
 class bart_tune(ctypes.Structure):
     _fields_ = [("n_trials", ctypes.c_int32), ("best_samples_per_lane", ctypes.c_int32),
                 ("best_tiles_per_item", ctypes.c_int32), ("best_ms", ctypes.c_float),
@@ -171,6 +177,7 @@ def load_library() -> ctypes.CDLL:
         L.bart_autotune.argtypes = [P, D, P, I32, I32, ctypes.POINTER(bart_tune)]
         L.bart_detect.argtypes = [P, P, I32, ctypes.POINTER(bart_detect_cfg), P, P, I32,
                                   ctypes.POINTER(I32)]
+        L.bart_measure_peaks.argtypes = [I32, I32, ctypes.POINTER(bart_peaks)]
         for name in EXPORTED:
             if name not in ("bart_last_error", "bart_version", "bart_destroy"):
                 getattr(L, name).restype = ctypes.c_int
@@ -386,13 +393,41 @@ def bart_form_rdm_static(adc, rdm, O: int, N: int, M: int, window: int = WINDOW_
                          stream: Optional[int] = None) -> None:
     """RDM of ``adc`` into ``rdm`` without any device allocation by the
     library (its workspace is a fixed array compiled into it); see
-    ``include/bartsim.h`` for the size limit and the sharing rules."""
+    ``include/bartsim.h`` for the size limit and the sharing rules.
+
+    ``adc`` ([O][N][M] complex64/complex128) and ``rdm`` ([M][N] float32)
+    must be contiguous CUDA tensors on one device; the call runs with that
+    device current (the C entry point takes the workspace and the launch
+    device from the current device)."""
     import torch
-    if stream is None:
-        stream = torch.cuda.current_stream(adc.device).cuda_stream
-    _check(load_library().bart_form_rdm_static(
-        ctypes.c_void_p(_ptr(adc)), _dtype_code(adc), int(O), int(N), int(M), int(window),
-        ctypes.c_void_p(_ptr(rdm)), ctypes.c_void_p(int(stream))))
+    O, N, M = int(O), int(N), int(M)
+    if not (isinstance(adc, torch.Tensor) and isinstance(rdm, torch.Tensor)):
+        raise TypeError("adc and rdm must be torch tensors")
+    if not (adc.is_cuda and rdm.is_cuda and adc.is_contiguous() and rdm.is_contiguous()):
+        raise ValueError("adc and rdm must be contiguous CUDA tensors")
+    if adc.device != rdm.device:
+        raise ValueError(f"adc is on {adc.device}, rdm on {rdm.device}")
+    if rdm.dtype != torch.float32:
+        raise TypeError(f"rdm must be float32, got {rdm.dtype}")
+    code = _dtype_code(adc)
+    if min(O, N, M) < 1 or adc.numel() != O * N * M:
+        raise ValueError(f"adc has {adc.numel()} samples, O*N*M = {O * N * M}")
+    if rdm.numel() != M * N:
+        raise ValueError(f"rdm has {rdm.numel()} cells, M*N = {M * N}")
+    with torch.cuda.device(adc.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(adc.device).cuda_stream
+        _check(load_library().bart_form_rdm_static(
+            ctypes.c_void_p(_ptr(adc)), code, O, N, M, int(window),
+            ctypes.c_void_p(_ptr(rdm)), ctypes.c_void_p(int(stream))))
+
+
+def bart_measure_peaks(device: int = 0, reps: int = 5) -> dict:
+    """Measured FP32 FMA (scalar and packed), MUFU sincos and FP64 FMA rates
+    of the device (register-only microbenchmarks, CUDA-event timed)."""
+    out = bart_peaks()
+    _check(load_library().bart_measure_peaks(int(device), int(reps), ctypes.byref(out)))
+    return {k: getattr(out, k) for k, _ in bart_peaks._fields_}
 
 
 def bart_get_visibility(ctx: int, state) -> None:

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libbartsim.so")
 SOURCES = ["capi.cu", "scene_bvh.cu", "visibility.cu", "synth.cu", "rdm.cu", "noise.cu", "detect.cu",
-           "adjoint.cu"]
+           "adjoint.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

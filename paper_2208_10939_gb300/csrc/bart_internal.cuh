@@ -256,10 +256,13 @@ void detect_carve(void *ws, const RadarDev &rd, int dtype, int bins, DetectBufs 
 int launch_detect(const void *adc, int dtype, const RadarDev &rd, const DetectDev &dd,
                   const DetectBufs &b, bart_point *points, int max_points, cudaStream_t s);
 
+// Record `msg` as the calling thread's bart_last_error text; returns code.
+int set_last_error(int code, const char *msg);
+
 // Size of the static workspace used by bart_form_rdm_static (16 MiB).
 constexpr int64_t kRdmStaticWorkspaceBytes = 16ll << 20;
-// Device address of that workspace on the current device (looked up on the
-// first call per device).  Returns BART_OK or BART_ECUDA with *err set.
+// Device address of that workspace on the current device (looked up on
+// every call).  Returns BART_OK or BART_ECUDA with *err set.
 int rdm_static_workspace(void **ws, const char **err);
 
 }  // namespace bart

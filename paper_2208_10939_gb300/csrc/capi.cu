@@ -76,6 +76,10 @@ struct MeshStore {
 
 }  // namespace
 
+namespace bart {
+int set_last_error(int code, const char *msg) { return fail(code, "%s", msg); }
+}  // namespace bart
+
 struct bart_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;

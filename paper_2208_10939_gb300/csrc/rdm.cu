@@ -12,7 +12,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <mutex>
 
 #include "bart_internal.cuh"
 
@@ -403,34 +402,22 @@ void launch_rdm(const void *adc, int dtype, const RadarDev &rd, int groups, void
 // Fixed workspace for bart_form_rdm_static: a statically sized device array
 // that exists on every GPU that loads this library, for as long as the
 // process lives.  Host code may not use its name as an address; the device
-// address is looked up once per device with cudaGetSymbolAddress.
+// address is looked up with cudaGetSymbolAddress on every call, with the
+// target device current (the lookup allocates nothing, and a fresh lookup
+// stays valid after cudaDeviceReset or under another context).
 // -------------------------------------------------------------------------
 static __device__ __align__(256) unsigned char g_rdm_static_ws[kRdmStaticWorkspaceBytes];
 
-constexpr int kMaxDevices = 64;
-
 int rdm_static_workspace(void **ws, const char **err)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_rdm_static_ws);
+    if (e != cudaSuccess || !p) {
         cudaGetLastError();
-        *err = "no usable current CUDA device";
+        *err = "cudaGetSymbolAddress of the static RDM workspace failed";
         return BART_ECUDA;
     }
-    static std::mutex mu;
-    static void *addr[kMaxDevices] = {nullptr};
-    std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_rdm_static_ws);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            *err = "cudaGetSymbolAddress of the static RDM workspace failed";
-            return BART_ECUDA;
-        }
-        addr[dev] = p;
-    }
-    *ws = addr[dev];
+    *ws = p;
     return BART_OK;
 }
 

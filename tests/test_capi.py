@@ -41,27 +41,30 @@ def test_library_exports_every_declared_symbol(lib):
         assert getattr(lib, name) is not None
 
 
+MIRRORS = ["bart_instance", "bart_radar", "bart_stats", "bart_timing", "bart_detect_cfg",
+           "bart_point", "bart_tune", "bart_peaks"]
+
+
 def test_struct_layouts_match_c(tmp_path):
+    """sizeof of every mirrored struct and the offset of every field agree
+    between C (gcc on the header) and the ctypes mirrors."""
+    lines, expect = [], []
+    for name in MIRRORS:
+        cls = getattr(pkg, name)
+        lines.append(f'printf("%zu\\n", sizeof({name}));')
+        expect.append(ctypes.sizeof(cls))
+        for field, _ in cls._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({name}, {field}));')
+            expect.append(getattr(cls, field).offset)
     prog = tmp_path / "sz.c"
-    prog.write_text(
-        '#include <stdio.h>\n#include <stddef.h>\n#include "bartsim.h"\n'
-        'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
-        ' sizeof(bart_instance), sizeof(bart_radar), sizeof(bart_stats),'
-        ' offsetof(bart_radar, tx), offsetof(bart_instance, pos), sizeof(bart_timing),'
-        ' offsetof(bart_timing, detect_ms), sizeof(bart_detect_cfg), sizeof(bart_point),'
-        ' offsetof(bart_point, r_bin), sizeof(bart_tune), offsetof(bart_tune, synthesis_ms));'
-        'return 0;}\n')
+    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "bartsim.h"\n'
+                    "int main(void){" + "".join(lines) + "return 0;}\n")
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)],
                    check=True)
     vals = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True,
                                         check=True).stdout.split()))
-    assert vals == [ctypes.sizeof(pkg.bart_instance), ctypes.sizeof(pkg.bart_radar),
-                    ctypes.sizeof(pkg.bart_stats), pkg.bart_radar.tx.offset,
-                    pkg.bart_instance.pos.offset, ctypes.sizeof(pkg.bart_timing),
-                    pkg.bart_timing.detect_ms.offset, ctypes.sizeof(pkg.bart_detect_cfg),
-                    ctypes.sizeof(pkg.bart_point), pkg.bart_point.r_bin.offset,
-                    ctypes.sizeof(pkg.bart_tune), pkg.bart_tune.synthesis_ms.offset]
+    assert vals == expect
 
 
 def test_version_and_error_string(lib):

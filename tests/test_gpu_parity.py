@@ -331,83 +331,6 @@ def test_invalid_configs_raise(sim):
         pkg.bart_destroy(ctx)
 
 
-@pytest.fixture(scope="module")
-def config2():
-    sc = sg.car_scene()
-    return sc, oracle.Frame(sc)
-
-
-def test_config2_full_size_sampled(sim, config2):
-    """The 20k-triangle moving sedan, 12 channels, 128 x 256, in the launch
-    configuration bench.py times (mixed, complex64): visibility bit-exact
-    over the whole frame, ADC entries sampled and summed by the oracle."""
-    sc, fr = config2
-    sim.load_scene(sc)
-    adc, st = sim.simulate(pkg.PATH_MIXED, stats=True)
-    assert np.array_equal(sim.visibility().cpu().numpy(), fr.state)
-    assert st["n_terms"] == fr.n_terms()
-    rng = np.random.default_rng(2)
-    r = sc.radar
-    E = 192
-    ent = np.stack([rng.integers(0, r.O, E), rng.integers(0, r.N, E), rng.integers(0, r.M, E)], 1)
-    ent[:12, 1] = r.N - 1
-    ent[12:24, 2] = r.M - 1                                      # last chirp / sample
-    ref = fr.adc_entries(ent)
-    got = adc.cpu().numpy()[ent[:, 0], ent[:, 1], ent[:, 2]]
-    err_m = rel_l2(got, ref)
-    a64 = sim.simulate(pkg.PATH_FP64).cpu().numpy()[ent[:, 0], ent[:, 1], ent[:, 2]]
-    err_d = rel_l2(a64, ref)
-    print(f"config2 sampled: mixed {err_m:.3e} fp64 {err_d:.3e} terms {st['n_terms']}")
-    assert err_m <= TOL_MIXED and err_d <= TOL_FP64
-
-
-def test_config2_doppler_and_range_bins(sim, config2):
-    """Eq. 4 / Eq. 5 on the full sedan frame: the strongest RDM cell lies
-    within a few bins of the range of the car's nearest face and at the
-    Doppler of 10 m/s approaching (-39.6 bins from zero)."""
-    sc, fr = config2
-    sim.load_scene(sc)
-    rdm = sim.rdm(sim.simulate(pkg.PATH_MIXED)).cpu().numpy()
-    r, d = np.unravel_index(np.argmax(rdm), rdm.shape)
-    prof = sg.radar_profile(sc.radar.M)
-    d_exp = sc.radar.N // 2 - 2 * 10.0 * sc.radar.Tc * sc.radar.N / prof["lam_c"]
-    assert abs(d - d_exp) <= 2.0, (d, d_exp)
-    rb = 2 * 30.0 * sc.radar.slope / sg.C0 / sc.radar.fs * sc.radar.M
-    assert abs(r - rb) <= 16, (r, rb)
-
-
-def test_config3_intersection_precision_study(sim):
-    """The full intersection (12 vehicles of 20k-200k triangles + 50k-triangle
-    ground, 192 channels, 512 samples) on a 2-chirp frame: visibility
-    bit-exact against the oracle's BVH over all antenna-facet pairs; the
-    mixed cube against the FP64 GPU cube (<= 1e-4) and both against
-    oracle-sampled entries."""
-    sc = sg.intersection_scene(N=2)
-    fr = oracle.Frame(sc)
-    sim.load_scene(sc)
-    adc_m, st = sim.simulate(pkg.PATH_MIXED, stats=True)
-    gpu_state = sim.visibility().cpu().numpy()
-    diff = int((gpu_state != fr.state).sum())
-    assert diff == 0, f"{diff} of {gpu_state.size} states differ"
-    assert st["n_terms"] == fr.n_terms()
-    a_m = adc_m.cpu().numpy()
-    del adc_m
-    a_d = sim.simulate(pkg.PATH_FP64).cpu().numpy()
-    err_md = rel_l2(a_m, a_d)
-    rng = np.random.default_rng(3)
-    r = sc.radar
-    E = 96
-    ent = np.stack([rng.integers(0, r.O, E), rng.integers(0, r.N, E), rng.integers(0, r.M, E)], 1)
-    ref = fr.adc_entries(ent)
-    err_mo = rel_l2(a_m[ent[:, 0], ent[:, 1], ent[:, 2]], ref)
-    err_do = rel_l2(a_d[ent[:, 0], ent[:, 1], ent[:, 2]], ref)
-    print(f"config3: facets {st['n_facets']} terms {st['n_terms']} records v/s/e "
-          f"{st['n_vertex']}/{st['n_series']}/{st['n_edge']}; mixed vs fp64 {err_md:.3e}, "
-          f"mixed vs oracle {err_mo:.3e}, fp64 vs oracle {err_do:.3e}")
-    assert err_do <= TOL_FP64
-    assert err_md <= TOL_MIXED and err_mo <= TOL_MIXED
-
-
 @pytest.mark.parametrize("path,tol", [(pkg.PATH_FP64, 1e-9), (pkg.PATH_MIXED, 1e-4)])
 def test_additive_noise_matches_oracle(sim, path, tol):
     """Same Philox stream and Box-Muller map on both sides; the noise scale
