@@ -99,9 +99,14 @@ def parse():
     ap.add_argument("--sedan-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dataset-scenes", type=int, default=4096,
+                    help="seeded dataset scenes (1-8 vehicles, 5k-200k facets) simulated by the "
+                         "batched dataset runner; 0 skips the line")
+    ap.add_argument("--dataset-per-scene", type=int, default=256,
+                    help="of those, how many are also simulated one per call (per-scene launches)")
     ap.add_argument("--batch-scenes", type=int, default=32,
-                    help="dataset scenes (seeded, 1-8 vehicles, 5k-200k facets) for the "
-                         "batched-vs-per-scene measurement; 0 skips it")
+                    help="small dataset scenes (5k-10k facets) for the batched / graph / "
+                         "autotuner comparison (2x this many); 0 skips it")
     ap.add_argument("--batch-size", type=int, default=8)
     ap.add_argument("--adjoint-reps", type=int, default=1,
                     help="timed runs of the perturbed-sedan gradient (0 skips)")
@@ -115,6 +120,12 @@ def parse():
     ap.add_argument("--no-sedan", action="store_true", help="skip the moving-sedan lines")
     ap.add_argument("--no-peaks", action="store_true",
                     help="skip the peak microbenchmarks (roofline against no measured peak)")
+    ap.add_argument("--chirps", type=int, default=0,
+                    help="profiling aid: headline frame with this many chirps (0: the workload's)")
+    ap.add_argument("--array", default=None, metavar="PxQ",
+                    help="profiling aid: headline frame with the first P TX and Q RX")
+    ap.add_argument("--no-flush", action="store_true",
+                    help="profiling aid: no L2 flush between steps (per-kernel DRAM counters)")
     ap.add_argument("--log", default=os.environ.get("BART_RUN_LOG"),
                     help="append the run's record (JSON line plus seeds, clocks, oracle errors, "
                          "grazing counts) to this JSONL file")
@@ -181,9 +192,7 @@ class Clocks:
 
 
 def _lit_per_channel(fr, r):
-    import oracle
-    lit = fr.state == oracle.LIT
-    return (lit[:r.P, None, :] & lit[None, r.P:, :]).sum(axis=2).reshape(-1)
+    return fr.lit_pairs().sum(axis=1)
 
 
 def _sample_entries(rng, r, E):
@@ -286,7 +295,8 @@ def dataset_batch(pkg, sg, torch, dev, K: int, bsz: int, tri_min: int = 5_000,
     pkg.bart_mesh_clear(sim.ctx)
     placed = []
     for sc in scenes:
-        ids = [pkg.bart_mesh_upload(sim.ctx, m.verts, m.tris, m.rho) for m in sc.meshes]
+        ids = [pkg.bart_mesh_upload(sim.ctx, m.verts, m.tris, m.rho, m.two_sided)
+               for m in sc.meshes]
         placed.append([pkg._Placed(ids[i.mesh_id], i) for i in sc.instances])
     radar = scenes[0].radar
     pkg.bart_radar_set(sim.ctx, radar)
@@ -373,6 +383,58 @@ def dataset_batch(pkg, sg, torch, dev, K: int, bsz: int, tri_min: int = 5_000,
         "sequence_4_frames": {"direct": len(g0) * len(seq) / direct_s,
                               "graph": len(g0) * len(seq) / graph_s},
     }
+
+
+def dataset_run(pkg, sg, torch, dev, K: int, K_single: int, n_check: int = 8) -> dict:
+    """Config 4: K seeded dataset scenes through the batched dataset runner
+    (batches cut by a 40M-facet budget, scenes generated ahead in spawned
+    worker processes, RDM shards and a resume manifest written to a
+    temporary directory): scene-frames/s of the device (frame + RDM per
+    batch, CUDA events) and of the whole run; the first K_single scenes
+    again one scene per call (per-scene launches); n_check scenes kept as ADC
+    cubes and checked against the oracle on sampled entries."""
+    import shutil
+    from paper_2208_10939_gb300 import dataset
+    import oracle
+    keep = [int(i) for i in np.linspace(0, K - 1, n_check).round()] if n_check else []
+    out = tempfile.mkdtemp(prefix="bart_dataset_")
+    gsim = dataset.GpuBatchSimulator(dev.index or 0)
+    try:
+        workers = max(0, min(15, (os.cpu_count() or 2) - 1))
+        st = dataset.run_dataset(out, K, sg.batch_scene, gsim, max_facets=40_000_000,
+                                 workers=workers, keep_adc=keep)
+        idx, _ = dataset.load_dataset(out)
+        assert len(idx) == K
+        shutil.rmtree(out, ignore_errors=True)
+        out1 = tempfile.mkdtemp(prefix="bart_dataset1_")
+        st1 = dataset.run_dataset(out1, K_single, sg.batch_scene, gsim, max_scenes=1,
+                                  workers=workers)
+        shutil.rmtree(out1, ignore_errors=True)
+    finally:
+        gsim.close()
+    worst, checked = 0.0, 0
+    r = sg.batch_scene(0).radar
+    for i in keep:
+        fr = oracle.Frame(sg.batch_scene(i))
+        rng = np.random.default_rng(4000 + i)
+        e = _sample_entries(rng, r, 32)
+        ref = fr.adc_entries(e)
+        got = st["adc"][i][e[:, 0], e[:, 1], e[:, 2]].astype(np.complex128)
+        worst = max(worst, float(np.linalg.norm(got - ref) / np.linalg.norm(ref)))
+        checked += len(e)
+    return {"workload": f"{K} seeded dataset scenes (1-8 vehicles, 5k-200k facets, "
+                        f"mean {st['facets'] // max(1, st['scenes'])}), 3TXx4RX, 128 x 256, "
+                        "mixed path + RDM, RDM shards + resume manifest",
+            "unit": "scene-frames/s",
+            "batched": {"value": st["scenes"] / st["device_s"], "device_s": st["device_s"],
+                        "wall_value": st["scenes"] / st["wall_s"], "wall_s": st["wall_s"],
+                        "batches": st["batches"], "facets": st["facets"],
+                        "scene_workers": workers},
+            "per_scene_launches": {"scenes": st1["scenes"],
+                                   "value": st1["scenes"] / st1["device_s"],
+                                   "device_s": st1["device_s"],
+                                   "wall_value": st1["scenes"] / st1["wall_s"]},
+            "oracle_check": {"scenes": keep, "entries": checked, "worst_rel_l2": worst}}
 
 
 def detect_timing(pkg, torch, sim, adc, stream, reps: int = 10) -> dict:
@@ -468,12 +530,13 @@ def measure_peaks(pkg, dev_index: int) -> dict:
 
 
 def timed_frames(pkg, torch, sim, adc, rdm, flush, stream, steps: int, path: int) -> dict:
-    """``steps`` frames (simulate + RDM), L2 flushed before each; per-step
-    device times (CUDA events on the launching stream) and the library's
-    per-stage times."""
+    """``steps`` frames (simulate + RDM), L2 flushed before each (unless
+    ``flush`` is None); per-step device times (CUDA events on the launching
+    stream) and the library's per-stage times."""
     step_ms, synth_ms, launches, tm = [], [], 0, None
     for _ in range(steps):
-        flush.zero_()
+        if flush is not None:
+            flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -498,19 +561,20 @@ def e2e_run(pkg, torch, sim, scene, path: int, steps: int, job_terms_per_step: f
     L = pkg.load_library()
     r = scene.radar
     hm = [(torch.from_numpy(m.verts).pin_memory(), torch.from_numpy(m.tris).pin_memory(),
-           torch.from_numpy(m.rho).pin_memory()) for m in scene.meshes]
+           torch.from_numpy(m.rho).pin_memory(), pkg.MESH_TWO_SIDED if m.two_sided else 0)
+          for m in scene.meshes]
     h_rdm = torch.empty((r.M, r.N), dtype=torch.float32).pin_memory()
     insts = pkg.make_instances(scene.instances)
     radar_c = pkg.make_radar(r)
     mid = ctypes.c_int32()
-    h2d = sum(v.numel() * 8 + t.numel() * 4 + p.numel() * 4 for v, t, p in hm)
+    h2d = sum(v.numel() * 8 + t.numel() * 4 + p.numel() * 4 for v, t, p, _ in hm)
     h2d += ctypes.sizeof(insts) + ctypes.sizeof(pkg.bart_radar)
 
     def step():
         pkg._check(L.bart_mesh_clear(sim.ctx))
-        for v, t, p in hm:
+        for v, t, p, fl in hm:
             pkg._check(L.bart_mesh_upload(sim.ctx, v.data_ptr(), v.shape[0], t.data_ptr(),
-                                          t.shape[0], p.data_ptr(), ctypes.byref(mid)))
+                                          t.shape[0], p.data_ptr(), fl, ctypes.byref(mid)))
         pkg._check(L.bart_scene_set(sim.ctx, ctypes.cast(insts, ctypes.c_void_p), len(insts)))
         pkg._check(L.bart_radar_set(sim.ctx, ctypes.byref(radar_c)))
         pkg._check(L.bart_frame_host(sim.ctx, float(scene.t0), path, h_rdm.data_ptr(), None))
@@ -539,7 +603,8 @@ def sedan_lines(pkg, sg, torch, dev, args, peaks) -> dict:
         r = scene.radar
         adc = torch.empty((r.O, r.N, r.M), dtype=torch.complex64, device=dev)
         rdm = torch.empty((r.M, r.N), dtype=torch.float32, device=dev)
-        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        flush = (None if args.no_flush else
+                 torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev))
         stream = torch.cuda.current_stream(dev)
         pkg.bart_set_timing(sim.ctx, True)
         _, st = sim.simulate(pkg.PATH_MIXED, out=adc, stats=True)
@@ -619,13 +684,22 @@ def main():
         seed = 2 + rank
         scene = sg.car_scene(seed=seed)
         workload = SEDAN
+    if args.chirps or args.array:
+        r0 = scene.radar
+        P_, Q_ = ((int(x) for x in args.array.lower().split("x")) if args.array
+                  else (r0.P, r0.Q))
+        scene.radar = sg.Radar(f0=r0.f0, slope=r0.slope, fs=r0.fs, Tc=r0.Tc, M=r0.M,
+                               N=args.chirps or r0.N, tx=r0.tx[:P_], rx=r0.rx[:Q_],
+                               intra_chirp_motion=r0.intra_chirp_motion)
+        workload += f" (profiling cut: {P_}TXx{Q_}RX, {scene.radar.N} chirps)"
     sim = pkg.Simulator(local)
     sim.load_scene(scene)
     r = scene.radar
     O, N, M = r.O, r.N, r.M
     adc = torch.empty((O, N, M), dtype=torch.complex64, device=dev)
     rdm = torch.empty((M, N), dtype=torch.float32, device=dev)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    flush = (None if args.no_flush else
+             torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev))
     pkg.bart_set_timing(sim.ctx, True)
     _, st = sim.simulate(pkg.PATH_MIXED, out=adc, stats=True)
     terms = st["n_terms"]
@@ -703,8 +777,10 @@ def main():
     if world == 1 and args.adjoint_reps > 0:
         adj = adjoint_timing(pkg, sg, torch, dev, args.adjoint_reps)
     batch = batch_small = None
+    if world == 1 and args.dataset_scenes > 0:
+        batch = dataset_run(pkg, sg, torch, dev, args.dataset_scenes,
+                            min(args.dataset_per_scene, args.dataset_scenes))
     if world == 1 and args.batch_scenes > 0:
-        batch = dataset_batch(pkg, sg, torch, dev, args.batch_scenes, args.batch_size)
         # small scenes, where per-scene launches leave the GPU under-filled
         batch_small = dataset_batch(pkg, sg, torch, dev, 2 * args.batch_scenes,
                                     2 * args.batch_size, 5_000, 10_000)
@@ -718,7 +794,8 @@ def main():
                    "adc": "complex64", "rdm": f"{M}x{N} fp32", "facets": st["n_facets"],
                    "echo_terms_per_frame": terms,
                    "l2": "working set larger than L2 (facet records, kinematics rows, ADC "
-                         "cube); also flushed between steps (256 MB write)",
+                         "cube)" + ("" if args.no_flush else
+                                    "; also flushed between steps (256 MB write)"),
                    "parallelism": f"replicas x{world}", "seed": seed,
                    "synthesis_layout": layout},
         "frames_per_s": frames,
@@ -732,7 +809,7 @@ def main():
         "grazing_pairs": st["n_grazing"],
         "moving_sedan": sedan,
         "differentiable_echo": adj,
-        "dataset_batch": batch,
+        "dataset": batch,
         "dataset_batch_small": batch_small,
     }
     if rank == 0:

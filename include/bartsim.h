@@ -60,6 +60,12 @@ extern "C" {
 #define BART_VIS_LIT   1     /* front facing and unoccluded */
 #define BART_VIS_GRAZE 2     /* within the grazing margins: excluded, counted */
 #define BART_VIS_OCCL  3     /* centroid->antenna segment hits another facet */
+#define BART_VIS_LIT_REV 4   /* two-sided facet lit on its reverse side, unoccluded */
+
+/* mesh flags (bart_mesh_upload) */
+#define BART_MESH_TWO_SIDED 1u   /* facets scatter from both sides (open surfaces:
+                                    plates, signs); a channel sees such a facet when
+                                    its TX and RX light the same side */
 
 #define BART_MAX_TX 16
 #define BART_MAX_RX 16
@@ -85,8 +91,10 @@ typedef struct bart_instance {
  * transmit frequency is f0 + slope*m/fs.
  * Constraints (else BART_EINVAL): M a multiple of 32 in [32, 1024];
  * 1 <= N <= 32768; 1 <= P <= BART_MAX_TX; 1 <= Q <= BART_MAX_RX;
- * f0, slope, fs > 0; Tc >= M/fs.  bart_form_rdm and bart_detect further
- * need M and N of the form 2^a 3^b (radix-2/3 FFTs; N in [2, 1024]). */
+ * f0, slope, fs > 0; Tc >= M/fs; far_field and delay_ref not both set;
+ * grazing_eps 0 (default 1e-6) or in (0, 0.1].  bart_form_rdm and
+ * bart_detect further need M and N of the form 2^a 3^b (radix-2/3 FFTs;
+ * N in [2, 1024]). */
 typedef struct bart_radar {
     double  f0;                  /* chirp start frequency, Hz */
     double  slope;               /* mu, Hz/s */
@@ -107,6 +115,20 @@ typedef struct bart_radar {
                                     instance origin at the chirp start, plus the
                                     origin's path at t_n + t_m; residual video
                                     phase from the origin's delay */
+    int32_t far_field;           /* 0: spherical waves from every facet centroid;
+                                    1: far field (the Eq. 7 radar equation with
+                                    the PO cross-section of the whole target):
+                                    every facet of an instance is seen along the
+                                    plane waves of the instance origin r, at the
+                                    origin's ranges (directions, amplitude,
+                                    obliquity, facet integral), its path the
+                                    plane-wave one |p_tx - r(t)| + |p_rx - r(t)|
+                                    - (t + r).(c_k - r(t_n)), and its visibility
+                                    segment runs from the centroid toward
+                                    p_a + (c_k - r(t0)) */
+    int32_t reserved0;           /* must be 0 */
+    double  grazing_eps;         /* facets with |cos| below this toward an antenna
+                                    are GRAZE (excluded, counted); 0 = 1e-6 */
 } bart_radar;
 
 /* Per-frame counters (filled when a non-NULL pointer is passed; doing so
@@ -145,6 +167,14 @@ const char *bart_last_error(void);
 /* Library version string. */
 const char *bart_version(void);
 
+/* Host-side fault injection for tests of the error paths: the nth device
+ * allocation the library makes from now on (nth >= 1; counted over every
+ * context of the process) fails with BART_ENOMEM before cudaMalloc is
+ * called, exactly as an out-of-memory cudaMalloc would surface; later
+ * allocations proceed.  nth = 0 disarms it.  Nothing reaches the GPU.
+ * Errors: EINVAL (nth < 0). */
+int bart_inject_alloc_failure(int32_t nth);
+
 /* Create a context on CUDA device `device`.  *out receives the handle.
  * Errors: EINVAL (bad device / NULL out), ECUDA. */
 int bart_create(bart_ctx **out, int device);
@@ -159,12 +189,14 @@ int bart_set_stream(bart_ctx *ctx, void *stream);
 /* Upload a triangle mesh (host pointers, copied; the caller may free them
  * on return).  verts: nv x 3 float64; tris: nf x 3 int32 vertex indices,
  * counter-clockwise seen from outside (outward normal (v1-v0)x(v2-v0));
- * rho: nf float32 reflectivities or NULL for all 1.  *mesh_id receives the
- * id used by bart_instance.  Errors: EINVAL (index out of range, nf < 1),
+ * rho: nf float32 reflectivities or NULL for all 1; flags: 0 or
+ * BART_MESH_TWO_SIDED (Sec. 2.2 visibility, the PO obliquity taken on the
+ * side the antennas light).  *mesh_id receives the id used by
+ * bart_instance.  Errors: EINVAL (index out of range, nf < 1, unknown flag),
  * ENOMEM, ECUDA. */
 int bart_mesh_upload(bart_ctx *ctx, const double *verts, int64_t nv,
                      const int32_t *tris, int64_t nf, const float *rho,
-                     int32_t *mesh_id);
+                     uint32_t flags, int32_t *mesh_id);
 
 /* Replace the vertices (and, if rho is not NULL, the reflectivities) of an
  * uploaded mesh from DEVICE arrays of the uploaded sizes (nv x 3 float64,
@@ -242,6 +274,7 @@ int bart_add_noise(bart_ctx *ctx, void *adc, int32_t dtype, double snr_db, uint6
  * the distances and the delay; visibility is recomputed at t0 and held
  * fixed (it is piecewise constant in the vertices).  Instance poses,
  * velocities and rho_scale are constants.  Works with scene partitions.
+ * Not available with far_field (EINVAL).
  * Errors: ESTATE, EINVAL, ENOMEM, ECUDA. */
 int bart_simulate_adjoint(bart_ctx *ctx, double t0, const void *grad_adc, int32_t dtype,
                           double *grad_verts, double *grad_rho);
@@ -411,10 +444,12 @@ int bart_detect(bart_ctx *ctx, const void *adc, int32_t dtype, const bart_detect
 int bart_frame_host(bart_ctx *ctx, double t0, int32_t path, float *rdm_host,
                     bart_stats *stats);
 
-/* Copy the frame-start visibility states of the last simulated frame into
- * the device buffer `state` (A x F uint8, A = P + Q antennas, TX first, then
- * RX).  Errors: ESTATE (no frame simulated). */
-int bart_get_visibility(bart_ctx *ctx, uint8_t *state);
+/* Copy the frame-start visibility states (BART_VIS_*) of the last
+ * simulated frame into the device buffer `state` (A x F uint8, A = P + Q
+ * antennas, TX first, then RX), and, when n_grazing is not NULL, store the
+ * number of (antenna, facet) pairs flagged BART_VIS_GRAZE there (host
+ * pointer; synchronises the stream).  Errors: ESTATE (no frame simulated). */
+int bart_get_visibility(bart_ctx *ctx, uint8_t *state, int64_t *n_grazing);
 
 /* Enable (1) or disable (0) recording of per-stage CUDA events.  The events
  * are recorded on the context's stream; enabling adds no synchronisation. */

@@ -30,7 +30,7 @@ _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-BACK, LIT, GRAZE, OCCL = 0, 1, 2, 3
+BACK, LIT, GRAZE, OCCL, LIT_REV = 0, 1, 2, 3, 4
 EPS_FACE = 1e-6      # |cos| below which a facet is grazing its antenna
 EPS_B = 1e-9         # barycentric margin of the segment/triangle test
 EPS_T = 1e-9         # segment-parameter margin of the segment/triangle test
@@ -56,7 +56,7 @@ class _Radar(ctypes.Structure):
                 ("fs", ctypes.c_double), ("Tc", ctypes.c_double),
                 ("M", ctypes.c_int), ("N", ctypes.c_int), ("P", ctypes.c_int),
                 ("Q", ctypes.c_int), ("intra_chirp_motion", ctypes.c_int),
-                ("tdm", ctypes.c_int), ("delay_ref", ctypes.c_int), ("pad_", ctypes.c_int)]
+                ("tdm", ctypes.c_int), ("delay_ref", ctypes.c_int), ("far_field", ctypes.c_int)]
 
 
 def _load():
@@ -68,21 +68,21 @@ def _load():
             P = ctypes.c_void_p
             lib.orc_world_vertices.argtypes = [P, P, ctypes.c_int64, P, P, P,
                                                ctypes.c_double, P]
-            lib.orc_visibility.argtypes = [P, ctypes.c_int64, P, ctypes.c_int,
+            lib.orc_visibility.argtypes = [P, ctypes.c_int64, P, ctypes.c_int, P, P,
                                            ctypes.c_double, ctypes.c_double,
                                            ctypes.c_double, P]
             lib.orc_facet_integral.argtypes = [P, P, P, P]
-            lib.orc_visibility_bvh.argtypes = [P, ctypes.c_int64, P, ctypes.c_int,
+            lib.orc_visibility_bvh.argtypes = [P, ctypes.c_int64, P, ctypes.c_int, P, P,
                                                ctypes.c_double, ctypes.c_double,
                                                ctypes.c_double, P]
-            lib.orc_visibility_pairs.argtypes = [P, ctypes.c_int64, P, P, ctypes.c_int64,
+            lib.orc_visibility_pairs.argtypes = [P, ctypes.c_int64, P, P, ctypes.c_int64, P, P,
                                                  ctypes.c_double, ctypes.c_double,
                                                  ctypes.c_double, P]
-            lib.orc_rcs_farfield.argtypes = [P, ctypes.c_int64, P, P, P, P,
+            lib.orc_rcs_farfield.argtypes = [P, ctypes.c_int64, P, P, P, P, P,
                                              ctypes.c_int, P]
-            lib.orc_adc_full.argtypes = [P, P, P, P, P, ctypes.c_int64, P, P,
+            lib.orc_adc_full.argtypes = [P, P, P, P, P, P, ctypes.c_int64, P, P,
                                          ctypes.POINTER(_Radar), P]
-            lib.orc_adc_entries.argtypes = [P, P, P, P, P, ctypes.c_int64, P, P,
+            lib.orc_adc_entries.argtypes = [P, P, P, P, P, P, ctypes.c_int64, P, P,
                                             ctypes.POINTER(_Radar), P,
                                             ctypes.c_int64, P]
             lib.orc_num_threads.restype = ctypes.c_int
@@ -131,41 +131,59 @@ def reference_points(scene, t: float) -> np.ndarray:
     return np.ascontiguousarray(ref[inst])
 
 
+def _opt(a, dtype, shape):
+    return None if a is None else np.ascontiguousarray(a, dtype).reshape(shape)
+
+
+def _ptr_or_none(a):
+    return None if a is None else _p(a)
+
+
 def visibility(tri: np.ndarray, antennas: np.ndarray, eps_face: float = EPS_FACE,
-               eps_b: float = EPS_B, eps_t: float = EPS_T) -> np.ndarray:
-    """Facet state per antenna, A x F uint8 (BACK, LIT, GRAZE, OCCL), by
-    brute force over all occluders (BART single bounce, Sec. 2.2)."""
+               eps_b: float = EPS_B, eps_t: float = EPS_T, fref=None,
+               two_sided=None) -> np.ndarray:
+    """Facet state per antenna, A x F uint8 (BACK, LIT, GRAZE, OCCL,
+    LIT_REV), by brute force over all occluders (BART single bounce, Sec.
+    2.2).  ``fref`` (F x 3): far-field segments toward p_a + (c_k - fref_k);
+    ``two_sided`` (F,): facets lit from either side."""
     tri = np.ascontiguousarray(tri, np.float64)
     ant = np.ascontiguousarray(antennas, np.float64).reshape(-1, 3)
     F, A = tri.shape[0], ant.shape[0]
+    fr, ts = _opt(fref, np.float64, (F, 3)), _opt(two_sided, np.uint8, (F,))
     st = np.empty((A, F), np.uint8)
-    _load().orc_visibility(_p(tri), F, _p(ant), A, eps_face, eps_b, eps_t, _p(st))
+    _load().orc_visibility(_p(tri), F, _p(ant), A, _ptr_or_none(fr), _ptr_or_none(ts),
+                           eps_face, eps_b, eps_t, _p(st))
     return st
 
 
 def visibility_bvh(tri: np.ndarray, antennas: np.ndarray, eps_face: float = EPS_FACE,
-                   eps_b: float = EPS_B, eps_t: float = EPS_T) -> np.ndarray:
+                   eps_b: float = EPS_B, eps_t: float = EPS_T, fref=None,
+                   two_sided=None) -> np.ndarray:
     """``visibility`` through the oracle's own top-down median-split BVH
     (for scenes too large for all pairs); same definition, same states."""
     tri = np.ascontiguousarray(tri, np.float64)
     ant = np.ascontiguousarray(antennas, np.float64).reshape(-1, 3)
     F, A = tri.shape[0], ant.shape[0]
+    fr, ts = _opt(fref, np.float64, (F, 3)), _opt(two_sided, np.uint8, (F,))
     st = np.empty((A, F), np.uint8)
-    _load().orc_visibility_bvh(_p(tri), F, _p(ant), A, eps_face, eps_b, eps_t, _p(st))
+    _load().orc_visibility_bvh(_p(tri), F, _p(ant), A, _ptr_or_none(fr), _ptr_or_none(ts),
+                               eps_face, eps_b, eps_t, _p(st))
     return st
 
 
 def visibility_pairs(tri: np.ndarray, antennas: np.ndarray, pairs: np.ndarray,
                      eps_face: float = EPS_FACE, eps_b: float = EPS_B,
-                     eps_t: float = EPS_T) -> np.ndarray:
+                     eps_t: float = EPS_T, fref=None, two_sided=None) -> np.ndarray:
     """States of selected (antenna, facet) pairs (E x 2), brute force over
     all occluders: the per-pair definition of ``visibility`` (Sec. 2.2)."""
     tri = np.ascontiguousarray(tri, np.float64)
     ant = np.ascontiguousarray(antennas, np.float64).reshape(-1, 3)
     pr = np.ascontiguousarray(pairs, np.int64).reshape(-1, 2)
+    F = tri.shape[0]
+    fr, ts = _opt(fref, np.float64, (F, 3)), _opt(two_sided, np.uint8, (F,))
     st = np.empty(pr.shape[0], np.uint8)
-    _load().orc_visibility_pairs(_p(tri), tri.shape[0], _p(ant), _p(pr), pr.shape[0],
-                                 eps_face, eps_b, eps_t, _p(st))
+    _load().orc_visibility_pairs(_p(tri), F, _p(ant), _p(pr), pr.shape[0], _ptr_or_none(fr),
+                                 _ptr_or_none(ts), eps_face, eps_b, eps_t, _p(st))
     return st
 
 
@@ -178,7 +196,8 @@ def facet_integral(tri9: np.ndarray, w: np.ndarray) -> complex:
     return complex(re.value, im.value)
 
 
-def rcs_farfield(tri: np.ndarray, rho: np.ndarray, t_hat, r_hat, freqs) -> np.ndarray:
+def rcs_farfield(tri: np.ndarray, rho: np.ndarray, t_hat, r_hat, freqs,
+                 two_sided=None) -> np.ndarray:
     """Far-field PO RCS sigma(f) (m^2) of a mesh for plane-wave directions
     (toward TX ``t_hat`` and RX ``r_hat``), Sec. 2.2 / Eq. 7's sigma."""
     tri = np.ascontiguousarray(tri, np.float64)
@@ -186,17 +205,20 @@ def rcs_farfield(tri: np.ndarray, rho: np.ndarray, t_hat, r_hat, freqs) -> np.nd
     t = np.ascontiguousarray(t_hat, np.float64) / np.linalg.norm(t_hat)
     r = np.ascontiguousarray(r_hat, np.float64) / np.linalg.norm(r_hat)
     f = np.ascontiguousarray(np.atleast_1d(freqs), np.float64)
+    ts = _opt(two_sided, np.uint8, (tri.shape[0],))
     out = np.empty(f.shape[0], np.float64)
-    _load().orc_rcs_farfield(_p(tri), tri.shape[0], _p(rho), _p(t), _p(r), _p(f),
-                             f.shape[0], _p(out))
+    _load().orc_rcs_farfield(_p(tri), tri.shape[0], _p(rho), _ptr_or_none(ts), _p(t), _p(r),
+                             _p(f), f.shape[0], _p(out))
     return out
 
 
 def _radar_struct(radar) -> _Radar:
+    ff, dr = bool(getattr(radar, "far_field", False)), bool(getattr(radar, "delay_ref", False))
+    if ff and dr:
+        raise ValueError("far_field and delay_ref are exclusive delay forms")
     return _Radar(radar.f0, radar.slope, radar.fs, radar.Tc, radar.M, radar.N,
                   radar.P, radar.Q, int(bool(radar.intra_chirp_motion)),
-                  int(bool(getattr(radar, "tdm", False))),
-                  int(bool(getattr(radar, "delay_ref", False))), 0)
+                  int(bool(getattr(radar, "tdm", False))), int(dr), int(ff))
 
 
 class Frame:
@@ -204,42 +226,56 @@ class Frame:
     force over all occluders up to 60k facets, the oracle's own BVH above."""
 
     def __init__(self, scene, state: np.ndarray | None = None, bvh: bool | None = None):
+        import scenegen
         self.scene = scene
         self.radar = scene.radar
+        self._rs = _radar_struct(self.radar)
         self.tri0, self.fvel, self.rho = world_facets(scene, scene.t0)
+        self.fref = reference_points(scene, scene.t0)
+        ts = scenegen.facet_two_sided(scene)
+        self.two_sided = ts if ts.any() else None
         if state is None:
             use_bvh = self.tri0.shape[0] > 60_000 if bvh is None else bvh
             fn = visibility_bvh if use_bvh else visibility
-            state = fn(self.tri0, self.radar.antennas)
+            state = fn(self.tri0, self.radar.antennas,
+                       eps_face=float(getattr(self.radar, "grazing_eps", EPS_FACE)),
+                       fref=self.fref if self._rs.far_field else None,
+                       two_sided=self.two_sided)
         self.state = state
-        self.fref = reference_points(scene, scene.t0)
-        self._rs = _radar_struct(self.radar)
+
+    def _args(self):
+        r = self.radar
+        return (_p(self.tri0), _p(self.fvel), _p(self.rho), _p(self.fref),
+                _ptr_or_none(self.two_sided), _p(self.state), self.tri0.shape[0], _p(r.tx),
+                _p(r.rx), ctypes.byref(self._rs))
 
     def adc_full(self) -> np.ndarray:
         """ADC cube [O][N][M] complex128 (Eqs. 7, 9-13)."""
         r = self.radar
         out = np.empty((r.O, r.N, r.M), np.complex128)
-        _load().orc_adc_full(_p(self.tri0), _p(self.fvel), _p(self.rho), _p(self.fref),
-                             _p(self.state), self.tri0.shape[0], _p(r.tx), _p(r.rx),
-                             ctypes.byref(self._rs), _p(out))
+        _load().orc_adc_full(*self._args(), _p(out))
         return out
 
     def adc_entries(self, entries: np.ndarray) -> np.ndarray:
         """Selected ADC entries; ``entries`` is E x 3 (o, n, m)."""
         e = np.ascontiguousarray(entries, np.int32).reshape(-1, 3)
         out = np.empty(e.shape[0], np.complex128)
-        r = self.radar
-        _load().orc_adc_entries(_p(self.tri0), _p(self.fvel), _p(self.rho), _p(self.fref),
-                                _p(self.state), self.tri0.shape[0], _p(r.tx), _p(r.rx),
-                                ctypes.byref(self._rs), _p(e), e.shape[0], _p(out))
+        _load().orc_adc_entries(*self._args(), _p(e), e.shape[0], _p(out))
         return out
+
+    def lit_pairs(self) -> np.ndarray:
+        """Boolean [O][F]: facet k seen by channel o (both antennas light the
+        same side of it)."""
+        r = self.radar
+        st = self.state
+        t, x = st[:r.P, None, :], st[None, r.P:, :]
+        both = ((t == LIT) & (x == LIT)) | ((t == LIT_REV) & (x == LIT_REV))
+        return both.reshape(r.O, -1)
 
     def n_terms(self) -> int:
         """Echo terms per frame: sum over channels of lit facets x N x M."""
         r = self.radar
-        lit = self.state == LIT
-        per_ch = (lit[:r.P, None, :] & lit[None, r.P:, :]).sum(axis=2)
-        return int(per_ch.sum()) * r.N * r.M
+        return int(self.lit_pairs().sum()) * r.N * r.M
 
 
 # ---------------------------------------------------------------------------

@@ -35,7 +35,7 @@
 #define ORC_C0 299792458.0
 #define ORC_PI 3.14159265358979323846
 
-enum { ORC_BACK = 0, ORC_LIT = 1, ORC_GRAZE = 2, ORC_OCCL = 3 };
+enum { ORC_BACK = 0, ORC_LIT = 1, ORC_GRAZE = 2, ORC_OCCL = 3, ORC_LIT_REV = 4 };
 
 int orc_num_threads(void)
 {
@@ -163,41 +163,74 @@ static int boxes_disjoint(const double *O, const double *Pa, const double *tri,
     return 0;
 }
 
-/* State of facet k seen from antenna a:
- *   BACK  : cos(angle between outward normal and antenna) <= -eps_face, or a
- *           zero-area facet (it has no normal and cannot be lit)
+/* Where the segment of facet k toward antenna a ends, and the segment
+ * itself (D = end - c): the antenna, or (far field) the antenna moved by the
+ * facet's offset from its instance origin ref, so that every facet of an
+ * instance looks along the same plane-wave direction p_a - ref:
+ *   end = p_a + (c - ref),  D = end - c. */
+static void segment_to(const double *c, const double *pa, const double *ref, double *D)
+{
+    double end[3];
+    for (int r = 0; r < 3; ++r) end[r] = ref ? pa[r] + (c[r] - ref[r]) : pa[r];
+    sub3(end, c, D);
+}
+
+/* Facing part of the state of facet k (tri) seen along segment D from its
+ * centroid:
+ *   BACK     cos(angle between outward normal and D) <= -eps_face on a
+ *            one-sided facet, or a zero-area facet (no normal, never lit)
+ *   LIT      cos >= eps_face (candidate; occlusion decides)
+ *   LIT_REV  a two-sided facet with cos <= -eps_face: lit on its reverse side
+ *   *graze   |cos| < eps_face (the facet is then GRAZE unless occluded) */
+static int facing_state(const double *tk, const double *D, int two_sided, double eps_face,
+                        int *graze)
+{
+    double e1[3], e2[3], n[3];
+    sub3(tk + 3, tk, e1);
+    sub3(tk + 6, tk, e2);
+    cross3(e1, e2, n);
+    const double cosang = dot3(n, D) / (sqrt(dot3(n, n)) * sqrt(dot3(D, D)));
+    *graze = 0;
+    if (dot3(n, n) == 0.0) return ORC_BACK;
+    if (cosang <= -eps_face) return two_sided ? ORC_LIT_REV : ORC_BACK;
+    *graze = fabs(cosang) < eps_face;
+    return ORC_LIT;
+}
+
+/* State of facet k seen from antenna a (BART single bounce, Sec. 2.2):
+ *   BACK / LIT / LIT_REV : facing, as above, and no occluder
  *   GRAZE : |cos| < eps_face, or no robust hit but a grazing one
- *   OCCL  : the centroid->antenna segment robustly hits another facet
- *   LIT   : otherwise
- * Brute force over every other facet.  state: A x F bytes. */
-void orc_visibility(const double *tri, int64_t F, const double *ant, int A,
-                    double eps_face, double eps_b, double eps_t, uint8_t *state)
+ *   OCCL  : the centroid->end segment robustly hits another facet
+ * Brute force over every other facet.  state: A x F bytes.  fref: per-facet
+ * instance origins (far-field segments) or NULL; two_sided: per-facet flags
+ * or NULL (all one-sided). */
+void orc_visibility(const double *tri, int64_t F, const double *ant, int A, const double *fref,
+                    const uint8_t *two_sided, double eps_face, double eps_b, double eps_t,
+                    uint8_t *state)
 {
 #pragma omp parallel for schedule(dynamic, 64) collapse(2)
     for (int a = 0; a < A; ++a) {
         for (int64_t k = 0; k < F; ++k) {
             const double *tk = tri + 9 * k;
-            double c[3], e1[3], e2[3], n[3], D[3];
+            double c[3], D[3], end[3];
             centroid3(tk, c);
-            sub3(tk + 3, tk, e1);
-            sub3(tk + 6, tk, e2);
-            cross3(e1, e2, n);
-            sub3(ant + 3 * a, c, D);
-            const double cosang = dot3(n, D) / (sqrt(dot3(n, n)) * sqrt(dot3(D, D)));
+            segment_to(c, ant + 3 * a, fref ? fref + 3 * k : NULL, D);
+            for (int r = 0; r < 3; ++r) end[r] = c[r] + D[r];
+            int graze;
+            const int face = facing_state(tk, D, two_sided && two_sided[k], eps_face, &graze);
             uint8_t st;
-            if (dot3(n, n) == 0.0 || cosang <= -eps_face) {   /* zero area: no normal */
+            if (face == ORC_BACK) {
                 st = ORC_BACK;
             } else {
-                int graze = fabs(cosang) < eps_face;
                 int hit = 0;
                 for (int64_t j = 0; j < F && !hit; ++j) {
                     if (j == k) continue;
-                    if (boxes_disjoint(c, ant + 3 * a, tri + 9 * j, 1e-6)) continue;
+                    if (boxes_disjoint(c, end, tri + 9 * j, 1e-6)) continue;
                     const int r = mt_segment(c, D, tri + 9 * j, eps_b, eps_t);
                     if (r == 2) hit = 1;
                     else if (r == 1) graze = 1;
                 }
-                st = hit ? ORC_OCCL : (graze ? ORC_GRAZE : ORC_LIT);
+                st = hit ? ORC_OCCL : (graze ? ORC_GRAZE : (uint8_t)face);
             }
             state[(int64_t)a * F + k] = st;
         }
@@ -310,7 +343,8 @@ static int seg_meets_box(const double *O, const double *D, const orc_node *nd)
 /* Visibility states (A x F) using the BVH above; same definition as
  * orc_visibility. */
 void orc_visibility_bvh(const double *tri, int64_t F, const double *ant, int A,
-                        double eps_face, double eps_b, double eps_t, uint8_t *state)
+                        const double *fref, const uint8_t *two_sided, double eps_face,
+                        double eps_b, double eps_t, uint8_t *state)
 {
     orc_bvh b;
     b.tri = tri;
@@ -327,18 +361,15 @@ void orc_visibility_bvh(const double *tri, int64_t F, const double *ant, int A,
     for (int a = 0; a < A; ++a) {
         for (int64_t k = 0; k < F; ++k) {
             const double *tk = tri + 9 * k;
-            double c[3], e1[3], e2[3], n[3], D[3];
+            double c[3], D[3];
             centroid3(tk, c);
-            sub3(tk + 3, tk, e1);
-            sub3(tk + 6, tk, e2);
-            cross3(e1, e2, n);
-            sub3(ant + 3 * a, c, D);
-            const double cosang = dot3(n, D) / (sqrt(dot3(n, n)) * sqrt(dot3(D, D)));
+            segment_to(c, ant + 3 * a, fref ? fref + 3 * k : NULL, D);
+            int graze;
+            const int face = facing_state(tk, D, two_sided && two_sided[k], eps_face, &graze);
             uint8_t st;
-            if (dot3(n, n) == 0.0 || cosang <= -eps_face) {
+            if (face == ORC_BACK) {
                 st = ORC_BACK;
             } else {
-                int graze = fabs(cosang) < eps_face;
                 int hit = 0;
                 int64_t stack[128];
                 int sp = 0;
@@ -359,7 +390,7 @@ void orc_visibility_bvh(const double *tri, int64_t F, const double *ant, int A,
                         stack[sp++] = nd->right;
                     }
                 }
-                st = hit ? ORC_OCCL : (graze ? ORC_GRAZE : ORC_LIT);
+                st = hit ? ORC_OCCL : (graze ? ORC_GRAZE : (uint8_t)face);
             }
             state[(int64_t)a * F + k] = st;
         }
@@ -373,34 +404,33 @@ void orc_visibility_bvh(const double *tri, int64_t F, const double *ant, int A,
  * int64 rows (a, k)), still by brute force over every other facet: used on
  * scenes too large for all pairs. */
 void orc_visibility_pairs(const double *tri, int64_t F, const double *ant, const int64_t *pairs,
-                          int64_t E, double eps_face, double eps_b, double eps_t, uint8_t *state)
+                          int64_t E, const double *fref, const uint8_t *two_sided,
+                          double eps_face, double eps_b, double eps_t, uint8_t *state)
 {
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t e = 0; e < E; ++e) {
         const int a = (int)pairs[2 * e];
         const int64_t k = pairs[2 * e + 1];
         const double *tk = tri + 9 * k;
-        double c[3], e1[3], e2[3], n[3], D[3];
+        double c[3], D[3], end[3];
         centroid3(tk, c);
-        sub3(tk + 3, tk, e1);
-        sub3(tk + 6, tk, e2);
-        cross3(e1, e2, n);
-        sub3(ant + 3 * a, c, D);
-        const double cosang = dot3(n, D) / (sqrt(dot3(n, n)) * sqrt(dot3(D, D)));
+        segment_to(c, ant + 3 * a, fref ? fref + 3 * k : NULL, D);
+        for (int r = 0; r < 3; ++r) end[r] = c[r] + D[r];
+        int graze;
+        const int face = facing_state(tk, D, two_sided && two_sided[k], eps_face, &graze);
         uint8_t st;
-        if (dot3(n, n) == 0.0 || cosang <= -eps_face) {
+        if (face == ORC_BACK) {
             st = ORC_BACK;
         } else {
-            int graze = fabs(cosang) < eps_face;
             int hit = 0;
             for (int64_t j = 0; j < F && !hit; ++j) {
                 if (j == k) continue;
-                if (boxes_disjoint(c, ant + 3 * a, tri + 9 * j, 1e-6)) continue;
+                if (boxes_disjoint(c, end, tri + 9 * j, 1e-6)) continue;
                 const int r = mt_segment(c, D, tri + 9 * j, eps_b, eps_t);
                 if (r == 2) hit = 1;
                 else if (r == 1) graze = 1;
             }
-            st = hit ? ORC_OCCL : (graze ? ORC_GRAZE : ORC_LIT);
+            st = hit ? ORC_OCCL : (graze ? ORC_GRAZE : (uint8_t)face);
         }
         state[e] = st;
     }
@@ -505,10 +535,11 @@ void orc_facet_integral(const double *tri, const double *w, double *re, double *
 
 /* sigma(f) = |sum_k rho_k (k/sqrt(pi)) o_k J_k(-k(t+r)) exp(-j k (t+r).c_k)|^2
  * over facets whose outward normal faces both unit directions t (toward
- * the transmitter) and r (toward the receiver); o_k = n_k.(t+r)/2 is the
- * scalar co-polarised obliquity (cos(theta) monostatic).  Occlusion is not
- * tested (convex or flat bodies only). */
-void orc_rcs_farfield(const double *tri, int64_t F, const float *rho,
+ * the transmitter) and r (toward the receiver) -- or, for a two-sided facet
+ * (two_sided[k], may be NULL), faces away from both (lit on its reverse);
+ * o_k = |n_k.(t+r)|/2 is the scalar co-polarised obliquity (cos(theta)
+ * monostatic).  Occlusion is not tested (convex or flat bodies only). */
+void orc_rcs_farfield(const double *tri, int64_t F, const float *rho, const uint8_t *two_sided,
                       const double *that, const double *rhat,
                       const double *freqs, int nfreq, double *sigma)
 {
@@ -525,8 +556,11 @@ void orc_rcs_farfield(const double *tri, int64_t F, const float *rho,
             sub3(tk + 6, tk, e2);
             cross3(e1, e2, nn);
             const double nl = sqrt(dot3(nn, nn));
-            if (dot3(nn, that) <= 0.0 || dot3(nn, rhat) <= 0.0) continue;
-            const double o = 0.5 * dot3(nn, b) / nl;
+            const double ct = dot3(nn, that), cr = dot3(nn, rhat);
+            const int front = ct > 0.0 && cr > 0.0;
+            const int rev = two_sided && two_sided[f] && ct < 0.0 && cr < 0.0;
+            if (!front && !rev) continue;
+            const double o = fabs(0.5 * dot3(nn, b) / nl);
             double w[3] = {-k * b[0], -k * b[1], -k * b[2]};
             double jr, ji;
             orc_facet_integral(tk, w, &jr, &ji);
@@ -550,7 +584,7 @@ typedef struct {
     int intra_chirp_motion;     /* tau evaluated at t_n + t_m (1) or t_n (0) */
     int tdm;                    /* 1: TX p transmits chirp n at (n P + p) T_c */
     int delay_ref;              /* 1: reference-point delay form (Eqs. 11-13 per target) */
-    int pad_;
+    int far_field;              /* 1: plane-wave directions and path from the instance origin */
 } orc_radar;
 
 /* One IF sample of channel o = p*Q + q, chirp n, sample m:
@@ -582,7 +616,22 @@ typedef struct {
  * i.e. the facet enters through the frequency response relative to the
  * reference point at the chirp's aspect (sigma_f), the delay of Eq. 12, its
  * motion within the chirp and the residual video phase belong to the
- * reference point. */
+ * reference point.
+ *
+ * Far field (far_field): every facet of an instance is seen along the plane
+ * waves of its instance origin r_i, at the origin's ranges: with r0 the
+ * origin at the chirp start, t = (p_tx - r0)/R_t, r = (p_rx - r0)/R_r,
+ * R_t = |p_tx - r0|, R_r = |p_rx - r0| (amplitude, obliquity and the facet
+ * integral use these), and the facet's path is the plane-wave one,
+ *   L_k(t) = |p_tx - r(t)| + |p_rx - r(t)| - (t + r).(c_k - r0),
+ * the origin moving within the chirp (t = t_n + t_m) and the projection held
+ * at the chirp start; tau = L_k / c enters Eq. 13 as above.  A flat plate
+ * centred on its origin then gives exactly the radar equation with the
+ * far-field PO cross-section 4 pi A^2 / lambda^2 at normal incidence.
+ *
+ * Two-sided facets (two_sided[k]): the channel sees the facet when both its
+ * antennas light the same side (LIT from both, or LIT_REV from both); the
+ * obliquity is |n_k . (t + r)| / 2, the normal turned toward the antennas. */
 static double path_len(const double *x, const double *ptx, const double *prx)
 {
     double ut[3], ur[3];
@@ -592,9 +641,9 @@ static double path_len(const double *x, const double *ptx, const double *prx)
 }
 
 static void adc_sample(const double *tri0, const double *fvel, const float *rho,
-                       const double *fref, const uint8_t *state, int64_t F, const double *tx,
-                       const double *rx, const orc_radar *rd, int o, int n, int m,
-                       double *out_re, double *out_im)
+                       const double *fref, const uint8_t *two_sided, const uint8_t *state,
+                       int64_t F, const double *tx, const double *rx, const orc_radar *rd, int o,
+                       int n, int m, double *out_re, double *out_im)
 {
     const int p = o / rd->Q, q = o % rd->Q;
     const double tn = (double)(rd->tdm ? (int64_t)n * rd->P + p : n) * rd->Tc;
@@ -609,22 +658,29 @@ static void adc_sample(const double *tri0, const double *fvel, const float *rho,
     const double amp0 = 1.0 / pow(4.0 * ORC_PI, 1.5);
     double sr = 0.0, si = 0.0;
     for (int64_t k = 0; k < F; ++k) {
-        if (st_t[k] != ORC_LIT || st_r[k] != ORC_LIT) continue;
+        const int lit = (st_t[k] == ORC_LIT && st_r[k] == ORC_LIT) ||
+                        (st_t[k] == ORC_LIT_REV && st_r[k] == ORC_LIT_REV);
+        if (!lit) continue;
         const double *vk = fvel + 3 * k;
         double tri[9];
         for (int i = 0; i < 9; ++i) tri[i] = tri0[9 * k + i] + vk[i % 3] * tn;
-        double c[3], e1[3], e2[3], nn[3], dt[3], dr[3];
+        double c[3], e1[3], e2[3], nn[3], dt[3], dr[3], r0[3];
         centroid3(tri, c);
         sub3(tri + 3, tri, e1);
         sub3(tri + 6, tri, e2);
         cross3(e1, e2, nn);
         const double nl = sqrt(dot3(nn, nn));
-        sub3(ptx, c, dt);
-        sub3(prx, c, dr);
+        if (rd->far_field || rd->delay_ref)
+            for (int r = 0; r < 3; ++r) r0[r] = fref[3 * k + r] + vk[r] * tn;
+        /* directions and ranges: from the centroid, or (far field) the origin */
+        const double *from = rd->far_field ? r0 : c;
+        sub3(ptx, from, dt);
+        sub3(prx, from, dr);
         const double Rt = sqrt(dot3(dt, dt)), Rr = sqrt(dot3(dr, dr));
         double b[3];
         for (int r = 0; r < 3; ++r) b[r] = dt[r] / Rt + dr[r] / Rr;
-        const double ok = 0.5 * dot3(nn, b) / nl;
+        double ok = 0.5 * dot3(nn, b) / nl;
+        if (two_sided && two_sided[k]) ok = fabs(ok);
         double w[3] = {-km * b[0], -km * b[1], -km * b[2]};
         double jr, ji;
         orc_facet_integral(tri, w, &jr, &ji);
@@ -632,7 +688,14 @@ static void adc_sample(const double *tri0, const double *fvel, const float *rho,
         const double a = lam * amp0 / (Rt * Rr) * s;
         /* round-trip delay at t_n + t_m */
         double phase;
-        if (!rd->delay_ref) {
+        if (rd->far_field) {
+            double rt[3], off[3];
+            for (int r = 0; r < 3; ++r) rt[r] = rd->intra_chirp_motion ? r0[r] + vk[r] * tm : r0[r];
+            sub3(c, r0, off);
+            const double tau = (path_len(rt, ptx, prx) - dot3(b, off)) / ORC_C0;
+            phase = 2.0 * ORC_PI *
+                (rd->f0 * tau + rd->slope * tm * tau - 0.5 * rd->slope * tau * tau);
+        } else if (!rd->delay_ref) {
             double ct[3] = {c[0], c[1], c[2]};
             if (rd->intra_chirp_motion)
                 for (int r = 0; r < 3; ++r) ct[r] = c[r] + vk[r] * tm;
@@ -640,11 +703,8 @@ static void adc_sample(const double *tri0, const double *fvel, const float *rho,
             phase = 2.0 * ORC_PI *
                 (rd->f0 * tau + rd->slope * tm * tau - 0.5 * rd->slope * tau * tau);
         } else {
-            double r0[3], rt[3];
-            for (int r = 0; r < 3; ++r) {
-                r0[r] = fref[3 * k + r] + vk[r] * tn;
-                rt[r] = rd->intra_chirp_motion ? r0[r] + vk[r] * tm : r0[r];
-            }
+            double rt[3];
+            for (int r = 0; r < 3; ++r) rt[r] = rd->intra_chirp_motion ? r0[r] + vk[r] * tm : r0[r];
             const double Lk = path_len(c, ptx, prx), Lr0 = path_len(r0, ptx, prx);
             const double Lrt = path_len(rt, ptx, prx);
             const double tau_f = (Lk - Lr0 + Lrt) / ORC_C0, tau_r = Lrt / ORC_C0;
@@ -660,8 +720,8 @@ static void adc_sample(const double *tri0, const double *fvel, const float *rho,
 
 /* Full ADC cube [O][N][M] (complex128, interleaved). */
 void orc_adc_full(const double *tri0, const double *fvel, const float *rho,
-                  const double *fref, const uint8_t *state, int64_t F, const double *tx,
-                  const double *rx, const orc_radar *rd, double *out)
+                  const double *fref, const uint8_t *two_sided, const uint8_t *state, int64_t F,
+                  const double *tx, const double *rx, const orc_radar *rd, double *out)
 {
     const int O = rd->P * rd->Q;
 #pragma omp parallel for schedule(dynamic, 1) collapse(2)
@@ -669,19 +729,19 @@ void orc_adc_full(const double *tri0, const double *fvel, const float *rho,
         for (int n = 0; n < rd->N; ++n)
             for (int m = 0; m < rd->M; ++m) {
                 const int64_t idx = ((int64_t)o * rd->N + n) * rd->M + m;
-                adc_sample(tri0, fvel, rho, fref, state, F, tx, rx, rd, o, n, m,
+                adc_sample(tri0, fvel, rho, fref, two_sided, state, F, tx, rx, rd, o, n, m,
                            out + 2 * idx, out + 2 * idx + 1);
             }
 }
 
 /* Selected entries (o, n, m) of the ADC cube; entries: E x 3 int32. */
 void orc_adc_entries(const double *tri0, const double *fvel, const float *rho,
-                     const double *fref, const uint8_t *state, int64_t F, const double *tx,
-                     const double *rx, const orc_radar *rd, const int32_t *entries,
-                     int64_t E, double *out)
+                     const double *fref, const uint8_t *two_sided, const uint8_t *state,
+                     int64_t F, const double *tx, const double *rx, const orc_radar *rd,
+                     const int32_t *entries, int64_t E, double *out)
 {
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t e = 0; e < E; ++e)
-        adc_sample(tri0, fvel, rho, fref, state, F, tx, rx, rd, entries[3 * e],
+        adc_sample(tri0, fvel, rho, fref, two_sided, state, F, tx, rx, rd, entries[3 * e],
                    entries[3 * e + 1], entries[3 * e + 2], out + 2 * e, out + 2 * e + 1);
 }

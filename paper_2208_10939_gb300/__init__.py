@@ -26,7 +26,8 @@ BART_ETIMEOUT, BART_ESTATE, BART_EDEVICE = -4, -5, -6
 PATH_FP64, PATH_MIXED = 0, 1
 C128, C64 = 0, 1
 WINDOW_HANN, WINDOW_RECT = 0, 1
-VIS_BACK, VIS_LIT, VIS_GRAZE, VIS_OCCL = 0, 1, 2, 3
+VIS_BACK, VIS_LIT, VIS_GRAZE, VIS_OCCL, VIS_LIT_REV = 0, 1, 2, 3, 4
+MESH_TWO_SIDED = 1
 MAX_TX = MAX_RX = 16
 
 EXPORTED = ["bart_last_error", "bart_version", "bart_create", "bart_destroy",
@@ -37,7 +38,7 @@ EXPORTED = ["bart_last_error", "bart_version", "bart_create", "bart_destroy",
             "bart_scene_partition", "bart_set_graph", "bart_set_synth_layout",
             "bart_autotune", "bart_rdm_adjoint", "bart_simulate_adjoint",
             "bart_simulate_adjoint_mixed",
-            "bart_mesh_update", "bart_measure_peaks"]
+            "bart_mesh_update", "bart_measure_peaks", "bart_inject_alloc_failure"]
 
 
 class BartError(RuntimeError):
@@ -60,7 +61,9 @@ class bart_radar(ctypes.Structure):
                 ("window", ctypes.c_int32),
                 ("tx", (ctypes.c_double * 3) * MAX_TX),
                 ("rx", (ctypes.c_double * 3) * MAX_RX),
-                ("tdm", ctypes.c_int32), ("delay_ref", ctypes.c_int32)]
+                ("tdm", ctypes.c_int32), ("delay_ref", ctypes.c_int32),
+                ("far_field", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("grazing_eps", ctypes.c_double)]
 
 
 class bart_stats(ctypes.Structure):
@@ -153,7 +156,7 @@ def load_library() -> ctypes.CDLL:
         L.bart_destroy.argtypes = [P]
         L.bart_destroy.restype = None
         L.bart_set_stream.argtypes = [P, P]
-        L.bart_mesh_upload.argtypes = [P, P, I64, P, I64, P, ctypes.POINTER(I32)]
+        L.bart_mesh_upload.argtypes = [P, P, I64, P, I64, P, ctypes.c_uint32, ctypes.POINTER(I32)]
         L.bart_mesh_clear.argtypes = [P]
         L.bart_scene_set.argtypes = [P, P, I32]
         L.bart_scene_facets.argtypes = [P, ctypes.POINTER(I64)]
@@ -161,7 +164,7 @@ def load_library() -> ctypes.CDLL:
         L.bart_simulate_frame.argtypes = [P, D, I32, P, I32, ctypes.POINTER(bart_stats)]
         L.bart_form_rdm.argtypes = [P, P, I32, P]
         L.bart_frame_host.argtypes = [P, D, I32, P, ctypes.POINTER(bart_stats)]
-        L.bart_get_visibility.argtypes = [P, P]
+        L.bart_get_visibility.argtypes = [P, P, ctypes.POINTER(I64)]
         L.bart_set_timing.argtypes = [P, I32]
         L.bart_get_timing.argtypes = [P, ctypes.POINTER(bart_timing)]
         L.bart_sync.argtypes = [P]
@@ -178,6 +181,7 @@ def load_library() -> ctypes.CDLL:
         L.bart_detect.argtypes = [P, P, I32, ctypes.POINTER(bart_detect_cfg), P, P, I32,
                                   ctypes.POINTER(I32)]
         L.bart_measure_peaks.argtypes = [I32, I32, ctypes.POINTER(bart_peaks)]
+        L.bart_inject_alloc_failure.argtypes = [I32]
         for name in EXPORTED:
             if name not in ("bart_last_error", "bart_version", "bart_destroy"):
                 getattr(L, name).restype = ctypes.c_int
@@ -220,14 +224,15 @@ def bart_set_stream(ctx: int, stream: int) -> None:
 
 
 def bart_mesh_upload(ctx: int, verts: np.ndarray, tris: np.ndarray,
-                     rho: Optional[np.ndarray] = None) -> int:
+                     rho: Optional[np.ndarray] = None, two_sided: bool = False) -> int:
     v = np.ascontiguousarray(verts, np.float64)
     t = np.ascontiguousarray(tris, np.int32)
     r = None if rho is None else np.ascontiguousarray(rho, np.float32)
     mid = ctypes.c_int32()
     _check(load_library().bart_mesh_upload(
         ctx, v.ctypes.data, v.shape[0], t.ctypes.data, t.shape[0],
-        None if r is None else r.ctypes.data, ctypes.byref(mid)))
+        None if r is None else r.ctypes.data, MESH_TWO_SIDED if two_sided else 0,
+        ctypes.byref(mid)))
     return mid.value
 
 
@@ -290,6 +295,8 @@ def make_radar(radar, window: int = WINDOW_HANN) -> bart_radar:
     r.window = int(window)
     r.tdm = int(bool(getattr(radar, "tdm", False)))
     r.delay_ref = int(bool(getattr(radar, "delay_ref", False)))
+    r.far_field = int(bool(getattr(radar, "far_field", False)))
+    r.grazing_eps = float(getattr(radar, "grazing_eps", 0.0) or 0.0)
     for p in range(min(r.P, MAX_TX)):
         for k in range(3):
             r.tx[p][k] = float(tx[p, k])
@@ -422,6 +429,12 @@ def bart_form_rdm_static(adc, rdm, O: int, N: int, M: int, window: int = WINDOW_
             ctypes.c_void_p(_ptr(rdm)), ctypes.c_void_p(int(stream))))
 
 
+def bart_inject_alloc_failure(nth: int) -> None:
+    """Make the library's nth device allocation from now fail with
+    BART_ENOMEM (host-side fault injection; 0 disarms)."""
+    _check(load_library().bart_inject_alloc_failure(int(nth)))
+
+
 def bart_measure_peaks(device: int = 0, reps: int = 5) -> dict:
     """Measured FP32 FMA (scalar and packed), MUFU sincos and FP64 FMA rates
     of the device (register-only microbenchmarks, CUDA-event timed)."""
@@ -430,8 +443,13 @@ def bart_measure_peaks(device: int = 0, reps: int = 5) -> dict:
     return {k: getattr(out, k) for k, _ in bart_peaks._fields_}
 
 
-def bart_get_visibility(ctx: int, state) -> None:
-    _check(load_library().bart_get_visibility(ctx, ctypes.c_void_p(_ptr(state))))
+def bart_get_visibility(ctx: int, state, grazing: bool = False):
+    """Copy the frame-start states into ``state`` (A x F uint8 on the
+    device); with ``grazing`` also return the number of GRAZE pairs."""
+    n = ctypes.c_int64(-1)
+    _check(load_library().bart_get_visibility(ctx, ctypes.c_void_p(_ptr(state)),
+                                              ctypes.byref(n) if grazing else None))
+    return n.value if grazing else None
 
 
 def bart_rdm_adjoint(ctx: int, adc, grad_rdm, grad_adc) -> None:
@@ -536,7 +554,7 @@ class Simulator:
         """Upload meshes, instances and radar of a scene object."""
         bart_mesh_clear(self.ctx)
         for m in scene.meshes:
-            bart_mesh_upload(self.ctx, m.verts, m.tris, m.rho)
+            bart_mesh_upload(self.ctx, m.verts, m.tris, m.rho, getattr(m, "two_sided", False))
         bart_scene_set(self.ctx, scene.instances)
         bart_radar_set(self.ctx, scene.radar, window)
         self.n_scenes = 1
@@ -550,7 +568,8 @@ class Simulator:
         bart_mesh_clear(self.ctx)
         insts, first = [], [0]
         for sc in scenes:
-            ids = [bart_mesh_upload(self.ctx, m.verts, m.tris, m.rho) for m in sc.meshes]
+            ids = [bart_mesh_upload(self.ctx, m.verts, m.tris, m.rho, getattr(m, "two_sided", False))
+                   for m in sc.meshes]
             for ins in sc.instances:
                 insts.append(_Placed(ids[ins.mesh_id], ins))
             first.append(len(insts))
@@ -603,12 +622,14 @@ class Simulator:
         host = buf[:k * POINT_DTYPE.itemsize].cpu().numpy()
         return host.view(POINT_DTYPE), n
 
-    def visibility(self):
+    def visibility(self, grazing: bool = False):
+        """Frame-start states (A x F uint8 tensor); with ``grazing`` the
+        tuple (states, number of GRAZE pairs)."""
         import torch
         A = int(self.radar.tx.shape[0]) + int(self.radar.rx.shape[0])
         st = torch.empty((A, self.n_facets), dtype=torch.uint8, device=f"cuda:{self.device}")
-        bart_get_visibility(self.ctx, st)
-        return st
+        n = bart_get_visibility(self.ctx, st, grazing)
+        return (st, n) if grazing else st
 
     def sync(self) -> None:
         bart_sync(self.ctx)

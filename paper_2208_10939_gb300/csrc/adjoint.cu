@@ -251,8 +251,8 @@ adjoint_fp64_kernel(SynthArgs A, int W, int NCH, const void *__restrict__ grad, 
             int flags = 0;
             R.kind = build_record<double>(tri, c0, vel, tn, ptx, prx, (double)A.fac[k].rho,
                                           A.rd.intra, k0, kmax,
-                                          A.rd.delay_ref ? A.ref64 + 3 * inst : nullptr, R.r,
-                                          &flags);
+                                          A.rd.delay_ref ? kDelayRef : kDelayFacet,
+                                          A.ref64 + 3 * inst, A.fac[k].two_sided, R.r, &flags);
             R.flags = flags;
             if constexpr (MX) {
                 // the path lengths' expansion about the row's middle sample
@@ -471,6 +471,7 @@ adjoint_fp64_kernel(SynthArgs A, int W, int NCH, const void *__restrict__ grad, 
             for (int r = 0; r < 3; ++r) c0[r] = A.c64[3 * k + r];
             const double rho = (double)A.fac[k].rho;
             const double *ref = A.rd.delay_ref ? A.ref64 + 3 * A.fac[k].inst : nullptr;
+            const int two_sided = A.fac[k].two_sided;
             for (int p = 0; p < 10; ++p) {
                 Dual dtri[9], dc0[3], out[kRecEntries];
                 for (int e = 0; e < kRecEntries; ++e) out[e] = Dual(0.0, 0.0);
@@ -480,7 +481,8 @@ adjoint_fp64_kernel(SynthArgs A, int W, int NCH, const void *__restrict__ grad, 
                 const Dual drho(rho, p == 9 ? 1.0 : 0.0);
                 int flags = 0;
                 const int kind = build_record<Dual>(dtri, dc0, vel, tn, ptx, prx, drho, A.rd.intra,
-                                                    k0, kmax, ref, out, &flags);
+                                                    k0, kmax, ref ? kDelayRef : kDelayFacet,
+                                                    ref, two_sided, out, &flags);
                 double gsum = 0.0;
                 if (kind == R.kind)
                     for (int e = 0; e < kRecEntries; ++e) gsum += mine[e] * out[e].d;

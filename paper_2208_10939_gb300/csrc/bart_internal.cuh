@@ -13,9 +13,10 @@ constexpr double kPi = 3.14159265358979323846;
 constexpr int kMaxAnt = BART_MAX_TX + BART_MAX_RX;
 
 // Visibility margins (BART single bounce, Sec. 2.2).  A facet whose normal
-// makes |cos| < kEpsFace with its antenna, or whose centroid->antenna segment
-// passes within the barycentric / parameter margins of another facet
-// without a clear hit, is "grazing": excluded and counted.
+// makes |cos| < eps_face with its antenna (kEpsFace unless the radar sets
+// grazing_eps), or whose centroid->antenna segment passes within the
+// barycentric / parameter margins of another facet without a clear hit, is
+// "grazing": excluded and counted.
 constexpr double kEpsFace = 1e-6;
 constexpr double kEpsB = 1e-9;
 constexpr double kEpsT = 1e-9;
@@ -38,6 +39,8 @@ struct RadarDev {
     int tdm;        // time-division MIMO: chirp n of TX p at (n P + p) Tc
     int delay_ref;  // reference-point delay form
     int slots;      // chirp slots per chirp index: P with tdm, else 1
+    int far_field;  // plane waves from each instance origin (see bartsim.h)
+    double eps_face;  // grazing threshold of |cos| toward an antenna
     double ant[kMaxAnt][3];   // TX 0..P-1, then RX P..P+Q-1
 };
 
@@ -49,7 +52,8 @@ struct __align__(16) FacetRec {
     float rho;      // reflectivity
     float n[3];     // unit outward normal
     int inst;       // instance index
-    float pad[2];
+    int two_sided;  // 1: lit from either side (BART_MESH_TWO_SIDED)
+    float pad;
 };
 static_assert(sizeof(FacetRec) == 80, "FacetRec layout");
 
@@ -72,6 +76,7 @@ struct MeshDesc {
     const int32_t *tris;
     const float *rho;
     int64_t nf;
+    int two_sided;
 };
 
 struct InstDev {
@@ -129,7 +134,8 @@ struct SceneSplit {
     const int32_t *root = nullptr;
 };
 void launch_visibility(const double *tri64, const float *tri32, const double *c64,
-                       const FacetRec *fac, const BvhNode *nodes, const int32_t *order, int64_t F, const RadarDev &rd,
+                       const FacetRec *fac, const double *ref64, const BvhNode *nodes,
+                       const int32_t *order, int64_t F, const RadarDev &rd,
                        const SceneSplit &sc, uint8_t *state, unsigned long long *n_graze,
                        int *status, cudaStream_t s);
 // lists 0..O-1: facets lit from both antennas of each channel; O..O+A-1: facets
@@ -161,7 +167,7 @@ struct SynthArgs {
     const int32_t *vcnt;
     int64_t F;
     const float4 *kin;       // [A][F][9] kinematics Taylor rows (mixed path)
-    const double *kquad;     // [A][F][3] R^2 quadratic of rows without a expansion
+    const double *kquad;     // [A][F][kKinQuadWords] FP64 data of rows without a expansion
     int n0, nc;              // chirp chunk
     void *out;
     int out_c64;
@@ -177,8 +183,11 @@ struct SynthArgs {
 };
 // per (antenna, lit facet) Taylor rows of R(t) over the frame (see synth.cu)
 constexpr int kKinRowWords = 9;    // float4 per row
-void launch_kin_coef(const double *c64, const FacetRec *fac, const double *vel64, int64_t F,
-                     const RadarDev &rd, float4 *coef, double *quad, cudaStream_t s);
+constexpr int kKinQuadWords = 5;   // doubles per row: R^2 = q0 + q1 t + q2 t^2 and, in the
+                                   // far field, l = l0 + l1 t (path R + l / R)
+void launch_kin_coef(const double *c64, const FacetRec *fac, const double *vel64,
+                     const double *ref64, int64_t F, const RadarDev &rd, float4 *coef,
+                     double *quad, cudaStream_t s);
 void launch_synth_mixed(const SynthArgs &a, cudaStream_t s);
 // scratch of the mixed path for F facets and a chunk of nc chirps
 // scene_F: facets of each scene (n_scene entries); tpi: 32-record tiles per

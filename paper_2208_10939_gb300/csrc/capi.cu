@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -12,12 +13,32 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "bart_internal.cuh"
 #include "bartsim.h"
 
 using namespace bart;
 
 namespace {
+
+// NVTX ranges for the stages of a call, as the host enqueues them (they show
+// the stages in Nsight timelines; header-only, no cost without a tool
+// attached): next() closes the open stage and opens another; leaving the
+// scope, on any return path, closes the last one
+struct Stages {
+    bool open = false;
+    void next(const char *name)
+    {
+        if (open) nvtxRangePop();
+        nvtxRangePushA(name);
+        open = true;
+    }
+    ~Stages()
+    {
+        if (open) nvtxRangePop();
+    }
+};
 
 thread_local std::string g_err;
 
@@ -40,6 +61,18 @@ int cuda_fail(cudaError_t e, const char *what)
                 cudaGetErrorString(e));
 }
 
+// Host-side fault injection (bart_inject_alloc_failure): the countdown-th
+// device allocation from now fails as if cudaMalloc had run out of memory.
+std::atomic<int64_t> g_fail_countdown{0};
+
+bool injected_alloc_failure()
+{
+    int64_t c = g_fail_countdown.load();
+    while (c > 0)
+        if (g_fail_countdown.compare_exchange_weak(c, c - 1)) return c == 1;
+    return false;
+}
+
 template <typename T> struct DevBuf {
     T *p = nullptr;
     size_t cap = 0;
@@ -48,6 +81,9 @@ template <typename T> struct DevBuf {
         if (n <= cap) return BART_OK;
         release();
         if (n == 0) return BART_OK;
+        if (injected_alloc_failure())
+            return fail(BART_ENOMEM, "cudaMalloc(%zu bytes) for %s failed: injected failure",
+                        n * sizeof(T), what);
         cudaError_t e = cudaMalloc(&p, n * sizeof(T));
         if (e != cudaSuccess) {
             p = nullptr;
@@ -72,6 +108,7 @@ struct MeshStore {
     DevBuf<float> rho;
     int64_t nv = 0, nf = 0;
     bool has_rho = false;
+    uint32_t flags = 0;
 };
 
 }  // namespace
@@ -109,7 +146,7 @@ struct bart_ctx {
     DevBuf<uint8_t> state;
     DevBuf<int32_t> blk_cnt, vis_idx, vis_cnt;
     DevBuf<float4> kin;                 // kinematics Taylor rows [A][F][9]
-    DevBuf<double> kquad;               // R^2 quadratics of the rows [A][F][3]
+    DevBuf<double> kquad;               // FP64 row data [A][F][kKinQuadWords]
     DevBuf<float2> partial;             // mixed-path per-item partial sums
     DevBuf<int32_t> item_off;
     DevBuf<int> item_counter;
@@ -249,6 +286,8 @@ static RadarDev make_rd(const bart_radar &r)
     d.tdm = r.tdm ? 1 : 0;
     d.delay_ref = r.delay_ref ? 1 : 0;
     d.slots = d.tdm ? r.P : 1;
+    d.far_field = r.far_field ? 1 : 0;
+    d.eps_face = r.grazing_eps > 0.0 ? r.grazing_eps : kEpsFace;
     for (int p = 0; p < r.P; ++p)
         for (int k = 0; k < 3; ++k) d.ant[p][k] = r.tx[p][k];
     for (int q = 0; q < r.Q; ++q)
@@ -277,7 +316,15 @@ extern "C" {
 
 const char *bart_last_error(void) { return g_err.c_str(); }
 
-const char *bart_version(void) { return "bartsim 0.1 (sm_103a)"; }
+const char *bart_version(void) { return "bartsim 0.2 (sm_103a)"; }
+
+int bart_inject_alloc_failure(int32_t nth)
+{
+    g_err.clear();
+    if (nth < 0) return fail(BART_EINVAL, "bart_inject_alloc_failure: nth=%d", nth);
+    g_fail_countdown.store(nth);
+    return BART_OK;
+}
 
 int bart_create(bart_ctx **out, int device)
 {
@@ -326,10 +373,12 @@ int bart_set_stream(bart_ctx *ctx, void *stream)
 }
 
 int bart_mesh_upload(bart_ctx *ctx, const double *verts, int64_t nv, const int32_t *tris,
-                     int64_t nf, const float *rho, int32_t *mesh_id)
+                     int64_t nf, const float *rho, uint32_t flags, int32_t *mesh_id)
 {
     g_err.clear();
     if (!ctx || !verts || !tris || !mesh_id) return fail(BART_EINVAL, "bart_mesh_upload: NULL argument");
+    if (flags & ~BART_MESH_TWO_SIDED)
+        return fail(BART_EINVAL, "bart_mesh_upload: unknown flags 0x%x", flags);
     if (nv < 3 || nf < 1) return fail(BART_EINVAL, "bart_mesh_upload: nv=%lld nf=%lld", (long long)nv, (long long)nf);
     if (nf > (int64_t)1 << 30) return fail(BART_EINVAL, "bart_mesh_upload: nf too large");
     for (int64_t i = 0; i < 3 * nf; ++i)
@@ -356,6 +405,7 @@ int bart_mesh_upload(bart_ctx *ctx, const double *verts, int64_t nv, const int32
     }
     CUDA_TRY(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
     m->has_rho = rho != nullptr;
+    m->flags = flags;
     m->nv = nv;
     m->nf = nf;
     *mesh_id = ctx->n_meshes++;
@@ -466,9 +516,16 @@ int bart_radar_set(bart_ctx *ctx, const bart_radar *r)
                     (double)r->M / r->fs);
     if (r->window != BART_WINDOW_HANN && r->window != BART_WINDOW_RECT)
         return fail(BART_EINVAL, "bart_radar_set: window=%d", r->window);
-    if ((r->tdm != 0 && r->tdm != 1) || (r->delay_ref != 0 && r->delay_ref != 1))
-        return fail(BART_EINVAL, "bart_radar_set: tdm=%d delay_ref=%d (0 or 1)", r->tdm,
-                    r->delay_ref);
+    if ((r->tdm != 0 && r->tdm != 1) || (r->delay_ref != 0 && r->delay_ref != 1) ||
+        (r->far_field != 0 && r->far_field != 1))
+        return fail(BART_EINVAL, "bart_radar_set: tdm=%d delay_ref=%d far_field=%d (0 or 1)",
+                    r->tdm, r->delay_ref, r->far_field);
+    if (r->far_field && r->delay_ref)
+        return fail(BART_EINVAL, "bart_radar_set: far_field and delay_ref are exclusive");
+    if (r->reserved0 != 0) return fail(BART_EINVAL, "bart_radar_set: reserved0 must be 0");
+    if (!(r->grazing_eps == 0.0 || (r->grazing_eps > 0.0 && r->grazing_eps <= 0.1)))
+        return fail(BART_EINVAL, "bart_radar_set: grazing_eps=%g (0 or in (0, 0.1])",
+                    r->grazing_eps);
     ctx->radar = *r;
     ++ctx->version;
     ctx->have_radar = true;
@@ -502,7 +559,8 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
     std::vector<MeshDesc> md(ctx->n_meshes);
     for (int i = 0; i < ctx->n_meshes; ++i) {
         MeshStore *m = ctx->pool[i];
-        md[i] = MeshDesc{m->verts.p, m->tris.p, m->has_rho ? m->rho.p : nullptr, m->nf};
+        md[i] = MeshDesc{m->verts.p, m->tris.p, m->has_rho ? m->rho.p : nullptr, m->nf,
+                         (m->flags & BART_MESH_TWO_SIDED) ? 1 : 0};
     }
     std::vector<InstDev> id(I);
     int64_t F = 0;
@@ -602,7 +660,7 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
         // kinematics: Taylor rows of R(t) per antenna and facet (one launch,
         // evaluated per record inside the synthesis)
         BART_TRY(ctx->kin.ensure((size_t)A * F * kKinRowWords, "kinematics rows"));
-        BART_TRY(ctx->kquad.ensure((size_t)A * F * 3, "kinematics quadratics"));
+        BART_TRY(ctx->kquad.ensure((size_t)A * F * kKinQuadWords, "kinematics quadratics"));
         BART_TRY(ctx->partial.ensure((size_t)synth_partial_words(scene_F.data(), B, rd, rd.N,
                                                                  tpi, ctx->layout_S),
                                      "synthesis partials"));
@@ -642,6 +700,8 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
         int launches = 0;
 
         // 1. world facets at t0
+        Stages nv;
+        nv.next("bart facets");
         launch_build_facets(ctx->d_meshes.p, ctx->d_insts.p, I, F, t0v, ctx->tri64.p, ctx->tri32.p,
                             ctx->c64.p, ctx->fac.p, ctx->aabb.p, ctx->vel32.p, ctx->bounds.p,
                             ctx->ref64.p, ctx->ref32.p, s);
@@ -650,16 +710,18 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
         // the mixed path's kinematics rows need only the world facets: they
         // run on a second stream beside the hierarchy build and visibility
         if (path == BART_PATH_MIXED) {
+            nv.next("bart kinematics rows");
             CUDA_TRY(cudaEventRecord(ctx->fork_ev, s), "cudaEventRecord");
             CUDA_TRY(cudaStreamWaitEvent(ctx->side, ctx->fork_ev, 0), "cudaStreamWaitEvent");
             if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_kin[0], ctx->side), "cudaEventRecord");
-            launch_kin_coef(ctx->c64.p, ctx->fac.p, ctx->vel64.p, F, rd, ctx->kin.p,
+            launch_kin_coef(ctx->c64.p, ctx->fac.p, ctx->vel64.p, ctx->ref64.p, F, rd, ctx->kin.p,
                             ctx->kquad.p, ctx->side);
             if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_kin[1], ctx->side), "cudaEventRecord");
             CUDA_TRY(cudaEventRecord(ctx->join_ev, ctx->side), "cudaEventRecord");
         }
         // 2. LBVH (batched scenes: one hierarchy with a subtree per scene)
         SceneSplit split;
+        nv.next("bart bvh");
         if (B > 1) {
             launch_lbvh_batched(ctx->fac.p, F, ctx->bounds.p, ctx->d_foff.p, B, ctx->keys.p,
                                 ctx->vals.p, ctx->keys_tmp.p, ctx->vals_tmp.p, ctx->sort_temp.p,
@@ -682,7 +744,9 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
         launches += F >= 2 ? 1 : 0;
         if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[2], s), "cudaEventRecord");
         // 3. visibility + per-channel lit lists (+ their per-scene ranges)
-        launch_visibility(ctx->tri64.p, ctx->tri32.p, ctx->c64.p, ctx->fac.p, ctx->nodes.p,
+        nv.next("bart visibility");
+        launch_visibility(ctx->tri64.p, ctx->tri32.p, ctx->c64.p, ctx->fac.p, ctx->ref64.p,
+                          ctx->nodes.p,
                           F >= 2 ? ctx->vals.p : nullptr, F, rd, split, ctx->state.p,
                           ctx->counters.p + 3, ctx->status.p, s);
         launch_compact(ctx->state.p, F, rd, ctx->blk_cnt.p, ctx->vis_idx.p, ctx->vis_cnt.p, s);
@@ -694,6 +758,7 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
         }
         if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[3], s), "cudaEventRecord");
         // 4. synthesis
+        nv.next("bart synthesis");
         SynthArgs a;
         a.fac = ctx->fac.p;
         a.tri64 = ctx->tri64.p;
@@ -882,6 +947,8 @@ static int run_adjoint(bart_ctx *ctx, double t0, const void *grad_adc, int32_t d
     if (!ctx || !grad_adc || !grad_verts) return fail(BART_EINVAL, "%s: NULL argument", name);
     if (dtype != BART_C64 && dtype != BART_C128)
         return fail(BART_EINVAL, "%s: dtype=%d", name, dtype);
+    if (ctx->have_radar && ctx->radar.far_field)
+        return fail(BART_EINVAL, "%s: not available in far-field mode", name);
     ctx->adj_grad = grad_adc;
     ctx->adj_grad_c64 = dtype == BART_C64;
     ctx->adj_gverts = grad_verts;
@@ -1024,6 +1091,8 @@ static int run_rdm(bart_ctx *ctx, const void *adc, int32_t dtype, float *rdm)
         BART_TRY(ensure_events(ctx->ev, 7));
         CUDA_TRY(cudaEventRecord(ctx->ev[5], ctx->stream), "cudaEventRecord");
     }
+    Stages nv;
+    nv.next("bart rdm");
     launch_rdm(adc, dtype, rd, groups, ctx->rdm_ws.p, rdm, ctx->stream);
     CUDA_TRY(cudaGetLastError(), "rdm launch");
     if (ctx->timing) {
@@ -1112,6 +1181,8 @@ int bart_detect(bart_ctx *ctx, const void *adc, int32_t dtype, const bart_detect
         BART_TRY(ensure_events(ctx->ev, 9));
         CUDA_TRY(cudaEventRecord(ctx->ev[7], ctx->stream), "cudaEventRecord");
     }
+    Stages nv;
+    nv.next("bart detect");
     ctx->detect_launches = launch_detect(adc, dtype, rd, dd, b, points, max_points, ctx->stream);
     CUDA_TRY(cudaGetLastError(), "bart_detect launch");
     if (rdm)
@@ -1216,7 +1287,7 @@ int bart_frame_host(bart_ctx *ctx, double t0, int32_t path, float *rdm_host, bar
     return BART_OK;
 }
 
-int bart_get_visibility(bart_ctx *ctx, uint8_t *state)
+int bart_get_visibility(bart_ctx *ctx, uint8_t *state, int64_t *n_grazing)
 {
     g_err.clear();
     if (!ctx || !state) return fail(BART_EINVAL, "bart_get_visibility: NULL argument");
@@ -1224,6 +1295,13 @@ int bart_get_visibility(bart_ctx *ctx, uint8_t *state)
     BART_TRY(set_device(ctx));
     CUDA_TRY(cudaMemcpyAsync(state, ctx->state.p, (size_t)ctx->frame_A * ctx->frame_F,
                              cudaMemcpyDeviceToDevice, ctx->stream), "state copy");
+    if (n_grazing) {
+        unsigned long long g = 0;
+        CUDA_TRY(cudaMemcpyAsync(&g, ctx->counters.p + 3, sizeof g, cudaMemcpyDeviceToHost,
+                                 ctx->stream), "grazing count copy");
+        CUDA_TRY(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+        *n_grazing = (int64_t)g;
+    }
     return BART_OK;
 }
 

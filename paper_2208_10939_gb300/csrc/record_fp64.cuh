@@ -12,7 +12,9 @@
 //   [6..]  d:  form coefficients (vertex / series / edge, see synth.cu)
 // Per-facet delay form: qt, qr from the facet centroid, ls = 0.  Reference-
 // point form (Eqs. 11-13 per target): qt, qr from the instance origin and
-// ls = L_facet - L_origin at the chirp start.
+// ls = L_facet - L_origin at the chirp start.  Far field: directions, ranges
+// and qt, qr from the instance origin, ls = -(t + r).(c - origin), the
+// plane-wave path shift (the residual video phase then uses L(t) + ls too).
 #pragma once
 
 #include "bart_internal.cuh"
@@ -62,17 +64,27 @@ __device__ __forceinline__ Dual sqrt_s(Dual a)
 __device__ __forceinline__ double val(double a) { return a; }
 __device__ __forceinline__ double val(Dual a) { return a.v; }
 
+// delay forms of build_record
+constexpr int kDelayFacet = 0;      // spherical waves from the facet centroid
+constexpr int kDelayRef = 1;        // reference-point form (Eqs. 11-13 per target)
+constexpr int kDelayFarField = 2;   // plane waves from the instance origin
+
+__device__ __forceinline__ double abs_s(double a) { return fabs(a); }
+__device__ __forceinline__ Dual abs_s(Dual a) { return a.v < 0.0 ? -a : a; }
+
 // Builds the record of one facet for channel antennas ptx/prx at chirp time
 // tn.  tri: world vertices at t0 (9), c0: the stored centroid at t0 (3), vel:
-// instance velocity, rho: reflectivity, ref: the instance origin at t0 for
-// the reference-point delay form (NULL: per-facet form).  Returns the form
+// instance velocity, rho: reflectivity, form: kDelay*, ref: the instance
+// origin at t0 (used by the reference-point and far-field forms), two_sided:
+// obliquity |n.(t + r)|/2 (the side the antennas light).  Returns the form
 // (kRec*), the sinc flags of the edge form in *flags.  Branches depend on
 // values only, so the double and dual builds take the same path.
 template <typename Sc>
 __device__ __forceinline__ int build_record(const Sc *tri, const Sc *c0, const double *vel,
                                             double tn, const double *ptx, const double *prx,
                                             Sc rho, int intra, double k0, double kmax,
-                                            const double *ref, Sc *out, int *flags)
+                                            int form, const double *ref, int two_sided, Sc *out,
+                                            int *flags)
 {
     Sc cc[3], dv[9];
     for (int r = 0; r < 3; ++r) cc[r] = c0[r];
@@ -85,19 +97,31 @@ __device__ __forceinline__ int build_record(const Sc *tri, const Sc *c0, const d
     const Sc nl = sqrt_s(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
     const Sc area = 0.5 * nl;
     for (int r = 0; r < 3; ++r) nn[r] = nn[r] / nl;
+    // the instance origin at the chirp start (a constant of the facet
+    // parameters) and the channel's vectors from it
+    double gt[3] = {0.0, 0.0, 0.0}, gr[3] = {0.0, 0.0, 0.0}, ro[3] = {0.0, 0.0, 0.0};
+    if (form != kDelayFacet)
+        for (int r = 0; r < 3; ++r) {
+            ro[r] = ref[r] + vel[r] * tn;
+            gt[r] = ptx[r] - ro[r];
+            gr[r] = prx[r] - ro[r];
+        }
+    const double qt0 = gt[0] * gt[0] + gt[1] * gt[1] + gt[2] * gt[2];
+    const double qr0 = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
     Sc dt[3], dr[3];
     for (int r = 0; r < 3; ++r) {
-        dt[r] = ptx[r] - cc[r];
-        dr[r] = prx[r] - cc[r];
+        dt[r] = form == kDelayFarField ? Sc(gt[r]) : ptx[r] - cc[r];
+        dr[r] = form == kDelayFarField ? Sc(gr[r]) : prx[r] - cc[r];
     }
     const Sc Rt2 = dt[0] * dt[0] + dt[1] * dt[1] + dt[2] * dt[2];
     const Sc Rr2 = dr[0] * dr[0] + dr[1] * dr[1] + dr[2] * dr[2];
     const Sc Rt = sqrt_s(Rt2), Rr = sqrt_s(Rr2);
     Sc b[3];
     for (int r = 0; r < 3; ++r) b[r] = dt[r] / Rt + dr[r] / Rr;
-    const Sc ok = 0.5 * (nn[0] * b[0] + nn[1] * b[1] + nn[2] * b[2]);
+    Sc ok = 0.5 * (nn[0] * b[0] + nn[1] * b[1] + nn[2] * b[2]);
+    if (two_sided) ok = abs_s(ok);
     const Sc g = rho * ok / (Rt * Rr);
-    if (!ref) {
+    if (form == kDelayFacet) {
         out[0] = Rt2;
         out[3] = Rr2;
         out[kRecLs] = Sc(0.0);
@@ -106,19 +130,15 @@ __device__ __forceinline__ int build_record(const Sc *tri, const Sc *c0, const d
             out[4] = -2.0 * (dr[0] * vel[0] + dr[1] * vel[1] + dr[2] * vel[2]);
         }
     } else {
-        // the instance origin at the chirp start (a constant of the facet
-        // parameters): its path polynomial, and the facet's offset from it
-        double gt[3], gr[3];
-        for (int r = 0; r < 3; ++r) {
-            const double o = ref[r] + vel[r] * tn;
-            gt[r] = ptx[r] - o;
-            gr[r] = prx[r] - o;
-        }
-        const double qt0 = gt[0] * gt[0] + gt[1] * gt[1] + gt[2] * gt[2];
-        const double qr0 = gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2];
+        // the origin's path polynomial; the facet enters through ls
         out[0] = Sc(qt0);
         out[3] = Sc(qr0);
-        out[kRecLs] = (Rt + Rr) - (::sqrt(qt0) + ::sqrt(qr0));
+        if (form == kDelayRef) {
+            out[kRecLs] = (Rt + Rr) - (::sqrt(qt0) + ::sqrt(qr0));
+        } else {
+            out[kRecLs] = -(b[0] * (cc[0] - ro[0]) + b[1] * (cc[1] - ro[1]) +
+                            b[2] * (cc[2] - ro[2]));
+        }
         if (intra) {
             out[1] = Sc(-2.0 * (gt[0] * vel[0] + gt[1] * vel[1] + gt[2] * vel[2]));
             out[4] = Sc(-2.0 * (gr[0] * vel[0] + gr[1] * vel[1] + gr[2] * vel[2]));

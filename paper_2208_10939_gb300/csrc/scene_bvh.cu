@@ -101,7 +101,8 @@ __global__ void build_facets_kernel(const MeshDesc *__restrict__ meshes,
         rec.n[2] = (float)(nz * inl);
         rec.rho = m.rho ? m.rho[j] * in.rho_scale : in.rho_scale;
         rec.inst = lo;
-        rec.pad[0] = rec.pad[1] = 0.f;
+        rec.two_sided = m.two_sided;
+        rec.pad = 0.f;
         fac[f] = rec;
         // conservative FP32 box: outward rounding plus a pad covering the
         // FP32 slab test of a segment of <= ~200 m length

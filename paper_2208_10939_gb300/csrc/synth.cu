@@ -70,37 +70,56 @@ constexpr int kKinRow = kKinMaxDeg + 1;    // float4 per antenna-facet row
 // Rows are formed for every facet that is not certainly back-facing (a
 // superset of the lit ones): the kernel then needs only the world facets and
 // runs beside the hierarchy build and visibility.  The facing decision is
-// the visibility kernel's FP32 pre-test: |cos32 - cos| < 6e-7.
+// the visibility kernel's FP32 pre-test: |cos32 - cos| < 6e-7 (two-sided
+// facets always get rows).
+// Far field: the row is the facet's plane-wave path from the instance
+// origin r, g(t) = |r(t) - p_a| + l(t) / |r(t) - p_a| with
+// l(t) = (r(t) - p_a).(c_k - r), expanded from the series of R = |r - p_a|
+// and of 1/R (b_0 = 1/a_0, b_j = -sum_{i=1}^{j} a_i b_{j-i} / a_0).
 __global__ void kin_coef_kernel(const double *__restrict__ c64, const FacetRec *__restrict__ fac,
-                                const double *__restrict__ vel64, int64_t F, RadarDev rd,
+                                const double *__restrict__ vel64,
+                                const double *__restrict__ ref64, int64_t F, RadarDev rd,
                                 float4 *__restrict__ coef, double *__restrict__ quad)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int a = blockIdx.y;
     if (k >= F) return;
-    {
-        const float D0 = (float)(rd.ant[a][0] - c64[3 * k]);
-        const float D1 = (float)(rd.ant[a][1] - c64[3 * k + 1]);
-        const float D2 = (float)(rd.ant[a][2] - c64[3 * k + 2]);
+    const int inst = fac[k].inst;
+    const double *from = rd.far_field ? ref64 + 3 * inst : c64 + 3 * k;
+    if (!fac[k].two_sided) {
+        const float D0 = (float)(rd.ant[a][0] - from[0]);
+        const float D1 = (float)(rd.ant[a][1] - from[1]);
+        const float D2 = (float)(rd.ant[a][2] - from[2]);
         const float dd = fmaf(D0, D0, fmaf(D1, D1, D2 * D2));
         const float cs = fmaf(fac[k].n[0], D0, fmaf(fac[k].n[1], D1, fac[k].n[2] * D2)) *
                          rsqrtf(dd);
-        if (dd > 0.f && cs <= -((float)kEpsFace + 2e-6f)) return;   // certainly BACK
+        if (dd > 0.f && cs <= -((float)rd.eps_face + 2e-6f)) return;   // certainly BACK
     }
-    const int inst = fac[k].inst;
     const double vx = vel64[3 * inst], vy = vel64[3 * inst + 1], vz = vel64[3 * inst + 2];
-    const double dx = c64[3 * k] - rd.ant[a][0];
-    const double dy = c64[3 * k + 1] - rd.ant[a][1];
-    const double dz = c64[3 * k + 2] - rd.ant[a][2];
+    const double dx = from[0] - rd.ant[a][0];
+    const double dy = from[1] - rd.ant[a][1];
+    const double dz = from[2] - rd.ant[a][2];
     const double A = dx * dx + dy * dy + dz * dz;
     const double B = 2.0 * (dx * vx + dy * vy + dz * vz);
     const double Cq = vx * vx + vy * vy + vz * vz;
+    // far field: l(t) = l0 + l1 t, the facet's offset from the origin
+    // projected on r(t) - p_a
+    double l0 = 0.0, l1 = 0.0, doff = 0.0;
+    if (rd.far_field) {
+        const double ox = c64[3 * k] - from[0], oy = c64[3 * k + 1] - from[1],
+                     oz = c64[3 * k + 2] - from[2];
+        l0 = dx * ox + dy * oy + dz * oz;
+        l1 = vx * ox + vy * oy + vz * oz;
+        doff = sqrt(ox * ox + oy * oy + oz * oz);
+    }
     const double f0c = rd.f0 / kC0;
     const int64_t row = (int64_t)a * F + k;
-    double *qd = quad + 3 * row;
+    double *qd = quad + kKinQuadWords * row;
     qd[0] = A;
     qd[1] = B;
     qd[2] = Cq;
+    qd[3] = l0;
+    qd[4] = l1;
     // expansion point: the middle chirp slot; tau in slots
     const double sc = 0.5 * (double)(rd.N * rd.slots - 1);
     const double tc = sc * rd.Tc;
@@ -111,7 +130,7 @@ __global__ void kin_coef_kernel(const double *__restrict__ c64, const FacetRec *
     const double rho = tmax * sqrt(q2 / q0);
     int deg = -1;
     if (rho < 0.25) {
-        double bound = a0 * rho * rho / (1.0 - rho);
+        double bound = (a0 + doff) * rho * rho / (1.0 - rho);
         for (int d = 1; d <= kKinMaxDeg; ++d, bound *= rho)
             if (bound <= 1e-11) { deg = d; break; }
     }
@@ -131,6 +150,21 @@ __global__ void kin_coef_kernel(const double *__restrict__ c64, const FacetRec *
         for (int l = 1; l < j; ++l) sacc -= aj[l] * aj[j - l];
         aj[j] = sacc * inv2a0;
     }
+    if (rd.far_field) {
+        // g = R + (L0 + L1 tau) / R, tau in slots about the middle one
+        const double L0 = l0 + l1 * tc, L1 = l1 * rd.Tc;
+        double bj[kKinMaxDeg + 1];
+        bj[0] = 1.0 / a0;
+#pragma unroll
+        for (int j = 1; j <= kKinMaxDeg; ++j) {
+            double sacc = 0.0;
+#pragma unroll
+            for (int i = 1; i <= j; ++i) sacc += aj[i] * bj[j - i];
+            bj[j] = -sacc * bj[0];
+        }
+#pragma unroll
+        for (int j = kKinMaxDeg; j >= 0; --j) aj[j] += L0 * bj[j] + (j > 0 ? L1 * bj[j - 1] : 0.0);
+    }
     // rows above the degree are zero, so two rows of different degrees can
     // share one Horner loop
     for (int j = 0; j <= kKinMaxDeg; ++j) {
@@ -145,12 +179,13 @@ __global__ void kin_coef_kernel(const double *__restrict__ c64, const FacetRec *
     }
 }
 
-void launch_kin_coef(const double *c64, const FacetRec *fac, const double *vel64, int64_t F,
-                     const RadarDev &rd, float4 *coef, double *quad, cudaStream_t s)
+void launch_kin_coef(const double *c64, const FacetRec *fac, const double *vel64,
+                     const double *ref64, int64_t F, const RadarDev &rd, float4 *coef,
+                     double *quad, cudaStream_t s)
 {
     const int T = 128;
     dim3 grid((unsigned int)((F + T - 1) / T), (unsigned int)rd.A);
-    kin_coef_kernel<<<grid, T, 0, s>>>(c64, fac, vel64, F, rd, coef, quad);
+    kin_coef_kernel<<<grid, T, 0, s>>>(c64, fac, vel64, ref64, F, rd, coef, quad);
 }
 
 // double-float helpers: values xh + xl with |xl| <= ulp(xh) / 2; every
@@ -188,12 +223,14 @@ __device__ __forceinline__ float4 kin_finish(float xh, float xl, float R, float 
     return make_float4(x0, hi, lo, R);
 }
 
-// a row without a convergent expansion: FP64 square root at slot s
+// a row without a convergent expansion: FP64 square root at slot s (far
+// field: R + l / R)
 __device__ __forceinline__ float4 kin_fallback(const double *__restrict__ quad, int s, double Tc,
                                                double f0c, double mu_f0)
 {
     const double t = (double)s * Tc;
-    const double R = sqrt(quad[0] + t * (quad[1] + t * quad[2]));
+    double R = sqrt(quad[0] + t * (quad[1] + t * quad[2]));
+    R += (quad[3] + t * quad[4]) / R;
     const double x0u = R * f0c;
     double x1 = x0u * mu_f0;
     x1 -= floor(x1);
@@ -396,8 +433,8 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
     const float tau_s = (float)sl - K.s_mid;
     const float4 *kin_t = A.kin + (int64_t)tx * F * kKinRow;
     const float4 *kin_r = A.kin + (int64_t)(P + rx) * F * kKinRow;
-    const double *quad_t = A.kquad + (int64_t)tx * F * 3;
-    const double *quad_r = A.kquad + (int64_t)(P + rx) * F * 3;
+    const double *quad_t = A.kquad + (int64_t)tx * F * kKinQuadWords;
+    const double *quad_r = A.kquad + (int64_t)(P + rx) * F * kKinQuadWords;
 
     for (int base = rbeg; base < rend; base += LPR) {
         // ---------------- build one record per lane ----------------
@@ -410,24 +447,48 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
             const float4 vv = reinterpret_cast<const float4 *>(A.vel32)[fr.inst];
             float4 kt, kr;
             kin_eval2(kin_t + (int64_t)k * kKinRow, kin_r + (int64_t)k * kKinRow,
-                      quad_t + 3 * (int64_t)k, quad_r + 3 * (int64_t)k, sl, tau_s, A.rd.Tc,
+                      quad_t + kKinQuadWords * (int64_t)k, quad_r + kKinQuadWords * (int64_t)k,
+                      sl, tau_s, A.rd.Tc,
                       K.f0c_d, K.mu_f0_d, K.mfh, K.mfl, kt, kr);
-            const float cx = fmaf(vv.x, tn, fr.c[0]);
-            const float cy = fmaf(vv.y, tn, fr.c[1]);
-            const float cz = fmaf(vv.z, tn, fr.c[2]);
-            float th[3] = {ptx[0] - cx, ptx[1] - cy, ptx[2] - cz};
-            float rh[3] = {prx[0] - cx, prx[1] - cy, prx[2] - cz};
-            const float it = rsqrtf(th[0] * th[0] + th[1] * th[1] + th[2] * th[2]);
-            const float ir = rsqrtf(rh[0] * rh[0] + rh[1] * rh[1] + rh[2] * rh[2]);
+            // directions t, r and the amplitude's ranges: from the facet
+            // centroid, or (far field) from the instance origin, whose
+            // plane waves every facet of the instance sees
+            float th[3], rh[3], Rt, Rr;
+            if (A.rd.far_field) {
+                const float4 rf = reinterpret_cast<const float4 *>(A.ref32)[fr.inst];
+                const float ox = fmaf(vv.x, tn, rf.x), oy = fmaf(vv.y, tn, rf.y),
+                            oz = fmaf(vv.z, tn, rf.z);
+                th[0] = ptx[0] - ox; th[1] = ptx[1] - oy; th[2] = ptx[2] - oz;
+                rh[0] = prx[0] - ox; rh[1] = prx[1] - oy; rh[2] = prx[2] - oz;
+                Rt = sqrtf(th[0] * th[0] + th[1] * th[1] + th[2] * th[2]);
+                Rr = sqrtf(rh[0] * rh[0] + rh[1] * rh[1] + rh[2] * rh[2]);
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    th[r] /= Rt;
+                    rh[r] /= Rr;
+                }
+            } else {
+                const float cx = fmaf(vv.x, tn, fr.c[0]);
+                const float cy = fmaf(vv.y, tn, fr.c[1]);
+                const float cz = fmaf(vv.z, tn, fr.c[2]);
+                th[0] = ptx[0] - cx; th[1] = ptx[1] - cy; th[2] = ptx[2] - cz;
+                rh[0] = prx[0] - cx; rh[1] = prx[1] - cy; rh[2] = prx[2] - cz;
+                const float it = rsqrtf(th[0] * th[0] + th[1] * th[1] + th[2] * th[2]);
+                const float ir = rsqrtf(rh[0] * rh[0] + rh[1] * rh[1] + rh[2] * rh[2]);
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    th[r] *= it;
+                    rh[r] *= ir;
+                }
+                Rt = kt.w;
+                Rr = kr.w;
+            }
             float b[3];
 #pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                th[r] *= it;
-                rh[r] *= ir;
-                b[r] = th[r] + rh[r];
-            }
-            const float Rt = kt.w, Rr = kr.w, L = Rt + Rr;
-            const float o_k = 0.5f * (fr.n[0] * b[0] + fr.n[1] * b[1] + fr.n[2] * b[2]);
+            for (int r = 0; r < 3; ++r) b[r] = th[r] + rh[r];
+            const float L = kt.w + kr.w;            // the facet's path at the chirp start
+            float o_k = 0.5f * (fr.n[0] * b[0] + fr.n[1] * b[1] + fr.n[2] * b[2]);
+            if (fr.two_sided) o_k = fabsf(o_k);    // the side both antennas light
             const float g = __fdividef(fr.rho * o_k, Rt * Rr);
             // in-plane part of b, formed once: u_v, |b_t|^2 and n x b_t all derive
             // from it, so every form evaluates J exactly at one wave vector
@@ -441,6 +502,7 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
             // the delay's motion within the chirp and the residual video phase
             // follow the facet centroid, or (reference-point form) the
             // instance origin: path Lp, its first and second time derivatives
+            // (far field: the origin's motion, the facet's plane-wave path)
             float Lp = L, Ld = 0.f, Ldd = 0.f;
             {
                 float ut[3] = {th[0], th[1], th[2]}, ur[3] = {rh[0], rh[1], rh[2]};
@@ -1023,10 +1085,10 @@ synth_fp64_kernel(SynthArgs A, int W, int NCH)
             for (int i = 0; i < 9; ++i) tri[i] = A.tri64[9 * k + i];
             for (int r = 0; r < 3; ++r) c0[r] = A.c64[3 * k + r];
             int flags = 0;
-            cls = R.kind = build_record<double>(tri, c0, vel, tn, ptx, prx, (double)A.fac[k].rho,
-                                                A.rd.intra, k0, kmax,
-                                                A.rd.delay_ref ? A.ref64 + 3 * inst : nullptr,
-                                                rec, &flags);
+            cls = R.kind = build_record<double>(
+                tri, c0, vel, tn, ptx, prx, (double)A.fac[k].rho, A.rd.intra, k0, kmax,
+                A.rd.far_field ? kDelayFarField : A.rd.delay_ref ? kDelayRef : kDelayFacet,
+                A.ref64 + 3 * inst, A.fac[k].two_sided, rec, &flags);
             R.flags = flags;
             R.qt[0] = rec[0];
             R.qt[1] = rec[1];
@@ -1058,7 +1120,10 @@ synth_fp64_kernel(SynthArgs A, int W, int NCH)
                                  sqrt(R.qr[0] + t * (R.qr[1] + t * R.qt[2]));
                 const double fmc = fm * inv_c;
                 const double kp = fm * inv_f0;
-                double thc = fmc * (L + R.ls) - mu_2c2 * L * L;
+                // residual video phase: the origin's path (reference-point
+                // form), else the facet's own, plane-wave in the far field
+                const double Lv = A.rd.far_field ? L + R.ls : L;
+                double thc = fmc * (L + R.ls) - mu_2c2 * Lv * Lv;
                 thc -= rint(thc);
                 double re = 0.0, im = 0.0;
                 if (R.kind == kRecVertex) {

@@ -3,7 +3,11 @@
 // TX and seen from the RX.  Each (antenna, facet) pair gets a state from the
 // facet-centroid -> antenna segment cast through the LBVH:
 //   BACK  (facing away), LIT, GRAZE (within margins: excluded, counted),
-//   OCCL  (a robust hit on another facet).
+//   OCCL  (a robust hit on another facet), LIT_REV (a two-sided facet lit on
+//   its reverse side).
+// In far-field mode the segment ends at p_a + (c_k - r), r the instance
+// origin at the frame start: every facet of an instance looks along the same
+// plane-wave direction, over the origin's range.
 // The segment/triangle decision is Moller-Trumbore (1997) in FP64 with one
 // IEEE rounding per operation in a fixed order (explicit __d*_rn intrinsics:
 // no FMA contraction), so states are reproducible bit for bit by any
@@ -147,7 +151,7 @@ constexpr int kStack = 64;
 __global__ void __launch_bounds__(128)
 visibility_kernel(const double *__restrict__ tri64, const float4 *__restrict__ tri32,
                   const double *__restrict__ c64, const FacetRec *__restrict__ fac,
-                  const BvhNode *__restrict__ nodes,
+                  const double *__restrict__ ref64, const BvhNode *__restrict__ nodes,
                   const int32_t *__restrict__ order, int64_t F, RadarDev rd, SceneSplit sc,
                   uint8_t *__restrict__ state, unsigned long long *n_graze, int *status)
 {
@@ -159,18 +163,23 @@ visibility_kernel(const double *__restrict__ tri64, const float4 *__restrict__ t
         // start close together and traverse similar BVH paths
         const int64_t k = order ? (int64_t)order[gid] : gid;
         const double c[3] = {c64[3 * k], c64[3 * k + 1], c64[3 * k + 2]};
-        const double pa[3] = {rd.ant[a][0], rd.ant[a][1], rd.ant[a][2]};
+        double pa[3] = {rd.ant[a][0], rd.ant[a][1], rd.ant[a][2]};
+        if (rd.far_field) {                 // end = p_a + (c - r): the plane-wave segment
+            const double *r0 = ref64 + 3 * fac[k].inst;
+            for (int r = 0; r < 3; ++r) pa[r] = __dadd_rn(pa[r], __dsub_rn(c[r], r0[r]));
+        }
         double D[3];
         sub3(pa, c, D);
         const float Df[3] = {(float)D[0], (float)D[1], (float)D[2]};
         // FP32 pre-test of the facing test below.  n32 is the unit normal
         // formed in FP64 and rounded (error < 2e-7), Df the rounded segment
         // (relative error 2^-24 per component); with the dot product's and
-        // rsqrt's rounding, |cos32 - cos| < 6e-7, so beyond +-(kEpsFace + 2e-6)
+        // rsqrt's rounding, |cos32 - cos| < 6e-7, so beyond +-(eps_face + 2e-6)
         // the FP64 decision is certain.  Slivers (2A below 1e-6 of the
         // squared edge scale), whose FP64 normal direction is ill-conditioned,
         // always take the FP64 test.
-        int face = 1;                                  // 0 back, 2 front, 1 undecided
+        const bool two = fac[k].two_sided != 0;
+        int face = 1;                        // 0 back, 2 front, 3 reverse (two-sided), 1 undecided
         {
             const FacetRec *fr = fac + k;
             const float n0 = fr->n[0], n1 = fr->n[1], n2 = fr->n[2];
@@ -182,10 +191,10 @@ visibility_kernel(const double *__restrict__ tri64, const float4 *__restrict__ t
             }
             const float dd = fmaf(Df[0], Df[0], fmaf(Df[1], Df[1], Df[2] * Df[2]));
             const float cos32 = fmaf(n0, Df[0], fmaf(n1, Df[1], n2 * Df[2])) * rsqrtf(dd);
-            constexpr float thr = (float)kEpsFace + 2e-6f;
+            const float thr = (float)rd.eps_face + 2e-6f;
             if (2.f * fr->area >= 4e-6f * L2 && dd > 0.f) {
                 if (cos32 >= thr) face = 2;
-                else if (cos32 <= -thr) face = 0;
+                else if (cos32 <= -thr) face = two ? 3 : 0;
             }
         }
         uint8_t st;
@@ -200,8 +209,9 @@ visibility_kernel(const double *__restrict__ tri64, const float4 *__restrict__ t
             cross3(e1, e2, n);
             const double cosang = __ddiv_rn(
                 dot3(n, D), __dmul_rn(__dsqrt_rn(dot3(n, n)), __dsqrt_rn(dot3(D, D))));
-            if (dot3(n, n) == 0.0 || cosang <= -kEpsFace) face = 0;   // zero area: no normal
-            else graze = fabs(cosang) < kEpsFace;
+            if (dot3(n, n) == 0.0) face = 0;                  // zero area: no normal
+            else if (cosang <= -rd.eps_face) face = two ? 3 : 0;
+            else graze = fabs(cosang) < rd.eps_face;
         }
         if (face == 0) {
             st = BART_VIS_BACK;
@@ -264,7 +274,8 @@ visibility_kernel(const double *__restrict__ tri64, const float4 *__restrict__ t
                     }
                 }
             }
-            st = hit ? BART_VIS_OCCL : (graze ? BART_VIS_GRAZE : BART_VIS_LIT);
+            st = hit ? BART_VIS_OCCL
+                     : (graze ? BART_VIS_GRAZE : (face == 3 ? BART_VIS_LIT_REV : BART_VIS_LIT));
         }
         state[(int64_t)a * F + k] = st;
         graze_flag = (st == BART_VIS_GRAZE);
@@ -274,20 +285,22 @@ visibility_kernel(const double *__restrict__ tri64, const float4 *__restrict__ t
 }
 
 void launch_visibility(const double *tri64, const float *tri32, const double *c64,
-                       const FacetRec *fac, const BvhNode *nodes, const int32_t *order, int64_t F, const RadarDev &rd,
+                       const FacetRec *fac, const double *ref64, const BvhNode *nodes,
+                       const int32_t *order, int64_t F, const RadarDev &rd,
                        const SceneSplit &sc, uint8_t *state, unsigned long long *n_graze,
                        int *status, cudaStream_t s)
 {
     const int T = 128;
     dim3 grid((unsigned int)((F + T - 1) / T), (unsigned int)rd.A);
     visibility_kernel<<<grid, T, 0, s>>>(tri64, reinterpret_cast<const float4 *>(tri32), c64,
-                                         fac, nodes, order, F, rd, sc, state, n_graze, status);
+                                         fac, ref64, nodes, order, F, rd, sc, state, n_graze,
+                                         status);
 }
 
 // -------------------------------------------------------------------------
 // compaction into ascending facet lists: list l < O holds the facets lit
-// from TX p AND RX q of channel l = p Q + q; list O + a holds the facets lit
-// from antenna a (used by the kinematics)
+// from TX p AND RX q of channel l = p Q + q on the same side (both LIT, or
+// both LIT_REV); list O + a holds the facets lit from antenna a
 // -------------------------------------------------------------------------
 constexpr int kCompactBlk = 1024;
 
@@ -296,10 +309,13 @@ int64_t compact_blk_words(int64_t F, int L) { return (int64_t)L * ((F + kCompact
 __device__ __forceinline__ bool in_list(const uint8_t *state, int64_t F, int l, int O, int P,
                                         int Q, int64_t k)
 {
-    if (l >= O) return state[(int64_t)(l - O) * F + k] == BART_VIS_LIT;
+    if (l >= O) {
+        const uint8_t s = state[(int64_t)(l - O) * F + k];
+        return s == BART_VIS_LIT || s == BART_VIS_LIT_REV;
+    }
     const int p = l / Q, q = l % Q;
-    return state[(int64_t)p * F + k] == BART_VIS_LIT &&
-           state[(int64_t)(P + q) * F + k] == BART_VIS_LIT;
+    const uint8_t st = state[(int64_t)p * F + k], sr = state[(int64_t)(P + q) * F + k];
+    return st == sr && (st == BART_VIS_LIT || st == BART_VIS_LIT_REV);
 }
 
 __global__ void compact_count_kernel(const uint8_t *__restrict__ state, int64_t F, int O, int P,

@@ -42,6 +42,7 @@ class Mesh:
     tris: np.ndarray               # (nf, 3) int32
     rho: np.ndarray                # (nf,)  float32 reflectivity (1 = PEC)
     name: str = "mesh"
+    two_sided: bool = False        # facets scatter from both sides (open surfaces)
 
     def __post_init__(self):
         self.verts = np.ascontiguousarray(self.verts, dtype=np.float64)
@@ -90,6 +91,8 @@ class Radar:
     intra_chirp_motion: bool = True
     tdm: bool = False              # time-division MIMO: TX p sends chirp n at (n P + p) Tc
     delay_ref: bool = False        # reference-point delay form (one tau(t) per instance)
+    far_field: bool = False        # plane waves from each instance origin, at its ranges
+    grazing_eps: float = 1e-6      # |cos| below which a facet grazes its antenna
 
     def __post_init__(self):
         self.tx = np.ascontiguousarray(np.asarray(self.tx, np.float64).reshape(-1, 3))
@@ -489,3 +492,9 @@ def flatten(scene: Scene):
             np.concatenate(inst_idx), np.concatenate(rho).astype(np.float32),
             np.ascontiguousarray(pos), np.ascontiguousarray(rot),
             np.ascontiguousarray(vel))
+
+
+def facet_two_sided(scene: Scene) -> np.ndarray:
+    """Per-facet two-sided flags (uint8) in the order of ``flatten``."""
+    return np.concatenate([np.full(scene.meshes[i.mesh_id].nf, int(scene.meshes[i.mesh_id].two_sided),
+                                   np.uint8) for i in scene.instances])

@@ -86,3 +86,9 @@ def test_null_arguments_are_rejected(lib):
     assert lib.bart_sync(None) == pkg.BART_EINVAL
     assert lib.bart_radar_set(None, None) == pkg.BART_EINVAL
     assert b"NULL" in lib.bart_last_error()
+
+
+def test_alloc_failure_injection_is_armed_and_disarmed_on_the_host(lib):
+    assert lib.bart_inject_alloc_failure(-1) == pkg.BART_EINVAL
+    assert lib.bart_inject_alloc_failure(3) == pkg.BART_OK
+    assert lib.bart_inject_alloc_failure(0) == pkg.BART_OK

@@ -190,12 +190,26 @@ def test_table2_replica(sim, M):
 
 def test_config1_beat_bin_and_closed_form(sim):
     """Config 1 on the GPU: the RDM peak sits at range bin 100 (Eq. 4), zero
-    Doppler; the oracle's far-field RCS of the same mesh is 4 pi A^2/lambda^2."""
+    Doppler; and the same plate in far-field mode, seen by a monostatic
+    antenna, gives the radar equation with sigma = 4 pi A^2 / lambda^2
+    (59.19 dBsm at 77 GHz) on every sample, to 1e-9 (FP64 path)."""
     sc, fr, ref = frame("plate_config1")
     sim.load_scene(sc)
     rdm = sim.rdm(sim.simulate(pkg.PATH_FP64)).cpu().numpy()
     r, d = np.unravel_index(np.argmax(rdm), rdm.shape)
     assert (r, d) == (100, sc.radar.N // 2)
+    ff = sg.plate_scene()
+    ff.radar = sg.make_radar(128, 64, 1, 1, 5.12e6, 30e12, 2.0, centre=(0.0, 0.0, 0.0))
+    ff.radar.far_field = True                          # monostatic: b normal to the plate
+    sim.load_scene(ff)
+    x = sim.simulate(pkg.PATH_FP64).cpu().numpy()[0]
+    rr = ff.radar
+    tm = np.arange(rr.M) / rr.fs
+    lam = sg.C0 / (rr.f0 + rr.slope * tm)
+    expect = np.sqrt(4 * np.pi / lam ** 2) * lam / ((4 * np.pi) ** 1.5 * 20.0 ** 2)
+    for n in range(rr.N):
+        np.testing.assert_allclose(np.abs(x[n]), expect, rtol=1e-9)
+    assert abs(10 * np.log10(4 * np.pi / (sg.C0 / 77e9) ** 2) - 59.19) < 0.01
 
 
 def test_intra_chirp_motion_off(sim):

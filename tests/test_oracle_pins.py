@@ -673,3 +673,149 @@ def test_reference_form_residual_video_phase_closed_form():
     expect = np.exp(-1j * np.pi * r.slope * (tau_r ** 2 - tau_k ** 2))
     assert abs(np.angle(expect)) > 0.1                 # a visible difference
     assert np.abs(ratio - expect).max() <= 1e-9
+
+
+# ---------------------------------------------------------------------------
+# far-field mode, two-sided facets, grazing threshold
+# ---------------------------------------------------------------------------
+def _far_radar(M=128, N=2, P=1, Q=1, slope=30e12, fs=5.12e6, **kw):
+    r = sg.make_radar(M, N, P, Q, fs, slope, tx_spacing_wl=2.0, centre=(0.0, 0.0, 0.0), **kw)
+    r.far_field = True
+    return r
+
+
+def test_far_field_plate_is_the_radar_equation_with_4piA2_over_lambda2():
+    """Far-field mode, 1 m plate (200 facets) centred on its origin 20 m away,
+    broadside, monostatic: every ADC sample is sqrt(P) of Eq. 7 with
+    sigma = 4 pi A^2 / lambda^2 (the facet integrals sum to the plate's
+    exactly under plane waves), and its phase is Eq. 13's with tau = 2R/c."""
+    r = _far_radar()
+    sc = sg.Scene([sg.plate(1.0, 1.0, 10)], [sg.Instance(0, (0, 20.0, 0), np.eye(3), (0, 0, 0))], r)
+    adc = oracle.Frame(sc).adc_full()
+    tm = np.arange(r.M) / r.fs
+    lam = C0 / (r.f0 + r.slope * tm)
+    sigma = 4 * np.pi * 1.0 / lam ** 2
+    amp = np.sqrt(sigma) * lam / ((4 * np.pi) ** 1.5 * 20.0 ** 2)
+    tau = 2 * 20.0 / C0
+    ph = 2 * np.pi * (r.f0 * tau + r.slope * tm * tau - 0.5 * r.slope * tau * tau)
+    for n in range(r.N):
+        np.testing.assert_allclose(np.abs(adc[0, n]), amp, rtol=1e-12)
+        assert np.max(np.abs(np.angle(adc[0, n] * np.exp(-1j * ph)))) < 1e-9
+
+
+def _sphere_far_field_sigma(adc, r, R):
+    tm = np.arange(r.M) / r.fs
+    lam = C0 / (r.f0 + r.slope * tm)
+    # |x|^2 = sigma lambda^2 / ((4 pi)^3 R^4)
+    return np.abs(adc) ** 2 * (4 * np.pi) ** 3 * R ** 4 / lam ** 2
+
+
+@pytest.mark.slow
+def test_far_field_sphere_band_averaged_pi_a2():
+    """Far-field mode, faceted sphere a = 0.1 m (20 480 facets) 15 m away: the
+    cross-section read off the ADC amplitude, averaged over the 0.75 GHz
+    sweep (one period of the sphere's sin(2ka)/(ka) ripple), is pi a^2
+    within 0.5 dB; convex, so far-field visibility lights exactly the
+    facets facing the plane wave."""
+    a, R = 0.1, 15.0
+    r = _far_radar(N=1)
+    sc = sg.Scene([sg.icosphere(a, 5)], [sg.Instance(0, (0, R, 0), np.eye(3), (0, 0, 0))], r)
+    fr = oracle.Frame(sc)
+    v = fr.tri0.reshape(-1, 3, 3)
+    n = np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0])
+    cos = (n @ np.array([0, -1.0, 0])) / np.linalg.norm(n, axis=1)
+    clear = np.abs(np.abs(cos) - oracle.EPS_FACE) > 1e-9
+    exp = np.where(cos >= oracle.EPS_FACE, oracle.LIT,
+                   np.where(cos <= -oracle.EPS_FACE, oracle.BACK, oracle.GRAZE))
+    assert np.array_equal(fr.state[0][clear], exp[clear])
+    sig = _sphere_far_field_sigma(fr.adc_full()[0, 0], r, R)
+    err_db = 10 * np.log10(sig.mean() / (np.pi * a * a))
+    assert abs(err_db) < 0.5, err_db
+
+
+def test_two_sided_plate_seen_from_behind_equals_flipped_plate():
+    """A two-sided plate whose outward normal faces away from the radar is
+    lit on its reverse side (LIT_REV) and scatters exactly like the same
+    plate with reversed winding seen from the front; one-sided it is BACK."""
+    radar = sg.make_radar(64, 3, 2, 2, 5.12e6, 30e12, 2.0, centre=(0.0, 0.0, 0.0))
+    rot = sg.rot_z(np.pi + 0.15)                          # normal turned away, oblique
+    inst = sg.Instance(0, (0.3, 9.0, 0.1), rot, (0.2, -3.0, 0.0))
+    base = sg.plate(0.3, 0.2, 3)
+    one = oracle.Frame(sg.Scene([base], [inst], radar))
+    assert (one.state == oracle.BACK).all()
+    two = sg.Mesh(base.verts, base.tris, base.rho, two_sided=True)
+    fr2 = oracle.Frame(sg.Scene([two], [inst], radar))
+    assert (fr2.state == oracle.LIT_REV).all()
+    flipped = sg.Mesh(base.verts, base.tris[:, ::-1], base.rho)
+    frf = oracle.Frame(sg.Scene([flipped], [inst], radar))
+    assert (frf.state == oracle.LIT).all()
+    a, b = fr2.adc_full(), frf.adc_full()
+    assert np.abs(a).max() > 0
+    assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
+
+
+def test_two_sided_facet_needs_both_antennas_on_one_side():
+    """TX in front of a two-sided plate and RX behind it: each antenna lights
+    one side (LIT / LIT_REV), so no channel sees the plate (no ray passes
+    through a facet); TX and RX behind it: the reverse side is seen."""
+    tx = np.array([[0.0, 0.0, 0.0]])
+    rx = np.array([[0.0, 20.0, 0.0], [0.5, 21.0, 0.0]])
+    radar = sg.Radar(f0=77e9, slope=30e12, fs=5.12e6, Tc=64 / 5.12e6 + 1e-5, M=64, N=2,
+                     tx=tx, rx=rx)
+    plate = sg.plate(0.2, 0.2, 2)
+    two = sg.Mesh(plate.verts, plate.tris, plate.rho, two_sided=True)
+    sc = sg.Scene([two], [sg.Instance(0, (0, 10.0, 0), np.eye(3), (0, 0, 0))], radar)
+    fr = oracle.Frame(sc)
+    assert (fr.state[0] == oracle.LIT).all() and (fr.state[1:] == oracle.LIT_REV).all()
+    assert not fr.lit_pairs().any()
+    assert np.abs(fr.adc_full()).max() == 0.0
+    radar2 = sg.Radar(f0=77e9, slope=30e12, fs=5.12e6, Tc=radar.Tc, M=64, N=2, tx=rx[:1], rx=rx)
+    fr2 = oracle.Frame(sg.Scene([two], sc.instances, radar2))
+    assert fr2.lit_pairs().all()
+
+
+def test_grazing_threshold_is_a_parameter():
+    """A facet whose normal makes cos = 5e-6 with the antenna direction is
+    LIT at the default threshold (1e-6) and GRAZE at 1e-5."""
+    c = 5e-6
+    s_ = math.sqrt(1 - c * c)
+    # triangle in the plane with unit normal n = (0, -c, s) ... seen from +Y far away
+    n = np.array([0.0, c, s_])
+    e1 = np.array([1.0, 0.0, 0.0])
+    e2 = np.cross(n, e1)
+    v0 = np.array([0.0, 10.0, 0.0])
+    tri = np.concatenate([v0, v0 + 0.01 * e1, v0 + 0.01 * e2])
+    c0 = tri.reshape(3, 3).mean(0)
+    ant = c0 + np.array([0.0, 100.0, 0.0])                   # along +Y from the centroid
+    tri = tri.reshape(1, 9)
+    assert oracle.visibility(tri, ant[None])[0, 0] == oracle.LIT
+    assert oracle.visibility(tri, ant[None], eps_face=1e-5)[0, 0] == oracle.GRAZE
+    assert oracle.visibility(tri, ant[None] * np.array([1, -1, 1]) + [0, 2 * c0[1], 0],
+                             eps_face=1e-5)[0, 0] == oracle.GRAZE
+
+
+def test_far_field_shadow_is_the_parallel_projection():
+    """Far-field visibility: a 2 m plate at y = 10 shadows part of a 1 m plate
+    at y = 12 along the plane-wave direction of the back plate's origin (a
+    parallel projection), not along rays to the antenna (a perspective one)."""
+    front, back = sg.plate(2.0, 2.0, 4), sg.plate(1.0, 1.0, 12)
+    r = _far_radar(M=32, N=1)
+    org = np.array([1.07, 12.0, 0.33])
+    sc = sg.Scene([front, back], [sg.Instance(0, (0, 10.0, 0), np.eye(3), (0, 0, 0)),
+                                  sg.Instance(1, org, np.eye(3), (0, 0, 0))], r)
+    fr = oracle.Frame(sc)
+    st = fr.state[0]
+    nf = front.nf
+    assert (st[:nf] == oracle.LIT).all()
+    c = fr.tri0[nf:].reshape(-1, 3, 3).mean(1)
+    d = (r.tx[0] - org) / np.linalg.norm(r.tx[0] - org)        # the plane-wave direction
+    s = (10.0 - c[:, 1]) / d[1]
+    hit = c + s[:, None] * d
+    inside = (np.abs(hit[:, 0]) < 1.0) & (np.abs(hit[:, 2]) < 1.0)
+    assert np.min(np.abs(np.abs(hit[:, [0, 2]]) - 1.0)) > 1e-6
+    assert inside.any() and (~inside).any()
+    assert np.array_equal(st[nf:], np.where(inside, oracle.OCCL, oracle.LIT))
+    # and it differs from the perspective shadow of the same scene
+    r.far_field = False
+    persp = oracle.Frame(sg.Scene(sc.meshes, sc.instances, r)).state[0]
+    assert not np.array_equal(persp[nf:], st[nf:])
