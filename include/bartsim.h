@@ -304,13 +304,14 @@ int bart_simulate_adjoint_mixed(bart_ctx *ctx, double t0, const void *grad_adc, 
 int bart_set_graph(bart_ctx *ctx, int32_t enable);
 
 /* Work layout of the mixed-path synthesis kernel: samples_per_lane 16 (or
- * 0, the default) or 8 (where M allows: M divides 256 or 256 divides M);
+ * 0, the default), 8 (where M allows: M divides 256 or 256 divides M) or 32
+ * (M = 256, 512 or 1024);
  * tiles_per_item = 32-record tiles per work item (0 = default, scaled with
  * the largest scene).  The results differ only by FP32 summation order.
  * Errors: EINVAL. */
 int bart_set_synth_layout(bart_ctx *ctx, int32_t samples_per_lane, int32_t tiles_per_item);
 
-#define BART_TUNE_MAX 16
+#define BART_TUNE_MAX 24
 /* Autotuner result: every trial's layout and best synthesis time. */
 typedef struct bart_tune {
     int32_t n_trials;
@@ -323,7 +324,7 @@ typedef struct bart_tune {
 } bart_tune;
 
 /* Time the mixed-path synthesis of the current scene at t0 for each
- * candidate layout (samples per lane 16 and, where M allows, 8; tiles per
+ * candidate layout (samples per lane 16 and, where M allows, 32 and 8; tiles per
  * item 8 ... 512), each run once to warm up and then `reps` times (best
  * time kept, CUDA events around the synthesis launches), and keep the
  * fastest layout for later frames (as bart_set_synth_layout).  adc: device

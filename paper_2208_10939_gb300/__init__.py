@@ -106,7 +106,7 @@ POINT_DTYPE = np.dtype([("range", "<f8"), ("rate", "<f8"), ("azimuth", "<f8"), (
                         ("y", "<f8"), ("power", "<f8"), ("r_bin", "<i4"), ("d_bin", "<i4")])
 assert POINT_DTYPE.itemsize == ctypes.sizeof(bart_point) == 56
 
-TUNE_MAX = 16
+TUNE_MAX = 24
 
 
 class bart_peaks(ctypes.Structure):

@@ -991,8 +991,9 @@ int bart_set_synth_layout(bart_ctx *ctx, int32_t samples_per_lane, int32_t tiles
 {
     g_err.clear();
     if (!ctx) return fail(BART_EINVAL, "bart_set_synth_layout: ctx is NULL");
-    if (samples_per_lane != 0 && samples_per_lane != 8 && samples_per_lane != 16)
-        return fail(BART_EINVAL, "bart_set_synth_layout: samples_per_lane=%d (0, 8 or 16)",
+    if (samples_per_lane != 0 && samples_per_lane != 8 && samples_per_lane != 16 &&
+        samples_per_lane != 32)
+        return fail(BART_EINVAL, "bart_set_synth_layout: samples_per_lane=%d (0, 8, 16 or 32)",
                     samples_per_lane);
     if (tiles_per_item < 0 || tiles_per_item > 65536)
         return fail(BART_EINVAL, "bart_set_synth_layout: tiles_per_item=%d", tiles_per_item);
@@ -1016,6 +1017,7 @@ int bart_autotune(bart_ctx *ctx, double t0, void *adc, int32_t dtype, int32_t re
     ctx->graph = false;
     std::memset(out, 0, sizeof *out);
     std::vector<int> Ss = {0};
+    if (synth_layout_samples(ctx->radar.M, 32) == 32) Ss.push_back(32);
     if (synth_layout_samples(ctx->radar.M, 8) == 8) Ss.push_back(8);
     const int tpis[] = {8, 16, 32, 64, 128, 256, 512};
     int rc = BART_OK;
@@ -1064,7 +1066,7 @@ int bart_autotune(bart_ctx *ctx, double t0, void *adc, int32_t dtype, int32_t re
         ++ctx->version;
         return rc;
     }
-    ctx->layout_S = out->best_samples_per_lane == 8 ? 8 : 0;
+    ctx->layout_S = out->best_samples_per_lane == 16 ? 0 : out->best_samples_per_lane;
     ctx->tpi_override = out->best_tiles_per_item;
     ++ctx->version;
     return BART_OK;

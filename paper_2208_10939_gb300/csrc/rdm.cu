@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 
 #include "bart_internal.cuh"
 
@@ -141,14 +142,12 @@ __global__ void range_fft_kernel(const typename Cplx<T>::type *__restrict__ adc,
 }
 
 // one block per (RB consecutive range bins, channel): Doppler FFT of the
-// channel's RB columns.  CUBE = false: |Y|^2 written per channel, [o][r][d']
-// (summed by rdm_sum_kernel); CUBE = true: the complex Y written, [o][r][d']
-// (summed by rdm_cube_sum_kernel and kept for the angle spectrum).  d' is the
-// Doppler bin after the N/2 shift.
-template <typename T, bool CUBE>
+// channel's RB columns, the complex Y written, [o][r][d'] (summed by
+// rdm_cube_sum_kernel and kept for the angle spectrum and the adjoint); d' is
+// the Doppler bin after the N/2 shift.
+template <typename T>
 __global__ void doppler_kernel(const typename Cplx<T>::type *__restrict__ X, int N, int M,
-                               int RB, int window, T *__restrict__ pw_out,
-                               typename Cplx<T>::type *__restrict__ cube_out)
+                               int RB, int window, typename Cplx<T>::type *__restrict__ cube_out)
 {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -173,13 +172,11 @@ __global__ void doppler_kernel(const typename Cplx<T>::type *__restrict__ X, int
         const int c = i / N, d = i % N;
         const C v = res[i];
         const int ds = d + (N >> 1);
-        const int64_t at = ((int64_t)o * M + r0 + c) * N + (ds >= N ? ds - N : ds);
-        if (CUBE) cube_out[at] = v;
-        else pw_out[at] = v.x * v.x + v.y * v.y;
+        cube_out[((int64_t)o * M + r0 + c) * N + (ds >= N ? ds - N : ds)] = v;
     }
 }
 
-// RDM[g][r][d] = sum over the O channels of group g, in channel order
+// RDM[g][r][d] = sum over the O partial maps of group g, in order
 template <typename T>
 __global__ void rdm_sum_kernel(const T *__restrict__ pw, int O, int64_t MN, int groups,
                                float *__restrict__ rdm)
@@ -206,6 +203,97 @@ __global__ void rdm_cube_sum_kernel(const typename Cplx<T>::type *__restrict__ Y
         acc += v.x * v.x + v.y * v.y;
     }
     rdm[i] = (float)acc;
+}
+
+// -------------------------------------------------------------------------
+// The RDM without the complex range-Doppler cube (bart_form_rdm): the range
+// pass transforms TN consecutive chirps of one channel per block and writes
+// them transposed, Xt[o][r][n], so that the Doppler pass reads every range
+// bin's N chirps as one contiguous run; the Doppler pass transforms RB range
+// bins of a group of channels per block and sums |Y|^2 over the group's
+// channels in shared memory, in channel order; the groups' partial maps are
+// then added in group order.  HBM traffic per sample: ADC read, Xt write, Xt
+// read (3 x 8 bytes for complex64) against 4 x 8 for a per-channel power
+// array.
+// -------------------------------------------------------------------------
+template <typename T>
+__global__ void range_fft_t_kernel(const typename Cplx<T>::type *__restrict__ adc,
+                                   typename Cplx<T>::type *__restrict__ Xt, int N, int M, int TN,
+                                   int window)
+{
+    using C = typename Cplx<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf0 = reinterpret_cast<C *>(smem_raw);
+    C *buf1 = buf0 + TN * M;
+    C *tw = buf1 + TN * M;
+    fill_twiddles<T>(tw, M);
+    const int o = blockIdx.y;
+    const int n0 = blockIdx.x * TN;
+    const int rows = min(TN, N - n0);
+    const C *in = adc + ((int64_t)o * N + n0) * M;
+    for (int i = threadIdx.x; i < TN * M; i += blockDim.x) {
+        const int c = i / M, m = i % M;
+        C v;
+        if (c < rows) {
+            v = in[i];
+            const T w = window_val<T>(m, M, window);
+            v.x *= w;
+            v.y *= w;
+        } else {
+            v.x = v.y = (T)0;
+        }
+        buf0[i] = v;
+    }
+    __syncthreads();
+    const C *res = stockham<C, T>(buf0, buf1, tw, M, TN);
+    C *out = Xt + (int64_t)o * M * N + n0;
+    for (int i = threadIdx.x; i < M * TN; i += blockDim.x) {
+        const int r = i / TN, c = i % TN;
+        if (c < rows) out[(int64_t)r * N + c] = res[c * M + r];
+    }
+}
+
+template <typename T>
+__global__ void doppler_sum_kernel(const typename Cplx<T>::type *__restrict__ Xt, int N, int M,
+                                   int RB, int CPB, int O, int window, T *__restrict__ part)
+{
+    using C = typename Cplx<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf0 = reinterpret_cast<C *>(smem_raw);
+    C *buf1 = buf0 + RB * N;
+    C *tw = buf1 + RB * N;
+    T *acc = reinterpret_cast<T *>(tw + tw_len(N));
+    fill_twiddles<T>(tw, N);
+    const int r0 = blockIdx.x * RB;
+    const int gg = blockIdx.y;                       // group of channels (over all scenes)
+    const int G = (O + CPB - 1) / CPB;               // groups per scene
+    const int scene = gg / G, g = gg % G;
+    const int o0 = scene * O + g * CPB, o1 = scene * O + min(O, (g + 1) * CPB);
+    for (int i = threadIdx.x; i < RB * N; i += blockDim.x) acc[i] = (T)0;
+    for (int o = o0; o < o1; ++o) {
+        const C *src = Xt + ((int64_t)o * M + r0) * N;
+        for (int i = threadIdx.x; i < RB * N; i += blockDim.x) {
+            const int n = i % N;
+            const T w = window_val<T>(n, N, window);
+            C v = src[i];
+            v.x *= w;
+            v.y *= w;
+            buf0[i] = v;
+        }
+        __syncthreads();
+        const C *res = stockham<C, T>(buf0, buf1, tw, N, RB);
+        for (int i = threadIdx.x; i < RB * N; i += blockDim.x) {
+            const C v = res[i];
+            acc[i] += v.x * v.x + v.y * v.y;
+        }
+        __syncthreads();
+    }
+    T *dst = part + (int64_t)gg * M * N;
+    for (int i = threadIdx.x; i < RB * N; i += blockDim.x) {
+        const int c = i / N, d = i % N;
+        const int ds = d + (N >> 1);
+        dst[(int64_t)(r0 + c) * N + (ds >= N ? ds - N : ds)] = acc[i];
+    }
 }
 
 // range bins per Doppler block: the largest power of two RB with RB N <= 512
@@ -286,8 +374,8 @@ static int rdm_rb(int N, int M)
     return rb;
 }
 
-// workspace: the range-FFT output (O N M complex) followed by the
-// per-channel Doppler power (O M N reals of the same precision)
+// workspace: the range-FFT output (O N M complex) followed by the channel
+// groups' partial maps (at most O M N reals of the same precision)
 int64_t rdm_workspace_bytes(const RadarDev &rd, int dtype)
 {
     const int64_t e = dtype == BART_C64 ? 8 : 16;
@@ -307,17 +395,36 @@ static void range_fft(const void *adc, const RadarDev &rd, void *X, cudaStream_t
         reinterpret_cast<const C *>(adc), reinterpret_cast<C *>(X), M, rd.window);
 }
 
-template <typename T, bool CUBE>
-static void doppler(const void *X, const RadarDev &rd, T *pw, void *cube, cudaStream_t s)
+template <typename T>
+static void doppler(const void *X, const RadarDev &rd, void *cube, cudaStream_t s)
 {
     using C = typename Cplx<T>::type;
     const int M = rd.M, N = rd.N;
     const int RB = rdm_rb(N, M);
     const size_t sm2 = (size_t)(2 * RB * N + tw_len(N)) * sizeof(C);
-    cudaFuncSetAttribute(doppler_kernel<T, CUBE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(doppler_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sm2);
-    doppler_kernel<T, CUBE><<<dim3((unsigned int)(M / RB), (unsigned int)rd.O), 256, sm2, s>>>(
-        reinterpret_cast<const C *>(X), N, M, RB, rd.window, pw, reinterpret_cast<C *>(cube));
+    doppler_kernel<T><<<dim3((unsigned int)(M / RB), (unsigned int)rd.O), 256, sm2, s>>>(
+        reinterpret_cast<const C *>(X), N, M, RB, rd.window, reinterpret_cast<C *>(cube));
+}
+
+// chirps per range-FFT block: the largest power of two TN <= N whose two
+// ping-pong buffers fit in ~128 KB of shared memory
+static int rdm_tn(int N, int M, size_t csize)
+{
+    int tn = 1;
+    while (2 * tn <= N && (size_t)2 * (2 * tn) * M * csize <= (128u << 10)) tn *= 2;
+    return tn;
+}
+
+// channels summed per Doppler block: the whole scene's channels when they
+// fill the GPU, else fewer, as a divisor-free split (the last group shorter)
+static int rdm_cpb(int O, int blocks_per_channel_group, int scenes)
+{
+    int cpb = O;
+    while (cpb > 1 && (int64_t)blocks_per_channel_group * scenes * ((O + cpb - 1) / cpb) < 4 * 152)
+        cpb = (cpb + 1) / 2;
+    return cpb;
 }
 
 template <typename T>
@@ -325,13 +432,30 @@ static void run_rdm(const void *adc, const RadarDev &rd, int groups, void *ws, f
                     cudaStream_t s)
 {
     using C = typename Cplx<T>::type;
-    RadarDev all = rd;                 // every group's channels in one pass
-    all.O = rd.O * groups;
-    range_fft<T>(adc, all, ws, s);
-    T *pw = reinterpret_cast<T *>(reinterpret_cast<C *>(ws) + (int64_t)all.O * rd.N * rd.M);
-    doppler<T, false>(ws, all, pw, nullptr, s);
-    const int64_t MN = (int64_t)rd.M * rd.N;
-    rdm_sum_kernel<T><<<(unsigned int)((MN * groups + 255) / 256), 256, 0, s>>>(pw, rd.O, MN,
+    const int M = rd.M, N = rd.N, O = rd.O;
+    const int64_t Oall = (int64_t)O * groups;
+    // range pass, transposed output Xt[o][r][n]
+    const int TN = rdm_tn(N, M, sizeof(C));
+    const size_t sm1 = (size_t)(2 * TN * M + tw_len(M)) * sizeof(C);
+    cudaFuncSetAttribute(range_fft_t_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sm1);
+    const int t1 = std::min(1024, std::max(128, TN * M / 4));
+    range_fft_t_kernel<T><<<dim3((unsigned int)((N + TN - 1) / TN), (unsigned int)Oall), t1, sm1,
+                            s>>>(reinterpret_cast<const C *>(adc), reinterpret_cast<C *>(ws), N,
+                                 M, TN, rd.window);
+    // Doppler pass and the per-group channel sums
+    const int RB = rdm_rb(N, M);
+    const int CPB = rdm_cpb(O, M / RB, groups);
+    const int G = (O + CPB - 1) / CPB;
+    T *part = reinterpret_cast<T *>(reinterpret_cast<C *>(ws) + Oall * N * M);
+    const size_t sm2 = (size_t)(2 * RB * N + tw_len(N)) * sizeof(C) + (size_t)RB * N * sizeof(T);
+    cudaFuncSetAttribute(doppler_sum_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sm2);
+    doppler_sum_kernel<T><<<dim3((unsigned int)(M / RB), (unsigned int)(G * groups)), 256, sm2,
+                            s>>>(reinterpret_cast<const C *>(ws), N, M, RB, CPB, O, rd.window,
+                                 part);
+    const int64_t MN = (int64_t)M * N;
+    rdm_sum_kernel<T><<<(unsigned int)((MN * groups + 255) / 256), 256, 0, s>>>(part, G, MN,
                                                                                groups, rdm);
 }
 
@@ -341,7 +465,7 @@ static void run_rdm_cube(const void *adc, const RadarDev &rd, void *X, void *cub
 {
     using C = typename Cplx<T>::type;
     range_fft<T>(adc, rd, X, s);
-    doppler<T, true>(X, rd, nullptr, cube, s);
+    doppler<T>(X, rd, cube, s);
     const int64_t MN = (int64_t)rd.M * rd.N;
     rdm_cube_sum_kernel<T><<<(unsigned int)((MN + 255) / 256), 256, 0, s>>>(
         reinterpret_cast<const C *>(cube), rd.O, MN, rdm);
@@ -358,7 +482,7 @@ static void run_rdm_adjoint(const void *adc, const float *grad_rdm, const RadarD
     const int M = rd.M, N = rd.N;
     // forward cube Y (and the RDM, unused) into `cube`
     range_fft<T>(adc, all, X, s);
-    doppler<T, true>(X, all, nullptr, cube, s);
+    doppler<T>(X, all, cube, s);
     const int RB = rdm_rb(N, M);
     const size_t sm2 = (size_t)(2 * RB * N + tw_len(N)) * sizeof(C);
     cudaFuncSetAttribute(doppler_adjoint_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,

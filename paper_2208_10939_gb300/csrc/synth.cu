@@ -347,12 +347,213 @@ __device__ __forceinline__ uint64_t fsub2(uint64_t a, uint64_t b)
     return d;
 }
 
+// The record of facet k for one chirp row (see RecM): kinematics rows
+// evaluated at the row's chirp slot, directions, obliquity, amplitude, the
+// in-plane projections u_v and the form's coefficients.  Returns the form.
+struct MixRow {
+    const float4 *kin_t, *kin_r;     // kinematics rows of the row's TX and RX
+    const double *quad_t, *quad_r;   // their FP64 fallback data
+    int sl;                          // chirp slot
+    float tau_s, tn;                 // slot offset from the expansion point; chirp start (s)
+    float ptx[3], prx[3];            // antenna positions
+};
+
+__device__ __forceinline__ int build_mixed_record(const SynthArgs &A, const MixConsts &K,
+                                                  const MixRow &w, int k, float *R)
+{
+    const FacetRec fr = A.fac[k];
+    const float4 vv = reinterpret_cast<const float4 *>(A.vel32)[fr.inst];
+    float4 kt, kr;
+    kin_eval2(w.kin_t + (int64_t)k * kKinRow, w.kin_r + (int64_t)k * kKinRow,
+              w.quad_t + kKinQuadWords * (int64_t)k, w.quad_r + kKinQuadWords * (int64_t)k,
+              w.sl, w.tau_s, A.rd.Tc, K.f0c_d, K.mu_f0_d, K.mfh, K.mfl, kt, kr);
+    // directions t, r and the amplitude's ranges: from the facet
+    // centroid, or (far field) from the instance origin, whose
+    // plane waves every facet of the instance sees
+    float th[3], rh[3], Rt, Rr;
+    if (A.rd.far_field) {
+        const float4 rf = reinterpret_cast<const float4 *>(A.ref32)[fr.inst];
+        const float ox = fmaf(vv.x, w.tn, rf.x), oy = fmaf(vv.y, w.tn, rf.y),
+                    oz = fmaf(vv.z, w.tn, rf.z);
+        th[0] = w.ptx[0] - ox; th[1] = w.ptx[1] - oy; th[2] = w.ptx[2] - oz;
+        rh[0] = w.prx[0] - ox; rh[1] = w.prx[1] - oy; rh[2] = w.prx[2] - oz;
+        Rt = sqrtf(th[0] * th[0] + th[1] * th[1] + th[2] * th[2]);
+        Rr = sqrtf(rh[0] * rh[0] + rh[1] * rh[1] + rh[2] * rh[2]);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            th[r] /= Rt;
+            rh[r] /= Rr;
+        }
+    } else {
+        const float cx = fmaf(vv.x, w.tn, fr.c[0]);
+        const float cy = fmaf(vv.y, w.tn, fr.c[1]);
+        const float cz = fmaf(vv.z, w.tn, fr.c[2]);
+        th[0] = w.ptx[0] - cx; th[1] = w.ptx[1] - cy; th[2] = w.ptx[2] - cz;
+        rh[0] = w.prx[0] - cx; rh[1] = w.prx[1] - cy; rh[2] = w.prx[2] - cz;
+        const float it = rsqrtf(th[0] * th[0] + th[1] * th[1] + th[2] * th[2]);
+        const float ir = rsqrtf(rh[0] * rh[0] + rh[1] * rh[1] + rh[2] * rh[2]);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            th[r] *= it;
+            rh[r] *= ir;
+        }
+        Rt = kt.w;
+        Rr = kr.w;
+    }
+    float b[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) b[r] = th[r] + rh[r];
+    const float L = kt.w + kr.w;            // the facet's path at the chirp start
+    float o_k = 0.5f * (fr.n[0] * b[0] + fr.n[1] * b[1] + fr.n[2] * b[2]);
+    if (fr.two_sided) o_k = fabsf(o_k);    // the side both antennas light
+    const float g = __fdividef(fr.rho * o_k, Rt * Rr);
+    // in-plane part of b, formed once: u_v, |b_t|^2 and n x b_t all derive
+    // from it, so every form evaluates J exactly at one wave vector
+    // (|b|^2 - (b.n)^2 would cancel catastrophically near specular)
+    const float bn = fr.n[0] * b[0] + fr.n[1] * b[1] + fr.n[2] * b[2];
+    const float bt[3] = {b[0] - bn * fr.n[0], b[1] - bn * fr.n[1], b[2] - bn * fr.n[2]};
+    float u[3];
+#pragma unroll
+    for (int v = 0; v < 3; ++v)
+        u[v] = bt[0] * fr.dv[3 * v] + bt[1] * fr.dv[3 * v + 1] + bt[2] * fr.dv[3 * v + 2];
+    // the delay's motion within the chirp and the residual video phase
+    // follow the facet centroid, or (reference-point form) the
+    // instance origin: path Lp, its first and second time derivatives
+    // (far field: the origin's motion, the facet's plane-wave path)
+    float Lp = L, Ld = 0.f, Ldd = 0.f;
+    {
+        float ut[3] = {th[0], th[1], th[2]}, ur[3] = {rh[0], rh[1], rh[2]};
+        float Rtp = Rt, Rrp = Rr;
+        if (A.rd.delay_ref) {
+            const float4 rf = reinterpret_cast<const float4 *>(A.ref32)[fr.inst];
+            const float ox = fmaf(vv.x, w.tn, rf.x), oy = fmaf(vv.y, w.tn, rf.y),
+                        oz = fmaf(vv.z, w.tn, rf.z);
+            float gt[3] = {w.ptx[0] - ox, w.ptx[1] - oy, w.ptx[2] - oz};
+            float gr[3] = {w.prx[0] - ox, w.prx[1] - oy, w.prx[2] - oz};
+            Rtp = sqrtf(gt[0] * gt[0] + gt[1] * gt[1] + gt[2] * gt[2]);
+            Rrp = sqrtf(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
+            Lp = Rtp + Rrp;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                ut[r] = gt[r] / Rtp;
+                ur[r] = gr[r] / Rrp;
+            }
+        }
+        if (A.rd.intra) {
+            const float v2 = vv.x * vv.x + vv.y * vv.y + vv.z * vv.z;
+            const float vt = vv.x * ut[0] + vv.y * ut[1] + vv.z * ut[2];
+            const float vr = vv.x * ur[0] + vv.y * ur[1] + vv.z * ur[2];
+            Ld = -(vt + vr);
+            Ldd = __fdividef(v2 - vt * vt, Rtp) + __fdividef(v2 - vr * vr, Rrp);
+        }
+    }
+    float hi = kt.y + kr.y;
+    hi = hi >= 1.f ? hi - 1.f : hi;
+    const float loc = (kt.z + kr.z) + K.f0c_fs * Ld - K.mu_c2fs * Lp * Ld;
+    const float p2 = K.half_f0c_fs2 * Ldd + K.mu_c_fs2 * Ld;
+    const float ph0c = red1((kt.x + kr.x) - K.mu_2c2 * Lp * Lp);
+    const float umin = fminf(fminf(u[0], u[1]), u[2]);
+    const float umax = fmaxf(fmaxf(u[0], u[1]), u[2]);
+    const float dmin = fminf(fminf(fabsf(u[0] - u[1]), fabsf(u[1] - u[2])),
+                             fabsf(u[0] - u[2]));
+    const float A2 = 2.f * fr.area * g;
+    if (K.kmax * (umax - umin) < (float)kSeriesKD) {
+        R[0] = ph0c;
+        R[1] = hi;
+        R[2] = loc;
+        R[3] = p2;
+        const float ub = (u[0] + u[1] + u[2]) * (1.f / 3.f);
+        R[4] = red1(-K.f0c * ub);
+        R[5] = -K.muc * ub;
+        const float y0 = K.k0 * (u[0] - ub), y1 = K.k0 * (u[1] - ub),
+                    y2 = K.k0 * (u[2] - ub);
+        const float e2 = y0 * y1 + y0 * y2 + y1 * y2, e3 = y0 * y1 * y2;
+        float h[kSeriesTerms];
+        h[0] = 1.f;
+        h[1] = 0.f;
+        h[2] = -e2;
+#pragma unroll
+        for (int p = 3; p < kSeriesTerms; ++p) h[p] = -e2 * h[p - 2] + e3 * h[p - 3];
+        const float sc = A2 * K.k0 * K.k0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            R[6 + i] = ((i & 1) ? -sc : sc) * h[2 * i] * (float)c_inv_fact[2 * i + 2];
+#pragma unroll
+        for (int i = 0; i < 7; ++i)
+            R[14 + i] = ((i & 1) ? sc : -sc) * h[2 * i + 1] * (float)c_inv_fact[2 * i + 3];
+        return kRecSeries;
+    } else if (K.kmax * dmin < (float)kEdgeKd) {
+        R[0] = ph0c;
+        R[1] = hi;
+        R[2] = loc;
+        R[3] = p2;
+        const float bt2 = bt[0] * bt[0] + bt[1] * bt[1] + bt[2] * bt[2];
+        const float nxb[3] = {fr.n[1] * bt[2] - fr.n[2] * bt[1],
+                              fr.n[2] * bt[0] - fr.n[0] * bt[2],
+                              fr.n[0] * bt[1] - fr.n[1] * bt[0]};
+        int flags = 0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const int i1 = (i + 1) % 3;
+            const float e[3] = {fr.dv[3 * i1] - fr.dv[3 * i],
+                                fr.dv[3 * i1 + 1] - fr.dv[3 * i + 1],
+                                fr.dv[3 * i1 + 2] - fr.dv[3 * i + 2]};
+            const float beta = 0.5f * (u[i] + u[i1]);
+            const float gam = 0.5f * (u[i1] - u[i]);
+            const float ci = (e[0] * nxb[0] + e[1] * nxb[1] + e[2] * nxb[2]) / bt2;
+            R[4 + 4 * i] = red1(-K.f0c * beta);
+            R[5 + 4 * i] = -K.muc * beta;
+            R[6 + 4 * i] = K.k0 * gam;
+            R[7 + 4 * i] = K.k0 * ci * g;
+            if (K.kmax * fabsf(gam) < (float)kSincSeries) flags |= 1 << i;
+        }
+        R[16] = __int_as_float(flags);
+        return kRecEdge;
+    } else {
+        R[15] = hi;
+        R[16] = p2;
+        // vertex steps = the centroid's step times e^{j x_v},
+        // x_v = -2 pi mu/(fs c) u_v, from its Taylor series (error
+        // below x^6/720 = 1.4e-9 for |x| < 0.1), else sincospi
+        float sc_, cc_;
+        sincospif(2.f * red1(hi + loc), &sc_, &cc_);
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            const float ua = u[v], ub_ = u[(v + 1) % 3], uc = u[(v + 2) % 3];
+            R[v] = red1(ph0c - K.f0c * ua);
+            const float lo = loc - K.muc * ua;
+            R[3 + v] = lo;
+            R[6 + v] = __fdividef(-A2, (ua - ub_) * (ua - uc));
+            float s_, c_;
+            const float x = -6.283185307179586f * K.muc * ua;
+            if (fabsf(x) < 0.1f) {
+                const float x2 = x * x;
+                const float cx = fmaf(x2, fmaf(x2, 1.f / 24.f, -0.5f), 1.f);
+                const float sx = x * fmaf(x2, fmaf(x2, 1.f / 120.f, -1.f / 6.f), 1.f);
+                c_ = fmaf(cc_, cx, -sc_ * sx);
+                s_ = fmaf(sc_, cx, cc_ * sx);
+            } else {
+                sincospif(2.f * red1(hi + lo), &s_, &c_);
+            }
+            R[9 + v] = c_;
+            R[12 + v] = s_;
+            // 2 cos(2 step) = 2 - 4 sin^2 = 4 cos^2 - 2, taken from the
+            // smaller of sin and cos so that only its own rounding remains
+            // (the recurrence is most sensitive to it near angle 0 and pi)
+            R[17 + v] = fabsf(s_) < fabsf(c_) ? fmaf(-4.f * s_, s_, 2.f)
+                                              : fmaf(4.f * c_, c_, -2.f);
+            R[20 + v] = 8.f * c_ * s_;                // 4 sin(2 step)
+        }
+    }
+    return kRecVertex;
+}
+
 // S: consecutive samples per lane; LPR: lanes per chirp row (RPW = 32/LPR
 // rows of the same channel share a warp, e.g. two 256-sample chirps at
 // S = 16).  A 32-record tile holds LPR facets x RPW chirps: lane l builds
 // the record of facet (l mod LPR) for its own row.
 template <int S, int LPR>
-__global__ void __launch_bounds__(kMixWarps * 32, kMixMinBlocks)
+__global__ void __launch_bounds__(kMixWarps * 32, S >= 32 ? 6 : kMixMinBlocks)
 synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
 {
     constexpr int RPW = 32 / LPR;
@@ -435,201 +636,25 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
     const float4 *kin_r = A.kin + (int64_t)(P + rx) * F * kKinRow;
     const double *quad_t = A.kquad + (int64_t)tx * F * kKinQuadWords;
     const double *quad_r = A.kquad + (int64_t)(P + rx) * F * kKinQuadWords;
+    MixRow wrow;
+    wrow.kin_t = kin_t;
+    wrow.kin_r = kin_r;
+    wrow.quad_t = quad_t;
+    wrow.quad_r = quad_r;
+    wrow.sl = sl;
+    wrow.tau_s = tau_s;
+    wrow.tn = tn;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        wrow.ptx[r] = ptx[r];
+        wrow.prx[r] = prx[r];
+    }
 
     for (int base = rbeg; base < rend; base += LPR) {
         // ---------------- build one record per lane ----------------
         const bool valid = row_ok && base + col < rend;
         int cls = -1;
-        if (valid) {
-            float *R = sRec[warp][lane].f;
-            const int k = list[base + col];
-            const FacetRec fr = A.fac[k];
-            const float4 vv = reinterpret_cast<const float4 *>(A.vel32)[fr.inst];
-            float4 kt, kr;
-            kin_eval2(kin_t + (int64_t)k * kKinRow, kin_r + (int64_t)k * kKinRow,
-                      quad_t + kKinQuadWords * (int64_t)k, quad_r + kKinQuadWords * (int64_t)k,
-                      sl, tau_s, A.rd.Tc,
-                      K.f0c_d, K.mu_f0_d, K.mfh, K.mfl, kt, kr);
-            // directions t, r and the amplitude's ranges: from the facet
-            // centroid, or (far field) from the instance origin, whose
-            // plane waves every facet of the instance sees
-            float th[3], rh[3], Rt, Rr;
-            if (A.rd.far_field) {
-                const float4 rf = reinterpret_cast<const float4 *>(A.ref32)[fr.inst];
-                const float ox = fmaf(vv.x, tn, rf.x), oy = fmaf(vv.y, tn, rf.y),
-                            oz = fmaf(vv.z, tn, rf.z);
-                th[0] = ptx[0] - ox; th[1] = ptx[1] - oy; th[2] = ptx[2] - oz;
-                rh[0] = prx[0] - ox; rh[1] = prx[1] - oy; rh[2] = prx[2] - oz;
-                Rt = sqrtf(th[0] * th[0] + th[1] * th[1] + th[2] * th[2]);
-                Rr = sqrtf(rh[0] * rh[0] + rh[1] * rh[1] + rh[2] * rh[2]);
-#pragma unroll
-                for (int r = 0; r < 3; ++r) {
-                    th[r] /= Rt;
-                    rh[r] /= Rr;
-                }
-            } else {
-                const float cx = fmaf(vv.x, tn, fr.c[0]);
-                const float cy = fmaf(vv.y, tn, fr.c[1]);
-                const float cz = fmaf(vv.z, tn, fr.c[2]);
-                th[0] = ptx[0] - cx; th[1] = ptx[1] - cy; th[2] = ptx[2] - cz;
-                rh[0] = prx[0] - cx; rh[1] = prx[1] - cy; rh[2] = prx[2] - cz;
-                const float it = rsqrtf(th[0] * th[0] + th[1] * th[1] + th[2] * th[2]);
-                const float ir = rsqrtf(rh[0] * rh[0] + rh[1] * rh[1] + rh[2] * rh[2]);
-#pragma unroll
-                for (int r = 0; r < 3; ++r) {
-                    th[r] *= it;
-                    rh[r] *= ir;
-                }
-                Rt = kt.w;
-                Rr = kr.w;
-            }
-            float b[3];
-#pragma unroll
-            for (int r = 0; r < 3; ++r) b[r] = th[r] + rh[r];
-            const float L = kt.w + kr.w;            // the facet's path at the chirp start
-            float o_k = 0.5f * (fr.n[0] * b[0] + fr.n[1] * b[1] + fr.n[2] * b[2]);
-            if (fr.two_sided) o_k = fabsf(o_k);    // the side both antennas light
-            const float g = __fdividef(fr.rho * o_k, Rt * Rr);
-            // in-plane part of b, formed once: u_v, |b_t|^2 and n x b_t all derive
-            // from it, so every form evaluates J exactly at one wave vector
-            // (|b|^2 - (b.n)^2 would cancel catastrophically near specular)
-            const float bn = fr.n[0] * b[0] + fr.n[1] * b[1] + fr.n[2] * b[2];
-            const float bt[3] = {b[0] - bn * fr.n[0], b[1] - bn * fr.n[1], b[2] - bn * fr.n[2]};
-            float u[3];
-#pragma unroll
-            for (int v = 0; v < 3; ++v)
-                u[v] = bt[0] * fr.dv[3 * v] + bt[1] * fr.dv[3 * v + 1] + bt[2] * fr.dv[3 * v + 2];
-            // the delay's motion within the chirp and the residual video phase
-            // follow the facet centroid, or (reference-point form) the
-            // instance origin: path Lp, its first and second time derivatives
-            // (far field: the origin's motion, the facet's plane-wave path)
-            float Lp = L, Ld = 0.f, Ldd = 0.f;
-            {
-                float ut[3] = {th[0], th[1], th[2]}, ur[3] = {rh[0], rh[1], rh[2]};
-                float Rtp = Rt, Rrp = Rr;
-                if (A.rd.delay_ref) {
-                    const float4 rf = reinterpret_cast<const float4 *>(A.ref32)[fr.inst];
-                    const float ox = fmaf(vv.x, tn, rf.x), oy = fmaf(vv.y, tn, rf.y),
-                                oz = fmaf(vv.z, tn, rf.z);
-                    float gt[3] = {ptx[0] - ox, ptx[1] - oy, ptx[2] - oz};
-                    float gr[3] = {prx[0] - ox, prx[1] - oy, prx[2] - oz};
-                    Rtp = sqrtf(gt[0] * gt[0] + gt[1] * gt[1] + gt[2] * gt[2]);
-                    Rrp = sqrtf(gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]);
-                    Lp = Rtp + Rrp;
-#pragma unroll
-                    for (int r = 0; r < 3; ++r) {
-                        ut[r] = gt[r] / Rtp;
-                        ur[r] = gr[r] / Rrp;
-                    }
-                }
-                if (A.rd.intra) {
-                    const float v2 = vv.x * vv.x + vv.y * vv.y + vv.z * vv.z;
-                    const float vt = vv.x * ut[0] + vv.y * ut[1] + vv.z * ut[2];
-                    const float vr = vv.x * ur[0] + vv.y * ur[1] + vv.z * ur[2];
-                    Ld = -(vt + vr);
-                    Ldd = __fdividef(v2 - vt * vt, Rtp) + __fdividef(v2 - vr * vr, Rrp);
-                }
-            }
-            float hi = kt.y + kr.y;
-            hi = hi >= 1.f ? hi - 1.f : hi;
-            const float loc = (kt.z + kr.z) + K.f0c_fs * Ld - K.mu_c2fs * Lp * Ld;
-            const float p2 = K.half_f0c_fs2 * Ldd + K.mu_c_fs2 * Ld;
-            const float ph0c = red1((kt.x + kr.x) - K.mu_2c2 * Lp * Lp);
-            const float umin = fminf(fminf(u[0], u[1]), u[2]);
-            const float umax = fmaxf(fmaxf(u[0], u[1]), u[2]);
-            const float dmin = fminf(fminf(fabsf(u[0] - u[1]), fabsf(u[1] - u[2])),
-                                     fabsf(u[0] - u[2]));
-            const float A2 = 2.f * fr.area * g;
-            if (K.kmax * (umax - umin) < (float)kSeriesKD) {
-                cls = kRecSeries;
-                R[0] = ph0c;
-                R[1] = hi;
-                R[2] = loc;
-                R[3] = p2;
-                const float ub = (u[0] + u[1] + u[2]) * (1.f / 3.f);
-                R[4] = red1(-K.f0c * ub);
-                R[5] = -K.muc * ub;
-                const float y0 = K.k0 * (u[0] - ub), y1 = K.k0 * (u[1] - ub),
-                            y2 = K.k0 * (u[2] - ub);
-                const float e2 = y0 * y1 + y0 * y2 + y1 * y2, e3 = y0 * y1 * y2;
-                float h[kSeriesTerms];
-                h[0] = 1.f;
-                h[1] = 0.f;
-                h[2] = -e2;
-#pragma unroll
-                for (int p = 3; p < kSeriesTerms; ++p) h[p] = -e2 * h[p - 2] + e3 * h[p - 3];
-                const float sc = A2 * K.k0 * K.k0;
-#pragma unroll
-                for (int i = 0; i < 8; ++i)
-                    R[6 + i] = ((i & 1) ? -sc : sc) * h[2 * i] * (float)c_inv_fact[2 * i + 2];
-#pragma unroll
-                for (int i = 0; i < 7; ++i)
-                    R[14 + i] = ((i & 1) ? sc : -sc) * h[2 * i + 1] * (float)c_inv_fact[2 * i + 3];
-            } else if (K.kmax * dmin < (float)kEdgeKd) {
-                cls = kRecEdge;
-                R[0] = ph0c;
-                R[1] = hi;
-                R[2] = loc;
-                R[3] = p2;
-                const float bt2 = bt[0] * bt[0] + bt[1] * bt[1] + bt[2] * bt[2];
-                const float nxb[3] = {fr.n[1] * bt[2] - fr.n[2] * bt[1],
-                                      fr.n[2] * bt[0] - fr.n[0] * bt[2],
-                                      fr.n[0] * bt[1] - fr.n[1] * bt[0]};
-                int flags = 0;
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    const int i1 = (i + 1) % 3;
-                    const float e[3] = {fr.dv[3 * i1] - fr.dv[3 * i],
-                                        fr.dv[3 * i1 + 1] - fr.dv[3 * i + 1],
-                                        fr.dv[3 * i1 + 2] - fr.dv[3 * i + 2]};
-                    const float beta = 0.5f * (u[i] + u[i1]);
-                    const float gam = 0.5f * (u[i1] - u[i]);
-                    const float ci = (e[0] * nxb[0] + e[1] * nxb[1] + e[2] * nxb[2]) / bt2;
-                    R[4 + 4 * i] = red1(-K.f0c * beta);
-                    R[5 + 4 * i] = -K.muc * beta;
-                    R[6 + 4 * i] = K.k0 * gam;
-                    R[7 + 4 * i] = K.k0 * ci * g;
-                    if (K.kmax * fabsf(gam) < (float)kSincSeries) flags |= 1 << i;
-                }
-                R[16] = __int_as_float(flags);
-            } else {
-                cls = kRecVertex;
-                R[15] = hi;
-                R[16] = p2;
-                // vertex steps = the centroid's step times e^{j x_v},
-                // x_v = -2 pi mu/(fs c) u_v, from its Taylor series (error
-                // below x^6/720 = 1.4e-9 for |x| < 0.1), else sincospi
-                float sc_, cc_;
-                sincospif(2.f * red1(hi + loc), &sc_, &cc_);
-#pragma unroll
-                for (int v = 0; v < 3; ++v) {
-                    const float ua = u[v], ub_ = u[(v + 1) % 3], uc = u[(v + 2) % 3];
-                    R[v] = red1(ph0c - K.f0c * ua);
-                    const float lo = loc - K.muc * ua;
-                    R[3 + v] = lo;
-                    R[6 + v] = __fdividef(-A2, (ua - ub_) * (ua - uc));
-                    float s_, c_;
-                    const float x = -6.283185307179586f * K.muc * ua;
-                    if (fabsf(x) < 0.1f) {
-                        const float x2 = x * x;
-                        const float cx = fmaf(x2, fmaf(x2, 1.f / 24.f, -0.5f), 1.f);
-                        const float sx = x * fmaf(x2, fmaf(x2, 1.f / 120.f, -1.f / 6.f), 1.f);
-                        c_ = fmaf(cc_, cx, -sc_ * sx);
-                        s_ = fmaf(sc_, cx, cc_ * sx);
-                    } else {
-                        sincospif(2.f * red1(hi + lo), &s_, &c_);
-                    }
-                    R[9 + v] = c_;
-                    R[12 + v] = s_;
-                    // 2 cos(2 step) = 2 - 4 sin^2 = 4 cos^2 - 2, taken from the
-                    // smaller of sin and cos so that only its own rounding remains
-                    // (the recurrence is most sensitive to it near angle 0 and pi)
-                    R[17 + v] = fabsf(s_) < fabsf(c_) ? fmaf(-4.f * s_, s_, 2.f)
-                                                      : fmaf(4.f * c_, c_, -2.f);
-                    R[20 + v] = 8.f * c_ * s_;                // 4 sin(2 step)
-                }
-            }
-        }
+        if (valid) cls = build_mixed_record(A, K, wrow, list[base + col], sRec[warp][lane].f);
         __syncwarp();
         const unsigned int mv = __ballot_sync(0xffffffffu, cls == kRecVertex);
         const unsigned int ms = __ballot_sync(0xffffffffu, cls == kRecSeries || cls == kRecEdge);
@@ -926,13 +951,15 @@ int synth_tiles_per_item(int64_t F) { return (int)std::max<int64_t>(16, ((F + 31
 // lane layout of the mixed kernel: S samples per lane, LPR lanes per chirp
 // row, W warps per row.  16 samples per lane halve the per-lane start-up
 // work (MUFU start phasors, the first samples of each recurrence) against
-// 8; S_req = 8 asks for the 8-sample layout where M allows it (autotuner
-// candidate).
+// 8; S_req = 8 asks for the 8-sample layout where M allows it, S_req = 32
+// for 32 samples per lane (M = 256, 512, 1024: half the per-lane start-up
+// work again, at fewer resident warps; autotuner candidates).
 struct MixLayout {
     int S, LPR, W;
 };
 static MixLayout mix_layout(int M, int S_req)
 {
+    if (S_req == 32 && (M == 256 || M == 512 || M == 1024)) return {32, M / 32, 1};
     if (S_req == 8) {
         if (M <= 256 && 256 % M == 0) return {8, M / 8, 1};
         if (M % 256 == 0) return {8, 32, M / 256};
@@ -994,7 +1021,13 @@ void launch_synth_mixed(const SynthArgs &a0, cudaStream_t s)
     synth_items_kernel<<<1, 1024, 0, s>>>(a.vcnt, a.VO, a.tiles_per_item, a.nc, 32 / L.LPR,
                                           L.W, a.item_off, a.item_counter);
     const int64_t items = a.max_items;
-    if (L.S == 16) {
+    if (L.S == 32) {
+        switch (L.LPR) {
+        case 8: run_mixed<32, 8>(a, K, L.W, items, s); break;
+        case 16: run_mixed<32, 16>(a, K, L.W, items, s); break;
+        default: run_mixed<32, 32>(a, K, L.W, items, s); break;
+        }
+    } else if (L.S == 16) {
         switch (L.LPR) {
         case 2: run_mixed<16, 2>(a, K, L.W, items, s); break;
         case 4: run_mixed<16, 4>(a, K, L.W, items, s); break;

@@ -261,6 +261,26 @@ def test_layout_edge_sizes_match_oracle(sim, M, N, P, Q):
     assert err <= TOL_MIXED
 
 
+@pytest.mark.parametrize("M,N", [(256, 5), (512, 3), (1024, 2)])
+@pytest.mark.parametrize("S", [32, 8, 16])
+def test_samples_per_lane_layouts_match_oracle(sim, M, N, S):
+    """Every lane layout of the mixed kernel where M allows it -- 32 samples
+    per lane (8, 16 or 32 lanes per chirp row, 4 / 2 / 1 rows per warp),
+    8 and 16 -- on a moving small car with a ragged record tail: the whole
+    cube against the oracle."""
+    sc = sg.small_car_scene(ntri=700, M=M, N=N, P=2, Q=2)
+    fr = oracle.Frame(sc)
+    ref = fr.adc_full()
+    sim.load_scene(sc)
+    pkg.bart_set_synth_layout(sim.ctx, S, 0)
+    try:
+        err = rel_l2(sim.simulate(pkg.PATH_MIXED).cpu().numpy(), ref)
+    finally:
+        pkg.bart_set_synth_layout(sim.ctx, 0, 0)
+    print(f"M={M} S={S}: mixed relL2 {err:.3e}")
+    assert err <= TOL_MIXED
+
+
 def test_kinematics_fallback_rows_match_oracle(sim):
     """A target 2 m from the radar receding at 15 m/s over 4096 chirps: the
     per-(antenna, facet) path-length series about the middle chirp cannot
