@@ -98,6 +98,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--sedan-steps", type=int, default=20)
+    ap.add_argument("--spectral-steps", type=int, default=5,
+                    help="timed frames of the spectral path on the headline frame (0 skips)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--dataset-scenes", type=int, default=4096,
@@ -201,7 +203,7 @@ def _sample_entries(rng, r, E):
                      rng.integers(0, r.M, E)], 1).astype(np.int32)
 
 
-def cpu_baseline(scene, seconds: float, adc=None) -> dict:
+def cpu_baseline(scene, seconds: float, adc=None, others=None) -> dict:
     """The FP64 oracle as it stands, on the host cores: echo terms/s of its
     synthesis over a random sample of ADC entries of the same frame (sized
     to ~``seconds`` of work), and the full-frame oracle time extrapolated
@@ -236,6 +238,9 @@ def cpu_baseline(scene, seconds: float, adc=None) -> dict:
         got = adc[e[:, 0], e[:, 1], e[:, 2]].astype(np.complex128)
         out["gpu_frame_rel_l2_vs_oracle"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
         out["gpu_frame_checked_entries"] = int(E)
+    for name, cube in (others or {}).items():
+        got = cube[e[:, 0], e[:, 1], e[:, 2]].astype(np.complex128)
+        out[f"{name}_rel_l2_vs_oracle"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
     return out
 
 
@@ -760,7 +765,22 @@ def main():
                 "peak_basis": peak_basis}
 
     e2e = e2e_run(pkg, torch, sim, scene, pkg.PATH_MIXED, args.e2e_steps, job_terms_per_step)
-    h_adc = adc.cpu().numpy() if rank == 0 and world == 1 and not args.no_cpu_baseline else None
+    want_host = rank == 0 and world == 1 and not args.no_cpu_baseline
+    h_adc = adc.cpu().numpy() if want_host else None
+    # the spectral path (inverse-FFT route) on the same frame
+    spectral, h_spec = None, None
+    if args.spectral_steps > 0 and world == 1:
+        sim.simulate(pkg.PATH_SPECTRAL, out=adc)
+        sim.sync()
+        ts = timed_frames(pkg, torch, sim, adc, rdm, flush, stream, args.spectral_steps,
+                          pkg.PATH_SPECTRAL)
+        spectral = {"value": terms * len(ts["step_ms"]) / (sum(ts["step_ms"]) / 1e3),
+                    "unit": UNIT, "ms_per_step": statistics.mean(ts["step_ms"]),
+                    "synthesis_ms": statistics.mean(ts["synth_ms"]),
+                    "speedup_vs_mixed_synthesis": statistics.mean(tf["synth_ms"]) /
+                    statistics.mean(ts["synth_ms"])}
+        if want_host:
+            h_spec = adc.cpu().numpy()
     stages = {k: last_tm[k] for k in ("scene_ms", "bvh_ms", "visibility_ms", "kinematics_ms",
                                       "synthesis_ms", "rdm_ms")}
     sim.close()
@@ -769,8 +789,11 @@ def main():
 
     cpu = None
     if h_adc is not None:
-        cpu = cpu_baseline(scene, args.cpu_seconds, h_adc)
-        del h_adc
+        cpu = cpu_baseline(scene, args.cpu_seconds, h_adc,
+                           None if h_spec is None else {"spectral_frame": h_spec})
+        if spectral is not None and "spectral_frame_rel_l2_vs_oracle" in cpu:
+            spectral["rel_l2_vs_oracle"] = cpu["spectral_frame_rel_l2_vs_oracle"]
+        del h_adc, h_spec
     sedan = None
     if world == 1 and not args.no_sedan and args.workload == "intersection":
         sedan = sedan_lines(pkg, sg, torch, dev, args, peaks)
@@ -802,6 +825,7 @@ def main():
         "frames_per_s": frames,
         "stages_ms_last_step": stages,
         "roofline": roofline,
+        "spectral_path": spectral,
         "clocks": clk,
         "e2e": e2e,
         "gpu_launches": tf["launches"],

@@ -46,6 +46,10 @@ extern "C" {
 #define BART_PATH_FP64  0    /* every quantity in FP64, exact per-sample delay */
 #define BART_PATH_MIXED 1    /* FP64 path length + mod-1 reduction, FP32 phasors,
                                 compensated (Kahan) accumulation */
+#define BART_PATH_SPECTRAL 2 /* the mixed path's records, each chirp row summed by the
+                                inverse-FFT route (Sec. 3.2): facet lines spread onto a
+                                uniform beat-frequency grid of 2M cells, one inverse FFT
+                                per row (a type-1 non-uniform FFT); needs M = 2^a 3^b */
 
 /* complex sample types of an ADC cube (interleaved re, im) */
 #define BART_C128 0          /* complex double */
@@ -241,7 +245,7 @@ int bart_radar_set(bart_ctx *ctx, const bart_radar *radar);
  *   3. per (channel, chirp) the physical-optics coefficient of every facet
  *      lit from TX and RX, and the dechirped IF samples (Eqs. 7, 9-13).
  * adc: device pointer to O*N*M complex samples of type `dtype`, written
- * completely.  path: BART_PATH_FP64 or BART_PATH_MIXED.
+ * completely.  path: BART_PATH_FP64, BART_PATH_MIXED or BART_PATH_SPECTRAL.
  * stats: optional host pointer (NULL = fully asynchronous).
  * Errors: ESTATE (no radar / scene), EINVAL, ENOMEM, ECUDA. */
 int bart_simulate_frame(bart_ctx *ctx, double t0, int32_t path, void *adc,

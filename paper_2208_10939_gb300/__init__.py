@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "libbartsim.so")
 
 BART_OK, BART_EINVAL, BART_ENOMEM, BART_ECUDA = 0, -1, -2, -3
 BART_ETIMEOUT, BART_ESTATE, BART_EDEVICE = -4, -5, -6
-PATH_FP64, PATH_MIXED = 0, 1
+PATH_FP64, PATH_MIXED, PATH_SPECTRAL = 0, 1, 2
 C128, C64 = 0, 1
 WINDOW_HANN, WINDOW_RECT = 0, 1
 VIS_BACK, VIS_LIT, VIS_GRAZE, VIS_OCCL, VIS_LIT_REV = 0, 1, 2, 3, 4

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libbartsim.so")
 SOURCES = ["capi.cu", "scene_bvh.cu", "visibility.cu", "synth.cu", "rdm.cu", "noise.cu", "detect.cu",
-           "adjoint.cu", "peaks.cu"]
+           "adjoint.cu", "peaks.cu", "spectral.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -38,8 +38,9 @@ def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
     t = os.path.getmtime(obj)
-    deps = [src, os.path.join(CSRC, "bart_internal.cuh"), os.path.join(CSRC, "record_fp64.cuh"),
-            os.path.join(INCLUDE, "bartsim.h")]
+    deps = [src, os.path.join(INCLUDE, "bartsim.h")] + [
+        os.path.join(CSRC, h) for h in ("bart_internal.cuh", "record_fp64.cuh", "mixed_record.cuh",
+                                        "fft_stockham.cuh")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

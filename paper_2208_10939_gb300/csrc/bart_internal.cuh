@@ -200,6 +200,12 @@ int64_t synth_max_items(const int64_t *scene_F, int n_scene, const RadarDev &rd,
 int synth_layout_samples(int M, int S_req);
 int synth_tiles_per_item(int64_t F);
 void launch_synth_fp64(const SynthArgs &a, cudaStream_t s);
+// spectral path (spectral.cu): 1 / (Fourier transform of the spreading
+// kernels) at the M samples, host-computed (2 M floats: main grid, then the
+// quadratic-phase grids); whether M's shared-memory footprint fits
+bool spectral_supported(int M);
+void spectral_tables(int M, float *host);
+void launch_synth_spectral(const SynthArgs &a, const float *inv_psi, cudaStream_t s);
 // chunks per chirp row of the FP64 synthesis; with more than one, SynthArgs
 // partial must hold chunks x VO x N x M double2 (the chunks' partial sums)
 int synth_fp64_chunks(const RadarDev &rd, int VO, int64_t F);

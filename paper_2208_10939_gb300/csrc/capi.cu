@@ -155,6 +155,8 @@ struct bart_ctx {
     DevBuf<unsigned char> rdm_ws, adc_own;
     DevBuf<double> noise_scratch;
     DevBuf<float> rdm_own;
+    DevBuf<float> spec_tab;             // spectral path: 1 / kernel transforms [2][M]
+    int spec_M = 0;
     DevBuf<unsigned char> det_ws;       // detection: cube, RDM, steering table, lists
     DevBuf<unsigned char> adj_ws;       // adjoints: RDM cube scratch
     DevBuf<double> gfac;                // synthesis adjoint: per-facet gradients [F][10]
@@ -239,6 +241,7 @@ struct bart_ctx {
         vis_cnt.release(); kin.release(); kquad.release(); partial.release(); item_off.release();
         item_counter.release(); counters.release(); status.release();
         rdm_ws.release(); adc_own.release(); rdm_own.release(); noise_scratch.release();
+        spec_tab.release();
         fg.release();
         det_ws.release(); adj_ws.release(); gfac.release(); d_voff.release(); d_foff.release(); d_root.release(); vstart.release();
         vcnt.release(); mkeys.release(); skeys.release();
@@ -543,9 +546,13 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
 {
     if (!ctx->have_radar) return fail(BART_ESTATE, "bart_simulate_frame: radar not set");
     if (ctx->insts.empty()) return fail(BART_ESTATE, "bart_simulate_frame: scene has no instances");
-    if (path != BART_PATH_FP64 && path != BART_PATH_MIXED && path != kPathAdjoint &&
-        path != kPathAdjointMixed)
+    if (path != BART_PATH_FP64 && path != BART_PATH_MIXED && path != BART_PATH_SPECTRAL &&
+        path != kPathAdjoint && path != kPathAdjointMixed)
         return fail(BART_EINVAL, "bart_simulate_frame: path=%d", path);
+    if (path == BART_PATH_SPECTRAL &&
+        (!is_fft_len(ctx->radar.M) || !spectral_supported(ctx->radar.M)))
+        return fail(BART_EINVAL, "bart_simulate_frame: the spectral path needs M of the form "
+                    "2^a 3^b (M=%d)", ctx->radar.M);
     if (dtype != BART_C64 && dtype != BART_C128)
         return fail(BART_EINVAL, "bart_simulate_frame: dtype=%d", dtype);
     if (!adc) return fail(BART_EINVAL, "bart_simulate_frame: adc is NULL");
@@ -656,17 +663,29 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
                         ? ctx->tpi_override
                         : synth_tiles_per_item(*std::max_element(scene_F.begin(), scene_F.end()));
     int64_t max_items = 0;
-    if (path == BART_PATH_MIXED) {
+    const bool mixed_rows = path == BART_PATH_MIXED || path == BART_PATH_SPECTRAL;
+    if (path == BART_PATH_SPECTRAL && ctx->spec_M != rd.M) {
+        std::vector<float> tab(2 * (size_t)rd.M);
+        spectral_tables(rd.M, tab.data());
+        BART_TRY(ctx->spec_tab.ensure(tab.size(), "spectral kernel tables"));
+        CUDA_TRY(cudaMemcpyAsync(ctx->spec_tab.p, tab.data(), tab.size() * sizeof(float),
+                                 cudaMemcpyHostToDevice, s), "spectral table copy");
+        CUDA_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+        ctx->spec_M = rd.M;
+    }
+    if (mixed_rows) {
         // kinematics: Taylor rows of R(t) per antenna and facet (one launch,
         // evaluated per record inside the synthesis)
         BART_TRY(ctx->kin.ensure((size_t)A * F * kKinRowWords, "kinematics rows"));
         BART_TRY(ctx->kquad.ensure((size_t)A * F * kKinQuadWords, "kinematics quadratics"));
-        BART_TRY(ctx->partial.ensure((size_t)synth_partial_words(scene_F.data(), B, rd, rd.N,
-                                                                 tpi, ctx->layout_S),
-                                     "synthesis partials"));
-        max_items = synth_max_items(scene_F.data(), B, rd, rd.N, tpi, ctx->layout_S);
-        BART_TRY(ctx->item_off.ensure((size_t)B * O + 1, "synthesis item table"));
-        BART_TRY(ctx->item_counter.ensure(1, "synthesis item counter"));
+        if (path == BART_PATH_MIXED) {
+            BART_TRY(ctx->partial.ensure((size_t)synth_partial_words(scene_F.data(), B, rd, rd.N,
+                                                                     tpi, ctx->layout_S),
+                                         "synthesis partials"));
+            max_items = synth_max_items(scene_F.data(), B, rd, rd.N, tpi, ctx->layout_S);
+            BART_TRY(ctx->item_off.ensure((size_t)B * O + 1, "synthesis item table"));
+            BART_TRY(ctx->item_counter.ensure(1, "synthesis item counter"));
+        }
         if (!ctx->side) {
             CUDA_TRY(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking),
                      "cudaStreamCreateWithFlags");
@@ -707,9 +726,10 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
                             ctx->ref64.p, ctx->ref32.p, s);
         launches += 1;
         if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[1], s), "cudaEventRecord");
-        // the mixed path's kinematics rows need only the world facets: they
-        // run on a second stream beside the hierarchy build and visibility
-        if (path == BART_PATH_MIXED) {
+        // the mixed and spectral paths' kinematics rows need only the world
+        // facets: they run on a second stream beside the hierarchy build and
+        // visibility
+        if (mixed_rows) {
             nv.next("bart kinematics rows");
             CUDA_TRY(cudaEventRecord(ctx->fork_ev, s), "cudaEventRecord");
             CUDA_TRY(cudaStreamWaitEvent(ctx->side, ctx->fork_ev, 0), "cudaStreamWaitEvent");
@@ -800,6 +820,17 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
             if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_syn[1], s), "cudaEventRecord");
             ctx->chunks = 1;
             launches += 4;
+        } else if (path == BART_PATH_SPECTRAL) {
+            a.kin = ctx->kin.p;
+            a.kquad = ctx->kquad.p;
+            a.n0 = 0;
+            a.nc = rd.N;
+            CUDA_TRY(cudaStreamWaitEvent(s, ctx->join_ev, 0), "cudaStreamWaitEvent");
+            if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_syn[0], s), "cudaEventRecord");
+            launch_synth_spectral(a, ctx->spec_tab.p, s);
+            if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_syn[1], s), "cudaEventRecord");
+            ctx->chunks = 1;
+            launches += 2;
         } else if (path == kPathAdjoint || path == kPathAdjointMixed) {
             a.n0 = 0;
             a.nc = rd.N;

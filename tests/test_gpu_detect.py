@@ -256,3 +256,28 @@ def test_config2_detect_full_size():
     r_res = sg.C0 * r.fs / (2 * r.slope * r.M)
     assert abs(best["range"] - 30.0) < 3.0 + r_res     # 30 m slant range to the car centre
     assert -11.0 < best["rate"] < -8.0                  # closing at ~10 m/s
+
+
+def test_noise_free_cfar_on_the_spectral_cube_matches_fp64():
+    """CA-CFAR (Pfa 1e-6, guard 2x2, train 8x4) on the noise-free moving
+    sedan: the FP64 cube's detections are the targets; the mixed path's
+    rounding repeats with its 16-sample lane layout and puts paired echoes
+    every M/16 range bins around -104 dB, which CFAR (no noise floor) picks
+    up; the spectral path has no per-lane structure -- its detections are
+    the FP64 cube's."""
+    sc = sg.car_scene()
+    s = pkg.Simulator(0)
+    try:
+        s.load_scene(sc)
+        cfg = dict(guard_r=2, guard_d=2, train_r=8, train_d=4, pfa=1e-6, angle_bins=512)
+        sets = {}
+        for path in (pkg.PATH_FP64, pkg.PATH_SPECTRAL, pkg.PATH_MIXED):
+            adc = s.simulate(path)
+            pts, n = s.detect(adc, max_points=65536, **cfg)
+            assert n <= 65536
+            sets[path] = set(zip(pts["r_bin"].tolist(), pts["d_bin"].tolist()))
+        print(f"noise-free sedan CFAR detections: fp64 {len(sets[pkg.PATH_FP64])}, spectral "
+              f"{len(sets[pkg.PATH_SPECTRAL])}, mixed {len(sets[pkg.PATH_MIXED])}")
+        assert sets[pkg.PATH_SPECTRAL] == sets[pkg.PATH_FP64]
+    finally:
+        s.close()

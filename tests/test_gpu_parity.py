@@ -102,14 +102,18 @@ def test_fp64_adc_matches_oracle(sim, name):
     assert err <= TOL_FP64
 
 
+@pytest.mark.parametrize("path", [pkg.PATH_MIXED, pkg.PATH_SPECTRAL])
 @pytest.mark.parametrize("name", list(CASES))
-def test_mixed_adc_matches_oracle(sim, name):
+def test_mixed_adc_matches_oracle(sim, name, path):
+    """The FP32 paths (direct mixed sum, spectral route): ADC cube <= 1e-4
+    relative L2 and RDM peaks within 0.1 dB of the oracle's."""
     sc, fr, ref = frame(name)
     sim.load_scene(sc)
-    adc, st = sim.simulate(pkg.PATH_MIXED, stats=True)
+    adc, st = sim.simulate(path, stats=True)
+    assert st["n_terms"] == fr.n_terms()
     a = adc.cpu().numpy()
     err = rel_l2(a, ref)
-    print(f"{name}: mixed relL2 {err:.3e}")
+    print(f"{name}: path {path} relL2 {err:.3e}")
     assert err <= TOL_MIXED
     if sc.radar.N & (sc.radar.N - 1):
         return                                  # radix-2 RDM needs a power-of-two N
@@ -259,6 +263,10 @@ def test_layout_edge_sizes_match_oracle(sim, M, N, P, Q):
     err = rel_l2(sim.simulate(pkg.PATH_MIXED).cpu().numpy(), ref)
     print(f"M={M} N={N} P={P} Q={Q}: mixed relL2 {err:.3e}")
     assert err <= TOL_MIXED
+    if M in (1024, 96, 768):                       # 2^a 3^b: the spectral path too
+        err_s = rel_l2(sim.simulate(pkg.PATH_SPECTRAL).cpu().numpy(), ref)
+        print(f"M={M}: spectral relL2 {err_s:.3e}")
+        assert err_s <= TOL_MIXED
 
 
 @pytest.mark.parametrize("M,N", [(256, 5), (512, 3), (1024, 2)])
@@ -382,3 +390,35 @@ def test_additive_noise_matches_oracle(sim, path, tol):
     assert torch.equal(again, noisy)                       # deterministic
     snr = 10 * np.log10(np.mean(np.abs(clean.cpu().numpy()) ** 2) / np.mean(np.abs(n_gpu) ** 2))
     assert abs(snr - 12.0) < 0.2
+
+
+def _large_facet_scenes():
+    big = sg.plate(1.25, 1.25, 1)                       # two 1.25 m triangles, ~320 wavelengths
+    radar = sg.make_radar(128, 4, 2, 2, 5.12e6, 30e12, 2.0, centre=(0.0, 0.0, 0.0))
+    plate = sg.Scene([big], [sg.Instance(0, (0.2, 8.0, 0.1), sg.rot_z(0.02), (0.0, -3.0, 0.0))],
+                     radar)
+    r3 = sg.intersection_scene(N=2).radar                # 12.5 MHz/us, 10.24 Msps, 512 samples
+    r3 = sg.Radar(f0=r3.f0, slope=r3.slope, fs=r3.fs, Tc=r3.Tc, M=r3.M, N=2,
+                  tx=r3.tx[[0, 11]], rx=r3.rx[[0, 15]])
+    ground = sg.Scene([sg.ground(20.0, 32, centre=(3.0, 30.0))],     # 0.625 m cells, config 3's size
+                      [sg.Instance(0, (0, 0, 0), np.eye(3), (0, 0, 0))], r3)
+    return {"plate_1p25m": plate, "ground_config3_cells": ground}
+
+
+@pytest.mark.parametrize("name", ["plate_1p25m", "ground_config3_cells"])
+def test_large_facets_match_oracle(sim, name):
+    """Facets far larger than a wavelength -- a 1.25 m broadside plate
+    (2 facets) and ground cells of the intersection's 0.625 m -- whose
+    in-plane projections reach hundreds of cycles: their vertex phases are
+    formed in FP64, so the FP32 paths stay within 1e-4 (they reached 1e-4
+    before)."""
+    sc = _large_facet_scenes()[name]
+    fr = oracle.Frame(sc)
+    ref = fr.adc_full()
+    sim.load_scene(sc)
+    a64 = sim.simulate(pkg.PATH_FP64).cpu().numpy()
+    assert rel_l2(a64, ref) <= TOL_FP64
+    for path in (pkg.PATH_MIXED, pkg.PATH_SPECTRAL):
+        err = rel_l2(sim.simulate(path).cpu().numpy(), ref)
+        print(f"{name}: path {path} relL2 {err:.3e}")
+        assert err <= TOL_MIXED

@@ -68,17 +68,21 @@ def test_config2_whole_cube_both_paths(sim):
     adc_d = sim.simulate(pkg.PATH_FP64)
     rdm_d = sim.rdm(adc_d).cpu().numpy().astype(np.float64)
     a_d = adc_d.cpu().numpy()
+    adc_s = sim.simulate(pkg.PATH_SPECTRAL)
+    rdm_s = sim.rdm(adc_s).cpu().numpy().astype(np.float64)
+    err_s = rel_l2(adc_s.cpu().numpy(), ref)
     err_m, err_d = rel_l2(a_m, ref), rel_l2(a_d, ref)
     r_ref = oracle.range_doppler_map(ref)
     pk = rdm_peaks(r_ref)
     db_m = np.abs(10 * np.log10(rdm_m[pk[:, 0], pk[:, 1]] / r_ref[pk[:, 0], pk[:, 1]]))
     db_d = np.abs(10 * np.log10(rdm_d[pk[:, 0], pk[:, 1]] / r_ref[pk[:, 0], pk[:, 1]]))
-    print(f"config2 whole cube ({st['n_terms']} terms): mixed relL2 {err_m:.3e}, fp64 relL2 "
-          f"{err_d:.3e}; {len(pk)} RDM peaks within 40 dB, worst mixed {db_m.max():.2e} dB, "
-          f"fp64 {db_d.max():.2e} dB")
+    db_s = np.abs(10 * np.log10(rdm_s[pk[:, 0], pk[:, 1]] / r_ref[pk[:, 0], pk[:, 1]]))
+    print(f"config2 whole cube ({st['n_terms']} terms): mixed relL2 {err_m:.3e}, spectral "
+          f"{err_s:.3e}, fp64 relL2 {err_d:.3e}; {len(pk)} RDM peaks within 40 dB, worst mixed "
+          f"{db_m.max():.2e} dB, spectral {db_s.max():.2e} dB, fp64 {db_d.max():.2e} dB")
     assert len(pk) >= 3
-    assert err_d <= TOL_FP64 and err_m <= TOL_MIXED
-    assert db_m.max() <= TOL_PEAK_DB and db_d.max() <= TOL_PEAK_DB
+    assert err_d <= TOL_FP64 and err_m <= TOL_MIXED and err_s <= TOL_MIXED
+    assert max(db_m.max(), db_s.max(), db_d.max()) <= TOL_PEAK_DB
 
 
 def _channels_scene(sc, tx_idx, rx_idx):
@@ -101,6 +105,7 @@ def test_config3_timed_frame(sim):
     assert st["n_grazing"] == int((fr.state == oracle.GRAZE).sum())
     assert st["n_terms"] == fr.n_terms()
     a_m = adc_m.cpu().numpy()
+    a_s = sim.simulate(pkg.PATH_SPECTRAL, out=adc_m).cpu().numpy()
     del adc_m
     torch.cuda.empty_cache()
 
@@ -116,6 +121,8 @@ def test_config3_timed_frame(sim):
     ref = fr.adc_entries(ent)
     err_mo = rel_l2(a_m[ent[:, 0], ent[:, 1], ent[:, 2]], ref)
     err_row = rel_l2(a_m[97, 131], ref[E:])
+    err_so = rel_l2(a_s[ent[:, 0], ent[:, 1], ent[:, 2]], ref)
+    err_srow = rel_l2(a_s[97, 131], ref[E:])
 
     # plain FP64 path: TX 11 x RX {0, 15}, whole channels at 256 x 512
     sc2 = _channels_scene(sc, [11], [0, 15])
@@ -131,12 +138,15 @@ def test_config3_timed_frame(sim):
     err_do = rel_l2(a_d[ent2[:, 0], ent2[:, 1], ent2[:, 2]], ref2)
     chans = [11 * 16 + 0, 11 * 16 + 15]
     err_md = rel_l2(a_m[chans], a_d)
+    err_sd = rel_l2(a_s[chans], a_d)
     print(f"config3 timed frame: {st['n_facets']} facets, {st['n_terms']} terms, records v/s/e "
           f"{st['n_vertex']}/{st['n_series']}/{st['n_edge']}, grazing {st['n_grazing']}; mixed vs "
           f"oracle {err_mo:.3e} ({len(ent)} entries), chirp row {err_row:.3e}; fp64 (2 whole "
           f"channels, {st2['n_terms']} terms) vs oracle {err_do:.3e}; mixed vs fp64 on those "
-          f"channels {err_md:.3e}")
+          f"channels {err_md:.3e}; spectral vs oracle {err_so:.3e}, chirp row {err_srow:.3e}, "
+          f"vs fp64 channels {err_sd:.3e}")
     assert err_mo <= TOL_MIXED and err_row <= TOL_MIXED
+    assert err_so <= TOL_MIXED and err_srow <= TOL_MIXED and err_sd <= TOL_MIXED
     assert err_do <= TOL_FP64
     assert err_md <= TOL_MIXED
 
