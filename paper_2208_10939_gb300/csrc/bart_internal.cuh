@@ -93,13 +93,16 @@ constexpr int kStatusStackOverflow = 1;
 
 // ---- scene + BVH (scene_bvh.cu) ----
 // tri32: per facet 12 floats -- the world vertices rounded to FP32 and the
-// largest |coordinate| among them (for the visibility FP32 pre-test)
+// largest |coordinate| among them (for the visibility FP32 pre-test);
+// fac_lo: per facet 12 floats, the rounding residues of the FP32 centroid
+// and vertex offsets in FacetRec (c - (double)rec.c, dv - (double)rec.dv),
+// so that c and dv are available as double-float pairs
 // the world-facet kernel (its t0 argument is updated in replayed frame graphs)
 const void *build_facets_kernel_fn(int *t0_arg_index, int *n_args);
 void launch_build_facets(const MeshDesc *meshes, const InstDev *insts, int n_inst,
                          int64_t F, double t0, double *tri64, float *tri32, double *c64,
                          FacetRec *fac, float *aabb, float *vel32, unsigned int *bounds,
-                         double *ref64, float *ref32, cudaStream_t s);
+                         double *ref64, float *ref32, float *fac_lo, cudaStream_t s);
 void launch_morton(const FacetRec *fac, int64_t F, const unsigned int *bounds,
                    uint32_t *keys, int32_t *vals, cudaStream_t s);
 // Stable LSD radix sort of (key, value) pairs on the low `bits` bits.
@@ -158,6 +161,7 @@ struct SynthArgs {
     const float *vel32;      // per instance, 4 floats (xyz, pad)
     const double *ref64;     // per instance, origin at t0 (3 doubles)
     const float *ref32;      // per instance, origin at t0 (4 floats)
+    const float *fac_lo;     // per facet 12 floats: residues of FacetRec c[3], dv[9]
     const int32_t *vis_idx;  // [O][F]
     const int32_t *vis_cnt;  // [O + A]
     // virtual channels: VO = scenes x O rows of the output; row v reads

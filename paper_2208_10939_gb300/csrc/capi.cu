@@ -138,6 +138,7 @@ struct bart_ctx {
     DevBuf<double> ref64;               // instance origins at t0 (delay reference points)
     DevBuf<float> ref32;
     DevBuf<FacetRec> fac;
+    DevBuf<float> fac_lo;
     DevBuf<unsigned int> bounds;
     DevBuf<uint32_t> keys, keys_tmp, sort_temp;
     DevBuf<int32_t> vals, vals_tmp;
@@ -233,7 +234,8 @@ struct bart_ctx {
             delete m;
         }
         d_meshes.release(); d_insts.release(); tri64.release(); tri32.release(); c64.release();
-        vel64.release(); vel32.release(); aabb.release(); fac.release(); bounds.release();
+        vel64.release(); vel32.release(); aabb.release(); fac.release(); fac_lo.release();
+        bounds.release();
         ref64.release(); ref32.release();
         keys.release(); keys_tmp.release(); sort_temp.release(); vals.release();
         vals_tmp.release(); nodes.release(); parent.release(); leaf_parent.release();
@@ -606,6 +608,7 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
     BART_TRY(ctx->ref32.ensure(4 * I, "instance origins (f32)"));
     BART_TRY(ctx->aabb.ensure(6 * F, "facet boxes"));
     BART_TRY(ctx->fac.ensure(F, "facet records"));
+    BART_TRY(ctx->fac_lo.ensure(12 * F, "facet record residues"));
     BART_TRY(ctx->keys.ensure(F, "morton keys"));
     BART_TRY(ctx->keys_tmp.ensure(F, "morton keys"));
     BART_TRY(ctx->vals.ensure(F, "sort values"));
@@ -723,7 +726,7 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
         nv.next("bart facets");
         launch_build_facets(ctx->d_meshes.p, ctx->d_insts.p, I, F, t0v, ctx->tri64.p, ctx->tri32.p,
                             ctx->c64.p, ctx->fac.p, ctx->aabb.p, ctx->vel32.p, ctx->bounds.p,
-                            ctx->ref64.p, ctx->ref32.p, s);
+                            ctx->ref64.p, ctx->ref32.p, ctx->fac_lo.p, s);
         launches += 1;
         if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[1], s), "cudaEventRecord");
         // the mixed and spectral paths' kinematics rows need only the world
@@ -787,6 +790,7 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
         a.vel32 = ctx->vel32.p;
         a.ref64 = ctx->ref64.p;
         a.ref32 = ctx->ref32.p;
+        a.fac_lo = ctx->fac_lo.p;
         a.vis_idx = ctx->vis_idx.p;
         a.vis_cnt = ctx->vis_cnt.p;
         a.VO = B * O;

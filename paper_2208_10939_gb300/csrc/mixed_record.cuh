@@ -34,6 +34,45 @@ __device__ __forceinline__ void df_horner_step(float &xh, float &xl, float t, fl
     xl = __fsub_rn(sl, __fsub_rn(xh, sh));
 }
 
+// a + b = s + e exactly (Knuth's two-sum)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// unit vector of d = sh + sl (|sl| ~ ulp(sh)) as double-float pairs: the
+// norm's square in double-float, 1/sqrt by rsqrtf and one Newton step on
+// its double-float residual h = 1 - |d|^2 r0^2 (|h| ~ 1e-7, so the step
+// leaves ~h^2), then d r
+__device__ __forceinline__ void df_unit(const float sh[3], const float sl[3], float uh[3],
+                                        float ul[3])
+{
+    float p[3], pe = 0.f, cross = 0.f;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        p[r] = __fmul_rn(sh[r], sh[r]);
+        pe += __fmaf_rn(sh[r], sh[r], -p[r]);
+        cross += sh[r] * sl[r];
+    }
+    float q1, e1, qh, e2;
+    two_sum(p[0], p[1], q1, e1);
+    two_sum(q1, p[2], qh, e2);
+    const float ql = (e1 + e2) + pe + 2.f * cross;
+    const float r0 = rsqrtf(qh);
+    const float y = __fmul_rn(r0, r0), yl = __fmaf_rn(r0, r0, -y);
+    const float z = __fmul_rn(qh, y);
+    const float zl = __fmaf_rn(qh, y, -z) + (qh * yl + ql * y);
+    const float h = __fsub_rn(1.f, z) - zl;     // 1 - z exact: z is within 1e-6 of 1
+    const float rl = 0.5f * r0 * h;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        uh[r] = __fmul_rn(sh[r], r0);
+        ul[r] = __fmaf_rn(sh[r], r0, -uh[r]) + (sh[r] * rl + sl[r] * r0);
+    }
+}
+
 // (x0, hi, lo, R) from the double-float cycles x0u = xh + xl and R:
 // x0 = frac(x0u), hi + lo = frac(x0u mu / (fs f0)), hi a multiple of 2^-14
 __device__ __forceinline__ float4 kin_finish(float xh, float xl, float R, float mfh, float mfl)
@@ -101,6 +140,7 @@ __device__ __forceinline__ void kin_eval2(const float4 *__restrict__ rt,
 
 struct MixConsts {
     float f0c;            // f0 / c                    cycles per metre at f0
+    float f0c_lo;         // its rounding residue (f0 / c = f0c + f0c_lo in double-float)
     float muc;            // mu / (fs c)               cycles per metre per sample
     float f0c_fs;         // f0 / (c fs)
     float mu_c2fs;        // mu / (c^2 fs)
@@ -115,6 +155,7 @@ struct MixConsts {
     float out_scale;      // C (c / (2 pi f0))^2
     float tc;
     float ant[kMaxAnt][3];
+    float ant_lo[kMaxAnt][3];   // rounding residues of ant
 };
 
 // One record per (facet, channel, chirp), 24 words in shared memory; the
@@ -157,35 +198,45 @@ __device__ __forceinline__ int build_mixed_record(const SynthArgs &A, const MixC
     // directions t, r and the amplitude's ranges: from the facet
     // centroid, or (far field) from the instance origin, whose
     // plane waves every facet of the instance sees
+    // The origin o(t_n) = o0 + v t_n is never formed in FP32: at tens of
+    // metres its rounding would repeat with the instance's per-chirp step
+    // v T_c (the same for every facet of the instance, so coherent across
+    // them: a Doppler spur).  Each direction is normalised from the
+    // constant B = p - o0 and the small D = -v t_n instead.
     float th[3], rh[3], Rt, Rr;
+    const float D[3] = {-vv.x * w.tn, -vv.y * w.tn, -vv.z * w.tn};
+    float o0[3];
     if (A.rd.far_field) {
         const float4 rf = reinterpret_cast<const float4 *>(A.ref32)[fr.inst];
-        const float ox = fmaf(vv.x, w.tn, rf.x), oy = fmaf(vv.y, w.tn, rf.y),
-                    oz = fmaf(vv.z, w.tn, rf.z);
-        th[0] = w.ptx[0] - ox; th[1] = w.ptx[1] - oy; th[2] = w.ptx[2] - oz;
-        rh[0] = w.prx[0] - ox; rh[1] = w.prx[1] - oy; rh[2] = w.prx[2] - oz;
-        Rt = sqrtf(th[0] * th[0] + th[1] * th[1] + th[2] * th[2]);
-        Rr = sqrtf(rh[0] * rh[0] + rh[1] * rh[1] + rh[2] * rh[2]);
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            th[r] /= Rt;
-            rh[r] /= Rr;
-        }
+        o0[0] = rf.x; o0[1] = rf.y; o0[2] = rf.z;
     } else {
-        const float cx = fmaf(vv.x, w.tn, fr.c[0]);
-        const float cy = fmaf(vv.y, w.tn, fr.c[1]);
-        const float cz = fmaf(vv.z, w.tn, fr.c[2]);
-        th[0] = w.ptx[0] - cx; th[1] = w.ptx[1] - cy; th[2] = w.ptx[2] - cz;
-        rh[0] = w.prx[0] - cx; rh[1] = w.prx[1] - cy; rh[2] = w.prx[2] - cz;
-        const float it = rsqrtf(th[0] * th[0] + th[1] * th[1] + th[2] * th[2]);
-        const float ir = rsqrtf(rh[0] * rh[0] + rh[1] * rh[1] + rh[2] * rh[2]);
+        o0[0] = fr.c[0]; o0[1] = fr.c[1]; o0[2] = fr.c[2];
+    }
+    {
+        float Bt[3], Br[3];
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
-            th[r] *= it;
-            rh[r] *= ir;
+            Bt[r] = w.ptx[r] - o0[r];
+            Br[r] = w.prx[r] - o0[r];
         }
-        Rt = kt.w;
-        Rr = kr.w;
+        const float dd = D[0] * D[0] + D[1] * D[1] + D[2] * D[2];
+        const float qt = (Bt[0] * Bt[0] + Bt[1] * Bt[1] + Bt[2] * Bt[2]) +
+                         fmaf(2.f, Bt[0] * D[0] + Bt[1] * D[1] + Bt[2] * D[2], dd);
+        const float qr = (Br[0] * Br[0] + Br[1] * Br[1] + Br[2] * Br[2]) +
+                         fmaf(2.f, Br[0] * D[0] + Br[1] * D[1] + Br[2] * D[2], dd);
+        const float it = rsqrtf(qt), ir = rsqrtf(qr);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            th[r] = fmaf(Bt[r], it, D[r] * it);
+            rh[r] = fmaf(Br[r], ir, D[r] * ir);
+        }
+        if (A.rd.far_field) {
+            Rt = qt * it;
+            Rr = qr * ir;
+        } else {
+            Rt = kt.w;
+            Rr = kr.w;
+        }
     }
     float b[3];
 #pragma unroll
@@ -242,51 +293,82 @@ __device__ __forceinline__ int build_mixed_record(const SynthArgs &A, const MixC
     // Large facets (f0 |u_v| / c beyond 64 cycles, |u| over ~0.25 m): the
     // FP32 offsets, directions and the product f0 u / c would put ~1e-4 rad
     // into the vertex phases, so u_v and the phases derived from it are
-    // formed in FP64 from the FP64 world vertices (the FP32 values remain
-    // for the weights and steps, which need only relative accuracy).
-    double ud[3];
+    // formed in double-float arithmetic (FP32 pairs, ~1e-12 relative) from
+    // the FP32 centroid, offsets and antenna positions and their rounding
+    // residues; the FP32 u_v remain for the weights and steps, which need
+    // only relative accuracy.  u_v = b . dv_v with b = t + r the sum of the
+    // unit vectors toward the antennas (dv_v lies in the facet plane, so
+    // b's in-plane part gives the same product).
+    float ul[3] = {0.f, 0.f, 0.f};
     const bool large = K.f0c * fmaxf(fmaxf(fabsf(u[0]), fabsf(u[1])), fabsf(u[2])) > 64.f;
     if (large) {
-        const double vx = A.vel64[3 * fr.inst], vy = A.vel64[3 * fr.inst + 1],
-                     vz = A.vel64[3 * fr.inst + 2];
-        const double tnd = (double)w.sl * A.rd.Tc;
-        const double *c0 = A.c64 + 3 * (int64_t)k;
-        const double c[3] = {c0[0] + vx * tnd, c0[1] + vy * tnd, c0[2] + vz * tnd};
-        double from[3] = {c[0], c[1], c[2]};
+        const float *res = A.fac_lo + 12 * (int64_t)k;
+        // the origin of the directions at the chirp start: the centroid,
+        // or (far field) the instance origin
+        float oh[3], ol[3];
         if (A.rd.far_field) {
-            const double *r0 = A.ref64 + 3 * fr.inst;
-            from[0] = r0[0] + vx * tnd;
-            from[1] = r0[1] + vy * tnd;
-            from[2] = r0[2] + vz * tnd;
+            const float4 rf = reinterpret_cast<const float4 *>(A.ref32)[fr.inst];
+            oh[0] = rf.x; oh[1] = rf.y; oh[2] = rf.z;
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+                ol[r] = (float)(A.ref64[3 * fr.inst + r] - (double)oh[r]);
+        } else {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                oh[r] = fr.c[r];
+                ol[r] = res[r];
+            }
         }
-        const int tx = w.ant_t, rx = w.ant_r;
-        double bd[3], dt[3], dr[3];
-        for (int r = 0; r < 3; ++r) {
-            dt[r] = A.rd.ant[tx][r] - from[r];
-            dr[r] = A.rd.ant[rx][r] - from[r];
+        const float vel[3] = {vv.x, vv.y, vv.z};
+        float bh[3] = {0.f, 0.f, 0.f}, bl[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int ant = e == 0 ? w.ant_t : w.ant_r;
+            float sh[3], sl[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                // antenna - origin - v t_n, as sh + sl
+                float d1, e1, d2, e2;
+                two_sum(K.ant[ant][r], -oh[r], d1, e1);
+                two_sum(d1, -(vel[r] * w.tn), d2, e2);
+                sh[r] = d2;
+                sl[r] = (e1 + e2) + (K.ant_lo[ant][r] - ol[r]);
+            }
+            float th_[3], tl_[3];
+            df_unit(sh, sl, th_, tl_);
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                float s_, e_;
+                two_sum(bh[r], th_[r], s_, e_);
+                bh[r] = s_;
+                bl[r] = bl[r] + tl_[r] + e_;
+            }
         }
-        const double it = 1.0 / sqrt(dt[0] * dt[0] + dt[1] * dt[1] + dt[2] * dt[2]);
-        const double ir = 1.0 / sqrt(dr[0] * dr[0] + dr[1] * dr[1] + dr[2] * dr[2]);
-        for (int r = 0; r < 3; ++r) bd[r] = dt[r] * it + dr[r] * ir;
-        const double *tv = A.tri64 + 9 * (int64_t)k;
-        const double e1[3] = {tv[3] - tv[0], tv[4] - tv[1], tv[5] - tv[2]};
-        const double e2[3] = {tv[6] - tv[0], tv[7] - tv[1], tv[8] - tv[2]};
-        double nd[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
-                        e1[0] * e2[1] - e1[1] * e2[0]};
-        const double in = 1.0 / sqrt(nd[0] * nd[0] + nd[1] * nd[1] + nd[2] * nd[2]);
-        const double bn = (bd[0] * nd[0] + bd[1] * nd[1] + bd[2] * nd[2]) * in * in;
-        for (int r = 0; r < 3; ++r) bd[r] -= bn * nd[r];
+#pragma unroll
         for (int v = 0; v < 3; ++v) {
-            ud[v] = bd[0] * (tv[3 * v] - c0[0]) + bd[1] * (tv[3 * v + 1] - c0[1]) +
-                    bd[2] * (tv[3 * v + 2] - c0[2]);
-            u[v] = (float)ud[v];
+            float p[3], pe = 0.f;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const float dh = fr.dv[3 * v + r], dl = res[3 + 3 * v + r];
+                p[r] = __fmul_rn(bh[r], dh);
+                pe += __fmaf_rn(bh[r], dh, -p[r]) + bh[r] * dl + bl[r] * dh;
+            }
+            float q, e1, uh_, e2;
+            two_sum(p[0], p[1], q, e1);
+            two_sum(q, p[2], uh_, e2);
+            const float ulo = (e1 + e2) + pe;
+            u[v] = uh_ + ulo;
+            ul[v] = ulo - (u[v] - uh_);
         }
     }
-    // frac(x0 - f0 u / c) for a u of the record: FP64 on large facets
-    auto vphase = [&](float x0, float uf, double udv) -> float {
-        if (!large) return red1(x0 - K.f0c * uf);
-        const double y = (double)x0 - K.f0c_d * udv;
-        return (float)(y - rint(y));
+    // frac(x0 - f0 u / c) for a u of the record (u + ul in double-float on
+    // large facets; ul = 0 otherwise)
+    auto vphase = [&](float x0, float uh, float ulo) -> float {
+        if (!large) return red1(x0 - K.f0c * uh);
+        float y = __fmul_rn(K.f0c, uh);
+        const float yl = __fmaf_rn(K.f0c, uh, -y) + (K.f0c * ulo + K.f0c_lo * uh);
+        y = __fsub_rn(y, rintf(y));               // exact
+        return red1(__fsub_rn(x0, y) - yl);
     };
     const float umin = fminf(fminf(u[0], u[1]), u[2]);
     const float umax = fmaxf(fmaxf(u[0], u[1]), u[2]);
@@ -337,7 +419,10 @@ __device__ __forceinline__ int build_mixed_record(const SynthArgs &A, const MixC
             const float beta = 0.5f * (u[i] + u[i1]);
             const float gam = 0.5f * (u[i1] - u[i]);
             const float ci = (e[0] * nxb[0] + e[1] * nxb[1] + e[2] * nxb[2]) / bt2;
-            R[4 + 4 * i] = vphase(0.f, beta, 0.5 * (ud[i] + ud[i1]));
+            // the mid-edge projection in double-float: halving is exact
+            float bs, be;
+            two_sum(u[i], u[i1], bs, be);
+            R[4 + 4 * i] = vphase(0.f, 0.5f * bs, 0.5f * (be + ul[i] + ul[i1]));
             R[5 + 4 * i] = -K.muc * beta;
             R[6 + 4 * i] = K.k0 * gam;
             R[7 + 4 * i] = K.k0 * ci * g;
@@ -356,7 +441,7 @@ __device__ __forceinline__ int build_mixed_record(const SynthArgs &A, const MixC
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
             const float ua = u[v], ub_ = u[(v + 1) % 3], uc = u[(v + 2) % 3];
-            R[v] = vphase(ph0c, ua, ud[v]);
+            R[v] = vphase(ph0c, ua, ul[v]);
             const float lo = loc - K.muc * ua;
             R[3 + v] = lo;
             R[6 + v] = __fdividef(-A2, (ua - ub_) * (ua - uc));
@@ -436,6 +521,7 @@ inline MixConsts mix_consts(const RadarDev &rd)
     const double c = kC0, fs = rd.fs, mu = rd.slope, f0 = rd.f0;
     const double f_max = f0 + mu * (rd.M - 1) / fs;
     K.f0c = (float)(f0 / c);
+    K.f0c_lo = (float)(f0 / c - (double)K.f0c);
     K.muc = (float)(mu / (fs * c));
     K.f0c_fs = (float)(f0 / (c * fs));
     K.mu_c2fs = (float)(mu / (c * c * fs));
@@ -455,7 +541,10 @@ inline MixConsts mix_consts(const RadarDev &rd)
     K.out_scale = (float)(camp * lk * lk);
     K.tc = (float)rd.Tc;
     for (int a = 0; a < kMaxAnt; ++a)
-        for (int r = 0; r < 3; ++r) K.ant[a][r] = (float)rd.ant[a][r];
+        for (int r = 0; r < 3; ++r) {
+            K.ant[a][r] = (float)rd.ant[a][r];
+            K.ant_lo[a][r] = (float)(rd.ant[a][r] - (double)K.ant[a][r]);
+        }
     return K;
 }
 

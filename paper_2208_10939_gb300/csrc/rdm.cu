@@ -10,8 +10,10 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "bart_internal.cuh"
+#include "fft_reg.cuh"
 #include "fft_stockham.cuh"
 
 namespace bart {
@@ -197,6 +199,98 @@ __global__ void doppler_sum_kernel(const typename Cplx<T>::type *__restrict__ Xt
     }
 }
 
+// -------------------------------------------------------------------------
+// Register-resident variant (complex64, power-of-two M and N, fft_reg.cuh):
+// the same two passes without the transposed intermediate.  The range pass
+// keeps X[o][n][r] in natural order (each thread holds R0 samples of a row,
+// loaded and stored with unit stride across the row's T threads); the
+// Doppler pass gives each of RB consecutive range bins T threads (bins
+// fastest, so a warp's loads of one chirp are RB consecutive complex) and
+// sums |Y|^2 over its channel group in registers, each thread owning the
+// same R0 cells for every channel.  Blocks loop over rows (range) or
+// channels (Doppler) so that the per-thread twiddles and window values,
+// computed once, serve many transforms.
+// -------------------------------------------------------------------------
+constexpr int kRegThreads = 256;
+
+template <int M>
+__global__ void __launch_bounds__(kRegThreads, 2)
+range_fft_reg_kernel(const float2 *__restrict__ adc, float2 *__restrict__ X, int64_t rows,
+                     int window)
+{
+    using namespace fftr;
+    constexpr int R0 = Plan<M>::R0, T = M / R0, RPB = kRegThreads / T;
+    __shared__ float2 buf[RPB * M];
+    const int g = threadIdx.x / T, tid = threadIdx.x % T;
+    FftTw<M> tw;
+    tw.init(tid);
+    float wv[R0];
+#pragma unroll
+    for (int k = 0; k < R0; ++k) wv[k] = window_val<float>(tid + T * k, M, window);
+    for (int64_t row0 = (int64_t)blockIdx.x * RPB; row0 < rows; row0 += (int64_t)gridDim.x * RPB) {
+        const int64_t row = row0 + g;
+        const bool valid = row < rows;
+        float2 a[R0];
+        const float2 *in = adc + row * M + tid;
+#pragma unroll
+        for (int k = 0; k < R0; ++k) {
+            const float2 v = valid ? in[T * k] : make_float2(0.f, 0.f);
+            a[k] = make_float2(v.x * wv[k], v.y * wv[k]);
+        }
+        fft<M>(a, tid, buf + g * M, tw);
+        if (valid) {
+            float2 *out = X + row * M;
+#pragma unroll
+            for (int i = 0; i < R0; ++i) out[fft_out_index<M>(tid, i)] = a[i];
+        }
+        __syncthreads();      // buf is reused by the next row
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kRegThreads, 2)
+doppler_sum_reg_kernel(const float2 *__restrict__ X, int M, int CPB, int O, int window,
+                       float *__restrict__ part)
+{
+    using namespace fftr;
+    constexpr int R0 = Plan<N>::R0, T = N / R0, RB = kRegThreads / T;
+    __shared__ float2 buf[RB * (N + 1)];
+    const int c = threadIdx.x % RB, tid = threadIdx.x / RB;
+    FftTw<N> tw;
+    tw.init(tid);
+    float wv[R0];
+#pragma unroll
+    for (int k = 0; k < R0; ++k) wv[k] = window_val<float>(tid + T * k, N, window);
+    const int r = blockIdx.x * RB + c;
+    const int gg = blockIdx.y;                       // group of channels (over all scenes)
+    const int G = (O + CPB - 1) / CPB;               // groups per scene
+    const int scene = gg / G, gi = gg % G;
+    const int o0 = scene * O + gi * CPB, o1 = scene * O + min(O, (gi + 1) * CPB);
+    float acc[R0];
+#pragma unroll
+    for (int i = 0; i < R0; ++i) acc[i] = 0.f;
+    for (int o = o0; o < o1; ++o) {
+        float2 a[R0];
+        const float2 *in = X + ((int64_t)o * N + tid) * M + r;
+#pragma unroll
+        for (int k = 0; k < R0; ++k) {
+            const float2 v = in[(int64_t)T * k * M];
+            a[k] = make_float2(v.x * wv[k], v.y * wv[k]);
+        }
+        fft<N>(a, tid, buf + c * (N + 1), tw);
+#pragma unroll
+        for (int i = 0; i < R0; ++i) acc[i] = fmaf(a[i].x, a[i].x, fmaf(a[i].y, a[i].y, acc[i]));
+        __syncthreads();
+    }
+    float *dst = part + (int64_t)gg * M * N + (int64_t)r * N;
+#pragma unroll
+    for (int i = 0; i < R0; ++i) {
+        const int d = fft_out_index<N>(tid, i);
+        const int ds = d + (N >> 1);
+        dst[ds >= N ? ds - N : ds] = acc[i];
+    }
+}
+
 // range bins per Doppler block: the largest power of two RB with RB N <= 512
 // that divides M
 // -------------------------------------------------------------------------
@@ -328,6 +422,69 @@ static int rdm_cpb(int O, int blocks_per_channel_group, int scenes)
     return cpb;
 }
 
+// the register-resident kernels of lengths M (range) and N (Doppler)
+template <int M>
+static void range_reg_launch(const float2 *adc, float2 *X, int64_t rows, int window,
+                             cudaStream_t s)
+{
+    constexpr int RPB = kRegThreads / (M / fftr::Plan<M>::R0);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, range_fft_reg_kernel<M>, kRegThreads, 0);
+    const int64_t need = (rows + RPB - 1) / RPB;
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)sms * std::max(1, per_sm)));
+    range_fft_reg_kernel<M><<<(unsigned int)grid, kRegThreads, 0, s>>>(adc, X, rows, window);
+}
+
+template <int N>
+static void doppler_reg_launch(const float2 *X, int M, int O, int groups, int window, float *part,
+                               int *G_out, cudaStream_t s)
+{
+    constexpr int RB = kRegThreads / (N / fftr::Plan<N>::R0);
+    const int CPB = rdm_cpb(O, M / RB, groups);
+    const int G = (O + CPB - 1) / CPB;
+    *G_out = G;
+    doppler_sum_reg_kernel<N><<<dim3((unsigned int)(M / RB), (unsigned int)(G * groups)),
+                                kRegThreads, 0, s>>>(X, M, CPB, O, window, part);
+}
+
+static bool reg_len_ok(int L) { return L >= 16 && L <= 1024 && is_pow2_len(L); }
+
+// columns per Doppler block of the register kernels
+static int reg_rb(int N) { return kRegThreads / (N / (N == 32 || N == 64 || N == 512 ? 8 : 16)); }
+
+static bool rdm_reg_supported(const RadarDev &rd)
+{
+    return reg_len_ok(rd.M) && reg_len_ok(rd.N) && rd.M % reg_rb(rd.N) == 0;
+}
+
+static int run_rdm_reg(const float2 *adc, const RadarDev &rd, int groups, float2 *X, float *part,
+                       cudaStream_t s)
+{
+    const int64_t rows = (int64_t)rd.O * groups * rd.N;
+    switch (rd.M) {
+    case 16: range_reg_launch<16>(adc, X, rows, rd.window, s); break;
+    case 32: range_reg_launch<32>(adc, X, rows, rd.window, s); break;
+    case 64: range_reg_launch<64>(adc, X, rows, rd.window, s); break;
+    case 128: range_reg_launch<128>(adc, X, rows, rd.window, s); break;
+    case 256: range_reg_launch<256>(adc, X, rows, rd.window, s); break;
+    case 512: range_reg_launch<512>(adc, X, rows, rd.window, s); break;
+    default: range_reg_launch<1024>(adc, X, rows, rd.window, s); break;
+    }
+    int G = 1;
+    switch (rd.N) {
+    case 16: doppler_reg_launch<16>(X, rd.M, rd.O, groups, rd.window, part, &G, s); break;
+    case 32: doppler_reg_launch<32>(X, rd.M, rd.O, groups, rd.window, part, &G, s); break;
+    case 64: doppler_reg_launch<64>(X, rd.M, rd.O, groups, rd.window, part, &G, s); break;
+    case 128: doppler_reg_launch<128>(X, rd.M, rd.O, groups, rd.window, part, &G, s); break;
+    case 256: doppler_reg_launch<256>(X, rd.M, rd.O, groups, rd.window, part, &G, s); break;
+    case 512: doppler_reg_launch<512>(X, rd.M, rd.O, groups, rd.window, part, &G, s); break;
+    default: doppler_reg_launch<1024>(X, rd.M, rd.O, groups, rd.window, part, &G, s); break;
+    }
+    return G;
+}
+
 template <typename T>
 static void run_rdm(const void *adc, const RadarDev &rd, int groups, void *ws, float *rdm,
                     cudaStream_t s)
@@ -335,6 +492,15 @@ static void run_rdm(const void *adc, const RadarDev &rd, int groups, void *ws, f
     using C = typename Cplx<T>::type;
     const int M = rd.M, N = rd.N, O = rd.O;
     const int64_t Oall = (int64_t)O * groups;
+    const int64_t MN = (int64_t)M * N;
+    if (std::is_same<T, float>::value && rdm_reg_supported(rd)) {
+        float2 *X = reinterpret_cast<float2 *>(ws);
+        float *part = reinterpret_cast<float *>(X + Oall * N * M);
+        const int G = run_rdm_reg(reinterpret_cast<const float2 *>(adc), rd, groups, X, part, s);
+        rdm_sum_kernel<float><<<(unsigned int)((MN * groups + 255) / 256), 256, 0, s>>>(
+            part, G, MN, groups, rdm);
+        return;
+    }
     // range pass, transposed output Xt[o][r][n]
     const int TN = rdm_tn(N, M, sizeof(C));
     const size_t sm1 = (size_t)(2 * TN * M + tw_len(M)) * sizeof(C);
@@ -355,7 +521,6 @@ static void run_rdm(const void *adc, const RadarDev &rd, int groups, void *ws, f
     doppler_sum_kernel<T><<<dim3((unsigned int)(M / RB), (unsigned int)(G * groups)), 256, sm2,
                             s>>>(reinterpret_cast<const C *>(ws), N, M, RB, CPB, O, rd.window,
                                  part);
-    const int64_t MN = (int64_t)M * N;
     rdm_sum_kernel<T><<<(unsigned int)((MN * groups + 255) / 256), 256, 0, s>>>(part, G, MN,
                                                                                groups, rdm);
 }

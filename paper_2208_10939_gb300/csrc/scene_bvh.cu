@@ -44,7 +44,8 @@ __global__ void build_facets_kernel(const MeshDesc *__restrict__ meshes,
                                     double *__restrict__ c64, FacetRec *__restrict__ fac,
                                     float *__restrict__ aabb, float *__restrict__ vel32,
                                     unsigned int *__restrict__ bounds,
-                                    double *__restrict__ ref64, float *__restrict__ ref32)
+                                    double *__restrict__ ref64, float *__restrict__ ref32,
+                                    float *__restrict__ fac_lo)
 {
     const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     float cf[3] = {0.f, 0.f, 0.f};
@@ -93,8 +94,13 @@ __global__ void build_facets_kernel(const MeshDesc *__restrict__ meshes,
             cf[r] = rec.c[r];
         }
         rec.area = (float)(0.5 * nl);
+        for (int r = 0; r < 3; ++r) fac_lo[12 * f + r] = (float)(c[r] - (double)rec.c[r]);
         for (int k = 0; k < 3; ++k)
-            for (int r = 0; r < 3; ++r) rec.dv[3 * k + r] = (float)(v[3 * k + r] - c[r]);
+            for (int r = 0; r < 3; ++r) {
+                const double d = v[3 * k + r] - c[r];
+                rec.dv[3 * k + r] = (float)d;
+                fac_lo[12 * f + 3 + 3 * k + r] = (float)(d - (double)rec.dv[3 * k + r]);
+            }
         const double inl = nl > 0.0 ? 1.0 / nl : 0.0;
         rec.n[0] = (float)(nx * inl);
         rec.n[1] = (float)(ny * inl);
@@ -148,21 +154,21 @@ __global__ void build_facets_kernel(const MeshDesc *__restrict__ meshes,
 const void *build_facets_kernel_fn(int *t0_arg_index, int *n_args)
 {
     *t0_arg_index = 4;      // meshes, insts, n_inst, F, t0, tri64, tri32, c64, fac, aabb,
-    *n_args = 14;           // vel32, bounds, ref64, ref32
+    *n_args = 15;           // vel32, bounds, ref64, ref32, fac_lo
     return reinterpret_cast<const void *>(build_facets_kernel);
 }
 
 void launch_build_facets(const MeshDesc *meshes, const InstDev *insts, int n_inst, int64_t F,
                          double t0, double *tri64, float *tri32, double *c64, FacetRec *fac,
                          float *aabb, float *vel32, unsigned int *bounds, double *ref64,
-                         float *ref32, cudaStream_t s)
+                         float *ref32, float *fac_lo, cudaStream_t s)
 {
     cudaMemsetAsync(bounds, 0xff, 3 * sizeof(unsigned int), s);
     cudaMemsetAsync(bounds + 3, 0, 3 * sizeof(unsigned int), s);
     const int T = 256;
     const unsigned int G = (unsigned int)((F + T - 1) / T);
     build_facets_kernel<<<G, T, 0, s>>>(meshes, insts, n_inst, F, t0, tri64, tri32, c64, fac,
-                                        aabb, vel32, bounds, ref64, ref32);
+                                        aabb, vel32, bounds, ref64, ref32, fac_lo);
 }
 
 // -------------------------------------------------------------------------

@@ -156,6 +156,24 @@ def test_rdm_mixed_radix_lengths(O, N, M, dtype):
     assert np.abs(out.cpu().numpy() - ref).max() <= tol * ref.max()
 
 
+@pytest.mark.parametrize("O,N,M", [(2, 16, 256), (3, 32, 64), (2, 64, 128), (2, 128, 512),
+                                   (1, 256, 1024), (2, 512, 32), (1, 1024, 32), (3, 16, 128)])
+def test_rdm_power_of_two_register_path(O, N, M):
+    """complex64 cubes with power-of-two M and N take the register-resident
+    FFT kernels (every radix plan from 16 to 1024 points appears as M or N;
+    the last case, whose 16-chirp Doppler blocks span 256 range bins,
+    falls back to the shared-memory Stockham path); against numpy's FFT
+    route on a seeded random cube."""
+    rng = np.random.default_rng(O * 104729 + N * 17 + M)
+    cube = (rng.normal(size=(O, N, M)) + 1j * rng.normal(size=(O, N, M))).astype(np.complex64)
+    x = torch.from_numpy(cube).cuda()
+    ref = oracle.range_doppler_map(cube.astype(np.complex128))
+    out = torch.empty((M, N), dtype=torch.float32, device="cuda")
+    pkg.bart_form_rdm_static(x, out, O, N, M)
+    torch.cuda.synchronize()
+    assert np.abs(out.cpu().numpy() - ref).max() <= 1e-5 * ref.max()
+
+
 @pytest.mark.parametrize("M", [256, 384, 512])
 def test_table2_replica(sim, M):
     """Table 2's three experiments (40 m, approaching at 10 m/s, 256 / 384 /
