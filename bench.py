@@ -468,36 +468,42 @@ def detect_timing(pkg, torch, sim, adc, stream, reps: int = 10) -> dict:
 
 
 def adjoint_timing(pkg, sg, torch, dev, reps: int) -> dict:
-    """Differentiable echo on the perturbed-sedan inverse problem: the
-    sedan as target, its copy with 5 mm vertex noise (seed 5) as the
-    variable, L = ||adc(v) - adc_target||^2; forward and adjoint times (CUDA
-    events) and gradient throughput in echo terms per second, FP64 and
-    mixed precision (mixed-path forward, adjoint with FP32 per-sample work),
-    and the mixed gradient's relative L2 distance to the FP64 one."""
+    """Differentiable echo, the RDM inverse problem: the sedan's RDM as
+    target, its copy with 5 mm vertex noise (seed 5) as the variable,
+    L = ||RDM(v, rho) - RDM_target||^2 through both adjoints
+    (bart_rdm_adjoint, then the echo adjoint) with gradients for the vertex
+    positions and the per-facet reflectivities; forward (echo + RDM + loss)
+    and backward times (CUDA events), gradient throughput in echo terms per
+    second, FP64 and mixed precision (mixed-path forward, the FP32 adjoint
+    route), and the mixed gradients' relative L2 distance to the FP64
+    ones."""
     from paper_2208_10939_gb300 import autograd as bag
     s = pkg.Simulator(dev.index or 0)
     try:
         sc = sg.car_scene()
-        out = {"workload": "sedan 20k tris, target vs 5 mm vertex noise (seed 5), "
-                           "L = ||adc - adc_target||^2"}
+        out = {"workload": "sedan 20k tris, RDM target vs 5 mm vertex noise (seed 5), "
+                           "L = ||RDM(v, rho) - RDM_target||^2, gradients for vertices and "
+                           "reflectivities"}
         grads = {}
         for prec in ("fp64", "mixed"):
             es = bag.EchoScene(s, sc, precision=prec)
             v_true = es.vertex_tensor(sc, dev)
+            rho0 = torch.from_numpy(sc.meshes[0].rho.copy()).to(dev)
             with torch.no_grad():
-                target = bag.echo(v_true, None, es).clone()
+                target = bag.range_doppler_map(bag.echo(v_true, None, es), s).clone()
             rng = np.random.default_rng(5)
             v0 = v_true + torch.from_numpy(0.005 * rng.normal(size=tuple(v_true.shape))).to(dev)
             st = pkg.bart_simulate_frame(s.ctx, 0.0, pkg.PATH_FP64,
-                                         torch.empty_like(target, dtype=torch.complex128),
-                                         stats=True)
+                                         torch.empty(s.adc_shape(), dtype=torch.complex128,
+                                                     device=dev), stats=True)
             fwd, bwd = [], []
             for rep in range(reps + 1):          # the first pass warms up (allocations)
                 verts = v0.clone().requires_grad_(True)
+                rho = rho0.clone().requires_grad_(True)
                 e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
                 e0.record()
-                adc = bag.echo(verts, None, es)
-                loss = (adc - target).abs().pow(2).sum()
+                rdm = bag.range_doppler_map(bag.echo(verts, rho, es), s)
+                loss = (rdm - target).pow(2).sum()
                 e1.record()
                 loss.backward()
                 e2.record()
@@ -505,16 +511,19 @@ def adjoint_timing(pkg, sg, torch, dev, reps: int) -> dict:
                 if rep > 0:
                     fwd.append(e0.elapsed_time(e1))
                     bwd.append(e0.elapsed_time(e2) - e0.elapsed_time(e1))
-            grads[prec] = verts.grad.detach().clone()
+            grads[prec] = (verts.grad.detach().clone(), rho.grad.detach().clone())
             terms = st["n_terms"]
             key = "" if prec == "fp64" else "_mixed"
             out["forward_ms" + key] = min(fwd)
             out["backward_ms" + key] = min(bwd)
+            out["backward_over_forward" + key] = min(bwd) / min(fwd)
             out["gradient_terms_per_s" + key] = terms / (min(bwd) / 1e3)
             out["terms"] = terms
-            out["parameters"] = int(verts.numel())
-        out["mixed_gradient_rel_l2_vs_fp64"] = float(
-            torch.linalg.norm(grads["mixed"] - grads["fp64"]) / torch.linalg.norm(grads["fp64"]))
+            out["parameters"] = int(verts.numel() + rho.numel())
+        for i, name in ((0, "vertices"), (1, "reflectivity")):
+            out[f"mixed_gradient_rel_l2_vs_fp64_{name}"] = float(
+                torch.linalg.norm(grads["mixed"][i] - grads["fp64"][i]) /
+                torch.linalg.norm(grads["fp64"][i]))
         return out
     finally:
         s.close()

@@ -281,6 +281,55 @@ class Frame:
 # ---------------------------------------------------------------------------
 # range-Doppler map (Sec. 3.3)
 # ---------------------------------------------------------------------------
+def echo_gradient(scene, W: np.ndarray, h: float = 1e-6, state: np.ndarray | None = None):
+    """Reference gradient of the real functional L = Re sum conj(W) adc of
+    the ADC cube (every differentiable loss of the cube reduces to one at
+    the point of evaluation, with W = dL/dRe(adc) + i dL/dIm(adc)) with
+    respect to the mesh-local vertex coordinates and the per-facet
+    reflectivities of a scene with one instance, the visibility held at
+    ``state`` (default: the scene's own) -- the fixed-mask derivative the
+    differentiable echo defines.
+
+    Vertex coordinates: fourth-order central differences
+    (8 (L(+h) - L(-h)) - (L(+2h) - L(-2h))) / (12 h) of this module's
+    FP64 frame (truncation O(h^4)).  Reflectivities: L is linear in each
+    rho_f (Eq. 7's amplitude), so (L(rho_f + 1) - L(rho_f - 1)) / 2 is
+    exact.  Returns (dL/dverts (nv, 3), dL/drho (nf,))."""
+    import copy
+    if len(scene.instances) != 1 or len(scene.meshes) != 1:
+        raise ValueError("echo_gradient takes a scene with one mesh and one instance")
+    mesh = scene.meshes[0]
+    if state is None:
+        state = Frame(scene).state
+
+    def loss(verts, rho):
+        m = copy.copy(mesh)
+        m.verts = verts
+        m.rho = rho
+        sc = copy.copy(scene)
+        sc.meshes = [m]
+        return float((np.conj(W) * Frame(sc, state=state).adc_full()).real.sum())
+
+    v0 = np.asarray(mesh.verts, np.float64)
+    r0 = np.asarray(mesh.rho)
+    gv = np.zeros_like(v0)
+    for i in range(v0.shape[0]):
+        for c in range(3):
+            f = {}
+            for k in (-2, -1, 1, 2):
+                v = v0.copy()
+                v[i, c] += k * h
+                f[k] = loss(v, r0)
+            gv[i, c] = (8.0 * (f[1] - f[-1]) - (f[2] - f[-2])) / (12.0 * h)
+    gr = np.zeros(r0.shape[0])
+    for j in range(r0.shape[0]):
+        rp, rm = r0.astype(np.float64).copy(), r0.astype(np.float64).copy()
+        rp[j] += 1.0
+        rm[j] -= 1.0
+        gr[j] = 0.5 * (loss(v0, rp) - loss(v0, rm))
+    return gv, gr
+
+
 def hann(L: int) -> np.ndarray:
     """Symmetric Hann window w[i] = 0.5 - 0.5 cos(2 pi i / (L-1))."""
     if L == 1:

@@ -13,9 +13,18 @@
 //   2. per record, each of the 10 parameters is pushed through the record
 //      construction in forward-mode dual numbers and dotted with rbar.
 // Facet gradients are then mapped to mesh-local vertices (transpose of the
-// instance rotation) and reflectivities.  The mixed variant
-// (bart_simulate_adjoint_mixed) runs stage 1 of vertex-form records in FP32
-// (adj_vertex_mixed); series and edge records and stage 2 stay FP64.
+// instance rotation) and reflectivities.
+//
+// The mixed variant (bart_simulate_adjoint_mixed) takes vertex-form records
+// of the per-facet delay form (all but ~1e-3 of a frame) through FP32 only:
+// stage 1 from the forward mixed record (mixed_record.cuh: the vertex
+// phases, beat frequencies and weights the forward mixed and spectral paths
+// use) with the lanes' phasors advanced by rotation (adj_vertex_f32), and
+// stage 2 as one hand-derived reverse pass through the record construction
+// (vertex_reverse_f32) instead of ten dual-number passes.  FP64 runs at
+// 1/64 of the FP32 rate on this GPU, so the FP64 route of the plain adjoint
+// is kept for the other records (series and edge forms, the reference-point
+// and far-field delay forms) only.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -23,6 +32,7 @@
 #include <type_traits>
 
 #include "bart_internal.cuh"
+#include "mixed_record.cuh"
 #include "record_fp64.cuh"
 
 namespace bart {
@@ -171,6 +181,226 @@ __device__ __forceinline__ void adj_vertex_mixed(const RecAX &X, int m0, double 
     }
 }
 
+// FP32 vertex-form record of the mixed adjoint: the forward mixed record's
+// phase model ph_v(m) = ph0_v + (hi + lo_v) m + p2 m^2 (cycles) and weights
+// w_v, the chirp-start path L0 = R_t + R_r and its rate Ld, and the
+// adjoint's d sqrt(Q) / dQ = 0.5 / R(t) = it + itd t (TX; ir, ird for the
+// RX) to first order in the fast time t
+struct RecF {
+    int kind, pad;          // kind = kRouteF32 (the same leading member as RecA)
+    float ph0[3], lo[3], w[3];
+    float hi, p2, L0, Ld, it, ir, itd, ird;
+};
+constexpr int kRouteF32 = -1;
+
+// Stage 1 of a RecF record over one lane's S samples m0 .. m0 + S - 1: the
+// phasors start from sincospi at m0 and rotate by the chord step of the
+// lane (the curvature p2 (S - 1)^2 / 4 cycles, below 1e-6, is left out);
+// out = {sum zr_v (3), sum fmc zi_v (3), sum aL, sum aL t, sum aL t^2} with
+// z_v = conj(G) exp(j 2 pi ph_v), a = -sum_v w_v zi_v,
+// aL = a (fmc - mu L / c^2), fmc = f_m / c, t = m / fs.
+template <int S>
+__device__ __forceinline__ void adj_vertex_f32(const RecF &F, int m0, const MixConsts &K,
+                                               float muc2, float inv_fs, const float *gr,
+                                               const float *gi, float *out)
+{
+    const float fm0 = (float)m0;
+    const float hm = red1(F.hi * fm0);             // exact: hi is a multiple of 2^-14
+    float zc[3], zs[3], cs[3], ss[3];
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+        const float ph = red1(F.ph0[v] + hm + fmaf(F.lo[v], fm0, F.p2 * fm0 * fm0));
+        sincospif(2.f * ph, &zs[v], &zc[v]);
+        const float st = red1(F.hi + fmaf(F.p2, 2.f * fm0 + (float)(S - 1), F.lo[v]));
+        sincospif(2.f * st, &ss[v], &cs[v]);
+    }
+    float Sw[3] = {0.f, 0.f, 0.f}, Su[3] = {0.f, 0.f, 0.f}, A0 = 0.f, A1 = 0.f, A2 = 0.f;
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+        const float m = fm0 + (float)j;
+        const float fmc = fmaf(m, K.muc, K.f0c);
+        const float t = m * inv_fs;
+        const float L = fmaf(F.Ld, t, F.L0);
+        float a = 0.f;
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+            const float zr = fmaf(gr[j], zc[v], -gi[j] * zs[v]);
+            const float zi = fmaf(gr[j], zs[v], gi[j] * zc[v]);
+            Sw[v] += zr;
+            Su[v] = fmaf(fmc, zi, Su[v]);
+            a = fmaf(-F.w[v], zi, a);
+            const float nc = fmaf(zc[v], cs[v], -zs[v] * ss[v]);
+            zs[v] = fmaf(zc[v], ss[v], zs[v] * cs[v]);
+            zc[v] = nc;
+        }
+        const float aL = a * fmaf(-muc2, L, fmc);
+        A0 += aL;
+        A1 = fmaf(aL, t, A1);
+        A2 = fmaf(aL * t, t, A2);
+    }
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+        out[v] = Sw[v];
+        out[3 + v] = Su[v];
+    }
+    out[6] = A0;
+    out[7] = A1;
+    out[8] = A2;
+}
+
+__device__ __forceinline__ void cross3(const float *a, const float *b, float *c)
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+__device__ __forceinline__ float dot3(const float *a, const float *b)
+{
+    return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2]));
+}
+
+// k_max d_min of the FP32 route (the forward's vertex form starts at kEdgeKd)
+constexpr float kAdjF32Kd = 1.0f;
+
+// k_max times the smallest gap between the facet's in-plane projections
+// u_v = b . dv_v, at the row's chirp start, at least `kd` (FP32 estimate)
+__device__ __forceinline__ bool vertex_well_separated(const FacetRec &fr, const MixRow &w,
+                                                      float kmax, float kd)
+{
+    float b[3] = {0.f, 0.f, 0.f};
+    for (int e = 0; e < 2; ++e) {
+        const float *p = e == 0 ? w.ptx : w.prx;
+        const float d[3] = {p[0] - fr.c[0], p[1] - fr.c[1], p[2] - fr.c[2]};
+        const float id = rsqrtf(dot3(d, d));
+        for (int r = 0; r < 3; ++r) b[r] = fmaf(d[r], id, b[r]);
+    }
+    float u[3];
+    for (int v = 0; v < 3; ++v) u[v] = dot3(b, fr.dv + 3 * v);
+    const float dmin = fminf(fminf(fabsf(u[0] - u[1]), fabsf(u[1] - u[2])), fabsf(u[0] - u[2]));
+    return kmax * dmin >= kd;
+}
+
+// Stage 2 of a vertex-form record, per-facet delay form: the record entries
+// (record_fp64.cuh)
+//   qt0 = |p_t - c(t_n)|^2, qt1 = -2 (p_t - c(t_n)).v (intra-chirp motion),
+//   the same for the RX, u_v = b_t . dv_v, w_v = -A2 / ((u_v - u_a)(u_v - u_b)),
+//   b = t + r, b_t its part in the facet plane, A2 = 2 area rho o / (R_t R_r),
+//   o = n.b / 2 (|.| for two-sided facets),
+// are reversed in FP32 from their adjoints bar = {qt0, qt1, qr0, qr1, u (3),
+// w (3)} to the adjoints of the nine world vertex coordinates at the frame
+// start (c = their mean, dv_v = vertex_v - c) and of rho: g[10].
+__device__ __forceinline__ void vertex_reverse_f32(const FacetRec &fr, const float *vel, float tn,
+                                                   const float *pt, const float *pr, int intra,
+                                                   const float *bar, float *g)
+{
+    float dv[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) dv[i] = fr.dv[i];
+    float dt[3], dr[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const float cc = fmaf(vel[r], tn, fr.c[r]);
+        dt[r] = pt[r] - cc;
+        dr[r] = pr[r] - cc;
+    }
+    const float Rt = sqrtf(dot3(dt, dt)), Rr = sqrtf(dot3(dr, dr));
+    const float iRt = 1.f / Rt, iRr = 1.f / Rr;
+    float b[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) b[r] = fmaf(dt[r], iRt, dr[r] * iRr);
+    const float e1[3] = {dv[3] - dv[0], dv[4] - dv[1], dv[5] - dv[2]};
+    const float e2[3] = {dv[6] - dv[0], dv[7] - dv[1], dv[8] - dv[2]};
+    float nr[3];
+    cross3(e1, e2, nr);
+    const float nl = sqrtf(dot3(nr, nr)), inl = 1.f / nl;
+    const float nn[3] = {nr[0] * inl, nr[1] * inl, nr[2] * inl};
+    const float area = 0.5f * nl;
+    const float okr = 0.5f * dot3(nn, b);
+    const float sg = (fr.two_sided && okr < 0.f) ? -1.f : 1.f;
+    const float ok = sg * okr;
+    const float iRR = iRt * iRr;
+    const float gg = fr.rho * ok * iRR;
+    const float bn = dot3(b, nn);
+    const float bt[3] = {b[0] - bn * nn[0], b[1] - bn * nn[1], b[2] - bn * nn[2]};
+    float u[3];
+#pragma unroll
+    for (int v = 0; v < 3; ++v) u[v] = dot3(bt, dv + 3 * v);
+    const float A2 = 2.f * area * gg;
+    // w_v = -A2 / D_v, D_v = (u_v - u_a)(u_v - u_b)
+    float ub[3] = {bar[4], bar[5], bar[6]};
+    float A2b = 0.f;
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+        const int a = (v + 1) % 3, c = (v + 2) % 3;
+        const float da = u[v] - u[a], dc = u[v] - u[c];
+        const float iD = 1.f / (da * dc);
+        const float wb = bar[7 + v];
+        A2b -= wb * iD;
+        const float Db = wb * A2 * iD * iD;
+        ub[v] += Db * (dc + da);
+        ub[a] -= Db * dc;
+        ub[c] -= Db * da;
+    }
+    const float areab = 2.f * gg * A2b, gb = 2.f * area * A2b;
+    g[9] = gb * ok * iRR;
+    const float okb = gb * fr.rho * iRR;
+    float Rtb = -gb * gg * iRt, Rrb = -gb * gg * iRr;
+    // u_v = bt . dv_v
+    float btb[3] = {0.f, 0.f, 0.f}, dvb[9];
+#pragma unroll
+    for (int v = 0; v < 3; ++v)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            btb[r] = fmaf(ub[v], dv[3 * v + r], btb[r]);
+            dvb[3 * v + r] = ub[v] * bt[r];
+        }
+    // bt = b - (b.n) n, o = s (n.b) / 2
+    const float bnb = -dot3(nn, btb);
+    float bb[3], nnb[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        bb[r] = btb[r] + bnb * nn[r] + 0.5f * sg * okb * nn[r];
+        nnb[r] = -bn * btb[r] + bnb * b[r] + 0.5f * sg * okb * b[r];
+    }
+    // n = nr / |nr|, area = |nr| / 2
+    const float nnd = dot3(nn, nnb);
+    float nrb[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) nrb[r] = (nnb[r] - nn[r] * nnd) * inl + 0.5f * areab * nn[r];
+    // nr = e1 x e2
+    float e1b[3], e2b[3];
+    cross3(e2, nrb, e1b);
+    cross3(nrb, e1, e2b);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        dvb[3 + r] += e1b[r];
+        dvb[6 + r] += e2b[r];
+        dvb[r] -= e1b[r] + e2b[r];
+    }
+    // b = dt / R_t + dr / R_r; R = |d|; qt0 = |dt|^2, qt1 = -2 dt.v
+    const float bdt = dot3(bb, dt), bdr = dot3(bb, dr);
+    float ccb[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        float dtb = bb[r] * iRt - dt[r] * (bdt * iRt * iRt * iRt) + Rtb * iRt * dt[r] +
+                    2.f * bar[0] * dt[r];
+        float drb = bb[r] * iRr - dr[r] * (bdr * iRr * iRr * iRr) + Rrb * iRr * dr[r] +
+                    2.f * bar[2] * dr[r];
+        if (intra) {
+            dtb -= 2.f * bar[1] * vel[r];
+            drb -= 2.f * bar[3] * vel[r];
+        }
+        ccb[r] = -(dtb + drb);
+    }
+    // c(t_n) = c + v t_n, dv_v = vertex_v - c, c = mean of the vertices
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const float cb = ccb[r] - (dvb[r] + dvb[3 + r] + dvb[6 + r]);
+#pragma unroll
+        for (int v = 0; v < 3; ++v) g[3 * v + r] = dvb[3 * v + r] + cb * (1.f / 3.f);
+    }
+}
+
 __device__ __forceinline__ float warp_sum_f(float v)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -181,11 +411,16 @@ constexpr int kAdjMixMinBlocks = 4;   // resident blocks the mixed variant's reg
 
 template <int S, bool MX>
 __global__ void __launch_bounds__(kAdjWarps * 32, MX ? kAdjMixMinBlocks : 1)
-adjoint_fp64_kernel(SynthArgs A, int W, int NCH, const void *__restrict__ grad, int grad_c64,
-                    double *__restrict__ gfac)
+adjoint_fp64_kernel(SynthArgs A, MixConsts K, int W, int NCH, const void *__restrict__ grad,
+                    int grad_c64, double *__restrict__ gfac)
 {
     using Rec = typename std::conditional<MX, RecAX, RecA>::type;
-    __shared__ Rec sR[kAdjWarps][32];
+    // a lane's record: FP64 (Rec) or, in the mixed variant's FP32 route, RecF
+    union RecU {
+        Rec x;
+        RecF f;
+    };
+    __shared__ RecU sU[kAdjWarps][32];          // .x.kind == kRouteF32: the FP32 route
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t gw = (int64_t)blockIdx.x * kAdjWarps + warp;
     const int N = A.rd.N, M = A.rd.M;
@@ -233,6 +468,36 @@ adjoint_fp64_kernel(SynthArgs A, int W, int NCH, const void *__restrict__ grad, 
     const int32_t *list = A.vis_idx + (int64_t)o * F + (A.vstart ? A.vstart[vrow] : 0);
     const int cnt = A.vcnt[vrow];
 
+    // the mixed variant's FP32 route: per-facet delay form, near field
+    const bool f32_route = MX && !A.rd.delay_ref && !A.rd.far_field;
+    float gfr[S], gfi[S];
+    MixRow w;
+    float muc2 = 0.f, inv_fs = 0.f;
+    if constexpr (MX) {
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            gfr[j] = (float)gr[j];
+            gfi[j] = (float)gi[j];
+        }
+        const int slot = A.rd.tdm ? tx : 0;
+        w.kin_t = A.kin + (int64_t)tx * F * kKinRow;
+        w.kin_r = A.kin + (int64_t)(P + rx) * F * kKinRow;
+        w.quad_t = A.kquad + (int64_t)tx * F * kKinQuadWords;
+        w.quad_r = A.kquad + (int64_t)(P + rx) * F * kKinQuadWords;
+        w.sl = n * A.rd.slots + slot;
+        w.ant_t = tx;
+        w.ant_r = P + rx;
+        w.tau_s = (float)w.sl - K.s_mid;
+        w.tn = (float)w.sl * K.tc;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            w.ptx[r] = K.ant[tx][r];
+            w.prx[r] = K.ant[P + rx][r];
+        }
+        muc2 = (float)(mu / (c * c));
+        inv_fs = (float)(1.0 / fs);
+    }
+
     const int nbat = (cnt + 31) / 32;
     const int bat0 = (int)((int64_t)nbat * chunk / NCH);
     const int bat1 = (int)((int64_t)nbat * (chunk + 1) / NCH);
@@ -240,14 +505,60 @@ adjoint_fp64_kernel(SynthArgs A, int W, int NCH, const void *__restrict__ grad, 
         const bool valid = base + lane < cnt;
         int64_t k = 0;
         double vel[3] = {0.0, 0.0, 0.0};
+        int f32 = 0;
         if (valid) {
             k = list[base + lane];
             const int inst = A.fac[k].inst;
             for (int r = 0; r < 3; ++r) vel[r] = A.vel64[3 * inst + r];
+            if constexpr (MX) {
+                if (f32_route) {
+                    float Rm[24];
+                    // the FP32 route also needs the vertex form well away from its
+                    // edge-form limit (k_max d_min = kEdgeKd): the derivative of a
+                    // pair of nearly equal projections cancels as 1 / (k d)^2
+                    if (build_mixed_record(A, K, w, (int)k, Rm, true) == kRecVertex &&
+                        vertex_well_separated(A.fac[k], w, K.kmax, kAdjF32Kd)) {
+                        f32 = 1;
+                        RecF &Fr = sU[warp][lane].f;
+                        Fr.kind = kRouteF32;
+#pragma unroll
+                        for (int v = 0; v < 3; ++v) {
+                            Fr.ph0[v] = Rm[v];
+                            Fr.lo[v] = Rm[3 + v];
+                            Fr.w[v] = Rm[6 + v];
+                        }
+                        Fr.hi = Rm[15];
+                        Fr.p2 = Rm[16];
+                        // chirp-start ranges and the path's rate (FP32 suffices
+                        // for the factors d sqrt(Q) / dQ and fmc - mu L / c^2)
+                        const FacetRec fr = A.fac[k];
+                        const float4 vv = reinterpret_cast<const float4 *>(A.vel32)[fr.inst];
+                        const float vf[3] = {vv.x, vv.y, vv.z};
+                        float dt[3], dr[3];
+                        for (int r = 0; r < 3; ++r) {
+                            const float cc = fmaf(vf[r], w.tn, fr.c[r]);
+                            dt[r] = w.ptx[r] - cc;
+                            dr[r] = w.prx[r] - cc;
+                        }
+                        const float Rt = sqrtf(dot3(dt, dt)), Rr = sqrtf(dot3(dr, dr));
+                        const float Rtd = A.rd.intra ? -dot3(vf, dt) / Rt : 0.f;
+                        const float Rrd = A.rd.intra ? -dot3(vf, dr) / Rr : 0.f;
+                        Fr.L0 = Rt + Rr;
+                        Fr.Ld = Rtd + Rrd;
+                        Fr.it = 0.5f / Rt;
+                        Fr.ir = 0.5f / Rr;
+                        Fr.itd = -Fr.it * Rtd / Rt;
+                        Fr.ird = -Fr.ir * Rrd / Rr;
+                    }
+                }
+            }
+        }
+        if (valid && !f32) {
+            const int inst = A.fac[k].inst;
             double tri[9], c0[3];
             for (int i = 0; i < 9; ++i) tri[i] = A.tri64[9 * k + i];
             for (int r = 0; r < 3; ++r) c0[r] = A.c64[3 * k + r];
-            Rec &R = sR[warp][lane];
+            Rec &R = sU[warp][lane].x;
             int flags = 0;
             R.kind = build_record<double>(tri, c0, vel, tn, ptx, prx, (double)A.fac[k].rho,
                                           A.rd.intra, k0, kmax,
@@ -297,11 +608,26 @@ adjoint_fp64_kernel(SynthArgs A, int W, int NCH, const void *__restrict__ grad, 
         double mine[kRecEntries];
 #pragma unroll
         for (int e = 0; e < kRecEntries; ++e) mine[e] = 0.0;
+        float mine_f[9];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) mine_f[e] = 0.f;
         unsigned int mask = __ballot_sync(0xffffffffu, valid);
         while (mask) {
             const int i = __ffs(mask) - 1;
             mask &= mask - 1;
-            const Rec &R = sR[warp][i];
+            if constexpr (MX) {
+                if (sU[warp][i].x.kind == kRouteF32) {   // uniform over the warp (record i)
+                    float part[9];
+                    adj_vertex_f32<S>(sU[warp][i].f, m0, K, muc2, inv_fs, gfr, gfi, part);
+#pragma unroll
+                    for (int e = 0; e < 9; ++e) {
+                        const float tot = warp_sum_f(part[e]);
+                        if (lane == i) mine_f[e] = tot;
+                    }
+                    continue;
+                }
+            }
+            const Rec &R = sU[warp][i].x;
             const double *d = R.r + kRecD;
             bool mixed_done = false;
             if constexpr (MX) {
@@ -463,9 +789,30 @@ adjoint_fp64_kernel(SynthArgs A, int W, int NCH, const void *__restrict__ grad, 
             }
             }
         }
+        // the FP32 route: one reverse pass of the vertex-form record
+        if (valid && f32) {
+            const RecF &Fr = sU[warp][lane].f;
+            const float twopi = 6.283185307179586f;
+            float bar[10], gp[10];
+            bar[0] = twopi * fmaf(Fr.it, mine_f[6], Fr.itd * mine_f[7]);
+            bar[1] = twopi * fmaf(Fr.it, mine_f[7], Fr.itd * mine_f[8]);
+            bar[2] = twopi * fmaf(Fr.ir, mine_f[6], Fr.ird * mine_f[7]);
+            bar[3] = twopi * fmaf(Fr.ir, mine_f[7], Fr.ird * mine_f[8]);
+#pragma unroll
+            for (int v = 0; v < 3; ++v) {
+                bar[4 + v] = twopi * Fr.w[v] * mine_f[3 + v];
+                bar[7 + v] = mine_f[v];
+            }
+            const FacetRec fr = A.fac[k];
+            const float4 vv = reinterpret_cast<const float4 *>(A.vel32)[fr.inst];
+            const float vf[3] = {vv.x, vv.y, vv.z};
+            vertex_reverse_f32(fr, vf, w.tn, w.ptx, w.prx, A.rd.intra, bar, gp);
+#pragma unroll
+            for (int p = 0; p < 10; ++p) atomicAdd(gfac + 10 * k + p, (double)gp[p]);
+        }
         // reverse through the record construction, one parameter at a time
-        if (valid) {
-            const Rec &R = sR[warp][lane];
+        if (valid && !f32) {
+            const Rec &R = sU[warp][lane].x;
             double tri[9], c0[3];
             for (int q = 0; q < 9; ++q) tri[q] = A.tri64[9 * k + q];
             for (int r = 0; r < 3; ++r) c0[r] = A.c64[3 * k + r];
@@ -525,6 +872,7 @@ template <bool MX>
 static void launch_adjoint(const SynthArgs &a, const void *grad, int grad_c64, double *gfac,
                            cudaStream_t s)
 {
+    const MixConsts K = mix_consts(a.rd);
     const int M = a.rd.M;
     int S = kAdjS;
     while (S > 1 && M % (32 * S) != 0) S >>= 1;
@@ -547,10 +895,10 @@ static void launch_adjoint(const SynthArgs &a, const void *grad, int grad_c64, d
     const int64_t warps = rows * NCH;
     const unsigned int grid = (unsigned int)((warps + kAdjWarps - 1) / kAdjWarps);
     switch (S) {
-    case 8: adjoint_fp64_kernel<8, MX><<<grid, kAdjWarps * 32, 0, s>>>(a, W, NCH, grad, grad_c64, gfac); break;
-    case 4: adjoint_fp64_kernel<4, MX><<<grid, kAdjWarps * 32, 0, s>>>(a, W, NCH, grad, grad_c64, gfac); break;
-    case 2: adjoint_fp64_kernel<2, MX><<<grid, kAdjWarps * 32, 0, s>>>(a, W, NCH, grad, grad_c64, gfac); break;
-    default: adjoint_fp64_kernel<1, MX><<<grid, kAdjWarps * 32, 0, s>>>(a, W, NCH, grad, grad_c64, gfac); break;
+    case 8: adjoint_fp64_kernel<8, MX><<<grid, kAdjWarps * 32, 0, s>>>(a, K, W, NCH, grad, grad_c64, gfac); break;
+    case 4: adjoint_fp64_kernel<4, MX><<<grid, kAdjWarps * 32, 0, s>>>(a, K, W, NCH, grad, grad_c64, gfac); break;
+    case 2: adjoint_fp64_kernel<2, MX><<<grid, kAdjWarps * 32, 0, s>>>(a, K, W, NCH, grad, grad_c64, gfac); break;
+    default: adjoint_fp64_kernel<1, MX><<<grid, kAdjWarps * 32, 0, s>>>(a, K, W, NCH, grad, grad_c64, gfac); break;
     }
 }
 

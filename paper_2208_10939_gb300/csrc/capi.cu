@@ -666,7 +666,8 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
                         ? ctx->tpi_override
                         : synth_tiles_per_item(*std::max_element(scene_F.begin(), scene_F.end()));
     int64_t max_items = 0;
-    const bool mixed_rows = path == BART_PATH_MIXED || path == BART_PATH_SPECTRAL;
+    const bool mixed_rows = path == BART_PATH_MIXED || path == BART_PATH_SPECTRAL ||
+                            path == kPathAdjointMixed;
     if (path == BART_PATH_SPECTRAL && ctx->spec_M != rd.M) {
         std::vector<float> tab(2 * (size_t)rd.M);
         spectral_tables(rd.M, tab.data());
@@ -838,6 +839,11 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
         } else if (path == kPathAdjoint || path == kPathAdjointMixed) {
             a.n0 = 0;
             a.nc = rd.N;
+            if (path == kPathAdjointMixed) {
+                a.kin = ctx->kin.p;
+                a.kquad = ctx->kquad.p;
+                CUDA_TRY(cudaStreamWaitEvent(s, ctx->join_ev, 0), "cudaStreamWaitEvent");
+            }
             if (path == kPathAdjoint)
                 launch_adjoint_fp64(a, ctx->adj_grad, ctx->adj_grad_c64, ctx->gfac.p, s);
             else

@@ -187,7 +187,8 @@ struct MixRow {
 };
 
 __device__ __forceinline__ int build_mixed_record(const SynthArgs &A, const MixConsts &K,
-                                                  const MixRow &w, int k, float *R)
+                                                  const MixRow &w, int k, float *R,
+                                                  bool exact_u = false)
 {
     const FacetRec fr = A.fac[k];
     const float4 vv = reinterpret_cast<const float4 *>(A.vel32)[fr.inst];
@@ -300,7 +301,10 @@ __device__ __forceinline__ int build_mixed_record(const SynthArgs &A, const MixC
     // unit vectors toward the antennas (dv_v lies in the facet plane, so
     // b's in-plane part gives the same product).
     float ul[3] = {0.f, 0.f, 0.f};
-    const bool large = K.f0c * fmaxf(fmaxf(fabsf(u[0]), fabsf(u[1])), fabsf(u[2])) > 64.f;
+    // (exact_u: every facet, for the adjoint, whose vertex-sum cancellation
+    // amplifies the FP32 rounding of f0 u / c)
+    const bool large =
+        exact_u || K.f0c * fmaxf(fmaxf(fabsf(u[0]), fabsf(u[1])), fabsf(u[2])) > 64.f;
     if (large) {
         const float *res = A.fac_lo + 12 * (int64_t)k;
         // the origin of the directions at the chirp start: the centroid,

@@ -227,18 +227,23 @@ range_fft_reg_kernel(const float2 *__restrict__ adc, float2 *__restrict__ X, int
     float wv[R0];
 #pragma unroll
     for (int k = 0; k < R0; ++k) wv[k] = window_val<float>(tid + T * k, M, window);
-    for (int64_t row0 = (int64_t)blockIdx.x * RPB; row0 < rows; row0 += (int64_t)gridDim.x * RPB) {
-        const int64_t row = row0 + g;
-        const bool valid = row < rows;
-        float2 a[R0];
-        const float2 *in = adc + row * M + tid;
+    const int64_t stride = (int64_t)gridDim.x * RPB;
+    int64_t row = (int64_t)blockIdx.x * RPB + g;
+    // the next row's samples are loaded while the current one is transformed
+    float2 nx[R0];
 #pragma unroll
-        for (int k = 0; k < R0; ++k) {
-            const float2 v = valid ? in[T * k] : make_float2(0.f, 0.f);
-            a[k] = make_float2(v.x * wv[k], v.y * wv[k]);
-        }
+    for (int k = 0; k < R0; ++k)
+        nx[k] = row < rows ? adc[row * M + tid + T * k] : make_float2(0.f, 0.f);
+    for (int64_t row0 = (int64_t)blockIdx.x * RPB; row0 < rows; row0 += stride, row += stride) {
+        float2 a[R0];
+#pragma unroll
+        for (int k = 0; k < R0; ++k) a[k] = make_float2(nx[k].x * wv[k], nx[k].y * wv[k]);
+        const int64_t next = row + stride;
+#pragma unroll
+        for (int k = 0; k < R0; ++k)
+            nx[k] = next < rows ? adc[next * M + tid + T * k] : make_float2(0.f, 0.f);
         fft<M>(a, tid, buf + g * M, tw);
-        if (valid) {
+        if (row < rows) {
             float2 *out = X + row * M;
 #pragma unroll
             for (int i = 0; i < R0; ++i) out[fft_out_index<M>(tid, i)] = a[i];
@@ -247,14 +252,35 @@ range_fft_reg_kernel(const float2 *__restrict__ adc, float2 *__restrict__ X, int
     }
 }
 
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int NPEND>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(NPEND) : "memory");
+}
+
+// Doppler pass over channels o0 .. o1 - 1 of the cube X ([o][n][r], rows of
+// M range bins); the next channel's tile is copied into shared memory
+// (cp.async, two stages) while the current one is transformed.  With
+// `accumulate` the partial map adds the values already in `part` (the
+// channel-chunked schedule).
 template <int N>
 __global__ void __launch_bounds__(kRegThreads, 2)
 doppler_sum_reg_kernel(const float2 *__restrict__ X, int M, int CPB, int O, int window,
-                       float *__restrict__ part)
+                       int accumulate, float *__restrict__ part)
 {
     using namespace fftr;
     constexpr int R0 = Plan<N>::R0, T = N / R0, RB = kRegThreads / T;
-    __shared__ float2 buf[RB * (N + 1)];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *buf = reinterpret_cast<float2 *>(smem_raw);                 // RB (N + 1)
+    float2 *stage = buf + RB * (N + 1);                                  // 2 x R0 x 256
     const int c = threadIdx.x % RB, tid = threadIdx.x / RB;
     FftTw<N> tw;
     tw.init(tid);
@@ -266,15 +292,31 @@ doppler_sum_reg_kernel(const float2 *__restrict__ X, int M, int CPB, int O, int 
     const int G = (O + CPB - 1) / CPB;               // groups per scene
     const int scene = gg / G, gi = gg % G;
     const int o0 = scene * O + gi * CPB, o1 = scene * O + min(O, (gi + 1) * CPB);
+    // a thread's own R0 samples of channel o into stage s: slot k at
+    // (s R0 + k) 256 + threadIdx.x (a warp's slots are consecutive)
+    auto issue = [&](int o, int st) {
+        const float2 *in = X + ((int64_t)o * N + tid) * M + r;
+#pragma unroll
+        for (int k = 0; k < R0; ++k)
+            cp_async8(stage + (st * R0 + k) * kRegThreads + threadIdx.x, in + (int64_t)T * k * M);
+        cp_async_commit();
+    };
     float acc[R0];
 #pragma unroll
     for (int i = 0; i < R0; ++i) acc[i] = 0.f;
+    if (o0 < o1) issue(o0, 0);
     for (int o = o0; o < o1; ++o) {
+        const int st = (o - o0) & 1;
+        if (o + 1 < o1) {
+            issue(o + 1, st ^ 1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
         float2 a[R0];
-        const float2 *in = X + ((int64_t)o * N + tid) * M + r;
 #pragma unroll
         for (int k = 0; k < R0; ++k) {
-            const float2 v = in[(int64_t)T * k * M];
+            const float2 v = stage[(st * R0 + k) * kRegThreads + threadIdx.x];
             a[k] = make_float2(v.x * wv[k], v.y * wv[k]);
         }
         fft<N>(a, tid, buf + c * (N + 1), tw);
@@ -287,8 +329,16 @@ doppler_sum_reg_kernel(const float2 *__restrict__ X, int M, int CPB, int O, int 
     for (int i = 0; i < R0; ++i) {
         const int d = fft_out_index<N>(tid, i);
         const int ds = d + (N >> 1);
-        dst[ds >= N ? ds - N : ds] = acc[i];
+        float *p = dst + (ds >= N ? ds - N : ds);
+        *p = accumulate ? *p + acc[i] : acc[i];
     }
+}
+
+template <int N>
+static size_t doppler_reg_smem()
+{
+    constexpr int R0 = fftr::Plan<N>::R0, T = N / R0, RB = kRegThreads / T;
+    return (size_t)(RB * (N + 1) + 2 * R0 * kRegThreads) * sizeof(float2);
 }
 
 // range bins per Doppler block: the largest power of two RB with RB N <= 512
@@ -439,14 +489,15 @@ static void range_reg_launch(const float2 *adc, float2 *X, int64_t rows, int win
 
 template <int N>
 static void doppler_reg_launch(const float2 *X, int M, int O, int groups, int window, float *part,
-                               int *G_out, cudaStream_t s)
+                               int CPB, int accumulate, cudaStream_t s)
 {
     constexpr int RB = kRegThreads / (N / fftr::Plan<N>::R0);
-    const int CPB = rdm_cpb(O, M / RB, groups);
     const int G = (O + CPB - 1) / CPB;
-    *G_out = G;
+    const size_t sm = doppler_reg_smem<N>();
+    cudaFuncSetAttribute(doppler_sum_reg_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sm);
     doppler_sum_reg_kernel<N><<<dim3((unsigned int)(M / RB), (unsigned int)(G * groups)),
-                                kRegThreads, 0, s>>>(X, M, CPB, O, window, part);
+                                kRegThreads, sm, s>>>(X, M, CPB, O, window, accumulate, part);
 }
 
 static bool reg_len_ok(int L) { return L >= 16 && L <= 1024 && is_pow2_len(L); }
@@ -459,30 +510,63 @@ static bool rdm_reg_supported(const RadarDev &rd)
     return reg_len_ok(rd.M) && reg_len_ok(rd.N) && rd.M % reg_rb(rd.N) == 0;
 }
 
+static void range_reg_dispatch(const float2 *adc, float2 *X, int64_t rows, int M, int window,
+                               cudaStream_t s)
+{
+    switch (M) {
+    case 16: range_reg_launch<16>(adc, X, rows, window, s); break;
+    case 32: range_reg_launch<32>(adc, X, rows, window, s); break;
+    case 64: range_reg_launch<64>(adc, X, rows, window, s); break;
+    case 128: range_reg_launch<128>(adc, X, rows, window, s); break;
+    case 256: range_reg_launch<256>(adc, X, rows, window, s); break;
+    case 512: range_reg_launch<512>(adc, X, rows, window, s); break;
+    default: range_reg_launch<1024>(adc, X, rows, window, s); break;
+    }
+}
+
+static void doppler_reg_dispatch(const float2 *X, int N, int M, int O, int groups, int window,
+                                 float *part, int CPB, int accumulate, cudaStream_t s)
+{
+    switch (N) {
+    case 16: doppler_reg_launch<16>(X, M, O, groups, window, part, CPB, accumulate, s); break;
+    case 32: doppler_reg_launch<32>(X, M, O, groups, window, part, CPB, accumulate, s); break;
+    case 64: doppler_reg_launch<64>(X, M, O, groups, window, part, CPB, accumulate, s); break;
+    case 128: doppler_reg_launch<128>(X, M, O, groups, window, part, CPB, accumulate, s); break;
+    case 256: doppler_reg_launch<256>(X, M, O, groups, window, part, CPB, accumulate, s); break;
+    case 512: doppler_reg_launch<512>(X, M, O, groups, window, part, CPB, accumulate, s); break;
+    default: doppler_reg_launch<1024>(X, M, O, groups, window, part, CPB, accumulate, s); break;
+    }
+}
+
+// Channels per chunk of the single-scene schedule: the range pass's output
+// of a chunk (about 32 MiB) is read back by the chunk's Doppler pass while
+// it is still in L2, so that HBM sees the ADC cube once.
+constexpr int64_t kRdmChunkBytes = 32ll << 20;
+
+// Returns the number of partial maps per scene left in `part`.
 static int run_rdm_reg(const float2 *adc, const RadarDev &rd, int groups, float2 *X, float *part,
                        cudaStream_t s)
 {
-    const int64_t rows = (int64_t)rd.O * groups * rd.N;
-    switch (rd.M) {
-    case 16: range_reg_launch<16>(adc, X, rows, rd.window, s); break;
-    case 32: range_reg_launch<32>(adc, X, rows, rd.window, s); break;
-    case 64: range_reg_launch<64>(adc, X, rows, rd.window, s); break;
-    case 128: range_reg_launch<128>(adc, X, rows, rd.window, s); break;
-    case 256: range_reg_launch<256>(adc, X, rows, rd.window, s); break;
-    case 512: range_reg_launch<512>(adc, X, rows, rd.window, s); break;
-    default: range_reg_launch<1024>(adc, X, rows, rd.window, s); break;
+    const int M = rd.M, N = rd.N, O = rd.O;
+    const int RB = reg_rb(N);
+    const int64_t per_ch = (int64_t)N * M * (int64_t)sizeof(float2);
+    const int Cc = (int)std::max<int64_t>(1, std::min<int64_t>(O, kRdmChunkBytes / per_ch));
+    if (groups == 1 && Cc < O) {
+        // channel chunks: Doppler blocks of CPB channels, G groups per chunk,
+        // the chunks adding into the same G partial maps in order
+        const int CPB = rdm_cpb(Cc, M / RB, 1);
+        const int G = (Cc + CPB - 1) / CPB;
+        for (int c0 = 0; c0 < O; c0 += Cc) {
+            const int cn = std::min(Cc, O - c0);
+            range_reg_dispatch(adc + (int64_t)c0 * N * M, X, (int64_t)cn * N, M, rd.window, s);
+            doppler_reg_dispatch(X, N, M, cn, 1, rd.window, part, CPB, c0 > 0, s);
+        }
+        return G;
     }
-    int G = 1;
-    switch (rd.N) {
-    case 16: doppler_reg_launch<16>(X, rd.M, rd.O, groups, rd.window, part, &G, s); break;
-    case 32: doppler_reg_launch<32>(X, rd.M, rd.O, groups, rd.window, part, &G, s); break;
-    case 64: doppler_reg_launch<64>(X, rd.M, rd.O, groups, rd.window, part, &G, s); break;
-    case 128: doppler_reg_launch<128>(X, rd.M, rd.O, groups, rd.window, part, &G, s); break;
-    case 256: doppler_reg_launch<256>(X, rd.M, rd.O, groups, rd.window, part, &G, s); break;
-    case 512: doppler_reg_launch<512>(X, rd.M, rd.O, groups, rd.window, part, &G, s); break;
-    default: doppler_reg_launch<1024>(X, rd.M, rd.O, groups, rd.window, part, &G, s); break;
-    }
-    return G;
+    range_reg_dispatch(adc, X, (int64_t)O * groups * N, M, rd.window, s);
+    const int CPB = rdm_cpb(O, M / RB, groups);
+    doppler_reg_dispatch(X, N, M, O, groups, rd.window, part, CPB, 0, s);
+    return (O + CPB - 1) / CPB;
 }
 
 template <typename T>

@@ -25,13 +25,14 @@
 // spreading each warp evaluates queued records with its lanes over the
 // samples.  Work per record ~ W grid cells instead of M samples.
 //
-// One CTA per chirp row; the row's record list is split into 32 segments,
-// one per lane (neighbouring facets sit at neighbouring beat frequencies, so
-// lanes far apart in the list rarely add to the same grid cell at once),
-// the warps interleaved within each segment.  (Lanes on consecutive list
-// entries -- warps of one mesh region, less divergence -- measured 1.9x
-// slower on the intersection frame: the shared-memory adds of a warp then
-// collide.)
+// One CTA per chirp row; the row's record list is split into one chunk per
+// warp and each chunk into 32 lane runs (neighbouring facets sit at
+// neighbouring beat frequencies, so lanes runs apart rarely add to the same
+// grid cell at once).  Measured on the intersection frame: lanes on
+// consecutive list entries 1.9x slower (a warp's shared-memory adds
+// collide); 32 list-wide lane segments with the warps interleaved 1.13x
+// slower (warps mixing the ground's and the vehicles' record forms
+// diverge); dynamic 1024-record chunks 1.09x slower.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -148,7 +149,7 @@ synth_spectral_kernel(SynthArgs A, MixConsts K, SpecConsts C, const float *__res
     const int i_end = min(cnt, (lane + 1) * seg);
     unsigned long long nV = 0, nSr = 0, nE = 0;
     const float twopi = 6.283185307179586f;
-    for (int i = lane * seg + warp; i < i_end; i += nwarp) {
+    auto process = [&](int i) {
         float R[24];
         const int cls = build_mixed_record(A, K, w, list[i], R);
         if (cls == kRecVertex) {
@@ -274,6 +275,16 @@ synth_spectral_kernel(SynthArgs A, MixConsts K, SpecConsts C, const float *__res
                 }
             }
         }
+        };
+    // warp w takes the w-th eighth of the list, its lanes consecutive runs of
+    // it: each warp stays mostly within one mesh (fewer divergent forms,
+    // e.g. the ground's large static facets apart from the vehicles'), while
+    // the lanes, runs apart, rarely add to the same grid cell at once
+    {
+        const int wchunk = (cnt + nwarp - 1) / nwarp, lseg = (wchunk + 31) / 32;
+        const int i0 = warp * wchunk + lane * lseg;
+        const int i1 = min(cnt, min((warp + 1) * wchunk, i0 + lseg));
+        for (int i = i0; i < i1; ++i) process(i);
     }
     __syncthreads();
     // queued series / edge records: a warp per record, its lanes over the samples

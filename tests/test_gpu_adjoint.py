@@ -102,6 +102,30 @@ def test_adjoint_matches_oracle_central_differences(sim, name):
     assert checked >= 6
 
 
+@pytest.mark.parametrize("name", ["oblique_plate", "point"])
+def test_adjoint_matches_oracle_reference_gradient(sim, name):
+    """The whole gradient vector (every vertex coordinate and reflectivity)
+    of both adjoints against the oracle's reference gradient
+    (oracle.echo_gradient: fourth-order central differences of the FP64
+    oracle frame, the visibility held at the scene's own)."""
+    sc = CASES[name]()
+    sim.load_scene(sc)
+    shape = sim.adc_shape()
+    W = weights(shape, 21)
+    gv_ref, gr_ref = oracle.echo_gradient(sc, W)
+    Wt = torch.from_numpy(W).cuda()
+    nv, nf = sc.meshes[0].verts.shape[0], sc.meshes[0].nf
+    for mixed, tol in ((False, 1e-7), (True, 3e-5)):
+        gv = torch.empty((nv, 3), dtype=torch.float64, device="cuda")
+        gr = torch.empty(nf, dtype=torch.float64, device="cuda")
+        pkg.bart_simulate_adjoint(sim.ctx, 0.0, Wt, gv, gr, mixed=mixed)
+        ev = np.linalg.norm(gv.cpu().numpy() - gv_ref) / np.linalg.norm(gv_ref)
+        er = np.linalg.norm(gr.cpu().numpy() - gr_ref) / np.linalg.norm(gr_ref)
+        print(f"{name}: {'mixed' if mixed else 'fp64'} adjoint vs oracle reference gradient: "
+              f"vertices {ev:.3e}, reflectivity {er:.3e}")
+        assert ev <= tol and er <= tol
+
+
 def test_directional_derivative_matches_gpu_forward(sim):
     sc = small_car()
     es = bag.EchoScene(sim, sc)
@@ -203,5 +227,77 @@ def test_perturbed_sedan_inverse_problem_gradient():
             fd = (lp - lm) / 2e-7
             an = float((g * u).sum())
             assert abs(fd - an) <= 1e-5 * abs(an), (fd, an)
+    finally:
+        s.close()
+
+
+def test_sedan_rdm_loss_chain_against_central_differences():
+    """Config-5 chain at full size: the 20k-facet sedan's RDM as target, its
+    copy with 5 mm vertex noise (seed 5) as the variable,
+    L = ||RDM(v, rho) - RDM_target||^2 through both adjoints (the RDM's,
+    then the FP64 echo's); the vertex and reflectivity gradients against
+    central differences of the GPU FP64 forward with an FP64 RDM
+    (oracle.range_doppler_map) on seeded coordinates, two facets'
+    reflectivities and one random direction."""
+    s = pkg.Simulator(0)
+    try:
+        sc = sg.car_scene()
+        es = bag.EchoScene(s, sc)
+        v_true = es.vertex_tensor(sc, "cuda")
+        rho0 = torch.from_numpy(sc.meshes[0].rho.copy()).cuda()
+        with torch.no_grad():
+            target = bag.range_doppler_map(bag.echo(v_true, None, es), s).clone()
+        rng = np.random.default_rng(5)
+        v0 = v_true + torch.from_numpy(0.005 * rng.normal(size=tuple(v_true.shape))).cuda()
+        verts = v0.clone().requires_grad_(True)
+        rho = rho0.clone().requires_grad_(True)
+        rdm = bag.range_doppler_map(bag.echo(verts, rho, es), s)
+        (rdm - target).pow(2).sum().backward()
+        gv, gr = verts.grad.clone(), rho.grad.clone()
+        T = target.double().cpu().numpy()
+
+        def loss(v, r=None):
+            with torch.no_grad():
+                a = bag.echo(v, r, es)
+                vis = s.visibility().clone()
+                return float(((oracle.range_doppler_map(a.cpu().numpy()) - T) ** 2).sum()), vis
+
+        h = 1e-6
+        scale = float(gv.abs().max())
+        checked = 0
+        for flat in rng.choice(v0.numel(), size=8, replace=False):
+            e = torch.zeros_like(v0).view(-1)
+            e[int(flat)] = h
+            e = e.view_as(v0)
+            (lp, sp), (lm, sm) = loss(v0 + e), loss(v0 - e)
+            if not torch.equal(sp, sm):
+                continue
+            fd = (lp - lm) / (2 * h)
+            an = float(gv.view(-1)[int(flat)])
+            assert abs(fd - an) <= 1e-4 * scale + 1e-4 * abs(an), (int(flat), fd, an)
+            checked += 1
+        assert checked >= 6
+        directions = 0
+        for _ in range(4):              # a direction whose +-h runs keep the visibility
+            u = torch.zeros_like(v0)      # (over 100 random vertices: fewer grazing facets)
+            pick = torch.from_numpy(rng.choice(v0.shape[0], size=100, replace=False)).cuda()
+            u[pick] = torch.from_numpy(rng.normal(size=(100, 3))).cuda()
+            (lp, sp), (lm, sm) = loss(v0 + 1e-7 * u), loss(v0 - 1e-7 * u)
+            if not torch.equal(sp, sm):
+                continue
+            fd = (lp - lm) / 2e-7
+            an = float((gv * u).sum())
+            assert abs(fd - an) <= 1e-4 * abs(an), (fd, an)
+            directions += 1
+            break
+        assert directions == 1
+        for f in rng.choice(rho0.numel(), size=2, replace=False):
+            dr = torch.zeros_like(rho0)
+            dr[int(f)] = 1e-3
+            rp, rm = rho0 + dr, rho0 - dr            # float32: divide by the real step
+            fd = (loss(v0, rp)[0] - loss(v0, rm)[0]) / (float(rp[int(f)]) - float(rm[int(f)]))
+            assert abs(fd - float(gr[int(f)])) <= 1e-4 * float(gr.abs().max()) + 1e-4 * abs(fd)
+        print(f"sedan RDM-loss chain: {checked} coordinates, one direction, 2 reflectivities "
+              f"match central differences")
     finally:
         s.close()

@@ -819,3 +819,39 @@ def test_far_field_shadow_is_the_parallel_projection():
     r.far_field = False
     persp = oracle.Frame(sg.Scene(sc.meshes, sc.instances, r)).state[0]
     assert not np.array_equal(persp[nf:], st[nf:])
+
+
+def test_reference_gradient_rigid_translation_is_the_phase_derivative():
+    """The oracle's reference gradient (oracle.echo_gradient) pinned by
+    physics: moving the whole tiny plate rigidly by d along a direction e
+    changes each sample by d/dd adc = i k_m (dL/dd) adc to leading order,
+    with k_m = 2 pi f_m / c the sample's wavenumber and dL/dd = -(t + r).e
+    the bistatic path's rate (Eq. 13's phase; the amplitude's 1/(R_t R_r)
+    and the residual video phase add terms ~1e-4 relative at 9 m).  The
+    summed vertex gradient along e must equal Re sum conj(W) d adc/dd;
+    reflectivity enters Eq. 7 linearly, so dL/drho_f must reproduce the
+    facet's share of L exactly."""
+    sc = sg.point_target_scene(9.0, 0.0, M=128, N=4, P=1, Q=2, edge=0.6e-3)
+    sc.instances[0].pos = np.array([1.5, 9.0, 0.4])
+    fr = oracle.Frame(sc)
+    adc = fr.adc_full()
+    rng = np.random.default_rng(17)
+    W = rng.normal(size=adc.shape) + 1j * rng.normal(size=adc.shape)
+    gv, gr = oracle.echo_gradient(sc, W)
+    r = sc.radar
+    c = sc.instances[0].pos + sc.meshes[0].verts.mean(0)
+    f_m = r.f0 + r.slope * np.arange(r.M) / r.fs
+    k_m = 2 * np.pi * f_m / oracle.C0
+    for e in (np.array([0.0, 1.0, 0.0]), np.array([0.6, 0.8, 0.0]), np.array([0.0, 0.6, 0.8])):
+        dadc = np.empty_like(adc)
+        for o in range(r.O):
+            t_hat = (c - r.tx[o // r.Q]) / np.linalg.norm(c - r.tx[o // r.Q])
+            r_hat = (c - r.rx[o % r.Q]) / np.linalg.norm(c - r.rx[o % r.Q])
+            dL = (t_hat + r_hat) @ e          # the path grows as the plate recedes
+            dadc[o] = 1j * k_m[None, :] * dL * adc[o]
+        expect = float((np.conj(W) * dadc).real.sum())
+        got = float((gv @ e).sum())
+        assert abs(got - expect) <= 1e-3 * abs(expect), (e, got, expect)
+    # linearity in rho: L = sum_f rho_f dL/drho_f
+    L = float((np.conj(W) * adc).real.sum())
+    assert abs(float(sc.meshes[0].rho.astype(np.float64) @ gr) - L) <= 1e-12 * abs(L) + 1e-30
