@@ -11,8 +11,10 @@ LBVH build, BART visibility, FP64 kinematics rows, echo synthesis (mixed
 path) and the windowed range-Doppler FFT into the RDM.
 
 Metric: echo terms/s (lit facet x channel x chirp x sample); frames/s, the
-moving-sedan frame (20k triangles, 12 channels, 128 x 256) and the plain-FP64
-path are reported beside it.  Inputs are resident in HBM when the timed
+spectral (inverse-FFT) path on the same frame, the RDM against HBM, the
+moving-sedan frame (20k triangles, 12 channels, 128 x 256), the plain-FP64
+path, the differentiable echo and the dataset runner are reported beside
+it.  Inputs are resident in HBM when the timed
 region starts; the frame's working set (facet records, kinematics rows,
 ADC cube) is far larger than L2, which is also flushed (256 MB write)
 between timed steps.
@@ -51,10 +53,10 @@ OPS_PER_TERM = 24
 # DRAM bytes (read + write) per echo term of one synthesis launch and the
 # FMA-pipe activity, from ncu captures of the synthesis kernel; valid only
 # while the kernel's sources hash to the value they had at the capture
-SYNTH_PROFILE = {"sources_sha256_16": "53733f6d827c31d3", "samples_per_lane": 16,
-                 "dram_bytes_per_term": (3.977547e9 + 22.273792e6) / 50804670464,
-                 "fma_pipe_active": 0.703}
-SYNTH_SOURCES = ("synth.cu", "bart_internal.cuh", "record_fp64.cuh")
+SYNTH_PROFILE = {"sources_sha256_16": "b142b1b25ac9e278", "samples_per_lane": 16,
+                 "dram_bytes_per_term": (4.842676e9 + 21.771008e6) / 50804670464,
+                 "fma_pipe_active": 0.679}
+SYNTH_SOURCES = ("synth.cu", "bart_internal.cuh", "record_fp64.cuh", "mixed_record.cuh")
 
 
 def synth_sources_hash() -> str:
@@ -129,6 +131,11 @@ def parse():
                     help="profiling aid: headline frame with the first P TX and Q RX")
     ap.add_argument("--no-flush", action="store_true",
                     help="profiling aid: no L2 flush between steps (per-kernel DRAM counters)")
+    ap.add_argument("--probe", default=None, choices=["rdm", "adjoint"],
+                    help="run one stage alone for a profiler capture and print its time: "
+                         "the RDM of a seeded 192 x 256 x 512 complex64 cube with the "
+                         "intersection radar, or the mixed adjoint of the sedan for a "
+                         "seeded dL/d(adc)")
     ap.add_argument("--log", default=os.environ.get("BART_RUN_LOG"),
                     help="append the run's record (JSON line plus seeds, clocks, oracle errors, "
                          "grazing counts) to this JSONL file")
@@ -529,6 +536,16 @@ def adjoint_timing(pkg, sg, torch, dev, reps: int) -> dict:
         s.close()
 
 
+def measured_hbm_gbs():
+    """The measured HBM copy bandwidth of the GB300s, else the
+    recipe's fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback (6.8 TB/s)"
+
+
 def measure_peaks(pkg, dev_index: int) -> dict:
     """Measured FP32 FMA-pipe, MUFU and FP64 rates of this GPU (the library's
     own register-only microbenchmarks)."""
@@ -548,7 +565,7 @@ def timed_frames(pkg, torch, sim, adc, rdm, flush, stream, steps: int, path: int
     """``steps`` frames (simulate + RDM), L2 flushed before each (unless
     ``flush`` is None); per-step device times (CUDA events on the launching
     stream) and the library's per-stage times."""
-    step_ms, synth_ms, launches, tm = [], [], 0, None
+    step_ms, synth_ms, rdm_ms, launches, tm = [], [], [], 0, None
     for _ in range(steps):
         if flush is not None:
             flush.zero_()
@@ -562,8 +579,10 @@ def timed_frames(pkg, torch, sim, adc, rdm, flush, stream, steps: int, path: int
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
         synth_ms.append(tm["synthesis_ms"])
+        rdm_ms.append(tm["rdm_ms"])
         launches += tm["launches"]
-    return {"step_ms": step_ms, "synth_ms": synth_ms, "launches": launches, "last": tm}
+    return {"step_ms": step_ms, "synth_ms": synth_ms, "rdm_ms": rdm_ms, "launches": launches,
+            "last": tm}
 
 
 def e2e_run(pkg, torch, sim, scene, path: int, steps: int, job_terms_per_step: float) -> dict:
@@ -671,10 +690,62 @@ def sedan_lines(pkg, sg, torch, dev, args, peaks) -> dict:
         sim.close()
 
 
+def run_probe(args) -> None:
+    """One stage alone (for ncu captures of a representative launch): warm-up
+    launches, then ``--steps`` timed ones (CUDA events); prints one JSON
+    line."""
+    import torch
+    import paper_2208_10939_gb300 as pkg
+    import scenegen as sg
+    dev = torch.device("cuda:0")
+    sim = pkg.Simulator(0)
+    rng = np.random.default_rng(1)
+    try:
+        if args.probe == "rdm":
+            O, N, M = 192, 256, 512
+            radar = sg.make_radar(M, N, 12, 16, 10.24e6, 12.5e12, tx_spacing_wl=8.0)
+            pkg.bart_radar_set(sim.ctx, radar)
+            cube = torch.complex(torch.from_numpy(rng.normal(size=(O, N, M)).astype(np.float32)),
+                                 torch.from_numpy(rng.normal(size=(O, N, M)).astype(np.float32)))
+            x = cube.to(dev)
+            out = torch.empty((M, N), dtype=torch.float32, device=dev)
+            run = lambda: pkg.bart_form_rdm(sim.ctx, x, out)
+            what = f"RDM of a {O}x{N}x{M} complex64 cube"
+        else:
+            sc = sg.car_scene()
+            sim.load_scene(sc)
+            shape = sim.adc_shape()
+            G = torch.from_numpy(rng.normal(size=shape) + 1j * rng.normal(size=shape)).to(dev)
+            nv = sum(sc.meshes[i.mesh_id].verts.shape[0] for i in sc.instances)
+            nf = sum(sc.meshes[i.mesh_id].tris.shape[0] for i in sc.instances)
+            gv = torch.empty((nv, 3), dtype=torch.float64, device=dev)
+            gr = torch.empty(nf, dtype=torch.float64, device=dev)
+            run = lambda: pkg.bart_simulate_adjoint(sim.ctx, 0.0, G, gv, gr, mixed=True)
+            what = "mixed adjoint of the sedan (vertex and reflectivity gradients)"
+        for _ in range(max(1, args.warmup)):
+            run()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(max(1, args.steps)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            run()
+            e1.record()
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        print(json.dumps({"probe": args.probe, "what": what, "ms_median": statistics.median(ms),
+                          "ms_min": min(ms), "steps": len(ms)}))
+    finally:
+        sim.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.probe:
+        run_probe(args)
         return
     import torch
     world, rank, local = dist_env()
@@ -792,6 +863,16 @@ def main():
             h_spec = adc.cpu().numpy()
     stages = {k: last_tm[k] for k in ("scene_ms", "bvh_ms", "visibility_ms", "kinematics_ms",
                                       "synthesis_ms", "rdm_ms")}
+    # the RDM against HBM: algorithmic bytes = the complex64 cube read once
+    # plus the FP32 map written once, over the library's RDM stage time
+    hbm_peak, hbm_basis = measured_hbm_gbs()
+    rdm_bytes = O * N * M * 8 + M * N * 4
+    rdm_ms = statistics.median(tf["rdm_ms"]) if tf.get("rdm_ms") else stages["rdm_ms"]
+    rdm_line = {"bound": "hbm", "kernels": "range_fft_reg_kernel, doppler_sum_reg_kernel, "
+                                          "rdm_sum_kernel",
+                "ms": rdm_ms, "algorithmic_bytes": rdm_bytes,
+                "achieved": rdm_bytes / (rdm_ms / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                "frac": rdm_bytes / (rdm_ms / 1e3) / 1e9 / hbm_peak, "peak_basis": hbm_basis}
     sim.close()
     del adc, rdm, flush
     torch.cuda.empty_cache()
@@ -835,6 +916,7 @@ def main():
         "stages_ms_last_step": stages,
         "roofline": roofline,
         "spectral_path": spectral,
+        "rdm": rdm_line,
         "clocks": clk,
         "e2e": e2e,
         "gpu_launches": tf["launches"],

@@ -259,27 +259,6 @@ __device__ __forceinline__ float dot3(const float *a, const float *b)
     return fmaf(a[0], b[0], fmaf(a[1], b[1], a[2] * b[2]));
 }
 
-// k_max d_min of the FP32 route (the forward's vertex form starts at kEdgeKd)
-constexpr float kAdjF32Kd = 1.0f;
-
-// k_max times the smallest gap between the facet's in-plane projections
-// u_v = b . dv_v, at the row's chirp start, at least `kd` (FP32 estimate)
-__device__ __forceinline__ bool vertex_well_separated(const FacetRec &fr, const MixRow &w,
-                                                      float kmax, float kd)
-{
-    float b[3] = {0.f, 0.f, 0.f};
-    for (int e = 0; e < 2; ++e) {
-        const float *p = e == 0 ? w.ptx : w.prx;
-        const float d[3] = {p[0] - fr.c[0], p[1] - fr.c[1], p[2] - fr.c[2]};
-        const float id = rsqrtf(dot3(d, d));
-        for (int r = 0; r < 3; ++r) b[r] = fmaf(d[r], id, b[r]);
-    }
-    float u[3];
-    for (int v = 0; v < 3; ++v) u[v] = dot3(b, fr.dv + 3 * v);
-    const float dmin = fminf(fminf(fabsf(u[0] - u[1]), fabsf(u[1] - u[2])), fabsf(u[0] - u[2]));
-    return kmax * dmin >= kd;
-}
-
 // Stage 2 of a vertex-form record, per-facet delay form: the record entries
 // (record_fp64.cuh)
 //   qt0 = |p_t - c(t_n)|^2, qt1 = -2 (p_t - c(t_n)).v (intra-chirp motion),
@@ -513,11 +492,14 @@ adjoint_fp64_kernel(SynthArgs A, MixConsts K, int W, int NCH, const void *__rest
             if constexpr (MX) {
                 if (f32_route) {
                     float Rm[24];
-                    // the FP32 route also needs the vertex form well away from its
-                    // edge-form limit (k_max d_min = kEdgeKd): the derivative of a
-                    // pair of nearly equal projections cancels as 1 / (k d)^2
-                    if (build_mixed_record(A, K, w, (int)k, Rm, true) == kRecVertex &&
-                        vertex_well_separated(A.fac[k], w, K.kmax, kAdjF32Kd)) {
+                    // (a stricter vertex-form limit for this route, k_max d_min
+                    // >= kd instead of kEdgeKd = 0.03, trades speed for accuracy
+                    // on the sedan: kd 0.1 / 0.25 / 0.5 / 1.0 gave 19 / 32 / 51 /
+                    // 76 ms at 4.7e-5 / 2.9e-5 / 4.6e-6 / 2.3e-6 from the FP64
+                    // adjoint, against 13 ms at 5.7e-5: the derivative of a
+                    // nearly equal projection pair cancels as 1 / (k d), which
+                    // amplifies the FP32 phase steps' rounding)
+                    if (build_mixed_record(A, K, w, (int)k, Rm, true) == kRecVertex) {
                         f32 = 1;
                         RecF &Fr = sU[warp][lane].f;
                         Fr.kind = kRouteF32;
@@ -873,6 +855,7 @@ static void launch_adjoint(const SynthArgs &a, const void *grad, int grad_c64, d
                            cudaStream_t s)
 {
     const MixConsts K = mix_consts(a.rd);
+
     const int M = a.rd.M;
     int S = kAdjS;
     while (S > 1 && M % (32 * S) != 0) S >>= 1;

@@ -324,13 +324,20 @@ doppler_sum_reg_kernel(const float2 *__restrict__ X, int M, int CPB, int O, int 
         for (int i = 0; i < R0; ++i) acc[i] = fmaf(a[i].x, a[i].x, fmaf(a[i].y, a[i].y, acc[i]));
         __syncthreads();
     }
-    float *dst = part + (int64_t)gg * M * N + (int64_t)r * N;
+    // the block's RB x N map through shared memory (the exchange buffer,
+    // free after the last transform), then written row by row
+    float *tile = reinterpret_cast<float *>(buf);
 #pragma unroll
     for (int i = 0; i < R0; ++i) {
         const int d = fft_out_index<N>(tid, i);
         const int ds = d + (N >> 1);
-        float *p = dst + (ds >= N ? ds - N : ds);
-        *p = accumulate ? *p + acc[i] : acc[i];
+        tile[c * (N + 1) + (ds >= N ? ds - N : ds)] = acc[i];
+    }
+    __syncthreads();
+    float *dst = part + (int64_t)gg * M * N + (int64_t)blockIdx.x * RB * N;
+    for (int j = threadIdx.x; j < RB * N; j += kRegThreads) {
+        const float v = tile[(j / N) * (N + 1) + j % N];
+        dst[j] = accumulate ? dst[j] + v : v;
     }
 }
 
@@ -538,31 +545,16 @@ static void doppler_reg_dispatch(const float2 *X, int N, int M, int O, int group
     }
 }
 
-// Channels per chunk of the single-scene schedule: the range pass's output
-// of a chunk (about 32 MiB) is read back by the chunk's Doppler pass while
-// it is still in L2, so that HBM sees the ADC cube once.
-constexpr int64_t kRdmChunkBytes = 32ll << 20;
-
-// Returns the number of partial maps per scene left in `part`.
+// Returns the number of partial maps per scene left in `part`.  (A
+// channel-chunked schedule -- range and Doppler passes over chunks of ~32
+// MiB so that the range output is read back from L2 -- measured 5x slower
+// on the 192 x 256 x 512 cube: twelve short launches, each a fraction of a
+// wave, and the chunks' partial maps added in place.)
 static int run_rdm_reg(const float2 *adc, const RadarDev &rd, int groups, float2 *X, float *part,
                        cudaStream_t s)
 {
     const int M = rd.M, N = rd.N, O = rd.O;
     const int RB = reg_rb(N);
-    const int64_t per_ch = (int64_t)N * M * (int64_t)sizeof(float2);
-    const int Cc = (int)std::max<int64_t>(1, std::min<int64_t>(O, kRdmChunkBytes / per_ch));
-    if (groups == 1 && Cc < O) {
-        // channel chunks: Doppler blocks of CPB channels, G groups per chunk,
-        // the chunks adding into the same G partial maps in order
-        const int CPB = rdm_cpb(Cc, M / RB, 1);
-        const int G = (Cc + CPB - 1) / CPB;
-        for (int c0 = 0; c0 < O; c0 += Cc) {
-            const int cn = std::min(Cc, O - c0);
-            range_reg_dispatch(adc + (int64_t)c0 * N * M, X, (int64_t)cn * N, M, rd.window, s);
-            doppler_reg_dispatch(X, N, M, cn, 1, rd.window, part, CPB, c0 > 0, s);
-        }
-        return G;
-    }
     range_reg_dispatch(adc, X, (int64_t)O * groups * N, M, rd.window, s);
     const int CPB = rdm_cpb(O, M / RB, groups);
     doppler_reg_dispatch(X, N, M, O, groups, rd.window, part, CPB, 0, s);

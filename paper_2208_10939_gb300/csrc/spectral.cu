@@ -49,6 +49,7 @@ namespace {
 
 constexpr int kSpecThreads = 256;
 constexpr int kQueue = 2048;      // series / edge records of a row deferred to the CTA
+constexpr int kSpecBlocksPerWarp = 8;   // list blocks per warp (interleaved over the warps)
 constexpr int kW0 = 8;            // taps of the main grid's kernel
 constexpr int kW1 = 4;            // taps of the two quadratic-phase grids
 constexpr int kD0 = 9;            // degree of the main kernel's tap polynomials
@@ -276,15 +277,21 @@ synth_spectral_kernel(SynthArgs A, MixConsts K, SpecConsts C, const float *__res
             }
         }
         };
-    // warp w takes the w-th eighth of the list, its lanes consecutive runs of
-    // it: each warp stays mostly within one mesh (fewer divergent forms,
-    // e.g. the ground's large static facets apart from the vehicles'), while
-    // the lanes, runs apart, rarely add to the same grid cell at once
+    // the list in kSpecBlocksPerWarp x nwarp blocks; warp w takes blocks w,
+    // w + nwarp, ... (a similar mix of meshes for every warp; measured the
+    // same as one contiguous eighth per warp) and its lanes consecutive runs
+    // of each block: a warp
+    // stays mostly within one mesh (fewer divergent record forms, e.g. the
+    // ground's large static facets apart from the vehicles'), while the
+    // lanes, runs apart, rarely add to the same grid cell at once
     {
-        const int wchunk = (cnt + nwarp - 1) / nwarp, lseg = (wchunk + 31) / 32;
-        const int i0 = warp * wchunk + lane * lseg;
-        const int i1 = min(cnt, min((warp + 1) * wchunk, i0 + lseg));
-        for (int i = i0; i < i1; ++i) process(i);
+        const int nb = kSpecBlocksPerWarp * nwarp;
+        const int bs = (cnt + nb - 1) / nb, lseg = (bs + 31) / 32;
+        for (int b = warp; b < nb; b += nwarp) {
+            const int i0 = b * bs + lane * lseg;
+            const int i1 = min(cnt, min((b + 1) * bs, i0 + lseg));
+            for (int i = i0; i < i1; ++i) process(i);
+        }
     }
     __syncthreads();
     // queued series / edge records: a warp per record, its lanes over the samples

@@ -174,11 +174,11 @@ def test_rdm_power_of_two_register_path(O, N, M):
     assert np.abs(out.cpu().numpy() - ref).max() <= 1e-5 * ref.max()
 
 
-def test_rdm_channel_chunked_schedule(sim):
-    """A cube larger than the 32 MiB chunk of the register path's
-    single-scene schedule (40 channels x 256 chirps x 512 samples: chunks of
-    32 and 8 channels adding into the same partial maps) against numpy's FFT
-    route on a seeded random cube."""
+def test_rdm_register_path_many_channel_groups(sim):
+    """The register path through a context on a 40-channel cube (256 chirps
+    x 512 samples, 42 MB: the Doppler pass splits the channels into groups
+    whose partial maps are summed in order) against numpy's FFT route on a
+    seeded random cube."""
     O, N, M = 40, 256, 512
     radar = sg.make_radar(M, N, 5, 8, 10.24e6, 12.5e12, tx_spacing_wl=8.0)
     s2 = pkg.Simulator(0)
