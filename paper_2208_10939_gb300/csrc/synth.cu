@@ -275,10 +275,16 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
     const int cnt = A.vcnt[vrow];
     const int ipu = max(1, ((cnt + 31) / 32 + TPI - 1) / TPI);
     const int local = item - A.item_off[vrow];
-    const int jchunk = local % ipu;
-    const int rowseg = local / ipu;
+    // consecutive items take one record chunk through the row's chirp groups
+    // and sample segments, so that the chunk's facet records and kinematics
+    // rows, read from HBM by the first of them, are L2 hits for the others;
+    // the partial sums keep their (chirp group, segment)-major slots, which
+    // the reduction adds in chunk order
+    const int nrs = ngroups * W;
+    const int jchunk = local / nrs;
+    const int rowseg = local % nrs;
+    const int64_t pslot = (int64_t)A.item_off[vrow] + (int64_t)rowseg * ipu + jchunk;
     const int seg = rowseg % W, grp = rowseg / W;
-    (void)ngroups;
     const int rbeg = jchunk * TPI * 32;
     const int rend = min(cnt, rbeg + TPI * 32);
     const int nl_raw = grp * RPW + row;
@@ -457,7 +463,7 @@ synth_mixed_kernel(SynthArgs A, MixConsts K, int W)
         __syncwarp();
     }
     // unscaled partial sums of this item
-    float2 *dst = A.partial + (int64_t)item * (32 * S) + lane * S;
+    float2 *dst = A.partial + pslot * (32 * S) + lane * S;
 #pragma unroll
     for (int k = 0; k < S2; ++k) {
         float r0, r1, i0, i1;
