@@ -50,16 +50,17 @@ SEDAN = "moving sedan 20k tris, 3TXx4RX (12 ch), 128 chirps x 256 samples"
 # 24 FP32 FMA-pipe operations (plus 6 SFU operations when the phasors come from
 # sincos); the roofline counts operations of the FMA pipe, whatever their kind
 OPS_PER_TERM = 24
-# DRAM bytes (read + write) of one synthesis launch per (channel, lit facet)
-# pair and the FMA-pipe activity, from ncu captures of the synthesis kernel.
-# A work item takes one record chunk of a channel through all its chirps, so
-# a (channel, facet) record's inputs come from HBM once and from L2 for the
-# other chirps: the traffic grows with the channels' lit-facet counts,
-# terms / (N M), not with the terms.  Valid only while the kernel's sources
+# DRAM traffic of one synthesis launch and the FMA-pipe activity, from ncu
+# captures of the synthesis kernel on 4 TX x 4 RX cuts of the frame.  A work
+# item takes one record chunk of a channel through all its chirps, so a
+# (channel, lit facet) record's inputs come from HBM once and from L2 for the
+# other chirps: reads grow with those pairs (terms / (N M)), not with the
+# terms (16 and 64 chirps read 3.41 and 3.28 GB); the items' partial sums
+# grow with the (channel, chirp) rows.  Valid only while the kernel's sources
 # hash to the value they had at the capture.
 SYNTH_PROFILE = {"sources_sha256_16": "035bf3819eff3c31", "samples_per_lane": 16,
-                 "dram_bytes_per_channel_facet": (3.408008e9 + 21.753344e6) /
-                 (50804670464 / (16 * 512)),
+                 "dram_read_bytes_per_channel_facet": 3.277169152e9 / (4 * 50804670464 / (64 * 512)),
+                 "dram_write_bytes_per_row": 75.109632e6 / (16 * 64),
                  "fma_pipe_active": 0.686}
 SYNTH_SOURCES = ("synth.cu", "bart_internal.cuh", "record_fp64.cuh", "mixed_record.cuh")
 
@@ -843,8 +844,10 @@ def main():
                 "achieved": achieved, "peak": peak, "unit": "Top/s (FP32 FMA-pipe operations)",
                 "frac": achieved / peak,
                 "traffic": None if prof is None
-                else prof["dram_bytes_per_channel_facet"] * terms / (N * M) / synth_launches,
-                "traffic_unit": "bytes per launch (ncu dram read + write of a cut, scaled per (channel, lit facet))",
+                else (prof["dram_read_bytes_per_channel_facet"] * terms / (N * M)
+                      + prof["dram_write_bytes_per_row"] * O * N) / synth_launches,
+                "traffic_unit": "bytes per launch (ncu dram reads of a cut per (channel, lit facet) "
+                                "+ writes per (channel, chirp) row)",
                 "ops_per_term": OPS_PER_TERM, "launch_ms": synth_avg_ms,
                 "ncu_fma_pipe_active": None if prof is None else prof["fma_pipe_active"],
                 "peak_basis": peak_basis}

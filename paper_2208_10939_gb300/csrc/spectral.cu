@@ -25,14 +25,16 @@
 // spreading each warp evaluates queued records with its lanes over the
 // samples.  Work per record ~ W grid cells instead of M samples.
 //
-// One CTA per chirp row; the row's record list is split into one chunk per
-// warp and each chunk into 32 lane runs (neighbouring facets sit at
-// neighbouring beat frequencies, so lanes runs apart rarely add to the same
-// grid cell at once).  Measured on the intersection frame: lanes on
-// consecutive list entries 1.9x slower (a warp's shared-memory adds
-// collide); 32 list-wide lane segments with the warps interleaved 1.13x
-// slower (warps mixing the ground's and the vehicles' record forms
-// diverge); dynamic 1024-record chunks 1.09x slower.
+// One CTA per chirp row.  The row's record list is cut into 64 blocks that
+// the warps take from a shared counter; a warp's lanes take consecutive runs
+// of a block (neighbouring facets sit at neighbouring beat frequencies, so
+// lane runs apart rarely add to the same grid cell at once, while a warp
+// stays mostly within one mesh and its record forms).  Measured on the
+// intersection frame: lanes on consecutive list entries 2.4x slower (a
+// warp's shared-memory adds collide); 32 list-wide lane segments with the
+// warps interleaved 1.23x slower (warps mixing the ground's and the
+// vehicles' record forms diverge); blocks dealt to the warps in turn 1.08x
+// slower (the warps finish at different times).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -111,7 +113,7 @@ synth_spectral_kernel(SynthArgs A, MixConsts K, SpecConsts C, const float *__res
     float *dre = reinterpret_cast<float *>(tw + tw_len(G));
     float *dim = dre + M;
     int *queue = reinterpret_cast<int *>(dim + M);
-    __shared__ int s_qn;
+    __shared__ int s_qn, s_next;
 
     const int row = blockIdx.x;
     const int nc = A.nc;
@@ -123,7 +125,7 @@ synth_spectral_kernel(SynthArgs A, MixConsts K, SpecConsts C, const float *__res
     const int64_t F = A.F;
     for (int i = threadIdx.x; i < 6 * G; i += blockDim.x) gr0[i] = 0.f;
     for (int i = threadIdx.x; i < 2 * M; i += blockDim.x) dre[i] = 0.f;
-    if (threadIdx.x == 0) s_qn = 0;
+    if (threadIdx.x == 0) s_qn = s_next = 0;
     fill_twiddles<float>(tw, G, -1);
     __syncthreads();
 
@@ -277,17 +279,20 @@ synth_spectral_kernel(SynthArgs A, MixConsts K, SpecConsts C, const float *__res
             }
         }
         };
-    // the list in kSpecBlocksPerWarp x nwarp blocks; warp w takes blocks w,
-    // w + nwarp, ... (a similar mix of meshes for every warp; measured the
-    // same as one contiguous eighth per warp) and its lanes consecutive runs
-    // of each block: a warp
+    // the list in kSpecBlocksPerWarp x nwarp blocks, which the warps take in
+    // turn from a shared counter (a warp whose blocks hold cheaper records
+    // takes more of them), its lanes consecutive runs of each block: a warp
     // stays mostly within one mesh (fewer divergent record forms, e.g. the
     // ground's large static facets apart from the vehicles'), while the
     // lanes, runs apart, rarely add to the same grid cell at once
     {
         const int nb = kSpecBlocksPerWarp * nwarp;
         const int bs = (cnt + nb - 1) / nb, lseg = (bs + 31) / 32;
-        for (int b = warp; b < nb; b += nwarp) {
+        for (;;) {
+            int b = 0;
+            if (lane == 0) b = atomicAdd(&s_next, 1);
+            b = __shfl_sync(0xffffffffu, b, 0);
+            if (b >= nb) break;
             const int i0 = b * bs + lane * lseg;
             const int i1 = min(cnt, min((b + 1) * bs, i0 + lseg));
             for (int i = i0; i < i1; ++i) process(i);
