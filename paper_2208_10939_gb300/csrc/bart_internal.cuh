@@ -90,6 +90,7 @@ struct InstDev {
 
 // Device status word bits (latched, read by bart_sync).
 constexpr int kStatusStackOverflow = 1;
+constexpr int kStatusWaitTimeout = 2;   // a bounded device wait expired (see bart_sync)
 
 // ---- scene + BVH (scene_bvh.cu) ----
 // tri32: per facet 12 floats -- the world vertices rounded to FP32 and the
@@ -235,8 +236,9 @@ void launch_add_noise(void *adc, int dtype, int64_t n, double snr_db, uint64_t s
 int64_t rdm_workspace_bytes(const RadarDev &rd, int dtype);
 // groups: independent cubes of rd.O channels each, back to back (batched
 // scenes); rdm receives groups x M x N; ws holds groups x rdm_workspace_bytes
+// status: the context's device status word (kStatusWaitTimeout), or NULL
 void launch_rdm(const void *adc, int dtype, const RadarDev &rd, int groups, void *ws, float *rdm,
-                cudaStream_t s);
+                int *status, cudaStream_t s);
 
 // RDM that also keeps the complex range-Doppler cube Y[o][r][d'] (Doppler
 // shifted) in `cube`; X is an O*N*M complex scratch of the same precision.

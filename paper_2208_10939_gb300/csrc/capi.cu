@@ -1136,7 +1136,7 @@ static int run_rdm(bart_ctx *ctx, const void *adc, int32_t dtype, float *rdm)
     }
     Stages nv;
     nv.next("bart rdm");
-    launch_rdm(adc, dtype, rd, groups, ctx->rdm_ws.p, rdm, ctx->stream);
+    launch_rdm(adc, dtype, rd, groups, ctx->rdm_ws.p, rdm, ctx->status.p, ctx->stream);
     CUDA_TRY(cudaGetLastError(), "rdm launch");
     if (ctx->timing) {
         CUDA_TRY(cudaEventRecord(ctx->ev[6], ctx->stream), "cudaEventRecord");
@@ -1305,7 +1305,7 @@ int bart_form_rdm_static(const void *adc, int32_t dtype, int32_t O, int32_t N, i
     const char *err = nullptr;
     const int rc = rdm_static_workspace(&ws, &err);
     if (rc != BART_OK) return fail(rc, "bart_form_rdm_static: %s", err);
-    launch_rdm(adc, dtype, rd, 1, ws, rdm, reinterpret_cast<cudaStream_t>(stream));
+    launch_rdm(adc, dtype, rd, 1, ws, rdm, nullptr, reinterpret_cast<cudaStream_t>(stream));
     CUDA_TRY(cudaGetLastError(), "bart_form_rdm_static launch");
     return BART_OK;
 }
@@ -1409,6 +1409,8 @@ int bart_sync(bart_ctx *ctx)
     CUDA_TRY(cudaMemcpy(&st, ctx->status.p, sizeof st, cudaMemcpyDeviceToHost), "status copy");
     if (st) {
         cudaMemset(ctx->status.p, 0, sizeof st);
+        if (st & kStatusWaitTimeout)
+            return fail(BART_ETIMEOUT, "a bounded device wait expired (RDM tile copy)");
         if (st & kStatusStackOverflow)
             return fail(BART_EDEVICE, "BVH traversal stack overflow (facets marked grazing)");
         return fail(BART_EDEVICE, "device status 0x%x", st);

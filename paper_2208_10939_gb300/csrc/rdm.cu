@@ -6,6 +6,7 @@
 // Mixed-radix (2, 3) Stockham autosort FFTs in shared memory
 // (fft_stockham.cuh).  Both passes are HBM-bound: each reads and writes the
 // cube once.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -341,6 +342,208 @@ doppler_sum_reg_kernel(const float2 *__restrict__ X, int M, int CPB, int O, int 
     }
 }
 
+// -------------------------------------------------------------------------
+// Doppler pass with TMA tile loads (N <= 256): the block's tile of channel o
+// -- its RB range bins over the N chirps, a 2-D box of the cube X viewed as
+// [O N] rows x [2 M] floats -- comes in by one cp.async.bulk.tensor copy,
+// double-buffered and completed on an mbarrier.  One thread issues, every
+// thread waits on the stage's barrier (bounded: on expiry the block records
+// kStatusWaitTimeout, waits -- again bounded -- for its copy in flight and
+// stops).  Otherwise as doppler_sum_reg_kernel.  A box dimension holds at
+// most 256 elements, so the tile's 2 RB floats and N rows limit it to
+// 32 <= N <= 256.
+// -------------------------------------------------------------------------
+constexpr int kTmaWaitLimit = 1 << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait for the phase `parity` of `bar`; false if the limit expired
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    for (int i = 0; i < kTmaWaitLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+template <int N>
+struct TmaDoppler {
+    static constexpr int R0 = fftr::Plan<N>::R0, T = N / R0, RB = kRegThreads / T;
+    static constexpr uint32_t kTileBytes = (uint32_t)N * RB * 8;
+    // stage tiles (two, 1024-byte aligned), the exchange buffer, two barriers
+    static constexpr size_t kStageOff = 0;
+    static constexpr size_t kBufOff = 2 * (size_t)kTileBytes;
+    static constexpr size_t kBarOff = kBufOff + (size_t)RB * (N + 1) * 8;
+    static constexpr size_t kSmem = kBarOff + 16 + 1024;     // + alignment slack
+};
+
+template <int N>
+__global__ void __launch_bounds__(kRegThreads, 2)
+doppler_sum_tma_kernel(const __grid_constant__ CUtensorMap tmap, int M, int CPB, int O,
+                       int window, int *status, float *__restrict__ part)
+{
+    using namespace fftr;
+    using Q = TmaDoppler<N>;
+    constexpr int R0 = Q::R0, T = Q::T, RB = Q::RB;
+    extern __shared__ unsigned char smem_dyn[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~uintptr_t(1023));
+    float2 *stage = reinterpret_cast<float2 *>(base + Q::kStageOff);      // [2][N][RB]
+    float2 *buf = reinterpret_cast<float2 *>(base + Q::kBufOff);          // RB (N + 1)
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + Q::kBarOff);      // [2]
+    __shared__ int s_err;
+    const int c = threadIdx.x % RB, tid = threadIdx.x / RB;
+    const int r0 = blockIdx.x * RB;
+    const int gg = blockIdx.y;
+    const int G = (O + CPB - 1) / CPB;
+    const int scene = gg / G, gi = gg % G;
+    const int o0 = scene * O + gi * CPB, o1 = scene * O + min(O, (gi + 1) * CPB);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_err = 0;
+    }
+    __syncthreads();
+    // thread 0: the tile of channel o into stage st (x in floats: 2 r0)
+    auto issue = [&](int o, int st) {
+        mbar_expect_tx(&bar[st], Q::kTileBytes);
+        tma_load_2d(stage + (size_t)st * N * RB, &tmap, 2 * r0, o * N, &bar[st]);
+    };
+    if (threadIdx.x == 0 && o0 < o1) issue(o0, 0);
+    FftTw<N> tw;
+    tw.init(tid);
+    float wv[R0];
+#pragma unroll
+    for (int k = 0; k < R0; ++k) wv[k] = window_val<float>(tid + T * k, N, window);
+    float acc[R0];
+#pragma unroll
+    for (int i = 0; i < R0; ++i) acc[i] = 0.f;
+    int o = o0;
+    for (; o < o1; ++o) {
+        const int it = o - o0, st = it & 1;
+        // the other stage was released by the barrier that ended the last
+        // iteration: its next tile goes in while this one is transformed
+        if (threadIdx.x == 0 && o + 1 < o1) issue(o + 1, st ^ 1);
+        if (!mbar_wait_bounded(&bar[st], (uint32_t)(it >> 1) & 1u)) s_err = 1;
+        __syncthreads();
+        if (s_err) break;
+        const float2 *tile = stage + (size_t)st * N * RB;
+        float2 a[R0];
+#pragma unroll
+        for (int k = 0; k < R0; ++k) {
+            const float2 v = tile[(tid + T * k) * RB + c];
+            a[k] = make_float2(v.x * wv[k], v.y * wv[k]);
+        }
+        fft<N>(a, tid, buf + c * (N + 1), tw);
+#pragma unroll
+        for (int i = 0; i < R0; ++i) acc[i] = fmaf(a[i].x, a[i].x, fmaf(a[i].y, a[i].y, acc[i]));
+        __syncthreads();
+    }
+    if (s_err) {
+        // stop: record the expiry, let the copy in flight (if any) land first
+        if (threadIdx.x == 0) {
+            if (status) atomicOr(status, kStatusWaitTimeout);
+            const int it = o - o0;
+            mbar_wait_bounded(&bar[it & 1], (uint32_t)(it >> 1) & 1u);
+            if (o + 1 < o1) mbar_wait_bounded(&bar[(it + 1) & 1], (uint32_t)((it + 1) >> 1) & 1u);
+        }
+        __syncthreads();
+        return;
+    }
+    float *tilem = reinterpret_cast<float *>(buf);
+#pragma unroll
+    for (int i = 0; i < R0; ++i) {
+        const int d = fft_out_index<N>(tid, i);
+        const int ds = d + (N >> 1);
+        tilem[c * (N + 1) + (ds >= N ? ds - N : ds)] = acc[i];
+    }
+    __syncthreads();
+    float *dst = part + (int64_t)gg * M * N + (int64_t)r0 * N;
+    for (int j = threadIdx.x; j < RB * N; j += kRegThreads) dst[j] = tilem[(j / N) * (N + 1) + j % N];
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// the driver's tensor-map encoder, through the runtime's entry-point query
+static EncodeTiledFn tensor_map_encoder()
+{
+    static const EncodeTiledFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return static_cast<EncodeTiledFn>(nullptr);
+        }
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+// TMA Doppler pass over X ([rows][M] complex64, rows = O groups N); false
+// (nothing launched) when the tensor map cannot be made
+template <int N>
+static bool doppler_tma_launch(const float2 *X, int M, int O, int groups, int window, float *part,
+                               int CPB, int *status, cudaStream_t s)
+{
+    using Q = TmaDoppler<N>;
+    const EncodeTiledFn enc = tensor_map_encoder();
+    if (!enc || (reinterpret_cast<uintptr_t>(X) & 15u) != 0) return false;
+    CUtensorMap map;
+    const cuuint64_t dims[2] = {(cuuint64_t)2 * M, (cuuint64_t)O * groups * N};
+    const cuuint64_t strides[1] = {(cuuint64_t)M * sizeof(float2)};
+    const cuuint32_t box[2] = {(cuuint32_t)(2 * Q::RB), (cuuint32_t)N};
+    const cuuint32_t estr[2] = {1, 1};
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2 *>(X), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    const int G = (O + CPB - 1) / CPB;
+    cudaFuncSetAttribute(doppler_sum_tma_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)Q::kSmem);
+    doppler_sum_tma_kernel<N><<<dim3((unsigned int)(M / Q::RB), (unsigned int)(G * groups)),
+                                kRegThreads, Q::kSmem, s>>>(map, M, CPB, O, window, status, part);
+    return true;
+}
+
 template <int N>
 static size_t doppler_reg_smem()
 {
@@ -532,8 +735,21 @@ static void range_reg_dispatch(const float2 *adc, float2 *X, int64_t rows, int M
 }
 
 static void doppler_reg_dispatch(const float2 *X, int N, int M, int O, int groups, int window,
-                                 float *part, int CPB, int accumulate, cudaStream_t s)
+                                 float *part, int CPB, int accumulate, int *status,
+                                 cudaStream_t s)
 {
+    // TMA tile loads where one box covers the tile (32 <= N <= 256 chirps)
+    if (!accumulate) {
+        bool done = false;
+        switch (N) {
+        case 32: done = doppler_tma_launch<32>(X, M, O, groups, window, part, CPB, status, s); break;
+        case 64: done = doppler_tma_launch<64>(X, M, O, groups, window, part, CPB, status, s); break;
+        case 128: done = doppler_tma_launch<128>(X, M, O, groups, window, part, CPB, status, s); break;
+        case 256: done = doppler_tma_launch<256>(X, M, O, groups, window, part, CPB, status, s); break;
+        default: break;
+        }
+        if (done) return;
+    }
     switch (N) {
     case 16: doppler_reg_launch<16>(X, M, O, groups, window, part, CPB, accumulate, s); break;
     case 32: doppler_reg_launch<32>(X, M, O, groups, window, part, CPB, accumulate, s); break;
@@ -551,19 +767,19 @@ static void doppler_reg_dispatch(const float2 *X, int N, int M, int O, int group
 // on the 192 x 256 x 512 cube: twelve short launches, each a fraction of a
 // wave, and the chunks' partial maps added in place.)
 static int run_rdm_reg(const float2 *adc, const RadarDev &rd, int groups, float2 *X, float *part,
-                       cudaStream_t s)
+                       int *status, cudaStream_t s)
 {
     const int M = rd.M, N = rd.N, O = rd.O;
     const int RB = reg_rb(N);
     range_reg_dispatch(adc, X, (int64_t)O * groups * N, M, rd.window, s);
     const int CPB = rdm_cpb(O, M / RB, groups);
-    doppler_reg_dispatch(X, N, M, O, groups, rd.window, part, CPB, 0, s);
+    doppler_reg_dispatch(X, N, M, O, groups, rd.window, part, CPB, 0, status, s);
     return (O + CPB - 1) / CPB;
 }
 
 template <typename T>
 static void run_rdm(const void *adc, const RadarDev &rd, int groups, void *ws, float *rdm,
-                    cudaStream_t s)
+                    int *status, cudaStream_t s)
 {
     using C = typename Cplx<T>::type;
     const int M = rd.M, N = rd.N, O = rd.O;
@@ -572,7 +788,8 @@ static void run_rdm(const void *adc, const RadarDev &rd, int groups, void *ws, f
     if (std::is_same<T, float>::value && rdm_reg_supported(rd)) {
         float2 *X = reinterpret_cast<float2 *>(ws);
         float *part = reinterpret_cast<float *>(X + Oall * N * M);
-        const int G = run_rdm_reg(reinterpret_cast<const float2 *>(adc), rd, groups, X, part, s);
+        const int G =
+            run_rdm_reg(reinterpret_cast<const float2 *>(adc), rd, groups, X, part, status, s);
         rdm_sum_kernel<float><<<(unsigned int)((MN * groups + 255) / 256), 256, 0, s>>>(
             part, G, MN, groups, rdm);
         return;
@@ -658,10 +875,10 @@ void launch_rdm_cube(const void *adc, int dtype, const RadarDev &rd, void *X, vo
 }
 
 void launch_rdm(const void *adc, int dtype, const RadarDev &rd, int groups, void *ws, float *rdm,
-                cudaStream_t s)
+                int *status, cudaStream_t s)
 {
-    if (dtype == BART_C64) run_rdm<float>(adc, rd, groups, ws, rdm, s);
-    else run_rdm<double>(adc, rd, groups, ws, rdm, s);
+    if (dtype == BART_C64) run_rdm<float>(adc, rd, groups, ws, rdm, status, s);
+    else run_rdm<double>(adc, rd, groups, ws, rdm, status, s);
 }
 
 // -------------------------------------------------------------------------
