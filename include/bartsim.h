@@ -179,6 +179,15 @@ const char *bart_version(void);
  * Errors: EINVAL (nth < 0). */
 int bart_inject_alloc_failure(int32_t nth);
 
+/* Self-test of the bounded device waits (the TMA-fed Doppler pass of
+ * bart_form_rdm waits on mbarriers for its tile copies, with a limit): one
+ * block waits `polls` polls (1 .. 2^20) on a barrier that nothing
+ * completes, so the wait expires by design, and the context's device status
+ * records it.  The next bart_sync returns BART_ETIMEOUT, clears the status,
+ * and the context stays usable.  Enqueued on the context's stream.
+ * Errors: EINVAL (ctx NULL, polls out of range), ECUDA. */
+int bart_selftest_wait_timeout(bart_ctx *ctx, int32_t polls);
+
 /* Create a context on CUDA device `device`.  *out receives the handle.
  * Errors: EINVAL (bad device / NULL out), ECUDA. */
 int bart_create(bart_ctx **out, int device);

@@ -38,7 +38,8 @@ EXPORTED = ["bart_last_error", "bart_version", "bart_create", "bart_destroy",
             "bart_scene_partition", "bart_set_graph", "bart_set_synth_layout",
             "bart_autotune", "bart_rdm_adjoint", "bart_simulate_adjoint",
             "bart_simulate_adjoint_mixed",
-            "bart_mesh_update", "bart_measure_peaks", "bart_inject_alloc_failure"]
+            "bart_mesh_update", "bart_measure_peaks", "bart_inject_alloc_failure",
+            "bart_selftest_wait_timeout"]
 
 
 class BartError(RuntimeError):
@@ -182,6 +183,7 @@ def load_library() -> ctypes.CDLL:
                                   ctypes.POINTER(I32)]
         L.bart_measure_peaks.argtypes = [I32, I32, ctypes.POINTER(bart_peaks)]
         L.bart_inject_alloc_failure.argtypes = [I32]
+        L.bart_selftest_wait_timeout.argtypes = [P, I32]
         for name in EXPORTED:
             if name not in ("bart_last_error", "bart_version", "bart_destroy"):
                 getattr(L, name).restype = ctypes.c_int
@@ -433,6 +435,12 @@ def bart_inject_alloc_failure(nth: int) -> None:
     """Make the library's nth device allocation from now fail with
     BART_ENOMEM (host-side fault injection; 0 disarms)."""
     _check(load_library().bart_inject_alloc_failure(int(nth)))
+
+
+def bart_selftest_wait_timeout(ctx: int, polls: int = 4096) -> None:
+    """Enqueue the bounded-wait self-test: a wait that expires by design;
+    the next bart_sync raises BartError(BART_ETIMEOUT)."""
+    _check(load_library().bart_selftest_wait_timeout(ctx, int(polls)))
 
 
 def bart_measure_peaks(device: int = 0, reps: int = 5) -> dict:

@@ -331,6 +331,18 @@ int bart_inject_alloc_failure(int32_t nth)
     return BART_OK;
 }
 
+int bart_selftest_wait_timeout(bart_ctx *ctx, int32_t polls)
+{
+    g_err.clear();
+    if (!ctx) return fail(BART_EINVAL, "bart_selftest_wait_timeout: ctx is NULL");
+    if (polls < 1 || polls > (1 << 20))
+        return fail(BART_EINVAL, "bart_selftest_wait_timeout: polls=%d outside [1, 2^20]", polls);
+    BART_TRY(set_device(ctx));
+    launch_wait_selftest(polls, ctx->status.p, ctx->stream);
+    CUDA_TRY(cudaGetLastError(), "wait self-test launch");
+    return BART_OK;
+}
+
 int bart_create(bart_ctx **out, int device)
 {
     g_err.clear();

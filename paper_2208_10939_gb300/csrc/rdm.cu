@@ -383,9 +383,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return ok != 0;
 }
 // bounded wait for the phase `parity` of `bar`; false if the limit expired
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  int limit = kTmaWaitLimit)
 {
-    for (int i = 0; i < kTmaWaitLimit; ++i)
+    for (int i = 0; i < limit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }
@@ -397,6 +398,33 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
         "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
+}
+
+// The expiry path of the bounded mbarrier wait, exercised on purpose: a
+// barrier expecting one arrival that never comes, waited on by every thread
+// for `polls` polls; on expiry the status word gets kStatusWaitTimeout, as
+// in the Doppler pass.  The barrier is invalidated before the block exits.
+__global__ void wait_selftest_kernel(int polls, int *status)
+{
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_expired;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_expired = 0;
+    }
+    __syncthreads();
+    if (!mbar_wait_bounded(&bar, 0u, polls)) s_expired = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_expired && status) atomicOr(status, kStatusWaitTimeout);
+        asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar)) : "memory");
+    }
+}
+
+void launch_wait_selftest(int polls, int *status, cudaStream_t s)
+{
+    wait_selftest_kernel<<<1, 64, 0, s>>>(polls, status);
 }
 
 template <int N>

@@ -1,7 +1,9 @@
-"""Failure detection without a GPU fault: a device allocation made to fail on
+"""Failure detection without a GPU fault.  A device allocation made to fail on
 the host (bart_inject_alloc_failure) surfaces as BART_ENOMEM from
 bart_simulate_frame with the failing buffer named, whichever allocation of
-the frame fails, and the context stays usable afterwards."""
+the frame fails, and the context stays usable afterwards.  A bounded device
+wait that expires (an mbarrier nothing completes, by design) surfaces as
+BART_ETIMEOUT from bart_sync, and the context stays usable."""
 import numpy as np
 import pytest
 import torch
@@ -55,3 +57,28 @@ def test_static_rdm_allocates_nothing_even_when_allocation_would_fail():
         assert torch.isfinite(rdm).all()
     finally:
         pkg.bart_inject_alloc_failure(0)
+
+
+def test_bounded_wait_expiry_reports_etimeout_and_the_context_stays_usable():
+    """The bounded device waits' expiry path, exercised on purpose: a block
+    waits a few thousand polls on an mbarrier that nothing completes (the
+    mechanism the TMA-fed Doppler pass uses for its tile copies).  The wait
+    ends, bart_sync reports BART_ETIMEOUT once, and the same context then
+    forms an RDM that matches the oracle (the TMA Doppler pass included)."""
+    import oracle
+    sc = sg.small_car_scene(ntri=400, M=64, N=32, P=2, Q=2)
+    sim = pkg.Simulator(0)
+    try:
+        sim.load_scene(sc)
+        pkg.bart_selftest_wait_timeout(sim.ctx, 4096)
+        with pytest.raises(pkg.BartError) as ei:
+            sim.sync()
+        assert ei.value.code == pkg.BART_ETIMEOUT, ei.value
+        sim.sync()                                   # the status was cleared
+        adc = sim.simulate(pkg.PATH_FP64)
+        rdm = sim.rdm(adc.to(torch.complex64).contiguous()).cpu().numpy()
+        sim.sync()
+        ref = oracle.range_doppler_map(adc.cpu().numpy().astype(np.complex64).astype(np.complex128))
+        assert np.abs(rdm - ref).max() <= 1e-5 * ref.max()
+    finally:
+        sim.close()
