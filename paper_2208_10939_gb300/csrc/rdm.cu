@@ -269,13 +269,11 @@ __device__ __forceinline__ void cp_async_wait()
 
 // Doppler pass over channels o0 .. o1 - 1 of the cube X ([o][n][r], rows of
 // M range bins); the next channel's tile is copied into shared memory
-// (cp.async, two stages) while the current one is transformed.  With
-// `accumulate` the partial map adds the values already in `part` (the
-// channel-chunked schedule).
+// (cp.async, two stages) while the current one is transformed.
 template <int N>
 __global__ void __launch_bounds__(kRegThreads, 2)
 doppler_sum_reg_kernel(const float2 *__restrict__ X, int M, int CPB, int O, int window,
-                       int accumulate, float *__restrict__ part)
+                       float *__restrict__ part)
 {
     using namespace fftr;
     constexpr int R0 = Plan<N>::R0, T = N / R0, RB = kRegThreads / T;
@@ -338,7 +336,7 @@ doppler_sum_reg_kernel(const float2 *__restrict__ X, int M, int CPB, int O, int 
     float *dst = part + (int64_t)gg * M * N + (int64_t)blockIdx.x * RB * N;
     for (int j = threadIdx.x; j < RB * N; j += kRegThreads) {
         const float v = tile[(j / N) * (N + 1) + j % N];
-        dst[j] = accumulate ? dst[j] + v : v;
+        dst[j] = v;
     }
 }
 
@@ -727,7 +725,7 @@ static void range_reg_launch(const float2 *adc, float2 *X, int64_t rows, int win
 
 template <int N>
 static void doppler_reg_launch(const float2 *X, int M, int O, int groups, int window, float *part,
-                               int CPB, int accumulate, cudaStream_t s)
+                               int CPB, cudaStream_t s)
 {
     constexpr int RB = kRegThreads / (N / fftr::Plan<N>::R0);
     const int G = (O + CPB - 1) / CPB;
@@ -735,7 +733,7 @@ static void doppler_reg_launch(const float2 *X, int M, int O, int groups, int wi
     cudaFuncSetAttribute(doppler_sum_reg_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sm);
     doppler_sum_reg_kernel<N><<<dim3((unsigned int)(M / RB), (unsigned int)(G * groups)),
-                                kRegThreads, sm, s>>>(X, M, CPB, O, window, accumulate, part);
+                                kRegThreads, sm, s>>>(X, M, CPB, O, window, part);
 }
 
 static bool reg_len_ok(int L) { return L >= 16 && L <= 1024 && is_pow2_len(L); }
@@ -763,11 +761,11 @@ static void range_reg_dispatch(const float2 *adc, float2 *X, int64_t rows, int M
 }
 
 static void doppler_reg_dispatch(const float2 *X, int N, int M, int O, int groups, int window,
-                                 float *part, int CPB, int accumulate, int *status,
+                                 float *part, int CPB, int *status,
                                  cudaStream_t s)
 {
     // TMA tile loads where one box covers the tile (32 <= N <= 256 chirps)
-    if (!accumulate) {
+    {
         bool done = false;
         switch (N) {
         case 32: done = doppler_tma_launch<32>(X, M, O, groups, window, part, CPB, status, s); break;
@@ -779,13 +777,13 @@ static void doppler_reg_dispatch(const float2 *X, int N, int M, int O, int group
         if (done) return;
     }
     switch (N) {
-    case 16: doppler_reg_launch<16>(X, M, O, groups, window, part, CPB, accumulate, s); break;
-    case 32: doppler_reg_launch<32>(X, M, O, groups, window, part, CPB, accumulate, s); break;
-    case 64: doppler_reg_launch<64>(X, M, O, groups, window, part, CPB, accumulate, s); break;
-    case 128: doppler_reg_launch<128>(X, M, O, groups, window, part, CPB, accumulate, s); break;
-    case 256: doppler_reg_launch<256>(X, M, O, groups, window, part, CPB, accumulate, s); break;
-    case 512: doppler_reg_launch<512>(X, M, O, groups, window, part, CPB, accumulate, s); break;
-    default: doppler_reg_launch<1024>(X, M, O, groups, window, part, CPB, accumulate, s); break;
+    case 16: doppler_reg_launch<16>(X, M, O, groups, window, part, CPB, s); break;
+    case 32: doppler_reg_launch<32>(X, M, O, groups, window, part, CPB, s); break;
+    case 64: doppler_reg_launch<64>(X, M, O, groups, window, part, CPB, s); break;
+    case 128: doppler_reg_launch<128>(X, M, O, groups, window, part, CPB, s); break;
+    case 256: doppler_reg_launch<256>(X, M, O, groups, window, part, CPB, s); break;
+    case 512: doppler_reg_launch<512>(X, M, O, groups, window, part, CPB, s); break;
+    default: doppler_reg_launch<1024>(X, M, O, groups, window, part, CPB, s); break;
     }
 }
 
@@ -801,7 +799,7 @@ static int run_rdm_reg(const float2 *adc, const RadarDev &rd, int groups, float2
     const int RB = reg_rb(N);
     range_reg_dispatch(adc, X, (int64_t)O * groups * N, M, rd.window, s);
     const int CPB = rdm_cpb(O, M / RB, groups);
-    doppler_reg_dispatch(X, N, M, O, groups, rd.window, part, CPB, 0, status, s);
+    doppler_reg_dispatch(X, N, M, O, groups, rd.window, part, CPB, status, s);
     return (O + CPB - 1) / CPB;
 }
 

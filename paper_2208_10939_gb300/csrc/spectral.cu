@@ -148,8 +148,6 @@ synth_spectral_kernel(SynthArgs A, MixConsts K, SpecConsts C, const float *__res
     const int32_t *list = A.vis_idx + (int64_t)o * F + (A.vstart ? A.vstart[vrow] : 0);
     const int cnt = A.vcnt[vrow];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    const int seg = (cnt + 31) / 32;
-    const int i_end = min(cnt, (lane + 1) * seg);
     unsigned long long nV = 0, nSr = 0, nE = 0;
     const float twopi = 6.283185307179586f;
     auto process = [&](int i) {
