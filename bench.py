@@ -58,7 +58,7 @@ OPS_PER_TERM = 24
 # terms (16 and 64 chirps read 3.41 and 3.28 GB); the items' partial sums
 # grow with the (channel, chirp) rows.  Valid only while the kernel's sources
 # hash to the value they had at the capture.
-SYNTH_PROFILE = {"sources_sha256_16": "6bea74869664e921", "samples_per_lane": 16,
+SYNTH_PROFILE = {"sources_sha256_16": "4239e3318de9d32c", "samples_per_lane": 16,
                  "dram_read_bytes_per_channel_facet": 3.277169152e9 / (4 * 50804670464 / (64 * 512)),
                  "dram_write_bytes_per_row": 75.109632e6 / (16 * 64),
                  "fma_pipe_active": 0.686}

@@ -236,12 +236,12 @@ void launch_add_noise(void *adc, int dtype, int64_t n, double snr_db, uint64_t s
 int64_t rdm_workspace_bytes(const RadarDev &rd, int dtype);
 // groups: independent cubes of rd.O channels each, back to back (batched
 // scenes); rdm receives groups x M x N; ws holds groups x rdm_workspace_bytes
-// one block waiting `polls` polls on an mbarrier that nothing completes
-// (the bounded-wait expiry path; sets kStatusWaitTimeout in *status)
-void launch_wait_selftest(int polls, int *status, cudaStream_t s);
 // status: the context's device status word (kStatusWaitTimeout), or NULL
 void launch_rdm(const void *adc, int dtype, const RadarDev &rd, int groups, void *ws, float *rdm,
                 int *status, cudaStream_t s);
+// one block waiting `polls` polls on an mbarrier that nothing completes
+// (the bounded-wait expiry path; sets kStatusWaitTimeout in *status)
+void launch_wait_selftest(int polls, int *status, cudaStream_t s);
 
 // RDM that also keeps the complex range-Doppler cube Y[o][r][d'] (Doppler
 // shifted) in `cube`; X is an O*N*M complex scratch of the same precision.
