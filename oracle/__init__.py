@@ -85,6 +85,16 @@ def _load():
             lib.orc_adc_entries.argtypes = [P, P, P, P, P, P, ctypes.c_int64, P, P,
                                             ctypes.POINTER(_Radar), P,
                                             ctypes.c_int64, P]
+            lib.orc_bounce2_facets.argtypes = [P, P, P, P, ctypes.c_int64, P, ctypes.c_int, P,
+                                               ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_double, ctypes.c_int64, P, P, P, P, P]
+            lib.orc_bounce2_facets.restype = ctypes.c_int64
+            lib.orc_rcs_farfield_bounce2.argtypes = [P, ctypes.c_int64, P, P, P, P, P,
+                                                     ctypes.c_int, P]
+            lib.orc_adc_bounce2_entries.argtypes = [P, P, P, P, P, ctypes.c_int64, P, P, P,
+                                                    ctypes.c_int64, P, P,
+                                                    ctypes.POINTER(_Radar), P,
+                                                    ctypes.c_int64, P]
             lib.orc_num_threads.restype = ctypes.c_int
             lib.orc_set_threads.argtypes = [ctypes.c_int]
             _lib = lib
@@ -212,6 +222,53 @@ def rcs_farfield(tri: np.ndarray, rho: np.ndarray, t_hat, r_hat, freqs,
     return out
 
 
+def bounce2_facets(tri: np.ndarray, fvel: np.ndarray, rho: np.ndarray, antennas: np.ndarray,
+                   P: int, state: np.ndarray, two_sided=None, eps_face: float = EPS_FACE,
+                   eps_b: float = EPS_B, eps_t: float = EPS_T) -> dict:
+    """Virtual facets of the double-bounce paths (Sec. 2.2: forward and
+    backward rays connected through two facets; the geometric-optics /
+    physical-optics reading stated in ``oracle.c``) of transmitters 0..P-1:
+    ``pab`` (V x 4: TX p, first facet a, second facet b, side of b), ``tri``
+    (V x 9 frame-start vertices), ``src`` (V x 3 image source), ``usrc``
+    (V x 3 its velocity), ``w`` (V: -rho_a rho_b), in (p, a, b, fan) order."""
+    tri = np.ascontiguousarray(tri, np.float64)
+    F = tri.shape[0]
+    fv = np.ascontiguousarray(fvel, np.float64).reshape(F, 3)
+    rh = np.ascontiguousarray(rho, np.float32).reshape(F)
+    ant = np.ascontiguousarray(antennas, np.float64).reshape(-1, 3)
+    st = np.ascontiguousarray(state, np.uint8)
+    ts = _opt(two_sided, np.uint8, (F,))
+    cap = 1024
+    while True:
+        out = dict(pab=np.zeros((cap, 4), np.int32), tri=np.zeros((cap, 9)),
+                   src=np.zeros((cap, 3)), usrc=np.zeros((cap, 3)), w=np.zeros(cap))
+        n = int(_load().orc_bounce2_facets(
+            _p(tri), _p(fv), _p(rh), _ptr_or_none(ts), F, _p(ant), int(P), _p(st),
+            eps_face, eps_b, eps_t, cap, _p(out["pab"]), _p(out["tri"]), _p(out["src"]),
+            _p(out["usrc"]), _p(out["w"])))
+        if n <= cap:
+            return {k: np.ascontiguousarray(v[:n]) for k, v in out.items()}
+        cap = n
+
+
+def rcs_farfield_bounce2(tri: np.ndarray, rho: np.ndarray, t_hat, r_hat, freqs,
+                         two_sided=None) -> np.ndarray:
+    """Far-field double-bounce PO cross-section sigma(f) (m^2) of a mesh
+    for plane-wave directions (toward TX ``t_hat`` and RX ``r_hat``): the
+    double-bounce reading of Sec. 2.2 with the image source at infinity, no
+    occlusion test."""
+    tri = np.ascontiguousarray(tri, np.float64)
+    rho = np.ascontiguousarray(rho, np.float32)
+    t = np.ascontiguousarray(t_hat, np.float64) / np.linalg.norm(t_hat)
+    r = np.ascontiguousarray(r_hat, np.float64) / np.linalg.norm(r_hat)
+    f = np.ascontiguousarray(np.atleast_1d(freqs), np.float64)
+    ts = _opt(two_sided, np.uint8, (tri.shape[0],))
+    out = np.empty(f.shape[0], np.float64)
+    _load().orc_rcs_farfield_bounce2(_p(tri), tri.shape[0], _p(rho), _ptr_or_none(ts), _p(t),
+                                     _p(r), _p(f), f.shape[0], _p(out))
+    return out
+
+
 def _radar_struct(radar) -> _Radar:
     ff, dr = bool(getattr(radar, "far_field", False)), bool(getattr(radar, "delay_ref", False))
     if ff and dr:
@@ -242,6 +299,30 @@ class Frame:
                        fref=self.fref if self._rs.far_field else None,
                        two_sided=self.two_sided)
         self.state = state
+        self.double_bounce = bool(getattr(self.radar, "double_bounce", False))
+        if self.double_bounce and (self._rs.far_field or self._rs.delay_ref):
+            raise ValueError("double bounce takes the per-facet delay form")
+        self.bounce = None
+        if self.double_bounce:
+            self.bounce = bounce2_facets(self.tri0, self.fvel, self.rho, self.radar.antennas,
+                                         self.radar.P, self.state, two_sided=self.two_sided,
+                                         eps_face=float(getattr(self.radar, "grazing_eps",
+                                                                EPS_FACE)))
+
+    def bounce_entries(self, entries: np.ndarray) -> np.ndarray:
+        """Double-bounce part of selected ADC entries (E x 3: o, n, m)."""
+        r = self.radar
+        e = np.ascontiguousarray(entries, np.int32).reshape(-1, 3)
+        out = np.zeros(e.shape[0], np.complex128)
+        b = self.bounce
+        if b is None or b["w"].shape[0] == 0:
+            return out
+        _load().orc_adc_bounce2_entries(
+            _p(b["pab"]), _p(b["tri"]), _p(b["src"]), _p(b["usrc"]), _p(b["w"]),
+            b["w"].shape[0], _p(self.fvel), _ptr_or_none(self.two_sided), _p(self.state),
+            self.tri0.shape[0], _p(r.tx), _p(r.rx), ctypes.byref(self._rs), _p(e), e.shape[0],
+            _p(out))
+        return out
 
     def _args(self):
         r = self.radar
@@ -254,6 +335,10 @@ class Frame:
         r = self.radar
         out = np.empty((r.O, r.N, r.M), np.complex128)
         _load().orc_adc_full(*self._args(), _p(out))
+        if self.double_bounce:
+            o, n, m = np.meshgrid(np.arange(r.O), np.arange(r.N), np.arange(r.M), indexing="ij")
+            e = np.stack([o.ravel(), n.ravel(), m.ravel()], 1)
+            out += self.bounce_entries(e).reshape(out.shape)
         return out
 
     def adc_entries(self, entries: np.ndarray) -> np.ndarray:
@@ -261,6 +346,8 @@ class Frame:
         e = np.ascontiguousarray(entries, np.int32).reshape(-1, 3)
         out = np.empty(e.shape[0], np.complex128)
         _load().orc_adc_entries(*self._args(), _p(e), e.shape[0], _p(out))
+        if self.double_bounce:
+            out += self.bounce_entries(e)
         return out
 
     def lit_pairs(self) -> np.ndarray:

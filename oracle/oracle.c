@@ -745,3 +745,383 @@ void orc_adc_entries(const double *tri0, const double *fvel, const float *rho,
         adc_sample(tri0, fvel, rho, fref, two_sided, state, F, tx, rx, rd, entries[3 * e],
                    entries[3 * e + 1], entries[3 * e + 2], out + 2 * e, out + 2 * e + 1);
 }
+
+/* ------------------------------------------------------------------ */
+/* double bounce (Sec. 2.2: forward and backward rays connected       */
+/* through two facets)                                                 */
+/* ------------------------------------------------------------------ */
+/*
+ * The paper names multi-bounce paths (a forward ray from TX and a backward
+ * ray from RX joined on a facet after further reflections) but prints no
+ * formula for them.  Reading used here for two facets, geometric optics at
+ * the first and physical optics at the second:
+ *
+ *  - the forward ray from TX p reaches facet a (a lit from TX p, its
+ *    single-bounce state LIT or LIT_REV: side s_a = +1 / -1) and reflects
+ *    specularly: beyond a, the reflected field is that of the image source
+ *    p' = p - 2 ((p - x0_a).n_a / |n_a|^2) n_a (mirror of p in a's plane),
+ *    confined to the beam of rays from p' through the triangle a;
+ *  - the part of facet b inside that beam, Pi_ab = b clipped by a's front
+ *    half-space (s_a n_a.(x - x0_a) >= 0) and the three planes through p'
+ *    and a's edges (each keeping a's third vertex), is lit by the image
+ *    source; b must face p' (cos >= eps_face, or <= -eps_face on a
+ *    two-sided b: side s_b = -1);
+ *  - the a -> b leg is the segment from the specular point s (where the
+ *    line p' -> c_Pi meets a's plane, c_Pi the mean of Pi's vertices) to
+ *    c_Pi; the pair is dropped when that segment hits, or grazes, any facet
+ *    other than a and b (the Moller-Trumbore test and margins of the
+ *    single-bounce visibility);
+ *  - the backward ray from RX q meets b: b's single-bounce state from RX q
+ *    is LIT for s_b = +1, LIT_REV for s_b = -1;
+ *  - Pi_ab is split into the fan (Pi_0, Pi_i, Pi_i+1); sub-triangles whose
+ *    |cross| is at most 1e-6 |n_b| (clip slivers) are dropped; each kept
+ *    one is a virtual facet that scatters like a single-bounce facet of the
+ *    echo synthesis below, with the transmitter replaced by p' and the
+ *    reflectivity by -rho_a rho_b (-1: the reflection coefficient of a
+ *    perfectly conducting plane for the scalar, co-polarised field; rho_b
+ *    is the PO facet's own, as in the single bounce);
+ *  - pairs, clips and visibility are decided on the frame-start geometry,
+ *    like the single-bounce states; afterwards a virtual facet moves with b
+ *    and p' with a's plane: p'(t) = p'_0 + u t, u = 2 (v_a.n_a / |n_a|^2) n_a.
+ *
+ * All decisions use one IEEE rounding per operation in the order written
+ * (the library built with -ffp-contract=off), so they are reproducible.
+ */
+#define ORC_DB_MAXV 7
+#define ORC_DB_SLIVER 1e-6
+
+/* Sutherland-Hodgman step: the part of the convex polygon (n vertices) with
+ * g.(x - base) >= 0.  Returns the new vertex count. */
+static int clip_keep(const double *in, int n, const double *g, const double *base, double *out)
+{
+    int k = 0;
+    for (int i = 0; i < n; ++i) {
+        const double *P = in + 3 * i, *Q = in + 3 * ((i + 1) % n);
+        double d[3];
+        sub3(P, base, d);
+        const double fP = dot3(g, d);
+        sub3(Q, base, d);
+        const double fQ = dot3(g, d);
+        if (fP >= 0.0) {
+            for (int r = 0; r < 3; ++r) out[3 * k + r] = P[r];
+            ++k;
+        }
+        if ((fP >= 0.0) != (fQ >= 0.0)) {
+            const double t = fP / (fP - fQ);
+            for (int r = 0; r < 3; ++r) out[3 * k + r] = P[r] + t * (Q[r] - P[r]);
+            ++k;
+        }
+    }
+    return k;
+}
+
+/* The beam of facet a for a source at p' (point source, dir == NULL) or for
+ * plane waves toward the image direction dir (the far-field form): four
+ * half-spaces (g, base). */
+static void beam_planes(const double *ta, int side_a, const double *src, const double *dir,
+                        double *g, double *base)
+{
+    double e1[3], e2[3], n[3];
+    sub3(ta + 3, ta, e1);
+    sub3(ta + 6, ta, e2);
+    cross3(e1, e2, n);
+    for (int r = 0; r < 3; ++r) {
+        g[r] = side_a > 0 ? n[r] : -n[r];
+        base[r] = ta[r];
+    }
+    for (int i = 0; i < 3; ++i) {
+        const double *xi = ta + 3 * i, *xj = ta + 3 * ((i + 1) % 3), *xk = ta + 3 * ((i + 2) % 3);
+        double m[3], d[3];
+        if (dir) {
+            double e[3];
+            sub3(xj, xi, e);
+            cross3(e, dir, m);
+            sub3(xk, xi, d);
+            for (int r = 0; r < 3; ++r) base[3 * (i + 1) + r] = xi[r];
+        } else {
+            double u[3], v[3];
+            sub3(xi, src, u);
+            sub3(xj, src, v);
+            cross3(u, v, m);
+            sub3(xk, src, d);
+            for (int r = 0; r < 3; ++r) base[3 * (i + 1) + r] = src[r];
+        }
+        const double s = dot3(m, d) < 0.0 ? -1.0 : 1.0;
+        for (int r = 0; r < 3; ++r) g[3 * (i + 1) + r] = s * m[r];
+    }
+}
+
+/* Pi = triangle tb clipped by the four half-spaces; returns its vertex count */
+static int beam_clip(const double *tb, const double *g, const double *base, double *poly)
+{
+    double buf[3 * ORC_DB_MAXV];
+    int n = 3;
+    for (int i = 0; i < 9; ++i) poly[i] = tb[i];
+    for (int h = 0; h < 4 && n >= 3; ++h) {
+        n = clip_keep(poly, n, g + 3 * h, base + 3 * h, buf);
+        for (int i = 0; i < 3 * n; ++i) poly[i] = buf[i];
+    }
+    return n;
+}
+
+/* Virtual facets of the double-bounce paths of transmitters 0..P-1 (the
+ * reading above), in the order (p, a, b, fan index).  tri: F x 9 frame-start
+ * world vertices; fvel: F x 3 velocities; rho: F reflectivities; two_sided:
+ * F flags or NULL; ant: antennas (TX first); state: single-bounce states
+ * (TX rows 0..P-1 used).  Writes up to cap facets: pab (4 int32 each: p, a,
+ * b, s_b), vtri (9), src (p'_0, 3), usrc (u, 3), w (-rho_a rho_b); returns
+ * the total count (call again with a larger cap when it exceeds cap). */
+int64_t orc_bounce2_facets(const double *tri, const double *fvel, const float *rho,
+                           const uint8_t *two_sided, int64_t F, const double *ant, int P,
+                           const uint8_t *state, double eps_face, double eps_b, double eps_t,
+                           int64_t cap, int32_t *pab, double *vtri, double *src, double *usrc,
+                           double *w)
+{
+    int64_t count = 0;
+    for (int p = 0; p < P; ++p) {
+        const double *pt = ant + 3 * p;
+        for (int64_t a = 0; a < F; ++a) {
+            const uint8_t st = state[(int64_t)p * F + a];
+            if (st != ORC_LIT && st != ORC_LIT_REV) continue;
+            const double *ta = tri + 9 * a;
+            double e1[3], e2[3], na[3], d[3], img[3], u[3];
+            sub3(ta + 3, ta, e1);
+            sub3(ta + 6, ta, e2);
+            cross3(e1, e2, na);
+            const double nn = dot3(na, na);
+            sub3(pt, ta, d);
+            const double sc = (2.0 * dot3(d, na)) / nn;
+            for (int r = 0; r < 3; ++r) img[r] = pt[r] - sc * na[r];
+            const double su = (2.0 * dot3(fvel + 3 * a, na)) / nn;
+            for (int r = 0; r < 3; ++r) u[r] = su * na[r];
+            double g[12], base[12];
+            beam_planes(ta, st == ORC_LIT ? 1 : -1, img, NULL, g, base);
+            for (int64_t b = 0; b < F; ++b) {
+                if (b == a) continue;
+                const double *tb = tri + 9 * b;
+                double f1[3], f2[3], nb[3], cb[3], D[3];
+                sub3(tb + 3, tb, f1);
+                sub3(tb + 6, tb, f2);
+                cross3(f1, f2, nb);
+                const double nbb = dot3(nb, nb);
+                if (nbb == 0.0) continue;
+                centroid3(tb, cb);
+                sub3(img, cb, D);
+                const double cosang = dot3(nb, D) / (sqrt(nbb) * sqrt(dot3(D, D)));
+                int side_b;
+                if (cosang >= eps_face) side_b = 1;
+                else if (two_sided && two_sided[b] && cosang <= -eps_face) side_b = -1;
+                else continue;
+                double poly[3 * ORC_DB_MAXV];
+                const int K = beam_clip(tb, g, base, poly);
+                if (K < 3) continue;
+                const double thr = ORC_DB_SLIVER * sqrt(nbb);
+                int keep[ORC_DB_MAXV];
+                int nkeep = 0;
+                for (int i = 1; i + 1 < K; ++i) {
+                    double x1[3], x2[3], cr[3];
+                    sub3(poly + 3 * i, poly, x1);
+                    sub3(poly + 3 * (i + 1), poly, x2);
+                    cross3(x1, x2, cr);
+                    keep[i] = sqrt(dot3(cr, cr)) > thr;
+                    nkeep += keep[i];
+                }
+                if (nkeep == 0) continue;
+                /* the a -> b leg: specular point s on a's plane -> c_Pi */
+                double cp[3] = {0.0, 0.0, 0.0}, sp[3], Dl[3], t1[3], t2[3];
+                for (int i = 0; i < K; ++i)
+                    for (int r = 0; r < 3; ++r) cp[r] = cp[r] + poly[3 * i + r];
+                for (int r = 0; r < 3; ++r) cp[r] = cp[r] / (double)K;
+                sub3(ta, img, t1);
+                sub3(cp, img, t2);
+                const double lam = dot3(na, t1) / dot3(na, t2);
+                for (int r = 0; r < 3; ++r) sp[r] = img[r] + lam * t2[r];
+                sub3(cp, sp, Dl);
+                int blocked = 0;
+                for (int64_t j = 0; j < F && !blocked; ++j) {
+                    if (j == a || j == b) continue;
+                    if (boxes_disjoint(sp, cp, tri + 9 * j, 1e-6)) continue;
+                    if (mt_segment(sp, Dl, tri + 9 * j, eps_b, eps_t) != 0) blocked = 1;
+                }
+                if (blocked) continue;
+                for (int i = 1; i + 1 < K; ++i) {
+                    if (!keep[i]) continue;
+                    if (count < cap) {
+                        int32_t *q = pab + 4 * count;
+                        q[0] = p;
+                        q[1] = (int32_t)a;
+                        q[2] = (int32_t)b;
+                        q[3] = side_b;
+                        double *vt = vtri + 9 * count;
+                        for (int r = 0; r < 3; ++r) {
+                            vt[r] = poly[r];
+                            vt[3 + r] = poly[3 * i + r];
+                            vt[6 + r] = poly[3 * (i + 1) + r];
+                            src[3 * count + r] = img[r];
+                            usrc[3 * count + r] = u[r];
+                        }
+                        w[count] = -((double)rho[a] * (double)rho[b]);
+                    }
+                    ++count;
+                }
+            }
+        }
+    }
+    return count;
+}
+
+/* Far-field double-bounce PO cross-section (plane waves, the reading above
+ * with the image source at infinity): for unit directions t (toward TX) and
+ * r (toward RX), every ordered pair (a, b), a != b, with a facing t (side
+ * s_a: n_a.t > 0, or < 0 on a two-sided a), t' = t - 2 (t.n_a) n_a / |n_a|^2
+ * the direction toward the image source, b facing t' and r on one side
+ * (both cosines > 0, or both < 0 on a two-sided b), Pi_ab = b clipped by
+ * a's front half-space and the prism of a along t'; each fan sub-triangle T
+ * of Pi_ab adds
+ *   -rho_a rho_b (k / sqrt(pi)) o_b J_T(-k (t' + r)) exp(j k L(c_T)),
+ *   o_b = |n_b.(t' + r)| / 2 (n_b unit),
+ *   L(x) = -(t' + r).x - 2 (t.n_a)(n_a.x0_a) / |n_a|^2,
+ * the path of the reflected plane wave relative to the origin (the image
+ * wave matches the incident one on a's plane).  sigma = |sum|^2.  No
+ * occlusion test (open, convex configurations such as a dihedral). */
+void orc_rcs_farfield_bounce2(const double *tri, int64_t F, const float *rho,
+                              const uint8_t *two_sided, const double *that, const double *rhat,
+                              const double *freqs, int nfreq, double *sigma)
+{
+    for (int fi = 0; fi < nfreq; ++fi) {
+        const double k = 2.0 * ORC_PI * freqs[fi] / ORC_C0;
+        double sr = 0.0, si = 0.0;
+        for (int64_t a = 0; a < F; ++a) {
+            const double *ta = tri + 9 * a;
+            double e1[3], e2[3], na[3], tp[3];
+            sub3(ta + 3, ta, e1);
+            sub3(ta + 6, ta, e2);
+            cross3(e1, e2, na);
+            const double nn = dot3(na, na);
+            if (nn == 0.0) continue;
+            const double ct = dot3(na, that);
+            int side_a;
+            if (ct > 0.0) side_a = 1;
+            else if (two_sided && two_sided[a] && ct < 0.0) side_a = -1;
+            else continue;
+            for (int r = 0; r < 3; ++r) tp[r] = that[r] - (2.0 * ct / nn) * na[r];
+            const double shift = -2.0 * ct * dot3(na, ta) / nn;
+            double g[12], base[12];
+            beam_planes(ta, side_a, NULL, tp, g, base);
+            double bv[3] = {tp[0] + rhat[0], tp[1] + rhat[1], tp[2] + rhat[2]};
+            for (int64_t b = 0; b < F; ++b) {
+                if (b == a) continue;
+                const double *tb = tri + 9 * b;
+                double f1[3], f2[3], nb[3];
+                sub3(tb + 3, tb, f1);
+                sub3(tb + 6, tb, f2);
+                cross3(f1, f2, nb);
+                const double nbl = sqrt(dot3(nb, nb));
+                if (nbl == 0.0) continue;
+                const double c1 = dot3(nb, tp), c2 = dot3(nb, rhat);
+                const int front = c1 > 0.0 && c2 > 0.0;
+                const int rev = two_sided && two_sided[b] && c1 < 0.0 && c2 < 0.0;
+                if (!front && !rev) continue;
+                double poly[3 * ORC_DB_MAXV];
+                const int K = beam_clip(tb, g, base, poly);
+                const double o = fabs(0.5 * dot3(nb, bv) / nbl);
+                const double s = -((double)rho[a] * (double)rho[b]) * (k / sqrt(ORC_PI)) * o;
+                for (int i = 1; i + 1 < K; ++i) {
+                    double sub[9], cT[3], x1[3], x2[3], cr[3];
+                    for (int r = 0; r < 3; ++r) {
+                        sub[r] = poly[r];
+                        sub[3 + r] = poly[3 * i + r];
+                        sub[6 + r] = poly[3 * (i + 1) + r];
+                    }
+                    sub3(sub + 3, sub, x1);
+                    sub3(sub + 6, sub, x2);
+                    cross3(x1, x2, cr);
+                    if (sqrt(dot3(cr, cr)) <= ORC_DB_SLIVER * nbl) continue;
+                    centroid3(sub, cT);
+                    double wv[3] = {-k * bv[0], -k * bv[1], -k * bv[2]};
+                    double jr, ji;
+                    orc_facet_integral(sub, wv, &jr, &ji);
+                    const double ph = k * (-dot3(bv, cT) + shift);
+                    const double pr = cos(ph), pi_ = sin(ph);
+                    sr += s * (jr * pr - ji * pi_);
+                    si += s * (jr * pi_ + ji * pr);
+                }
+            }
+        }
+        sigma[fi] = sr * sr + si * si;
+    }
+}
+
+/* Double-bounce part of selected ADC entries (o, n, m): every virtual facet
+ * v of TX p = o / Q (orc_bounce2_facets) whose facet b is seen from RX
+ * q = o % Q on side s_b scatters as a single-bounce facet of adc_sample
+ * (facet delay form) with
+ *   vertices vtri_v + v_b t_n, transmitter p'(t_n) = src_v + usrc_v t_n,
+ *   reflectivity w_v, obliquity n_v.(t' + r) / 2 (|.| on a two-sided b),
+ *   delay at t_n + t_m: (|c(t) - p'(t)| + |c(t) - p_rx|) / c,
+ *   c(t) = c_v(t_n) + v_b t_m, p'(t) = p'(t_n) + usrc_v t_m
+ * (the motion within the chirp when intra_chirp_motion is set). */
+void orc_adc_bounce2_entries(const int32_t *pab, const double *vtri, const double *src,
+                             const double *usrc, const double *w, int64_t V,
+                             const double *fvel, const uint8_t *two_sided, const uint8_t *state,
+                             int64_t F, const double *tx, const double *rx, const orc_radar *rd,
+                             const int32_t *entries, int64_t E, double *out)
+{
+    (void)tx;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t e = 0; e < E; ++e) {
+        const int o = entries[3 * e], n = entries[3 * e + 1], m = entries[3 * e + 2];
+        const int p = o / rd->Q, q = o % rd->Q;
+        const double tn = (double)(rd->tdm ? (int64_t)n * rd->P + p : n) * rd->Tc;
+        const double tm = (double)m / rd->fs;
+        const double fm = rd->f0 + rd->slope * tm;
+        const double km = 2.0 * ORC_PI * fm / ORC_C0;
+        const double lam = ORC_C0 / fm;
+        const double prx[3] = {rx[3 * q], rx[3 * q + 1], rx[3 * q + 2]};
+        const uint8_t *st_r = state + (int64_t)(rd->P + q) * F;
+        const double amp0 = 1.0 / pow(4.0 * ORC_PI, 1.5);
+        double sr = 0.0, si = 0.0;
+        for (int64_t v = 0; v < V; ++v) {
+            const int32_t *g = pab + 4 * v;
+            if (g[0] != p) continue;
+            const int64_t b = g[2];
+            if (st_r[b] != (g[3] > 0 ? ORC_LIT : ORC_LIT_REV)) continue;
+            const double *vb = fvel + 3 * b;
+            double tri[9], ptx[3];
+            for (int i = 0; i < 9; ++i) tri[i] = vtri[9 * v + i] + vb[i % 3] * tn;
+            for (int r = 0; r < 3; ++r) ptx[r] = src[3 * v + r] + usrc[3 * v + r] * tn;
+            double c[3], e1[3], e2[3], nn[3], dt[3], dr[3];
+            centroid3(tri, c);
+            sub3(tri + 3, tri, e1);
+            sub3(tri + 6, tri, e2);
+            cross3(e1, e2, nn);
+            const double nl = sqrt(dot3(nn, nn));
+            sub3(ptx, c, dt);
+            sub3(prx, c, dr);
+            const double Rt = sqrt(dot3(dt, dt)), Rr = sqrt(dot3(dr, dr));
+            double bb[3];
+            for (int r = 0; r < 3; ++r) bb[r] = dt[r] / Rt + dr[r] / Rr;
+            double ok = 0.5 * dot3(nn, bb) / nl;
+            if (two_sided && two_sided[b]) ok = fabs(ok);
+            double wv[3] = {-km * bb[0], -km * bb[1], -km * bb[2]};
+            double jr, ji;
+            orc_facet_integral(tri, wv, &jr, &ji);
+            const double s = w[v] * (km / sqrt(ORC_PI)) * ok;
+            const double amp = lam * amp0 / (Rt * Rr) * s;
+            double ct[3] = {c[0], c[1], c[2]}, pt[3] = {ptx[0], ptx[1], ptx[2]};
+            if (rd->intra_chirp_motion)
+                for (int r = 0; r < 3; ++r) {
+                    ct[r] = c[r] + vb[r] * tm;
+                    pt[r] = ptx[r] + usrc[3 * v + r] * tm;
+                }
+            const double tau = path_len(ct, pt, prx) / ORC_C0;
+            const double phase = 2.0 * ORC_PI *
+                (rd->f0 * tau + rd->slope * tm * tau - 0.5 * rd->slope * tau * tau);
+            const double cr = cos(phase), ci = sin(phase);
+            sr += amp * (jr * cr - ji * ci);
+            si += amp * (jr * ci + ji * cr);
+        }
+        out[2 * e] = sr;
+        out[2 * e + 1] = si;
+    }
+}

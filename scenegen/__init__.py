@@ -93,6 +93,7 @@ class Radar:
     delay_ref: bool = False        # reference-point delay form (one tau(t) per instance)
     far_field: bool = False        # plane waves from each instance origin, at its ranges
     grazing_eps: float = 1e-6      # |cos| below which a facet grazes its antenna
+    double_bounce: bool = False    # add the two-facet (double-bounce) paths
 
     def __post_init__(self):
         self.tx = np.ascontiguousarray(np.asarray(self.tx, np.float64).reshape(-1, 3))
@@ -209,6 +210,34 @@ def ground(size: float = 100.0, n: int = 158, centre=(0.0, 50.0),
     t2 = np.stack([a, c, d], 1)
     tris = np.stack([t1, t2], 1).reshape(-1, 3).astype(np.int32)
     return Mesh(verts, tris, np.full(len(tris), rho, np.float32), "ground")
+
+
+def dihedral(size: float = 0.1, n: int = 2, rho: float = 1.0) -> Mesh:
+    """Right-angle dihedral corner: two square plates of side ``size`` on the
+    local Z axis (the fold), plate A in the X-Z plane (x in [0, size],
+    normal +Y) and plate B in the Y-Z plane (y in [0, size], normal +X), z in
+    [-size/2, size/2]; each an n x n grid of squares, 2 triangles each.  The
+    opening faces the local direction (1, 1, 0)."""
+    s = (np.arange(n + 1) / n) * size
+    z = (np.arange(n + 1) / n - 0.5) * size
+    verts, tris = [], []
+    for plate_id in range(2):
+        base = len(verts)
+        for i in range(n + 1):
+            for j in range(n + 1):
+                verts.append((s[i], 0.0, z[j]) if plate_id == 0 else (0.0, s[i], z[j]))
+        want = np.array([0.0, 1.0, 0.0]) if plate_id == 0 else np.array([1.0, 0.0, 0.0])
+        idx = lambda i, j: base + i * (n + 1) + j
+        for i in range(n):
+            for j in range(n):
+                for t in ((idx(i, j), idx(i + 1, j), idx(i + 1, j + 1)),
+                          (idx(i, j), idx(i + 1, j + 1), idx(i, j + 1))):
+                    v0, v1, v2 = (np.array(verts[k]) for k in t)
+                    if np.dot(np.cross(v1 - v0, v2 - v0), want) < 0:
+                        t = (t[0], t[2], t[1])
+                    tris.append(t)
+    tris = np.asarray(tris, np.int32)
+    return Mesh(np.asarray(verts), tris, np.full(len(tris), rho, np.float32), "dihedral")
 
 
 def icosphere(radius: float = 0.1, subdiv: int = 5, rho: float = 1.0) -> Mesh:
@@ -473,6 +502,37 @@ def small_car_scene(seed: int = 11, ntri: int = 1500, M: int = 128, N: int = 6,
     2 TX x 2 RX, a few chirps.  Same geometry recipe as ``car_scene``."""
     s = car_scene(seed=seed, ntri=ntri, slant=slant, speed=speed, M=M, N=N, P=P, Q=Q)
     s.name = "small_car"
+    return s
+
+
+def dihedral_scene(range_m: float = 6.0, size: float = 0.1, n: int = 2, alpha_deg: float = 45.0,
+                   M: int = 128, N: int = 4, P: int = 1, Q: int = 2, speed: float = 0.0,
+                   slope: float = 30e12, fs: float = 5.12e6) -> Scene:
+    """A dihedral corner (``dihedral``) on the Y axis at ``range_m`` from a
+    radar at the origin, its fold vertical, turned so that the radar sees
+    plate A at ``alpha_deg`` (45: along the opening's bisector); moving
+    ``speed`` m/s along +Y.  Double-bounce paths on."""
+    radar = make_radar(M, N, P, Q, fs, slope, tx_spacing_wl=2.0, centre=(0.0, 0.0, 0.0))
+    radar.double_bounce = True
+    # the local direction (cos a, sin a, 0) toward the radar: world -Y
+    a = math.radians(alpha_deg)
+    inst = Instance(0, pos=(0.0, range_m, 0.0), rot=rot_z(-math.pi / 2 - a),
+                    vel=(0.0, speed, 0.0))
+    return Scene([dihedral(size, n)], [inst], radar, name="dihedral")
+
+
+def car_ground_scene(seed: int = 11, ntri: int = 1500, ground_size: float = 12.0,
+                     ground_n: int = 6, M: int = 128, N: int = 4, P: int = 2, Q: int = 2,
+                     slant: float = 18.0, speed: float = 12.0) -> Scene:
+    """``small_car_scene``'s sedan on a static ground patch (``ground_size``
+    square, ``ground_n`` x ``ground_n`` squares) centred under it, double-
+    bounce paths on: the car-ground and ground-car multipath of a road."""
+    s = small_car_scene(seed=seed, ntri=ntri, M=M, N=N, P=P, Q=Q, slant=slant, speed=speed)
+    pos = s.instances[0].pos
+    s.meshes.append(ground(ground_size, ground_n, centre=(pos[0], pos[1])))
+    s.instances.append(Instance(1, pos=(0.0, 0.0, 0.0), rot=np.eye(3), vel=(0.0, 0.0, 0.0)))
+    s.radar.double_bounce = True
+    s.name = "car_ground"
     return s
 
 

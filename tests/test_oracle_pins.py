@@ -855,3 +855,229 @@ def test_reference_gradient_rigid_translation_is_the_phase_derivative():
     # linearity in rho: L = sum_f rho_f dL/drho_f
     L = float((np.conj(W) * adc).real.sum())
     assert abs(float(sc.meshes[0].rho.astype(np.float64) @ gr) - L) <= 1e-12 * abs(L) + 1e-30
+
+
+# ---------------------------------------------------------------------------
+# double bounce (Sec. 2.2, forward and backward rays joined through two
+# facets; geometric optics at the first facet, physical optics at the second)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("alpha", [12.0, 20.0, 30.0, 45.0, 60.0])
+def test_double_bounce_dihedral_closed_form(alpha):
+    """A right-angle dihedral of two A x A PEC plates, seen in the plane
+    normal to its fold at angle alpha from plate A: geometric optics lights
+    A tan(alpha) x A of plate B through plate A (and all of plate A through
+    B) and both paths return along the incidence, in phase, so the
+    double-bounce PO cross-section is 16 pi A^4 sin^2(alpha) / lambda^2 for
+    alpha <= 45 deg (cos^2 beyond; 8 pi A^4 / lambda^2 on the bisector,
+    the textbook dihedral value).  The mesh is translated off the origin so
+    that each path's image-wave phase offset matters."""
+    A = 0.1
+    m = sg.dihedral(A, 3)
+    tri = m.verts[m.tris].reshape(-1, 9) + np.tile([0.031, -0.017, 0.052], 3)
+    a = math.radians(alpha)
+    t = np.array([math.cos(a), math.sin(a), 0.0])
+    freqs = np.array([76.0e9, 77.3e9, 80.9e9])
+    sig = oracle.rcs_farfield_bounce2(tri, m.rho, t, t, freqs)
+    lam = C0 / freqs
+    ref = 16.0 * math.pi * A ** 4 * min(math.sin(a), math.cos(a)) ** 2 / lam ** 2
+    np.testing.assert_allclose(sig, ref, rtol=1e-9)
+
+
+def _ground_and_plate(plate_vel=(0.0, -5.0, 0.0), ground_vel=(0.0, 0.0, 0.0), blocker=False,
+                      P=1, Q=2, tdm=False, intra=True, reverse_ground=False):
+    """Two big ground triangles (z = 0, normal +Z; or, ``reverse_ground``,
+    wound the other way and two-sided, so lit on their reverse side), a 0.2 m
+    plate facing the radar 10 m out and 0.5 m up, radar 1.5 m up; optionally
+    a small plate lying across the ground -> plate leg of the double
+    bounce."""
+    tris = [[0, 2, 1], [0, 3, 2]] if reverse_ground else [[0, 1, 2], [0, 2, 3]]
+    g = sg.Mesh(np.array([[-50, -50, 0], [50, -50, 0], [50, 50, 0], [-50, 50, 0]], float),
+                np.array(tris, np.int32), np.ones(2, np.float32), "gnd",
+                two_sided=reverse_ground)
+    radar = sg.make_radar(128, 4, P, Q, 5.12e6, 30e12, tx_spacing_wl=2.0,
+                          centre=(0.0, 0.0, 1.5), intra_chirp_motion=intra, tdm=tdm)
+    radar.double_bounce = True
+    meshes = [g, sg.plate(0.2, 0.2, 1)]
+    insts = [sg.Instance(0, (0, 0, 0), np.eye(3), ground_vel),
+             sg.Instance(1, (0.0, 10.0, 0.5), np.eye(3), plate_vel)]
+    if blocker:
+        # a 0.3 m square at z = 0.05 around y = 7.75, facing down: across the
+        # ray from the specular point (y ~ 7.5) up to the plate
+        meshes.append(sg.plate(0.4, 0.3, 1))
+        rx = np.array([[1, 0, 0], [0, 0, -1], [0, 1, 0]], float)   # local -Y -> world -Z
+        insts.append(sg.Instance(2, (0.0, 7.75, 0.05), rx, (0, 0, 0)))
+    return sg.Scene(meshes, insts, radar)
+
+
+def _entries(radar, step=5):
+    return np.array([(o, n, m) for o in range(radar.O) for n in range(radar.N)
+                     for m in range(0, radar.M, step)], np.int32)
+
+
+@pytest.mark.parametrize("tdm,reverse_ground", [(False, False), (True, False), (False, True)])
+def test_double_bounce_is_the_echo_of_the_image_antenna(tdm, reverse_ground):
+    """Image theory: over a flat conducting ground the path TX -> ground ->
+    plate -> RX is the single-bounce echo of the plate seen from the mirror
+    image of the TX (reflection coefficient -1).  The plate's beam footprint
+    lies inside one ground triangle, so the ground -> plate virtual facets
+    are the plate's own triangles and the identity is exact, with the plate
+    moving (and moving within the chirp)."""
+    sc = _ground_and_plate(P=2 if tdm else 1, tdm=tdm, reverse_ground=reverse_ground)
+    fr = oracle.Frame(sc)
+    expect = oracle.LIT_REV if reverse_ground else oracle.LIT
+    assert (fr.state[:sc.radar.P, :2] == expect).all()
+    b = fr.bounce
+    sel = b["pab"][:, 1] < 2                       # first facet on the ground
+    for p in range(sc.radar.P):
+        assert set(b["pab"][sel & (b["pab"][:, 0] == p), 2]) == {2, 3}
+    assert sel.sum() == 2 * sc.radar.P
+    for p in range(sc.radar.P):
+        tx = sc.radar.tx[p]
+        src = b["src"][sel & (b["pab"][:, 0] == p)]
+        np.testing.assert_allclose(src, np.tile([tx[0], tx[1], -tx[2]], (2, 1)), atol=1e-12)
+    np.testing.assert_array_equal(b["usrc"][sel], 0.0)
+    np.testing.assert_array_equal(b["w"][sel], -1.0)
+    ent = _entries(sc.radar)
+    fr.bounce = {k: v[sel] for k, v in b.items()}
+    lhs = fr.bounce_entries(ent)
+    import copy
+    plate_inst = copy.deepcopy(sc.instances[1])
+    plate_inst.mesh_id = 0
+    for p in range(sc.radar.P):
+        r2 = copy.deepcopy(sc.radar)
+        r2.tx = fr.bounce["src"][fr.bounce["pab"][:, 0] == p][:1].copy()
+        r2.double_bounce = False
+        r2.tdm = False
+        sc2 = sg.Scene([sc.meshes[1]], [plate_inst], r2)
+        rows = ent[:, 0] // sc.radar.Q == p
+        e2 = ent[rows].copy()
+        e2[:, 0] %= sc.radar.Q
+        # the TDM chirp of TX p starts at (n P + p) Tc: shift the plate there
+        if tdm:
+            sc2.t0 = 0.0
+            r2.Tc = sc.radar.Tc
+            rhs = np.empty(e2.shape[0], complex)
+            for n in range(sc.radar.N):
+                r3 = copy.deepcopy(r2)
+                s3 = sg.Scene([sc.meshes[1]], [copy.deepcopy(plate_inst)], r3)
+                s3.instances[0].pos = s3.instances[0].pos + s3.instances[0].vel * (
+                    (n * sc.radar.P + p) * sc.radar.Tc)
+                k = e2[:, 1] == n
+                e3 = e2[k].copy()
+                e3[:, 1] = 0
+                rhs[k] = oracle.Frame(s3).adc_entries(e3)
+        else:
+            rhs = oracle.Frame(sc2).adc_entries(e2)
+        np.testing.assert_allclose(lhs[rows], -rhs, rtol=0, atol=1e-12 * np.abs(rhs).max())
+
+
+def test_double_bounce_moving_mirror_moves_the_image_twice_as_fast():
+    """A ground plane rising at 0.3 m/s mirrors the TX at height h into
+    2 * 0.3 t - h: the image source moves at 0.6 m/s.  With the plate static
+    and motion within the chirp held off, chirp n of the ground -> plate
+    path is the single-bounce echo of the plate from an antenna at that
+    moved image."""
+    sc = _ground_and_plate(plate_vel=(0.0, 0.0, 0.0), ground_vel=(0.0, 0.0, 0.3), intra=False)
+    fr = oracle.Frame(sc)
+    b = fr.bounce
+    sel = b["pab"][:, 1] < 2
+    np.testing.assert_allclose(b["usrc"][sel], np.tile([0.0, 0.0, 0.6], (2, 1)), atol=1e-15)
+    fr.bounce = {k: v[sel] for k, v in b.items()}
+    import copy
+    plate_inst = copy.deepcopy(sc.instances[1])
+    plate_inst.mesh_id = 0
+    tx = sc.radar.tx[0]
+    for n in range(sc.radar.N):
+        tn = n * sc.radar.Tc
+        e = np.array([(o, n, m) for o in range(sc.radar.O) for m in range(0, 128, 9)], np.int32)
+        lhs = fr.bounce_entries(e)
+        r2 = copy.deepcopy(sc.radar)
+        r2.tx = np.array([[tx[0], tx[1], 0.6 * tn - tx[2]]])
+        r2.double_bounce = False
+        e2 = e.copy()
+        e2[:, 1] = 0
+        rhs = oracle.Frame(sg.Scene([sc.meshes[1]], [plate_inst], r2)).adc_entries(e2)
+        np.testing.assert_allclose(lhs, -rhs, rtol=0, atol=1e-11 * np.abs(rhs).max())
+
+
+def test_double_bounce_beams_tile_the_lit_facet():
+    """A ground grid's facets split the plate among their beams: the clipped
+    pieces (all virtual facets with the plate as second facet) cover it
+    exactly once, so their areas add up to the plate's area, and every
+    piece lies in the plate's plane."""
+    sc = _ground_and_plate()
+    sc.meshes[0] = sg.ground(2.0, 16, centre=(0.0, 7.5))      # 0.125 m squares
+    fr = oracle.Frame(sc)
+    b = fr.bounce
+    F0 = sc.meshes[0].nf
+    tri0 = fr.tri0
+    for k in (F0, F0 + 1):                             # the plate's two triangles
+        sel = (b["pab"][:, 2] == k) & (b["pab"][:, 1] < F0)
+        assert len(set(b["pab"][sel, 1])) >= 3          # several ground facets share it
+        v = b["tri"][sel].reshape(-1, 3, 3)
+        area = 0.5 * np.linalg.norm(np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0]), axis=1).sum()
+        t = tri0[k].reshape(3, 3)
+        ref = 0.5 * np.linalg.norm(np.cross(t[1] - t[0], t[2] - t[0]))
+        assert abs(area / ref - 1.0) < 1e-12
+        np.testing.assert_allclose(v[:, :, 1], 10.0, atol=1e-12)
+
+
+def test_double_bounce_leg_between_the_facets_can_be_blocked():
+    """A plate lying across the ray from the ground's specular point up to
+    the lit plate removes exactly that path (the leg's segment test); the
+    single-bounce states of the ground and the plate are unchanged."""
+    free = oracle.Frame(_ground_and_plate())
+    blk = oracle.Frame(_ground_and_plate(blocker=True))
+    np.testing.assert_array_equal(free.state[:, :4], blk.state[:, :4])
+    pf, pb = free.bounce["pab"], blk.bounce["pab"]
+    ground_to_plate = lambda pab: (pab[:, 1] < 2) & (pab[:, 2] >= 2) & (pab[:, 2] < 4)
+    assert ground_to_plate(pf).sum() == 2
+    assert ground_to_plate(pb).sum() == 0
+
+
+def test_double_bounce_no_reflected_light_behind_the_mirror():
+    """Rays from the image source reach the region behind the ground plane
+    before they cross it: a plate there (0.3 m below the ground, facing the
+    image) is inside the cone from the image through a ground facet, but
+    the reflection lights only the ground's front half-space, so it gets no
+    double-bounce path."""
+    sc = _ground_and_plate()
+    sc.meshes.append(sg.plate(0.3, 0.3, 1))
+    rx = np.array([[1, 0, 0], [0, 0, -1], [0, 1, 0]], float)     # faces -Z
+    sc.instances.append(sg.Instance(2, (0.0, 3.0, -0.3), rx, (0, 0, 0)))
+    fr = oracle.Frame(sc)
+    pab = fr.bounce["pab"]
+    assert ((pab[:, 1] < 2) & (pab[:, 2] < 4)).sum() == 2      # ground -> the upper plate
+    assert not np.isin(pab[:, 2], [4, 5]).any()
+
+
+def test_double_bounce_image_moves_within_the_chirp():
+    """With motion within the chirp on, a rising ground (0.3 m/s) moves the
+    image source during the chirp too: for one virtual facet, the sample
+    with motion on differs from the sample with motion off only by the
+    phase of Eq. 13 at the delays computed here from the image position
+    (x, y, 0.6 t - h) of a TX at height h, the plate static."""
+    import copy
+    outs = {}
+    for intra in (False, True):
+        sc = _ground_and_plate(plate_vel=(0.0, 0.0, 0.0), ground_vel=(0.0, 0.0, 0.3),
+                               intra=intra)
+        fr = oracle.Frame(sc)
+        b = fr.bounce
+        sel = np.flatnonzero(b["pab"][:, 1] < 2)[:1]
+        fr.bounce = {k: v[sel] for k, v in b.items()}
+        e = np.array([(1, 3, m) for m in range(0, 128, 3)], np.int32)
+        outs[intra] = fr.bounce_entries(e)
+        tri = b["tri"][sel[0]].reshape(3, 3)
+    r = sc.radar
+    c = tri.mean(axis=0)
+    tx, rxp = r.tx[0], r.rx[1]
+    tn = 3 * r.Tc
+    tm = np.arange(0, 128, 3) / r.fs
+    def phase(t_img):
+        img = np.stack([np.full_like(t_img, tx[0]), np.full_like(t_img, tx[1]),
+                        0.6 * t_img - tx[2]], 1)
+        tau = (np.linalg.norm(c - img, axis=1) + np.linalg.norm(c - rxp)) / C0
+        return 2 * np.pi * (r.f0 * tau + r.slope * tm * tau - 0.5 * r.slope * tau ** 2)
+    expect = np.exp(1j * (phase(tn + tm) - phase(np.full_like(tm, tn))))
+    np.testing.assert_allclose(outs[True] / outs[False], expect, rtol=0, atol=1e-9)
