@@ -130,7 +130,21 @@ typedef struct bart_radar {
                                     - (t + r).(c_k - r(t_n)), and its visibility
                                     segment runs from the centroid toward
                                     p_a + (c_k - r(t0)) */
-    int32_t reserved0;           /* must be 0 */
+    int32_t double_bounce;       /* 0: single bounce only; 1: also the double-bounce
+                                    paths of Sec. 2.2 (forward and backward rays
+                                    joined through two facets), read as geometric
+                                    optics at the first facet a (the field beyond
+                                    it that of TX p mirrored in a's plane, within
+                                    the beam through a) and physical optics on the
+                                    part of the second facet b that the beam
+                                    lights; the a -> b leg must be unoccluded and
+                                    b seen from RX q; reflectivity -rho_a rho_b.
+                                    Decided on the frame-start geometry; always
+                                    FP64; one scene per frame, per-facet delay
+                                    form (not with far_field or delay_ref), no
+                                    adjoint; frames then synchronise the stream
+                                    once and are not replayed as graphs.  See
+                                    bart_get_bounce_facets. */
     double  grazing_eps;         /* facets with |cos| below this toward an antenna
                                     are GRAZE (excluded, counted); 0 = 1e-6 */
 } bart_radar;
@@ -145,6 +159,9 @@ typedef struct bart_stats {
     int64_t n_series;       /* (facet, channel, chirp) records by the series form */
     int64_t n_edge;         /* records by the edge form */
     int64_t n_vertex;       /* records by the vertex form */
+    int64_t n_bounce_facets;   /* double-bounce virtual facets (bart_get_bounce_facets) */
+    int64_t n_bounce_terms;    /* double-bounce echo terms: (virtual facet, channel,
+                                  chirp) records with b seen from the RX, x M */
 } bart_stats;
 
 /* Per-stage device times of the last frame, from CUDA events recorded on
@@ -464,6 +481,20 @@ int bart_frame_host(bart_ctx *ctx, double t0, int32_t path, float *rdm_host,
  * number of (antenna, facet) pairs flagged BART_VIS_GRAZE there (host
  * pointer; synchronises the stream).  Errors: ESTATE (no frame simulated). */
 int bart_get_visibility(bart_ctx *ctx, uint8_t *state, int64_t *n_grazing);
+
+/* The virtual facets of the last frame's double-bounce paths (Sec. 2.2;
+ * bart_radar.double_bounce): each is one fan piece (Pi_0, Pi_i, Pi_i+1) of
+ * the part Pi_ab of facet b lit by TX p's reflection from facet a.  Host
+ * buffers, cap entries each: pab (4 int32: p, a, b, side of b lit: +1 the
+ * front, -1 the reverse of a two-sided facet), tri (9 doubles: frame-start
+ * vertices), src (3: the image source, TX p mirrored in a's plane, at the
+ * frame start), usrc (3: its velocity), w (1: -rho_a rho_b).  Order: TX, then
+ * a in ascending index, then the order of the BVH traversal (deterministic
+ * for a scene).  *n receives the count (all of them; min(cap, n) written).
+ * Synchronises the stream.  BART_ESTATE without a frame; the count is 0 when
+ * the frame had double bounce off. */
+int bart_get_bounce_facets(bart_ctx *ctx, int32_t *pab, double *tri, double *src, double *usrc,
+                           double *w, int64_t cap, int64_t *n);
 
 /* Enable (1) or disable (0) recording of per-stage CUDA events.  The events
  * are recorded on the context's stream; enabling adds no synchronisation. */

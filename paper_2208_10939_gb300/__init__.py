@@ -39,7 +39,7 @@ EXPORTED = ["bart_last_error", "bart_version", "bart_create", "bart_destroy",
             "bart_autotune", "bart_rdm_adjoint", "bart_simulate_adjoint",
             "bart_simulate_adjoint_mixed",
             "bart_mesh_update", "bart_measure_peaks", "bart_inject_alloc_failure",
-            "bart_selftest_wait_timeout"]
+            "bart_selftest_wait_timeout", "bart_get_bounce_facets"]
 
 
 class BartError(RuntimeError):
@@ -63,7 +63,7 @@ class bart_radar(ctypes.Structure):
                 ("tx", (ctypes.c_double * 3) * MAX_TX),
                 ("rx", (ctypes.c_double * 3) * MAX_RX),
                 ("tdm", ctypes.c_int32), ("delay_ref", ctypes.c_int32),
-                ("far_field", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("far_field", ctypes.c_int32), ("double_bounce", ctypes.c_int32),
                 ("grazing_eps", ctypes.c_double)]
 
 
@@ -71,7 +71,8 @@ class bart_stats(ctypes.Structure):
     _fields_ = [("n_facets", ctypes.c_int64), ("n_terms", ctypes.c_int64),
                 ("n_lit_pairs", ctypes.c_int64), ("n_grazing", ctypes.c_int64),
                 ("n_series", ctypes.c_int64), ("n_edge", ctypes.c_int64),
-                ("n_vertex", ctypes.c_int64)]
+                ("n_vertex", ctypes.c_int64), ("n_bounce_facets", ctypes.c_int64),
+                ("n_bounce_terms", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -166,6 +167,7 @@ def load_library() -> ctypes.CDLL:
         L.bart_form_rdm.argtypes = [P, P, I32, P]
         L.bart_frame_host.argtypes = [P, D, I32, P, ctypes.POINTER(bart_stats)]
         L.bart_get_visibility.argtypes = [P, P, ctypes.POINTER(I64)]
+        L.bart_get_bounce_facets.argtypes = [P, P, P, P, P, P, I64, ctypes.POINTER(I64)]
         L.bart_set_timing.argtypes = [P, I32]
         L.bart_get_timing.argtypes = [P, ctypes.POINTER(bart_timing)]
         L.bart_sync.argtypes = [P]
@@ -298,6 +300,7 @@ def make_radar(radar, window: int = WINDOW_HANN) -> bart_radar:
     r.tdm = int(bool(getattr(radar, "tdm", False)))
     r.delay_ref = int(bool(getattr(radar, "delay_ref", False)))
     r.far_field = int(bool(getattr(radar, "far_field", False)))
+    r.double_bounce = int(bool(getattr(radar, "double_bounce", False)))
     r.grazing_eps = float(getattr(radar, "grazing_eps", 0.0) or 0.0)
     for p in range(min(r.P, MAX_TX)):
         for k in range(3):
@@ -458,6 +461,23 @@ def bart_get_visibility(ctx: int, state, grazing: bool = False):
     _check(load_library().bart_get_visibility(ctx, ctypes.c_void_p(_ptr(state)),
                                               ctypes.byref(n) if grazing else None))
     return n.value if grazing else None
+
+
+def bart_get_bounce_facets(ctx: int) -> dict:
+    """The last frame's double-bounce virtual facets (host numpy arrays):
+    ``pab`` (V x 4: TX, first facet, second facet, side), ``tri`` (V x 9),
+    ``src`` (V x 3 image source), ``usrc`` (V x 3 its velocity), ``w`` (V)."""
+    L = load_library()
+    n = ctypes.c_int64(0)
+    _check(L.bart_get_bounce_facets(ctx, None, None, None, None, None, 0, ctypes.byref(n)))
+    V = int(n.value)
+    out = dict(pab=np.zeros((V, 4), np.int32), tri=np.zeros((V, 9)), src=np.zeros((V, 3)),
+               usrc=np.zeros((V, 3)), w=np.zeros(V))
+    if V:
+        _check(L.bart_get_bounce_facets(ctx, *(ctypes.c_void_p(out[k].ctypes.data)
+                                               for k in ("pab", "tri", "src", "usrc", "w")),
+                                        V, ctypes.byref(n)))
+    return out
 
 
 def bart_rdm_adjoint(ctx: int, adc, grad_rdm, grad_adc) -> None:
@@ -638,6 +658,10 @@ class Simulator:
         st = torch.empty((A, self.n_facets), dtype=torch.uint8, device=f"cuda:{self.device}")
         n = bart_get_visibility(self.ctx, st, grazing)
         return (st, n) if grazing else st
+
+    def bounce_facets(self) -> dict:
+        """The last frame's double-bounce virtual facets (bart_get_bounce_facets)."""
+        return bart_get_bounce_facets(self.ctx)
 
     def sync(self) -> None:
         bart_sync(self.ctx)

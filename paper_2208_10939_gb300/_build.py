@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libbartsim.so")
 SOURCES = ["capi.cu", "scene_bvh.cu", "visibility.cu", "synth.cu", "rdm.cu", "noise.cu", "detect.cu",
-           "adjoint.cu", "peaks.cu", "spectral.cu"]
+           "adjoint.cu", "peaks.cu", "spectral.cu", "bounce.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -40,7 +40,7 @@ def _stale(obj: str, src: str) -> bool:
     t = os.path.getmtime(obj)
     deps = [src, os.path.join(INCLUDE, "bartsim.h")] + [
         os.path.join(CSRC, h) for h in ("bart_internal.cuh", "record_fp64.cuh", "mixed_record.cuh",
-                                        "fft_stockham.cuh")]
+                                        "fft_stockham.cuh", "fft_reg.cuh", "geom64.cuh")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

@@ -227,6 +227,36 @@ void launch_adjoint_scatter(const double *gfac, const FacetRec *fac, const InstD
                             const MeshDesc *meshes, const int64_t *voff, int64_t F, double *gverts,
                             int64_t n_vert_words, double *grho, cudaStream_t s);
 
+// ---- double bounce (bounce.cu) ----
+// One virtual facet of a double-bounce path (Sec. 2.2: TX p -> facet a ->
+// facet b -> RX): a fan piece of b's part lit by the reflection from a.
+struct BounceFacet {
+    double tri[9];           // frame-start vertices
+    double src[3];           // image source p'_0 (TX p mirrored in a's plane)
+    double usrc[3];          // its velocity (a's plane moving)
+    double w;                // -rho_a rho_b
+    int32_t p, a, b, side;   // TX, first facet, second facet, side of b lit (+1 / -1)
+};
+static_assert(sizeof(BounceFacet) == 144, "BounceFacet layout");
+// words of the scan scratch for n items (the last one receives the total)
+int64_t bounce_scan_words(int64_t n);
+// pieces per (TX p, i-th facet lit from p) item into cnt (P F), their
+// exclusive scan into off (P F) and the total into blk[bounce_scan_words - 1]
+void launch_bounce_count(const double *tri64, const FacetRec *fac, const double *vel64,
+                         const BvhNode *nodes, const uint8_t *state, const int32_t *vis_idx,
+                         const int32_t *vis_cnt, int64_t F, const RadarDev &rd, int32_t *cnt,
+                         int64_t *off, int64_t *blk, int *status, cudaStream_t s);
+void launch_bounce_fill(const double *tri64, const FacetRec *fac, const double *vel64,
+                        const BvhNode *nodes, const uint8_t *state, const int32_t *vis_idx,
+                        const int32_t *vis_cnt, int64_t F, const RadarDev &rd,
+                        const int64_t *off, BounceFacet *vf, int *status, cudaStream_t s);
+// adds the double-bounce echo of every channel into the cube (records:
+// counter of (virtual facet, channel, chirp) records, or NULL)
+void launch_bounce_synth(const BounceFacet *vf, const int64_t *off, const int64_t *total,
+                         const FacetRec *fac, const double *vel64, const uint8_t *state,
+                         int64_t F, const RadarDev &rd, void *out, int out_c64,
+                         unsigned long long *records, cudaStream_t s);
+
 // ---- additive noise (noise.cu) ----
 int64_t noise_scratch_words();   // doubles
 void launch_add_noise(void *adc, int dtype, int64_t n, double snr_db, uint64_t seed,

@@ -1,0 +1,565 @@
+// Double-bounce paths (Sec. 2.2: the forward ray from a TX and the backward
+// ray from an RX joined through two facets).  The paper names such paths
+// but gives no formula; the reading implemented here is geometric optics at
+// the first facet a and physical optics at the second facet b:
+//
+//  * a is lit from TX p (single-bounce state LIT or LIT_REV, side s_a);
+//    beyond a, the reflected field is that of the image source
+//    p' = p - 2 ((p - x0_a).n_a / |n_a|^2) n_a, confined to the beam of rays
+//    from p' through the triangle a;
+//  * Pi_ab = b clipped by a's front half-space (s_a n_a.(x - x0_a) >= 0) and
+//    the three planes through p' and a's edges (each keeping a's third
+//    vertex) is the part of b that the reflection lights; b must face p'
+//    (cos >= eps_face; <= -eps_face on a two-sided b, side s_b = -1);
+//  * the a -> b leg, from the specular point s (where the line p' -> c_Pi
+//    meets a's plane; c_Pi the mean of Pi's vertices) to c_Pi, must not hit
+//    or graze any facet other than a and b (the Moller-Trumbore test and
+//    margins of the single-bounce visibility);
+//  * Pi_ab is split into the fan (Pi_0, Pi_i, Pi_i+1) without clip slivers
+//    (|cross| <= 1e-6 |n_b|); each piece is a virtual facet that scatters
+//    toward RX q like a single-bounce facet, with the TX replaced by p' and
+//    the reflectivity by -rho_a rho_b, when b is seen from RX q on side s_b;
+//  * pairs, clips and the leg are decided on the frame-start geometry; a
+//    virtual facet then moves with b, and p' with a's plane:
+//    p'(t) = p'_0 + u t, u = 2 (v_a.n_a / |n_a|^2) n_a.
+//
+// Discovery: one thread per (TX, lit facet a) casts a's beam through the
+// LBVH (a box is skipped when it lies outside one of the four half-spaces
+// by more than a rounding margin), clips every candidate b and casts the
+// leg's segment.  Every decision takes one IEEE rounding per operation in a
+// fixed order (geom64.cuh), so the virtual facets are reproducible bit for
+// bit.  A count pass, an exclusive scan and a fill pass write them in
+// (TX, a, traversal) order.  Synthesis: FP64, one warp per (channel, chirp,
+// sample segment), the FP64 path's record forms with the TX leg's own
+// quadratic in fast time; it adds into the cube the single-bounce
+// synthesis wrote.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bart_internal.cuh"
+#include "geom64.cuh"
+#include "record_fp64.cuh"
+
+namespace bart {
+
+namespace {
+
+constexpr int kDbMaxV = 7;          // a triangle clipped by four half-spaces
+constexpr double kDbSliver = 1e-6;  // fan pieces with |cross| <= this |n_b| are dropped
+
+__device__ __forceinline__ void centroid3(const double *t, double *c)
+{
+    for (int r = 0; r < 3; ++r)
+        c[r] = __ddiv_rn(__dadd_rn(__dadd_rn(t[r], t[3 + r]), t[6 + r]), 3.0);
+}
+
+// Sutherland-Hodgman step: the part of the convex polygon with
+// g.(x - base) >= 0
+__device__ int clip_keep(const double *in, int n, const double *g, const double *base,
+                         double *out)
+{
+    int k = 0;
+    for (int i = 0; i < n; ++i) {
+        const double *P = in + 3 * i, *Q = in + 3 * ((i + 1) % n);
+        double d[3];
+        sub3(P, base, d);
+        const double fP = dot3(g, d);
+        sub3(Q, base, d);
+        const double fQ = dot3(g, d);
+        if (fP >= 0.0) {
+            for (int r = 0; r < 3; ++r) out[3 * k + r] = P[r];
+            ++k;
+        }
+        if ((fP >= 0.0) != (fQ >= 0.0)) {
+            const double t = __ddiv_rn(fP, __dsub_rn(fP, fQ));
+            for (int r = 0; r < 3; ++r)
+                out[3 * k + r] = __dadd_rn(P[r], __dmul_rn(t, __dsub_rn(Q[r], P[r])));
+            ++k;
+        }
+    }
+    return k;
+}
+
+// The beam of a from the image source img: a's front half-space and the
+// three planes through img and a's edges, as (g, base) pairs
+__device__ void beam_planes(const double *ta, int side_a, const double *img, double *g,
+                            double *base)
+{
+    double e1[3], e2[3], n[3];
+    sub3(ta + 3, ta, e1);
+    sub3(ta + 6, ta, e2);
+    cross3(e1, e2, n);
+    for (int r = 0; r < 3; ++r) {
+        g[r] = side_a > 0 ? n[r] : -n[r];
+        base[r] = ta[r];
+    }
+    for (int i = 0; i < 3; ++i) {
+        const double *xi = ta + 3 * i, *xj = ta + 3 * ((i + 1) % 3), *xk = ta + 3 * ((i + 2) % 3);
+        double u[3], v[3], m[3], d[3];
+        sub3(xi, img, u);
+        sub3(xj, img, v);
+        cross3(u, v, m);
+        sub3(xk, img, d);
+        const bool flip = dot3(m, d) < 0.0;
+        for (int r = 0; r < 3; ++r) {
+            g[3 * (i + 1) + r] = flip ? -m[r] : m[r];
+            base[3 * (i + 1) + r] = img[r];
+        }
+    }
+}
+
+// whether a node box may hold points of every half-space (conservative: the
+// margin covers the clip's rounding, far below it)
+__device__ __forceinline__ bool box_meets_beam(const float *bmin, const float *bmax,
+                                               const double *g, const double *base)
+{
+    for (int h = 0; h < 4; ++h) {
+        const double *gh = g + 3 * h, *bh = base + 3 * h;
+        double f = 0.0, scale = 1.0, gs = 0.0;
+        for (int r = 0; r < 3; ++r) {
+            const double x = gh[r] >= 0.0 ? (double)bmax[r] : (double)bmin[r];
+            f += gh[r] * (x - bh[r]);
+            gs += fabs(gh[r]);
+            scale = fmax(scale, fmax(fabs(x), fabs(bh[r])));
+        }
+        if (f < -1e-9 * gs * scale) return false;
+    }
+    return true;
+}
+
+struct DbOut {
+    const int64_t *off;      // fill pass: first output slot of each item
+    BounceFacet *vf;         // fill pass: output
+    int32_t *cnt;            // count pass: pieces per item
+};
+
+// one thread per item (p, i): TX p, the i-th facet lit from TX p
+template <bool FILL>
+__global__ void __launch_bounds__(128)
+bounce_discover_kernel(const double *__restrict__ tri64, const FacetRec *__restrict__ fac,
+                       const double *__restrict__ vel64, const BvhNode *__restrict__ nodes,
+                       const uint8_t *__restrict__ state, const int32_t *__restrict__ vis_idx,
+                       const int32_t *__restrict__ vis_cnt, int64_t F, RadarDev rd, DbOut io,
+                       int *status)
+{
+    const int p = blockIdx.y;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= F) return;
+    const int64_t item = (int64_t)p * F + i;
+    if (i >= vis_cnt[rd.O + p] || F < 2) {
+        if (!FILL) io.cnt[item] = 0;
+        return;
+    }
+    const int64_t a = vis_idx[(int64_t)(rd.O + p) * F + i];
+    const double *ta = tri64 + 9 * a;
+    const double pt[3] = {rd.ant[p][0], rd.ant[p][1], rd.ant[p][2]};
+    double e1[3], e2[3], na[3], d[3], img[3], u[3];
+    sub3(ta + 3, ta, e1);
+    sub3(ta + 6, ta, e2);
+    cross3(e1, e2, na);
+    const double nn = dot3(na, na);
+    sub3(pt, ta, d);
+    const double sc = __ddiv_rn(__dmul_rn(2.0, dot3(d, na)), nn);
+    for (int r = 0; r < 3; ++r) img[r] = __dsub_rn(pt[r], __dmul_rn(sc, na[r]));
+    const double *va = vel64 + 3 * fac[a].inst;
+    const double su = __ddiv_rn(__dmul_rn(2.0, dot3(va, na)), nn);
+    for (int r = 0; r < 3; ++r) u[r] = __dmul_rn(su, na[r]);
+    const int side_a = state[(int64_t)p * F + a] == BART_VIS_LIT ? 1 : -1;
+    double g[12], base[12];
+    beam_planes(ta, side_a, img, g, base);
+    const double w_a = (double)fac[a].rho;
+
+    int32_t count = 0;
+    int64_t slot = FILL ? io.off[item] : 0;
+    int stack[kStack];
+    int sp = 0;
+    stack[sp++] = 0;
+    while (sp > 0) {
+        const BvhNode nd = nodes[stack[--sp]];
+        const int ch[2] = {nd.left, nd.right};
+        const bool hh[2] = {box_meets_beam(nd.lmin, nd.lmax, g, base),
+                            box_meets_beam(nd.rmin, nd.rmax, g, base)};
+        for (int c = 0; c < 2; ++c) {
+            if (!hh[c]) continue;
+            if (ch[c] >= 0) {
+                if (sp < kStack) stack[sp++] = ch[c];
+                else atomicOr(status, kStatusStackOverflow);
+                continue;
+            }
+            const int64_t b = ~ch[c];
+            if (b == a) continue;
+            const double *tb = tri64 + 9 * b;
+            double f1[3], f2[3], nb[3], cb[3], D[3];
+            sub3(tb + 3, tb, f1);
+            sub3(tb + 6, tb, f2);
+            cross3(f1, f2, nb);
+            const double nbb = dot3(nb, nb);
+            if (nbb == 0.0) continue;
+            centroid3(tb, cb);
+            sub3(img, cb, D);
+            const double cosang =
+                __ddiv_rn(dot3(nb, D), __dmul_rn(__dsqrt_rn(nbb), __dsqrt_rn(dot3(D, D))));
+            int side_b;
+            if (cosang >= rd.eps_face) side_b = 1;
+            else if (fac[b].two_sided && cosang <= -rd.eps_face) side_b = -1;
+            else continue;
+            double poly[3 * kDbMaxV], buf[3 * kDbMaxV];
+            int K = 3;
+            for (int q = 0; q < 9; ++q) poly[q] = tb[q];
+            for (int h = 0; h < 4 && K >= 3; ++h) {
+                K = clip_keep(poly, K, g + 3 * h, base + 3 * h, buf);
+                for (int q = 0; q < 3 * K; ++q) poly[q] = buf[q];
+            }
+            if (K < 3) continue;
+            const double thr = __dmul_rn(kDbSliver, __dsqrt_rn(nbb));
+            unsigned keep = 0;
+            for (int q = 1; q + 1 < K; ++q) {
+                double x1[3], x2[3], cr[3];
+                sub3(poly + 3 * q, poly, x1);
+                sub3(poly + 3 * (q + 1), poly, x2);
+                cross3(x1, x2, cr);
+                if (__dsqrt_rn(dot3(cr, cr)) > thr) keep |= 1u << q;
+            }
+            if (!keep) continue;
+            // the a -> b leg: specular point on a's plane -> c_Pi
+            double cp[3] = {0.0, 0.0, 0.0}, spt[3], Dl[3], t1[3], t2[3];
+            for (int q = 0; q < K; ++q)
+                for (int r = 0; r < 3; ++r) cp[r] = __dadd_rn(cp[r], poly[3 * q + r]);
+            for (int r = 0; r < 3; ++r) cp[r] = __ddiv_rn(cp[r], (double)K);
+            sub3(ta, img, t1);
+            sub3(cp, img, t2);
+            const double lam = __ddiv_rn(dot3(na, t1), dot3(na, t2));
+            for (int r = 0; r < 3; ++r) spt[r] = __dadd_rn(img[r], __dmul_rn(lam, t2[r]));
+            sub3(cp, spt, Dl);
+            bool blocked = false;
+            {
+                const float o[3] = {(float)spt[0], (float)spt[1], (float)spt[2]};
+                float inv[3];
+                for (int r = 0; r < 3; ++r) {
+                    float dd = (float)Dl[r];
+                    if (fabsf(dd) < 1e-30f) dd = copysignf(1e-30f, dd);
+                    inv[r] = 1.0f / dd;
+                }
+                int st2[kStack];
+                int sp2 = 0;
+                st2[sp2++] = 0;
+                while (sp2 > 0 && !blocked) {
+                    const BvhNode m2 = nodes[st2[--sp2]];
+                    const int c2[2] = {m2.left, m2.right};
+                    const bool h2[2] = {slab_hit(m2.lmin, m2.lmax, o, inv),
+                                        slab_hit(m2.rmin, m2.rmax, o, inv)};
+                    for (int e = 0; e < 2 && !blocked; ++e) {
+                        if (!h2[e]) continue;
+                        if (c2[e] >= 0) {
+                            if (sp2 < kStack) {
+                                st2[sp2++] = c2[e];
+                            } else {
+                                atomicOr(status, kStatusStackOverflow);
+                                blocked = true;
+                            }
+                            continue;
+                        }
+                        const int64_t j = ~c2[e];
+                        if (j == a || j == b) continue;
+                        double tj[9];
+                        for (int q = 0; q < 9; ++q) tj[q] = tri64[9 * j + q];
+                        if (mt_segment(spt, Dl, tj) != 0) blocked = true;
+                    }
+                }
+            }
+            if (blocked) continue;
+            const double w = -__dmul_rn(w_a, (double)fac[b].rho);
+            for (int q = 1; q + 1 < K; ++q) {
+                if (!(keep & (1u << q))) continue;
+                if (FILL) {
+                    BounceFacet &v = io.vf[slot++];
+                    v.p = p;
+                    v.a = (int32_t)a;
+                    v.b = (int32_t)b;
+                    v.side = side_b;
+                    for (int r = 0; r < 3; ++r) {
+                        v.tri[r] = poly[r];
+                        v.tri[3 + r] = poly[3 * q + r];
+                        v.tri[6 + r] = poly[3 * (q + 1) + r];
+                        v.src[r] = img[r];
+                        v.usrc[r] = u[r];
+                    }
+                    v.w = w;
+                }
+                ++count;
+            }
+        }
+    }
+    if (!FILL) io.cnt[item] = count;
+}
+
+// ---- exclusive scan of int32 counts into int64 offsets -------------------
+constexpr int kScanBlk = 1024;
+
+__global__ void scan_blocks_kernel(const int32_t *__restrict__ in, int64_t n,
+                                   int64_t *__restrict__ out, int64_t *__restrict__ blk)
+{
+    __shared__ int64_t s_w[kScanBlk / 32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int64_t k = (int64_t)blockIdx.x * kScanBlk + t;
+    const int64_t v = k < n ? in[k] : 0;
+    int64_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const int64_t wv = s_w[lane];
+        int64_t wx = wv;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, wx, o);
+            if (lane >= o) wx += y;
+        }
+        s_w[lane] = wx - wv;
+        if (lane == 31) blk[blockIdx.x] = wx;
+    }
+    __syncthreads();
+    if (k < n) out[k] = s_w[warp] + x - v;
+}
+
+// one warp: exclusive scan of the block totals; blk[nblk] = the grand total
+__global__ void scan_totals_kernel(int64_t *__restrict__ blk, int64_t nblk)
+{
+    const int lane = threadIdx.x;
+    int64_t run = 0;
+    for (int64_t b0 = 0; b0 < nblk; b0 += 32) {
+        const int64_t b = b0 + lane;
+        const int64_t v = b < nblk ? blk[b] : 0;
+        int64_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (b < nblk) blk[b] = run + x - v;
+        run += __shfl_sync(0xffffffffu, x, 31);
+    }
+    if (lane == 0) blk[nblk] = run;
+}
+
+__global__ void scan_add_kernel(int64_t *__restrict__ out, int64_t n,
+                                const int64_t *__restrict__ blk)
+{
+    const int64_t k = (int64_t)blockIdx.x * kScanBlk + threadIdx.x;
+    if (k < n) out[k] += blk[blockIdx.x];
+}
+
+// ---- synthesis ----------------------------------------------------------
+constexpr int kDbWarps = 4;
+
+struct RecB {
+    double qt[3], qr[3];       // R_t(t)^2 and R_r(t)^2 over the fast time
+    double d[22];              // form coefficients (record_fp64.cuh)
+    int kind, flags;
+};
+
+template <int S>
+__global__ void __launch_bounds__(kDbWarps * 32)
+bounce_synth_kernel(const BounceFacet *__restrict__ vf, const int64_t *__restrict__ off,
+                    const int64_t *__restrict__ total,
+                    const FacetRec *__restrict__ fac, const double *__restrict__ vel64,
+                    const uint8_t *__restrict__ state, int64_t F, RadarDev rd, int W, void *out,
+                    int out_c64, unsigned long long *records)
+{
+    __shared__ RecB sR[kDbWarps][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t gw = (int64_t)blockIdx.x * kDbWarps + warp;
+    const int N = rd.N;
+    if (gw >= (int64_t)rd.O * N * W) return;
+    const int seg = (int)(gw % W);
+    const int64_t unit = gw / W;
+    const int o = (int)(unit / N), n = (int)(unit % N);
+    const int p = o / rd.Q, q = o % rd.Q;
+    const int m0 = (seg * 32 + lane) * S;
+    const double c = kC0, f0 = rd.f0, mu = rd.slope, fs = rd.fs;
+    const double f_max = f0 + mu * (rd.M - 1) / fs;
+    const double k0 = 2.0 * kPi * f0 / c, kmax = 2.0 * kPi * f_max / c;
+    const double tn = (double)((int64_t)n * rd.slots + (rd.tdm ? p : 0)) * rd.Tc;
+    const double *prx = rd.ant[rd.P + q];
+    const uint8_t *st_r = state + (int64_t)(rd.P + q) * F;
+    // the virtual facets of TX p: items p F .. (p + 1) F - 1 of the scan
+    const int64_t v0 = off[(int64_t)p * F];
+    const int64_t v1 = p + 1 < rd.P ? off[(int64_t)(p + 1) * F] : *total;
+
+    double accr[S], acci[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) accr[j] = acci[j] = 0.0;
+    unsigned long long nrec = 0;
+    const double inv_fs = 1.0 / fs, inv_c = 1.0 / c, inv_f0 = 1.0 / f0;
+    const double mu_2c2 = mu / (2.0 * c * c);
+    for (int64_t base = v0; base < v1; base += 32) {
+        const int64_t v = base + lane;
+        bool valid = false;
+        if (v < v1) {
+            const BounceFacet &B = vf[v];
+            valid = st_r[B.b] == (B.side > 0 ? BART_VIS_LIT : BART_VIS_LIT_REV);
+            if (valid) {
+                const double *vb = vel64 + 3 * fac[B.b].inst;
+                double tri[9], c0[3], ptx[3], rec[kRecEntries];
+                for (int r = 0; r < 9; ++r) tri[r] = B.tri[r];
+                centroid3(tri, c0);
+                for (int r = 0; r < 3; ++r) ptx[r] = B.src[r] + B.usrc[r] * tn;
+                int flags = 0;
+                RecB &R = sR[warp][lane];
+                R.kind = build_record<double>(tri, c0, vb, tn, ptx, prx, B.w, rd.intra, k0, kmax,
+                                              kDelayFacet, nullptr, fac[B.b].two_sided, rec,
+                                              &flags);
+                R.flags = flags;
+                R.qt[0] = rec[0];
+                R.qr[0] = rec[3];
+                if (rd.intra) {
+                    // the TX leg runs from the moving image: relative velocity v_b - u
+                    double dt[3], wv[3];
+                    for (int r = 0; r < 3; ++r) {
+                        dt[r] = ptx[r] - (c0[r] + vb[r] * tn);
+                        wv[r] = vb[r] - B.usrc[r];
+                    }
+                    R.qt[1] = -2.0 * (dt[0] * wv[0] + dt[1] * wv[1] + dt[2] * wv[2]);
+                    R.qt[2] = wv[0] * wv[0] + wv[1] * wv[1] + wv[2] * wv[2];
+                    R.qr[1] = rec[4];
+                    R.qr[2] = rec[2];
+                } else {
+                    R.qt[1] = R.qt[2] = R.qr[1] = R.qr[2] = 0.0;
+                }
+                for (int r = 0; r < 22; ++r) R.d[r] = rec[kRecD + r];
+            }
+        }
+        __syncwarp();
+        unsigned int mask = __ballot_sync(0xffffffffu, valid);
+        nrec += __popc(mask);
+        while (mask) {
+            const int i = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const RecB &R = sR[warp][i];
+#pragma unroll 1
+            for (int j = 0; j < S; ++j) {
+                const double t = (double)(m0 + j) * inv_fs;
+                const double fm = f0 + mu * t;
+                const double L = sqrt(R.qt[0] + t * (R.qt[1] + t * R.qt[2])) +
+                                 sqrt(R.qr[0] + t * (R.qr[1] + t * R.qr[2]));
+                const double fmc = fm * inv_c;
+                const double kp = fm * inv_f0;
+                double thc = fmc * L - mu_2c2 * L * L;
+                thc -= rint(thc);
+                double re = 0.0, im = 0.0;
+                if (R.kind == kRecVertex) {
+                    for (int e = 0; e < 3; ++e) {
+                        double s_, c_;
+                        sincospi(2.0 * (thc - fmc * R.d[e]), &s_, &c_);
+                        re += R.d[3 + e] * c_;
+                        im += R.d[3 + e] * s_;
+                    }
+                } else if (R.kind == kRecSeries) {
+                    double s_, c_;
+                    sincospi(2.0 * (thc - fmc * R.d[0]), &s_, &c_);
+                    const double k2 = kp * kp;
+                    double aa = R.d[8], bb = R.d[15];
+                    for (int e = 6; e >= 0; --e) aa = aa * k2 + R.d[1 + e];
+                    for (int e = 5; e >= 0; --e) bb = bb * k2 + R.d[9 + e];
+                    const double pr_ = aa * k2, pi_ = bb * k2 * kp;
+                    re = c_ * pr_ - s_ * pi_;
+                    im = c_ * pi_ + s_ * pr_;
+                } else {
+                    for (int e = 0; e < 3; ++e) {
+                        double s_, c_;
+                        sincospi(2.0 * (thc - fmc * R.d[3 * e]), &s_, &c_);
+                        const double x = kp * R.d[3 * e + 1];
+                        double sn;
+                        if (R.flags & (1 << e)) {
+                            const double x2 = x * x;
+                            sn = 1.0 + x2 * (-1.0 / 6 + x2 * (1.0 / 120 + x2 * (-1.0 / 5040 +
+                                 x2 * (1.0 / 362880 + x2 * (-1.0 / 39916800)))));
+                        } else {
+                            sn = sin(x) / x;
+                        }
+                        const double coef = kp * R.d[3 * e + 2] * sn;
+                        re -= coef * s_;
+                        im += coef * c_;
+                    }
+                }
+                accr[j] += re;
+                acci[j] += im;
+            }
+        }
+        __syncwarp();
+    }
+    if (lane == 0 && seg == 0 && records) atomicAdd(records, nrec);
+    const double camp = 2.0 * sqrt(kPi) / pow(4.0 * kPi, 1.5);
+    const int64_t row = ((int64_t)o * N + n) * rd.M + m0;
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+        const double fm = f0 + mu * (double)(m0 + j) / fs;
+        const double km = 2.0 * kPi * fm / c;
+        const double sc = camp / (km * km);
+        if (out_c64) {
+            float2 &y = reinterpret_cast<float2 *>(out)[row + j];
+            y.x += (float)(accr[j] * sc);
+            y.y += (float)(acci[j] * sc);
+        } else {
+            double2 &y = reinterpret_cast<double2 *>(out)[row + j];
+            y.x += accr[j] * sc;
+            y.y += acci[j] * sc;
+        }
+    }
+}
+
+}  // namespace
+
+int64_t bounce_scan_words(int64_t n) { return (n + kScanBlk - 1) / kScanBlk + 1; }
+
+void launch_bounce_count(const double *tri64, const FacetRec *fac, const double *vel64,
+                         const BvhNode *nodes, const uint8_t *state, const int32_t *vis_idx,
+                         const int32_t *vis_cnt, int64_t F, const RadarDev &rd, int32_t *cnt,
+                         int64_t *off, int64_t *blk, int *status, cudaStream_t s)
+{
+    const int T = 128;
+    DbOut io{nullptr, nullptr, cnt};
+    dim3 grid((unsigned int)((F + T - 1) / T), (unsigned int)rd.P);
+    bounce_discover_kernel<false><<<grid, T, 0, s>>>(tri64, fac, vel64, nodes, state, vis_idx,
+                                                     vis_cnt, F, rd, io, status);
+    const int64_t n = (int64_t)rd.P * F;
+    const int64_t nblk = (n + kScanBlk - 1) / kScanBlk;
+    scan_blocks_kernel<<<(unsigned int)nblk, kScanBlk, 0, s>>>(cnt, n, off, blk);
+    scan_totals_kernel<<<1, 32, 0, s>>>(blk, nblk);
+    scan_add_kernel<<<(unsigned int)nblk, kScanBlk, 0, s>>>(off, n, blk);
+}
+
+void launch_bounce_fill(const double *tri64, const FacetRec *fac, const double *vel64,
+                        const BvhNode *nodes, const uint8_t *state, const int32_t *vis_idx,
+                        const int32_t *vis_cnt, int64_t F, const RadarDev &rd,
+                        const int64_t *off, BounceFacet *vf, int *status, cudaStream_t s)
+{
+    const int T = 128;
+    DbOut io{off, vf, nullptr};
+    dim3 grid((unsigned int)((F + T - 1) / T), (unsigned int)rd.P);
+    bounce_discover_kernel<true><<<grid, T, 0, s>>>(tri64, fac, vel64, nodes, state, vis_idx,
+                                                    vis_cnt, F, rd, io, status);
+}
+
+void launch_bounce_synth(const BounceFacet *vf, const int64_t *off, const int64_t *total,
+                         const FacetRec *fac,
+                         const double *vel64, const uint8_t *state, int64_t F,
+                         const RadarDev &rd, void *out, int out_c64, unsigned long long *records,
+                         cudaStream_t s)
+{
+    const int M = rd.M;                // a multiple of 32
+    int S = 8;                         // samples per lane: the largest of 8, 4, 2, 1 dividing M / 32
+    while ((M / 32) % S) S /= 2;
+    const int W = M / (32 * S);
+    const int64_t warps = (int64_t)rd.O * rd.N * W;
+    const unsigned int grid = (unsigned int)((warps + kDbWarps - 1) / kDbWarps);
+    switch (S) {
+    case 8: bounce_synth_kernel<8><<<grid, kDbWarps * 32, 0, s>>>(vf, off, total, fac, vel64, state, F, rd, W, out, out_c64, records); break;
+    case 4: bounce_synth_kernel<4><<<grid, kDbWarps * 32, 0, s>>>(vf, off, total, fac, vel64, state, F, rd, W, out, out_c64, records); break;
+    case 2: bounce_synth_kernel<2><<<grid, kDbWarps * 32, 0, s>>>(vf, off, total, fac, vel64, state, F, rd, W, out, out_c64, records); break;
+    default: bounce_synth_kernel<1><<<grid, kDbWarps * 32, 0, s>>>(vf, off, total, fac, vel64, state, F, rd, W, out, out_c64, records); break;
+    }
+}
+
+}  // namespace bart

@@ -173,6 +173,12 @@ struct bart_ctx {
     DevBuf<int64_t> d_foff;             // facet offsets of the scenes [B + 1]
     DevBuf<int32_t> d_root;             // BVH root of each scene [B]
     DevBuf<int32_t> vstart, vcnt;       // per (scene, channel) list ranges [B O]
+    // double bounce: pieces per (TX, lit facet) item, their offsets, the scan
+    // scratch (its last word the total) and the virtual facets of the frame
+    DevBuf<int32_t> db_cnt;
+    DevBuf<int64_t> db_off, db_blk;
+    DevBuf<BounceFacet> db_vf;
+    int64_t db_n = 0;
     DevBuf<uint32_t> mkeys, skeys;      // batched sort scratch
     int tpi_override = 0;               // synthesis tiles per item (autotuner), 0 = default
     int layout_S = 0;                   // synthesis samples per lane request, 0 = default
@@ -247,6 +253,7 @@ struct bart_ctx {
         fg.release();
         det_ws.release(); adj_ws.release(); gfac.release(); d_voff.release(); d_foff.release(); d_root.release(); vstart.release();
         vcnt.release(); mkeys.release(); skeys.release();
+        db_cnt.release(); db_off.release(); db_blk.release(); db_vf.release();
         if (count_host) cudaFreeHost(count_host);
     }
 };
@@ -356,7 +363,7 @@ int bart_create(bart_ctx **out, int device)
     bart_ctx *c = new (std::nothrow) bart_ctx();
     if (!c) return fail(BART_ENOMEM, "bart_create: host allocation failed");
     c->device = device;
-    int rc = c->counters.ensure(4, "counters");
+    int rc = c->counters.ensure(5, "counters");
     if (rc == BART_OK) rc = c->status.ensure(1, "status");
     if (rc == BART_OK) rc = c->bounds.ensure(6, "bounds");
     if (rc != BART_OK) {
@@ -539,7 +546,11 @@ int bart_radar_set(bart_ctx *ctx, const bart_radar *r)
                     r->tdm, r->delay_ref, r->far_field);
     if (r->far_field && r->delay_ref)
         return fail(BART_EINVAL, "bart_radar_set: far_field and delay_ref are exclusive");
-    if (r->reserved0 != 0) return fail(BART_EINVAL, "bart_radar_set: reserved0 must be 0");
+    if (r->double_bounce != 0 && r->double_bounce != 1)
+        return fail(BART_EINVAL, "bart_radar_set: double_bounce=%d (0 or 1)", r->double_bounce);
+    if (r->double_bounce && (r->far_field || r->delay_ref))
+        return fail(BART_EINVAL, "bart_radar_set: double_bounce takes the per-facet delay form "
+                    "(far_field and delay_ref off)");
     if (!(r->grazing_eps == 0.0 || (r->grazing_eps > 0.0 && r->grazing_eps <= 0.1)))
         return fail(BART_EINVAL, "bart_radar_set: grazing_eps=%g (0 or in (0, 0.1])",
                     r->grazing_eps);
@@ -647,6 +658,15 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
         CUDA_TRY(cudaMemcpyAsync(ctx->d_voff.p, voff.data(), I * sizeof(int64_t),
                                  cudaMemcpyHostToDevice, s), "vertex offset copy");
     }
+    const bool bounce = ctx->radar.double_bounce != 0;
+    if (bounce && (B > 1 || path == kPathAdjoint || path == kPathAdjointMixed))
+        return fail(BART_EINVAL, "double_bounce: one scene per frame and no adjoint");
+    if (bounce) {
+        const int64_t items = (int64_t)rd.P * F;
+        BART_TRY(ctx->db_cnt.ensure((size_t)items, "double-bounce counts"));
+        BART_TRY(ctx->db_off.ensure((size_t)items, "double-bounce offsets"));
+        BART_TRY(ctx->db_blk.ensure((size_t)bounce_scan_words(items), "double-bounce scan"));
+    }
     if (B > 1) {
         BART_TRY(ctx->d_foff.ensure(B + 1, "scene facet offsets"));
         BART_TRY(ctx->d_root.ensure(B, "scene roots"));
@@ -730,7 +750,7 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
     // kinematics rows on a second stream, forked after the world facets and
     // joined before the synthesis): run directly, or recorded into a frame graph
     auto enqueue = [&](double t0v, bool tm, cudaStream_t s) -> int {
-        CUDA_TRY(cudaMemsetAsync(ctx->counters.p, 0, 4 * sizeof(unsigned long long), s), "memset");
+        CUDA_TRY(cudaMemsetAsync(ctx->counters.p, 0, 5 * sizeof(unsigned long long), s), "memset");
         if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[0], s), "cudaEventRecord");
         int launches = 0;
 
@@ -791,6 +811,32 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
             launch_scene_lists(ctx->vis_idx.p, ctx->vis_cnt.p, F, O, ctx->d_foff.p, B, ctx->vstart.p,
                                ctx->vcnt.p, s);
             launches += 1;
+        }
+        // 3b. double-bounce virtual facets: count, scan, read the total
+        // (a host synchronisation: frame graphs are off with double bounce),
+        // allocate, fill
+        if (bounce) {
+            nv.next("bart double bounce");
+            const int64_t items = (int64_t)rd.P * F;
+            const int64_t tw = bounce_scan_words(items);
+            launch_bounce_count(ctx->tri64.p, ctx->fac.p, ctx->vel64.p, ctx->nodes.p,
+                                ctx->state.p, ctx->vis_idx.p, ctx->vis_cnt.p, F, rd,
+                                ctx->db_cnt.p, ctx->db_off.p, ctx->db_blk.p, ctx->status.p, s);
+            int64_t total = 0;
+            CUDA_TRY(cudaMemcpyAsync(&total, ctx->db_blk.p + tw - 1, sizeof total,
+                                     cudaMemcpyDeviceToHost, s), "double-bounce count copy");
+            CUDA_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+            ctx->db_n = total;
+            launches += 4;
+            if (total > 0) {
+                BART_TRY(ctx->db_vf.ensure((size_t)total, "double-bounce virtual facets"));
+                launch_bounce_fill(ctx->tri64.p, ctx->fac.p, ctx->vel64.p, ctx->nodes.p,
+                                   ctx->state.p, ctx->vis_idx.p, ctx->vis_cnt.p, F, rd,
+                                   ctx->db_off.p, ctx->db_vf.p, ctx->status.p, s);
+                launches += 1;
+            }
+        } else {
+            ctx->db_n = 0;
         }
         if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[3], s), "cudaEventRecord");
         // 4. synthesis
@@ -873,6 +919,15 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
             ctx->chunks = 1;
             launches += fp64_chunks > 1 ? 2 : 1;
         }
+        // 5. the double-bounce echo, added into the cube (FP64 on every path)
+        if (bounce && ctx->db_n > 0) {
+            nv.next("bart double-bounce synthesis");
+            launch_bounce_synth(ctx->db_vf.p, ctx->db_off.p,
+                                ctx->db_blk.p + bounce_scan_words((int64_t)rd.P * F) - 1,
+                                ctx->fac.p, ctx->vel64.p, ctx->state.p, F, rd, adc,
+                                dtype == BART_C64, ctx->counters.p + 4, s);
+            launches += 1;
+        }
         if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[4], s), "cudaEventRecord");
         ctx->path = path;
         ctx->frame_launches = launches;
@@ -883,7 +938,7 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
     };
 
     const bool use_graph = ctx->graph && !stats && !ctx->timing && path != kPathAdjoint &&
-                           path != kPathAdjointMixed;
+                           path != kPathAdjointMixed && !bounce;
     if (use_graph) {
         bart_ctx::FrameGraph &g = ctx->fg;
         const bool hit = g.exec && g.version == ctx->version && g.path == path &&
@@ -966,7 +1021,7 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
     ctx->frame_A = A;
     if (stats) {
         std::vector<int32_t> cnt(O);
-        unsigned long long ctr[4];
+        unsigned long long ctr[5];
         CUDA_TRY(cudaMemcpyAsync(cnt.data(), ctx->vis_cnt.p, O * sizeof(int32_t),
                                  cudaMemcpyDeviceToHost, s), "stats copy");
         CUDA_TRY(cudaMemcpyAsync(ctr, ctx->counters.p, sizeof ctr, cudaMemcpyDeviceToHost, s),
@@ -981,6 +1036,8 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
         stats->n_series = (int64_t)ctr[1];
         stats->n_edge = (int64_t)ctr[2];
         stats->n_grazing = (int64_t)ctr[3];
+        stats->n_bounce_facets = ctx->db_n;
+        stats->n_bounce_terms = (int64_t)ctr[4] * rd.M;
     }
     return BART_OK;
 }
@@ -1356,6 +1413,39 @@ int bart_get_visibility(bart_ctx *ctx, uint8_t *state, int64_t *n_grazing)
                                  ctx->stream), "grazing count copy");
         CUDA_TRY(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
         *n_grazing = (int64_t)g;
+    }
+    return BART_OK;
+}
+
+int bart_get_bounce_facets(bart_ctx *ctx, int32_t *pab, double *tri, double *src, double *usrc,
+                           double *w, int64_t cap, int64_t *n)
+{
+    g_err.clear();
+    if (!ctx || !n) return fail(BART_EINVAL, "bart_get_bounce_facets: NULL argument");
+    if (!ctx->have_frame) return fail(BART_ESTATE, "bart_get_bounce_facets: no frame simulated");
+    if (cap < 0) return fail(BART_EINVAL, "bart_get_bounce_facets: cap=%lld", (long long)cap);
+    *n = ctx->db_n;
+    const int64_t k = std::min(cap, ctx->db_n);
+    if (k == 0) return BART_OK;
+    if (!pab || !tri || !src || !usrc || !w)
+        return fail(BART_EINVAL, "bart_get_bounce_facets: NULL output with cap > 0");
+    BART_TRY(set_device(ctx));
+    std::vector<BounceFacet> h((size_t)k);
+    CUDA_TRY(cudaMemcpyAsync(h.data(), ctx->db_vf.p, (size_t)k * sizeof(BounceFacet),
+                             cudaMemcpyDeviceToHost, ctx->stream), "virtual facet copy");
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
+    for (int64_t i = 0; i < k; ++i) {
+        const BounceFacet &v = h[(size_t)i];
+        pab[4 * i] = v.p;
+        pab[4 * i + 1] = v.a;
+        pab[4 * i + 2] = v.b;
+        pab[4 * i + 3] = v.side;
+        for (int r = 0; r < 9; ++r) tri[9 * i + r] = v.tri[r];
+        for (int r = 0; r < 3; ++r) {
+            src[3 * i + r] = v.src[r];
+            usrc[3 * i + r] = v.usrc[r];
+        }
+        w[i] = v.w;
     }
     return BART_OK;
 }

@@ -17,53 +17,9 @@
 #include <stdint.h>
 
 #include "bart_internal.cuh"
+#include "geom64.cuh"
 
 namespace bart {
-
-__device__ __forceinline__ void sub3(const double *a, const double *b, double *o)
-{
-    o[0] = __dsub_rn(a[0], b[0]);
-    o[1] = __dsub_rn(a[1], b[1]);
-    o[2] = __dsub_rn(a[2], b[2]);
-}
-__device__ __forceinline__ double dot3(const double *a, const double *b)
-{
-    double s = __dmul_rn(a[0], b[0]);
-    s = __dadd_rn(s, __dmul_rn(a[1], b[1]));
-    s = __dadd_rn(s, __dmul_rn(a[2], b[2]));
-    return s;
-}
-__device__ __forceinline__ void cross3(const double *a, const double *b, double *o)
-{
-    o[0] = __dsub_rn(__dmul_rn(a[1], b[2]), __dmul_rn(a[2], b[1]));
-    o[1] = __dsub_rn(__dmul_rn(a[2], b[0]), __dmul_rn(a[0], b[2]));
-    o[2] = __dsub_rn(__dmul_rn(a[0], b[1]), __dmul_rn(a[1], b[0]));
-}
-
-// 2 = hit with margin, 1 = grazing (inside the margins), 0 = miss
-__device__ int mt_segment(const double *O, const double *D, const double *tri)
-{
-    double e1[3], e2[3], P[3], T[3], Qv[3];
-    sub3(tri + 3, tri, e1);
-    sub3(tri + 6, tri, e2);
-    cross3(D, e2, P);
-    const double det = dot3(e1, P);
-    if (det == 0.0) return 0;
-    const double inv = __ddiv_rn(1.0, det);
-    sub3(O, tri, T);
-    const double u = __dmul_rn(dot3(T, P), inv);
-    if (u < -kEpsB || u > __dadd_rn(1.0, kEpsB)) return 0;
-    cross3(T, e1, Qv);
-    const double v = __dmul_rn(dot3(D, Qv), inv);
-    const double uv = __dadd_rn(u, v);
-    if (v < -kEpsB || uv > __dadd_rn(1.0, kEpsB)) return 0;
-    const double t = __dmul_rn(dot3(e2, Qv), inv);
-    if (t < -kEpsT || t > __dadd_rn(1.0, kEpsT)) return 0;
-    if (u >= kEpsB && v >= kEpsB && uv <= __dsub_rn(1.0, kEpsB) && t >= kEpsT &&
-        t <= __dsub_rn(1.0, kEpsT))
-        return 2;
-    return 1;
-}
 
 // FP32 pre-test of the FP64 test above: 0 when it certainly returns 0 (a
 // miss), 2 when it certainly returns 2 (a hit inside every margin), 1 when
@@ -132,21 +88,6 @@ __device__ __forceinline__ int mt_fp32_classify(const float4 t0, const float4 t1
     return inside ? 2 : 1;
 }
 
-__device__ __forceinline__ bool slab_hit(const float *bmin, const float *bmax, const float *o,
-                                         const float *inv)
-{
-    float tn = -1e-3f, tf = 1.0f + 1e-3f;
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-        const float t0 = (bmin[r] - o[r]) * inv[r];
-        const float t1 = (bmax[r] - o[r]) * inv[r];
-        tn = fmaxf(tn, fminf(t0, t1));
-        tf = fminf(tf, fmaxf(t0, t1));
-    }
-    return tn <= tf;
-}
-
-constexpr int kStack = 64;
 
 __global__ void __launch_bounds__(128)
 visibility_kernel(const double *__restrict__ tri64, const float4 *__restrict__ tri32,
