@@ -45,6 +45,8 @@ UNIT = "terms/s"
 WORKLOAD = ("intersection: 12 vehicles (20k-200k tris) + 50k-tri ground, 12TXx16RX (192 ch), "
             "256 chirps x 512 samples")
 SEDAN = "moving sedan 20k tris, 3TXx4RX (12 ch), 128 chirps x 256 samples"
+BOUNCE = ("moving sedan 20k tris on a 20 m x 20 m static ground (0.5 m cells, 3200 tris), "
+          "3TXx4RX (12 ch), 128 chirps x 256 samples, single + double bounce")
 # algorithmic work of one echo term in the mixed path: 3 vertex phases, 3 unit
 # phasors, 3 real x complex weighted accumulates and their compensation, about
 # 24 FP32 FMA-pipe operations (plus 6 SFU operations when the phasors come from
@@ -129,6 +131,8 @@ def parse():
     ap.add_argument("--workload", default="intersection", choices=["intersection", "sedan"],
                     help="headline frame (the sedan for quick profiling runs)")
     ap.add_argument("--no-sedan", action="store_true", help="skip the moving-sedan lines")
+    ap.add_argument("--bounce-steps", type=int, default=5,
+                    help="timed frames of the sedan-on-ground double-bounce line (0 skips)")
     ap.add_argument("--no-peaks", action="store_true",
                     help="skip the peak microbenchmarks (roofline against no measured peak)")
     ap.add_argument("--chirps", type=int, default=0,
@@ -137,11 +141,12 @@ def parse():
                     help="profiling aid: headline frame with the first P TX and Q RX")
     ap.add_argument("--no-flush", action="store_true",
                     help="profiling aid: no L2 flush between steps (per-kernel DRAM counters)")
-    ap.add_argument("--probe", default=None, choices=["rdm", "adjoint"],
+    ap.add_argument("--probe", default=None, choices=["rdm", "adjoint", "bounce"],
                     help="run one stage alone for a profiler capture and print its time: "
                          "the RDM of a seeded 192 x 256 x 512 complex64 cube with the "
-                         "intersection radar, or the mixed adjoint of the sedan for a "
-                         "seeded dL/d(adc)")
+                         "intersection radar, the mixed adjoint of the sedan for a "
+                         "seeded dL/d(adc), or a mixed-path frame of the sedan on a ground "
+                         "patch with double bounce")
     ap.add_argument("--log", default=os.environ.get("BART_RUN_LOG"),
                     help="append the run's record (JSON line plus seeds, clocks, oracle errors, "
                          "grazing counts) to this JSONL file")
@@ -696,6 +701,59 @@ def sedan_lines(pkg, sg, torch, dev, args, peaks) -> dict:
         sim.close()
 
 
+def double_bounce_lines(pkg, sg, torch, dev, args, peaks) -> dict:
+    """The sedan on a ground patch with the double-bounce paths (Sec. 2.2,
+    two facets): mixed-path frames (simulate + RDM) with and without double
+    bounce, the discovery and FP64 synthesis stage times, the virtual facets
+    and the double-bounce echo terms."""
+    scene = sg.sedan_ground_scene()
+    sim = pkg.Simulator(dev.index or 0)
+    try:
+        r = scene.radar
+        adc = torch.empty((r.O, r.N, r.M), dtype=torch.complex64, device=dev)
+        rdm = torch.empty((r.M, r.N), dtype=torch.float32, device=dev)
+        flush = (None if args.no_flush else
+                 torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev))
+        stream = torch.cuda.current_stream(dev)
+        out = {"workload": BOUNCE}
+        for on in (False, True):
+            scene.radar.double_bounce = on
+            sim.load_scene(scene)
+            pkg.bart_set_timing(sim.ctx, True)
+            _, st = sim.simulate(pkg.PATH_MIXED, out=adc, stats=True)
+            for _ in range(3):
+                sim.simulate(pkg.PATH_MIXED, out=adc)
+                sim.rdm(adc, rdm)
+            sim.sync()
+            tf = timed_frames(pkg, torch, sim, adc, rdm, flush, stream, args.bounce_steps,
+                              pkg.PATH_MIXED)
+            key = "with_double_bounce" if on else "single_bounce_only"
+            out[key] = {"ms_per_step": statistics.mean(tf["step_ms"]),
+                        "frames_per_s": 1e3 / statistics.mean(tf["step_ms"]),
+                        "echo_terms_single_bounce": st["n_terms"]}
+            if on:
+                dsc, syn = [], []
+                for _ in range(args.bounce_steps):
+                    sim.simulate(pkg.PATH_MIXED, out=adc)
+                    tm = pkg.bart_get_timing(sim.ctx)
+                    dsc.append(tm["bounce_discovery_ms"])
+                    syn.append(tm["bounce_synthesis_ms"])
+                bt = st["n_bounce_terms"]
+                out.update({
+                    "facets": st["n_facets"], "virtual_facets": st["n_bounce_facets"],
+                    "double_bounce_terms_per_frame": bt,
+                    "discovery_ms": statistics.median(dsc),
+                    "bounce_synthesis_ms": statistics.median(syn),
+                    "bounce_synthesis_terms_per_s": bt / (statistics.median(syn) / 1e3),
+                    "gpu_launches": tf["launches"]})
+                if peaks:
+                    out["fp64_fma_tops_measured"] = peaks["fp64_fma_tops"]
+        scene.radar.double_bounce = True
+        return out
+    finally:
+        sim.close()
+
+
 def run_probe(args) -> None:
     """One stage alone (for ncu captures of a representative launch): warm-up
     launches, then ``--steps`` timed ones (CUDA events); prints one JSON
@@ -717,6 +775,12 @@ def run_probe(args) -> None:
             out = torch.empty((M, N), dtype=torch.float32, device=dev)
             run = lambda: pkg.bart_form_rdm(sim.ctx, x, out)
             what = f"RDM of a {O}x{N}x{M} complex64 cube"
+        elif args.probe == "bounce":
+            sc = sg.sedan_ground_scene()
+            sim.load_scene(sc)
+            x = torch.empty(sim.adc_shape(), dtype=torch.complex64, device=dev)
+            run = lambda: sim.simulate(pkg.PATH_MIXED, out=x)
+            what = "mixed-path frame of the sedan on a ground patch, double bounce on"
         else:
             sc = sg.car_scene()
             sim.load_scene(sc)
@@ -902,6 +966,9 @@ def main():
     sedan = None
     if world == 1 and not args.no_sedan and args.workload == "intersection":
         sedan = sedan_lines(pkg, sg, torch, dev, args, peaks)
+    bounce = None
+    if world == 1 and args.bounce_steps > 0:
+        bounce = double_bounce_lines(pkg, sg, torch, dev, args, peaks)
     adj = None
     if world == 1 and args.adjoint_reps > 0:
         adj = adjoint_timing(pkg, sg, torch, dev, args.adjoint_reps)
@@ -939,6 +1006,7 @@ def main():
         "peaks": peaks,
         "grazing_pairs": st["n_grazing"],
         "moving_sedan": sedan,
+        "double_bounce": bounce,
         "differentiable_echo": adj,
         "dataset": batch,
         "dataset_batch_small": batch_small,

@@ -179,6 +179,12 @@ typedef struct bart_timing {
     int32_t launches;        /* kernels launched by the last simulate + form_rdm */
     float   detect_ms;       /* last bart_detect (RDM, CFAR, angle, points) */
     int32_t detect_launches; /* kernels launched by the last bart_detect */
+    float   bounce_discovery_ms;  /* double bounce: virtual-facet count, scan and
+                                     fill, with the host read of the count (inside
+                                     visibility_ms); 0 without double bounce */
+    float   bounce_synthesis_ms;  /* double bounce: the FP64 synthesis of the virtual
+                                     facets (inside synthesis_ms on the FP64 and
+                                     spectral paths, after it on the mixed path) */
 } bart_timing;
 
 /* Text of the calling thread's last error ("" if none).  Valid until the

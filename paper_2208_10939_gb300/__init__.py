@@ -83,7 +83,8 @@ class bart_timing(ctypes.Structure):
                 ("visibility_ms", ctypes.c_float), ("kinematics_ms", ctypes.c_float),
                 ("synthesis_ms", ctypes.c_float), ("rdm_ms", ctypes.c_float),
                 ("synthesis_launches", ctypes.c_int32), ("launches", ctypes.c_int32),
-                ("detect_ms", ctypes.c_float), ("detect_launches", ctypes.c_int32)]
+                ("detect_ms", ctypes.c_float), ("detect_launches", ctypes.c_int32),
+                ("bounce_discovery_ms", ctypes.c_float), ("bounce_synthesis_ms", ctypes.c_float)]
 
     def as_dict(self) -> dict:
         return {f: (float(getattr(self, f)) if t is ctypes.c_float else int(getattr(self, f)))

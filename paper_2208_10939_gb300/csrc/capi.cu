@@ -212,6 +212,8 @@ struct bart_ctx {
                                         // 7/8 detect
     std::vector<cudaEvent_t> ev_kin;    // before / after the kinematics rows
     std::vector<cudaEvent_t> ev_syn;    // before / after the synthesis
+    std::vector<cudaEvent_t> ev_db;     // double bounce: discovery, synthesis (pairs)
+    bool timed_bounce = false;          // the last timed frame recorded ev_db
     cudaStream_t cap_stream = nullptr;  // frame-graph recording stream
     cudaStream_t side = nullptr;        // kinematics rows beside the hierarchy build
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
@@ -229,6 +231,7 @@ struct bart_ctx {
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
         for (cudaEvent_t e : ev_kin) cudaEventDestroy(e);
         for (cudaEvent_t e : ev_syn) cudaEventDestroy(e);
+        for (cudaEvent_t e : ev_db) cudaEventDestroy(e);
         if (cap_stream) cudaStreamDestroy(cap_stream);
         if (side) cudaStreamDestroy(side);
         if (fork_ev) cudaEventDestroy(fork_ev);
@@ -745,6 +748,7 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
                                          "FP64 synthesis partials"));
     }
     if (ctx->timing) BART_TRY(ensure_events(ctx->ev, 7));
+    if (ctx->timing && bounce) BART_TRY(ensure_events(ctx->ev_db, 4));
 
     // every launch of the frame, on the caller's stream (the mixed path's
     // kinematics rows on a second stream, forked after the world facets and
@@ -819,6 +823,7 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
             nv.next("bart double bounce");
             const int64_t items = (int64_t)rd.P * F;
             const int64_t tw = bounce_scan_words(items);
+            if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_db[0], s), "cudaEventRecord");
             launch_bounce_count(ctx->tri64.p, ctx->fac.p, ctx->vel64.p, ctx->nodes.p,
                                 ctx->state.p, ctx->vis_idx.p, ctx->vis_cnt.p, F, rd,
                                 ctx->db_cnt.p, ctx->db_off.p, ctx->db_blk.p, ctx->status.p, s);
@@ -835,6 +840,7 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
                                    ctx->db_off.p, ctx->db_vf.p, ctx->status.p, s);
                 launches += 1;
             }
+            if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_db[1], s), "cudaEventRecord");
         } else {
             ctx->db_n = 0;
         }
@@ -922,12 +928,15 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
         // 5. the double-bounce echo, added into the cube (FP64 on every path)
         if (bounce && ctx->db_n > 0) {
             nv.next("bart double-bounce synthesis");
+            if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_db[2], s), "cudaEventRecord");
             launch_bounce_synth(ctx->db_vf.p, ctx->db_off.p,
                                 ctx->db_blk.p + bounce_scan_words((int64_t)rd.P * F) - 1,
                                 ctx->fac.p, ctx->vel64.p, ctx->state.p, F, rd, adc,
                                 dtype == BART_C64, ctx->counters.p + 4, s);
+            if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_db[3], s), "cudaEventRecord");
             launches += 1;
         }
+        ctx->timed_bounce = tm && bounce;
         if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[4], s), "cudaEventRecord");
         ctx->path = path;
         ctx->frame_launches = launches;
@@ -1485,6 +1494,10 @@ int bart_get_timing(bart_ctx *ctx, bart_timing *out)
         }
     } else {
         out->synthesis_ms = elapsed(ctx->ev[3], ctx->ev[4]);
+    }
+    if (ctx->timed_bounce) {
+        out->bounce_discovery_ms = elapsed(ctx->ev_db[0], ctx->ev_db[1]);
+        if (ctx->db_n > 0) out->bounce_synthesis_ms = elapsed(ctx->ev_db[2], ctx->ev_db[3]);
     }
     out->synthesis_launches = ctx->chunks;
     out->launches = ctx->frame_launches;

@@ -536,6 +536,20 @@ def car_ground_scene(seed: int = 11, ntri: int = 1500, ground_size: float = 12.0
     return s
 
 
+def sedan_ground_scene(ground_size: float = 20.0, ground_n: int = 40, **kw) -> Scene:
+    """``car_scene``'s moving sedan (20k triangles, 3 TX x 4 RX, 128 chirps x
+    256 samples) on a static ground patch (``ground_size`` square of
+    ``ground_n`` x ``ground_n`` squares, 0.5 m cells by default) centred
+    under it, double-bounce paths on."""
+    s = car_scene(**kw)
+    pos = s.instances[0].pos
+    s.meshes.append(ground(ground_size, ground_n, centre=(pos[0], pos[1])))
+    s.instances.append(Instance(1, pos=(0.0, 0.0, 0.0), rot=np.eye(3), vel=(0.0, 0.0, 0.0)))
+    s.radar.double_bounce = True
+    s.name = "sedan_ground"
+    return s
+
+
 def flatten(scene: Scene):
     """Concatenate instance meshes: per-facet local vertex triples, instance
     index, reflectivity, and the per-instance pose arrays.  Pure bookkeeping."""
