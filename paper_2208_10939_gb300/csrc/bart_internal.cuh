@@ -238,24 +238,41 @@ struct BounceFacet {
     int32_t p, a, b, side;   // TX, first facet, second facet, side of b lit (+1 / -1)
 };
 static_assert(sizeof(BounceFacet) == 144, "BounceFacet layout");
-// words of the scan scratch for n items (the last one receives the total)
+// A candidate (first facet a, second facet b) of TX p: b in a box that
+// meets a's beam and facing TX p's image in a (side of b)
+struct BounceCand {
+    int32_t a, b, p, side;
+};
+// words of the scan scratch for n counts (the last one receives the total)
 int64_t bounce_scan_words(int64_t n);
-// pieces per (TX p, i-th facet lit from p) item into cnt (P F), their
-// exclusive scan into off (P F) and the total into blk[bounce_scan_words - 1]
-void launch_bounce_count(const double *tri64, const FacetRec *fac, const double *vel64,
-                         const BvhNode *nodes, const uint8_t *state, const int32_t *vis_idx,
-                         const int32_t *vis_cnt, int64_t F, const RadarDev &rd, int32_t *cnt,
-                         int64_t *off, int64_t *blk, int *status, cudaStream_t s);
-void launch_bounce_fill(const double *tri64, const FacetRec *fac, const double *vel64,
-                        const BvhNode *nodes, const uint8_t *state, const int32_t *vis_idx,
-                        const int32_t *vis_cnt, int64_t F, const RadarDev &rd,
-                        const int64_t *off, BounceFacet *vf, int *status, cudaStream_t s);
-// adds the double-bounce echo of every channel into the cube (records:
-// counter of (virtual facet, channel, chirp) records, or NULL)
-void launch_bounce_synth(const BounceFacet *vf, const int64_t *off, const int64_t *total,
-                         const FacetRec *fac, const double *vel64, const uint8_t *state,
+// exclusive scan of n int32 counts into off, the total into blk[bounce_scan_words(n) - 1]
+void launch_bounce_scan(const int32_t *cnt, int64_t n, int64_t *off, int64_t *blk,
+                        cudaStream_t s);
+// pass 1 over the (TX p, i-th facet lit from p) items, P F of them: the
+// candidates per item into cnt (count), or the candidates at off (fill)
+void launch_bounce_candidates(bool fill, const double *tri64, const FacetRec *fac,
+                              const double *vel64, const BvhNode *nodes, const uint8_t *state,
+                              const int32_t *vis_idx, const int32_t *vis_cnt, int64_t F,
+                              const RadarDev &rd, int32_t *cnt, const int64_t *off,
+                              BounceCand *cand, int *status, cudaStream_t s);
+// pass 2 over the candidates: the virtual facets per candidate into pcnt
+// (count: clip, slivers, the a -> b leg), or written at poff (fill)
+void launch_bounce_pairs(bool fill, const double *tri64, const FacetRec *fac,
+                         const double *vel64, const BvhNode *nodes, const uint8_t *state,
+                         const BounceCand *cand, int64_t ncand, int64_t F, const RadarDev &rd,
+                         int32_t *pcnt, const int64_t *poff, BounceFacet *vf, int *status,
+                         cudaStream_t s);
+// txoff[p] (p <= P): the first virtual facet of TX p (txoff[P] = all of them)
+void launch_bounce_tx_offsets(const int64_t *cand_off, const int64_t *ncand, const int64_t *poff,
+                              const int64_t *npieces, int64_t F, int P, int64_t *txoff,
+                              cudaStream_t s);
+// adds the double-bounce echo of every channel into the cube, the
+// per-sample work in FP32 (fp32_eval: FP64 records, FP32 phasors) or in
+// FP64; records: counter of (virtual facet, channel, chirp) records, or NULL
+void launch_bounce_synth(const BounceFacet *vf, const int64_t *txoff, const FacetRec *fac,
+                         const double *vel64, const uint8_t *state,
                          int64_t F, const RadarDev &rd, void *out, int out_c64,
-                         unsigned long long *records, cudaStream_t s);
+                         bool fp32_eval, unsigned long long *records, cudaStream_t s);
 
 // ---- additive noise (noise.cu) ----
 int64_t noise_scratch_words();   // doubles

@@ -127,50 +127,150 @@ __device__ __forceinline__ bool box_meets_beam(const float *bmin, const float *b
     return true;
 }
 
-struct DbOut {
-    const int64_t *off;      // fill pass: first output slot of each item
-    BounceFacet *vf;         // fill pass: output
-    int32_t *cnt;            // count pass: pieces per item
-};
+// a's image of TX p and its velocity (the mirror moving with a's plane),
+// a's normal (|n_a|^2 = nn)
+__device__ __forceinline__ void image_of(const double *ta, const double *pt, const double *va,
+                                         double *na, double &nn, double *img, double *u)
+{
+    double e1[3], e2[3], d[3];
+    sub3(ta + 3, ta, e1);
+    sub3(ta + 6, ta, e2);
+    cross3(e1, e2, na);
+    nn = dot3(na, na);
+    sub3(pt, ta, d);
+    const double sc = __ddiv_rn(__dmul_rn(2.0, dot3(d, na)), nn);
+    for (int r = 0; r < 3; ++r) img[r] = __dsub_rn(pt[r], __dmul_rn(sc, na[r]));
+    const double su = __ddiv_rn(__dmul_rn(2.0, dot3(va, na)), nn);
+    for (int r = 0; r < 3; ++r) u[r] = __dmul_rn(su, na[r]);
+}
 
-// one thread per item (p, i): TX p, the i-th facet lit from TX p
+// the side of b that faces the image (+1 front, -1 reverse of a two-sided
+// b), 0 when it does not face it beyond eps_face
+__device__ __forceinline__ int facing_image(const double *tb, const double *img, bool two_sided,
+                                            double eps_face, double *nbb_out)
+{
+    double f1[3], f2[3], nb[3], cb[3], D[3];
+    sub3(tb + 3, tb, f1);
+    sub3(tb + 6, tb, f2);
+    cross3(f1, f2, nb);
+    const double nbb = dot3(nb, nb);
+    *nbb_out = nbb;
+    if (nbb == 0.0) return 0;
+    centroid3(tb, cb);
+    sub3(img, cb, D);
+    const double cosang =
+        __ddiv_rn(dot3(nb, D), __dmul_rn(__dsqrt_rn(nbb), __dsqrt_rn(dot3(D, D))));
+    if (cosang >= eps_face) return 1;
+    if (two_sided && cosang <= -eps_face) return -1;
+    return 0;
+}
+
+// Pi = tb clipped by the beam; returns its vertex count and the fan pieces
+// kept (bit q: piece (Pi_0, Pi_q, Pi_q+1) is not a sliver)
+__device__ __forceinline__ int clip_to_beam(const double *tb, const double *g, const double *base,
+                                            double nbb, double *poly, unsigned *keep)
+{
+    double buf[3 * kDbMaxV];
+    int K = 3;
+    for (int q = 0; q < 9; ++q) poly[q] = tb[q];
+    for (int h = 0; h < 4 && K >= 3; ++h) {
+        K = clip_keep(poly, K, g + 3 * h, base + 3 * h, buf);
+        for (int q = 0; q < 3 * K; ++q) poly[q] = buf[q];
+    }
+    *keep = 0;
+    if (K < 3) return K;
+    const double thr = __dmul_rn(kDbSliver, __dsqrt_rn(nbb));
+    for (int q = 1; q + 1 < K; ++q) {
+        double x1[3], x2[3], cr[3];
+        sub3(poly + 3 * q, poly, x1);
+        sub3(poly + 3 * (q + 1), poly, x2);
+        cross3(x1, x2, cr);
+        if (__dsqrt_rn(dot3(cr, cr)) > thr) *keep |= 1u << q;
+    }
+    return K;
+}
+
+// whether the a -> b leg (specular point on a's plane -> mean of Pi's
+// vertices) hits or grazes a facet other than a and b
+__device__ bool leg_blocked(const double *poly, int K, const double *ta, const double *na,
+                            const double *img, const double *__restrict__ tri64,
+                            const BvhNode *__restrict__ nodes, int64_t a, int64_t b, int *status)
+{
+    double cp[3] = {0.0, 0.0, 0.0}, spt[3], Dl[3], t1[3], t2[3];
+    for (int q = 0; q < K; ++q)
+        for (int r = 0; r < 3; ++r) cp[r] = __dadd_rn(cp[r], poly[3 * q + r]);
+    for (int r = 0; r < 3; ++r) cp[r] = __ddiv_rn(cp[r], (double)K);
+    sub3(ta, img, t1);
+    sub3(cp, img, t2);
+    const double lam = __ddiv_rn(dot3(na, t1), dot3(na, t2));
+    for (int r = 0; r < 3; ++r) spt[r] = __dadd_rn(img[r], __dmul_rn(lam, t2[r]));
+    sub3(cp, spt, Dl);
+    const float o[3] = {(float)spt[0], (float)spt[1], (float)spt[2]};
+    float inv[3];
+    for (int r = 0; r < 3; ++r) {
+        float dd = (float)Dl[r];
+        if (fabsf(dd) < 1e-30f) dd = copysignf(1e-30f, dd);
+        inv[r] = 1.0f / dd;
+    }
+    int st[kStack];
+    int sp = 0;
+    st[sp++] = 0;
+    while (sp > 0) {
+        const BvhNode m = nodes[st[--sp]];
+        const int c[2] = {m.left, m.right};
+        const bool h[2] = {slab_hit(m.lmin, m.lmax, o, inv), slab_hit(m.rmin, m.rmax, o, inv)};
+        for (int e = 0; e < 2; ++e) {
+            if (!h[e]) continue;
+            if (c[e] >= 0) {
+                if (sp < kStack) {
+                    st[sp++] = c[e];
+                } else {
+                    atomicOr(status, kStatusStackOverflow);
+                    return true;
+                }
+                continue;
+            }
+            const int64_t j = ~c[e];
+            if (j == a || j == b) continue;
+            double tj[9];
+            for (int q = 0; q < 9; ++q) tj[q] = tri64[9 * j + q];
+            if (mt_segment(spt, Dl, tj) != 0) return true;
+        }
+    }
+    return false;
+}
+
+// Pass 1, one thread per item (p, i): TX p, a = the i-th facet lit from TX
+// p.  a's beam through the LBVH; every facet b != a in a box that meets the
+// beam and facing the image is a candidate (count, or write (a, b, p, side)
+// at the item's offset).
 template <bool FILL>
 __global__ void __launch_bounds__(128)
-bounce_discover_kernel(const double *__restrict__ tri64, const FacetRec *__restrict__ fac,
-                       const double *__restrict__ vel64, const BvhNode *__restrict__ nodes,
-                       const uint8_t *__restrict__ state, const int32_t *__restrict__ vis_idx,
-                       const int32_t *__restrict__ vis_cnt, int64_t F, RadarDev rd, DbOut io,
-                       int *status)
+bounce_cand_kernel(const double *__restrict__ tri64, const FacetRec *__restrict__ fac,
+                   const double *__restrict__ vel64, const BvhNode *__restrict__ nodes,
+                   const uint8_t *__restrict__ state, const int32_t *__restrict__ vis_idx,
+                   const int32_t *__restrict__ vis_cnt, int64_t F, RadarDev rd,
+                   int32_t *__restrict__ cnt, const int64_t *__restrict__ off,
+                   BounceCand *__restrict__ cand, int *status)
 {
     const int p = blockIdx.y;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= F) return;
     const int64_t item = (int64_t)p * F + i;
     if (i >= vis_cnt[rd.O + p] || F < 2) {
-        if (!FILL) io.cnt[item] = 0;
+        if (!FILL) cnt[item] = 0;
         return;
     }
     const int64_t a = vis_idx[(int64_t)(rd.O + p) * F + i];
     const double *ta = tri64 + 9 * a;
     const double pt[3] = {rd.ant[p][0], rd.ant[p][1], rd.ant[p][2]};
-    double e1[3], e2[3], na[3], d[3], img[3], u[3];
-    sub3(ta + 3, ta, e1);
-    sub3(ta + 6, ta, e2);
-    cross3(e1, e2, na);
-    const double nn = dot3(na, na);
-    sub3(pt, ta, d);
-    const double sc = __ddiv_rn(__dmul_rn(2.0, dot3(d, na)), nn);
-    for (int r = 0; r < 3; ++r) img[r] = __dsub_rn(pt[r], __dmul_rn(sc, na[r]));
-    const double *va = vel64 + 3 * fac[a].inst;
-    const double su = __ddiv_rn(__dmul_rn(2.0, dot3(va, na)), nn);
-    for (int r = 0; r < 3; ++r) u[r] = __dmul_rn(su, na[r]);
+    double na[3], nn, img[3], u[3];
+    image_of(ta, pt, vel64 + 3 * fac[a].inst, na, nn, img, u);
     const int side_a = state[(int64_t)p * F + a] == BART_VIS_LIT ? 1 : -1;
     double g[12], base[12];
     beam_planes(ta, side_a, img, g, base);
-    const double w_a = (double)fac[a].rho;
-
     int32_t count = 0;
-    int64_t slot = FILL ? io.off[item] : 0;
+    int64_t slot = FILL ? off[item] : 0;
     int stack[kStack];
     int sp = 0;
     stack[sp++] = 0;
@@ -188,109 +288,85 @@ bounce_discover_kernel(const double *__restrict__ tri64, const FacetRec *__restr
             }
             const int64_t b = ~ch[c];
             if (b == a) continue;
-            const double *tb = tri64 + 9 * b;
-            double f1[3], f2[3], nb[3], cb[3], D[3];
-            sub3(tb + 3, tb, f1);
-            sub3(tb + 6, tb, f2);
-            cross3(f1, f2, nb);
-            const double nbb = dot3(nb, nb);
-            if (nbb == 0.0) continue;
-            centroid3(tb, cb);
-            sub3(img, cb, D);
-            const double cosang =
-                __ddiv_rn(dot3(nb, D), __dmul_rn(__dsqrt_rn(nbb), __dsqrt_rn(dot3(D, D))));
-            int side_b;
-            if (cosang >= rd.eps_face) side_b = 1;
-            else if (fac[b].two_sided && cosang <= -rd.eps_face) side_b = -1;
-            else continue;
-            double poly[3 * kDbMaxV], buf[3 * kDbMaxV];
-            int K = 3;
-            for (int q = 0; q < 9; ++q) poly[q] = tb[q];
-            for (int h = 0; h < 4 && K >= 3; ++h) {
-                K = clip_keep(poly, K, g + 3 * h, base + 3 * h, buf);
-                for (int q = 0; q < 3 * K; ++q) poly[q] = buf[q];
-            }
-            if (K < 3) continue;
-            const double thr = __dmul_rn(kDbSliver, __dsqrt_rn(nbb));
-            unsigned keep = 0;
-            for (int q = 1; q + 1 < K; ++q) {
-                double x1[3], x2[3], cr[3];
-                sub3(poly + 3 * q, poly, x1);
-                sub3(poly + 3 * (q + 1), poly, x2);
-                cross3(x1, x2, cr);
-                if (__dsqrt_rn(dot3(cr, cr)) > thr) keep |= 1u << q;
-            }
-            if (!keep) continue;
-            // the a -> b leg: specular point on a's plane -> c_Pi
-            double cp[3] = {0.0, 0.0, 0.0}, spt[3], Dl[3], t1[3], t2[3];
-            for (int q = 0; q < K; ++q)
-                for (int r = 0; r < 3; ++r) cp[r] = __dadd_rn(cp[r], poly[3 * q + r]);
-            for (int r = 0; r < 3; ++r) cp[r] = __ddiv_rn(cp[r], (double)K);
-            sub3(ta, img, t1);
-            sub3(cp, img, t2);
-            const double lam = __ddiv_rn(dot3(na, t1), dot3(na, t2));
-            for (int r = 0; r < 3; ++r) spt[r] = __dadd_rn(img[r], __dmul_rn(lam, t2[r]));
-            sub3(cp, spt, Dl);
-            bool blocked = false;
-            {
-                const float o[3] = {(float)spt[0], (float)spt[1], (float)spt[2]};
-                float inv[3];
-                for (int r = 0; r < 3; ++r) {
-                    float dd = (float)Dl[r];
-                    if (fabsf(dd) < 1e-30f) dd = copysignf(1e-30f, dd);
-                    inv[r] = 1.0f / dd;
-                }
-                int st2[kStack];
-                int sp2 = 0;
-                st2[sp2++] = 0;
-                while (sp2 > 0 && !blocked) {
-                    const BvhNode m2 = nodes[st2[--sp2]];
-                    const int c2[2] = {m2.left, m2.right};
-                    const bool h2[2] = {slab_hit(m2.lmin, m2.lmax, o, inv),
-                                        slab_hit(m2.rmin, m2.rmax, o, inv)};
-                    for (int e = 0; e < 2 && !blocked; ++e) {
-                        if (!h2[e]) continue;
-                        if (c2[e] >= 0) {
-                            if (sp2 < kStack) {
-                                st2[sp2++] = c2[e];
-                            } else {
-                                atomicOr(status, kStatusStackOverflow);
-                                blocked = true;
-                            }
-                            continue;
-                        }
-                        const int64_t j = ~c2[e];
-                        if (j == a || j == b) continue;
-                        double tj[9];
-                        for (int q = 0; q < 9; ++q) tj[q] = tri64[9 * j + q];
-                        if (mt_segment(spt, Dl, tj) != 0) blocked = true;
-                    }
-                }
-            }
-            if (blocked) continue;
-            const double w = -__dmul_rn(w_a, (double)fac[b].rho);
-            for (int q = 1; q + 1 < K; ++q) {
-                if (!(keep & (1u << q))) continue;
-                if (FILL) {
-                    BounceFacet &v = io.vf[slot++];
-                    v.p = p;
-                    v.a = (int32_t)a;
-                    v.b = (int32_t)b;
-                    v.side = side_b;
-                    for (int r = 0; r < 3; ++r) {
-                        v.tri[r] = poly[r];
-                        v.tri[3 + r] = poly[3 * q + r];
-                        v.tri[6 + r] = poly[3 * (q + 1) + r];
-                        v.src[r] = img[r];
-                        v.usrc[r] = u[r];
-                    }
-                    v.w = w;
-                }
-                ++count;
-            }
+            double nbb;
+            const int side_b = facing_image(tri64 + 9 * b, img, fac[b].two_sided != 0,
+                                            rd.eps_face, &nbb);
+            if (!side_b) continue;
+            if (FILL) cand[slot++] = BounceCand{(int32_t)a, (int32_t)b, p, side_b};
+            ++count;
         }
     }
-    if (!FILL) io.cnt[item] = count;
+    if (!FILL) cnt[item] = count;
+}
+
+// Pass 2, one thread per candidate: b clipped to a's beam, the fan's
+// non-sliver pieces and the a -> b leg.  Count pass: pieces (0 when the leg
+// is blocked or nothing is lit); fill pass: writes them at the candidate's
+// offset (the leg already decided).
+template <bool FILL>
+__global__ void __launch_bounds__(128)
+bounce_pair_kernel(const double *__restrict__ tri64, const FacetRec *__restrict__ fac,
+                   const double *__restrict__ vel64, const BvhNode *__restrict__ nodes,
+                   const uint8_t *__restrict__ state, const BounceCand *__restrict__ cand,
+                   int64_t ncand, int64_t F, RadarDev rd, int32_t *__restrict__ pcnt, const int64_t *__restrict__ poff,
+                   BounceFacet *__restrict__ vf, int *status)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncand) return;
+    if (FILL && pcnt[c] == 0) return;
+    const BounceCand C = cand[c];
+    const double *ta = tri64 + 9 * (int64_t)C.a, *tb = tri64 + 9 * (int64_t)C.b;
+    const double pt[3] = {rd.ant[C.p][0], rd.ant[C.p][1], rd.ant[C.p][2]};
+    double na[3], nn, img[3], u[3];
+    image_of(ta, pt, vel64 + 3 * fac[C.a].inst, na, nn, img, u);
+    const int side_a = state[(int64_t)C.p * F + C.a] == BART_VIS_LIT ? 1 : -1;
+    double g[12], base[12];
+    beam_planes(ta, side_a, img, g, base);
+    double f1[3], f2[3], nb[3];
+    sub3(tb + 3, tb, f1);
+    sub3(tb + 6, tb, f2);
+    cross3(f1, f2, nb);
+    const double nbb = dot3(nb, nb);
+    double poly[3 * kDbMaxV];
+    unsigned keep;
+    const int K = clip_to_beam(tb, g, base, nbb, poly, &keep);
+    if (!FILL) {
+        const bool lit = K >= 3 && keep != 0 &&
+                         !leg_blocked(poly, K, ta, na, img, tri64, nodes, C.a, C.b, status);
+        pcnt[c] = lit ? __popc(keep) : 0;
+        return;
+    }
+    int64_t slot = poff[c];
+    const double w = -__dmul_rn((double)fac[C.a].rho, (double)fac[C.b].rho);
+    for (int q = 1; q + 1 < K; ++q) {
+        if (!(keep & (1u << q))) continue;
+        BounceFacet &v = vf[slot++];
+        v.p = C.p;
+        v.a = C.a;
+        v.b = C.b;
+        v.side = C.side;
+        for (int r = 0; r < 3; ++r) {
+            v.tri[r] = poly[r];
+            v.tri[3 + r] = poly[3 * q + r];
+            v.tri[6 + r] = poly[3 * (q + 1) + r];
+            v.src[r] = img[r];
+            v.usrc[r] = u[r];
+        }
+        v.w = w;
+    }
+}
+
+// first virtual facet of each TX: the pieces of its first candidate
+__global__ void bounce_tx_offsets_kernel(const int64_t *__restrict__ cand_off,
+                                         const int64_t *__restrict__ ncand,
+                                         const int64_t *__restrict__ poff,
+                                         const int64_t *__restrict__ npieces, int64_t F, int P,
+                                         int64_t *__restrict__ txoff)
+{
+    const int p = threadIdx.x;
+    if (p > P) return;
+    const int64_t c = p < P ? cand_off[(int64_t)p * F] : *ncand;
+    txoff[p] = c < *ncand ? poff[c] : *npieces;
 }
 
 // ---- exclusive scan of int32 counts into int64 offsets -------------------
@@ -359,10 +435,94 @@ struct RecB {
     int kind, flags;
 };
 
+// one sample (fast time t, frequency fm) of an FP64 record, before the
+// common factor C / k_m^2
+__device__ __forceinline__ void eval_rec64(const RecB &R, double t, double fm, double inv_c,
+                                           double inv_f0, double mu_2c2, double &re, double &im)
+{
+    const double L = sqrt(R.qt[0] + t * (R.qt[1] + t * R.qt[2])) +
+                     sqrt(R.qr[0] + t * (R.qr[1] + t * R.qr[2]));
+    const double fmc = fm * inv_c;
+    const double kp = fm * inv_f0;
+    double thc = fmc * L - mu_2c2 * L * L;
+    thc -= rint(thc);
+    re = 0.0;
+    im = 0.0;
+    if (R.kind == kRecVertex) {
+        for (int e = 0; e < 3; ++e) {
+            double s_, c_;
+            sincospi(2.0 * (thc - fmc * R.d[e]), &s_, &c_);
+            re += R.d[3 + e] * c_;
+            im += R.d[3 + e] * s_;
+        }
+    } else if (R.kind == kRecSeries) {
+        double s_, c_;
+        sincospi(2.0 * (thc - fmc * R.d[0]), &s_, &c_);
+        const double k2 = kp * kp;
+        double aa = R.d[8], bb = R.d[15];
+        for (int e = 6; e >= 0; --e) aa = aa * k2 + R.d[1 + e];
+        for (int e = 5; e >= 0; --e) bb = bb * k2 + R.d[9 + e];
+        const double pr_ = aa * k2, pi_ = bb * k2 * kp;
+        re = c_ * pr_ - s_ * pi_;
+        im = c_ * pi_ + s_ * pr_;
+    } else {
+        for (int e = 0; e < 3; ++e) {
+            double s_, c_;
+            sincospi(2.0 * (thc - fmc * R.d[3 * e]), &s_, &c_);
+            const double x = kp * R.d[3 * e + 1];
+            double sn;
+            if (R.flags & (1 << e)) {
+                const double x2 = x * x;
+                sn = 1.0 + x2 * (-1.0 / 6 + x2 * (1.0 / 120 + x2 * (-1.0 / 5040 +
+                     x2 * (1.0 / 362880 + x2 * (-1.0 / 39916800)))));
+            } else {
+                sn = sin(x) / x;
+            }
+            const double coef = kp * R.d[3 * e + 2] * sn;
+            re -= coef * s_;
+            im += coef * c_;
+        }
+    }
+}
+
+// The FP64 record of virtual facet B for one (channel, chirp): the FP64
+// path's record (record_fp64.cuh) from the facet's position at the chirp
+// start tn, with the image source in place of the TX and, for the delay's
+// motion within the chirp, the TX leg's own relative velocity v_b - u
+__device__ void build_rec64(const BounceFacet &B, const double *vb, double tn, const double *prx,
+                            const RadarDev &rd, double k0, double kmax, int two_sided, RecB &R)
+{
+    double tri[9], c0[3], ptx[3], rec[kRecEntries];
+    for (int r = 0; r < 9; ++r) tri[r] = B.tri[r];
+    centroid3(tri, c0);
+    for (int r = 0; r < 3; ++r) ptx[r] = B.src[r] + B.usrc[r] * tn;
+    int flags = 0;
+    R.kind = build_record<double>(tri, c0, vb, tn, ptx, prx, B.w, rd.intra, k0, kmax,
+                                  kDelayFacet, nullptr, two_sided, rec,
+                                  &flags);
+    R.flags = flags;
+    R.qt[0] = rec[0];
+    R.qr[0] = rec[3];
+    if (rd.intra) {
+        // the TX leg runs from the moving image: relative velocity v_b - u
+        double dt[3], wv[3];
+        for (int r = 0; r < 3; ++r) {
+            dt[r] = ptx[r] - (c0[r] + vb[r] * tn);
+            wv[r] = vb[r] - B.usrc[r];
+        }
+        R.qt[1] = -2.0 * (dt[0] * wv[0] + dt[1] * wv[1] + dt[2] * wv[2]);
+        R.qt[2] = wv[0] * wv[0] + wv[1] * wv[1] + wv[2] * wv[2];
+        R.qr[1] = rec[4];
+        R.qr[2] = rec[2];
+    } else {
+        R.qt[1] = R.qt[2] = R.qr[1] = R.qr[2] = 0.0;
+    }
+    for (int r = 0; r < 22; ++r) R.d[r] = rec[kRecD + r];
+}
+
 template <int S>
 __global__ void __launch_bounds__(kDbWarps * 32)
-bounce_synth_kernel(const BounceFacet *__restrict__ vf, const int64_t *__restrict__ off,
-                    const int64_t *__restrict__ total,
+bounce_synth_kernel(const BounceFacet *__restrict__ vf, const int64_t *__restrict__ txoff,
                     const FacetRec *__restrict__ fac, const double *__restrict__ vel64,
                     const uint8_t *__restrict__ state, int64_t F, RadarDev rd, int W, void *out,
                     int out_c64, unsigned long long *records)
@@ -383,9 +543,7 @@ bounce_synth_kernel(const BounceFacet *__restrict__ vf, const int64_t *__restric
     const double tn = (double)((int64_t)n * rd.slots + (rd.tdm ? p : 0)) * rd.Tc;
     const double *prx = rd.ant[rd.P + q];
     const uint8_t *st_r = state + (int64_t)(rd.P + q) * F;
-    // the virtual facets of TX p: items p F .. (p + 1) F - 1 of the scan
-    const int64_t v0 = off[(int64_t)p * F];
-    const int64_t v1 = p + 1 < rd.P ? off[(int64_t)(p + 1) * F] : *total;
+    const int64_t v0 = txoff[p], v1 = txoff[p + 1];      // the virtual facets of TX p
 
     double accr[S], acci[S];
 #pragma unroll
@@ -400,34 +558,8 @@ bounce_synth_kernel(const BounceFacet *__restrict__ vf, const int64_t *__restric
             const BounceFacet &B = vf[v];
             valid = st_r[B.b] == (B.side > 0 ? BART_VIS_LIT : BART_VIS_LIT_REV);
             if (valid) {
-                const double *vb = vel64 + 3 * fac[B.b].inst;
-                double tri[9], c0[3], ptx[3], rec[kRecEntries];
-                for (int r = 0; r < 9; ++r) tri[r] = B.tri[r];
-                centroid3(tri, c0);
-                for (int r = 0; r < 3; ++r) ptx[r] = B.src[r] + B.usrc[r] * tn;
-                int flags = 0;
-                RecB &R = sR[warp][lane];
-                R.kind = build_record<double>(tri, c0, vb, tn, ptx, prx, B.w, rd.intra, k0, kmax,
-                                              kDelayFacet, nullptr, fac[B.b].two_sided, rec,
-                                              &flags);
-                R.flags = flags;
-                R.qt[0] = rec[0];
-                R.qr[0] = rec[3];
-                if (rd.intra) {
-                    // the TX leg runs from the moving image: relative velocity v_b - u
-                    double dt[3], wv[3];
-                    for (int r = 0; r < 3; ++r) {
-                        dt[r] = ptx[r] - (c0[r] + vb[r] * tn);
-                        wv[r] = vb[r] - B.usrc[r];
-                    }
-                    R.qt[1] = -2.0 * (dt[0] * wv[0] + dt[1] * wv[1] + dt[2] * wv[2]);
-                    R.qt[2] = wv[0] * wv[0] + wv[1] * wv[1] + wv[2] * wv[2];
-                    R.qr[1] = rec[4];
-                    R.qr[2] = rec[2];
-                } else {
-                    R.qt[1] = R.qt[2] = R.qr[1] = R.qr[2] = 0.0;
-                }
-                for (int r = 0; r < 22; ++r) R.d[r] = rec[kRecD + r];
+                build_rec64(B, vel64 + 3 * fac[B.b].inst, tn, prx, rd, k0, kmax,
+                            fac[B.b].two_sided, sR[warp][lane]);
             }
         }
         __syncwarp();
@@ -441,48 +573,188 @@ bounce_synth_kernel(const BounceFacet *__restrict__ vf, const int64_t *__restric
             for (int j = 0; j < S; ++j) {
                 const double t = (double)(m0 + j) * inv_fs;
                 const double fm = f0 + mu * t;
-                const double L = sqrt(R.qt[0] + t * (R.qt[1] + t * R.qt[2])) +
-                                 sqrt(R.qr[0] + t * (R.qr[1] + t * R.qr[2]));
-                const double fmc = fm * inv_c;
-                const double kp = fm * inv_f0;
-                double thc = fmc * L - mu_2c2 * L * L;
-                thc -= rint(thc);
-                double re = 0.0, im = 0.0;
-                if (R.kind == kRecVertex) {
-                    for (int e = 0; e < 3; ++e) {
-                        double s_, c_;
-                        sincospi(2.0 * (thc - fmc * R.d[e]), &s_, &c_);
-                        re += R.d[3 + e] * c_;
-                        im += R.d[3 + e] * s_;
-                    }
-                } else if (R.kind == kRecSeries) {
-                    double s_, c_;
-                    sincospi(2.0 * (thc - fmc * R.d[0]), &s_, &c_);
-                    const double k2 = kp * kp;
-                    double aa = R.d[8], bb = R.d[15];
-                    for (int e = 6; e >= 0; --e) aa = aa * k2 + R.d[1 + e];
-                    for (int e = 5; e >= 0; --e) bb = bb * k2 + R.d[9 + e];
-                    const double pr_ = aa * k2, pi_ = bb * k2 * kp;
-                    re = c_ * pr_ - s_ * pi_;
-                    im = c_ * pi_ + s_ * pr_;
-                } else {
-                    for (int e = 0; e < 3; ++e) {
-                        double s_, c_;
-                        sincospi(2.0 * (thc - fmc * R.d[3 * e]), &s_, &c_);
-                        const double x = kp * R.d[3 * e + 1];
-                        double sn;
-                        if (R.flags & (1 << e)) {
-                            const double x2 = x * x;
-                            sn = 1.0 + x2 * (-1.0 / 6 + x2 * (1.0 / 120 + x2 * (-1.0 / 5040 +
-                                 x2 * (1.0 / 362880 + x2 * (-1.0 / 39916800)))));
-                        } else {
-                            sn = sin(x) / x;
-                        }
-                        const double coef = kp * R.d[3 * e + 2] * sn;
-                        re -= coef * s_;
-                        im += coef * c_;
-                    }
+                double re, im;
+                eval_rec64(R, t, fm, inv_c, inv_f0, mu_2c2, re, im);
+                accr[j] += re;
+                acci[j] += im;
+            }
+        }
+        __syncwarp();
+    }
+    if (lane == 0 && seg == 0 && records) atomicAdd(records, nrec);
+    const double camp = 2.0 * sqrt(kPi) / pow(4.0 * kPi, 1.5);
+    const int64_t row = ((int64_t)o * N + n) * rd.M + m0;
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+        const double fm = f0 + mu * (double)(m0 + j) / fs;
+        const double km = 2.0 * kPi * fm / c;
+        const double sc = camp / (km * km);
+        if (out_c64) {
+            float2 &y = reinterpret_cast<float2 *>(out)[row + j];
+            y.x += (float)(accr[j] * sc);
+            y.y += (float)(acci[j] * sc);
+        } else {
+            double2 &y = reinterpret_cast<double2 *>(out)[row + j];
+            y.x += accr[j] * sc;
+            y.y += acci[j] * sc;
+        }
+    }
+}
+
+// FP32 form of a vertex-form record for one (channel, chirp): the phase of
+// vertex v at sample m is A_v + B_v m + C m^2 cycles (the path to second
+// order in fast time; the third-order term stays below 1e-12 m over a
+// chirp), B_v = Bhi_v + Blo_v with Bhi_v a multiple of 2^-14 (so that
+// Bhi_v m is exact in FP32 for m < 2^10) and |Blo_v| <= 2^-15; wt_v the
+// vertex weight of the facet integral (record_fp64.cuh)
+struct RecV {
+    float A[3], Bhi[3], Blo[3], wt[3];
+    float C;
+    int vertex;                // 1: use this form; 0: the FP64 record (series / edge form)
+};
+
+__device__ __forceinline__ double red1d(double x) { return x - rint(x); }
+__device__ __forceinline__ float red1f(float x) { return x - rintf(x); }
+
+// the vertex phases' quadratics from the FP64 record R: each leg's path
+// sqrt(q0 + q1 t + q2 t^2) expanded to L0 + L1 t + L2 t^2, the phase
+// f(t) L(t) / c - mu L(t)^2 / (2 c^2) of Eq. 13 to second order, the
+// vertex terms' -f(t) u_v / c added
+__device__ __forceinline__ void vertex_quadratics(const RecB &R, const RadarDev &rd, RecV &V)
+{
+    V.vertex = R.kind == kRecVertex;
+    if (!V.vertex) return;
+    const double c = kC0, f0 = rd.f0, mu = rd.slope, fs = rd.fs;
+    double L0 = 0.0, L1 = 0.0, L2 = 0.0;
+    const double *qs[2] = {R.qt, R.qr};
+    for (int l = 0; l < 2; ++l) {
+        const double *q = qs[l];
+        const double a0 = sqrt(q[0]);
+        const double inv = 0.5 / a0;
+        const double a1 = q[1] * inv;
+        L0 += a0;
+        L1 += a1;
+        L2 += (q[2] - a1 * a1) * inv;
+    }
+    const double f0c = f0 / c, muc = mu / c, mu2c2 = mu / (2.0 * c * c);
+    const double th0 = f0c * L0 - mu2c2 * L0 * L0;
+    const double th1 = (f0c * L1 + muc * L0 - 2.0 * mu2c2 * L0 * L1) / fs;
+    const double th2 = (f0c * L2 + muc * L1 - mu2c2 * (L1 * L1 + 2.0 * L0 * L2)) / (fs * fs);
+    const double mucfs = muc / fs;
+    for (int v = 0; v < 3; ++v) {
+        const double u = R.d[v];
+        V.A[v] = (float)red1d(th0 - f0c * u);
+        const double b = red1d(th1 - mucfs * u);
+        const double bhi = rint(b * 16384.0) / 16384.0;
+        V.Bhi[v] = (float)bhi;
+        V.Blo[v] = (float)(b - bhi);
+        V.wt[v] = (float)R.d[3 + v];
+    }
+    V.C = (float)th2;
+}
+
+// The double-bounce synthesis with the per-sample work in FP32: records in
+// FP64 as above (one per lane, 32 per batch), vertex-form records evaluated
+// by every lane over its S samples from an FP32 start phasor and its chord
+// step (the curvature C (S - 1)^2 / 4 cycles, below 1e-5, is left out),
+// batch sums in FP32 added to FP64 totals; series- and edge-form records by
+// the FP64 evaluation.
+template <int S>
+__global__ void __launch_bounds__(kDbWarps * 32)
+bounce_synth_f32_kernel(const BounceFacet *__restrict__ vf, const int64_t *__restrict__ txoff,
+                        const FacetRec *__restrict__ fac, const double *__restrict__ vel64,
+                        const uint8_t *__restrict__ state, int64_t F, RadarDev rd, int W,
+                        void *out, int out_c64, unsigned long long *records)
+{
+    __shared__ RecB sR[kDbWarps][32];
+    __shared__ RecV sV[kDbWarps][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t gw = (int64_t)blockIdx.x * kDbWarps + warp;
+    const int N = rd.N;
+    if (gw >= (int64_t)rd.O * N * W) return;
+    const int seg = (int)(gw % W);
+    const int64_t unit = gw / W;
+    const int o = (int)(unit / N), n = (int)(unit % N);
+    const int p = o / rd.Q, q = o % rd.Q;
+    const int m0 = (seg * 32 + lane) * S;
+    const double c = kC0, f0 = rd.f0, mu = rd.slope, fs = rd.fs;
+    const double f_max = f0 + mu * (rd.M - 1) / fs;
+    const double k0 = 2.0 * kPi * f0 / c, kmax = 2.0 * kPi * f_max / c;
+    const double tn = (double)((int64_t)n * rd.slots + (rd.tdm ? p : 0)) * rd.Tc;
+    const double *prx = rd.ant[rd.P + q];
+    const uint8_t *st_r = state + (int64_t)(rd.P + q) * F;
+    const int64_t v0 = txoff[p], v1 = txoff[p + 1];
+    const double inv_fs = 1.0 / fs, inv_c = 1.0 / c, inv_f0 = 1.0 / f0;
+    const double mu_2c2 = mu / (2.0 * c * c);
+    const float fm0 = (float)m0, fm0sq = fm0 * fm0, chord = 2.f * fm0 + (float)(S - 1);
+
+    double accr[S], acci[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) accr[j] = acci[j] = 0.0;
+    unsigned long long nrec = 0;
+    for (int64_t base = v0; base < v1; base += 32) {
+        const int64_t v = base + lane;
+        bool valid = false;
+        if (v < v1) {
+            const BounceFacet &B = vf[v];
+            valid = st_r[B.b] == (B.side > 0 ? BART_VIS_LIT : BART_VIS_LIT_REV);
+            if (valid) {
+                build_rec64(B, vel64 + 3 * fac[B.b].inst, tn, prx, rd, k0, kmax,
+                            fac[B.b].two_sided, sR[warp][lane]);
+                vertex_quadratics(sR[warp][lane], rd, sV[warp][lane]);
+            }
+        }
+        __syncwarp();
+        const unsigned int mask = __ballot_sync(0xffffffffu, valid);
+        const unsigned int vmask = __ballot_sync(0xffffffffu, valid && sV[warp][lane].vertex);
+        nrec += __popc(mask);
+        float ar[S], ai[S];
+#pragma unroll
+        for (int j = 0; j < S; ++j) ar[j] = ai[j] = 0.f;
+        unsigned int m = vmask;
+        while (m) {
+            const int i = __ffs(m) - 1;
+            m &= m - 1;
+            const RecV &V = sV[warp][i];
+            float zc[3], zs[3], cs[3], ss[3];
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                const float ph = red1f(red1f(V.Bhi[e] * fm0) +
+                                       (V.A[e] + fmaf(V.Blo[e], fm0, V.C * fm0sq)));
+                sincospif(2.f * ph, &zs[e], &zc[e]);
+                const float st = red1f(V.Bhi[e] + fmaf(V.C, chord, V.Blo[e]));
+                sincospif(2.f * st, &ss[e], &cs[e]);
+            }
+#pragma unroll
+            for (int j = 0; j < S; ++j) {
+                float tr = 0.f, ti = 0.f;
+#pragma unroll
+                for (int e = 0; e < 3; ++e) {
+                    tr = fmaf(V.wt[e], zc[e], tr);
+                    ti = fmaf(V.wt[e], zs[e], ti);
+                    const float nc = fmaf(zc[e], cs[e], -zs[e] * ss[e]);
+                    zs[e] = fmaf(zc[e], ss[e], zs[e] * cs[e]);
+                    zc[e] = nc;
                 }
+                ar[j] += tr;
+                ai[j] += ti;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+            accr[j] += (double)ar[j];
+            acci[j] += (double)ai[j];
+        }
+        m = mask & ~vmask;
+        while (m) {
+            const int i = __ffs(m) - 1;
+            m &= m - 1;
+            const RecB &R = sR[warp][i];
+#pragma unroll 1
+            for (int j = 0; j < S; ++j) {
+                const double t = (double)(m0 + j) * inv_fs;
+                double re, im;
+                eval_rec64(R, t, f0 + mu * t, inv_c, inv_f0, mu_2c2, re, im);
                 accr[j] += re;
                 acci[j] += im;
             }
@@ -513,53 +785,87 @@ bounce_synth_kernel(const BounceFacet *__restrict__ vf, const int64_t *__restric
 
 int64_t bounce_scan_words(int64_t n) { return (n + kScanBlk - 1) / kScanBlk + 1; }
 
-void launch_bounce_count(const double *tri64, const FacetRec *fac, const double *vel64,
-                         const BvhNode *nodes, const uint8_t *state, const int32_t *vis_idx,
-                         const int32_t *vis_cnt, int64_t F, const RadarDev &rd, int32_t *cnt,
-                         int64_t *off, int64_t *blk, int *status, cudaStream_t s)
+void launch_bounce_scan(const int32_t *cnt, int64_t n, int64_t *off, int64_t *blk,
+                        cudaStream_t s)
 {
-    const int T = 128;
-    DbOut io{nullptr, nullptr, cnt};
-    dim3 grid((unsigned int)((F + T - 1) / T), (unsigned int)rd.P);
-    bounce_discover_kernel<false><<<grid, T, 0, s>>>(tri64, fac, vel64, nodes, state, vis_idx,
-                                                     vis_cnt, F, rd, io, status);
-    const int64_t n = (int64_t)rd.P * F;
     const int64_t nblk = (n + kScanBlk - 1) / kScanBlk;
-    scan_blocks_kernel<<<(unsigned int)nblk, kScanBlk, 0, s>>>(cnt, n, off, blk);
+    if (nblk > 0) scan_blocks_kernel<<<(unsigned int)nblk, kScanBlk, 0, s>>>(cnt, n, off, blk);
     scan_totals_kernel<<<1, 32, 0, s>>>(blk, nblk);
-    scan_add_kernel<<<(unsigned int)nblk, kScanBlk, 0, s>>>(off, n, blk);
+    if (nblk > 0) scan_add_kernel<<<(unsigned int)nblk, kScanBlk, 0, s>>>(off, n, blk);
 }
 
-void launch_bounce_fill(const double *tri64, const FacetRec *fac, const double *vel64,
-                        const BvhNode *nodes, const uint8_t *state, const int32_t *vis_idx,
-                        const int32_t *vis_cnt, int64_t F, const RadarDev &rd,
-                        const int64_t *off, BounceFacet *vf, int *status, cudaStream_t s)
+void launch_bounce_candidates(bool fill, const double *tri64, const FacetRec *fac,
+                              const double *vel64, const BvhNode *nodes, const uint8_t *state,
+                              const int32_t *vis_idx, const int32_t *vis_cnt, int64_t F,
+                              const RadarDev &rd, int32_t *cnt, const int64_t *off,
+                              BounceCand *cand, int *status, cudaStream_t s)
 {
     const int T = 128;
-    DbOut io{off, vf, nullptr};
     dim3 grid((unsigned int)((F + T - 1) / T), (unsigned int)rd.P);
-    bounce_discover_kernel<true><<<grid, T, 0, s>>>(tri64, fac, vel64, nodes, state, vis_idx,
-                                                    vis_cnt, F, rd, io, status);
+    if (fill)
+        bounce_cand_kernel<true><<<grid, T, 0, s>>>(tri64, fac, vel64, nodes, state, vis_idx,
+                                                    vis_cnt, F, rd, cnt, off, cand, status);
+    else
+        bounce_cand_kernel<false><<<grid, T, 0, s>>>(tri64, fac, vel64, nodes, state, vis_idx,
+                                                     vis_cnt, F, rd, cnt, off, cand, status);
 }
 
-void launch_bounce_synth(const BounceFacet *vf, const int64_t *off, const int64_t *total,
-                         const FacetRec *fac,
-                         const double *vel64, const uint8_t *state, int64_t F,
-                         const RadarDev &rd, void *out, int out_c64, unsigned long long *records,
+void launch_bounce_pairs(bool fill, const double *tri64, const FacetRec *fac,
+                         const double *vel64, const BvhNode *nodes, const uint8_t *state,
+                         const BounceCand *cand, int64_t ncand, int64_t F, const RadarDev &rd,
+                         int32_t *pcnt, const int64_t *poff, BounceFacet *vf, int *status,
                          cudaStream_t s)
 {
+    if (ncand <= 0) return;
+    const int T = 128;
+    const unsigned int grid = (unsigned int)((ncand + T - 1) / T);
+    if (fill)
+        bounce_pair_kernel<true><<<grid, T, 0, s>>>(tri64, fac, vel64, nodes, state, cand, ncand,
+                                                    F, rd, pcnt, poff, vf, status);
+    else
+        bounce_pair_kernel<false><<<grid, T, 0, s>>>(tri64, fac, vel64, nodes, state, cand,
+                                                     ncand, F, rd, pcnt, poff, vf, status);
+}
+
+void launch_bounce_tx_offsets(const int64_t *cand_off, const int64_t *ncand, const int64_t *poff,
+                              const int64_t *npieces, int64_t F, int P, int64_t *txoff,
+                              cudaStream_t s)
+{
+    bounce_tx_offsets_kernel<<<1, 64, 0, s>>>(cand_off, ncand, poff, npieces, F, P, txoff);
+}
+
+void launch_bounce_synth(const BounceFacet *vf, const int64_t *txoff, const FacetRec *fac,
+                         const double *vel64, const uint8_t *state, int64_t F,
+                         const RadarDev &rd, void *out, int out_c64, bool fp32_eval,
+                         unsigned long long *records, cudaStream_t s)
+{
     const int M = rd.M;                // a multiple of 32
-    int S = 8;                         // samples per lane: the largest of 8, 4, 2, 1 dividing M / 32
+    // samples per lane: the largest power of two up to 16 (FP32 evaluation)
+    // or 8 (FP64) that divides M / 32
+    int S = fp32_eval ? 16 : 8;
     while ((M / 32) % S) S /= 2;
     const int W = M / (32 * S);
     const int64_t warps = (int64_t)rd.O * rd.N * W;
     const unsigned int grid = (unsigned int)((warps + kDbWarps - 1) / kDbWarps);
-    switch (S) {
-    case 8: bounce_synth_kernel<8><<<grid, kDbWarps * 32, 0, s>>>(vf, off, total, fac, vel64, state, F, rd, W, out, out_c64, records); break;
-    case 4: bounce_synth_kernel<4><<<grid, kDbWarps * 32, 0, s>>>(vf, off, total, fac, vel64, state, F, rd, W, out, out_c64, records); break;
-    case 2: bounce_synth_kernel<2><<<grid, kDbWarps * 32, 0, s>>>(vf, off, total, fac, vel64, state, F, rd, W, out, out_c64, records); break;
-    default: bounce_synth_kernel<1><<<grid, kDbWarps * 32, 0, s>>>(vf, off, total, fac, vel64, state, F, rd, W, out, out_c64, records); break;
+    const dim3 blk(kDbWarps * 32);
+#define BART_DB_LAUNCH(K, SS) K<SS><<<grid, blk, 0, s>>>(vf, txoff, fac, vel64, state, F, rd, W, out, out_c64, records)
+    if (fp32_eval) {
+        switch (S) {
+        case 16: BART_DB_LAUNCH(bounce_synth_f32_kernel, 16); break;
+        case 8: BART_DB_LAUNCH(bounce_synth_f32_kernel, 8); break;
+        case 4: BART_DB_LAUNCH(bounce_synth_f32_kernel, 4); break;
+        case 2: BART_DB_LAUNCH(bounce_synth_f32_kernel, 2); break;
+        default: BART_DB_LAUNCH(bounce_synth_f32_kernel, 1); break;
+        }
+    } else {
+        switch (S) {
+        case 8: BART_DB_LAUNCH(bounce_synth_kernel, 8); break;
+        case 4: BART_DB_LAUNCH(bounce_synth_kernel, 4); break;
+        case 2: BART_DB_LAUNCH(bounce_synth_kernel, 2); break;
+        default: BART_DB_LAUNCH(bounce_synth_kernel, 1); break;
+        }
     }
+#undef BART_DB_LAUNCH
 }
 
 }  // namespace bart

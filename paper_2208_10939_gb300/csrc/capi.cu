@@ -178,6 +178,10 @@ struct bart_ctx {
     DevBuf<int32_t> db_cnt;
     DevBuf<int64_t> db_off, db_blk;
     DevBuf<BounceFacet> db_vf;
+    DevBuf<BounceCand> db_cand;         // candidates (a, b) of every (TX, lit facet a)
+    DevBuf<int32_t> db_pcnt;            // virtual facets per candidate
+    DevBuf<int64_t> db_poff, db_pblk;   // their offsets and scan scratch
+    DevBuf<int64_t> db_txoff;           // first virtual facet of each TX [P + 1]
     int64_t db_n = 0;
     DevBuf<uint32_t> mkeys, skeys;      // batched sort scratch
     int tpi_override = 0;               // synthesis tiles per item (autotuner), 0 = default
@@ -257,6 +261,8 @@ struct bart_ctx {
         det_ws.release(); adj_ws.release(); gfac.release(); d_voff.release(); d_foff.release(); d_root.release(); vstart.release();
         vcnt.release(); mkeys.release(); skeys.release();
         db_cnt.release(); db_off.release(); db_blk.release(); db_vf.release();
+        db_cand.release(); db_pcnt.release(); db_poff.release(); db_pblk.release();
+        db_txoff.release();
         if (count_host) cudaFreeHost(count_host);
     }
 };
@@ -816,30 +822,55 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
                                ctx->vcnt.p, s);
             launches += 1;
         }
-        // 3b. double-bounce virtual facets: count, scan, read the total
-        // (a host synchronisation: frame graphs are off with double bounce),
-        // allocate, fill
+        // 3b. double-bounce virtual facets, in two passes, each a count, a
+        // scan, a host read of the total (frame graphs are off with double
+        // bounce), an allocation and a fill: the candidates (a, b) of each
+        // (TX, lit facet a), then each candidate's virtual facets
         if (bounce) {
             nv.next("bart double bounce");
             const int64_t items = (int64_t)rd.P * F;
             const int64_t tw = bounce_scan_words(items);
             if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_db[0], s), "cudaEventRecord");
-            launch_bounce_count(ctx->tri64.p, ctx->fac.p, ctx->vel64.p, ctx->nodes.p,
-                                ctx->state.p, ctx->vis_idx.p, ctx->vis_cnt.p, F, rd,
-                                ctx->db_cnt.p, ctx->db_off.p, ctx->db_blk.p, ctx->status.p, s);
+            launch_bounce_candidates(false, ctx->tri64.p, ctx->fac.p, ctx->vel64.p, ctx->nodes.p,
+                                     ctx->state.p, ctx->vis_idx.p, ctx->vis_cnt.p, F, rd,
+                                     ctx->db_cnt.p, nullptr, nullptr, ctx->status.p, s);
+            launch_bounce_scan(ctx->db_cnt.p, items, ctx->db_off.p, ctx->db_blk.p, s);
+            int64_t ncand = 0;
+            CUDA_TRY(cudaMemcpyAsync(&ncand, ctx->db_blk.p + tw - 1, sizeof ncand,
+                                     cudaMemcpyDeviceToHost, s), "double-bounce count copy");
+            CUDA_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+            const int64_t pw = bounce_scan_words(ncand);
+            BART_TRY(ctx->db_cand.ensure((size_t)std::max<int64_t>(ncand, 1), "double-bounce candidates"));
+            BART_TRY(ctx->db_pcnt.ensure((size_t)std::max<int64_t>(ncand, 1), "double-bounce piece counts"));
+            BART_TRY(ctx->db_poff.ensure((size_t)std::max<int64_t>(ncand, 1), "double-bounce piece offsets"));
+            BART_TRY(ctx->db_pblk.ensure((size_t)pw, "double-bounce scan"));
+            BART_TRY(ctx->db_txoff.ensure((size_t)rd.P + 1, "double-bounce TX offsets"));
+            if (ncand > 0) {
+                launch_bounce_candidates(true, ctx->tri64.p, ctx->fac.p, ctx->vel64.p,
+                                         ctx->nodes.p, ctx->state.p, ctx->vis_idx.p,
+                                         ctx->vis_cnt.p, F, rd, nullptr, ctx->db_off.p,
+                                         ctx->db_cand.p, ctx->status.p, s);
+                launch_bounce_pairs(false, ctx->tri64.p, ctx->fac.p, ctx->vel64.p, ctx->nodes.p,
+                                    ctx->state.p, ctx->db_cand.p, ncand, F, rd, ctx->db_pcnt.p,
+                                    nullptr, nullptr, ctx->status.p, s);
+            }
+            launch_bounce_scan(ctx->db_pcnt.p, ncand, ctx->db_poff.p, ctx->db_pblk.p, s);
             int64_t total = 0;
-            CUDA_TRY(cudaMemcpyAsync(&total, ctx->db_blk.p + tw - 1, sizeof total,
+            CUDA_TRY(cudaMemcpyAsync(&total, ctx->db_pblk.p + pw - 1, sizeof total,
                                      cudaMemcpyDeviceToHost, s), "double-bounce count copy");
             CUDA_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
             ctx->db_n = total;
-            launches += 4;
+            launches += 4 + (ncand > 0 ? 2 : 0) + (ncand > 0 ? 3 : 1);
             if (total > 0) {
                 BART_TRY(ctx->db_vf.ensure((size_t)total, "double-bounce virtual facets"));
-                launch_bounce_fill(ctx->tri64.p, ctx->fac.p, ctx->vel64.p, ctx->nodes.p,
-                                   ctx->state.p, ctx->vis_idx.p, ctx->vis_cnt.p, F, rd,
-                                   ctx->db_off.p, ctx->db_vf.p, ctx->status.p, s);
+                launch_bounce_pairs(true, ctx->tri64.p, ctx->fac.p, ctx->vel64.p, ctx->nodes.p,
+                                    ctx->state.p, ctx->db_cand.p, ncand, F, rd, ctx->db_pcnt.p,
+                                    ctx->db_poff.p, ctx->db_vf.p, ctx->status.p, s);
                 launches += 1;
             }
+            launch_bounce_tx_offsets(ctx->db_off.p, ctx->db_blk.p + tw - 1, ctx->db_poff.p,
+                                     ctx->db_pblk.p + pw - 1, F, rd.P, ctx->db_txoff.p, s);
+            launches += 1;
             if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_db[1], s), "cudaEventRecord");
         } else {
             ctx->db_n = 0;
@@ -929,10 +960,9 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
         if (bounce && ctx->db_n > 0) {
             nv.next("bart double-bounce synthesis");
             if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_db[2], s), "cudaEventRecord");
-            launch_bounce_synth(ctx->db_vf.p, ctx->db_off.p,
-                                ctx->db_blk.p + bounce_scan_words((int64_t)rd.P * F) - 1,
-                                ctx->fac.p, ctx->vel64.p, ctx->state.p, F, rd, adc,
-                                dtype == BART_C64, ctx->counters.p + 4, s);
+            launch_bounce_synth(ctx->db_vf.p, ctx->db_txoff.p, ctx->fac.p, ctx->vel64.p, ctx->state.p, F, rd, adc,
+                                dtype == BART_C64, path != BART_PATH_FP64,
+                                ctx->counters.p + 4, s);
             if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_db[3], s), "cudaEventRecord");
             launches += 1;
         }

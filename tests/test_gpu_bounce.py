@@ -145,6 +145,28 @@ def test_fp32_paths_with_double_bounce_match_oracle(sim, name, path):
     assert e <= TOL_MIXED
 
 
+@pytest.mark.parametrize("name", ["dihedral_tdm_30deg", "fine_ground", "car_ground"])
+@pytest.mark.parametrize("path", [pkg.PATH_MIXED, pkg.PATH_SPECTRAL])
+def test_fp32_double_bounce_part_matches_oracle(sim, name, path):
+    """The double-bounce part alone (the cube with double bounce minus the
+    cube without, the single-bounce part being the same launch sequence in
+    both) against the oracle's double-bounce entries: the FP64 records and
+    FP32 phasors of the mixed and spectral paths within 1e-4 of that part."""
+    sc, fr, ref = case(name)
+    bref = fr.bounce_entries(np.argwhere(np.ones(ref.shape, bool))).reshape(ref.shape)
+    sim.load_scene(sc)
+    on = sim.simulate(path).cpu().numpy().astype(np.complex128)
+    sc.radar.double_bounce = False
+    try:
+        sim.load_scene(sc)
+        off = sim.simulate(path).cpu().numpy().astype(np.complex128)
+    finally:
+        sc.radar.double_bounce = True
+    e = rel_l2(on - off, bref)
+    print(f"{name} path {path}: double-bounce part relL2 {e:.3e}")
+    assert e <= TOL_MIXED
+
+
 def test_dihedral_closed_form_through_the_c_abi(sim):
     """A 0.1 m dihedral 300 m out on its bisector, monostatic: the
     double-bounce part of every ADC sample (the frame with double bounce
