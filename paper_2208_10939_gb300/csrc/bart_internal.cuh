@@ -267,12 +267,26 @@ void launch_bounce_tx_offsets(const int64_t *cand_off, const int64_t *ncand, con
                               const int64_t *npieces, int64_t F, int P, int64_t *txoff,
                               cudaStream_t s);
 // adds the double-bounce echo of every channel into the cube, the
-// per-sample work in FP32 (fp32_eval: FP64 records, FP32 phasors) or in
-// FP64; records: counter of (virtual facet, channel, chirp) records, or NULL
+// per-sample work in FP32 (fp32_eval: records from slow-time rows, FP32
+// phasors, the record lists cut into NCH chunks whose partial sums a
+// reduction adds in order) or in FP64; records: counter of (virtual facet,
+// channel, chirp) records, or NULL
 void launch_bounce_synth(const BounceFacet *vf, const int64_t *txoff, const FacetRec *fac,
                          const double *vel64, const uint8_t *state,
                          int64_t F, const RadarDev &rd, void *out, int out_c64,
-                         bool fp32_eval, unsigned long long *records, cudaStream_t s);
+                         bool fp32_eval, const void *rows, const void *geo, int NCH,
+                         double2 *partial, unsigned long long *records, cudaStream_t s);
+// chunks per record list of the FP32 evaluation; with more than one,
+// launch_bounce_synth needs partial: chunks x O x N x M double2
+int bounce_synth_chunks(const RadarDev &rd);
+// the FP32 evaluation's per-frame data: slow-time rows of each virtual
+// facet's 1 + Q legs (bounce_row_bytes per facet) and its FP32 geometry
+// (bounce_geo_bytes per facet)
+int64_t bounce_row_bytes(const RadarDev &rd);
+int64_t bounce_geo_bytes();
+void launch_bounce_rows(const BounceFacet *vf, int64_t V, const FacetRec *fac,
+                        const double *vel64, const RadarDev &rd, void *rows, void *geo,
+                        cudaStream_t s);
 
 // ---- additive noise (noise.cu) ----
 int64_t noise_scratch_words();   // doubles

@@ -36,6 +36,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "bart_internal.cuh"
 #include "geom64.cuh"
 #include "record_fp64.cuh"
@@ -45,6 +47,12 @@ namespace bart {
 namespace {
 
 constexpr int kDbMaxV = 7;          // a triangle clipped by four half-spaces
+
+// the middle chirp slot's start time (the rows' expansion point)
+__host__ __device__ inline double bounce_mid_time(const RadarDev &rd)
+{
+    return 0.5 * (double)(rd.N * rd.slots - 1) * rd.Tc;
+}
 constexpr double kDbSliver = 1e-6;  // fan pieces with |cross| <= this |n_b| are dropped
 
 __device__ __forceinline__ void centroid3(const double *t, double *c)
@@ -108,21 +116,40 @@ __device__ void beam_planes(const double *ta, int side_a, const double *img, dou
     }
 }
 
-// whether a node box may hold points of every half-space (conservative: the
-// margin covers the clip's rounding, far below it)
-__device__ __forceinline__ bool box_meets_beam(const float *bmin, const float *bmax,
-                                               const double *g, const double *base)
+// The beam's four half-spaces rounded to FP32 for the traversal's box
+// culling, each with the size sum_r |g_r| that scales its margin
+struct Beam32 {
+    float g[12], base[12], gs[4];
+};
+
+__device__ __forceinline__ void beam_to_f32(const double *g, const double *base, Beam32 &b)
 {
+    for (int i = 0; i < 12; ++i) {
+        b.g[i] = (float)g[i];
+        b.base[i] = (float)base[i];
+    }
+    for (int h = 0; h < 4; ++h)
+        b.gs[h] = fabsf(b.g[3 * h]) + fabsf(b.g[3 * h + 1]) + fabsf(b.g[3 * h + 2]);
+}
+
+// box_meets_beam in FP32: a box is skipped only when its farthest corner
+// lies outside a half-space by more than 1e-5 sum_r |g_r| (|x_r| + |base_r|),
+// which covers the FP32 rounding of g, base and the sum (a few 1e-7 of that
+// size) and the FP64 test's own margin with room to spare
+__device__ __forceinline__ bool box_meets_beam32(const float *bmin, const float *bmax,
+                                                 const Beam32 &B)
+{
+#pragma unroll
     for (int h = 0; h < 4; ++h) {
-        const double *gh = g + 3 * h, *bh = base + 3 * h;
-        double f = 0.0, scale = 1.0, gs = 0.0;
+        const float *gh = B.g + 3 * h, *bh = B.base + 3 * h;
+        float f = 0.f, scale = 1.f;
+#pragma unroll
         for (int r = 0; r < 3; ++r) {
-            const double x = gh[r] >= 0.0 ? (double)bmax[r] : (double)bmin[r];
-            f += gh[r] * (x - bh[r]);
-            gs += fabs(gh[r]);
-            scale = fmax(scale, fmax(fabs(x), fabs(bh[r])));
+            const float x = gh[r] >= 0.f ? bmax[r] : bmin[r];
+            f = fmaf(gh[r], x - bh[r], f);
+            scale = fmaxf(scale, fabsf(x) + fabsf(bh[r]));
         }
-        if (f < -1e-9 * gs * scale) return false;
+        if (f < -1e-5f * B.gs[h] * scale) return false;
     }
     return true;
 }
@@ -269,6 +296,8 @@ bounce_cand_kernel(const double *__restrict__ tri64, const FacetRec *__restrict_
     const int side_a = state[(int64_t)p * F + a] == BART_VIS_LIT ? 1 : -1;
     double g[12], base[12];
     beam_planes(ta, side_a, img, g, base);
+    Beam32 bm;
+    beam_to_f32(g, base, bm);
     int32_t count = 0;
     int64_t slot = FILL ? off[item] : 0;
     int stack[kStack];
@@ -277,8 +306,8 @@ bounce_cand_kernel(const double *__restrict__ tri64, const FacetRec *__restrict_
     while (sp > 0) {
         const BvhNode nd = nodes[stack[--sp]];
         const int ch[2] = {nd.left, nd.right};
-        const bool hh[2] = {box_meets_beam(nd.lmin, nd.lmax, g, base),
-                            box_meets_beam(nd.rmin, nd.rmax, g, base)};
+        const bool hh[2] = {box_meets_beam32(nd.lmin, nd.lmax, bm),
+                            box_meets_beam32(nd.rmin, nd.rmax, bm)};
         for (int c = 0; c < 2; ++c) {
             if (!hh[c]) continue;
             if (ch[c] >= 0) {
@@ -601,30 +630,67 @@ bounce_synth_kernel(const BounceFacet *__restrict__ vf, const int64_t *__restric
     }
 }
 
-// FP32 form of a vertex-form record for one (channel, chirp): the phase of
-// vertex v at sample m is A_v + B_v m + C m^2 cycles (the path to second
-// order in fast time; the third-order term stays below 1e-12 m over a
-// chirp), B_v = Bhi_v + Blo_v with Bhi_v a multiple of 2^-14 (so that
-// Bhi_v m is exact in FP32 for m < 2^10) and |Blo_v| <= 2^-15; wt_v the
-// vertex weight of the facet integral (record_fp64.cuh)
+// FP32 form of a record for one (channel, chirp).  Every form is a sum of
+// phasors exp{j 2 pi (theta(m) - f_m u_c / c)} over its centres u_c (the
+// vertex form: the vertices; the edge form: the edge midpoints; the series
+// form: the vertices' mean) with amplitudes from x; the phase of centre c at
+// sample m is A_c + B_c m + C m^2 cycles (the path to second order in fast
+// time; the third-order term stays below 1e-12 m over a chirp), B_c = Bhi_c
+// + Blo_c with Bhi_c a multiple of 2^-14 (so that Bhi_c m is exact in FP32
+// for m < 2^10) and |Blo_c| <= 2^-15.  x: vertex form, the vertex weights
+// (x[0..2]); series form, the 15 coefficients of the polynomials in k_m^2
+// (record_fp64.cuh's d[1..15]); edge form, k0 gamma_e (x[0..2]) and the edge
+// amplitudes (x[3..5]), with flags bit e: sinc by its series.
 struct RecV {
-    float A[3], Bhi[3], Blo[3], wt[3];
+    float A[3], Bhi[3], Blo[3];
     float C;
-    int vertex;                // 1: use this form; 0: the FP64 record (series / edge form)
+    float x[15];
+    int kind, flags;
 };
 
 __device__ __forceinline__ double red1d(double x) { return x - rint(x); }
 __device__ __forceinline__ float red1f(float x) { return x - rintf(x); }
 
-// the vertex phases' quadratics from the FP64 record R: each leg's path
-// sqrt(q0 + q1 t + q2 t^2) expanded to L0 + L1 t + L2 t^2, the phase
-// f(t) L(t) / c - mu L(t)^2 / (2 c^2) of Eq. 13 to second order, the
-// vertex terms' -f(t) u_v / c added
-__device__ __forceinline__ void vertex_quadratics(const RecB &R, const RadarDev &rd, RecV &V)
+// the phase constants of Eq. 13 for the quadratics, formed once
+struct PhaseK {
+    double f0c, muc, mu2c2, inv_fs, inv_fs2, mucfs;
+};
+__device__ __forceinline__ PhaseK phase_consts(const RadarDev &rd)
 {
-    V.vertex = R.kind == kRecVertex;
-    if (!V.vertex) return;
-    const double c = kC0, f0 = rd.f0, mu = rd.slope, fs = rd.fs;
+    PhaseK P;
+    P.f0c = rd.f0 / kC0;
+    P.muc = rd.slope / kC0;
+    P.mu2c2 = rd.slope / (2.0 * kC0 * kC0);
+    P.inv_fs = 1.0 / rd.fs;
+    P.inv_fs2 = P.inv_fs * P.inv_fs;
+    P.mucfs = P.muc * P.inv_fs;
+    return P;
+}
+
+// the phase f(t) L(t) / c - mu L(t)^2 / (2 c^2) of Eq. 13 over the fast
+// time, L = L0 + L1 t + L2 t^2, as th0 + th1 m + th2 m^2 (cycles, samples m);
+// then centre c's A_c, Bhi_c, Blo_c and the common C
+__device__ __forceinline__ void path_phase(double L0, double L1, double L2, const PhaseK &K,
+                                           double &th0, double &th1, double &th2)
+{
+    th0 = K.f0c * L0 - K.mu2c2 * L0 * L0;
+    th1 = (K.f0c * L1 + K.muc * L0 - 2.0 * K.mu2c2 * L0 * L1) * K.inv_fs;
+    th2 = (K.f0c * L2 + K.muc * L1 - K.mu2c2 * (L1 * L1 + 2.0 * L0 * L2)) * K.inv_fs2;
+}
+__device__ __forceinline__ void centre_phase(double th0, double th1, double u, const PhaseK &K,
+                                             RecV &V, int c)
+{
+    V.A[c] = (float)red1d(th0 - K.f0c * u);
+    const double b = red1d(th1 - K.mucfs * u);
+    const double bhi = rint(b * 16384.0) * 0x1p-14;
+    V.Bhi[c] = (float)bhi;
+    V.Blo[c] = (float)(b - bhi);
+}
+
+// RecV of a full FP64 record: each leg's path sqrt(q0 + q1 t + q2 t^2)
+// expanded to second order, the centres and amplitudes rounded to FP32
+__device__ __forceinline__ void rec64_to_v(const RecB &R, const PhaseK &K, RecV &V)
+{
     double L0 = 0.0, L1 = 0.0, L2 = 0.0;
     const double *qs[2] = {R.qt, R.qr};
     for (int l = 0; l < 2; ++l) {
@@ -636,44 +702,265 @@ __device__ __forceinline__ void vertex_quadratics(const RecB &R, const RadarDev 
         L1 += a1;
         L2 += (q[2] - a1 * a1) * inv;
     }
-    const double f0c = f0 / c, muc = mu / c, mu2c2 = mu / (2.0 * c * c);
-    const double th0 = f0c * L0 - mu2c2 * L0 * L0;
-    const double th1 = (f0c * L1 + muc * L0 - 2.0 * mu2c2 * L0 * L1) / fs;
-    const double th2 = (f0c * L2 + muc * L1 - mu2c2 * (L1 * L1 + 2.0 * L0 * L2)) / (fs * fs);
-    const double mucfs = muc / fs;
-    for (int v = 0; v < 3; ++v) {
-        const double u = R.d[v];
-        V.A[v] = (float)red1d(th0 - f0c * u);
-        const double b = red1d(th1 - mucfs * u);
-        const double bhi = rint(b * 16384.0) / 16384.0;
-        V.Bhi[v] = (float)bhi;
-        V.Blo[v] = (float)(b - bhi);
-        V.wt[v] = (float)R.d[3 + v];
-    }
+    double th0, th1, th2;
+    path_phase(L0, L1, L2, K, th0, th1, th2);
     V.C = (float)th2;
+    V.kind = R.kind;
+    V.flags = R.flags;
+    if (R.kind == kRecVertex) {
+        for (int v = 0; v < 3; ++v) {
+            centre_phase(th0, th1, R.d[v], K, V, v);
+            V.x[v] = (float)R.d[3 + v];
+        }
+    } else if (R.kind == kRecSeries) {
+        centre_phase(th0, th1, R.d[0], K, V, 0);
+        for (int i = 0; i < 15; ++i) V.x[i] = (float)R.d[1 + i];
+    } else {
+        for (int e = 0; e < 3; ++e) {
+            centre_phase(th0, th1, R.d[3 * e], K, V, e);
+            V.x[e] = (float)R.d[3 * e + 1];
+            V.x[3 + e] = (float)R.d[3 * e + 2];
+        }
+    }
 }
 
-// The double-bounce synthesis with the per-sample work in FP32: records in
-// FP64 as above (one per lane, 32 per batch), vertex-form records evaluated
+// Slow-time row of one leg of a virtual facet: the path from the facet's
+// centroid to the leg's antenna (the image source for the TX leg, RX q for
+// leg 1 + q) as R(t_c + tau) = sum_j a_j tau^j about the frame's middle
+// chirp slot t_c.  R^2 is exactly the quadratic |D_c + w tau|^2 (both ends
+// move linearly), so the a_j follow from the square-root recursion, and
+// with rho = tau_max |w| / R(t_c) the terms beyond degree 6 are bounded by
+// R rho^7 / (1 - rho); a row whose bound exceeds 1e-11 m is marked a[0] = -1
+// (its records take the full FP64 build).  B = antenna - centroid at the
+// frame start and w = centroid velocity relative to the antenna give the
+// directions in FP32 from the constant B and the small drift -w t.
+constexpr int kDbDeg = 6;
+struct BounceRow {
+    double a[kDbDeg + 1];
+    float B[3], w[3];
+};
+// per virtual facet: unit normal, area and vertex offsets from the centroid
+struct BounceGeo {
+    float n[3], area, dv[9], pad[3];
+};
+
+__global__ void bounce_rows_kernel(const BounceFacet *__restrict__ vf, int64_t V,
+                                   const FacetRec *__restrict__ fac,
+                                   const double *__restrict__ vel64, RadarDev rd, double tc,
+                                   double tmax, BounceRow *__restrict__ rows,
+                                   BounceGeo *__restrict__ geo)
+{
+    const int L = 1 + rd.Q;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= V * L) return;
+    const int64_t v = i / L;
+    const int l = (int)(i % L);
+    const BounceFacet &B = vf[v];
+    double c0[3];
+    for (int r = 0; r < 3; ++r) c0[r] = (B.tri[r] + B.tri[3 + r] + B.tri[6 + r]) / 3.0;
+    const double *vb = vel64 + 3 * fac[B.b].inst;
+    double P[3], w[3];
+    for (int r = 0; r < 3; ++r) {
+        P[r] = l == 0 ? B.src[r] : rd.ant[rd.P + l - 1][r];
+        w[r] = l == 0 ? vb[r] - B.usrc[r] : vb[r];
+    }
+    double Dc[3];
+    for (int r = 0; r < 3; ++r) Dc[r] = (c0[r] - P[r]) + w[r] * tc;
+    const double q0 = Dc[0] * Dc[0] + Dc[1] * Dc[1] + Dc[2] * Dc[2];
+    const double q1 = 2.0 * (Dc[0] * w[0] + Dc[1] * w[1] + Dc[2] * w[2]);
+    const double q2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    BounceRow &R = rows[i];
+    const double a0 = sqrt(q0);
+    const double rho = tmax * sqrt(q2 / q0);
+    bool ok = q0 > 0.0 && rho < 0.25;
+    if (ok) {
+        double b = a0;
+        for (int j = 0; j <= kDbDeg; ++j) b *= rho;
+        ok = b / (1.0 - rho) <= 1e-11;
+    }
+    double a[kDbDeg + 1];
+    a[0] = ok ? a0 : -1.0;
+    const double inv2a0 = 0.5 / a0;
+    for (int j = 1; j <= kDbDeg; ++j) {
+        double s = j == 1 ? q1 : (j == 2 ? q2 : 0.0);
+        for (int k = 1; k < j; ++k) s -= a[k] * a[j - k];
+        a[j] = ok ? s * inv2a0 : 0.0;
+    }
+    for (int j = 0; j <= kDbDeg; ++j) R.a[j] = a[j];
+    for (int r = 0; r < 3; ++r) {
+        R.B[r] = (float)(P[r] - c0[r]);
+        R.w[r] = (float)w[r];
+    }
+    if (l == 0) {
+        BounceGeo &G = geo[v];
+        double e1[3], e2[3], n[3];
+        for (int r = 0; r < 3; ++r) {
+            e1[r] = B.tri[3 + r] - B.tri[r];
+            e2[r] = B.tri[6 + r] - B.tri[r];
+        }
+        n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+        n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+        n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+        const double nl = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        for (int r = 0; r < 3; ++r) G.n[r] = (float)(n[r] / nl);
+        G.area = (float)(0.5 * nl);
+        for (int k = 0; k < 9; ++k) G.dv[k] = (float)(B.tri[k] - c0[k % 3]);
+        G.pad[0] = G.pad[1] = G.pad[2] = 0.f;
+    }
+}
+
+// R, dR/dt and d2R/dt2 of a row at tau
+__device__ __forceinline__ void row_eval(const BounceRow &R, double tau, double &r0, double &r1,
+                                         double &r2)
+{
+    r0 = R.a[kDbDeg];
+    r1 = kDbDeg * R.a[kDbDeg];
+    r2 = kDbDeg * (kDbDeg - 1) * R.a[kDbDeg];
+    for (int j = kDbDeg - 1; j >= 0; --j) {
+        r0 = fma(r0, tau, R.a[j]);
+        if (j >= 1) r1 = fma(r1, tau, j * R.a[j]);
+        if (j >= 2) r2 = fma(r2, tau, j * (j - 1) * R.a[j]);
+    }
+}
+
+// 1 / n! in FP32 for the series form (n = 2 .. 16)
+__device__ __forceinline__ float inv_fact_f(int n)
+{
+    float f = 1.f;
+    for (int i = 2; i <= n; ++i) f *= (float)i;
+    return 1.f / f;
+}
+
+// The FP32 record of a virtual facet from its rows: FP64 only for the path
+// and the phase quadratics; directions, obliquity, projections and every
+// form's amplitudes in FP32 (record_fp64.cuh's forms and switches, with the
+// in-plane pair differences bt.(dv_a - dv_b) formed directly so that close
+// projections keep their relative accuracy).  Returns false when a row has
+// no expansion (the record then takes the full FP64 build).
+__device__ __forceinline__ bool lean_record(const BounceRow &Rt, const BounceRow &Rr,
+                                            const BounceGeo &G, float wrho, int two_sided,
+                                            double tau, float tn, const RadarDev &rd,
+                                            const PhaseK &K, float k0, float kmax, RecV &V)
+{
+    if (Rt.a[0] < 0.0 || Rr.a[0] < 0.0) return false;
+    double t0, t1, t2, s0, s1, s2;
+    row_eval(Rt, tau, t0, t1, t2);
+    row_eval(Rr, tau, s0, s1, s2);
+    float th[3], rh[3];
+    {
+        float dt[3], dr[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            dt[r] = fmaf(-Rt.w[r], tn, Rt.B[r]);
+            dr[r] = fmaf(-Rr.w[r], tn, Rr.B[r]);
+        }
+        const float it = rsqrtf(dt[0] * dt[0] + dt[1] * dt[1] + dt[2] * dt[2]);
+        const float ir = rsqrtf(dr[0] * dr[0] + dr[1] * dr[1] + dr[2] * dr[2]);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            th[r] = dt[r] * it;
+            rh[r] = dr[r] * ir;
+        }
+    }
+    const float b[3] = {th[0] + rh[0], th[1] + rh[1], th[2] + rh[2]};
+    const float bn = G.n[0] * b[0] + G.n[1] * b[1] + G.n[2] * b[2];
+    float ok = 0.5f * bn;
+    if (two_sided) ok = fabsf(ok);
+    const float g = __fdividef(wrho * ok, (float)t0 * (float)s0);
+    const float bt[3] = {b[0] - bn * G.n[0], b[1] - bn * G.n[1], b[2] - bn * G.n[2]};
+    float u[3], d[3];     // u_v, and d_v = u_v - u_{v+1} from the edge vectors
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+        const int w = (v + 1) % 3;
+        u[v] = bt[0] * G.dv[3 * v] + bt[1] * G.dv[3 * v + 1] + bt[2] * G.dv[3 * v + 2];
+        d[v] = bt[0] * (G.dv[3 * v] - G.dv[3 * w]) + bt[1] * (G.dv[3 * v + 1] - G.dv[3 * w + 1]) +
+               bt[2] * (G.dv[3 * v + 2] - G.dv[3 * w + 2]);
+    }
+    const float umin = fminf(fminf(u[0], u[1]), u[2]), umax = fmaxf(fmaxf(u[0], u[1]), u[2]);
+    const float dmin = fminf(fminf(fabsf(d[0]), fabsf(d[1])), fabsf(d[2]));
+    const float A2 = 2.f * G.area * g;
+    double th0, th1, th2;
+    path_phase(t0 + s0, rd.intra ? t1 + s1 : 0.0, rd.intra ? 0.5 * (t2 + s2) : 0.0, K, th0, th1,
+               th2);
+    V.C = (float)th2;
+    V.flags = 0;
+    if (kmax * (umax - umin) < (float)kSeriesKD) {
+        // series form: J = sum_p j^p h_p(y) / (p + 2)!  with y_v = k (u_v - ub)
+        const float y0 = k0 * (d[0] - d[2]) * (1.f / 3.f);
+        const float y1 = k0 * (d[1] - d[0]) * (1.f / 3.f);
+        const float y2 = k0 * (d[2] - d[1]) * (1.f / 3.f);
+        const float e2s = y0 * y1 + y0 * y2 + y1 * y2, e3s = y0 * y1 * y2;
+        float h[kSeriesTerms];
+        h[0] = 1.f;
+        h[1] = 0.f;
+        h[2] = -e2s;
+#pragma unroll
+        for (int q = 3; q < kSeriesTerms; ++q) h[q] = -e2s * h[q - 2] + e3s * h[q - 3];
+        const float sc = A2 * k0 * k0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) V.x[i] = ((i & 1) ? -sc : sc) * h[2 * i] * inv_fact_f(2 * i + 2);
+#pragma unroll
+        for (int i = 0; i < 7; ++i)
+            V.x[8 + i] = ((i & 1) ? sc : -sc) * h[2 * i + 1] * inv_fact_f(2 * i + 3);
+        centre_phase(th0, th1, (double)((u[0] + u[1] + u[2]) * (1.f / 3.f)), K, V, 0);
+        V.kind = kRecSeries;
+        return true;
+    }
+    if (kmax * dmin < (float)kEdgeKd) {
+        // edge form: J = sum_e (-j) k gamma_e-scaled sinc terms at the edge midpoints
+        const float bt2 = bt[0] * bt[0] + bt[1] * bt[1] + bt[2] * bt[2];
+        const float nxb[3] = {G.n[1] * bt[2] - G.n[2] * bt[1], G.n[2] * bt[0] - G.n[0] * bt[2],
+                              G.n[0] * bt[1] - G.n[1] * bt[0]};
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const int i1 = (i + 1) % 3;
+            const float e[3] = {G.dv[3 * i1] - G.dv[3 * i], G.dv[3 * i1 + 1] - G.dv[3 * i + 1],
+                                G.dv[3 * i1 + 2] - G.dv[3 * i + 2]};
+            const float gam = -0.5f * d[i];
+            V.x[i] = k0 * gam;
+            V.x[3 + i] = k0 * g * (e[0] * nxb[0] + e[1] * nxb[1] + e[2] * nxb[2]) / bt2;
+            if (kmax * fabsf(gam) < (float)kSincSeries) V.flags |= 1 << i;
+            centre_phase(th0, th1, (double)(0.5f * (u[i] + u[i1])), K, V, i);
+        }
+        V.kind = kRecEdge;
+        return true;
+    }
+    // vertex form: -A2 / ((u_v - u_{v+1}) (u_v - u_{v+2})) = A2 / (d_v d_{v+2})
+    V.x[0] = A2 / (d[0] * d[2]);
+    V.x[1] = A2 / (d[1] * d[0]);
+    V.x[2] = A2 / (d[2] * d[1]);
+#pragma unroll
+    for (int v = 0; v < 3; ++v) centre_phase(th0, th1, (double)u[v], K, V, v);
+    V.kind = kRecVertex;
+    return true;
+}
+
+// The double-bounce synthesis with the per-sample work in FP32: records
+// from the virtual facets' slow-time rows (lean_record; the full FP64 build,
+// rounded to the same FP32 form, where a row has no expansion), one per
+// lane, 32 per batch, records of every form evaluated
 // by every lane over its S samples from an FP32 start phasor and its chord
 // step (the curvature C (S - 1)^2 / 4 cycles, below 1e-5, is left out),
-// batch sums in FP32 added to FP64 totals; series- and edge-form records by
-// the FP64 evaluation.
+// the amplitudes of the series and edge forms per sample; batch sums in
+// FP32 added to FP64 totals.
 template <int S>
 __global__ void __launch_bounds__(kDbWarps * 32)
 bounce_synth_f32_kernel(const BounceFacet *__restrict__ vf, const int64_t *__restrict__ txoff,
                         const FacetRec *__restrict__ fac, const double *__restrict__ vel64,
                         const uint8_t *__restrict__ state, int64_t F, RadarDev rd, int W,
-                        void *out, int out_c64, unsigned long long *records)
+                        void *out, int out_c64, unsigned long long *records,
+                        const BounceRow *__restrict__ rows, const BounceGeo *__restrict__ geo,
+                        double tc, int NCH, double2 *__restrict__ partial)
 {
     __shared__ RecB sR[kDbWarps][32];
     __shared__ RecV sV[kDbWarps][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t gw = (int64_t)blockIdx.x * kDbWarps + warp;
     const int N = rd.N;
-    if (gw >= (int64_t)rd.O * N * W) return;
-    const int seg = (int)(gw % W);
-    const int64_t unit = gw / W;
+    if (gw >= (int64_t)rd.O * N * W * NCH) return;
+    const int chunk = (int)(gw % NCH);
+    const int seg = (int)(gw / NCH % W);
+    const int64_t unit = gw / ((int64_t)NCH * W);
     const int o = (int)(unit / N), n = (int)(unit % N);
     const int p = o / rd.Q, q = o % rd.Q;
     const int m0 = (seg * 32 + lane) * S;
@@ -683,10 +970,14 @@ bounce_synth_f32_kernel(const BounceFacet *__restrict__ vf, const int64_t *__res
     const double tn = (double)((int64_t)n * rd.slots + (rd.tdm ? p : 0)) * rd.Tc;
     const double *prx = rd.ant[rd.P + q];
     const uint8_t *st_r = state + (int64_t)(rd.P + q) * F;
-    const int64_t v0 = txoff[p], v1 = txoff[p + 1];
-    const double inv_fs = 1.0 / fs, inv_c = 1.0 / c, inv_f0 = 1.0 / f0;
-    const double mu_2c2 = mu / (2.0 * c * c);
+    // this warp's chunk of the virtual facets of TX p
+    const int64_t vt0 = txoff[p], nv = txoff[p + 1] - vt0;
+    const int64_t v0 = vt0 + nv * chunk / NCH, v1 = vt0 + nv * (chunk + 1) / NCH;
     const float fm0 = (float)m0, fm0sq = fm0 * fm0, chord = 2.f * fm0 + (float)(S - 1);
+    const PhaseK PK = phase_consts(rd);
+
+    const float kps = (float)(mu / (f0 * fs));       // k_m / k_0 = 1 + kps m
+    const float k0f = (float)k0, kmaxf = (float)kmax;
 
     double accr[S], acci[S];
 #pragma unroll
@@ -699,65 +990,101 @@ bounce_synth_f32_kernel(const BounceFacet *__restrict__ vf, const int64_t *__res
             const BounceFacet &B = vf[v];
             valid = st_r[B.b] == (B.side > 0 ? BART_VIS_LIT : BART_VIS_LIT_REV);
             if (valid) {
-                build_rec64(B, vel64 + 3 * fac[B.b].inst, tn, prx, rd, k0, kmax,
-                            fac[B.b].two_sided, sR[warp][lane]);
-                vertex_quadratics(sR[warp][lane], rd, sV[warp][lane]);
+                const int L = 1 + rd.Q;
+                const bool lean = lean_record(rows[v * L], rows[v * L + 1 + q], geo[v],
+                                              (float)B.w, fac[B.b].two_sided, tn - tc,
+                                              (float)tn, rd, PK, k0f, kmaxf, sV[warp][lane]);
+                if (!lean) {
+                    build_rec64(B, vel64 + 3 * fac[B.b].inst, tn, prx, rd, k0, kmax,
+                                fac[B.b].two_sided, sR[warp][lane]);
+                    rec64_to_v(sR[warp][lane], PK, sV[warp][lane]);
+                }
             }
         }
         __syncwarp();
-        const unsigned int mask = __ballot_sync(0xffffffffu, valid);
-        const unsigned int vmask = __ballot_sync(0xffffffffu, valid && sV[warp][lane].vertex);
+        unsigned int mask = __ballot_sync(0xffffffffu, valid);
         nrec += __popc(mask);
         float ar[S], ai[S];
 #pragma unroll
         for (int j = 0; j < S; ++j) ar[j] = ai[j] = 0.f;
-        unsigned int m = vmask;
-        while (m) {
-            const int i = __ffs(m) - 1;
-            m &= m - 1;
+        while (mask) {
+            const int i = __ffs(mask) - 1;
+            mask &= mask - 1;
             const RecV &V = sV[warp][i];
+            const int nc = V.kind == kRecSeries ? 1 : 3;
             float zc[3], zs[3], cs[3], ss[3];
 #pragma unroll
             for (int e = 0; e < 3; ++e) {
+                if (e >= nc) break;
                 const float ph = red1f(red1f(V.Bhi[e] * fm0) +
                                        (V.A[e] + fmaf(V.Blo[e], fm0, V.C * fm0sq)));
                 sincospif(2.f * ph, &zs[e], &zc[e]);
                 const float st = red1f(V.Bhi[e] + fmaf(V.C, chord, V.Blo[e]));
                 sincospif(2.f * st, &ss[e], &cs[e]);
             }
+            if (V.kind == kRecVertex) {
 #pragma unroll
-            for (int j = 0; j < S; ++j) {
-                float tr = 0.f, ti = 0.f;
+                for (int j = 0; j < S; ++j) {
+                    float tr = 0.f, ti = 0.f;
 #pragma unroll
-                for (int e = 0; e < 3; ++e) {
-                    tr = fmaf(V.wt[e], zc[e], tr);
-                    ti = fmaf(V.wt[e], zs[e], ti);
-                    const float nc = fmaf(zc[e], cs[e], -zs[e] * ss[e]);
-                    zs[e] = fmaf(zc[e], ss[e], zs[e] * cs[e]);
-                    zc[e] = nc;
+                    for (int e = 0; e < 3; ++e) {
+                        tr = fmaf(V.x[e], zc[e], tr);
+                        ti = fmaf(V.x[e], zs[e], ti);
+                        const float ncs = fmaf(zc[e], cs[e], -zs[e] * ss[e]);
+                        zs[e] = fmaf(zc[e], ss[e], zs[e] * cs[e]);
+                        zc[e] = ncs;
+                    }
+                    ar[j] += tr;
+                    ai[j] += ti;
                 }
-                ar[j] += tr;
-                ai[j] += ti;
+            } else if (V.kind == kRecSeries) {
+#pragma unroll
+                for (int j = 0; j < S; ++j) {
+                    const float kp = fmaf(kps, fm0 + (float)j, 1.f), k2 = kp * kp;
+                    float a = V.x[7], bb = V.x[14];
+#pragma unroll
+                    for (int e = 6; e >= 0; --e) a = fmaf(a, k2, V.x[e]);
+#pragma unroll
+                    for (int e = 5; e >= 0; --e) bb = fmaf(bb, k2, V.x[8 + e]);
+                    const float pr = a * k2, pi = bb * k2 * kp;
+                    ar[j] += fmaf(zc[0], pr, -zs[0] * pi);
+                    ai[j] += fmaf(zc[0], pi, zs[0] * pr);
+                    const float ncs = fmaf(zc[0], cs[0], -zs[0] * ss[0]);
+                    zs[0] = fmaf(zc[0], ss[0], zs[0] * cs[0]);
+                    zc[0] = ncs;
+                }
+            } else {
+#pragma unroll 1
+                for (int j = 0; j < S; ++j) {
+                    const float kp = fmaf(kps, fm0 + (float)j, 1.f);
+                    float tr = 0.f, ti = 0.f;
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) {
+                        const float xx = kp * V.x[e];
+                        float sn;
+                        if (V.flags & (1 << e)) {
+                            const float x2 = xx * xx;
+                            sn = 1.f + x2 * (-1.f / 6 + x2 * (1.f / 120 + x2 * (-1.f / 5040 +
+                                 x2 * (1.f / 362880))));
+                        } else {
+                            sn = sinf(xx) / xx;
+                        }
+                        const float coef = kp * V.x[3 + e] * sn;
+                        tr = fmaf(-coef, zs[e], tr);
+                        ti = fmaf(coef, zc[e], ti);
+                        const float ncs = fmaf(zc[e], cs[e], -zs[e] * ss[e]);
+                        zs[e] = fmaf(zc[e], ss[e], zs[e] * cs[e]);
+                        zc[e] = ncs;
+                    }
+                    ar[j] += tr;
+                    ai[j] += ti;
+                }
             }
         }
 #pragma unroll
         for (int j = 0; j < S; ++j) {
             accr[j] += (double)ar[j];
             acci[j] += (double)ai[j];
-        }
-        m = mask & ~vmask;
-        while (m) {
-            const int i = __ffs(m) - 1;
-            m &= m - 1;
-            const RecB &R = sR[warp][i];
-#pragma unroll 1
-            for (int j = 0; j < S; ++j) {
-                const double t = (double)(m0 + j) * inv_fs;
-                double re, im;
-                eval_rec64(R, t, f0 + mu * t, inv_c, inv_f0, mu_2c2, re, im);
-                accr[j] += re;
-                acci[j] += im;
-            }
         }
         __syncwarp();
     }
@@ -769,7 +1096,10 @@ bounce_synth_f32_kernel(const BounceFacet *__restrict__ vf, const int64_t *__res
         const double fm = f0 + mu * (double)(m0 + j) / fs;
         const double km = 2.0 * kPi * fm / c;
         const double sc = camp / (km * km);
-        if (out_c64) {
+        if (NCH > 1) {         // this chunk's scaled partial sums, added in order later
+            partial[(int64_t)chunk * rd.O * N * rd.M + row + j] =
+                make_double2(accr[j] * sc, acci[j] * sc);
+        } else if (out_c64) {
             float2 &y = reinterpret_cast<float2 *>(out)[row + j];
             y.x += (float)(accr[j] * sc);
             y.y += (float)(acci[j] * sc);
@@ -781,9 +1111,35 @@ bounce_synth_f32_kernel(const BounceFacet *__restrict__ vf, const int64_t *__res
     }
 }
 
+// adds the chunks' partial sums of each sample, in chunk order, into the cube
+__global__ void bounce_reduce_kernel(const double2 *__restrict__ partial, int64_t n, int NCH,
+                                     void *out, int out_c64)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double re = 0.0, im = 0.0;
+    for (int ch = 0; ch < NCH; ++ch) {
+        const double2 v = partial[(int64_t)ch * n + i];
+        re += v.x;
+        im += v.y;
+    }
+    if (out_c64) {
+        float2 &y = reinterpret_cast<float2 *>(out)[i];
+        y.x += (float)re;
+        y.y += (float)im;
+    } else {
+        double2 &y = reinterpret_cast<double2 *>(out)[i];
+        y.x += re;
+        y.y += im;
+    }
+}
+
 }  // namespace
 
 int64_t bounce_scan_words(int64_t n) { return (n + kScanBlk - 1) / kScanBlk + 1; }
+
+int64_t bounce_row_bytes(const RadarDev &rd) { return (int64_t)sizeof(BounceRow) * (1 + rd.Q); }
+int64_t bounce_geo_bytes() { return (int64_t)sizeof(BounceGeo); }
 
 void launch_bounce_scan(const int32_t *cnt, int64_t n, int64_t *off, int64_t *blk,
                         cudaStream_t s)
@@ -834,9 +1190,41 @@ void launch_bounce_tx_offsets(const int64_t *cand_off, const int64_t *ncand, con
     bounce_tx_offsets_kernel<<<1, 64, 0, s>>>(cand_off, ncand, poff, npieces, F, P, txoff);
 }
 
+void launch_bounce_rows(const BounceFacet *vf, int64_t V, const FacetRec *fac,
+                        const double *vel64, const RadarDev &rd, void *rows, void *geo,
+                        cudaStream_t s)
+{
+    if (V <= 0) return;
+    const double tc = bounce_mid_time(rd);
+    const int64_t n = V * (1 + rd.Q);
+    bounce_rows_kernel<<<(unsigned int)((n + 127) / 128), 128, 0, s>>>(
+        vf, V, fac, vel64, rd, tc, tc > 0.0 ? tc : rd.Tc, static_cast<BounceRow *>(rows),
+        static_cast<BounceGeo *>(geo));
+}
+
+// chunks of each (channel, chirp, segment) record list of the FP32
+// evaluation: about four waves of resident warps (a sedan frame has a few
+// thousand (channel, chirp) rows), at most 16
+int bounce_synth_chunks(const RadarDev &rd)
+{
+    static int sms = 0;
+    if (sms <= 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    int S = 16;
+    while ((rd.M / 32) % S) S /= 2;
+    const int64_t rows = (int64_t)rd.O * rd.N * (rd.M / (32 * S));
+    const int64_t target = 4 * (int64_t)sms * 12;     // ~12 resident warps per SM
+    return (int)std::max<int64_t>(1, std::min<int64_t>(16, (target + rows - 1) / rows));
+}
+
 void launch_bounce_synth(const BounceFacet *vf, const int64_t *txoff, const FacetRec *fac,
                          const double *vel64, const uint8_t *state, int64_t F,
                          const RadarDev &rd, void *out, int out_c64, bool fp32_eval,
+                         const void *rows, const void *geo, int NCH, double2 *partial,
                          unsigned long long *records, cudaStream_t s)
 {
     const int M = rd.M;                // a multiple of 32
@@ -846,26 +1234,38 @@ void launch_bounce_synth(const BounceFacet *vf, const int64_t *txoff, const Face
     while ((M / 32) % S) S /= 2;
     const int W = M / (32 * S);
     const int64_t warps = (int64_t)rd.O * rd.N * W;
-    const unsigned int grid = (unsigned int)((warps + kDbWarps - 1) / kDbWarps);
     const dim3 blk(kDbWarps * 32);
-#define BART_DB_LAUNCH(K, SS) K<SS><<<grid, blk, 0, s>>>(vf, txoff, fac, vel64, state, F, rd, W, out, out_c64, records)
-    if (fp32_eval) {
+    if (!fp32_eval) {
+        const unsigned int grid = (unsigned int)((warps + kDbWarps - 1) / kDbWarps);
+#define BART_DB_LAUNCH64(SS) bounce_synth_kernel<SS><<<grid, blk, 0, s>>>(vf, txoff, fac, vel64, state, F, rd, W, out, out_c64, records)
         switch (S) {
-        case 16: BART_DB_LAUNCH(bounce_synth_f32_kernel, 16); break;
-        case 8: BART_DB_LAUNCH(bounce_synth_f32_kernel, 8); break;
-        case 4: BART_DB_LAUNCH(bounce_synth_f32_kernel, 4); break;
-        case 2: BART_DB_LAUNCH(bounce_synth_f32_kernel, 2); break;
-        default: BART_DB_LAUNCH(bounce_synth_f32_kernel, 1); break;
+        case 8: BART_DB_LAUNCH64(8); break;
+        case 4: BART_DB_LAUNCH64(4); break;
+        case 2: BART_DB_LAUNCH64(2); break;
+        default: BART_DB_LAUNCH64(1); break;
         }
-    } else {
-        switch (S) {
-        case 8: BART_DB_LAUNCH(bounce_synth_kernel, 8); break;
-        case 4: BART_DB_LAUNCH(bounce_synth_kernel, 4); break;
-        case 2: BART_DB_LAUNCH(bounce_synth_kernel, 2); break;
-        default: BART_DB_LAUNCH(bounce_synth_kernel, 1); break;
-        }
+#undef BART_DB_LAUNCH64
+        return;
     }
-#undef BART_DB_LAUNCH
+    if (NCH < 1 || !partial) NCH = 1;
+    const BounceRow *R = static_cast<const BounceRow *>(rows);
+    const BounceGeo *G = static_cast<const BounceGeo *>(geo);
+    const double tc = bounce_mid_time(rd);
+    const unsigned int grid = (unsigned int)((warps * NCH + kDbWarps - 1) / kDbWarps);
+#define BART_DB_LAUNCH32(SS) bounce_synth_f32_kernel<SS><<<grid, blk, 0, s>>>(vf, txoff, fac, vel64, state, F, rd, W, out, out_c64, records, R, G, tc, NCH, partial)
+    switch (S) {
+    case 16: BART_DB_LAUNCH32(16); break;
+    case 8: BART_DB_LAUNCH32(8); break;
+    case 4: BART_DB_LAUNCH32(4); break;
+    case 2: BART_DB_LAUNCH32(2); break;
+    default: BART_DB_LAUNCH32(1); break;
+    }
+#undef BART_DB_LAUNCH32
+    if (NCH > 1) {
+        const int64_t n = (int64_t)rd.O * rd.N * M;
+        bounce_reduce_kernel<<<(unsigned int)((n + 255) / 256), 256, 0, s>>>(partial, n, NCH,
+                                                                           out, out_c64);
+    }
 }
 
 }  // namespace bart

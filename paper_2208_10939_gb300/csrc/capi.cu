@@ -182,6 +182,8 @@ struct bart_ctx {
     DevBuf<int32_t> db_pcnt;            // virtual facets per candidate
     DevBuf<int64_t> db_poff, db_pblk;   // their offsets and scan scratch
     DevBuf<int64_t> db_txoff;           // first virtual facet of each TX [P + 1]
+    DevBuf<unsigned char> db_rows;      // FP32 evaluation: slow-time rows and geometry
+    DevBuf<double2> db_part;            // FP32 evaluation: the chunks' partial sums
     int64_t db_n = 0;
     DevBuf<uint32_t> mkeys, skeys;      // batched sort scratch
     int tpi_override = 0;               // synthesis tiles per item (autotuner), 0 = default
@@ -262,7 +264,7 @@ struct bart_ctx {
         vcnt.release(); mkeys.release(); skeys.release();
         db_cnt.release(); db_off.release(); db_blk.release(); db_vf.release();
         db_cand.release(); db_pcnt.release(); db_poff.release(); db_pblk.release();
-        db_txoff.release();
+        db_txoff.release(); db_rows.release(); db_part.release();
         if (count_host) cudaFreeHost(count_host);
     }
 };
@@ -867,6 +869,19 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
                                     ctx->state.p, ctx->db_cand.p, ncand, F, rd, ctx->db_pcnt.p,
                                     ctx->db_poff.p, ctx->db_vf.p, ctx->status.p, s);
                 launches += 1;
+                if (path != BART_PATH_FP64) {
+                    BART_TRY(ctx->db_rows.ensure((size_t)(total * (bounce_row_bytes(rd) +
+                                                                   bounce_geo_bytes())),
+                                                 "double-bounce rows"));
+                    const int nch = bounce_synth_chunks(rd);
+                    if (nch > 1)
+                        BART_TRY(ctx->db_part.ensure((size_t)nch * O * rd.N * rd.M,
+                                                     "double-bounce partial sums"));
+                    launch_bounce_rows(ctx->db_vf.p, total, ctx->fac.p, ctx->vel64.p, rd,
+                                       ctx->db_rows.p + total * bounce_geo_bytes(),
+                                       ctx->db_rows.p, s);
+                    launches += 1;
+                }
             }
             launch_bounce_tx_offsets(ctx->db_off.p, ctx->db_blk.p + tw - 1, ctx->db_poff.p,
                                      ctx->db_pblk.p + pw - 1, F, rd.P, ctx->db_txoff.p, s);
@@ -962,9 +977,11 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
             if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_db[2], s), "cudaEventRecord");
             launch_bounce_synth(ctx->db_vf.p, ctx->db_txoff.p, ctx->fac.p, ctx->vel64.p, ctx->state.p, F, rd, adc,
                                 dtype == BART_C64, path != BART_PATH_FP64,
-                                ctx->counters.p + 4, s);
+                                ctx->db_rows.p + ctx->db_n * bounce_geo_bytes(), ctx->db_rows.p,
+                                path != BART_PATH_FP64 ? bounce_synth_chunks(rd) : 1,
+                                ctx->db_part.p, ctx->counters.p + 4, s);
             if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_db[3], s), "cudaEventRecord");
-            launches += 1;
+            launches += (path != BART_PATH_FP64 && bounce_synth_chunks(rd) > 1) ? 2 : 1;
         }
         ctx->timed_bounce = tm && bounce;
         if (tm) CUDA_TRY(cudaEventRecord(ctx->ev[4], s), "cudaEventRecord");
