@@ -171,6 +171,33 @@ __device__ __forceinline__ void image_of(const double *ta, const double *pt, con
     for (int r = 0; r < 3; ++r) u[r] = __dmul_rn(su, na[r]);
 }
 
+// whether b certainly does not face the image (so that facing_image would
+// return 0): FP32 from the rounded unit normal and centroid of the facet
+// record, whose errors (~1e-7 in the normal, ~1e-7 relative in the
+// centroid, so ~2e-6 / |D| in the direction) stay far inside the margin;
+// slivers and two-sided facets always take the FP64 test
+__device__ __forceinline__ bool surely_faces_away(const FacetRec &fr, const double *img,
+                                                  double eps_face)
+{
+    if (fr.two_sided) return false;
+    float L2 = 0.f;
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+        const float x = fr.dv[3 * v], y = fr.dv[3 * v + 1], z = fr.dv[3 * v + 2];
+        L2 = fmaxf(L2, fmaf(x, x, fmaf(y, y, z * z)));
+    }
+    if (2.f * fr.area < 4e-6f * L2) return false;
+    const float D[3] = {(float)img[0] - fr.c[0], (float)img[1] - fr.c[1], (float)img[2] - fr.c[2]};
+    const float dd = fmaf(D[0], D[0], fmaf(D[1], D[1], D[2] * D[2]));
+    if (!(dd > 0.f)) return false;
+    const float inv = rsqrtf(dd);
+    const float cs = fmaf(fr.n[0], D[0], fmaf(fr.n[1], D[1], fr.n[2] * D[2])) * inv;
+    const float scale = fmaxf(fmaxf(fabsf(fr.c[0]), fabsf(fr.c[1])), fabsf(fr.c[2])) +
+                        fmaxf(fmaxf(fabsf((float)img[0]), fabsf((float)img[1])),
+                              fabsf((float)img[2]));
+    return cs < -((float)eps_face + 2e-5f + 4e-7f * scale * inv);
+}
+
 // the side of b that faces the image (+1 front, -1 reverse of a two-sided
 // b), 0 when it does not face it beyond eps_face
 __device__ __forceinline__ int facing_image(const double *tb, const double *img, bool two_sided,
@@ -317,6 +344,7 @@ bounce_cand_kernel(const double *__restrict__ tri64, const FacetRec *__restrict_
             }
             const int64_t b = ~ch[c];
             if (b == a) continue;
+            if (surely_faces_away(fac[b], img, rd.eps_face)) continue;
             double nbb;
             const int side_b = facing_image(tri64 + 9 * b, img, fac[b].two_sided != 0,
                                             rd.eps_face, &nbb);
@@ -457,6 +485,10 @@ __global__ void scan_add_kernel(int64_t *__restrict__ out, int64_t n,
 
 // ---- synthesis ----------------------------------------------------------
 constexpr int kDbWarps = 4;
+// resident blocks per SM the FP32 synthesis is compiled for (a register
+// cap): measured on the sedan-over-ground frame, 2 (218 registers) 78 ms,
+// 3 (168) 69 ms, 4 (128, a few spills) 64 ms, 5 and 6 no faster
+constexpr int kDbF32Blocks = 4;
 
 struct RecB {
     double qt[3], qr[3];       // R_t(t)^2 and R_r(t)^2 over the fast time
@@ -944,7 +976,7 @@ __device__ __forceinline__ bool lean_record(const BounceRow &Rt, const BounceRow
 // the amplitudes of the series and edge forms per sample; batch sums in
 // FP32 added to FP64 totals.
 template <int S>
-__global__ void __launch_bounds__(kDbWarps * 32)
+__global__ void __launch_bounds__(kDbWarps * 32, kDbF32Blocks)
 bounce_synth_f32_kernel(const BounceFacet *__restrict__ vf, const int64_t *__restrict__ txoff,
                         const FacetRec *__restrict__ fac, const double *__restrict__ vel64,
                         const uint8_t *__restrict__ state, int64_t F, RadarDev rd, int W,
@@ -952,7 +984,6 @@ bounce_synth_f32_kernel(const BounceFacet *__restrict__ vf, const int64_t *__res
                         const BounceRow *__restrict__ rows, const BounceGeo *__restrict__ geo,
                         double tc, int NCH, double2 *__restrict__ partial)
 {
-    __shared__ RecB sR[kDbWarps][32];
     __shared__ RecV sV[kDbWarps][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t gw = (int64_t)blockIdx.x * kDbWarps + warp;
@@ -995,9 +1026,10 @@ bounce_synth_f32_kernel(const BounceFacet *__restrict__ vf, const int64_t *__res
                                               (float)B.w, fac[B.b].two_sided, tn - tc,
                                               (float)tn, rd, PK, k0f, kmaxf, sV[warp][lane]);
                 if (!lean) {
+                    RecB R64;
                     build_rec64(B, vel64 + 3 * fac[B.b].inst, tn, prx, rd, k0, kmax,
-                                fac[B.b].two_sided, sR[warp][lane]);
-                    rec64_to_v(sR[warp][lane], PK, sV[warp][lane]);
+                                fac[B.b].two_sided, R64);
+                    rec64_to_v(R64, PK, sV[warp][lane]);
                 }
             }
         }
