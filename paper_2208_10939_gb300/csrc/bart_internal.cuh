@@ -248,13 +248,18 @@ int64_t bounce_scan_words(int64_t n);
 // exclusive scan of n int32 counts into off, the total into blk[bounce_scan_words(n) - 1]
 void launch_bounce_scan(const int32_t *cnt, int64_t n, int64_t *off, int64_t *blk,
                         cudaStream_t s);
-// pass 1 over the (TX p, i-th facet lit from p) items, P F of them: the
-// candidates per item into cnt (count), or the candidates at off (fill)
+// subtrees NS (1, 2, 4 or 8) the candidate traversal splits the LBVH into,
+// and their roots (NS ints)
+int bounce_subtrees(const RadarDev &rd, int64_t F);
+void launch_bounce_roots(const BvhNode *nodes, int64_t F, int NS, int32_t *roots, cudaStream_t s);
+// pass 1 over the (TX p, i-th facet lit from p, subtree) items, P F NS of
+// them: the candidates per item into cnt (count), or the candidates at off
+// (fill)
 void launch_bounce_candidates(bool fill, const double *tri64, const FacetRec *fac,
                               const double *vel64, const BvhNode *nodes, const uint8_t *state,
                               const int32_t *vis_idx, const int32_t *vis_cnt, int64_t F,
-                              const RadarDev &rd, int32_t *cnt, const int64_t *off,
-                              BounceCand *cand, int *status, cudaStream_t s);
+                              const RadarDev &rd, int NS, const int32_t *roots, int32_t *cnt,
+                              const int64_t *off, BounceCand *cand, int *status, cudaStream_t s);
 // pass 2 over the candidates: the virtual facets per candidate into pcnt
 // (count: clip, slivers, the a -> b leg), or written at poff (fill)
 void launch_bounce_pairs(bool fill, const double *tri64, const FacetRec *fac,
@@ -264,7 +269,7 @@ void launch_bounce_pairs(bool fill, const double *tri64, const FacetRec *fac,
                          cudaStream_t s);
 // txoff[p] (p <= P): the first virtual facet of TX p (txoff[P] = all of them)
 void launch_bounce_tx_offsets(const int64_t *cand_off, const int64_t *ncand, const int64_t *poff,
-                              const int64_t *npieces, int64_t F, int P, int64_t *txoff,
+                              const int64_t *npieces, int64_t F, int P, int NS, int64_t *txoff,
                               cudaStream_t s);
 // adds the double-bounce echo of every channel into the cube, the
 // per-sample work in FP32 (fp32_eval: records from slow-time rows, FP32

@@ -37,6 +37,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <climits>
 
 #include "bart_internal.cuh"
 #include "geom64.cuh"
@@ -294,24 +295,57 @@ __device__ bool leg_blocked(const double *poly, int K, const double *ta, const d
     return false;
 }
 
-// Pass 1, one thread per item (p, i): TX p, a = the i-th facet lit from TX
-// p.  a's beam through the LBVH; every facet b != a in a box that meets the
-// beam and facing the image is a candidate (count, or write (a, b, p, side)
-// at the item's offset).
+// the roots of the NS subtrees the candidate traversal splits the LBVH
+// into: the nodes log2(NS) levels below the root, a leaf standing in for
+// itself and leaving its missing descendants kNoNode
+constexpr int kNoNode = INT32_MIN;
+__global__ void bounce_roots_kernel(const BvhNode *__restrict__ nodes, int64_t F, int NS,
+                                    int32_t *__restrict__ roots)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int32_t cur[8], nxt[8];
+    cur[0] = F >= 2 ? 0 : kNoNode;
+    int n = 1;
+    while (n < NS) {
+        for (int k = 0; k < n; ++k) {
+            const int32_t r = cur[k];
+            if (r >= 0) {
+                nxt[2 * k] = nodes[r].left;
+                nxt[2 * k + 1] = nodes[r].right;
+            } else {
+                nxt[2 * k] = r;
+                nxt[2 * k + 1] = kNoNode;
+            }
+        }
+        n *= 2;
+        for (int k = 0; k < n; ++k) cur[k] = nxt[k];
+    }
+    for (int k = 0; k < NS; ++k) roots[k] = cur[k];
+}
+
+// Pass 1, one thread per item (p, i, s): TX p, a = the i-th facet lit from
+// TX p, subtree s of the LBVH.  a's beam through the subtree; every facet
+// b != a in a box that meets the beam and facing the image is a candidate
+// (count, or write (a, b, p, side) at the item's offset).  Several subtrees
+// per facet spread the long traversals of facets whose beams cross many
+// boxes over several threads when the items alone would not fill the GPU.
 template <bool FILL>
 __global__ void __launch_bounds__(128)
 bounce_cand_kernel(const double *__restrict__ tri64, const FacetRec *__restrict__ fac,
                    const double *__restrict__ vel64, const BvhNode *__restrict__ nodes,
                    const uint8_t *__restrict__ state, const int32_t *__restrict__ vis_idx,
-                   const int32_t *__restrict__ vis_cnt, int64_t F, RadarDev rd,
-                   int32_t *__restrict__ cnt, const int64_t *__restrict__ off,
-                   BounceCand *__restrict__ cand, int *status)
+                   const int32_t *__restrict__ vis_cnt, int64_t F, RadarDev rd, int NS,
+                   const int32_t *__restrict__ roots, int32_t *__restrict__ cnt,
+                   const int64_t *__restrict__ off, BounceCand *__restrict__ cand, int *status)
 {
     const int p = blockIdx.y;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= F) return;
-    const int64_t item = (int64_t)p * F + i;
-    if (i >= vis_cnt[rd.O + p] || F < 2) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= F * NS) return;
+    const int64_t i = idx / NS;
+    const int sub = (int)(idx % NS);
+    const int64_t item = ((int64_t)p * F + i) * NS + sub;   // (TX, facet, subtree)
+    const int root = roots[sub];
+    if (i >= vis_cnt[rd.O + p] || F < 2 || root == kNoNode) {
         if (!FILL) cnt[item] = 0;
         return;
     }
@@ -327,30 +361,36 @@ bounce_cand_kernel(const double *__restrict__ tri64, const FacetRec *__restrict_
     beam_to_f32(g, base, bm);
     int32_t count = 0;
     int64_t slot = FILL ? off[item] : 0;
-    int stack[kStack];
-    int sp = 0;
-    stack[sp++] = 0;
-    while (sp > 0) {
-        const BvhNode nd = nodes[stack[--sp]];
-        const int ch[2] = {nd.left, nd.right};
-        const bool hh[2] = {box_meets_beam32(nd.lmin, nd.lmax, bm),
-                            box_meets_beam32(nd.rmin, nd.rmax, bm)};
-        for (int c = 0; c < 2; ++c) {
-            if (!hh[c]) continue;
-            if (ch[c] >= 0) {
-                if (sp < kStack) stack[sp++] = ch[c];
-                else atomicOr(status, kStatusStackOverflow);
-                continue;
+    // a leaf b met by the beam: a candidate when it faces the image
+    auto leaf = [&](int64_t b) {
+        if (b == a || surely_faces_away(fac[b], img, rd.eps_face)) return;
+        double nbb;
+        const int side_b = facing_image(tri64 + 9 * b, img, fac[b].two_sided != 0,
+                                        rd.eps_face, &nbb);
+        if (!side_b) return;
+        if (FILL) cand[slot++] = BounceCand{(int32_t)a, (int32_t)b, p, side_b};
+        ++count;
+    };
+    if (root < 0) {
+        leaf(~(int64_t)root);            // a subtree that is one facet (no box test)
+    } else {
+        int stack[kStack];
+        int sp = 0;
+        stack[sp++] = root;
+        while (sp > 0) {
+            const BvhNode nd = nodes[stack[--sp]];
+            const int ch[2] = {nd.left, nd.right};
+            const bool hh[2] = {box_meets_beam32(nd.lmin, nd.lmax, bm),
+                                box_meets_beam32(nd.rmin, nd.rmax, bm)};
+            for (int c = 0; c < 2; ++c) {
+                if (!hh[c]) continue;
+                if (ch[c] >= 0) {
+                    if (sp < kStack) stack[sp++] = ch[c];
+                    else atomicOr(status, kStatusStackOverflow);
+                    continue;
+                }
+                leaf(~(int64_t)ch[c]);
             }
-            const int64_t b = ~ch[c];
-            if (b == a) continue;
-            if (surely_faces_away(fac[b], img, rd.eps_face)) continue;
-            double nbb;
-            const int side_b = facing_image(tri64 + 9 * b, img, fac[b].two_sided != 0,
-                                            rd.eps_face, &nbb);
-            if (!side_b) continue;
-            if (FILL) cand[slot++] = BounceCand{(int32_t)a, (int32_t)b, p, side_b};
-            ++count;
         }
     }
     if (!FILL) cnt[item] = count;
@@ -418,11 +458,11 @@ __global__ void bounce_tx_offsets_kernel(const int64_t *__restrict__ cand_off,
                                          const int64_t *__restrict__ ncand,
                                          const int64_t *__restrict__ poff,
                                          const int64_t *__restrict__ npieces, int64_t F, int P,
-                                         int64_t *__restrict__ txoff)
+                                         int NS, int64_t *__restrict__ txoff)
 {
     const int p = threadIdx.x;
     if (p > P) return;
-    const int64_t c = p < P ? cand_off[(int64_t)p * F] : *ncand;
+    const int64_t c = p < P ? cand_off[(int64_t)p * F * NS] : *ncand;
     txoff[p] = c < *ncand ? poff[c] : *npieces;
 }
 
@@ -1182,20 +1222,35 @@ void launch_bounce_scan(const int32_t *cnt, int64_t n, int64_t *off, int64_t *bl
     if (nblk > 0) scan_add_kernel<<<(unsigned int)nblk, kScanBlk, 0, s>>>(off, n, blk);
 }
 
+int bounce_subtrees(const RadarDev &rd, int64_t F)
+{
+    const int64_t items = (int64_t)rd.P * F;
+    int NS = 1;
+    while (NS < 8 && items * NS < (1 << 21)) NS *= 2;
+    return NS;
+}
+
+void launch_bounce_roots(const BvhNode *nodes, int64_t F, int NS, int32_t *roots, cudaStream_t s)
+{
+    bounce_roots_kernel<<<1, 32, 0, s>>>(nodes, F, NS, roots);
+}
+
 void launch_bounce_candidates(bool fill, const double *tri64, const FacetRec *fac,
                               const double *vel64, const BvhNode *nodes, const uint8_t *state,
                               const int32_t *vis_idx, const int32_t *vis_cnt, int64_t F,
-                              const RadarDev &rd, int32_t *cnt, const int64_t *off,
-                              BounceCand *cand, int *status, cudaStream_t s)
+                              const RadarDev &rd, int NS, const int32_t *roots, int32_t *cnt,
+                              const int64_t *off, BounceCand *cand, int *status, cudaStream_t s)
 {
     const int T = 128;
-    dim3 grid((unsigned int)((F + T - 1) / T), (unsigned int)rd.P);
+    dim3 grid((unsigned int)((F * NS + T - 1) / T), (unsigned int)rd.P);
     if (fill)
         bounce_cand_kernel<true><<<grid, T, 0, s>>>(tri64, fac, vel64, nodes, state, vis_idx,
-                                                    vis_cnt, F, rd, cnt, off, cand, status);
+                                                    vis_cnt, F, rd, NS, roots, cnt, off, cand,
+                                                    status);
     else
         bounce_cand_kernel<false><<<grid, T, 0, s>>>(tri64, fac, vel64, nodes, state, vis_idx,
-                                                     vis_cnt, F, rd, cnt, off, cand, status);
+                                                     vis_cnt, F, rd, NS, roots, cnt, off, cand,
+                                                     status);
 }
 
 void launch_bounce_pairs(bool fill, const double *tri64, const FacetRec *fac,
@@ -1216,10 +1271,10 @@ void launch_bounce_pairs(bool fill, const double *tri64, const FacetRec *fac,
 }
 
 void launch_bounce_tx_offsets(const int64_t *cand_off, const int64_t *ncand, const int64_t *poff,
-                              const int64_t *npieces, int64_t F, int P, int64_t *txoff,
+                              const int64_t *npieces, int64_t F, int P, int NS, int64_t *txoff,
                               cudaStream_t s)
 {
-    bounce_tx_offsets_kernel<<<1, 64, 0, s>>>(cand_off, ncand, poff, npieces, F, P, txoff);
+    bounce_tx_offsets_kernel<<<1, 64, 0, s>>>(cand_off, ncand, poff, npieces, F, P, NS, txoff);
 }
 
 void launch_bounce_rows(const BounceFacet *vf, int64_t V, const FacetRec *fac,

@@ -176,6 +176,7 @@ struct bart_ctx {
     // double bounce: pieces per (TX, lit facet) item, their offsets, the scan
     // scratch (its last word the total) and the virtual facets of the frame
     DevBuf<int32_t> db_cnt;
+    DevBuf<int32_t> db_roots;           // the candidate traversal's subtree roots
     DevBuf<int64_t> db_off, db_blk;
     DevBuf<BounceFacet> db_vf;
     DevBuf<BounceCand> db_cand;         // candidates (a, b) of every (TX, lit facet a)
@@ -264,7 +265,7 @@ struct bart_ctx {
         vcnt.release(); mkeys.release(); skeys.release();
         db_cnt.release(); db_off.release(); db_blk.release(); db_vf.release();
         db_cand.release(); db_pcnt.release(); db_poff.release(); db_pblk.release();
-        db_txoff.release(); db_rows.release(); db_part.release();
+        db_txoff.release(); db_rows.release(); db_part.release(); db_roots.release();
         if (count_host) cudaFreeHost(count_host);
     }
 };
@@ -673,7 +674,8 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
     if (bounce && (B > 1 || path == kPathAdjoint || path == kPathAdjointMixed))
         return fail(BART_EINVAL, "double_bounce: one scene per frame and no adjoint");
     if (bounce) {
-        const int64_t items = (int64_t)rd.P * F;
+        const int64_t items = (int64_t)rd.P * F * bounce_subtrees(rd, F);
+        BART_TRY(ctx->db_roots.ensure(8, "double-bounce subtree roots"));
         BART_TRY(ctx->db_cnt.ensure((size_t)items, "double-bounce counts"));
         BART_TRY(ctx->db_off.ensure((size_t)items, "double-bounce offsets"));
         BART_TRY(ctx->db_blk.ensure((size_t)bounce_scan_words(items), "double-bounce scan"));
@@ -830,12 +832,15 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
         // (TX, lit facet a), then each candidate's virtual facets
         if (bounce) {
             nv.next("bart double bounce");
-            const int64_t items = (int64_t)rd.P * F;
+            const int NS = bounce_subtrees(rd, F);
+            const int64_t items = (int64_t)rd.P * F * NS;
             const int64_t tw = bounce_scan_words(items);
             if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_db[0], s), "cudaEventRecord");
+            launch_bounce_roots(ctx->nodes.p, F, NS, ctx->db_roots.p, s);
             launch_bounce_candidates(false, ctx->tri64.p, ctx->fac.p, ctx->vel64.p, ctx->nodes.p,
-                                     ctx->state.p, ctx->vis_idx.p, ctx->vis_cnt.p, F, rd,
-                                     ctx->db_cnt.p, nullptr, nullptr, ctx->status.p, s);
+                                     ctx->state.p, ctx->vis_idx.p, ctx->vis_cnt.p, F, rd, NS,
+                                     ctx->db_roots.p, ctx->db_cnt.p, nullptr, nullptr,
+                                     ctx->status.p, s);
             launch_bounce_scan(ctx->db_cnt.p, items, ctx->db_off.p, ctx->db_blk.p, s);
             int64_t ncand = 0;
             CUDA_TRY(cudaMemcpyAsync(&ncand, ctx->db_blk.p + tw - 1, sizeof ncand,
@@ -850,8 +855,8 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
             if (ncand > 0) {
                 launch_bounce_candidates(true, ctx->tri64.p, ctx->fac.p, ctx->vel64.p,
                                          ctx->nodes.p, ctx->state.p, ctx->vis_idx.p,
-                                         ctx->vis_cnt.p, F, rd, nullptr, ctx->db_off.p,
-                                         ctx->db_cand.p, ctx->status.p, s);
+                                         ctx->vis_cnt.p, F, rd, NS, ctx->db_roots.p, nullptr,
+                                         ctx->db_off.p, ctx->db_cand.p, ctx->status.p, s);
                 launch_bounce_pairs(false, ctx->tri64.p, ctx->fac.p, ctx->vel64.p, ctx->nodes.p,
                                     ctx->state.p, ctx->db_cand.p, ncand, F, rd, ctx->db_pcnt.p,
                                     nullptr, nullptr, ctx->status.p, s);
@@ -862,7 +867,7 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
                                      cudaMemcpyDeviceToHost, s), "double-bounce count copy");
             CUDA_TRY(cudaStreamSynchronize(s), "cudaStreamSynchronize");
             ctx->db_n = total;
-            launches += 4 + (ncand > 0 ? 2 : 0) + (ncand > 0 ? 3 : 1);
+            launches += 5 + (ncand > 0 ? 2 : 0) + (ncand > 0 ? 3 : 1);
             if (total > 0) {
                 BART_TRY(ctx->db_vf.ensure((size_t)total, "double-bounce virtual facets"));
                 launch_bounce_pairs(true, ctx->tri64.p, ctx->fac.p, ctx->vel64.p, ctx->nodes.p,
@@ -884,7 +889,7 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
                 }
             }
             launch_bounce_tx_offsets(ctx->db_off.p, ctx->db_blk.p + tw - 1, ctx->db_poff.p,
-                                     ctx->db_pblk.p + pw - 1, F, rd.P, ctx->db_txoff.p, s);
+                                     ctx->db_pblk.p + pw - 1, F, rd.P, NS, ctx->db_txoff.p, s);
             launches += 1;
             if (tm) CUDA_TRY(cudaEventRecord(ctx->ev_db[1], s), "cudaEventRecord");
         } else {
