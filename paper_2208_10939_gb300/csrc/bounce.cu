@@ -702,6 +702,9 @@ bounce_synth_kernel(const BounceFacet *__restrict__ vf, const int64_t *__restric
     }
 }
 
+__device__ __forceinline__ double red1d(double x) { return x - rint(x); }
+__device__ __forceinline__ float red1f(float x) { return x - rintf(x); }
+
 // FP32 form of a record for one (channel, chirp).  Every form is a sum of
 // phasors exp{j 2 pi (theta(m) - f_m u_c / c)} over its centres u_c (the
 // vertex form: the vertices; the edge form: the edge midpoints; the series
@@ -716,12 +719,20 @@ bounce_synth_kernel(const BounceFacet *__restrict__ vf, const int64_t *__restric
 struct RecV {
     float A[3], Bhi[3], Blo[3];
     float C;
+    float sc[3], ss[3];      // the chord step of each centre at m0 = 0 (cos, sin)
     float x[15];
     int kind, flags;
 };
 
-__device__ __forceinline__ double red1d(double x) { return x - rint(x); }
-__device__ __forceinline__ float red1f(float x) { return x - rintf(x); }
+// the centres' chord steps exp{j 2 pi (B_c + C (S - 1))} of a lane that
+// starts at m0 = 0 (a lane at m0 multiplies them by exp{j 4 pi C m0})
+__device__ __forceinline__ void chord_steps(RecV &V, float chord0)
+{
+    const int nc = V.kind == kRecSeries ? 1 : 3;
+    for (int c = 0; c < nc; ++c)
+        sincospif(2.f * red1f(V.Bhi[c] + fmaf(V.C, chord0, V.Blo[c])), &V.ss[c], &V.sc[c]);
+}
+
 
 // the phase constants of Eq. 13 for the quadratics, formed once
 struct PhaseK {
@@ -809,6 +820,7 @@ __device__ __forceinline__ void rec64_to_v(const RecB &R, const PhaseK &K, RecV 
 constexpr int kDbDeg = 6;
 struct BounceRow {
     double a[kDbDeg + 1];
+    float af[kDbDeg + 1];    // the same in FP32 (for the derivatives)
     float B[3], w[3];
 };
 // per virtual facet: unit normal, area and vertex offsets from the centroid
@@ -858,7 +870,10 @@ __global__ void bounce_rows_kernel(const BounceFacet *__restrict__ vf, int64_t V
         for (int k = 1; k < j; ++k) s -= a[k] * a[j - k];
         a[j] = ok ? s * inv2a0 : 0.0;
     }
-    for (int j = 0; j <= kDbDeg; ++j) R.a[j] = a[j];
+    for (int j = 0; j <= kDbDeg; ++j) {
+        R.a[j] = a[j];
+        R.af[j] = (float)a[j];
+    }
     for (int r = 0; r < 3; ++r) {
         R.B[r] = (float)(P[r] - c0[r]);
         R.w[r] = (float)w[r];
@@ -881,17 +896,21 @@ __global__ void bounce_rows_kernel(const BounceFacet *__restrict__ vf, int64_t V
     }
 }
 
-// R, dR/dt and d2R/dt2 of a row at tau
-__device__ __forceinline__ void row_eval(const BounceRow &R, double tau, double &r0, double &r1,
-                                         double &r2)
+// R (FP64), dR/dt and d2R/dt2 (FP32: they enter the phase only through
+// the slope's small velocity part and the curvature) of a row at tau
+__device__ __forceinline__ void row_eval(const BounceRow &R, double tau, double &r0, float &r1,
+                                         float &r2)
 {
     r0 = R.a[kDbDeg];
-    r1 = kDbDeg * R.a[kDbDeg];
-    r2 = kDbDeg * (kDbDeg - 1) * R.a[kDbDeg];
-    for (int j = kDbDeg - 1; j >= 0; --j) {
-        r0 = fma(r0, tau, R.a[j]);
-        if (j >= 1) r1 = fma(r1, tau, j * R.a[j]);
-        if (j >= 2) r2 = fma(r2, tau, j * (j - 1) * R.a[j]);
+#pragma unroll
+    for (int j = kDbDeg - 1; j >= 0; --j) r0 = fma(r0, tau, R.a[j]);
+    const float t = (float)tau;
+    r1 = kDbDeg * R.af[kDbDeg];
+    r2 = kDbDeg * (kDbDeg - 1) * R.af[kDbDeg];
+#pragma unroll
+    for (int j = kDbDeg - 1; j >= 1; --j) {
+        r1 = fmaf(r1, t, j * R.af[j]);
+        if (j >= 2) r2 = fmaf(r2, t, j * (j - 1) * R.af[j]);
     }
 }
 
@@ -912,10 +931,12 @@ __device__ __forceinline__ float inv_fact_f(int n)
 __device__ __forceinline__ bool lean_record(const BounceRow &Rt, const BounceRow &Rr,
                                             const BounceGeo &G, float wrho, int two_sided,
                                             double tau, float tn, const RadarDev &rd,
-                                            const PhaseK &K, float k0, float kmax, RecV &V)
+                                            const PhaseK &K, float k0, float kmax,
+                                            float chord0, RecV &V)
 {
     if (Rt.a[0] < 0.0 || Rr.a[0] < 0.0) return false;
-    double t0, t1, t2, s0, s1, s2;
+    double t0, s0;
+    float t1, t2, s1, s2;
     row_eval(Rt, tau, t0, t1, t2);
     row_eval(Rr, tau, s0, s1, s2);
     float th[3], rh[3];
@@ -952,8 +973,8 @@ __device__ __forceinline__ bool lean_record(const BounceRow &Rt, const BounceRow
     const float dmin = fminf(fminf(fabsf(d[0]), fabsf(d[1])), fabsf(d[2]));
     const float A2 = 2.f * G.area * g;
     double th0, th1, th2;
-    path_phase(t0 + s0, rd.intra ? t1 + s1 : 0.0, rd.intra ? 0.5 * (t2 + s2) : 0.0, K, th0, th1,
-               th2);
+    path_phase(t0 + s0, rd.intra ? (double)(t1 + s1) : 0.0,
+               rd.intra ? (double)(0.5f * (t2 + s2)) : 0.0, K, th0, th1, th2);
     V.C = (float)th2;
     V.flags = 0;
     if (kmax * (umax - umin) < (float)kSeriesKD) {
@@ -976,6 +997,7 @@ __device__ __forceinline__ bool lean_record(const BounceRow &Rt, const BounceRow
             V.x[8 + i] = ((i & 1) ? sc : -sc) * h[2 * i + 1] * inv_fact_f(2 * i + 3);
         centre_phase(th0, th1, (double)((u[0] + u[1] + u[2]) * (1.f / 3.f)), K, V, 0);
         V.kind = kRecSeries;
+        chord_steps(V, chord0);
         return true;
     }
     if (kmax * dmin < (float)kEdgeKd) {
@@ -995,6 +1017,7 @@ __device__ __forceinline__ bool lean_record(const BounceRow &Rt, const BounceRow
             centre_phase(th0, th1, (double)(0.5f * (u[i] + u[i1])), K, V, i);
         }
         V.kind = kRecEdge;
+        chord_steps(V, chord0);
         return true;
     }
     // vertex form: -A2 / ((u_v - u_{v+1}) (u_v - u_{v+2})) = A2 / (d_v d_{v+2})
@@ -1004,6 +1027,7 @@ __device__ __forceinline__ bool lean_record(const BounceRow &Rt, const BounceRow
 #pragma unroll
     for (int v = 0; v < 3; ++v) centre_phase(th0, th1, (double)u[v], K, V, v);
     V.kind = kRecVertex;
+    chord_steps(V, chord0);
     return true;
 }
 
@@ -1044,7 +1068,7 @@ bounce_synth_f32_kernel(const BounceFacet *__restrict__ vf, const int64_t *__res
     // this warp's chunk of the virtual facets of TX p
     const int64_t vt0 = txoff[p], nv = txoff[p + 1] - vt0;
     const int64_t v0 = vt0 + nv * chunk / NCH, v1 = vt0 + nv * (chunk + 1) / NCH;
-    const float fm0 = (float)m0, fm0sq = fm0 * fm0, chord = 2.f * fm0 + (float)(S - 1);
+    const float fm0 = (float)m0, fm0sq = fm0 * fm0;
     const PhaseK PK = phase_consts(rd);
 
     const float kps = (float)(mu / (f0 * fs));       // k_m / k_0 = 1 + kps m
@@ -1064,12 +1088,14 @@ bounce_synth_f32_kernel(const BounceFacet *__restrict__ vf, const int64_t *__res
                 const int L = 1 + rd.Q;
                 const bool lean = lean_record(rows[v * L], rows[v * L + 1 + q], geo[v],
                                               (float)B.w, fac[B.b].two_sided, tn - tc,
-                                              (float)tn, rd, PK, k0f, kmaxf, sV[warp][lane]);
+                                              (float)tn, rd, PK, k0f, kmaxf, (float)(S - 1),
+                                              sV[warp][lane]);
                 if (!lean) {
                     RecB R64;
                     build_rec64(B, vel64 + 3 * fac[B.b].inst, tn, prx, rd, k0, kmax,
                                 fac[B.b].two_sided, R64);
                     rec64_to_v(R64, PK, sV[warp][lane]);
+                    chord_steps(sV[warp][lane], (float)(S - 1));
                 }
             }
         }
@@ -1085,14 +1111,18 @@ bounce_synth_f32_kernel(const BounceFacet *__restrict__ vf, const int64_t *__res
             const RecV &V = sV[warp][i];
             const int nc = V.kind == kRecSeries ? 1 : 3;
             float zc[3], zs[3], cs[3], ss[3];
+            // the lane's chord step: the record's at m0 = 0 times
+            // exp{j 4 pi C m0} ~ (1 - x^2 / 2, x), |x| < 1e-2, error x^3 / 6
+            const float x = 12.566370614359172f * V.C * fm0;
+            const float xr = fmaf(-0.5f * x, x, 1.f);
 #pragma unroll
             for (int e = 0; e < 3; ++e) {
                 if (e >= nc) break;
                 const float ph = red1f(red1f(V.Bhi[e] * fm0) +
                                        (V.A[e] + fmaf(V.Blo[e], fm0, V.C * fm0sq)));
                 sincospif(2.f * ph, &zs[e], &zc[e]);
-                const float st = red1f(V.Bhi[e] + fmaf(V.C, chord, V.Blo[e]));
-                sincospif(2.f * st, &ss[e], &cs[e]);
+                cs[e] = fmaf(V.sc[e], xr, -V.ss[e] * x);
+                ss[e] = fmaf(V.sc[e], x, V.ss[e] * xr);
             }
             if (V.kind == kRecVertex) {
 #pragma unroll
