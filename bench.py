@@ -65,12 +65,19 @@ SYNTH_PROFILE = {"sources_sha256_16": "4239e3318de9d32c", "samples_per_lane": 16
                  "dram_write_bytes_per_row": 75.109632e6 / (16 * 64),
                  "fma_pipe_active": 0.686}
 SYNTH_SOURCES = ("synth.cu", "bart_internal.cuh", "record_fp64.cuh", "mixed_record.cuh")
+# the double-bounce synthesis: 3 centres x (2 accumulates + 4 rotation
+# operations) per vertex-form term; ncu figures of its launch on the
+# sedan-over-ground frame, valid while its sources hash as at the capture
+BOUNCE_OPS_PER_TERM = 18
+BOUNCE_SOURCES = ("bounce.cu", "bounce.cuh", "geom64.cuh", "record_fp64.cuh", "bart_internal.cuh")
+BOUNCE_PROFILE = {"sources_sha256_16": "02ca774a2072c928", "fma_pipe_active": 0.376, "fp64_pipe_active": 0.413,
+                  "issue_active": 0.606, "warps_active": 0.179}
 
 
-def synth_sources_hash() -> str:
+def synth_sources_hash(sources=SYNTH_SOURCES) -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in SYNTH_SOURCES:
+    for f in sources:
         with open(os.path.join(ROOT, "paper_2208_10939_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -739,6 +746,20 @@ def double_bounce_lines(pkg, sg, torch, dev, args, peaks) -> dict:
                     dsc.append(tm["bounce_discovery_ms"])
                     syn.append(tm["bounce_synthesis_ms"])
                 bt = st["n_bounce_terms"]
+                syn_s = statistics.median(syn) / 1e3
+                if peaks:
+                    ach = bt * BOUNCE_OPS_PER_TERM / syn_s / 1e12
+                    prof = (BOUNCE_PROFILE if BOUNCE_PROFILE["sources_sha256_16"] ==
+                            synth_sources_hash(BOUNCE_SOURCES) else None)
+                    out["roofline"] = {
+                        "bound": "alu", "kernel": "bounce_synth_f32_kernel<8>",
+                        "ops_per_term": BOUNCE_OPS_PER_TERM, "achieved": ach,
+                        "peak": peaks["fp32_fma_pipe_tops"], "frac": ach / peaks["fp32_fma_pipe_tops"],
+                        "unit": "Top/s (FP32 FMA-pipe operations)",
+                        "peak_basis": "measured (bart_measure_peaks)",
+                        "ncu": prof,
+                        "note": "per-record work (FP64 rows and phases, per-lane start "
+                                "phasors) is amortised over 8 samples per lane"}
                 out.update({
                     "facets": st["n_facets"], "virtual_facets": st["n_bounce_facets"],
                     "double_bounce_terms_per_frame": bt,

@@ -40,7 +40,8 @@ def _stale(obj: str, src: str) -> bool:
     t = os.path.getmtime(obj)
     deps = [src, os.path.join(INCLUDE, "bartsim.h")] + [
         os.path.join(CSRC, h) for h in ("bart_internal.cuh", "record_fp64.cuh", "mixed_record.cuh",
-                                        "fft_stockham.cuh", "fft_reg.cuh", "geom64.cuh")]
+                                        "fft_stockham.cuh", "fft_reg.cuh", "geom64.cuh",
+                                        "bounce.cuh")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

@@ -40,6 +40,7 @@
 #include <climits>
 
 #include "bart_internal.cuh"
+#include "bounce.cuh"
 #include "geom64.cuh"
 #include "record_fp64.cuh"
 

@@ -16,6 +16,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "bart_internal.cuh"
+#include "bounce.cuh"
 #include "bartsim.h"
 
 using namespace bart;
