@@ -23,16 +23,19 @@
 //    virtual facet then moves with b, and p' with a's plane:
 //    p'(t) = p'_0 + u t, u = 2 (v_a.n_a / |n_a|^2) n_a.
 //
-// Discovery: one thread per (TX, lit facet a) casts a's beam through the
-// LBVH (a box is skipped when it lies outside one of the four half-spaces
-// by more than a rounding margin), clips every candidate b and casts the
-// leg's segment.  Every decision takes one IEEE rounding per operation in a
-// fixed order (geom64.cuh), so the virtual facets are reproducible bit for
-// bit.  A count pass, an exclusive scan and a fill pass write them in
-// (TX, a, traversal) order.  Synthesis: FP64, one warp per (channel, chirp,
-// sample segment), the FP64 path's record forms with the TX leg's own
-// quadratic in fast time; it adds into the cube the single-bounce
-// synthesis wrote.
+// Discovery, in two passes of count / scan / fill: one thread per (TX,
+// facet a lit from it, LBVH subtree) casts a's beam through the subtree and
+// lists the facets b facing the image in boxes that meet the beam (FP32
+// culling with a rounding margin); one thread per candidate then clips b,
+// drops slivers and casts the leg's segment.  Every decision takes one IEEE
+// rounding per operation in a fixed order (geom64.cuh), so the virtual
+// facets are reproducible bit for bit, in (TX, a, subtree, traversal, fan)
+// order.  Synthesis: one warp per (channel, chirp, sample segment) adds into
+// the cube the single-bounce synthesis wrote; the FP64 path evaluates the
+// FP64 path's record forms sample by sample (the TX leg with its own
+// quadratic in fast time), the mixed and spectral paths build each record
+// from per-frame slow-time rows of the virtual facet's legs and evaluate it
+// with FP32 phasors.
 #include <cuda_runtime.h>
 #include <stdint.h>
 

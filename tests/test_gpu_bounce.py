@@ -66,6 +66,9 @@ CASES = {
     "ground_reverse_tdm": lambda: ground_plate_scene(reverse_ground=True, P=2, tdm=True),
     "fine_ground": fine_ground_scene,
     "car_ground": lambda: sg.car_ground_scene(ntri=1500, ground_n=6, M=128, N=4, P=2, Q=2),
+    # the bench's ground cells (0.5 m) under a 5000-triangle car: ~19k virtual facets
+    "car_ground_fine": lambda: sg.car_ground_scene(ntri=5000, ground_size=12.0, ground_n=24,
+                                                   M=128, N=4, P=2, Q=2),
 }
 _cache = {}
 
@@ -134,7 +137,8 @@ def test_fp64_adc_with_double_bounce_matches_oracle(sim, name):
 
 
 @pytest.mark.parametrize("name,path", [
-    (n, p) for n in ("dihedral", "dihedral_tdm_30deg", "fine_ground", "car_ground")
+    (n, p) for n in ("dihedral", "dihedral_tdm_30deg", "fine_ground", "car_ground",
+                     "car_ground_fine")
     for p in (pkg.PATH_MIXED, pkg.PATH_SPECTRAL)] + [("ground_reverse_tdm", pkg.PATH_MIXED)])
 def test_fp32_paths_with_double_bounce_match_oracle(sim, name, path):
     sc, fr, ref = case(name)
@@ -145,7 +149,8 @@ def test_fp32_paths_with_double_bounce_match_oracle(sim, name, path):
     assert e <= TOL_MIXED
 
 
-@pytest.mark.parametrize("name", ["dihedral_tdm_30deg", "fine_ground", "car_ground"])
+@pytest.mark.parametrize("name", ["dihedral_tdm_30deg", "fine_ground", "car_ground",
+                                  "car_ground_fine"])
 @pytest.mark.parametrize("path", [pkg.PATH_MIXED, pkg.PATH_SPECTRAL])
 def test_fp32_double_bounce_part_matches_oracle(sim, name, path):
     """The double-bounce part alone (the cube with double bounce minus the
