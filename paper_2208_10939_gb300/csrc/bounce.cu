@@ -822,9 +822,14 @@ __device__ __forceinline__ void rec64_to_v(const RecB &R, const PhaseK &K, RecV 
 // frame start and w = centroid velocity relative to the antenna give the
 // directions in FP32 from the constant B and the small drift -w t.
 constexpr int kDbDeg = 6;
+// the projections of the vertex offsets on the leg's unit vector toward its
+// antenna, p_v(t_c + tau) = sum_j pu[v][j] tau^j; a row is used only where
+// the terms beyond degree 3, at most |dv| rho^4 / (1 - rho), stay below 1e-9 m
+constexpr int kDbPDeg = 3;
 struct BounceRow {
     double a[kDbDeg + 1];
-    float af[kDbDeg + 1];    // the same in FP32 (for the derivatives)
+    double pu[3][kDbPDeg + 1];
+    float af[kDbDeg + 1];    // a in FP32 (for the derivatives)
     float B[3], w[3];
 };
 // per virtual facet: unit normal, area and vertex offsets from the centroid
@@ -860,11 +865,21 @@ __global__ void bounce_rows_kernel(const BounceFacet *__restrict__ vf, int64_t V
     BounceRow &R = rows[i];
     const double a0 = sqrt(q0);
     const double rho = tmax * sqrt(q2 / q0);
+    double dvmax = 0.0;              // the largest vertex offset (projection series bound)
+    for (int v = 0; v < 3; ++v) {
+        double q = 0.0;
+        for (int r = 0; r < 3; ++r) {
+            const double d = B.tri[3 * v + r] - c0[r];
+            q += d * d;
+        }
+        dvmax = fmax(dvmax, sqrt(q));
+    }
     bool ok = q0 > 0.0 && rho < 0.25;
     if (ok) {
-        double b = a0;
+        double b = a0, bp = dvmax;
         for (int j = 0; j <= kDbDeg; ++j) b *= rho;
-        ok = b / (1.0 - rho) <= 1e-11;
+        for (int j = 0; j <= kDbPDeg; ++j) bp *= rho;
+        ok = b / (1.0 - rho) <= 1e-11 && bp / (1.0 - rho) <= 1e-9;
     }
     double a[kDbDeg + 1];
     a[0] = ok ? a0 : -1.0;
@@ -877,6 +892,22 @@ __global__ void bounce_rows_kernel(const BounceFacet *__restrict__ vf, int64_t V
     for (int j = 0; j <= kDbDeg; ++j) {
         R.a[j] = a[j];
         R.af[j] = (float)a[j];
+    }
+    // 1 / R as a series (b_0 = 1 / a_0, b_j = -sum_i a_i b_{j - i} / a_0), and
+    // p_v = -(D_c + w tau).dv_v / R: the phase's projections in FP64
+    double rb[kDbPDeg + 1];
+    rb[0] = ok ? 1.0 / a0 : 0.0;
+    for (int j = 1; j <= kDbPDeg; ++j) {
+        double sacc = 0.0;
+        for (int k = 1; k <= j; ++k) sacc += a[k] * rb[j - k];
+        rb[j] = ok ? -sacc * rb[0] : 0.0;
+    }
+    for (int v = 0; v < 3; ++v) {
+        double dv[3];
+        for (int r = 0; r < 3; ++r) dv[r] = B.tri[3 * v + r] - c0[r];
+        const double n0 = -(Dc[0] * dv[0] + Dc[1] * dv[1] + Dc[2] * dv[2]);
+        const double n1 = -(w[0] * dv[0] + w[1] * dv[1] + w[2] * dv[2]);
+        for (int j = 0; j <= kDbPDeg; ++j) R.pu[v][j] = n0 * rb[j] + (j > 0 ? n1 * rb[j - 1] : 0.0);
     }
     for (int r = 0; r < 3; ++r) {
         R.B[r] = (float)(P[r] - c0[r]);
@@ -926,11 +957,13 @@ __device__ __forceinline__ float inv_fact_f(int n)
     return 1.f / f;
 }
 
-// The FP32 record of a virtual facet from its rows: FP64 only for the path
-// and the phase quadratics; directions, obliquity, projections and every
-// form's amplitudes in FP32 (record_fp64.cuh's forms and switches, with the
-// in-plane pair differences bt.(dv_a - dv_b) formed directly so that close
-// projections keep their relative accuracy).  Returns false when a row has
+// The FP32 record of a virtual facet from its rows: FP64 for the path, the
+// phase quadratics and the projections u_v that enter the phases (from the
+// rows' series of th.dv_v and rh.dv_v; u_v = b.dv_v as dv_v lies in the
+// facet's plane); directions, obliquity, the form switches and every form's
+// amplitudes in FP32 (record_fp64.cuh's forms, with the in-plane pair
+// differences bt.(dv_a - dv_b) formed directly so that close projections
+// keep their relative accuracy).  Returns false when a row has
 // no expansion (the record then takes the full FP64 build).
 __device__ __forceinline__ bool lean_record(const BounceRow &Rt, const BounceRow &Rr,
                                             const BounceGeo &G, float wrho, int two_sided,
@@ -979,6 +1012,23 @@ __device__ __forceinline__ bool lean_record(const BounceRow &Rt, const BounceRow
     double th0, th1, th2;
     path_phase(t0 + s0, rd.intra ? (double)(t1 + s1) : 0.0,
                rd.intra ? (double)(0.5f * (t2 + s2)) : 0.0, K, th0, th1, th2);
+    double ud[3];                    // u_v in FP64 for the phases
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+        double pt = Rt.pu[v][kDbPDeg], pr = Rr.pu[v][kDbPDeg];
+#pragma unroll
+        for (int j = kDbPDeg - 1; j >= 0; --j) {
+            pt = fma(pt, tau, Rt.pu[v][j]);
+            pr = fma(pr, tau, Rr.pu[v][j]);
+        }
+        ud[v] = pt + pr;
+    }
+    // the forms' weights must use the u_v of their phases: a mismatch of
+    // delta between them is amplified by the vertex terms' cancellation
+    // (~delta / |u_a - u_b| relative), so the pair differences come from
+    // the FP64 projections
+#pragma unroll
+    for (int v = 0; v < 3; ++v) d[v] = (float)(ud[v] - ud[(v + 1) % 3]);
     V.C = (float)th2;
     V.flags = 0;
     if (kmax * (umax - umin) < (float)kSeriesKD) {
@@ -999,7 +1049,7 @@ __device__ __forceinline__ bool lean_record(const BounceRow &Rt, const BounceRow
 #pragma unroll
         for (int i = 0; i < 7; ++i)
             V.x[8 + i] = ((i & 1) ? sc : -sc) * h[2 * i + 1] * inv_fact_f(2 * i + 3);
-        centre_phase(th0, th1, (double)((u[0] + u[1] + u[2]) * (1.f / 3.f)), K, V, 0);
+        centre_phase(th0, th1, (ud[0] + ud[1] + ud[2]) * (1.0 / 3.0), K, V, 0);
         V.kind = kRecSeries;
         chord_steps(V, chord0);
         return true;
@@ -1018,7 +1068,7 @@ __device__ __forceinline__ bool lean_record(const BounceRow &Rt, const BounceRow
             V.x[i] = k0 * gam;
             V.x[3 + i] = k0 * g * (e[0] * nxb[0] + e[1] * nxb[1] + e[2] * nxb[2]) / bt2;
             if (kmax * fabsf(gam) < (float)kSincSeries) V.flags |= 1 << i;
-            centre_phase(th0, th1, (double)(0.5f * (u[i] + u[i1])), K, V, i);
+            centre_phase(th0, th1, 0.5 * (ud[i] + ud[i1]), K, V, i);
         }
         V.kind = kRecEdge;
         chord_steps(V, chord0);
@@ -1029,7 +1079,7 @@ __device__ __forceinline__ bool lean_record(const BounceRow &Rt, const BounceRow
     V.x[1] = A2 / (d[1] * d[0]);
     V.x[2] = A2 / (d[2] * d[1]);
 #pragma unroll
-    for (int v = 0; v < 3; ++v) centre_phase(th0, th1, (double)u[v], K, V, v);
+    for (int v = 0; v < 3; ++v) centre_phase(th0, th1, ud[v], K, V, v);
     V.kind = kRecVertex;
     chord_steps(V, chord0);
     return true;
