@@ -958,12 +958,11 @@ __device__ __forceinline__ float inv_fact_f(int n)
 }
 
 // The FP32 record of a virtual facet from its rows: FP64 for the path, the
-// phase quadratics and the projections u_v that enter the phases (from the
-// rows' series of th.dv_v and rh.dv_v; u_v = b.dv_v as dv_v lies in the
-// facet's plane); directions, obliquity, the form switches and every form's
-// amplitudes in FP32 (record_fp64.cuh's forms, with the in-plane pair
-// differences bt.(dv_a - dv_b) formed directly so that close projections
-// keep their relative accuracy).  Returns false when a row has
+// phase quadratics and the projections u_v (from the rows' series of
+// th.dv_v and rh.dv_v; u_v = b.dv_v as dv_v lies in the facet's plane), from
+// which the form switches and the weights' pair differences come too;
+// directions, obliquity and every form's amplitudes in FP32
+// (record_fp64.cuh's forms).  Returns false when a row has
 // no expansion (the record then takes the full FP64 build).
 __device__ __forceinline__ bool lean_record(const BounceRow &Rt, const BounceRow &Rr,
                                             const BounceGeo &G, float wrho, int two_sided,
@@ -998,16 +997,6 @@ __device__ __forceinline__ bool lean_record(const BounceRow &Rt, const BounceRow
     if (two_sided) ok = fabsf(ok);
     const float g = __fdividef(wrho * ok, (float)t0 * (float)s0);
     const float bt[3] = {b[0] - bn * G.n[0], b[1] - bn * G.n[1], b[2] - bn * G.n[2]};
-    float u[3], d[3];     // u_v, and d_v = u_v - u_{v+1} from the edge vectors
-#pragma unroll
-    for (int v = 0; v < 3; ++v) {
-        const int w = (v + 1) % 3;
-        u[v] = bt[0] * G.dv[3 * v] + bt[1] * G.dv[3 * v + 1] + bt[2] * G.dv[3 * v + 2];
-        d[v] = bt[0] * (G.dv[3 * v] - G.dv[3 * w]) + bt[1] * (G.dv[3 * v + 1] - G.dv[3 * w + 1]) +
-               bt[2] * (G.dv[3 * v + 2] - G.dv[3 * w + 2]);
-    }
-    const float umin = fminf(fminf(u[0], u[1]), u[2]), umax = fmaxf(fmaxf(u[0], u[1]), u[2]);
-    const float dmin = fminf(fminf(fabsf(d[0]), fabsf(d[1])), fabsf(d[2]));
     const float A2 = 2.f * G.area * g;
     double th0, th1, th2;
     path_phase(t0 + s0, rd.intra ? (double)(t1 + s1) : 0.0,
@@ -1025,13 +1014,16 @@ __device__ __forceinline__ bool lean_record(const BounceRow &Rt, const BounceRow
     }
     // the forms' weights must use the u_v of their phases: a mismatch of
     // delta between them is amplified by the vertex terms' cancellation
-    // (~delta / |u_a - u_b| relative), so the pair differences come from
-    // the FP64 projections
+    // (~delta / |u_a - u_b| relative), so the pair differences d_v =
+    // u_v - u_{v+1} and the form switches come from the FP64 projections
+    float d[3];
 #pragma unroll
     for (int v = 0; v < 3; ++v) d[v] = (float)(ud[v] - ud[(v + 1) % 3]);
+    const float urange = (float)(fmax(fmax(ud[0], ud[1]), ud[2]) - fmin(fmin(ud[0], ud[1]), ud[2]));
+    const float dmin = fminf(fminf(fabsf(d[0]), fabsf(d[1])), fabsf(d[2]));
     V.C = (float)th2;
     V.flags = 0;
-    if (kmax * (umax - umin) < (float)kSeriesKD) {
+    if (kmax * urange < (float)kSeriesKD) {
         // series form: J = sum_p j^p h_p(y) / (p + 2)!  with y_v = k (u_v - ub)
         const float y0 = k0 * (d[0] - d[2]) * (1.f / 3.f);
         const float y1 = k0 * (d[1] - d[0]) * (1.f / 3.f);
