@@ -176,31 +176,35 @@ __device__ __forceinline__ void image_of(const double *ta, const double *pt, con
     for (int r = 0; r < 3; ++r) u[r] = __dmul_rn(su, na[r]);
 }
 
-// whether b certainly does not face the image (so that facing_image would
-// return 0): FP32 from the rounded unit normal and centroid of the facet
-// record, whose errors (~1e-7 in the normal, ~1e-7 relative in the
-// centroid, so ~2e-6 / |D| in the direction) stay far inside the margin;
-// slivers and two-sided facets always take the FP64 test
-__device__ __forceinline__ bool surely_faces_away(const FacetRec &fr, const double *img,
-                                                  double eps_face)
+// facing_image's decision when FP32 makes it certain, else 2: FP32 from
+// the rounded unit normal and centroid of the facet record, whose errors
+// (~1e-7 in the normal, ~1e-7 relative in the centroid, so ~2e-6 / |D| in
+// the direction) stay far inside the margin; slivers always take the FP64
+// test
+__device__ __forceinline__ int facing_image32(const FacetRec &fr, const double *img,
+                                              double eps_face)
 {
-    if (fr.two_sided) return false;
     float L2 = 0.f;
 #pragma unroll
     for (int v = 0; v < 3; ++v) {
         const float x = fr.dv[3 * v], y = fr.dv[3 * v + 1], z = fr.dv[3 * v + 2];
         L2 = fmaxf(L2, fmaf(x, x, fmaf(y, y, z * z)));
     }
-    if (2.f * fr.area < 4e-6f * L2) return false;
+    if (2.f * fr.area < 4e-6f * L2) return 2;
     const float D[3] = {(float)img[0] - fr.c[0], (float)img[1] - fr.c[1], (float)img[2] - fr.c[2]};
     const float dd = fmaf(D[0], D[0], fmaf(D[1], D[1], D[2] * D[2]));
-    if (!(dd > 0.f)) return false;
+    if (!(dd > 0.f)) return 2;
     const float inv = rsqrtf(dd);
     const float cs = fmaf(fr.n[0], D[0], fmaf(fr.n[1], D[1], fr.n[2] * D[2])) * inv;
     const float scale = fmaxf(fmaxf(fabsf(fr.c[0]), fabsf(fr.c[1])), fabsf(fr.c[2])) +
                         fmaxf(fmaxf(fabsf((float)img[0]), fabsf((float)img[1])),
                               fabsf((float)img[2]));
-    return cs < -((float)eps_face + 2e-5f + 4e-7f * scale * inv);
+    const float m = 2e-5f + 4e-7f * scale * inv;
+    const float e = (float)eps_face;
+    if (cs >= e + m) return 1;
+    if (cs <= -e - m) return fr.two_sided ? -1 : 0;
+    if (fabsf(cs) <= e - m) return 0;
+    return 2;
 }
 
 // the side of b that faces the image (+1 front, -1 reverse of a two-sided
@@ -367,10 +371,12 @@ bounce_cand_kernel(const double *__restrict__ tri64, const FacetRec *__restrict_
     int64_t slot = FILL ? off[item] : 0;
     // a leaf b met by the beam: a candidate when it faces the image
     auto leaf = [&](int64_t b) {
-        if (b == a || surely_faces_away(fac[b], img, rd.eps_face)) return;
-        double nbb;
-        const int side_b = facing_image(tri64 + 9 * b, img, fac[b].two_sided != 0,
-                                        rd.eps_face, &nbb);
+        if (b == a) return;
+        int side_b = facing_image32(fac[b], img, rd.eps_face);
+        if (side_b == 2) {
+            double nbb;
+            side_b = facing_image(tri64 + 9 * b, img, fac[b].two_sided != 0, rd.eps_face, &nbb);
+        }
         if (!side_b) return;
         if (FILL) cand[slot++] = BounceCand{(int32_t)a, (int32_t)b, p, side_b};
         ++count;
