@@ -1170,9 +1170,11 @@ bounce_synth_f32_kernel(const BounceFacet *__restrict__ vf, const int64_t *__res
 #pragma unroll
             for (int e = 0; e < 3; ++e) {
                 if (e >= nc) break;
+                // the phase reduced to [-1/2, 1/2] cycle: the SFU's sine and
+                // cosine over [-pi, pi] (absolute error ~4e-7)
                 const float ph = red1f(red1f(V.Bhi[e] * fm0) +
                                        (V.A[e] + fmaf(V.Blo[e], fm0, V.C * fm0sq)));
-                sincospif(2.f * ph, &zs[e], &zc[e]);
+                __sincosf(6.283185307179586f * ph, &zs[e], &zc[e]);
                 cs[e] = fmaf(V.sc[e], xr, -V.ss[e] * x);
                 ss[e] = fmaf(V.sc[e], x, V.ss[e] * xr);
             }
