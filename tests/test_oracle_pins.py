@@ -1081,3 +1081,21 @@ def test_double_bounce_image_moves_within_the_chirp():
         return 2 * np.pi * (r.f0 * tau + r.slope * tm * tau - 0.5 * r.slope * tau ** 2)
     expect = np.exp(1j * (phase(tn + tm) - phase(np.full_like(tm, tn))))
     np.testing.assert_allclose(outs[True] / outs[False], expect, rtol=0, atol=1e-9)
+
+
+def test_double_bounce_reverse_lit_two_sided_dihedral():
+    """The dihedral wound the other way round and two-sided is lit on the
+    reverse side of both plates: the same geometry, so the same
+    double-bounce cross-section (both facets take their side s = -1)."""
+    A = 0.1
+    m = sg.dihedral(A, 2)
+    tri = m.verts[m.tris].reshape(-1, 9) + np.tile([0.031, -0.017, 0.052], 3)
+    rev = tri.reshape(-1, 3, 3)[:, [0, 2, 1], :].reshape(-1, 9)
+    t = np.array([math.cos(math.radians(33.0)), math.sin(math.radians(33.0)), 0.0])
+    freqs = np.array([76.5e9, 79.0e9])
+    front = oracle.rcs_farfield_bounce2(tri, m.rho, t, t, freqs)
+    back = oracle.rcs_farfield_bounce2(rev, m.rho, t, t, freqs,
+                                       two_sided=np.ones(len(m.rho), np.uint8))
+    one_sided_back = oracle.rcs_farfield_bounce2(rev, m.rho, t, t, freqs)
+    np.testing.assert_allclose(back, front, rtol=1e-12)
+    np.testing.assert_array_equal(one_sided_back, 0.0)
