@@ -70,7 +70,7 @@ SYNTH_SOURCES = ("synth.cu", "bart_internal.cuh", "record_fp64.cuh", "mixed_reco
 # sedan-over-ground frame, valid while its sources hash as at the capture
 BOUNCE_OPS_PER_TERM = 18
 BOUNCE_SOURCES = ("bounce.cu", "bounce.cuh", "geom64.cuh", "record_fp64.cuh", "bart_internal.cuh")
-BOUNCE_PROFILE = {"sources_sha256_16": "afa19c88256e619b", "fma_pipe_active": 0.324, "fp64_pipe_active": 0.528,
+BOUNCE_PROFILE = {"sources_sha256_16": "0ad733dd979e3494", "fma_pipe_active": 0.324, "fp64_pipe_active": 0.528,
                   "issue_active": 0.523, "warps_active": 0.179}
 
 

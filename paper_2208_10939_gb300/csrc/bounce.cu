@@ -257,7 +257,8 @@ __device__ __forceinline__ int clip_to_beam(const double *tb, const double *g, c
 // vertices) hits or grazes a facet other than a and b
 __device__ bool leg_blocked(const double *poly, int K, const double *ta, const double *na,
                             const double *img, const double *__restrict__ tri64,
-                            const BvhNode *__restrict__ nodes, int64_t a, int64_t b, int *status)
+                            const float4 *__restrict__ tri32, const BvhNode *__restrict__ nodes,
+                            int64_t a, int64_t b, int *status)
 {
     double cp[3] = {0.0, 0.0, 0.0}, spt[3], Dl[3], t1[3], t2[3];
     for (int q = 0; q < K; ++q)
@@ -269,9 +270,12 @@ __device__ bool leg_blocked(const double *poly, int K, const double *ta, const d
     for (int r = 0; r < 3; ++r) spt[r] = __dadd_rn(img[r], __dmul_rn(lam, t2[r]));
     sub3(cp, spt, Dl);
     const float o[3] = {(float)spt[0], (float)spt[1], (float)spt[2]};
+    const float Df[3] = {(float)Dl[0], (float)Dl[1], (float)Dl[2]};
+    const float Dm = fmaxf(fmaxf(fabsf(Df[0]), fabsf(Df[1])), fabsf(Df[2]));
+    const float Om = fmaxf(fmaxf(fabsf(o[0]), fabsf(o[1])), fabsf(o[2]));
     float inv[3];
     for (int r = 0; r < 3; ++r) {
-        float dd = (float)Dl[r];
+        float dd = Df[r];
         if (fabsf(dd) < 1e-30f) dd = copysignf(1e-30f, dd);
         inv[r] = 1.0f / dd;
     }
@@ -295,6 +299,12 @@ __device__ bool leg_blocked(const double *poly, int K, const double *ta, const d
             }
             const int64_t j = ~c[e];
             if (j == a || j == b) continue;
+            // the FP32 pre-test decides certain misses and certain hits
+            // exactly as the FP64 test would; the rest take the FP64 test
+            const int pre = mt_fp32_classify(tri32[3 * j], tri32[3 * j + 1], tri32[3 * j + 2], o,
+                                             Df, Dm, Om);
+            if (pre == 0) continue;
+            if (pre == 2) return true;
             double tj[9];
             for (int q = 0; q < 9; ++q) tj[q] = tri64[9 * j + q];
             if (mt_segment(spt, Dl, tj) != 0) return true;
@@ -412,7 +422,8 @@ bounce_cand_kernel(const double *__restrict__ tri64, const FacetRec *__restrict_
 // offset (the leg already decided).
 template <bool FILL>
 __global__ void __launch_bounds__(128)
-bounce_pair_kernel(const double *__restrict__ tri64, const FacetRec *__restrict__ fac,
+bounce_pair_kernel(const double *__restrict__ tri64, const float4 *__restrict__ tri32,
+                   const FacetRec *__restrict__ fac,
                    const double *__restrict__ vel64, const BvhNode *__restrict__ nodes,
                    const uint8_t *__restrict__ state, const BounceCand *__restrict__ cand,
                    int64_t ncand, int64_t F, RadarDev rd, int32_t *__restrict__ pcnt, const int64_t *__restrict__ poff,
@@ -439,7 +450,7 @@ bounce_pair_kernel(const double *__restrict__ tri64, const FacetRec *__restrict_
     const int K = clip_to_beam(tb, g, base, nbb, poly, &keep);
     if (!FILL) {
         const bool lit = K >= 3 && keep != 0 &&
-                         !leg_blocked(poly, K, ta, na, img, tri64, nodes, C.a, C.b, status);
+                         !leg_blocked(poly, K, ta, na, img, tri64, tri32, nodes, C.a, C.b, status);
         pcnt[c] = lit ? __popc(keep) : 0;
         return;
     }
@@ -1337,20 +1348,21 @@ void launch_bounce_candidates(bool fill, const double *tri64, const FacetRec *fa
                                                      status);
 }
 
-void launch_bounce_pairs(bool fill, const double *tri64, const FacetRec *fac,
+void launch_bounce_pairs(bool fill, const double *tri64, const float *tri32, const FacetRec *fac,
                          const double *vel64, const BvhNode *nodes, const uint8_t *state,
                          const BounceCand *cand, int64_t ncand, int64_t F, const RadarDev &rd,
                          int32_t *pcnt, const int64_t *poff, BounceFacet *vf, int *status,
                          cudaStream_t s)
 {
     if (ncand <= 0) return;
+    const float4 *t32 = reinterpret_cast<const float4 *>(tri32);
     const int T = 128;
     const unsigned int grid = (unsigned int)((ncand + T - 1) / T);
     if (fill)
-        bounce_pair_kernel<true><<<grid, T, 0, s>>>(tri64, fac, vel64, nodes, state, cand, ncand,
+        bounce_pair_kernel<true><<<grid, T, 0, s>>>(tri64, t32, fac, vel64, nodes, state, cand, ncand,
                                                     F, rd, pcnt, poff, vf, status);
     else
-        bounce_pair_kernel<false><<<grid, T, 0, s>>>(tri64, fac, vel64, nodes, state, cand,
+        bounce_pair_kernel<false><<<grid, T, 0, s>>>(tri64, t32, fac, vel64, nodes, state, cand,
                                                      ncand, F, rd, pcnt, poff, vf, status);
 }
 

@@ -43,7 +43,7 @@ void launch_bounce_candidates(bool fill, const double *tri64, const FacetRec *fa
                               const int64_t *off, BounceCand *cand, int *status, cudaStream_t s);
 // pass 2 over the candidates: the virtual facets per candidate into pcnt
 // (count: clip, slivers, the a -> b leg), or written at poff (fill)
-void launch_bounce_pairs(bool fill, const double *tri64, const FacetRec *fac,
+void launch_bounce_pairs(bool fill, const double *tri64, const float *tri32, const FacetRec *fac,
                          const double *vel64, const BvhNode *nodes, const uint8_t *state,
                          const BounceCand *cand, int64_t ncand, int64_t F, const RadarDev &rd,
                          int32_t *pcnt, const int64_t *poff, BounceFacet *vf, int *status,

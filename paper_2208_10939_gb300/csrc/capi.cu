@@ -858,7 +858,7 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
                                          ctx->nodes.p, ctx->state.p, ctx->vis_idx.p,
                                          ctx->vis_cnt.p, F, rd, NS, ctx->db_roots.p, nullptr,
                                          ctx->db_off.p, ctx->db_cand.p, ctx->status.p, s);
-                launch_bounce_pairs(false, ctx->tri64.p, ctx->fac.p, ctx->vel64.p, ctx->nodes.p,
+                launch_bounce_pairs(false, ctx->tri64.p, ctx->tri32.p, ctx->fac.p, ctx->vel64.p, ctx->nodes.p,
                                     ctx->state.p, ctx->db_cand.p, ncand, F, rd, ctx->db_pcnt.p,
                                     nullptr, nullptr, ctx->status.p, s);
             }
@@ -871,7 +871,7 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
             launches += 5 + (ncand > 0 ? 2 : 0) + (ncand > 0 ? 3 : 1);
             if (total > 0) {
                 BART_TRY(ctx->db_vf.ensure((size_t)total, "double-bounce virtual facets"));
-                launch_bounce_pairs(true, ctx->tri64.p, ctx->fac.p, ctx->vel64.p, ctx->nodes.p,
+                launch_bounce_pairs(true, ctx->tri64.p, ctx->tri32.p, ctx->fac.p, ctx->vel64.p, ctx->nodes.p,
                                     ctx->state.p, ctx->db_cand.p, ncand, F, rd, ctx->db_pcnt.p,
                                     ctx->db_poff.p, ctx->db_vf.p, ctx->status.p, s);
                 launches += 1;
