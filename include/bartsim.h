@@ -143,8 +143,9 @@ typedef struct bart_radar {
                                     FP64; one scene per frame, per-facet delay
                                     form (not with far_field or delay_ref), no
                                     adjoint; frames then synchronise the stream
-                                    once and are not replayed as graphs.  See
-                                    bart_get_bounce_facets. */
+                                    twice (to size the candidates and the
+                                    virtual facets) and are not replayed as
+                                    graphs.  See bart_get_bounce_facets. */
     double  grazing_eps;         /* facets with |cos| below this toward an antenna
                                     are GRAZE (excluded, counted); 0 = 1e-6 */
 } bart_radar;
