@@ -252,6 +252,37 @@ int bart_scene_set(bart_ctx *ctx, const bart_instance *inst, int32_t n);
 /* Total facet count of the current scene (host out). */
 int bart_scene_facets(bart_ctx *ctx, int64_t *n_facets);
 
+/* The sizes of the buffers the context reads and writes.  The library
+ * receives bare addresses, so a caller (the Python binding) checks its
+ * buffers against these before each call.  Host-only: nothing is enqueued.
+ * Fields are 0 where the state they describe is not set yet. */
+typedef struct bart_dims {
+    int32_t device;        /* CUDA ordinal of the context */
+    int32_t have_radar;    /* 1 after a successful bart_radar_set */
+    int32_t n_scenes;      /* S: scenes of the partition (1 without one) */
+    int32_t O;             /* channels P*Q */
+    int32_t N;             /* chirps */
+    int32_t M;             /* samples per chirp */
+    int32_t A;             /* antennas P+Q */
+    int32_t n_meshes;      /* uploaded meshes */
+    int64_t n_facets;      /* facets of the current scene (grad_rho length) */
+    int64_t n_inst_verts;  /* vertex count summed over the instances' meshes
+                              (grad_verts holds 3 x this many) */
+    int64_t vis_antennas;  /* the last frame's visibility states: antennas ... */
+    int64_t vis_facets;    /* ... x facets (bart_get_visibility's output) */
+} bart_dims;
+
+/* Fill *out (host).  A simulation frame writes S*O*N*M samples; an RDM is
+ * S*M*N floats; bart_add_noise and bart_detect take one O*N*M cube.  No
+ * counterpart in the paper: bookkeeping of this interface.
+ * Errors: EINVAL (NULL argument). */
+int bart_get_dims(bart_ctx *ctx, bart_dims *out);
+
+/* Vertex and facet counts of uploaded mesh `mesh_id` (host outs): the sizes
+ * bart_mesh_update reads (3 x nv float64, nf float32).  No counterpart in
+ * the paper.  Errors: EINVAL (NULL argument, unknown mesh). */
+int bart_mesh_dims(bart_ctx *ctx, int32_t mesh_id, int64_t *nv, int64_t *nf);
+
 /* Split the instance table of the last bart_scene_set into independent
  * scenes simulated in one pass (dataset generation: many small scenes per
  * launch).  Instances [first[b], first[b+1]) form scene b, with

@@ -39,7 +39,8 @@ EXPORTED = ["bart_last_error", "bart_version", "bart_create", "bart_destroy",
             "bart_autotune", "bart_rdm_adjoint", "bart_simulate_adjoint",
             "bart_simulate_adjoint_mixed",
             "bart_mesh_update", "bart_measure_peaks", "bart_inject_alloc_failure",
-            "bart_selftest_wait_timeout", "bart_get_bounce_facets"]
+            "bart_selftest_wait_timeout", "bart_get_bounce_facets", "bart_get_dims",
+            "bart_mesh_dims"]
 
 
 class BartError(RuntimeError):
@@ -73,6 +74,17 @@ class bart_stats(ctypes.Structure):
                 ("n_series", ctypes.c_int64), ("n_edge", ctypes.c_int64),
                 ("n_vertex", ctypes.c_int64), ("n_bounce_facets", ctypes.c_int64),
                 ("n_bounce_terms", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+class bart_dims(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("have_radar", ctypes.c_int32),
+                ("n_scenes", ctypes.c_int32), ("O", ctypes.c_int32), ("N", ctypes.c_int32),
+                ("M", ctypes.c_int32), ("A", ctypes.c_int32), ("n_meshes", ctypes.c_int32),
+                ("n_facets", ctypes.c_int64), ("n_inst_verts", ctypes.c_int64),
+                ("vis_antennas", ctypes.c_int64), ("vis_facets", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -163,6 +175,8 @@ def load_library() -> ctypes.CDLL:
         L.bart_mesh_clear.argtypes = [P]
         L.bart_scene_set.argtypes = [P, P, I32]
         L.bart_scene_facets.argtypes = [P, ctypes.POINTER(I64)]
+        L.bart_get_dims.argtypes = [P, ctypes.POINTER(bart_dims)]
+        L.bart_mesh_dims.argtypes = [P, I32, ctypes.POINTER(I64), ctypes.POINTER(I64)]
         L.bart_radar_set.argtypes = [P, ctypes.POINTER(bart_radar)]
         L.bart_simulate_frame.argtypes = [P, D, I32, P, I32, ctypes.POINTER(bart_stats)]
         L.bart_form_rdm.argtypes = [P, P, I32, P]
@@ -208,6 +222,61 @@ def _ptr(t) -> int:
 
 
 # ---------------------------------------------------------------------------
+# buffer checks: the library receives bare addresses and reads or writes as
+# many elements as the context's shapes say, so every buffer is checked here
+# against bart_get_dims before the call
+# ---------------------------------------------------------------------------
+def _dims(ctx: int) -> "bart_dims":
+    d = bart_dims()
+    _check(load_library().bart_get_dims(ctx, ctypes.byref(d)))
+    return d
+
+
+def _cube(d: "bart_dims", scenes: bool = True) -> Optional[int]:
+    """Samples of the ADC buffer (all scenes, or one cube); None before a
+    radar is set (the C call then reports BART_ESTATE)."""
+    if not d.have_radar:
+        return None
+    return (d.n_scenes if scenes else 1) * d.O * d.N * d.M
+
+
+def _rdm_cells(d: "bart_dims", scenes: bool = True) -> Optional[int]:
+    if not d.have_radar:
+        return None
+    return (d.n_scenes if scenes else 1) * d.M * d.N
+
+
+def _device_buffer(t, name: str, d: "bart_dims", numel: Optional[int], dtype=None) -> None:
+    """Raise unless ``t`` is a contiguous CUDA tensor on the context's
+    device with ``numel`` elements (when given) of ``dtype`` (when given)."""
+    if not getattr(t, "is_cuda", False) or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    if t.device.index is not None and t.device.index != d.device:
+        raise ValueError(f"{name} is on {t.device}, the context on cuda:{d.device}")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} elements; the context's shapes need {numel}")
+
+
+def _host_buffer(a, name: str, numel: Optional[int]) -> None:
+    """Raise unless ``a`` is a C-contiguous float32 host array (numpy or a
+    CPU tensor) of ``numel`` elements (when given)."""
+    if isinstance(a, np.ndarray):
+        ok = a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]
+        n = a.size
+    else:
+        import torch
+        ok = (isinstance(a, torch.Tensor) and not a.is_cuda and a.is_contiguous()
+              and a.dtype == torch.float32)
+        n = a.numel() if isinstance(a, torch.Tensor) else -1
+    if not ok:
+        raise ValueError(f"{name} must be a C-contiguous float32 host array")
+    if numel is not None and n != numel:
+        raise ValueError(f"{name} has {n} elements; the context's shapes need {numel}")
+
+
+# ---------------------------------------------------------------------------
 # C-ABI mirrors
 # ---------------------------------------------------------------------------
 def bart_version() -> str:
@@ -245,10 +314,11 @@ def bart_mesh_update(ctx: int, mesh_id: int, verts, rho=None) -> None:
     """Replace an uploaded mesh's vertices (CUDA float64 nv x 3) and
     optionally reflectivities (CUDA float32 nf) in place, asynchronously."""
     import torch
-    if not verts.is_cuda or not verts.is_contiguous() or verts.dtype != torch.float64:
-        raise ValueError("verts must be a contiguous CUDA float64 tensor")
-    if rho is not None and (not rho.is_cuda or not rho.is_contiguous() or rho.dtype != torch.float32):
-        raise ValueError("rho must be a contiguous CUDA float32 tensor")
+    d = _dims(ctx)
+    nv, nf = bart_mesh_dims(ctx, mesh_id)
+    _device_buffer(verts, "verts", d, 3 * nv, torch.float64)
+    if rho is not None:
+        _device_buffer(rho, "rho", d, nf, torch.float32)
     _check(load_library().bart_mesh_update(ctx, int(mesh_id), ctypes.c_void_p(_ptr(verts)),
                                            None if rho is None else ctypes.c_void_p(_ptr(rho))))
 
@@ -287,6 +357,18 @@ def bart_scene_facets(ctx: int) -> int:
     n = ctypes.c_int64()
     _check(load_library().bart_scene_facets(ctx, ctypes.byref(n)))
     return n.value
+
+
+def bart_get_dims(ctx: int) -> dict:
+    """The context's buffer shapes (bart_dims as a dict)."""
+    return _dims(ctx).as_dict()
+
+
+def bart_mesh_dims(ctx: int, mesh_id: int):
+    """(vertex count, facet count) of an uploaded mesh."""
+    nv, nf = ctypes.c_int64(), ctypes.c_int64()
+    _check(load_library().bart_mesh_dims(ctx, int(mesh_id), ctypes.byref(nv), ctypes.byref(nf)))
+    return nv.value, nf.value
 
 
 def make_radar(radar, window: int = WINDOW_HANN) -> bart_radar:
@@ -329,8 +411,8 @@ def _dtype_code(t) -> int:
 def bart_simulate_frame(ctx: int, t0: float, path: int, adc, stats: bool = False):
     """Simulate one frame into the contiguous complex CUDA tensor ``adc``
     ([O][N][M]).  Returns the stats dict when ``stats`` (synchronises)."""
-    if not adc.is_cuda or not adc.is_contiguous():
-        raise ValueError("adc must be a contiguous CUDA tensor")
+    d = _dims(ctx)
+    _device_buffer(adc, "adc", d, _cube(d))
     st = bart_stats() if stats else None
     _check(load_library().bart_simulate_frame(
         ctx, float(t0), int(path), ctypes.c_void_p(_ptr(adc)), _dtype_code(adc),
@@ -339,18 +421,19 @@ def bart_simulate_frame(ctx: int, t0: float, path: int, adc, stats: bool = False
 
 
 def bart_form_rdm(ctx: int, adc, rdm) -> None:
+    """RDM ([S][M][N] float32) of the ADC cube ([S][O][N][M])."""
     import torch
-    if not (adc.is_cuda and rdm.is_cuda and adc.is_contiguous() and rdm.is_contiguous()):
-        raise ValueError("adc and rdm must be contiguous CUDA tensors")
-    if rdm.dtype != torch.float32:
-        raise TypeError("rdm must be float32")
+    d = _dims(ctx)
+    _device_buffer(adc, "adc", d, _cube(d))
+    _device_buffer(rdm, "rdm", d, _rdm_cells(d), torch.float32)
     _check(load_library().bart_form_rdm(ctx, ctypes.c_void_p(_ptr(adc)), _dtype_code(adc),
                                         ctypes.c_void_p(_ptr(rdm))))
 
 
 def bart_frame_host(ctx: int, t0: float, path: int, rdm_host, stats: bool = False):
     """Whole frame into a host float32 buffer (numpy array or CPU tensor,
-    ideally pinned) of M x N; synchronises."""
+    ideally pinned) of [S][M][N]; synchronises."""
+    _host_buffer(rdm_host, "rdm_host", _rdm_cells(_dims(ctx)))
     st = bart_stats() if stats else None
     _check(load_library().bart_frame_host(ctx, float(t0), int(path),
                                           ctypes.c_void_p(_ptr(rdm_host)),
@@ -360,9 +443,10 @@ def bart_frame_host(ctx: int, t0: float, path: int, rdm_host, stats: bool = Fals
 
 def bart_add_noise(ctx: int, adc, snr_db: float, seed: int, frame: int = 0) -> None:
     """Add white complex Gaussian noise at ``snr_db`` to the CUDA ADC tensor
-    in place (Philox4x32-10 counter-based, deterministic per seed/frame)."""
-    if not adc.is_cuda or not adc.is_contiguous():
-        raise ValueError("adc must be a contiguous CUDA tensor")
+    in place (Philox4x32-10 counter-based, deterministic per seed/frame).
+    ``adc`` is one [O][N][M] cube."""
+    d = _dims(ctx)
+    _device_buffer(adc, "adc", d, _cube(d, scenes=False))
     _check(load_library().bart_add_noise(ctx, ctypes.c_void_p(_ptr(adc)), _dtype_code(adc),
                                          float(snr_db), int(seed) & 0xFFFFFFFFFFFFFFFF,
                                          int(frame) & 0xFFFFFFFF))
@@ -383,16 +467,14 @@ def bart_detect(ctx: int, adc, cfg: bart_detect_cfg, points=None, rdm=None,
     records) or None; ``rdm``: CUDA float32 M x N tensor or None.  Returns
     the number of detections when ``sync`` (the call then synchronises)."""
     import torch
-    if not adc.is_cuda or not adc.is_contiguous():
-        raise ValueError("adc must be a contiguous CUDA tensor")
+    d = _dims(ctx)
+    _device_buffer(adc, "adc", d, _cube(d, scenes=False))
     max_points = 0
     if points is not None:
-        if not points.is_cuda or not points.is_contiguous() or points.dtype != torch.uint8:
-            raise ValueError("points must be a contiguous CUDA uint8 tensor")
+        _device_buffer(points, "points", d, None, torch.uint8)
         max_points = points.numel() // POINT_DTYPE.itemsize
-    if rdm is not None and (not rdm.is_cuda or not rdm.is_contiguous()
-                            or rdm.dtype != torch.float32):
-        raise ValueError("rdm must be a contiguous CUDA float32 tensor")
+    if rdm is not None:
+        _device_buffer(rdm, "rdm", d, _rdm_cells(d, scenes=False), torch.float32)
     n = ctypes.c_int32(-1)
     _check(load_library().bart_detect(
         ctx, ctypes.c_void_p(_ptr(adc)), _dtype_code(adc), ctypes.byref(cfg),
@@ -458,6 +540,10 @@ def bart_measure_peaks(device: int = 0, reps: int = 5) -> dict:
 def bart_get_visibility(ctx: int, state, grazing: bool = False):
     """Copy the frame-start states into ``state`` (A x F uint8 on the
     device); with ``grazing`` also return the number of GRAZE pairs."""
+    import torch
+    d = _dims(ctx)
+    _device_buffer(state, "state", d, d.vis_antennas * d.vis_facets if d.vis_facets else None,
+                   torch.uint8)
     n = ctypes.c_int64(-1)
     _check(load_library().bart_get_visibility(ctx, ctypes.c_void_p(_ptr(state)),
                                               ctypes.byref(n) if grazing else None))
@@ -484,11 +570,10 @@ def bart_get_bounce_facets(ctx: int) -> dict:
 def bart_rdm_adjoint(ctx: int, adc, grad_rdm, grad_adc) -> None:
     """grad_adc = dL/dRe(adc) + i dL/dIm(adc) for dL/dRDM = grad_rdm."""
     import torch
-    for t in (adc, grad_rdm, grad_adc):
-        if not t.is_cuda or not t.is_contiguous():
-            raise ValueError("adc, grad_rdm and grad_adc must be contiguous CUDA tensors")
-    if grad_rdm.dtype != torch.float32 or grad_adc.dtype != adc.dtype:
-        raise TypeError("grad_rdm must be float32 and grad_adc of adc's dtype")
+    d = _dims(ctx)
+    _device_buffer(adc, "adc", d, _cube(d))
+    _device_buffer(grad_rdm, "grad_rdm", d, _rdm_cells(d), torch.float32)
+    _device_buffer(grad_adc, "grad_adc", d, _cube(d), adc.dtype)
     _check(load_library().bart_rdm_adjoint(ctx, ctypes.c_void_p(_ptr(adc)), _dtype_code(adc),
                                            ctypes.c_void_p(_ptr(grad_rdm)),
                                            ctypes.c_void_p(_ptr(grad_adc))))
@@ -500,11 +585,11 @@ def bart_simulate_adjoint(ctx: int, t0: float, grad_adc, grad_verts, grad_rho=No
     gradients of a real loss with dL/dRe(adc) + i dL/dIm(adc) = grad_adc;
     ``mixed`` selects bart_simulate_adjoint_mixed (FP32 per-sample work)."""
     import torch
-    if not grad_adc.is_cuda or not grad_adc.is_contiguous():
-        raise ValueError("grad_adc must be a contiguous CUDA tensor")
-    for t in (grad_verts, grad_rho):
-        if t is not None and (not t.is_cuda or not t.is_contiguous() or t.dtype != torch.float64):
-            raise ValueError("gradient outputs must be contiguous CUDA float64 tensors")
+    d = _dims(ctx)
+    _device_buffer(grad_adc, "grad_adc", d, _cube(d))
+    _device_buffer(grad_verts, "grad_verts", d, 3 * d.n_inst_verts, torch.float64)
+    if grad_rho is not None:
+        _device_buffer(grad_rho, "grad_rho", d, d.n_facets, torch.float64)
     lib = load_library()
     fn = lib.bart_simulate_adjoint_mixed if mixed else lib.bart_simulate_adjoint
     _check(fn(ctx, float(t0), ctypes.c_void_p(_ptr(grad_adc)), _dtype_code(grad_adc),
@@ -523,8 +608,8 @@ def bart_set_synth_layout(ctx: int, samples_per_lane: int = 0, tiles_per_item: i
 def bart_autotune(ctx: int, t0: float, adc, reps: int = 3) -> dict:
     """Try the mixed-path synthesis layouts on the current scene, keep the
     fastest; returns the trial table (samples/lane, tiles/item, ms)."""
-    if not adc.is_cuda or not adc.is_contiguous():
-        raise ValueError("adc must be a contiguous CUDA tensor")
+    d = _dims(ctx)
+    _device_buffer(adc, "adc", d, _cube(d))
     t = bart_tune()
     _check(load_library().bart_autotune(ctx, float(t0), ctypes.c_void_p(_ptr(adc)),
                                         _dtype_code(adc), int(reps), ctypes.byref(t)))

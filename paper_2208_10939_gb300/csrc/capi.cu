@@ -536,6 +536,43 @@ int bart_scene_facets(bart_ctx *ctx, int64_t *n_facets)
     return BART_OK;
 }
 
+int bart_get_dims(bart_ctx *ctx, bart_dims *out)
+{
+    g_err.clear();
+    if (!ctx || !out) return fail(BART_EINVAL, "bart_get_dims: NULL argument");
+    std::memset(out, 0, sizeof *out);
+    out->device = ctx->device;
+    out->n_scenes = ctx->n_scenes;
+    out->n_meshes = ctx->n_meshes;
+    if (ctx->have_radar) {
+        out->have_radar = 1;
+        out->O = ctx->radar.P * ctx->radar.Q;
+        out->N = ctx->radar.N;
+        out->M = ctx->radar.M;
+        out->A = ctx->radar.P + ctx->radar.Q;
+    }
+    for (const bart_instance &i : ctx->insts) {
+        out->n_facets += ctx->pool[i.mesh_id]->nf;
+        out->n_inst_verts += ctx->pool[i.mesh_id]->nv;
+    }
+    if (ctx->have_frame) {
+        out->vis_antennas = ctx->frame_A;
+        out->vis_facets = ctx->frame_F;
+    }
+    return BART_OK;
+}
+
+int bart_mesh_dims(bart_ctx *ctx, int32_t mesh_id, int64_t *nv, int64_t *nf)
+{
+    g_err.clear();
+    if (!ctx || !nv || !nf) return fail(BART_EINVAL, "bart_mesh_dims: NULL argument");
+    if (mesh_id < 0 || mesh_id >= ctx->n_meshes)
+        return fail(BART_EINVAL, "bart_mesh_dims: mesh %d (have %d)", mesh_id, ctx->n_meshes);
+    *nv = ctx->pool[mesh_id]->nv;
+    *nf = ctx->pool[mesh_id]->nf;
+    return BART_OK;
+}
+
 int bart_radar_set(bart_ctx *ctx, const bart_radar *r)
 {
     g_err.clear();

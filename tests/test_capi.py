@@ -42,7 +42,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 MIRRORS = ["bart_instance", "bart_radar", "bart_stats", "bart_timing", "bart_detect_cfg",
-           "bart_point", "bart_tune", "bart_peaks"]
+           "bart_point", "bart_tune", "bart_peaks", "bart_dims"]
 
 
 def test_struct_layouts_match_c(tmp_path):
