@@ -15,7 +15,7 @@ into complex128), against the FP64 oracle.
   ends of the virtual array): against oracle entries to 1e-9 and against the
   mixed cube's same channels, every sample, to 1e-4.
 
-Bars (the benchmark spec): FP64 <= 1e-9 relative L2, mixed <= 1e-4 relative L2 and
+Bars: FP64 <= 1e-9 relative L2, mixed <= 1e-4 relative L2 and
 <= 0.1 dB at RDM peaks.
 """
 import numpy as np
