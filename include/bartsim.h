@@ -95,7 +95,8 @@ typedef struct bart_instance {
  * transmit frequency is f0 + slope*m/fs.
  * Constraints (else BART_EINVAL): M a multiple of 32 in [32, 1024];
  * 1 <= N <= 32768; 1 <= P <= BART_MAX_TX; 1 <= Q <= BART_MAX_RX;
- * f0, slope, fs > 0; Tc >= M/fs; far_field and delay_ref not both set;
+ * f0, slope, fs, Tc positive and finite; Tc >= M/fs; antenna positions
+ * finite; flags 0 or 1; far_field and delay_ref not both set;
  * grazing_eps 0 (default 1e-6) or in (0, 0.1].  bart_form_rdm and
  * bart_detect further need M and N of the form 2^a 3^b (radix-2/3 FFTs;
  * N in [2, 1024]). */
@@ -229,8 +230,8 @@ int bart_set_stream(bart_ctx *ctx, void *stream);
  * rho: nf float32 reflectivities or NULL for all 1; flags: 0 or
  * BART_MESH_TWO_SIDED (Sec. 2.2 visibility, the PO obliquity taken on the
  * side the antennas light).  *mesh_id receives the id used by
- * bart_instance.  Errors: EINVAL (index out of range, nf < 1, unknown flag),
- * ENOMEM, ECUDA. */
+ * bart_instance.  Errors: EINVAL (index out of range, nf < 1, unknown flag,
+ * a non-finite vertex coordinate or reflectivity), ENOMEM, ECUDA. */
 int bart_mesh_upload(bart_ctx *ctx, const double *verts, int64_t nv,
                      const int32_t *tris, int64_t nf, const float *rho,
                      uint32_t flags, int32_t *mesh_id);
@@ -246,7 +247,8 @@ int bart_mesh_update(bart_ctx *ctx, int32_t mesh_id, const double *verts, const 
 int bart_mesh_clear(bart_ctx *ctx);
 
 /* Set the scene's instances (host array of n, copied).  Each mesh_id must
- * name an uploaded mesh.  Errors: EINVAL. */
+ * name an uploaded mesh; positions, velocities, rotations and rho_scale must
+ * be finite.  Errors: EINVAL. */
 int bart_scene_set(bart_ctx *ctx, const bart_instance *inst, int32_t n);
 
 /* Total facet count of the current scene (host out). */
@@ -299,7 +301,9 @@ int bart_mesh_dims(bart_ctx *ctx, int32_t mesh_id, int64_t *nv, int64_t *nf);
  * Errors: EINVAL (bad offsets), ESTATE (no instances). */
 int bart_scene_partition(bart_ctx *ctx, const int32_t *first, int32_t n_scenes);
 
-/* Set the radar (host struct, copied and validated).  Errors: EINVAL. */
+/* Set the radar (host struct, copied and validated: sizes, positive finite
+ * f0/slope/fs/Tc with Tc >= M/fs, finite antenna positions, flags 0 or 1,
+ * exclusive modes).  Errors: EINVAL. */
 int bart_radar_set(bart_ctx *ctx, const bart_radar *radar);
 
 /* Simulate one frame starting at absolute time t0 (Sec. 3.2):

@@ -422,6 +422,13 @@ int bart_mesh_upload(bart_ctx *ctx, const double *verts, int64_t nv, const int32
         if (tris[i] < 0 || tris[i] >= nv)
             return fail(BART_EINVAL, "bart_mesh_upload: tris[%lld]=%d out of [0,%lld)",
                         (long long)i, tris[i], (long long)nv);
+    for (int64_t i = 0; i < 3 * nv; ++i)
+        if (!std::isfinite(verts[i]))
+            return fail(BART_EINVAL, "bart_mesh_upload: verts[%lld] is not finite", (long long)i);
+    if (rho)
+        for (int64_t i = 0; i < nf; ++i)
+            if (!std::isfinite(rho[i]))
+                return fail(BART_EINVAL, "bart_mesh_upload: rho[%lld] is not finite", (long long)i);
     BART_TRY(set_device(ctx));
     if (ctx->n_meshes == (int)ctx->pool.size()) {
         MeshStore *m = new (std::nothrow) MeshStore();
@@ -497,6 +504,11 @@ int bart_scene_set(bart_ctx *ctx, const bart_instance *inst, int32_t n)
         for (int k = 0; k < 3; ++k)
             if (!std::isfinite(inst[i].pos[k]) || !std::isfinite(inst[i].vel[k]))
                 return fail(BART_EINVAL, "bart_scene_set: instance %d has a non-finite pose", i);
+        for (int k = 0; k < 9; ++k)
+            if (!std::isfinite(inst[i].rot[k]))
+                return fail(BART_EINVAL, "bart_scene_set: instance %d has a non-finite rotation", i);
+        if (!std::isfinite(inst[i].rho_scale))
+            return fail(BART_EINVAL, "bart_scene_set: instance %d has a non-finite rho_scale", i);
     }
     ctx->insts.assign(inst, inst + n);
     ctx->scene_first.clear();
@@ -583,8 +595,19 @@ int bart_radar_set(bart_ctx *ctx, const bart_radar *r)
         return fail(BART_EINVAL, "bart_radar_set: N=%d out of [1,32768]", r->N);
     if (r->P < 1 || r->P > BART_MAX_TX || r->Q < 1 || r->Q > BART_MAX_RX)
         return fail(BART_EINVAL, "bart_radar_set: P=%d Q=%d out of range", r->P, r->Q);
-    if (!(r->f0 > 0) || !(r->slope > 0) || !(r->fs > 0) || !(r->Tc > 0))
-        return fail(BART_EINVAL, "bart_radar_set: f0, slope, fs, Tc must be positive");
+    if (!(r->f0 > 0) || !(r->slope > 0) || !(r->fs > 0) || !(r->Tc > 0) ||
+        !std::isfinite(r->f0) || !std::isfinite(r->slope) || !std::isfinite(r->fs) ||
+        !std::isfinite(r->Tc))
+        return fail(BART_EINVAL, "bart_radar_set: f0, slope, fs, Tc must be positive and finite");
+    for (int a = 0; a < r->P + r->Q; ++a) {
+        const double *x = a < r->P ? r->tx[a] : r->rx[a - r->P];
+        if (!std::isfinite(x[0]) || !std::isfinite(x[1]) || !std::isfinite(x[2]))
+            return fail(BART_EINVAL, "bart_radar_set: %s %d has a non-finite position",
+                        a < r->P ? "TX" : "RX", a < r->P ? a : a - r->P);
+    }
+    if (r->intra_chirp_motion != 0 && r->intra_chirp_motion != 1)
+        return fail(BART_EINVAL, "bart_radar_set: intra_chirp_motion=%d (0 or 1)",
+                    r->intra_chirp_motion);
     if (r->Tc < (double)r->M / r->fs * (1.0 - 1e-12))
         return fail(BART_EINVAL, "bart_radar_set: Tc=%g shorter than M/fs=%g", r->Tc,
                     (double)r->M / r->fs);

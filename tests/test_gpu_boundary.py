@@ -187,3 +187,42 @@ def test_boundary_rejects_bad_modes(sim):
     rc = L.bart_simulate_adjoint(sim.ctx, 0.0, ctypes.c_void_p(g.data_ptr()), pkg.C128,
                                  ctypes.c_void_p(gv.data_ptr()), None)
     assert rc == pkg.BART_EINVAL
+
+
+def test_boundary_rejects_non_finite_inputs(sim):
+    """Non-finite vertices, reflectivities, instance rotations or
+    reflectivity scales, radar parameters and antenna positions are refused
+    with EINVAL before anything reaches the GPU; the context stays usable."""
+    L = pkg.load_library()
+    sc = sg.plate_scene(n=2, M=64, N=2)
+    m = sc.meshes[0]
+    mid = ctypes.c_int32()
+    bad_v = m.verts.copy()
+    bad_v[1, 2] = float("nan")
+    assert L.bart_mesh_upload(sim.ctx, bad_v.ctypes.data, m.verts.shape[0], m.tris.ctypes.data,
+                              m.tris.shape[0], None, 0, ctypes.byref(mid)) == pkg.BART_EINVAL
+    bad_r = np.ones(m.tris.shape[0], np.float32)
+    bad_r[0] = np.inf
+    assert L.bart_mesh_upload(sim.ctx, m.verts.ctypes.data, m.verts.shape[0], m.tris.ctypes.data,
+                              m.tris.shape[0], bad_r.ctypes.data, 0,
+                              ctypes.byref(mid)) == pkg.BART_EINVAL
+    sim.load_scene(sc)
+    for field, value in (("rot", float("nan")), ("rho_scale", float("inf"))):
+        arr = pkg.make_instances(sc.instances)
+        if field == "rot":
+            arr[0].rot[4] = value
+        else:
+            arr[0].rho_scale = value
+        assert L.bart_scene_set(sim.ctx, ctypes.cast(arr, ctypes.c_void_p), 1) == pkg.BART_EINVAL
+    for mutate in (lambda r: setattr(r, "Tc", float("inf")),
+                   lambda r: setattr(r, "fs", float("nan")),
+                   lambda r: r.tx[0].__setitem__(1, float("nan")),
+                   lambda r: r.rx[r.Q - 1].__setitem__(0, float("-inf")),
+                   lambda r: setattr(r, "intra_chirp_motion", 2)):
+        r = pkg.make_radar(sc.radar)
+        mutate(r)
+        assert L.bart_radar_set(sim.ctx, ctypes.byref(r)) == pkg.BART_EINVAL
+    # the refusals left the loaded scene intact
+    a = sim.simulate(pkg.PATH_FP64).cpu().numpy()
+    ref = oracle.Frame(sc).adc_full()
+    assert rel_l2(a, ref) <= 1e-9
