@@ -524,6 +524,38 @@ int bart_frame_host(bart_ctx *ctx, double t0, int32_t path, float *rdm_host,
  * pointer; synchronises the stream).  Errors: ESTATE (no frame simulated). */
 int bart_get_visibility(bart_ctx *ctx, uint8_t *state, int64_t *n_grazing);
 
+/* One internal node of the bounding-volume hierarchy the visibility rays
+ * traverse (Sec. 2.2 ray tracing; a Karras LBVH over the frame-start
+ * facets).  left/right >= 0 name internal nodes, a negative child c is the
+ * leaf of facet ~c.  Each child's box (FP32, rounded outward from the FP64
+ * vertices) is stored in its parent. */
+typedef struct bart_bvh_node {
+    float   lmin[3];
+    int32_t left;
+    float   lmax[3];
+    int32_t right;
+    float   rmin[3];
+    int32_t pad0;
+    float   rmax[3];
+    int32_t pad1;
+} bart_bvh_node;
+
+/* Host copy of the last frame's hierarchy, for host-side checks of its
+ * invariants (every facet under exactly one leaf, every child's box inside
+ * its slot, each scene's subtree holding exactly its own facets).
+ * Writes *n_nodes = F - 1 internal nodes (0 when F = 1), *n_facets = F and
+ * *n_scenes = S of that frame; with nodes, roots and tri all NULL nothing
+ * else is done (a size query).  Otherwise, host buffers: nodes (n_nodes
+ * bart_bvh_node, node 0 the root of the whole hierarchy), roots (S int32:
+ * the root node of each scene's subtree, ~facet for a one-facet scene) and
+ * tri (F x 9 float64: the frame-start world vertices the boxes enclose).
+ * Synchronises the stream.  No counterpart in the paper: a diagnostic of
+ * this library's own data structure.
+ * Errors: EINVAL (NULL size pointers, some but not all buffers NULL),
+ * ESTATE (no frame simulated), ECUDA. */
+int bart_get_bvh(bart_ctx *ctx, bart_bvh_node *nodes, int32_t *roots, double *tri,
+                 int64_t *n_nodes, int64_t *n_facets, int32_t *n_scenes);
+
 /* The virtual facets of the last frame's double-bounce paths (Sec. 2.2;
  * bart_radar.double_bounce): each is one fan piece (Pi_0, Pi_i, Pi_i+1) of
  * the part Pi_ab of facet b lit by TX p's reflection from facet a.  Host

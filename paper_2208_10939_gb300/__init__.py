@@ -40,7 +40,7 @@ EXPORTED = ["bart_last_error", "bart_version", "bart_create", "bart_destroy",
             "bart_simulate_adjoint_mixed",
             "bart_mesh_update", "bart_measure_peaks", "bart_inject_alloc_failure",
             "bart_selftest_wait_timeout", "bart_get_bounce_facets", "bart_get_dims",
-            "bart_mesh_dims"]
+            "bart_mesh_dims", "bart_get_bvh"]
 
 
 class BartError(RuntimeError):
@@ -182,6 +182,8 @@ def load_library() -> ctypes.CDLL:
         L.bart_form_rdm.argtypes = [P, P, I32, P]
         L.bart_frame_host.argtypes = [P, D, I32, P, ctypes.POINTER(bart_stats)]
         L.bart_get_visibility.argtypes = [P, P, ctypes.POINTER(I64)]
+        L.bart_get_bvh.argtypes = [P, P, P, P, ctypes.POINTER(I64), ctypes.POINTER(I64),
+                                   ctypes.POINTER(I32)]
         L.bart_get_bounce_facets.argtypes = [P, P, P, P, P, P, I64, ctypes.POINTER(I64)]
         L.bart_set_timing.argtypes = [P, I32]
         L.bart_get_timing.argtypes = [P, ctypes.POINTER(bart_timing)]
@@ -550,6 +552,26 @@ def bart_get_visibility(ctx: int, state, grazing: bool = False):
     return n.value if grazing else None
 
 
+def bart_get_bvh(ctx: int) -> dict:
+    """Host copy of the last frame's hierarchy: ``nodes`` (F - 1 records of
+    ``diagnostics.BVH_NODE_DTYPE``), ``roots`` (int32 per scene) and ``tri``
+    (F x 9 frame-start vertices); check it with ``diagnostics.check_bvh``."""
+    from .diagnostics import BVH_NODE_DTYPE
+    L = load_library()
+    nn, nf, ns = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+    _check(L.bart_get_bvh(ctx, None, None, None, ctypes.byref(nn), ctypes.byref(nf),
+                          ctypes.byref(ns)))
+    out = dict(nodes=np.zeros(int(nn.value), BVH_NODE_DTYPE),
+               roots=np.zeros(int(ns.value), np.int32), tri=np.zeros((int(nf.value), 9)))
+    if out["nodes"].size == 0:               # one facet: no internal node to copy into
+        out["nodes"] = np.zeros(1, BVH_NODE_DTYPE)
+    _check(L.bart_get_bvh(ctx, *(ctypes.c_void_p(out[k].ctypes.data)
+                                 for k in ("nodes", "roots", "tri")),
+                          ctypes.byref(nn), ctypes.byref(nf), ctypes.byref(ns)))
+    out["nodes"] = out["nodes"][:int(nn.value)]
+    return out
+
+
 def bart_get_bounce_facets(ctx: int) -> dict:
     """The last frame's double-bounce virtual facets (host numpy arrays):
     ``pab`` (V x 4: TX, first facet, second facet, side), ``tri`` (V x 9),
@@ -672,6 +694,8 @@ class Simulator:
         bart_scene_set(self.ctx, scene.instances)
         bart_radar_set(self.ctx, scene.radar, window)
         self.n_scenes = 1
+        self.scene_foff = [0, sum(int(scene.meshes[i.mesh_id].tris.shape[0])
+                                  for i in scene.instances)]
         self.radar = scene.radar
         self.t0 = float(getattr(scene, "t0", 0.0))
         self.n_facets = bart_scene_facets(self.ctx)
@@ -689,6 +713,10 @@ class Simulator:
             first.append(len(insts))
         bart_scene_set(self.ctx, insts)
         bart_scene_partition(self.ctx, first)
+        self.scene_foff = [0]
+        for sc in scenes:
+            self.scene_foff.append(self.scene_foff[-1] + sum(
+                int(sc.meshes[i.mesh_id].tris.shape[0]) for i in sc.instances))
         self.radar = scenes[0].radar
         bart_radar_set(self.ctx, self.radar, window)
         self.t0 = float(getattr(scenes[0], "t0", 0.0))
@@ -744,6 +772,13 @@ class Simulator:
         st = torch.empty((A, self.n_facets), dtype=torch.uint8, device=f"cuda:{self.device}")
         n = bart_get_visibility(self.ctx, st, grazing)
         return (st, n) if grazing else st
+
+    def bvh(self) -> dict:
+        """The last frame's hierarchy (bart_get_bvh) with the scenes' facet
+        offsets ``foff``, ready for ``diagnostics.check_bvh``."""
+        out = bart_get_bvh(self.ctx)
+        out["foff"] = list(self.scene_foff)
+        return out
 
     def bounce_facets(self) -> dict:
         """The last frame's double-bounce virtual facets (bart_get_bounce_facets)."""

@@ -130,6 +130,7 @@ struct bart_ctx {
     bool tables_dirty = true;   // mesh / instance tables changed since the last frame
     int64_t frame_F = 0;
     int frame_A = 0;
+    int frame_B = 1;            // scenes of the last frame's partition
 
     DevBuf<MeshDesc> d_meshes;
     DevBuf<InstDev> d_insts;
@@ -1141,6 +1142,7 @@ static int run_frame(bart_ctx *ctx, double t0, int32_t path, void *adc, int32_t 
     ctx->have_frame = true;
     ctx->frame_F = F;
     ctx->frame_A = A;
+    ctx->frame_B = B;
     if (stats) {
         std::vector<int32_t> cnt(O);
         unsigned long long ctr[5];
@@ -1536,6 +1538,36 @@ int bart_get_visibility(bart_ctx *ctx, uint8_t *state, int64_t *n_grazing)
         CUDA_TRY(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
         *n_grazing = (int64_t)g;
     }
+    return BART_OK;
+}
+
+int bart_get_bvh(bart_ctx *ctx, bart_bvh_node *nodes, int32_t *roots, double *tri,
+                 int64_t *n_nodes, int64_t *n_facets, int32_t *n_scenes)
+{
+    static_assert(sizeof(bart_bvh_node) == sizeof(bart::BvhNode), "bart_bvh_node layout");
+    g_err.clear();
+    if (!ctx || !n_nodes || !n_facets || !n_scenes)
+        return fail(BART_EINVAL, "bart_get_bvh: NULL argument");
+    if (!ctx->have_frame) return fail(BART_ESTATE, "bart_get_bvh: no frame simulated");
+    const int64_t F = ctx->frame_F;
+    const int B = ctx->frame_B;
+    *n_nodes = F > 1 ? F - 1 : 0;
+    *n_facets = F;
+    *n_scenes = B;
+    if (!nodes && !roots && !tri) return BART_OK;
+    if (!nodes || !roots || !tri) return fail(BART_EINVAL, "bart_get_bvh: NULL buffer");
+    BART_TRY(set_device(ctx));
+    if (F > 1)
+        CUDA_TRY(cudaMemcpyAsync(nodes, ctx->nodes.p, (size_t)(F - 1) * sizeof(bart::BvhNode),
+                                 cudaMemcpyDeviceToHost, ctx->stream), "bvh node copy");
+    if (B > 1)
+        CUDA_TRY(cudaMemcpyAsync(roots, ctx->d_root.p, (size_t)B * sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, ctx->stream), "bvh root copy");
+    else
+        roots[0] = F > 1 ? 0 : ~0;
+    CUDA_TRY(cudaMemcpyAsync(tri, ctx->tri64.p, (size_t)F * 9 * sizeof(double),
+                             cudaMemcpyDeviceToHost, ctx->stream), "facet vertex copy");
+    CUDA_TRY(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize");
     return BART_OK;
 }
 
