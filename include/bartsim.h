@@ -452,6 +452,10 @@ int bart_rdm_adjoint(bart_ctx *ctx, const void *adc, int32_t dtype, const float 
  * overwrites the part it reads before reading it, so nothing carries over);
  * calls that overlap on the GPU, from any thread or stream, race on it and
  * must be serialised by the caller.  The call calls no cudaMalloc/cudaFree.
+ * Without a context there is no device status word: the Doppler pass's
+ * bounded waits for its tile copies (which bart_form_rdm reports through
+ * bart_sync as BART_ETIMEOUT) would, if one ever expired, leave the map
+ * incomplete without an error code here.
  * Errors: EINVAL, ECUDA. */
 int bart_form_rdm_static(const void *adc, int32_t dtype, int32_t O, int32_t N,
                          int32_t M, int32_t window, float *rdm, void *stream);
