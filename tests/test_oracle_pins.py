@@ -562,6 +562,43 @@ def test_cfar_brute_force_window():
     assert det[9, 3] and not np.isfinite(thr[1, 0])
 
 
+@pytest.mark.parametrize("n_el,bins", [(12, 512), (7, 96)])
+def test_angle_spectrum_is_the_zero_padded_fft_on_a_half_wave_ula(n_el, bins):
+    """Eq. 6 on a uniform half-wavelength array is an FFT across the
+    elements: with x_o = o lambda/2 and s_i = -1 + 2i/bins the steering phase
+    is pi o s_i = -pi o + 2 pi o i/bins, so the spectrum is
+    |bins * ifft(Y_o (-1)^o, bins)|^2 (numpy's inverse FFT, zero padded)."""
+    rng = np.random.default_rng(n_el)
+    lam = 3.9e-3
+    Y = rng.normal(size=n_el) + 1j * rng.normal(size=n_el)
+    x = np.arange(n_el) * lam / 2
+    want = np.abs(bins * np.fft.ifft(Y * (-1.0) ** np.arange(n_el), bins)) ** 2
+    got = oracle.angle_spectrum(Y, x, lam, bins)
+    assert np.allclose(got, want, rtol=1e-10, atol=1e-10 * want.max())
+
+
+def test_angle_spectrum_of_a_plane_wave_is_the_array_factor():
+    """A plane wave from sin(theta) = s0 on an N-element ULA of spacing d
+    (element phases exp(-j 2 pi x_o s0 / lambda)) gives the Dirichlet array
+    factor |sin(N pi d u / lambda) / sin(pi d u / lambda)|^2, u = s - s0, with
+    its main lobe (N^2) at s0 and its first nulls at u = +-lambda/(N d)."""
+    lam, d, n_el, bins = 3.9e-3, 3.9e-3 / 2, 16, 1024
+    s0 = 0.5 + 2.0 / bins * 3                      # on the grid
+    x = np.arange(n_el) * d
+    Y = np.exp(-2j * np.pi * x * s0 / lam)
+    s = -1.0 + 2.0 * np.arange(bins) / bins
+    u = s - s0
+    num = np.sin(n_el * np.pi * d * u / lam)
+    den = np.sin(np.pi * d * u / lam)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        af = np.where(np.abs(den) < 1e-12, float(n_el) ** 2, (num / den) ** 2)
+    got = oracle.angle_spectrum(Y, x, lam, bins)
+    assert np.allclose(got, af, rtol=1e-9, atol=1e-9 * n_el ** 2)
+    assert int(np.argmax(got)) == int(round((s0 + 1.0) * bins / 2))
+    null = int(round((s0 + lam / (n_el * d) + 1.0) * bins / 2))
+    assert got[null] <= 1e-9 * n_el ** 2
+
+
 def test_point_cloud_recovers_target_position():
     """A point-like plate at 14 m, 30 deg azimuth, seen by a 12-element
     virtual ULA: the strongest detection lies at the Eq. 4 range and the
