@@ -599,6 +599,29 @@ def test_angle_spectrum_of_a_plane_wave_is_the_array_factor():
     assert got[null] <= 1e-9 * n_el ** 2
 
 
+@pytest.mark.parametrize("tdm", [False, True])
+def test_point_cloud_rate_of_a_receding_target(tdm):
+    """Eq. 5: a point target receding at v, placed on Doppler bin k
+    (v = k lambda_c / (2 N T_r), T_r = T_c or, with time-division MIMO,
+    P T_c), is reported at range rate +v (positive receding) and at its Eq. 4
+    range; a sign error or a wrong repetition period moves it by bins."""
+    P, N, k = 2, 32, 3
+    sc = sg.point_target_scene(12.0, 0.0, M=128, N=N, P=P, Q=2, edge=0.6e-3)
+    r = sc.radar
+    r.tdm = tdm
+    B = r.slope * r.M / r.fs
+    lam_c = C0 / (r.f0 + 0.5 * B)
+    Tr = r.Tc * (P if tdm else 1)
+    v = k * lam_c / (2 * N * Tr)
+    sc.instances[0].vel = np.array([0.0, v, 0.0])
+    pts = oracle.point_cloud(oracle.Frame(sc).adc_full(), r, pfa=1e-4)
+    best = max(pts, key=lambda p: p[5])
+    assert abs(best[1] - v) < 1e-9 * v
+    assert best[7] == N // 2 + k
+    r_res = C0 * r.fs / (2 * r.slope * r.M)
+    assert abs(best[0] - 12.0) < r_res
+
+
 def test_point_cloud_recovers_target_position():
     """A point-like plate at 14 m, 30 deg azimuth, seen by a 12-element
     virtual ULA: the strongest detection lies at the Eq. 4 range and the
