@@ -16,6 +16,11 @@
 // decisions of a plain FP32 Moller-Trumbore without error bounds on cases
 // the FP64 test does not call grazing (the adversarial cases must provoke
 // them, or they would not probe the margins).
+// Also: the FP32 slab test (slab_hit) against the triangle's box -- rounded
+// outward from the FP64 vertices and padded by 1e-4 + 4e-6 max|coordinate|,
+// as the world-facet kernel builds it -- never drops a segment that the
+// FP64 test finds hitting or grazing the triangle (printed: slab_drops of
+// the hitting or grazing cases).
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -42,7 +47,7 @@ static double sym() { return 2.0 * uni() - 1.0; }                            // 
 static double logu(double lo, double hi) { return lo * std::pow(hi / lo, uni()); }
 
 struct Tally {
-    long cases = 0, violations = 0, decided = 0, naive_wrong = 0;
+    long cases = 0, violations = 0, decided = 0, naive_wrong = 0, slab_drops = 0, slab_checked = 0;
 };
 
 // plain FP32 test: 0 outside, 2 strictly inside, no rounding bounds
@@ -88,6 +93,29 @@ static void check(const double *tri, const double *O, const double *D, Tally &t)
     const int pre = mt_fp32_classify(t0, t1, t2, o, d, Dm, Om);
     const int exact = mt_segment(O, D, tri);
     if (exact != 1 && naive_fp32(f, f + 3, f + 6, o, d) != exact) ++t.naive_wrong;
+    if (exact != 0) {
+        float bmin[3], bmax[3], inv[3], mx = 0.f;
+        for (int r = 0; r < 3; ++r) {
+            const double lo = std::fmin(std::fmin(tri[r], tri[3 + r]), tri[6 + r]);
+            const double hi = std::fmax(std::fmax(tri[r], tri[3 + r]), tri[6 + r]);
+            float a = (float)lo, b = (float)hi;
+            mx = std::fmax(mx, std::fmax(std::fabs(a), std::fabs(b)));
+            if ((double)a > lo) a = std::nextafter(a, -INFINITY);
+            if ((double)b < hi) b = std::nextafter(b, INFINITY);
+            bmin[r] = a;
+            bmax[r] = b;
+        }
+        const float pad = 1e-4f + 4e-6f * mx;
+        for (int r = 0; r < 3; ++r) {
+            bmin[r] -= pad;
+            bmax[r] += pad;
+            float dd = d[r];
+            if (std::fabs(dd) < 1e-30f) dd = std::copysign(1e-30f, dd);
+            inv[r] = 1.0f / dd;
+        }
+        ++t.slab_checked;
+        if (!slab_hit(bmin, bmax, o, inv)) ++t.slab_drops;
+    }
     ++t.cases;
     if (pre != 1) {
         ++t.decided;
@@ -162,7 +190,7 @@ int main()
         for (int r = 0; r < 3; ++r) O[r] = tri[r] + u * e1[r] + v * e2[r] - tp * D[r];
         check(tri, O, D, t);
     }
-    std::printf("cases %ld violations %ld decided %ld naive_wrong %ld\n", t.cases, t.violations,
-                t.decided, t.naive_wrong);
-    return t.violations == 0 ? 0 : 1;
+    std::printf("cases %ld violations %ld decided %ld naive_wrong %ld slab_drops %ld of %ld\n",
+                t.cases, t.violations, t.decided, t.naive_wrong, t.slab_drops, t.slab_checked);
+    return t.violations == 0 && t.slab_drops == 0 ? 0 : 1;
 }

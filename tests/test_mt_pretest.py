@@ -10,7 +10,11 @@ functions from ``geom64.cuh`` unchanged as host code and compares them on
 1.6M seeded segments, most of them adversarial (through points 1e-13 ..
 1e-3 from an edge, ends near the plane, nearly parallel); a plain FP32 test
 without the bounds gets many of the same cases wrong, which shows that they
-probe the margins."""
+probe the margins.  The same run checks that the FP32 slab test against the
+padded, outward-rounded box never drops a segment that hits or grazes the
+triangle (the hierarchy traversal may only over-report candidates); with
+the pad left out, about four thousand of the 0.8M hitting or grazing
+segments are dropped, so the cases reach the pad's scale."""
 import os
 import re
 import shutil
@@ -33,10 +37,12 @@ def test_fp32_pretest_decides_only_what_fp64_decides(tmp_path):
                     "-I", CUDA_INC, os.path.join(ROOT, "tests", "mt_pretest_check.cpp"),
                     "-o", str(exe)], check=True)
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
-    m = re.search(r"cases (\d+) violations (\d+) decided (\d+) naive_wrong (\d+)", r.stdout)
+    m = re.search(r"cases (\d+) violations (\d+) decided (\d+) naive_wrong (\d+) "
+                  r"slab_drops (\d+) of (\d+)", r.stdout)
     assert m, r.stdout + r.stderr
-    cases, violations, decided, naive_wrong = map(int, m.groups())
+    cases, violations, decided, naive_wrong, drops, slab_cases = map(int, m.groups())
     assert violations == 0, r.stdout
+    assert drops == 0 and slab_cases > 100_000, r.stdout
     assert r.returncode == 0
     assert cases == 1_600_000 and decided > 100_000
     assert naive_wrong > 10_000
