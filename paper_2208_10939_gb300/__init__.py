@@ -262,10 +262,10 @@ def _device_buffer(t, name: str, d: "bart_dims", numel: Optional[int], dtype=Non
 
 
 def _host_buffer(a, name: str, numel: Optional[int]) -> None:
-    """Raise unless ``a`` is a C-contiguous float32 host array (numpy or a
-    CPU tensor) of ``numel`` elements (when given)."""
+    """Raise unless ``a`` is a writable C-contiguous float32 host array
+    (numpy or a CPU tensor) of ``numel`` elements (when given)."""
     if isinstance(a, np.ndarray):
-        ok = a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]
+        ok = a.dtype == np.float32 and a.flags["C_CONTIGUOUS"] and a.flags["WRITEABLE"]
         n = a.size
     else:
         import torch
@@ -273,7 +273,7 @@ def _host_buffer(a, name: str, numel: Optional[int]) -> None:
               and a.dtype == torch.float32)
         n = a.numel() if isinstance(a, torch.Tensor) else -1
     if not ok:
-        raise ValueError(f"{name} must be a C-contiguous float32 host array")
+        raise ValueError(f"{name} must be a writable C-contiguous float32 host array")
     if numel is not None and n != numel:
         raise ValueError(f"{name} has {n} elements; the context's shapes need {numel}")
 

@@ -179,8 +179,10 @@ def test_host_rdm_of_a_partitioned_frame(fake):
     lib = fake(scenes=S)
     pkg.bart_frame_host(1, 0.0, pkg.PATH_MIXED, np.empty((S, M, N), np.float32))
     pkg.bart_frame_host(1, 0.0, pkg.PATH_MIXED, torch.empty((S, M, N), dtype=F32))
+    frozen = np.empty((S, M, N), np.float32)
+    frozen.flags["WRITEABLE"] = False
     for bad in (np.empty((M, N), np.float32), np.empty((S, M, N), np.float64),
-                np.empty((S, N, M), np.float32).transpose(0, 2, 1)):
+                np.empty((S, N, M), np.float32).transpose(0, 2, 1), frozen):
         with pytest.raises(ValueError):
             pkg.bart_frame_host(1, 0.0, pkg.PATH_MIXED, bad)
     assert lib.calls == ["bart_frame_host"] * 2
