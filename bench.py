@@ -259,6 +259,19 @@ def cpu_baseline(scene, seconds: float, adc=None, others=None) -> dict:
                      f"oracle synthesis); oracle visibility of the frame (its own BVH) took "
                      f"{t_vis:.1f} s, untimed",
            "frame_s_extrapolated": frame_terms / rate + t_vis}
+    # the same oracle on one host core, on the first entries of the sample
+    # (about a quarter of the sample's time)
+    n_all = oracle.num_threads()
+    e1 = e[:max(16, E // (4 * max(1, n_all)))]
+    oracle.set_threads(1)
+    try:
+        t = time.perf_counter()
+        fr.adc_entries(e1)
+        dt1 = time.perf_counter() - t
+    finally:
+        oracle.set_threads(n_all)
+    out["one_core"] = {"value": int(per_ch[e1[:, 0]].sum()) / dt1, "unit": UNIT, "cores": 1,
+                       "sample": f"the first {len(e1)} of those entries"}
     if adc is not None:
         got = adc[e[:, 0], e[:, 1], e[:, 2]].astype(np.complex128)
         out["gpu_frame_rel_l2_vs_oracle"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))

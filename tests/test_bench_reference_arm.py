@@ -55,3 +55,20 @@ def test_reference_arm_under_torchrun_prints_once():
     assert len(lines) == 1
     _check_line(lines[0])
     assert lines[0]["n_gpus"] == 2
+
+
+def test_cpu_baseline_leg_reports_all_cores_and_one():
+    """bench.py's cpu_baseline leg on a small frame: the oracle's rate on
+    all host cores and on one, and the sampled entries' error of a cube
+    (here the oracle's own cube, so zero)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    import scenegen as sg
+    sc = sg.small_car_scene(ntri=600, M=64, N=4, P=2, Q=2)
+    cube = oracle.Frame(sc).adc_full()
+    out = bench.cpu_baseline(sc, 0.5, cube)
+    assert out["kind"] == "oracle" and out["value"] > 0 and out["cores"] == oracle.num_threads()
+    assert out["one_core"]["cores"] == 1 and out["one_core"]["value"] > 0
+    assert out["gpu_frame_rel_l2_vs_oracle"] == 0.0
+    assert oracle.num_threads() == out["cores"]          # the thread count is restored
