@@ -1,13 +1,20 @@
 """The seeded synthetic workloads have the sizes and structure the design
 states (CPU only): triangle counts, arrays, chirp profiles, lanes, speeds,
 ranges, and determinism per seed.  The radar profiles follow Table 2's rule
-T_c = M / fs + 10 us, with v_max = lambda_c / (4 T_c)."""
+T_c = M / fs + 10 us, with v_max = lambda_c / (4 T_c); the radar height and
+the lane centres are Table 1's (tests/golden/table1.json)."""
+import json
+import os
+
 import numpy as np
 import pytest
 
 import scenegen as sg
 
 C0 = sg.C0
+TABLE1 = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                     "table1.json")))
+LANES = TABLE1["lane_centres_x_m"]
 
 
 def n_tris(scene) -> int:
@@ -44,10 +51,11 @@ def test_moving_sedan_workload():
     lam0 = C0 / r.f0
     assert np.allclose(spacing(r.tx), 2 * lam0) and np.allclose(spacing(r.rx), lam0 / 2)
     centre = np.asarray(r.tx, np.float64).mean(axis=0)
+    assert centre[2] == TABLE1["radar_altitude_m"]
     ins = sc.instances[0]
     los = centre - np.asarray(ins.pos, np.float64)
     assert np.linalg.norm(los) == pytest.approx(30.0, abs=0.05)
-    assert ins.pos[0] == pytest.approx(2.0)
+    assert ins.pos[0] == pytest.approx(LANES[0])
     v = np.asarray(ins.vel, np.float64)
     assert np.linalg.norm(v) == pytest.approx(10.0, rel=1e-12)
     assert v @ los / np.linalg.norm(los) == pytest.approx(10.0, rel=1e-12)   # toward the radar
@@ -64,6 +72,8 @@ def test_intersection_workload():
     assert (r.slope, r.fs) == (12.5e12, 10.24e6)
     lam0 = C0 / r.f0
     assert np.allclose(spacing(r.tx), 8 * lam0) and np.allclose(spacing(r.rx), lam0 / 2)
+    assert np.all(np.asarray(r.tx, np.float64)[:, 2] == TABLE1["radar_altitude_m"])
+    assert np.diff(LANES) == pytest.approx([TABLE1["lane_width_m"]] * 2)
     names = [sc.meshes[i.mesh_id].name for i in sc.instances]
     ground = [i for i, n in zip(sc.instances, names) if n.startswith("ground")]
     assert len(ground) == 1 and sc.meshes[ground[0].mesh_id].tris.shape[0] == 2 * 158 * 158
@@ -76,7 +86,7 @@ def test_intersection_workload():
         cls = next(c for c in per_class if m.name.startswith(c))
         assert abs(m.tris.shape[0] - per_class[cls]) <= 0.01 * per_class[cls]
         x, y = float(ins.pos[0]), float(ins.pos[1])
-        assert min(abs(x - c) for c in (2.0, 5.75, 9.5)) < 1e-12
+        assert min(abs(x - c) for c in LANES) < 1e-12
         assert 10.0 <= y <= 80.0
         assert abs(ins.vel[1]) <= 15.0 and ins.vel[0] == 0.0 and ins.vel[2] == 0.0
         w = (np.asarray(ins.rot, np.float64).reshape(3, 3) @ m.verts.T).T + ins.pos
@@ -96,6 +106,7 @@ def test_dataset_scene_workload(index):
     assert (r.P, r.Q, r.N, r.M) == (3, 4, 128, 256)
     for ins in sc.instances:
         assert float(ins.pos[1]) >= 25.0
+        assert min(abs(float(ins.pos[0]) - c) for c in LANES) < 1e-12
         assert -10.0 <= float(ins.vel[1]) <= -0.5               # approaching
     assert n_tris(again) == n_tris(sc)
     for a, b in zip(sc.meshes, again.meshes):
